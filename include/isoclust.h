@@ -1,0 +1,210 @@
+/*
+ * isoclust.h -- C ABI of the GB300 (sm_103a) isoperimetric clustering hot path.
+ *
+ * Method: Javadi & Ashkboos, "An Efficient Parallel Data Clustering Algorithm
+ * Using Isoperimetric Number of Trees" (arXiv 1702.04739):
+ *   Section 2.1, eq. phi / eq. omega / eq. potential / eq. cost / eq. MISO,
+ *   Section 2.2 (Algorithm 1: decision, Algorithm 2: bisection, pipeline
+ *   steps 1-5), Section 3.5 (minimum spanning tree, global min/sum
+ *   reductions), Section 3.6 (Cut / eta arrays, Algorithm 4: labels by an
+ *   exclusive scan over Cut).
+ *
+ * Conventions shared by every entry point
+ *   - Array arguments are DEVICE pointers owned by the caller, row-major and
+ *     densely packed, unless stated otherwise.  The library reads inputs,
+ *     writes outputs, and never frees or retains either.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  All work is queued on it; every call synchronises `stream`
+ *     once before it returns so that the status it returns is final.
+ *   - Internal scratch memory is allocated by the library on the current
+ *     device, cached per device and reused by later calls (grow-only).  Calls
+ *     on the same device from several host threads are serialised.
+ *   - No call throws.  On a non-OK status the outputs are unspecified and
+ *     isoclust_last_error() holds a one-line reason (per host thread).
+ *   - Indices are 0-based.  n is limited to 2^31 - 2 points.
+ *
+ * Readings of the paper fixed by this library (each is applied identically by
+ * every entry point):
+ *   K  distance key: d2(i,j) = sum_t (x_it - x_jt)^2 evaluated in FP64 with
+ *      t ascending and separately rounded subtract, multiply, add (no FMA);
+ *      edges are ordered by (d2, min(i,j), max(i,j)), a strict total order,
+ *      so the minimum spanning tree (Section 2.2 step 2) is unique.
+ *   W  phi(e) = exp(-sqrt(d2)/sigma) (eq. phi); omega_i sums phi(x_i,x_j)
+ *      over all j != i (eq. omega; `include_self` adds the j = i term);
+ *      p_i = alpha * sum_{j != i} ||x_i - x_j|| (eq. potential).
+ *   B  the tree is rooted at `root`; Algorithm 1 visits the reverse of the
+ *      breadth-first order whose children are taken in ascending index, so
+ *      siblings fold into their parent in descending index order.
+ *   S  the bisection of Algorithm 2 is run to the last bit: beta is the
+ *      smallest non-negative double N at which Algorithm 1 answers YES.
+ *   L  cluster j (0-based) is the (j+1)-th cut vertex of Algorithm 1 at beta
+ *      together with every vertex joined into it; vertices in none of the k
+ *      sets are residual (label -1, residual flag 1).  i_k = cost of the k
+ *      sets (eq. cost) = MISO_k of the weighted tree.
+ */
+#ifndef ISOCLUST_H
+#define ISOCLUST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ISOCLUST_ABI_VERSION 1
+
+/* Status codes returned by every entry point. */
+typedef enum {
+    ISOCLUST_OK = 0,
+    ISOCLUST_ERR_INVALID_ARG = 1,   /* bad size, pointer, option or malformed tree */
+    ISOCLUST_ERR_K_GT_N = 2,        /* more clusters requested than points      */
+    ISOCLUST_ERR_NONFINITE = 3,     /* NaN or Inf in X (found on the device)    */
+    ISOCLUST_ERR_OOM = 4,           /* scratch allocation failed                */
+    ISOCLUST_ERR_CUDA = 5,          /* a CUDA runtime call failed               */
+    ISOCLUST_ERR_TIMEOUT = 6,       /* a bounded device wait ran out            */
+    ISOCLUST_ERR_NO_SOLUTION = 7,   /* no finite N makes Algorithm 1 answer YES */
+    ISOCLUST_ERR_INTERNAL = 8       /* an internal consistency check failed     */
+} isoclust_status;
+
+/* Element type of X. */
+enum { ISOCLUST_F32 = 0, ISOCLUST_F64 = 1 };
+
+/* omega_mode values. */
+enum {
+    ISOCLUST_OMEGA_FULL = 0,   /* eq. omega: sum over all j != i (default)          */
+    ISOCLUST_OMEGA_TREE = 1    /* sum of phi over the tree edges incident to x_i    */
+};
+
+/* precision values: arithmetic of the Boruvka candidate sweep.  Every path
+ * ends in the same FP64 key comparison, so all give the identical tree. */
+enum {
+    ISOCLUST_PREC_AUTO = 0,    /* FP64 sweep for F64 input, FP32 + FP64 recheck for F32 */
+    ISOCLUST_PREC_FP64 = 1,    /* FP64 sweep (exact keys directly)                       */
+    ISOCLUST_PREC_FP32 = 2     /* FP32 candidates, FP64 recheck inside a proven margin   */
+};
+
+typedef struct {
+    double alpha;               /* eq. potential scale; 0 (default) means p == 0       */
+    int32_t omega_mode;         /* ISOCLUST_OMEGA_*, default FULL                       */
+    int32_t precision;          /* ISOCLUST_PREC_*, default AUTO                        */
+    int32_t root;               /* root vertex of the tree (default 0)                  */
+    int32_t include_self;       /* 1: omega and p include the j = i term (default 0)   */
+    uint64_t spin_limit;        /* bound on every device-side wait loop (0 = default)  */
+} isoclust_opts;
+
+/* Default options (alpha 0, full-graph omega, AUTO precision, root 0). */
+isoclust_opts isoclust_opts_default(void);
+
+/* One-line description of the last non-OK status on this host thread. */
+const char *isoclust_last_error(void);
+
+/* Static name of a status code. */
+const char *isoclust_status_string(isoclust_status s);
+
+/* ABI version of the loaded library (ISOCLUST_ABI_VERSION). */
+int32_t isoclust_abi_version(void);
+
+/*
+ * isoclust_cluster_mst -- Section 2.2 steps 1-2 (and Section 3.5): the exact
+ * Euclidean minimum spanning tree of the n points under key K, found by a
+ * fused tiled distance + Boruvka min-outgoing-edge sweep and GPU union-find;
+ * the n x n matrix is never stored.
+ *   X       n x d points, dtype ISOCLUST_F32 or ISOCLUST_F64 (device).
+ *   edge_u, edge_v  [n-1] int32 (device, written): edge endpoints with
+ *           edge_u < edge_v.
+ *   edge_d2 [n-1] double (device, written): d2 of the edge (reading K).
+ *   Edges are written in increasing key order (d2, edge_u, edge_v).
+ * Errors: n < 2, d < 1, NULL pointers, bad dtype/options -> INVALID_ARG;
+ *         NaN/Inf in X -> NONFINITE.
+ */
+isoclust_status isoclust_cluster_mst(const void *X, int64_t n, int32_t d, int32_t dtype,
+                                     const isoclust_opts *opts,
+                                     int32_t *edge_u, int32_t *edge_v, double *edge_d2,
+                                     void *stream);
+
+/*
+ * isoclust_vertex_weights -- eq. omega and eq. potential (reading W) for all
+ * n points: omega[i] = sum_{j != i} exp(-||x_i - x_j|| / sigma) and
+ * p[i] = alpha * sum_{j != i} ||x_i - x_j||, in FP64-grade arithmetic.
+ *   omega [n] double (device, written); p [n] double (device, written) or
+ *   NULL when alpha == 0 is not needed.  opts->omega_mode is ignored here
+ *   (this is the full-graph form).
+ * Errors: as isoclust_cluster_mst, plus sigma <= 0 or non-finite -> INVALID_ARG.
+ */
+isoclust_status isoclust_vertex_weights(const void *X, int64_t n, int32_t d, int32_t dtype,
+                                        double sigma, const isoclust_opts *opts,
+                                        double *omega, double *p, void *stream);
+
+/*
+ * isoclust_tree_isoperimetric -- Algorithm 2 around Algorithm 1 (Section
+ * 2.2) computed as in Algorithm 4 (Section 3.6) on a rooted weighted tree:
+ * the exact k-th isoperimetric number MISO_k(T) and its minimising
+ * k-subpartition (readings B, S, L).
+ *   parent  [n] int32 (device): parent vertex; exactly one entry is -1 (the
+ *           root).  Must describe a tree, else INVALID_ARG.
+ *   phi_par [n] double (device): phi of the edge (v, parent[v]); the root's
+ *           entry is ignored.  Must be >= 0 and finite.
+ *   omega   [n] double (device): vertex weights, > 0 and finite.
+ *   p       [n] double (device) or NULL (p == 0): potentials, >= 0.
+ *   k       number of sets, 1 <= k <= n.
+ *   labels  [n] int32 (device, written): cluster 0..k-1 or -1 (residual).
+ *   residual[n] uint8 (device, written): 1 iff labels == -1.
+ *   i_k     [1] double (device, written): MISO_k(T) = cost of the k sets.
+ *   opts    may be NULL (defaults); opts->root is ignored (the tree's own
+ *           root is used).
+ * Errors: n < 1, k < 1, NULL pointers, malformed tree -> INVALID_ARG;
+ *         k > n -> K_GT_N; NaN/Inf or negative weights -> NONFINITE /
+ *         INVALID_ARG; no finite threshold -> NO_SOLUTION.
+ */
+isoclust_status isoclust_tree_isoperimetric(int64_t n, const int32_t *parent,
+                                            const double *phi_par, const double *omega,
+                                            const double *p, int32_t k,
+                                            const isoclust_opts *opts,
+                                            int32_t *labels, uint8_t *residual, double *i_k,
+                                            void *stream);
+
+/*
+ * isoclust_cluster -- the whole hot path (Section 2.2 steps 1-5, Section 3):
+ * minimum spanning tree of X, phi on its edges, omega (and p), the rooted
+ * tree's global min/sum statistics, the bisection of Algorithm 2 with the
+ * level-parallel Algorithm 1, and the labels of Algorithm 4.
+ *   X       n x d points (device), dtype ISOCLUST_F32 or ISOCLUST_F64.
+ *   k       number of clusters, 1 <= k <= n.  sigma > 0 (eq. phi).
+ *   labels  [n] int32, residual [n] uint8, i_k [1] double (device, written)
+ *           as in isoclust_tree_isoperimetric.
+ * Errors: as isoclust_cluster_mst and isoclust_vertex_weights; k > n -> K_GT_N.
+ */
+isoclust_status isoclust_cluster(const void *X, int64_t n, int32_t d, int32_t dtype,
+                                 int32_t k, double sigma, const isoclust_opts *opts,
+                                 int32_t *labels, uint8_t *residual, double *i_k,
+                                 void *stream);
+
+/*
+ * isoclust_cluster_detail -- isoclust_cluster that also returns the
+ * intermediate results of the path (every output pointer may be NULL):
+ *   parent [n] int32, phi_par [n] double   the MST rooted at opts->root
+ *   omega [n] double, p [n] double         the vertex weights used
+ *   beta [1] double                        the threshold of reading S
+ *   edge_u, edge_v [n-1] int32, edge_d2 [n-1] double  the MST edges (key order)
+ */
+isoclust_status isoclust_cluster_detail(const void *X, int64_t n, int32_t d, int32_t dtype,
+                                        int32_t k, double sigma, const isoclust_opts *opts,
+                                        int32_t *labels, uint8_t *residual, double *i_k,
+                                        int32_t *parent, double *phi_par, double *omega,
+                                        double *p, double *beta,
+                                        int32_t *edge_u, int32_t *edge_v, double *edge_d2,
+                                        void *stream);
+
+/* Per-stage device times (milliseconds, CUDA events on the call's stream)
+ * of the last isoclust_cluster / _detail call on this host thread:
+ * t[0] validation, t[1] weights, t[2] MST, t[3] tree orientation + stats,
+ * t[4] bisection, t[5] labels.  counts[0] = Boruvka rounds, counts[1] =
+ * rows rescanned after a candidate-margin overflow, counts[2] = Algorithm-1
+ * passes, counts[3] = tree depth.  Either pointer may be NULL. */
+void isoclust_last_profile(double *t_ms6, int64_t *counts4);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ISOCLUST_H */
