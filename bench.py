@@ -1,0 +1,316 @@
+#!/usr/bin/env python3
+"""Benchmark of the isoperimetric clustering hot path on GB300.
+
+One step = one call of isoclust_cluster on the 100,000-point, d = 64
+anisotropic-blob workload (FP32 storage, k = 20, sigma = 1): minimum spanning
+tree, vertex weights, tree orientation, the bisection of Algorithm 2 and the
+labels.  Inputs are resident in HBM; L2 is flushed (a 256 MiB write) before
+every step inside the timed region.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+N > 1 (torchrun, one rank per GPU): every rank clusters its own independent
+point set (replicas; the path has no cross-GPU exchange), value = total
+points over the slowest rank's time.  --impl reference times the FP64 CPU
+oracle on the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "points/s end-to-end"
+UNIT = "points/s"
+WORKLOAD = "blobs_n100k_d64"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FP32_LANES_PER_SM = 128
+
+
+def _peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+            "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle
+def _oracle_time(X, k, sigma, n_sample, threads):
+    import oracle
+    oracle.build()
+    oracle.set_threads(threads)
+    Xs = np.ascontiguousarray(X[:n_sample])
+    t0 = time.perf_counter()
+    oracle.cluster(Xs, k, sigma)
+    return time.perf_counter() - t0
+
+
+def _cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(X, k, sigma, n_sample=30000):
+    """The oracle as it stands, on a bounded sample, scaled to full n by the
+    O(n^2) cost of the path (all pairs for omega, Prim's n min-reductions)."""
+    n = X.shape[0]
+    cores = _cpu_cores()
+    t = _oracle_time(X, k, sigma, n_sample, cores)
+    t_full = t * (n / n_sample) ** 2
+    return {"value": n / t_full, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {n_sample} of the {n} points (full pipeline: Prim MST, omega, Algorithms 1-2) took "
+                      f"{t:.2f} s on {cores} threads; value = n / (t * (n/{n_sample})^2), the O(n^2) cost law"}
+
+
+def run_reference(args, X, k, sigma):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    steps_total = args.steps + args.warmup
+    n = X.shape[0]
+    n_sample = int(min(30000, max(5000, 30000 * (8.0 / max(steps_total, 1)) ** 0.5)))
+    cores = _cpu_cores()
+    for _ in range(args.warmup):
+        _oracle_time(X, k, sigma, n_sample, cores)
+    times = [_oracle_time(X, k, sigma, n_sample, cores) for _ in range(args.steps)]
+    t = sum(times) / len(times)
+    value = n / (t * (n / n_sample) ** 2)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1000.0 * (n / n_sample) ** 2,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "d": X.shape[1], "k": k, "sigma": sigma},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"each step: oracle on the first {n_sample} points, {t:.2f} s mean; "
+                                   f"scaled to n={n} by the O(n^2) cost law"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n", type=int, default=0,
+                    help="points of the same generator (profiling of a smaller case); default: the full 100,000")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gb300":
+        args.warmup = 3
+
+    from paper_1702_04739_gb300 import workloads
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    X, k, sigma = workloads.make(WORKLOAD, seed=rank)
+    if args.n:
+        X = workloads.blobs_anisotropic(seed=rank, n=args.n)[0]
+    if args.impl == "reference":
+        return run_reference(args, X, k, sigma)
+
+    import torch
+    from paper_1702_04739_gb300 import isoclust
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    n, d = X.shape
+    Xd = torch.from_numpy(X).to(dev)
+    labels = torch.empty(n, dtype=torch.int32, device=dev)
+    residual = torch.empty(n, dtype=torch.uint8, device=dev)
+    ik = torch.empty(1, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        flush.zero_()
+        isoclust.cluster_into(Xd, k, sigma, labels, residual, ik)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    prof = []
+    barrier()
+    torch.cuda.synchronize(dev)
+    l0 = isoclust.kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+        prof.append(isoclust.last_profile())
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    launches = isoclust.kernel_launches() - l0
+    clk = clocks.stop()
+    t_ms = ev0.elapsed_time(ev1)
+    if pg is not None:
+        tt = torch.tensor([t_ms], device=dev)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    ms_per_step = t_ms / args.steps
+    value = world * n / (ms_per_step / 1000.0)
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.from_numpy(X).pin_memory()
+        lh = torch.empty(n, dtype=torch.int32).pin_memory()
+        rh = torch.empty(n, dtype=torch.uint8).pin_memory()
+        ih = torch.empty(1, dtype=torch.float64).pin_memory()
+
+        def e2e_step():
+            flush.zero_()
+            Xd.copy_(Xh, non_blocking=True)
+            isoclust.cluster_into(Xd, k, sigma, labels, residual, ik)
+            lh.copy_(labels, non_blocking=True)
+            rh.copy_(residual, non_blocking=True)
+            ih.copy_(ik, non_blocking=True)
+        e2e_step()
+        torch.cuda.synchronize(dev)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        te = e0.elapsed_time(e1)
+        if pg is not None:
+            tt = torch.tensor([te], device=dev)
+            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": world * n / (te / args.steps / 1000.0), "unit": UNIT,
+               "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": int(n * 4 + n + 8)}
+
+    # roofline of the dominant kernel: the double-word omega sweep
+    peaks, src = _peaks()
+    w_ms = statistics.mean(p["weights_ms"] for p in prof)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = sms * FP32_LANES_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12   # T instr/s
+    pairs = n * (n - 1) / 2.0
+    ops_per_pair = 21.0 * d + 75.0       # FP32-pipe instructions of one double-word pair (d2 + sqrt/exp/accumulate)
+    achieved = pairs * ops_per_pair / (w_ms / 1000.0) / 1e12
+    stages = {key: round(statistics.mean(p[key] for p in prof), 3)
+              for key in ("validate_ms", "weights_ms", "mst_ms", "orient_ms", "search_ms", "labels_ms")}
+    counts = {key: prof[-1][key] for key in ("boruvka_rounds", "rescanned_rows", "alg1_passes", "tree_depth")}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "d": d, "k": k, "sigma": sigma, "storage": "f32",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "flushed by a 256 MiB write before every step (inside the timed region)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                     "frac": achieved / alu_peak, "traffic": None,
+                     "kernel": "k_weights_dw (omega, double-word FP32)",
+                     "note": f"FP32-pipe instructions: n(n-1)/2 pairs x (21 d + 75) per pair over the omega stage's "
+                             f"event time; peak = {sms} SMs x {FP32_LANES_PER_SM} lanes x max SM clock "
+                             f"({src} sm_max_mhz)"},
+        "stages_ms": stages, "counts": counts,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if e2e is not None:
+        line["e2e"] = e2e
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(X, k, sigma)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

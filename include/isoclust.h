@@ -104,6 +104,11 @@ const char *isoclust_status_string(isoclust_status s);
 /* ABI version of the loaded library (ISOCLUST_ABI_VERSION). */
 int32_t isoclust_abi_version(void);
 
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all devices, all threads).  Differences between two reads count the
+ * kernels of the calls made in between. */
+int64_t isoclust_kernel_launches(void);
+
 /*
  * isoclust_cluster_mst -- Section 2.2 steps 1-2 (and Section 3.5): the exact
  * Euclidean minimum spanning tree of the n points under key K, found by a

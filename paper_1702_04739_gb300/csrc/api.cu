@@ -1,0 +1,517 @@
+// api.cu -- the C ABI (include/isoclust.h): validation, scratch, orchestration.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <mutex>
+
+#include "common.cuh"
+#include "mst.cuh"
+#include "tree.cuh"
+
+namespace iso {
+cudaError_t weights_launch(const void *X, int64_t n, int32_t d, int dtype, bool fp64_path, double sigma,
+                           double alpha, int include_self, const unsigned long long *nnbits, double *omega,
+                           double *p, cudaStream_t s);
+
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// ---------------------------------------------------------------- errors
+static thread_local char g_err[512] = "";
+static thread_local double g_prof_ms[6] = {0, 0, 0, 0, 0, 0};
+static thread_local int64_t g_prof_cnt[4] = {0, 0, 0, 0};
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+isoclust_status fail(isoclust_status s, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+isoclust_status cuda_fail(cudaError_t e, const char *what) {
+    snprintf(g_err, sizeof(g_err), "CUDA error %d (%s) at %s", (int)e, cudaGetErrorString(e), what);
+    return e == cudaErrorMemoryAllocation ? ISOCLUST_ERR_OOM : ISOCLUST_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------- device info
+static std::mutex g_dev_mu;
+constexpr int MAX_DEV = 64;
+static int g_sms[MAX_DEV] = {0};
+static std::mutex g_call_mu[MAX_DEV];
+static void *g_scratch[MAX_DEV] = {nullptr};
+static size_t g_scratch_cap[MAX_DEV] = {0};
+
+static int current_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    return dev < MAX_DEV ? dev : 0;
+}
+
+int num_sms() {
+    int dev = current_device();
+    std::lock_guard<std::mutex> g(g_dev_mu);
+    if (g_sms[dev] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
+        g_sms[dev] = v;
+    }
+    return g_sms[dev];
+}
+
+// Caller holds g_call_mu[dev]; no work from an earlier call is in flight
+// (every call synchronises its stream before returning).
+void *scratch_acquire(size_t bytes, cudaStream_t stream, isoclust_status *st) {
+    (void)stream;
+    int dev = current_device();
+    if (g_scratch_cap[dev] >= bytes && g_scratch[dev]) return g_scratch[dev];
+    if (g_scratch[dev]) {
+        cudaDeviceSynchronize();
+        cudaFree(g_scratch[dev]);
+        g_scratch[dev] = nullptr;
+        g_scratch_cap[dev] = 0;
+    }
+    size_t want = bytes + bytes / 4 + (1u << 20);
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            *st = fail(ISOCLUST_ERR_OOM, "cannot allocate %zu bytes of device scratch", bytes);
+            return nullptr;
+        }
+        want = bytes;
+    }
+    g_scratch[dev] = p;
+    g_scratch_cap[dev] = want;
+    return p;
+}
+
+void scratch_release() {
+    int dev = current_device();
+    if (g_scratch[dev]) {
+        cudaFree(g_scratch[dev]);
+        g_scratch[dev] = nullptr;
+        g_scratch_cap[dev] = 0;
+    }
+}
+
+// ---------------------------------------------------------------- validation kernels
+namespace {
+constexpr int TPB = 256;
+
+template <class T>
+__global__ void k_check_finite(const T *__restrict__ X, int64_t count, uint32_t *st) {
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        if (!isfinite((double)X[i])) bad = true;
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(st, DEV_NONFINITE);
+}
+
+__global__ void k_tree_input(const int32_t *__restrict__ parent, int64_t n, int32_t *info, uint32_t *st) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    int32_t p = parent[v];
+    if (p == -1) {
+        atomicAdd(info + 0, 1);
+        atomicMin(info + 1, (int32_t)v);
+    } else if (p < 0 || p >= n || p == v) {
+        atomicOr(st, DEV_BAD_TREE);
+    }
+}
+
+__global__ void k_check_edges(const int32_t *counters, int64_t n, uint32_t *st) {
+    if (counters[MC_NEDGES] != n - 1 || counters[MC_NCOMP] != 1) atomicOr(st, DEV_EDGE_COUNT);
+}
+
+__global__ void k_copy_beta(const SearchState *S, double *beta) { beta[0] = S->beta; }
+}  // namespace
+
+cudaError_t check_finite(const void *X, int64_t count, int dtype, uint32_t *status, double *absmax, cudaStream_t s) {
+    (void)absmax;
+    int64_t gb = ceil_div(count, TPB), gmax = (int64_t)num_sms() * 16;
+    unsigned g = (unsigned)(gb < gmax ? gb : gmax);
+    if (g == 0) g = 1;
+    if (dtype == ISOCLUST_F64)
+        k_check_finite<double><<<g, TPB, 0, ISO_S(s)>>>((const double *)X, count, status);
+    else
+        k_check_finite<float><<<g, TPB, 0, ISO_S(s)>>>((const float *)X, count, status);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- helpers
+static isoclust_status map_status(uint32_t st, bool user_tree) {
+    if (st & DEV_NONFINITE) return fail(ISOCLUST_ERR_NONFINITE, "non-finite value in an input array");
+    if (st & DEV_BAD_TREE)
+        return user_tree ? fail(ISOCLUST_ERR_INVALID_ARG, "parent[] does not describe a rooted tree")
+                         : fail(ISOCLUST_ERR_INTERNAL, "internal: the spanning tree is malformed");
+    if (st & DEV_NEGATIVE)
+        return user_tree ? fail(ISOCLUST_ERR_INVALID_ARG, "omega must be > 0, phi and p >= 0")
+                         : fail(ISOCLUST_ERR_INTERNAL, "internal: a vertex weight is not positive");
+    if (st & DEV_TIMEOUT) return fail(ISOCLUST_ERR_TIMEOUT, "a bounded device wait ran out");
+    if (st & DEV_NO_SOLUTION) return fail(ISOCLUST_ERR_NO_SOLUTION, "no finite threshold gives k sets");
+    if (st & (DEV_INTERNAL | DEV_EDGE_COUNT)) return fail(ISOCLUST_ERR_INTERNAL, "internal consistency check failed (0x%x)", st);
+    return ISOCLUST_OK;
+}
+
+static isoclust_opts resolve_opts(const isoclust_opts *o) { return o ? *o : isoclust_opts_default(); }
+
+static isoclust_status check_opts(const isoclust_opts &o, int64_t n, int dtype) {
+    if (!(o.alpha >= 0.0) || !isfinite(o.alpha)) return fail(ISOCLUST_ERR_INVALID_ARG, "alpha must be finite and >= 0");
+    if (o.omega_mode != ISOCLUST_OMEGA_FULL && o.omega_mode != ISOCLUST_OMEGA_TREE)
+        return fail(ISOCLUST_ERR_INVALID_ARG, "unknown omega_mode %d", o.omega_mode);
+    if (o.precision < ISOCLUST_PREC_AUTO || o.precision > ISOCLUST_PREC_FP32)
+        return fail(ISOCLUST_ERR_INVALID_ARG, "unknown precision %d", o.precision);
+    if (o.precision == ISOCLUST_PREC_FP32 && dtype != ISOCLUST_F32)
+        return fail(ISOCLUST_ERR_INVALID_ARG, "precision FP32 needs F32 input");
+    if (o.root < 0 || o.root >= n) return fail(ISOCLUST_ERR_INVALID_ARG, "root %d out of range", o.root);
+    if (o.include_self != 0 && o.include_self != 1) return fail(ISOCLUST_ERR_INVALID_ARG, "include_self must be 0 or 1");
+    return ISOCLUST_OK;
+}
+
+static isoclust_status check_points(const void *X, int64_t n, int32_t d, int32_t dtype, int64_t min_n) {
+    if (!X) return fail(ISOCLUST_ERR_INVALID_ARG, "X is NULL");
+    if (n < min_n) return fail(ISOCLUST_ERR_INVALID_ARG, "n = %lld is below %lld", (long long)n, (long long)min_n);
+    if (n > 2147483646LL) return fail(ISOCLUST_ERR_INVALID_ARG, "n = %lld is too large", (long long)n);
+    if (d < 1) return fail(ISOCLUST_ERR_INVALID_ARG, "d = %d must be >= 1", d);
+    if (dtype != ISOCLUST_F32 && dtype != ISOCLUST_F64) return fail(ISOCLUST_ERR_INVALID_ARG, "unknown dtype %d", dtype);
+    if ((double)n * (double)d > 9.0e15) return fail(ISOCLUST_ERR_INVALID_ARG, "n*d too large");
+    return ISOCLUST_OK;
+}
+
+struct Events {
+    cudaEvent_t e[8];
+    bool ok = false;
+    Events() {
+        ok = true;
+        for (auto &x : e) ok = ok && cudaEventCreate(&x) == cudaSuccess;
+    }
+    ~Events() {
+        for (auto &x : e) cudaEventDestroy(x);
+    }
+    void rec(int i, cudaStream_t s) {
+        if (ok) cudaEventRecord(e[i], s);
+    }
+    double ms(int a, int b) {
+        float t = 0.f;
+        if (!ok || cudaEventElapsedTime(&t, e[a], e[b]) != cudaSuccess) return 0.0;
+        return (double)t;
+    }
+};
+
+static bool use_fp64_sweep(const isoclust_opts &o, int dtype) {
+    if (o.precision == ISOCLUST_PREC_FP64) return true;
+    if (o.precision == ISOCLUST_PREC_FP32) return false;
+    return dtype == ISOCLUST_F64;
+}
+
+// ---------------------------------------------------------------- the pipeline
+static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t dtype, int32_t k, double sigma,
+                                    const isoclust_opts *opts_in, int32_t *labels, uint8_t *residual, double *i_k,
+                                    int32_t *out_parent, double *out_phi, double *out_omega, double *out_p,
+                                    double *out_beta, int32_t *out_eu, int32_t *out_ev, double *out_ed2,
+                                    cudaStream_t s, bool need_labels) {
+    isoclust_status st;
+    if ((st = check_points(X, n, d, dtype, 2))) return st;
+    isoclust_opts o = resolve_opts(opts_in);
+    if ((st = check_opts(o, n, dtype))) return st;
+    if (need_labels) {
+        if (!labels || !residual || !i_k) return fail(ISOCLUST_ERR_INVALID_ARG, "labels, residual and i_k are required");
+        if (k < 1) return fail(ISOCLUST_ERR_INVALID_ARG, "k = %d must be >= 1", k);
+        if (k > n) return fail(ISOCLUST_ERR_K_GT_N, "k = %d exceeds n = %lld", k, (long long)n);
+        if (!(sigma > 0.0) || !isfinite(sigma)) return fail(ISOCLUST_ERR_INVALID_ARG, "sigma must be finite and > 0");
+    }
+    const bool fp64_sweep = use_fp64_sweep(o, dtype);
+    const int splits = mst_splits(n);
+
+    const int dev = current_device();
+    std::lock_guard<std::mutex> lock(g_call_mu[dev]);
+
+    // scratch layout (measured, then carved)
+    auto carve = [&](Arena &A, MstScratch &M, TreeScratch &TS, double **phi, double **om, double **pp, double **omtmp,
+                     uint32_t **status) {
+        *status = A.take<uint32_t>(4);
+        M.carve(A, n, splits);
+        if (need_labels) {
+            TS.carve(A, n);
+            *phi = A.take<double>(n);
+            *om = A.take<double>(n);
+            *pp = A.take<double>(n);
+            *omtmp = A.take<double>(n);
+        }
+    };
+    MstScratch M;
+    TreeScratch TS;
+    double *phi = nullptr, *om = nullptr, *pp = nullptr, *omtmp = nullptr;
+    uint32_t *status = nullptr;
+    Arena meas;
+    carve(meas, M, TS, &phi, &om, &pp, &omtmp, &status);
+    void *base = scratch_acquire(meas.off, s, &st);
+    if (!base) return st;
+    Arena A{(char *)base, meas.off + 4096, 0, false};
+    carve(A, M, TS, &phi, &om, &pp, &omtmp, &status);
+    if (A.overflow) return fail(ISOCLUST_ERR_INTERNAL, "scratch carve overflow");
+    if (out_phi) phi = out_phi;
+    if (out_omega) om = out_omega;
+    if (out_p) pp = out_p;
+
+    Events ev;
+    ev.rec(0, s);
+    ISO_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t) * 4, s));
+    if (need_labels) ISO_CUDA(cudaMemsetAsync(TS.status, 0, sizeof(uint32_t), s));
+    ISO_CUDA(check_finite(X, n * (int64_t)d, dtype, status, nullptr, s));
+    uint32_t hst = 0;
+    ISO_CUDA(cudaMemcpyAsync(&hst, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    ISO_CUDA(cudaStreamSynchronize(s));
+    if (hst) return map_status(hst, false);
+    ev.rec(1, s);
+
+    // Section 2.2 steps 1-2: minimum spanning tree
+    ISO_CUDA(mst_build(M, X, n, d, dtype, fp64_sweep, status, s));
+    k_check_edges<<<1, 1, 0, ISO_S(s)>>>(M.counters, n, status);
+    if (out_eu || out_ev || out_ed2) {
+        if (!(out_eu && out_ev && out_ed2)) return fail(ISOCLUST_ERR_INVALID_ARG, "edge outputs must be all or none");
+        ISO_CUDA(mst_sort_edges(M, out_eu, out_ev, out_ed2, s));
+    }
+    ev.rec(2, s);
+
+    if (need_labels) {
+        // eq. omega / eq. potential
+        const bool full = o.omega_mode == ISOCLUST_OMEGA_FULL;
+        if (full || o.alpha != 0.0) {
+            ISO_CUDA(nn_from_edges(M, M.eu, M.ev, M.ed2, s));
+            ISO_CUDA(weights_launch(X, n, d, dtype, false, sigma, o.alpha, o.include_self, M.nnbits,
+                                    full ? om : omtmp, pp, s));
+        }
+        ev.rec(3, s);
+        // Section 2.2 step 3: root the tree, BFS order; phi on tree edges
+        ISO_CUDA(orient_tree(TS, M.eu, M.ev, n, o.root, nullptr, s));
+        {
+            uint32_t h2 = 0;
+            ISO_CUDA(cudaMemcpyAsync(&h2, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+            ISO_CUDA(cudaStreamSynchronize(s));
+            uint32_t h3 = 0;
+            ISO_CUDA(cudaMemcpy(&h3, TS.status, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+            if (h2 | h3) return map_status(h2 | h3, false);
+        }
+        ISO_CUDA(phi_from_edges(TS, M.ed2, sigma, phi, s));
+        if (!full) ISO_CUDA(omega_tree_mode(TS, phi, o.include_self, om, s));
+        ev.rec(4, s);
+        // Algorithm 2 (search) + Algorithm 1, then Algorithm 4's labels
+        ISO_CUDA(tree_search_and_label(TS, phi, om, o.alpha != 0.0 ? pp : nullptr, k, labels, residual, i_k, s));
+        ev.rec(5, s);
+        if (out_parent) ISO_CUDA(cudaMemcpyAsync(out_parent, TS.T.parent, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+        if (out_beta) k_copy_beta<<<1, 1, 0, ISO_S(s)>>>(TS.search, out_beta);
+        if (out_p && o.alpha == 0.0) ISO_CUDA(cudaMemsetAsync(out_p, 0, sizeof(double) * n, s));
+    } else {
+        ev.rec(3, s);
+        ev.rec(4, s);
+        ev.rec(5, s);
+    }
+    ev.rec(6, s);
+    ISO_CUDA(cudaGetLastError());
+    ISO_CUDA(cudaStreamSynchronize(s));
+    uint32_t fin = 0;
+    ISO_CUDA(cudaMemcpy(&fin, status, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    int32_t cnt[8] = {0};
+    ISO_CUDA(cudaMemcpy(cnt, M.counters, sizeof(cnt), cudaMemcpyDeviceToHost));
+    SearchState ss;
+    memset(&ss, 0, sizeof(ss));
+    if (need_labels) {
+        uint32_t tf = 0;
+        ISO_CUDA(cudaMemcpy(&tf, TS.status, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+        fin |= tf;
+        ISO_CUDA(cudaMemcpy(&ss, TS.search, sizeof(ss), cudaMemcpyDeviceToHost));
+    }
+    g_prof_ms[0] = ev.ms(0, 1);
+    g_prof_ms[1] = ev.ms(2, 3);
+    g_prof_ms[2] = ev.ms(1, 2);
+    g_prof_ms[3] = ev.ms(3, 4);
+    g_prof_ms[4] = ev.ms(4, 5);
+    g_prof_ms[5] = ev.ms(5, 6);
+    g_prof_cnt[0] = cnt[MC_ROUNDS];
+    g_prof_cnt[1] = cnt[MC_OVF_TOTAL] + cnt[MC_OVERFLOW];
+    g_prof_cnt[2] = ss.passes + (need_labels ? 1 : 0);
+    g_prof_cnt[3] = ss.max_depth;
+    return map_status(fin, false);
+}
+
+}  // namespace iso
+
+using namespace iso;
+
+extern "C" {
+
+isoclust_opts isoclust_opts_default(void) {
+    isoclust_opts o;
+    o.alpha = 0.0;
+    o.omega_mode = ISOCLUST_OMEGA_FULL;
+    o.precision = ISOCLUST_PREC_AUTO;
+    o.root = 0;
+    o.include_self = 0;
+    o.spin_limit = 0;
+    return o;
+}
+
+const char *isoclust_last_error(void) { return g_err; }
+
+const char *isoclust_status_string(isoclust_status s) {
+    switch (s) {
+        case ISOCLUST_OK: return "ISOCLUST_OK";
+        case ISOCLUST_ERR_INVALID_ARG: return "ISOCLUST_ERR_INVALID_ARG";
+        case ISOCLUST_ERR_K_GT_N: return "ISOCLUST_ERR_K_GT_N";
+        case ISOCLUST_ERR_NONFINITE: return "ISOCLUST_ERR_NONFINITE";
+        case ISOCLUST_ERR_OOM: return "ISOCLUST_ERR_OOM";
+        case ISOCLUST_ERR_CUDA: return "ISOCLUST_ERR_CUDA";
+        case ISOCLUST_ERR_TIMEOUT: return "ISOCLUST_ERR_TIMEOUT";
+        case ISOCLUST_ERR_NO_SOLUTION: return "ISOCLUST_ERR_NO_SOLUTION";
+        case ISOCLUST_ERR_INTERNAL: return "ISOCLUST_ERR_INTERNAL";
+    }
+    return "ISOCLUST_UNKNOWN";
+}
+
+int32_t isoclust_abi_version(void) { return ISOCLUST_ABI_VERSION; }
+
+int64_t isoclust_kernel_launches(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
+
+void isoclust_last_profile(double *t_ms6, int64_t *counts4) {
+    if (t_ms6) for (int i = 0; i < 6; ++i) t_ms6[i] = g_prof_ms[i];
+    if (counts4) for (int i = 0; i < 4; ++i) counts4[i] = g_prof_cnt[i];
+}
+
+isoclust_status isoclust_cluster_mst(const void *X, int64_t n, int32_t d, int32_t dtype, const isoclust_opts *opts,
+                                     int32_t *edge_u, int32_t *edge_v, double *edge_d2, void *stream) {
+    if (!edge_u || !edge_v || !edge_d2) return fail(ISOCLUST_ERR_INVALID_ARG, "edge outputs are required");
+    return cluster_impl(X, n, d, dtype, 1, 1.0, opts, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                        nullptr, edge_u, edge_v, edge_d2, (cudaStream_t)stream, false);
+}
+
+isoclust_status isoclust_cluster(const void *X, int64_t n, int32_t d, int32_t dtype, int32_t k, double sigma,
+                                 const isoclust_opts *opts, int32_t *labels, uint8_t *residual, double *i_k,
+                                 void *stream) {
+    return cluster_impl(X, n, d, dtype, k, sigma, opts, labels, residual, i_k, nullptr, nullptr, nullptr, nullptr,
+                        nullptr, nullptr, nullptr, nullptr, (cudaStream_t)stream, true);
+}
+
+isoclust_status isoclust_cluster_detail(const void *X, int64_t n, int32_t d, int32_t dtype, int32_t k, double sigma,
+                                        const isoclust_opts *opts, int32_t *labels, uint8_t *residual, double *i_k,
+                                        int32_t *parent, double *phi_par, double *omega, double *p, double *beta,
+                                        int32_t *edge_u, int32_t *edge_v, double *edge_d2, void *stream) {
+    return cluster_impl(X, n, d, dtype, k, sigma, opts, labels, residual, i_k, parent, phi_par, omega, p, beta,
+                        edge_u, edge_v, edge_d2, (cudaStream_t)stream, true);
+}
+
+isoclust_status isoclust_vertex_weights(const void *X, int64_t n, int32_t d, int32_t dtype, double sigma,
+                                        const isoclust_opts *opts_in, double *omega, double *p, void *stream) {
+    isoclust_status st;
+    if ((st = check_points(X, n, d, dtype, 2))) return st;
+    if (!omega) return fail(ISOCLUST_ERR_INVALID_ARG, "omega is NULL");
+    if (!(sigma > 0.0) || !isfinite(sigma)) return fail(ISOCLUST_ERR_INVALID_ARG, "sigma must be finite and > 0");
+    isoclust_opts o = resolve_opts(opts_in);
+    if ((st = check_opts(o, n, dtype))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool fp64 = use_fp64_sweep(o, dtype);
+    const int splits = mst_splits(n);
+    const int dev = current_device();
+    std::lock_guard<std::mutex> lock(g_call_mu[dev]);
+    MstScratch M;
+    uint32_t *status = nullptr;
+    Arena meas;
+    status = meas.take<uint32_t>(4);
+    M.carve(meas, n, splits);
+    void *base = scratch_acquire(meas.off, s, &st);
+    if (!base) return st;
+    Arena A{(char *)base, meas.off + 4096, 0, false};
+    status = A.take<uint32_t>(4);
+    M.carve(A, n, splits);
+    ISO_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t) * 4, s));
+    ISO_CUDA(check_finite(X, n * (int64_t)d, dtype, status, nullptr, s));
+    uint32_t hst = 0;
+    ISO_CUDA(cudaMemcpyAsync(&hst, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    ISO_CUDA(cudaStreamSynchronize(s));
+    if (hst) return map_status(hst, false);
+    if (!fp64) ISO_CUDA(nn_sweep(M, X, n, d, dtype, fp64, status, s));
+    ISO_CUDA(weights_launch(X, n, d, dtype, fp64, sigma, o.alpha, o.include_self, M.nnbits, omega, p, s));
+    ISO_CUDA(cudaStreamSynchronize(s));
+    ISO_CUDA(cudaMemcpy(&hst, status, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    return map_status(hst, false);
+}
+
+isoclust_status isoclust_tree_isoperimetric(int64_t n, const int32_t *parent, const double *phi_par,
+                                            const double *omega, const double *p, int32_t k,
+                                            const isoclust_opts *opts, int32_t *labels, uint8_t *residual,
+                                            double *i_k, void *stream) {
+    (void)opts;
+    if (!parent || !phi_par || !omega || !labels || !residual || !i_k)
+        return fail(ISOCLUST_ERR_INVALID_ARG, "a required pointer is NULL");
+    if (n < 1) return fail(ISOCLUST_ERR_INVALID_ARG, "n = %lld must be >= 1", (long long)n);
+    if (n > 2147483646LL) return fail(ISOCLUST_ERR_INVALID_ARG, "n too large");
+    if (k < 1) return fail(ISOCLUST_ERR_INVALID_ARG, "k = %d must be >= 1", k);
+    if (k > n) return fail(ISOCLUST_ERR_K_GT_N, "k = %d exceeds n = %lld", k, (long long)n);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int dev = current_device();
+    std::lock_guard<std::mutex> lock(g_call_mu[dev]);
+    TreeScratch TS;
+    int32_t *eu = nullptr, *ev = nullptr;
+    const int64_t m = n > 1 ? n - 1 : 1;
+    Arena meas;
+    TS.carve(meas, n);
+    eu = meas.take<int32_t>(m);
+    ev = meas.take<int32_t>(m);
+    isoclust_status st;
+    void *base = scratch_acquire(meas.off, s, &st);
+    if (!base) return st;
+    Arena A{(char *)base, meas.off + 4096, 0, false};
+    TS.carve(A, n);
+    eu = A.take<int32_t>(m);
+    ev = A.take<int32_t>(m);
+
+    Events evs;
+    evs.rec(0, s);
+    ISO_CUDA(cudaMemsetAsync(TS.status, 0, sizeof(uint32_t), s));
+    int32_t init[2] = {0, 2147483647};
+    ISO_CUDA(cudaMemcpyAsync(TS.hostinfo, init, sizeof(init), cudaMemcpyHostToDevice, s));
+    k_tree_input<<<(unsigned)ceil_div(n, TPB), TPB, 0, ISO_S(s)>>>(parent, n, TS.hostinfo, TS.status);
+    int32_t info[2] = {0, 0};
+    uint32_t hst = 0;
+    ISO_CUDA(cudaMemcpyAsync(info, TS.hostinfo, sizeof(info), cudaMemcpyDeviceToHost, s));
+    ISO_CUDA(cudaMemcpyAsync(&hst, TS.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    ISO_CUDA(cudaStreamSynchronize(s));
+    if (hst) return map_status(hst, true);
+    if (info[0] != 1) return fail(ISOCLUST_ERR_INVALID_ARG, "parent[] has %d roots (need exactly 1)", info[0]);
+    const int32_t root = info[1];
+    if (n > 1) ISO_CUDA(edges_from_parent(TS, parent, n, eu, ev, s));
+    ISO_CUDA(orient_tree(TS, eu, ev, n, root, parent, s));
+    ISO_CUDA(cudaMemcpyAsync(&hst, TS.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    ISO_CUDA(cudaStreamSynchronize(s));
+    if (hst) return map_status(hst, true);
+    evs.rec(1, s);
+    ISO_CUDA(tree_search_and_label(TS, phi_par, omega, p, k, labels, residual, i_k, s));
+    evs.rec(2, s);
+    ISO_CUDA(cudaStreamSynchronize(s));
+    ISO_CUDA(cudaMemcpy(&hst, TS.status, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    SearchState ss;
+    ISO_CUDA(cudaMemcpy(&ss, TS.search, sizeof(ss), cudaMemcpyDeviceToHost));
+    g_prof_ms[0] = 0; g_prof_ms[1] = 0; g_prof_ms[2] = 0;
+    g_prof_ms[3] = evs.ms(0, 1);
+    g_prof_ms[4] = evs.ms(1, 2);
+    g_prof_ms[5] = 0;
+    g_prof_cnt[0] = 0; g_prof_cnt[1] = 0;
+    g_prof_cnt[2] = ss.passes + 1;
+    g_prof_cnt[3] = ss.max_depth;
+    return map_status(hst, true);
+}
+
+}  // extern "C"

@@ -1,0 +1,726 @@
+// tree.cu -- the tree half of the hot path.
+//
+//  * Orientation (Section 2.2 step 3, "BFS order and parent"): the tree is
+//    rooted by an Euler tour over the sorted adjacency plus Wyllie list
+//    ranking, so the work takes O(log n) launches whatever the tree depth.
+//    Subtree sizes from the tour give the preorder rank with children in
+//    ascending index; sorting by (depth, preorder) gives the canonical BFS
+//    order (children ascending), which fixes Algorithm 1's visiting order.
+//  * Algorithm 1 (decision) is evaluated for 32 thresholds at once, one warp
+//    lane per threshold.  Instead of one launch per depth level (Section 3.6)
+//    a warp starts at every leaf and walks towards the root; the last child
+//    to finish a vertex (an atomic arrival counter) folds all of that
+//    vertex's children in descending index order (the order Algorithm 1
+//    visits siblings, which replaces the ChildId sequencing) and continues
+//    upwards.  Every vertex is decided exactly once per pass, with no
+//    barrier and no spin-wait.
+//  * Algorithm 2 runs to the last bit as a 33-ary search over the ordered
+//    bit patterns of non-negative doubles, kept on the device.
+//  * Algorithm 4's labels: head pointers (eta) by pointer jumping, an
+//    exclusive scan over Cut in processing order, first k cuts kept.
+#include "tree.cuh"
+
+namespace iso {
+
+// ---------------------------------------------------------------- scratch
+void TreeScratch::carve(Arena &A, int64_t n) {
+    int64_t m = n > 0 ? n - 1 : 0;
+    int64_t M = 2 * m;
+    int64_t big = (M > n ? M : n) + 1;
+    T.n = n;
+    T.parent = A.take<int32_t>(n);
+    T.edge_of = A.take<int32_t>(n);
+    T.bfs_pos = A.take<int32_t>(n);
+    T.ch_off = A.take<int32_t>(n + 1);
+    T.ch_list = A.take<int32_t>(m > 0 ? m : 1);
+    T.adj_off = A.take<int32_t>(n + 1);
+    T.adj_key = A.take<uint64_t>(big);
+    T.leaves = A.take<int32_t>(n);
+    T.depth = A.take<int32_t>(n);
+    kbuf = A.take<uint64_t>(big);
+    vals = A.take<int32_t>(big);
+    vbuf = A.take<int32_t>(big);
+    rev = A.take<int32_t>(big);
+    succ = A.take<int32_t>(big);
+    succ2 = A.take<int32_t>(big);
+    rnk = A.take<int32_t>(big);
+    rnk2 = A.take<int32_t>(big);
+    flag = A.take<int32_t>(big);
+    fpos = A.take<int32_t>(big + 1);
+    size = A.take<int32_t>(n);
+    tmp32 = A.take<int32_t>(scan_tmp_elems(big + 1));
+    ssz = A.take<int64_t>(n);
+    sx = A.take<int64_t>(n);
+    tmp64 = A.take<int64_t>(scan_tmp_elems(n));
+    anc = A.take<int32_t>(n);
+    anc2 = A.take<int32_t>(n);
+    dep2 = A.take<int32_t>(n);
+    pre = A.take<int32_t>(n);
+    pre2 = A.take<int32_t>(n);
+    ib = A.take<int32_t>(n);
+    bkeys = A.take<uint64_t>(n);
+    dec = A.take<uint8_t>((size_t)n * DP_LANES);
+    wh = A.take<double>((size_t)n * DP_LANES);
+    ph = A.take<double>((size_t)n * DP_LANES);
+    rat = A.take<double>(n);
+    done = A.take<int32_t>(n);
+    head = A.take<int32_t>(n);
+    head2 = A.take<int32_t>(n);
+    cflag = A.take<int32_t>(n + 1);
+    cidx = A.take<int32_t>(n + 1);
+    search = A.take<SearchState>(1);
+    status = A.take<uint32_t>(1);
+    hostinfo = A.take<int32_t>(16);
+}
+
+namespace {
+
+constexpr int TPB = 256;
+inline unsigned blocks_for(int64_t n) { return (unsigned)(n > 0 ? ceil_div(n, TPB) : 1); }
+inline int log2_ceil(int64_t x) {
+    int l = 0;
+    while ((1LL << l) < x) ++l;
+    return l;
+}
+
+__device__ __forceinline__ void flag_status(uint32_t *st, uint32_t bit) { atomicOr(st, bit); }
+
+__device__ __forceinline__ uint8_t ld_cg_u8(const uint8_t *p) {
+    unsigned short v;
+    asm volatile("ld.global.cg.u8 %0, [%1];" : "=h"(v) : "l"(p));
+    return (uint8_t)v;
+}
+__device__ __forceinline__ double ld_cg_f64(const double *p) {
+    double v;
+    asm volatile("ld.global.cg.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+
+// ------------------------------------------------------------ orientation
+__global__ void k_dir_keys(const int32_t *__restrict__ eu, const int32_t *__restrict__ ev, int64_t m,
+                           int64_t n, uint64_t *__restrict__ keys, int32_t *__restrict__ vals,
+                           uint32_t *st) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m) return;
+    int64_t u = eu[e], v = ev[e];
+    if (u < 0 || u >= n || v < 0 || v >= n || u == v) {
+        flag_status(st, DEV_BAD_TREE);
+        u = 0; v = 0;
+    }
+    keys[2 * e] = ((uint64_t)u << 32) | (uint64_t)v;
+    vals[2 * e] = (int32_t)(2 * e);
+    keys[2 * e + 1] = ((uint64_t)v << 32) | (uint64_t)u;
+    vals[2 * e + 1] = (int32_t)(2 * e + 1);
+}
+
+__global__ void k_adj_off(const uint64_t *__restrict__ keys, int64_t M, int64_t n, int32_t *adj_off,
+                          uint32_t *st) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) adj_off[n] = (int32_t)M;
+    if (i >= M) return;
+    uint32_t s = (uint32_t)(keys[i] >> 32);
+    if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != s) adj_off[s] = (int32_t)i;
+    if (i > 0 && keys[i] == keys[i - 1]) flag_status(st, DEV_BAD_TREE);
+}
+
+__global__ void k_rev_succ(const uint64_t *__restrict__ keys, const int32_t *__restrict__ adj_off,
+                           int64_t M, int64_t n, int32_t *__restrict__ rev, int32_t *__restrict__ succ,
+                           uint32_t *st) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    uint64_t k = keys[i];
+    uint32_t u = (uint32_t)(k >> 32), v = (uint32_t)(k & 0xffffffffu);
+    int64_t lo = (v < n) ? adj_off[v] : -1, hi = (v < n) ? adj_off[v + 1] : -1;
+    if (lo < 0 || hi < 0 || hi < lo || hi > M) {   // vertex with no edges: not spanning
+        flag_status(st, DEV_BAD_TREE);
+        rev[i] = (int32_t)i;
+        succ[i] = -1;
+        return;
+    }
+    uint64_t target = ((uint64_t)v << 32) | (uint64_t)u;
+    int64_t a = lo, b = hi;
+    while (a < b) {
+        int64_t mid = (a + b) >> 1;
+        if (keys[mid] < target) a = mid + 1; else b = mid;
+    }
+    if (a >= hi || keys[a] != target) {
+        flag_status(st, DEV_BAD_TREE);
+        rev[i] = (int32_t)i;
+        succ[i] = -1;
+        return;
+    }
+    rev[i] = (int32_t)a;
+    int64_t nx = a + 1;
+    if (nx == hi) nx = lo;
+    succ[i] = (int32_t)nx;
+}
+
+__global__ void k_check_adj(const int32_t *__restrict__ adj_off, int64_t n, uint32_t *st) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n && adj_off[v] < 0) flag_status(st, DEV_BAD_TREE);
+}
+
+__global__ void k_break_tour(const int32_t *__restrict__ adj_off, const int32_t *__restrict__ rev,
+                             int32_t *succ, int32_t root, int64_t M, uint32_t *st) {
+    int32_t a = adj_off[root], b = adj_off[root + 1];
+    if (a < 0 || b <= a || b > M) { flag_status(st, DEV_BAD_TREE); return; }
+    int32_t last = rev[b - 1];
+    if (last >= 0 && last < M) succ[last] = -1;
+}
+
+__global__ void k_fill_i32(int32_t *p, int64_t n, int32_t v) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+// one Wyllie step: distance-to-end ranking along succ
+__global__ void k_wyllie(const int32_t *__restrict__ sin, const int32_t *__restrict__ rin,
+                         int32_t *__restrict__ sout, int32_t *__restrict__ rout, int64_t M) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    int32_t s = sin[i];
+    if (s >= 0) {
+        rout[i] = rin[i] + rin[s];
+        sout[i] = sin[s];
+    } else {
+        rout[i] = rin[i];
+        sout[i] = -1;
+    }
+}
+
+__global__ void k_check_ranked(const int32_t *__restrict__ succ, const int32_t *__restrict__ rnk,
+                               int64_t M, uint32_t *st) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    if (succ[i] != -1 || rnk[i] < 1 || rnk[i] > M) flag_status(st, DEV_BAD_TREE);
+}
+
+__global__ void k_orient(const uint64_t *__restrict__ keys, const int32_t *__restrict__ vals,
+                         const int32_t *__restrict__ rev, const int32_t *__restrict__ rnk, int64_t M,
+                         int64_t n, int32_t root, int32_t *__restrict__ parent, int32_t *__restrict__ size,
+                         int32_t *__restrict__ edge_of, int32_t *__restrict__ flag) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        parent[root] = -1;
+        size[root] = (int32_t)n;
+        edge_of[root] = -1;
+    }
+    if (i >= M) return;
+    int32_t j = rev[i];
+    int32_t pi = (int32_t)M - rnk[i], pj = (int32_t)M - rnk[j];
+    if (pi < pj) {
+        uint64_t k = keys[i];
+        int32_t u = (int32_t)(k >> 32), v = (int32_t)(k & 0xffffffffu);
+        parent[v] = u;
+        size[v] = (pj - pi + 1) / 2;
+        edge_of[v] = vals[i] >> 1;
+        flag[i] = 1;
+    } else {
+        flag[i] = 0;
+    }
+}
+
+__global__ void k_check_parent(const int32_t *__restrict__ got, const int32_t *__restrict__ want,
+                               int64_t n, uint32_t *st) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n && got[v] != want[v]) flag_status(st, DEV_BAD_TREE);
+}
+
+__global__ void k_scan_total(const int32_t *__restrict__ flag, int32_t *fpos, int64_t M) {
+    fpos[M] = M > 0 ? fpos[M - 1] + flag[M - 1] : 0;
+}
+
+__global__ void k_children(const uint64_t *__restrict__ keys, const int32_t *__restrict__ flag,
+                           const int32_t *__restrict__ fpos, int64_t M, int32_t *__restrict__ ch_list) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < M && flag[i]) ch_list[fpos[i]] = (int32_t)(keys[i] & 0xffffffffu);
+}
+
+__global__ void k_ch_off(const int32_t *__restrict__ adj_off, const int32_t *__restrict__ fpos,
+                         int64_t n, int32_t *__restrict__ ch_off) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v <= n) ch_off[v] = fpos[adj_off[v]];
+}
+
+__global__ void k_child_sizes(const int32_t *__restrict__ ch_list, const int32_t *__restrict__ size,
+                              int64_t m, int64_t *__restrict__ ssz) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < m) ssz[q] = size[ch_list[q]];
+}
+
+// preorder weight of each vertex: 1 + total size of its earlier siblings
+__global__ void k_pre_init(const int32_t *__restrict__ parent, const int32_t *__restrict__ ch_off,
+                           const int32_t *__restrict__ ch_list, const int64_t *__restrict__ sx, int64_t m,
+                           int32_t root, int32_t *__restrict__ anc, int32_t *__restrict__ dep,
+                           int32_t *__restrict__ pre) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q == 0) {
+        anc[root] = -1;
+        dep[root] = 0;
+        pre[root] = 0;
+    }
+    if (q >= m) return;
+    int32_t c = ch_list[q];
+    int32_t u = parent[c];
+    int64_t off = sx[q] - sx[ch_off[u]];
+    anc[c] = u;
+    dep[c] = 1;
+    pre[c] = (int32_t)(1 + off);
+}
+
+__global__ void k_jump_acc(const int32_t *__restrict__ ain, const int32_t *__restrict__ din,
+                           const int32_t *__restrict__ pin, int32_t *__restrict__ aout,
+                           int32_t *__restrict__ dout, int32_t *__restrict__ pout, int64_t n) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    int32_t a = ain[v];
+    if (a >= 0) {
+        dout[v] = din[v] + din[a];
+        pout[v] = pin[v] + pin[a];
+        aout[v] = ain[a];
+    } else {
+        dout[v] = din[v];
+        pout[v] = pin[v];
+        aout[v] = -1;
+    }
+}
+
+__global__ void k_bfs_keys(const int32_t *__restrict__ dep, const int32_t *__restrict__ pre, int64_t n,
+                           uint64_t *__restrict__ bkeys, int32_t *__restrict__ ib) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    bkeys[v] = ((uint64_t)(uint32_t)dep[v] << 32) | (uint64_t)(uint32_t)pre[v];
+    ib[v] = (int32_t)v;
+}
+
+__global__ void k_bfs_pos(const int32_t *__restrict__ ib, const uint64_t *__restrict__ bkeys, int64_t n,
+                          int32_t *__restrict__ bfs_pos, SearchState *S) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    bfs_pos[ib[i]] = (int32_t)i;
+    if (i == n - 1) S->max_depth = (int)(bkeys[i] >> 32);
+}
+
+__global__ void k_leaf_flags(const int32_t *__restrict__ ch_off, int64_t n, int32_t *__restrict__ flag) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) flag[v] = ch_off[v + 1] == ch_off[v] ? 1 : 0;
+}
+
+__global__ void k_leaf_list(const int32_t *__restrict__ flag, const int32_t *__restrict__ fpos, int64_t n,
+                            int32_t *__restrict__ leaves, SearchState *S) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    if (flag[v]) leaves[fpos[v]] = (int32_t)v;
+    if (v == n - 1) S->nleaves = fpos[v] + flag[v];
+}
+
+__global__ void k_edges_from_parent(const int32_t *__restrict__ parent, const int32_t *__restrict__ pos,
+                                    int64_t n, int32_t *__restrict__ eu, int32_t *__restrict__ ev) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    int32_t u = parent[v];
+    if (u >= 0) {
+        eu[pos[v]] = (int32_t)v;
+        ev[pos[v]] = u;
+    }
+}
+
+__global__ void k_nonroot_flags(const int32_t *__restrict__ parent, int64_t n, int32_t *__restrict__ flag) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) flag[v] = parent[v] >= 0 ? 1 : 0;
+}
+
+// ------------------------------------------------------------ stats + search
+// Section 2.2 step 4 / Section 3.5: phi*, phi_* over tree edges, omega*,
+// omega_*, p*, p_* over the vertices; fixed reduction order (deterministic).
+__global__ void __launch_bounds__(1024) k_stats(const int32_t *__restrict__ parent, const double *__restrict__ phi,
+                                                const double *__restrict__ omega, const double *__restrict__ p,
+                                                int64_t n, SearchState *S, uint32_t *st) {
+    __shared__ double sh[6][1024];
+    const int tid = threadIdx.x;
+    int64_t chunk = ceil_div(n, 1024);
+    int64_t a = tid * chunk, b = min((int64_t)n, a + chunk);
+    double fs = 0.0, fm = INFINITY, ws = 0.0, wm = INFINITY, ps = 0.0, pm = INFINITY;
+    uint32_t bad = 0;
+    for (int64_t v = a; v < b; ++v) {
+        double w = omega[v];
+        if (!(w > 0.0) || isinf(w)) bad |= (isnan(w) || isinf(w)) ? DEV_NONFINITE : DEV_NEGATIVE;
+        ws = ws + w;
+        wm = fmin(wm, w);
+        double pv = p ? p[v] : 0.0;
+        if (!(pv >= 0.0) || isinf(pv)) bad |= (isnan(pv) || isinf(pv)) ? DEV_NONFINITE : DEV_NEGATIVE;
+        ps = ps + pv;
+        pm = fmin(pm, pv);
+        if (parent[v] >= 0) {
+            double f = phi[v];
+            if (!(f >= 0.0) || isinf(f)) bad |= (isnan(f) || isinf(f)) ? DEV_NONFINITE : DEV_NEGATIVE;
+            fs = fs + f;
+            fm = fmin(fm, f);
+        }
+    }
+    if (bad) flag_status(st, bad);
+    sh[0][tid] = fs; sh[1][tid] = fm; sh[2][tid] = ws; sh[3][tid] = wm; sh[4][tid] = ps; sh[5][tid] = pm;
+    __syncthreads();
+    for (int s = 512; s > 0; s >>= 1) {
+        if (tid < s) {
+            sh[0][tid] = sh[0][tid] + sh[0][tid + s];
+            sh[1][tid] = fmin(sh[1][tid], sh[1][tid + s]);
+            sh[2][tid] = sh[2][tid] + sh[2][tid + s];
+            sh[3][tid] = fmin(sh[3][tid], sh[3][tid + s]);
+            sh[4][tid] = sh[4][tid] + sh[4][tid + s];
+            sh[5][tid] = fmin(sh[5][tid], sh[5][tid + s]);
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        double phs = sh[0][0], phm = n > 1 ? sh[1][0] : 0.0;
+        double wsum = sh[2][0], wmin = sh[3][0], psum = sh[4][0], pmin = sh[5][0];
+        double alpha0 = (phm + pmin) / wsum;
+        double beta0 = (phs + psum) / wmin;
+        S->stats[0] = phs; S->stats[1] = phm; S->stats[2] = wsum; S->stats[3] = wmin;
+        S->stats[4] = psum; S->stats[5] = pmin; S->stats[6] = alpha0; S->stats[7] = beta0;
+        S->have_lo = 0; S->have_hi = 0; S->done = 0; S->error = 0; S->passes = 0;
+        S->selected = 0; S->ik_bits = 0ull; S->beta = 0.0;
+        const double DMAX = 1.7976931348623157e308;
+        double b0 = (isfinite(beta0) && beta0 > 0.0) ? beta0 : 1.0;
+        double a0 = (isfinite(alpha0) && alpha0 > 0.0) ? alpha0 : 0.0;
+        double t[DP_LANES];
+        t[0] = 0.0;
+        t[1] = a0;
+        t[2] = b0;
+        double f = b0;
+        const double mult[10] = {2.0, 2.0, 4.0, 16.0, 256.0, 65536.0, 4294967296.0, 1.8446744073709552e19,
+                                 3.402823669209385e38, 1.157920892373162e77};
+        for (int q = 0; q < 10; ++q) {   // b0*2, *4, *16, *256, *2^16, ..., *2^512
+            f = f * mult[q];
+            t[3 + q] = isfinite(f) ? f : DMAX;
+        }
+        t[13] = DMAX;
+        unsigned long long lb = dbits(a0), hb = dbits(b0);
+        if (hb < lb) hb = lb;
+        unsigned long long g = hb - lb;
+        for (int q = 14; q < DP_LANES; ++q) {
+            unsigned long long s = (unsigned long long)(q - 13);
+            t[q] = bitsd(lb + (g / 19ull) * s + ((g % 19ull) * s) / 19ull);
+        }
+        for (int q = 0; q < DP_LANES; ++q) {
+            S->thr[q] = t[q];
+            S->cnt[q] = 0;
+        }
+    }
+}
+
+// Algorithm 1 for 32 thresholds: one lane per threshold, one warp per walk.
+struct DpArgs {
+    int64_t n;
+    const int32_t *parent, *ch_off, *ch_list, *leaves;
+    const double *phi, *omega, *p;
+};
+
+__global__ void __launch_bounds__(256) k_dp_pass(DpArgs A, SearchState *S, uint8_t *__restrict__ dec,
+                                                 double *__restrict__ wh, double *__restrict__ ph,
+                                                 int32_t *__restrict__ done, double *__restrict__ rat,
+                                                 int final_pass) {
+    if (!final_pass && S->done) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const double N = final_pass ? S->beta : S->thr[lane];
+    const int nleaves = S->nleaves;
+    int cuts = 0;
+    for (int64_t li = warp; li < nleaves; li += nwarps) {
+        int32_t v = A.leaves[li];
+        while (true) {
+            double w = A.omega[v];
+            double pv = A.p ? A.p[v] : 0.0;
+            const int32_t c0 = A.ch_off[v], c1 = A.ch_off[v + 1];
+            for (int32_t q = c1 - 1; q >= c0; --q) {   // siblings in descending index
+                const int32_t c = A.ch_list[q];
+                const size_t cl = (size_t)c * DP_LANES + lane;
+                const uint8_t dc = ld_cg_u8(dec + cl);
+                if (dc == DEC_JOIN) {
+                    w = __dadd_rn(w, ld_cg_f64(wh + cl));
+                    pv = __dadd_rn(pv, ld_cg_f64(ph + cl));
+                } else {
+                    pv = __dadd_rn(pv, A.phi[c]);       // cut or discarded child: boundary edge
+                }
+            }
+            const int32_t u = A.parent[v];
+            const double fe = u >= 0 ? A.phi[v] : 0.0;
+            const double nw = __dmul_rn(N, w);
+            const double fp = __dadd_rn(fe, pv);
+            uint8_t d;
+            if (fp <= nw) {
+                d = DEC_CUT;
+                ++cuts;
+                if (final_pass && lane == 0) rat[v] = __ddiv_rn(fp, w);
+            } else if (u >= 0 && __dsub_rn(pv, fe) < nw) {
+                d = DEC_JOIN;
+            } else {
+                d = DEC_DISCARD;
+            }
+            const size_t vl = (size_t)v * DP_LANES + lane;
+            dec[vl] = d;
+            wh[vl] = w;
+            ph[vl] = pv;
+            if (u < 0) break;
+            const int32_t nu = A.ch_off[u + 1] - A.ch_off[u];
+            if (nu == 1) { v = u; continue; }          // only child: no one to wait for
+            __threadfence();
+            __syncwarp();
+            int old = 0;
+            if (lane == 0) old = atomicAdd(done + u, 1);
+            old = __shfl_sync(0xffffffffu, old, 0);
+            if (old != nu - 1) break;                  // a sibling is still running
+            __threadfence();
+            v = u;
+        }
+    }
+    if (cuts) atomicAdd(&S->cnt[lane], cuts);
+}
+
+__global__ void k_search_update(SearchState *S, int32_t k, int last, uint32_t *st) {
+    if (threadIdx.x != 0 || S->done) return;
+    const unsigned long long NONE = ~0ull;
+    unsigned long long hi = S->have_hi ? S->hi_bits : NONE;
+    for (int t = 0; t < DP_LANES; ++t)
+        if (S->cnt[t] >= k && dbits(S->thr[t]) < hi) hi = dbits(S->thr[t]);
+    S->passes += 1;
+    if (hi == NONE) {
+        S->error = 1;
+        S->done = 1;
+        flag_status(st, DEV_NO_SOLUTION);
+        return;
+    }
+    bool have_lo = S->have_lo;
+    unsigned long long lo = S->lo_bits;
+    for (int t = 0; t < DP_LANES; ++t) {
+        unsigned long long b = dbits(S->thr[t]);
+        if (S->cnt[t] < k && b < hi && (!have_lo || b > lo)) { lo = b; have_lo = true; }
+    }
+    S->hi_bits = hi; S->have_hi = 1;
+    S->lo_bits = lo; S->have_lo = have_lo ? 1 : 0;
+    for (int t = 0; t < DP_LANES; ++t) S->cnt[t] = 0;
+    if (hi == 0ull || (have_lo && hi - lo <= 1ull)) {
+        S->done = 1;
+        S->beta = bitsd(hi);
+        return;
+    }
+    if (!have_lo) {   // 0.0 is always tried in the first pass; cannot happen
+        S->error = 1;
+        S->done = 1;
+        flag_status(st, DEV_INTERNAL);
+        return;
+    }
+    if (last) {
+        S->done = 1;
+        S->beta = bitsd(hi);
+        flag_status(st, DEV_INTERNAL);
+        return;
+    }
+    unsigned long long g = hi - lo;
+    for (int t = 1; t <= DP_LANES; ++t) {
+        unsigned long long s = (unsigned long long)t;
+        S->thr[t - 1] = bitsd(lo + (g / 33ull) * s + ((g % 33ull) * s) / 33ull);
+    }
+}
+
+// ------------------------------------------------------------ labels
+__global__ void k_head_init(const uint8_t *__restrict__ dec, const int32_t *__restrict__ parent, int64_t n,
+                            int32_t *__restrict__ head) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) head[v] = dec[(size_t)v * DP_LANES] == DEC_JOIN ? parent[v] : (int32_t)v;
+}
+
+__global__ void k_head_jump(const int32_t *__restrict__ hin, int32_t *__restrict__ hout, int64_t n) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) hout[v] = hin[hin[v]];
+}
+
+__global__ void k_cut_flags(const uint8_t *__restrict__ dec, const int32_t *__restrict__ bfs_pos, int64_t n,
+                            int32_t *__restrict__ cflag) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) cflag[n - 1 - bfs_pos[v]] = dec[(size_t)v * DP_LANES] == DEC_CUT ? 1 : 0;
+}
+
+__global__ void k_labels(const uint8_t *__restrict__ dec, const int32_t *__restrict__ bfs_pos,
+                         const int32_t *__restrict__ head, const int32_t *__restrict__ cidx,
+                         const double *__restrict__ rat, int64_t n, int32_t k, int32_t *__restrict__ labels,
+                         uint8_t *__restrict__ residual, SearchState *S) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    int32_t h = head[v];
+    int32_t c = dec[(size_t)h * DP_LANES] == DEC_CUT ? cidx[n - 1 - bfs_pos[h]] : -1;
+    int32_t lab = (c >= 0 && c < k) ? c : -1;
+    labels[v] = lab;
+    residual[v] = lab < 0 ? 1 : 0;
+    if (dec[(size_t)v * DP_LANES] == DEC_CUT) {
+        int32_t cv = cidx[n - 1 - bfs_pos[v]];
+        if (cv < k) {
+            atomicMax(&S->ik_bits, dbits(rat[v]));
+            atomicAdd(&S->selected, 1);
+        }
+    }
+}
+
+__global__ void k_finish(SearchState *S, int32_t k, double *i_k, uint32_t *st) {
+    if (threadIdx.x != 0) return;
+    if (S->error) return;
+    if (S->selected != k) flag_status(st, DEV_INTERNAL);
+    i_k[0] = bitsd(S->ik_bits);
+}
+
+__global__ void k_phi_from_edges(const int32_t *__restrict__ edge_of, const double *__restrict__ ed2,
+                                 int64_t n, double sigma, double *__restrict__ phi) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    int32_t e = edge_of[v];
+    if (e < 0) { phi[v] = 0.0; return; }
+    double dist = __dsqrt_rn(ed2[e]);
+    double y = __ddiv_rn(dist, sigma);
+    phi[v] = exp(-y);
+}
+
+__global__ void k_omega_tree(const uint64_t *__restrict__ adj_key, const int32_t *__restrict__ adj_off,
+                             const int32_t *__restrict__ parent, const double *__restrict__ phi, int64_t n,
+                             int32_t include_self, double *__restrict__ omega) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    double s = include_self ? 1.0 : 0.0;
+    for (int32_t i = adj_off[v]; i < adj_off[v + 1]; ++i) {
+        int32_t w = (int32_t)(adj_key[i] & 0xffffffffu);
+        double f = parent[v] == w ? phi[v] : phi[w];
+        s = __dadd_rn(s, f);
+    }
+    omega[v] = s;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+cudaError_t orient_tree(TreeScratch &S, const int32_t *eu, const int32_t *ev, int64_t n, int32_t root,
+                        const int32_t *expect_parent, cudaStream_t s) {
+    TreeDev &T = S.T;
+    T.n = n;
+    T.root = root;
+    cudaError_t e;
+    if (n == 1) {
+        k_fill_i32<<<1, 32, 0, ISO_S(s)>>>(T.parent, 1, -1);
+        k_fill_i32<<<1, 32, 0, ISO_S(s)>>>(T.edge_of, 1, -1);
+        k_fill_i32<<<1, 32, 0, ISO_S(s)>>>(T.bfs_pos, 1, 0);
+        k_fill_i32<<<1, 32, 0, ISO_S(s)>>>(T.ch_off, 2, 0);
+        k_fill_i32<<<1, 32, 0, ISO_S(s)>>>(T.adj_off, 2, 0);
+        k_fill_i32<<<1, 32, 0, ISO_S(s)>>>(T.leaves, 1, 0);
+        k_fill_i32<<<1, 32, 0, ISO_S(s)>>>(T.depth, 1, 0);
+        SearchState *SS = S.search;
+        int one = 1, zero = 0;
+        if ((e = cudaMemcpyAsync(&SS->nleaves, &one, sizeof(int), cudaMemcpyHostToDevice, s))) return e;
+        if ((e = cudaMemcpyAsync(&SS->max_depth, &zero, sizeof(int), cudaMemcpyHostToDevice, s))) return e;
+        return cudaStreamSynchronize(s);
+    }
+    const int64_t m = n - 1, M = 2 * m;
+    k_dir_keys<<<blocks_for(m), TPB, 0, ISO_S(s)>>>(eu, ev, m, n, T.adj_key, S.vals, S.status);
+    if ((e = sort_pairs_u64(T.adj_key, S.vals, S.kbuf, S.vbuf, M, s))) return e;
+    k_fill_i32<<<blocks_for(n + 1), TPB, 0, ISO_S(s)>>>(T.adj_off, n + 1, -1);
+    k_adj_off<<<blocks_for(M), TPB, 0, ISO_S(s)>>>(T.adj_key, M, n, T.adj_off, S.status);
+    k_check_adj<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(T.adj_off, n, S.status);
+    k_rev_succ<<<blocks_for(M), TPB, 0, ISO_S(s)>>>(T.adj_key, T.adj_off, M, n, S.rev, S.succ, S.status);
+    k_break_tour<<<1, 1, 0, ISO_S(s)>>>(T.adj_off, S.rev, S.succ, root, M, S.status);
+    k_fill_i32<<<blocks_for(M), TPB, 0, ISO_S(s)>>>(S.rnk, M, 1);
+    int32_t *sa = S.succ, *sb = S.succ2, *ra = S.rnk, *rb = S.rnk2;
+    const int L = log2_ceil(M) + 1;
+    for (int it = 0; it < L; ++it) {
+        k_wyllie<<<blocks_for(M), TPB, 0, ISO_S(s)>>>(sa, ra, sb, rb, M);
+        int32_t *t = sa; sa = sb; sb = t;
+        t = ra; ra = rb; rb = t;
+    }
+    k_check_ranked<<<blocks_for(M), TPB, 0, ISO_S(s)>>>(sa, ra, M, S.status);
+    uint32_t hst = 0;
+    if ((e = cudaMemcpyAsync(&hst, S.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s))) return e;
+    if ((e = cudaStreamSynchronize(s))) return e;
+    if (hst & DEV_BAD_TREE) return cudaSuccess;   // caller reads the status word
+
+    k_orient<<<blocks_for(M), TPB, 0, ISO_S(s)>>>(T.adj_key, S.vals, S.rev, ra, M, n, root, T.parent, S.size, T.edge_of,
+                                           S.flag);
+    if (expect_parent) k_check_parent<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(T.parent, expect_parent, n, S.status);
+    if ((e = exclusive_scan_i32(S.flag, S.fpos, M, S.tmp32, s))) return e;
+    k_scan_total<<<1, 1, 0, ISO_S(s)>>>(S.flag, S.fpos, M);
+    k_children<<<blocks_for(M), TPB, 0, ISO_S(s)>>>(T.adj_key, S.flag, S.fpos, M, T.ch_list);
+    k_ch_off<<<blocks_for(n + 1), TPB, 0, ISO_S(s)>>>(T.adj_off, S.fpos, n, T.ch_off);
+    k_child_sizes<<<blocks_for(m), TPB, 0, ISO_S(s)>>>(T.ch_list, S.size, m, S.ssz);
+    if ((e = exclusive_scan_i64(S.ssz, S.sx, m, S.tmp64, s))) return e;
+    k_pre_init<<<blocks_for(m), TPB, 0, ISO_S(s)>>>(T.parent, T.ch_off, T.ch_list, S.sx, m, root, S.anc, T.depth, S.pre);
+    int32_t *aa = S.anc, *ab = S.anc2, *da = T.depth, *db = S.dep2, *pa = S.pre, *pb = S.pre2;
+    const int Ln = log2_ceil(n) + 1;
+    for (int it = 0; it < Ln; ++it) {
+        k_jump_acc<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(aa, da, pa, ab, db, pb, n);
+        int32_t *t = aa; aa = ab; ab = t;
+        t = da; da = db; db = t;
+        t = pa; pa = pb; pb = t;
+    }
+    if (da != T.depth) {
+        if ((e = cudaMemcpyAsync(T.depth, da, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s))) return e;
+    }
+    k_bfs_keys<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(T.depth, pa, n, S.bkeys, S.ib);
+    if ((e = sort_pairs_u64(S.bkeys, S.ib, S.kbuf, S.vbuf, n, s))) return e;
+    k_bfs_pos<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.ib, S.bkeys, n, T.bfs_pos, S.search);
+    k_leaf_flags<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(T.ch_off, n, S.flag);
+    if ((e = exclusive_scan_i32(S.flag, S.fpos, n, S.tmp32, s))) return e;
+    k_leaf_list<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.flag, S.fpos, n, T.leaves, S.search);
+    return cudaGetLastError();
+}
+
+cudaError_t edges_from_parent(TreeScratch &S, const int32_t *parent, int64_t n, int32_t *eu, int32_t *ev,
+                              cudaStream_t s) {
+    cudaError_t e;
+    k_nonroot_flags<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(parent, n, S.cflag);
+    if ((e = exclusive_scan_i32(S.cflag, S.cidx, n, S.tmp32, s))) return e;
+    k_edges_from_parent<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(parent, S.cidx, n, eu, ev);
+    return cudaGetLastError();
+}
+
+cudaError_t tree_search_and_label(TreeScratch &S, const double *phi_par, const double *omega, const double *p,
+                                  int32_t k, int32_t *labels, uint8_t *residual, double *i_k, cudaStream_t s) {
+    const TreeDev &T = S.T;
+    const int64_t n = T.n;
+    cudaError_t e;
+    k_stats<<<1, 1024, 0, ISO_S(s)>>>(T.parent, phi_par, omega, p, n, S.search, S.status);
+    DpArgs A{n, T.parent, T.ch_off, T.ch_list, T.leaves, phi_par, omega, p};
+    const unsigned grid = (unsigned)(num_sms() * 8);
+    for (int pass = 0; pass < DP_SEARCH_PASSES; ++pass) {
+        if ((e = cudaMemsetAsync(S.done, 0, sizeof(int32_t) * n, s))) return e;
+        k_dp_pass<<<grid, 256, 0, ISO_S(s)>>>(A, S.search, S.dec, S.wh, S.ph, S.done, S.rat, 0);
+        k_search_update<<<1, 32, 0, ISO_S(s)>>>(S.search, k, pass == DP_SEARCH_PASSES - 1, S.status);
+    }
+    // Final call of Algorithm 1 at beta: Cut, eta and the set ratios.
+    if ((e = cudaMemsetAsync(S.done, 0, sizeof(int32_t) * n, s))) return e;
+    k_dp_pass<<<grid, 256, 0, ISO_S(s)>>>(A, S.search, S.dec, S.wh, S.ph, S.done, S.rat, 1);
+    // Algorithm 4: eta by pointer jumping, exclusive scan over Cut.
+    k_head_init<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.dec, T.parent, n, S.head);
+    int32_t *ha = S.head, *hb = S.head2;
+    const int Ln = log2_ceil(n) + 1;
+    for (int it = 0; it < Ln; ++it) {
+        k_head_jump<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(ha, hb, n);
+        int32_t *t = ha; ha = hb; hb = t;
+    }
+    k_cut_flags<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.dec, T.bfs_pos, n, S.cflag);
+    if ((e = exclusive_scan_i32(S.cflag, S.cidx, n, S.tmp32, s))) return e;
+    k_labels<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.dec, T.bfs_pos, ha, S.cidx, S.rat, n, k, labels, residual, S.search);
+    k_finish<<<1, 32, 0, ISO_S(s)>>>(S.search, k, i_k, S.status);
+    return cudaGetLastError();
+}
+
+cudaError_t phi_from_edges(const TreeScratch &S, const double *edge_d2, double sigma, double *phi_par,
+                           cudaStream_t s) {
+    k_phi_from_edges<<<blocks_for(S.T.n), TPB, 0, ISO_S(s)>>>(S.T.edge_of, edge_d2, S.T.n, sigma, phi_par);
+    return cudaGetLastError();
+}
+
+cudaError_t omega_tree_mode(const TreeScratch &S, const double *phi_par, int32_t include_self, double *omega,
+                            cudaStream_t s) {
+    k_omega_tree<<<blocks_for(S.T.n), TPB, 0, ISO_S(s)>>>(S.T.adj_key, S.T.adj_off, S.T.parent, phi_par, S.T.n,
+                                                   include_self, omega);
+    return cudaGetLastError();
+}
+
+}  // namespace iso

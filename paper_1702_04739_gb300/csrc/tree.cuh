@@ -1,0 +1,91 @@
+// tree.cuh -- rooted-tree preparation and Algorithms 1/2/4 on the device.
+#pragma once
+#include "common.cuh"
+
+namespace iso {
+
+constexpr int DP_LANES = 32;          // thresholds evaluated per Algorithm-1 pass
+constexpr int DP_SEARCH_PASSES = 14;  // 1 bracketing pass + 13 passes of 33-ary search
+enum : uint8_t { DEC_DISCARD = 0, DEC_CUT = 1, DEC_JOIN = 2 };
+
+// Device-resident search state of reading S (bisection to the last bit).
+struct SearchState {
+    unsigned long long lo_bits, hi_bits;
+    int have_lo, have_hi, done, error;
+    double thr[DP_LANES];
+    int cnt[DP_LANES];
+    double beta;
+    double stats[8];          // phi*, phi_*, omega*, omega_*, p*, p_*, alpha0, beta0
+    int passes;               // Algorithm-1 passes that did work
+    int max_depth;
+    int nleaves;
+    int selected;             // cuts among the first k (must equal k)
+    unsigned long long ik_bits;
+};
+
+// Rooted tree in device scratch.
+struct TreeDev {
+    int64_t n;
+    int32_t root;
+    int32_t *parent;     // [n], root -1
+    int32_t *edge_of;    // [n], input edge index of the parent edge (-1 at the root)
+    int32_t *bfs_pos;    // [n], position in the canonical BFS order
+    int32_t *ch_off;     // [n+1]
+    int32_t *ch_list;    // [max(n-1,1)], children ascending within each parent
+    int32_t *adj_off;    // [n+1] sorted adjacency (directed edges grouped by source)
+    uint64_t *adj_key;   // [2(n-1)] (src<<32 | dst), sorted
+    int32_t *leaves;     // [n]
+    int32_t *depth;      // [n]
+};
+
+struct TreeScratchSizes;
+
+// Carves (or measures) the scratch of the tree stage.
+struct TreeScratch {
+    TreeDev T;
+    // orientation temporaries
+    uint64_t *kbuf;
+    int32_t *vals, *vbuf;
+    int32_t *rev, *succ, *succ2, *rnk, *rnk2, *size, *flag, *fpos, *tmp32;
+    int64_t *ssz, *sx, *tmp64;
+    int32_t *anc, *anc2, *dep2, *pre, *pre2, *ib;
+    uint64_t *bkeys;
+    // DP
+    uint8_t *dec;
+    double *wh, *ph, *rat;
+    int32_t *done, *head, *head2, *cflag, *cidx;
+    SearchState *search;
+    uint32_t *status;
+    int32_t *hostinfo;   // small device block read back by the host
+
+    void carve(Arena &A, int64_t n);
+};
+
+// Orient the tree given by m = n-1 undirected edges (eu, ev) from `root`.
+// Writes T.parent, T.edge_of, T.bfs_pos, T.ch_off/ch_list, T.depth, leaves.
+// Flags DEV_BAD_TREE if the edges are not a spanning tree.  If
+// expect_parent != nullptr, also flags DEV_BAD_TREE when the orientation
+// differs from it.
+cudaError_t orient_tree(TreeScratch &S, const int32_t *eu, const int32_t *ev, int64_t n,
+                        int32_t root, const int32_t *expect_parent, cudaStream_t s);
+
+// Edges (eu, ev) from a parent array (root entry skipped), written into
+// S.fpos/S.flag-sized buffers; returns the buffers through out pointers.
+cudaError_t edges_from_parent(TreeScratch &S, const int32_t *parent, int64_t n, int32_t *eu,
+                              int32_t *ev, cudaStream_t s);
+
+// Algorithms 2 + 1 (search) and the labels of Algorithm 4.
+cudaError_t tree_search_and_label(TreeScratch &S, const double *phi_par, const double *omega,
+                                  const double *p, int32_t k, int32_t *labels, uint8_t *residual,
+                                  double *i_k, cudaStream_t s);
+
+// phi of each oriented parent edge from the MST edge d2 (eq. phi).
+cudaError_t phi_from_edges(const TreeScratch &S, const double *edge_d2, double sigma, double *phi_par,
+                           cudaStream_t s);
+
+// omega in the tree-incident mode: sum of phi over incident tree edges,
+// ascending neighbour index.
+cudaError_t omega_tree_mode(const TreeScratch &S, const double *phi_par, int32_t include_self,
+                            double *omega, cudaStream_t s);
+
+}  // namespace iso

@@ -1,0 +1,310 @@
+// weights.cu -- eq. omega and eq. potential on all pairs, FP64-grade.
+//
+// omega_i = sum_{j != i} exp(-||x_i - x_j|| / sigma) needs every term to
+// ~1e-14 relative, because i_k inherits omega's error.  GB300's FP64 pipe
+// runs at a small fraction of its FP32 rate, so for FP32 input every pair is
+// evaluated in double-word ("double-float") FP32 arithmetic:
+//   * the difference a - b is made exact by TwoSum (Knuth), its square by
+//     TwoProd with FMA (Dekker), and the d2 sum is a renormalised
+//     double-word accumulation (Joldes, Muller, Popescu 2017);
+//   * sqrt by one Newton correction of the correctly rounded FP32 root;
+//   * exp by table-driven argument reduction (Tang 1989): z = k ln2/64 + r
+//     with a three-part ln2/64, |r| <= ln2/128, a degree-5 Taylor polynomial
+//     whose r^2/2 term is double-word, and a 64-entry 2^(-j/64) table.
+// Each row is shifted by its nearest-neighbour distance, so the terms of a
+// row are exp(-(y_ij - y_i,nn)) <= 1 and the row sum stays inside FP32's
+// range; omega_i = exp(-y_i,nn) * sum is formed in FP64 at the end.
+// Rows are owned by threads (4x4 pairs per thread, 64x64 tiles), so each
+// row's sum has a fixed order: the result is deterministic.
+// FP64 input uses a plain FP64 kernel with the reference summation order.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace iso {
+
+struct ExpTable {
+    float2 t[64];   // 2^(-j/64) as (hi, lo)
+};
+
+ExpTable make_exp_table() {
+    ExpTable T;
+    for (int j = 0; j < 64; ++j) {
+        double v = exp2(-(double)j / 64.0);
+        float hi = (float)v;
+        float lo = (float)(v - (double)hi);
+        T.t[j] = make_float2(hi, lo);
+    }
+    return T;
+}
+
+namespace {
+constexpr int TPB = 256;
+constexpr int WT = 64;        // rows / columns per tile
+constexpr int WDC = 32;       // dims per shared-memory chunk
+constexpr int WPAD = WT + 4;
+
+// ln2/64 = C1 + C2 + C3 (C1 has 11 significant bits: k*C1 is exact for |k| < 2^13)
+#define ISO_C1 0x1.63p-7f
+#define ISO_C2 (-0x1.bd0106p-19f)
+#define ISO_C3 0x1.cf79acp-46f
+#define ISO_INV_C 92.33248261689366f
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+// (h, l) += (bh, bl), renormalised
+__device__ __forceinline__ void dw_add(float &h, float &l, float bh, float bl) {
+    float s, e;
+    two_sum(h, bh, s, e);
+    e = __fadd_rn(e, __fadd_rn(l, bl));
+    fast_two_sum(s, e, h, l);
+}
+
+struct RowAcc {
+    float wh, wl, ph, pl;
+};
+
+// exp(-z) * 1 for z given as a double-word, result as a double-word.
+__device__ __forceinline__ void dw_exp_neg(float zh, float zl, const float2 *__restrict__ tab, float &oh, float &ol) {
+    const float kf = rintf(__fmul_rn(zh, ISO_INV_C));
+    const int k = (int)kf;
+    const float t1 = __fmaf_rn(-kf, ISO_C1, zh);        // exact
+    float p2, p2e;
+    two_prod(kf, ISO_C2, p2, p2e);
+    float rh, re;
+    two_sum(t1, -p2, rh, re);
+    re = __fadd_rn(__fsub_rn(re, p2e), __fmaf_rn(-kf, ISO_C3, zl));
+    float rl;
+    fast_two_sum(rh, re, rh, rl);
+    // exp(-r) = 1 - r + r^2/2 - r^3/6 + r^4/24 - r^5/120
+    float s2, s2e;
+    two_prod(rh, rh, s2, s2e);
+    s2e = __fmaf_rn(__fadd_rn(rh, rh), rl, s2e);
+    const float h2 = __fmul_rn(0.5f, s2), h2e = __fmul_rn(0.5f, s2e);
+    const float poly = __fmaf_rn(__fmaf_rn(-1.0f / 120.0f, rh, 1.0f / 24.0f), rh, -1.0f / 6.0f);
+    const float tail = __fmul_rn(__fmul_rn(s2, rh), poly);
+    float eh, el;
+    two_sum(1.0f, -rh, eh, el);
+    el = __fadd_rn(__fsub_rn(el, rl), __fadd_rn(h2e, tail));
+    float eh2, el2;
+    two_sum(eh, h2, eh2, el2);
+    el2 = __fadd_rn(el2, el);
+    float mh, ml;
+    fast_two_sum(eh2, el2, mh, ml);
+    const float2 T = tab[k & 63];
+    float ph, pl;
+    two_prod(mh, T.x, ph, pl);
+    pl = __fmaf_rn(mh, T.y, pl);
+    pl = __fmaf_rn(ml, T.x, pl);
+    const float scale = __int_as_float((127 - (k >> 6)) << 23);
+    oh = __fmul_rn(ph, scale);
+    ol = __fmul_rn(pl, scale);
+}
+
+template <bool WITH_P>
+__global__ void __launch_bounds__(TPB, 2)
+k_weights_dw(const float *__restrict__ X, int64_t n, int32_t d, const unsigned long long *__restrict__ nnbits,
+             float is_h, float is_l, double inv_sigma, ExpTable tabv, double alpha, int include_self,
+             double *__restrict__ omega, double *__restrict__ pout) {
+    __shared__ __align__(16) float As[WDC][WPAD];
+    __shared__ __align__(16) float Bs[WDC][WPAD];
+    __shared__ float2 tab[64];
+    __shared__ float mw[WT][17][2];
+    __shared__ float mp[WITH_P ? WT : 1][17][2];
+
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int64_t row0 = (int64_t)blockIdx.x * WT;
+    if (tid < 64) tab[tid] = tabv.t[tid];
+
+    float sh_h[4], sh_l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int64_t r = row0 + ty * 4 + i;
+        double sh = 0.0;
+        if (r < n) {
+            double nd2 = bitsd(nnbits[r]);
+            sh = isfinite(nd2) ? __dmul_rn(__dsqrt_rn(nd2), inv_sigma) : 0.0;
+        }
+        sh_h[i] = (float)sh;
+        sh_l[i] = (float)(sh - (double)sh_h[i]);
+    }
+    RowAcc acc[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[i] = RowAcc{0.f, 0.f, 0.f, 0.f};
+
+    const int64_t ntiles = ceil_div(n, WT);
+    for (int64_t ct = 0; ct < ntiles; ++ct) {
+        const int64_t col0 = ct * WT;
+        float S[4][4], E[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) { S[i][j] = 0.f; E[i][j] = 0.f; }
+        for (int t0 = 0; t0 < d; t0 += WDC) {
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < (WT * WDC) / TPB; ++q) {
+                int idx = tid + q * TPB;
+                int r = idx / WDC, t = idx % WDC;
+                int64_t gr = row0 + r, gc = col0 + r;
+                int gt = t0 + t;
+                As[t][r] = (gr < n && gt < d) ? X[gr * d + gt] : 0.0f;
+                Bs[t][r] = (gc < n && gt < d) ? X[gc * d + gt] : 0.0f;
+            }
+            __syncthreads();
+            const int tl = min(WDC, d - t0);
+            for (int t = 0; t < tl; ++t) {
+                float4 a4 = *reinterpret_cast<const float4 *>(&As[t][ty * 4]);
+                float4 b4 = *reinterpret_cast<const float4 *>(&Bs[t][tx * 4]);
+                float a[4] = {a4.x, a4.y, a4.z, a4.w};
+                float b[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        float s, e;
+                        two_sum(a[i], -b[j], s, e);               // exact a - b
+                        float p = __fmul_rn(s, s);
+                        float q2 = __fmaf_rn(s, s, -p);             // exact s^2 = p + q2
+                        q2 = __fmaf_rn(__fadd_rn(s, s), e, q2);     // + 2 s e
+                        float hs, he;
+                        two_sum(S[i][j], p, hs, he);
+                        he = __fadd_rn(he, __fadd_rn(E[i][j], q2));
+                        fast_two_sum(hs, he, S[i][j], E[i][j]);
+                    }
+            }
+        }
+        // epilogue: sqrt, /sigma, shift, exp, row accumulation
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int64_t gr = row0 + ty * 4 + i;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int64_t gc = col0 + tx * 4 + j;
+                if (gr >= n || gc >= n || gc == gr) continue;
+                const float Sh = S[i][j], El = E[i][j];
+                float r = __fsqrt_rn(Sh);
+                float dl = 0.0f;
+                if (r > 0.0f) {
+                    float res = __fadd_rn(__fmaf_rn(-r, r, Sh), El);
+                    dl = __fmul_rn(res, __frcp_rn(__fadd_rn(r, r)));
+                }
+                if (WITH_P) dw_add(acc[i].ph, acc[i].pl, r, dl);
+                float yh, yl;
+                two_prod(r, is_h, yh, yl);
+                yl = __fmaf_rn(r, is_l, yl);
+                yl = __fmaf_rn(dl, is_h, yl);
+                fast_two_sum(yh, yl, yh, yl);
+                float zh, zl;
+                two_sum(yh, -sh_h[i], zh, zl);
+                zl = __fadd_rn(zl, __fsub_rn(yl, sh_l[i]));
+                fast_two_sum(zh, zl, zh, zl);
+                if (zh > 87.0f) continue;      // < 2^-125 of the row's largest term
+                float th, tl2;
+                dw_exp_neg(zh, zl, tab, th, tl2);
+                dw_add(acc[i].wh, acc[i].wl, th, tl2);
+            }
+        }
+    }
+    // merge the 16 column-threads of each row in fixed order
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        mw[ty * 4 + i][tx][0] = acc[i].wh;
+        mw[ty * 4 + i][tx][1] = acc[i].wl;
+        if (WITH_P) {
+            mp[ty * 4 + i][tx][0] = acc[i].ph;
+            mp[ty * 4 + i][tx][1] = acc[i].pl;
+        }
+    }
+    __syncthreads();
+    if (tid < WT) {
+        const int64_t r = row0 + tid;
+        if (r < n) {
+            float h = 0.f, l = 0.f, qh = 0.f, ql = 0.f;
+            for (int s = 0; s < 16; ++s) {
+                dw_add(h, l, mw[tid][s][0], mw[tid][s][1]);
+                if (WITH_P) dw_add(qh, ql, mp[tid][s][0], mp[tid][s][1]);
+            }
+            // the shift actually applied to this row's terms was the
+            // double-word (fh, fl) of sh; fh + fl is exact in FP64
+            double nd2 = bitsd(nnbits[r]);
+            double sh = isfinite(nd2) ? __dmul_rn(__dsqrt_rn(nd2), inv_sigma) : 0.0;
+            const float fh = (float)sh;
+            const float fl = (float)(sh - (double)fh);
+            double scale = exp(-__dadd_rn((double)fh, (double)fl));
+            double w = __dmul_rn(scale, __dadd_rn((double)h, (double)l));
+            if (include_self) w = __dadd_rn(w, 1.0);
+            omega[r] = w;
+            if (WITH_P && pout) pout[r] = __dmul_rn(alpha, __dadd_rn((double)qh, (double)ql));
+        }
+    }
+}
+
+// FP64 input: canonical FP64 terms, j ascending (the oracle's order).
+template <class T>
+__global__ void __launch_bounds__(TPB) k_weights_f64(const T *__restrict__ X, int64_t n, int32_t d, double sigma,
+                                                     double alpha, int include_self, double *__restrict__ omega,
+                                                     double *__restrict__ pout) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const T *xi = X + i * d;
+    double sw = 0.0, sd = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+        if (j == i) {
+            if (include_self) sw = __dadd_rn(sw, 1.0);
+            continue;
+        }
+        double d2 = exact_d2(xi, X + j * d, d);
+        double dist = __dsqrt_rn(d2);
+        sw = __dadd_rn(sw, exp(-__ddiv_rn(dist, sigma)));
+        if (alpha != 0.0) sd = __dadd_rn(sd, dist);
+    }
+    omega[i] = sw;
+    if (pout) pout[i] = alpha != 0.0 ? __dmul_rn(alpha, sd) : 0.0;
+}
+}  // namespace
+
+cudaError_t weights_launch(const void *X, int64_t n, int32_t d, int dtype, bool fp64_path, double sigma,
+                           double alpha, int include_self, const unsigned long long *nnbits, double *omega,
+                           double *p, cudaStream_t s) {
+    if (fp64_path || dtype == ISOCLUST_F64) {
+        unsigned g = (unsigned)ceil_div(n, TPB);
+        if (dtype == ISOCLUST_F64)
+            k_weights_f64<double><<<g, TPB, 0, ISO_S(s)>>>((const double *)X, n, d, sigma, alpha, include_self, omega, p);
+        else
+            k_weights_f64<float><<<g, TPB, 0, ISO_S(s)>>>((const float *)X, n, d, sigma, alpha, include_self, omega, p);
+        return cudaGetLastError();
+    }
+    static const ExpTable tab = make_exp_table();
+    const double is = 1.0 / sigma;
+    const float is_h = (float)is;
+    const float is_l = (float)(is - (double)is_h);
+    unsigned g = (unsigned)ceil_div(n, WT);
+    if (alpha != 0.0 && p)
+        k_weights_dw<true><<<g, TPB, 0, ISO_S(s)>>>((const float *)X, n, d, nnbits, is_h, is_l, is, tab, alpha, include_self,
+                                             omega, p);
+    else {
+        k_weights_dw<false><<<g, TPB, 0, ISO_S(s)>>>((const float *)X, n, d, nnbits, is_h, is_l, is, tab, alpha,
+                                              include_self, omega, p);
+        if (p) {
+            cudaError_t e = cudaMemsetAsync(p, 0, sizeof(double) * n, s);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace iso

@@ -1,0 +1,242 @@
+"""Thin Python binding of the isoclust C ABI (include/isoclust.h).
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+library libisoclust.so.  Inputs are torch CUDA tensors (device memory);
+outputs are allocated with torch on the same device; the call is queued on
+torch's current stream.  There is no CPU fallback: if the library cannot be
+loaded, or a tensor is not on a CUDA device, the call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import torch
+
+from . import build as _build
+
+F32, F64 = 0, 1
+OMEGA_FULL, OMEGA_TREE = 0, 1
+PREC_AUTO, PREC_FP64, PREC_FP32 = 0, 1, 2
+
+STATUS = {
+    0: "ISOCLUST_OK", 1: "ISOCLUST_ERR_INVALID_ARG", 2: "ISOCLUST_ERR_K_GT_N", 3: "ISOCLUST_ERR_NONFINITE",
+    4: "ISOCLUST_ERR_OOM", 5: "ISOCLUST_ERR_CUDA", 6: "ISOCLUST_ERR_TIMEOUT", 7: "ISOCLUST_ERR_NO_SOLUTION",
+    8: "ISOCLUST_ERR_INTERNAL",
+}
+
+
+class IsoclustError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("omega_mode", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("root", ctypes.c_int32), ("include_self", ctypes.c_int32), ("spin_limit", ctypes.c_uint64)]
+
+
+_lib = None
+_lock = threading.Lock()
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+_D = ctypes.c_double
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libisoclust.so (building it first if needed)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libisoclust.so not found at {path}; run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        lib.isoclust_opts_default.restype = Opts
+        lib.isoclust_last_error.restype = ctypes.c_char_p
+        lib.isoclust_status_string.restype = ctypes.c_char_p
+        lib.isoclust_status_string.argtypes = [ctypes.c_int]
+        lib.isoclust_abi_version.restype = _I32
+        lib.isoclust_kernel_launches.restype = _I64
+        lib.isoclust_cluster_mst.restype = ctypes.c_int
+        lib.isoclust_cluster_mst.argtypes = [_P, _I64, _I32, _I32, _P, _P, _P, _P, _P]
+        lib.isoclust_vertex_weights.restype = ctypes.c_int
+        lib.isoclust_vertex_weights.argtypes = [_P, _I64, _I32, _I32, _D, _P, _P, _P, _P]
+        lib.isoclust_tree_isoperimetric.restype = ctypes.c_int
+        lib.isoclust_tree_isoperimetric.argtypes = [_I64, _P, _P, _P, _P, _I32, _P, _P, _P, _P, _P]
+        lib.isoclust_cluster.restype = ctypes.c_int
+        lib.isoclust_cluster.argtypes = [_P, _I64, _I32, _I32, _I32, _D, _P, _P, _P, _P, _P]
+        lib.isoclust_cluster_detail.restype = ctypes.c_int
+        lib.isoclust_cluster_detail.argtypes = [_P, _I64, _I32, _I32, _I32, _D, _P, _P, _P, _P,
+                                                _P, _P, _P, _P, _P, _P, _P, _P, _P]
+        lib.isoclust_last_profile.restype = None
+        lib.isoclust_last_profile.argtypes = [_P, _P]
+        _lib = lib
+        return lib
+
+
+def opts(alpha: float = 0.0, omega_mode: int = OMEGA_FULL, precision: int = PREC_AUTO, root: int = 0,
+         include_self: bool = False, spin_limit: int = 0) -> Opts:
+    return Opts(float(alpha), int(omega_mode), int(precision), int(root), int(bool(include_self)), int(spin_limit))
+
+
+def _check(code: int):
+    if code != 0:
+        raise IsoclustError(code, (load().isoclust_last_error() or b"").decode())
+
+
+def _dev_ptr(t: torch.Tensor, dtype=None) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("isoclust takes CUDA tensors (device memory)")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _points(X: torch.Tensor):
+    if X.dim() != 2:
+        raise ValueError("X must be 2-D (n, d)")
+    if X.dtype == torch.float32:
+        dt = F32
+    elif X.dtype == torch.float64:
+        dt = F64
+    else:
+        raise TypeError("X must be float32 or float64")
+    return _dev_ptr(X), X.shape[0], X.shape[1], dt
+
+
+def _stream(device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def _opts_ptr(o):
+    return ctypes.byref(o) if o is not None else None
+
+
+def cluster_mst(X: torch.Tensor, o: Opts | None = None):
+    """(edge_u, edge_v, edge_d2) of the exact MST, in key order."""
+    lib = load()
+    xp, n, d, dt = _points(X)
+    m = max(n - 1, 0)
+    eu = torch.empty(m, dtype=torch.int32, device=X.device)
+    ev = torch.empty(m, dtype=torch.int32, device=X.device)
+    ed = torch.empty(m, dtype=torch.float64, device=X.device)
+    _check(lib.isoclust_cluster_mst(xp, n, d, dt, _opts_ptr(o), eu.data_ptr(), ev.data_ptr(), ed.data_ptr(),
+                                    _stream(X.device)))
+    return eu, ev, ed
+
+
+def vertex_weights(X: torch.Tensor, sigma: float, o: Opts | None = None, want_p: bool = True):
+    """(omega, p) of eq. omega / eq. potential."""
+    lib = load()
+    xp, n, d, dt = _points(X)
+    om = torch.empty(n, dtype=torch.float64, device=X.device)
+    p = torch.empty(n, dtype=torch.float64, device=X.device) if want_p else None
+    _check(lib.isoclust_vertex_weights(xp, n, d, dt, float(sigma), _opts_ptr(o), om.data_ptr(),
+                                       p.data_ptr() if p is not None else None, _stream(X.device)))
+    return om, p
+
+
+def tree_isoperimetric(parent: torch.Tensor, phi_par: torch.Tensor, omega: torch.Tensor, p, k: int,
+                       o: Opts | None = None):
+    """(labels, residual, i_k) of Algorithms 2 + 1 + 4 on a rooted weighted tree."""
+    lib = load()
+    n = parent.numel()
+    dev = parent.device
+    pp = _dev_ptr(parent, torch.int32)
+    fp = _dev_ptr(phi_par, torch.float64)
+    wp = _dev_ptr(omega, torch.float64)
+    qp = _dev_ptr(p, torch.float64) if p is not None else None
+    labels = torch.empty(n, dtype=torch.int32, device=dev)
+    residual = torch.empty(n, dtype=torch.uint8, device=dev)
+    ik = torch.empty(1, dtype=torch.float64, device=dev)
+    _check(lib.isoclust_tree_isoperimetric(n, pp, fp, wp, qp, int(k), _opts_ptr(o), labels.data_ptr(),
+                                           residual.data_ptr(), ik.data_ptr(), _stream(dev)))
+    return labels, residual, ik
+
+
+def cluster(X: torch.Tensor, k: int, sigma: float, o: Opts | None = None):
+    """(labels, residual, i_k) of the whole hot path."""
+    lib = load()
+    xp, n, d, dt = _points(X)
+    labels = torch.empty(n, dtype=torch.int32, device=X.device)
+    residual = torch.empty(n, dtype=torch.uint8, device=X.device)
+    ik = torch.empty(1, dtype=torch.float64, device=X.device)
+    _check(lib.isoclust_cluster(xp, n, d, dt, int(k), float(sigma), _opts_ptr(o), labels.data_ptr(),
+                                residual.data_ptr(), ik.data_ptr(), _stream(X.device)))
+    return labels, residual, ik
+
+
+def cluster_into(X: torch.Tensor, k: int, sigma: float, labels, residual, ik, o: Opts | None = None):
+    """cluster() writing into caller-provided device tensors."""
+    lib = load()
+    xp, n, d, dt = _points(X)
+    _check(lib.isoclust_cluster(xp, n, d, dt, int(k), float(sigma), _opts_ptr(o), labels.data_ptr(),
+                                residual.data_ptr(), ik.data_ptr(), _stream(X.device)))
+
+
+def cluster_detail(X: torch.Tensor, k: int, sigma: float, o: Opts | None = None) -> dict:
+    lib = load()
+    xp, n, d, dt = _points(X)
+    dev = X.device
+    out = dict(
+        labels=torch.empty(n, dtype=torch.int32, device=dev),
+        residual=torch.empty(n, dtype=torch.uint8, device=dev),
+        i_k=torch.empty(1, dtype=torch.float64, device=dev),
+        parent=torch.empty(n, dtype=torch.int32, device=dev),
+        phi_par=torch.empty(n, dtype=torch.float64, device=dev),
+        omega=torch.empty(n, dtype=torch.float64, device=dev),
+        p=torch.empty(n, dtype=torch.float64, device=dev),
+        beta=torch.empty(1, dtype=torch.float64, device=dev),
+        edge_u=torch.empty(max(n - 1, 0), dtype=torch.int32, device=dev),
+        edge_v=torch.empty(max(n - 1, 0), dtype=torch.int32, device=dev),
+        edge_d2=torch.empty(max(n - 1, 0), dtype=torch.float64, device=dev),
+    )
+    _check(lib.isoclust_cluster_detail(
+        xp, n, d, dt, int(k), float(sigma), _opts_ptr(o),
+        *[out[key].data_ptr() for key in ("labels", "residual", "i_k", "parent", "phi_par", "omega", "p", "beta",
+                                          "edge_u", "edge_v", "edge_d2")], _stream(dev)))
+    return out
+
+
+def kernel_launches() -> int:
+    """Cumulative count of kernels launched by libisoclust in this process."""
+    return int(load().isoclust_kernel_launches())
+
+
+def last_profile() -> dict:
+    """Per-stage device times (ms) and counters of the last call on this thread."""
+    lib = load()
+    t = (ctypes.c_double * 6)()
+    c = (ctypes.c_int64 * 4)()
+    lib.isoclust_last_profile(t, c)
+    return dict(validate_ms=t[0], weights_ms=t[1], mst_ms=t[2], orient_ms=t[3], search_ms=t[4], labels_ms=t[5],
+                boruvka_rounds=c[0], rescanned_rows=c[1], alg1_passes=c[2], tree_depth=c[3])
+
+
+@dataclass
+class HostResult:
+    labels: object
+    residual: object
+    i_k: float
+
+
+def cluster_host(X_host, k: int, sigma: float, o: Opts | None = None, device="cuda") -> HostResult:
+    """Host-buffer entry: copies X (pinned host) to the device, runs cluster(),
+    copies labels / residual / i_k back."""
+    Xd = X_host.to(device, non_blocking=True)
+    labels, residual, ik = cluster(Xd, k, sigma, o)
+    return HostResult(labels.cpu(), residual.cpu(), float(ik.cpu()[0]))
