@@ -169,6 +169,41 @@ isoclust_status isoclust_tree_isoperimetric(int64_t n, const int32_t *parent,
                                             void *stream);
 
 /*
+ * isoclust_tree_isoperimetric_noalloc -- the same computation and the same
+ * results as isoclust_tree_isoperimetric, for callers that cannot allocate
+ * device memory.  The paper has no counterpart; it exists for embedding.
+ *
+ * Who needs it: a host application that hands the whole device to its own
+ * memory pool (an inference server, or a framework whose allocator reserves
+ * all free memory up front), where a foreign cudaMalloc fails or breaks the
+ * pool's accounting; or a latency-bound loop that cannot afford cudaMalloc /
+ * cudaFree, which may synchronise the whole device.  This entry point calls
+ * neither, nor any other allocating routine: its scratch is a fixed 13 MiB
+ * array in the library's device memory, reserved on every GPU that loads
+ * the library until the process exits.  The caller still provides every
+ * input and output buffer.
+ *
+ * Limits and behaviour:
+ *   - n <= ISOCLUST_NOALLOC_MAX_N; larger trees are rejected with
+ *     ISOCLUST_ERR_INVALID_ARG and a message naming the limit.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the one array, which keeps the previous call's
+ *     contents (the call clears what must start at zero).  Calls from this
+ *     process are serialised and each completes before it returns; work that
+ *     overlapped on the GPU would race on the array.
+ *   - Arguments, errors and outputs are those of isoclust_tree_isoperimetric.
+ */
+#define ISOCLUST_NOALLOC_MAX_N 16384
+isoclust_status isoclust_tree_isoperimetric_noalloc(int64_t n, const int32_t *parent,
+                                                    const double *phi_par, const double *omega,
+                                                    const double *p, int32_t k,
+                                                    const isoclust_opts *opts,
+                                                    int32_t *labels, uint8_t *residual, double *i_k,
+                                                    void *stream);
+
+/*
  * isoclust_cluster -- the whole hot path (Section 2.2 steps 1-5, Section 3):
  * minimum spanning tree of X, phi on its edges, omega (and p), the rooted
  * tree's global min/sum statistics, the bisection of Algorithm 2 with the
