@@ -78,9 +78,12 @@ enum {
 /* precision values: arithmetic of the Boruvka candidate sweep.  Every path
  * ends in the same FP64 key comparison, so all give the identical tree. */
 enum {
-    ISOCLUST_PREC_AUTO = 0,    /* FP64 sweep for F64 input, FP32 + FP64 recheck for F32 */
+    ISOCLUST_PREC_AUTO = 0,    /* F64 input: FP64 sweep; F32 input: tensor-core sweep    */
     ISOCLUST_PREC_FP64 = 1,    /* FP64 sweep (exact keys directly)                       */
-    ISOCLUST_PREC_FP32 = 2     /* FP32 candidates, FP64 recheck inside a proven margin   */
+    ISOCLUST_PREC_FP32 = 2,    /* FP32 SIMT candidates, FP64 recheck in a proven margin  */
+    ISOCLUST_PREC_BF16_TC = 3  /* BF16 hi+lo Gram tiles on tcgen05 tensor cores with FP32
+                                  accumulation, FP64 recheck in a proven margin (F32
+                                  input, sm_103 only)                                    */
 };
 
 typedef struct {
@@ -242,6 +245,13 @@ isoclust_status isoclust_cluster_detail(const void *X, int64_t n, int32_t d, int
  * rows rescanned after a candidate-margin overflow, counts[2] = Algorithm-1
  * passes, counts[3] = tree depth.  Either pointer may be NULL. */
 void isoclust_last_profile(double *t_ms6, int64_t *counts4);
+
+/* Tile pairs of the omega sweep in the last isoclust_cluster / _detail call
+ * on this host thread: tiles2[0] = 64x64 tile pairs screened, tiles2[1] =
+ * tile pairs evaluated in double-word arithmetic (the rest held only terms
+ * below e^-(39 + ln n) of their row's largest term).  Zero when the screen
+ * did not run (F64 input, alpha > 0, or the FP64 precision option). */
+void isoclust_last_omega_tiles(int64_t *tiles2);
 
 #ifdef __cplusplus
 }

@@ -14,7 +14,7 @@
 namespace iso {
 cudaError_t weights_launch(const void *X, int64_t n, int32_t d, int dtype, bool fp64_path, double sigma,
                            double alpha, int include_self, const unsigned long long *nnbits, double *omega,
-                           double *p, cudaStream_t s);
+                           double *p, unsigned long long *tile_counts, cudaStream_t s);
 
 static std::atomic<long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -23,6 +23,7 @@ void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 static thread_local char g_err[512] = "";
 static thread_local double g_prof_ms[6] = {0, 0, 0, 0, 0, 0};
 static thread_local int64_t g_prof_cnt[4] = {0, 0, 0, 0};
+static thread_local unsigned long long g_prof_tiles[2] = {0, 0};
 
 void set_error(const char *fmt, ...) {
     va_list ap;
@@ -137,6 +138,35 @@ __global__ void k_check_edges(const int32_t *counters, int64_t n, uint32_t *st) 
 }
 
 __global__ void k_copy_beta(const SearchState *S, double *beta) { beta[0] = S->beta; }
+
+// Row order of the omega sweep: MST preorder (spatially coherent runs),
+// with rows whose nearest neighbour is far (y_nn > 16) moved to the end.
+__global__ void k_order_keys(const int32_t *__restrict__ pre, const unsigned long long *__restrict__ nnbits,
+                             int64_t n, double inv_sigma, uint64_t *__restrict__ key, int32_t *__restrict__ val) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    double y = sqrt(__longlong_as_double((long long)nnbits[v])) * inv_sigma;
+    uint64_t far = (y > 16.0) ? 1ull : 0ull;
+    key[v] = (far << 32) | (uint64_t)(uint32_t)pre[v];
+    val[v] = (int32_t)v;
+}
+
+__global__ void k_gather_rows(const float *__restrict__ X, const int32_t *__restrict__ perm,
+                              const unsigned long long *__restrict__ nnbits, int64_t n, int32_t d,
+                              float *__restrict__ Xp, unsigned long long *__restrict__ nnp) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * (int64_t)d) return;
+    int64_t r = idx / d, t = idx - r * d;
+    int64_t src = perm[r];
+    Xp[idx] = X[src * d + t];
+    if (t == 0) nnp[r] = nnbits[src];
+}
+
+__global__ void k_scatter_rows(const double *__restrict__ vp, const int32_t *__restrict__ perm, int64_t n,
+                               double *__restrict__ v) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) v[perm[r]] = vp[r];
+}
 }  // namespace
 
 cudaError_t check_finite(const void *X, int64_t count, int dtype, uint32_t *status, double *absmax, cudaStream_t s) {
@@ -172,10 +202,10 @@ static isoclust_status check_opts(const isoclust_opts &o, int64_t n, int dtype) 
     if (!(o.alpha >= 0.0) || !isfinite(o.alpha)) return fail(ISOCLUST_ERR_INVALID_ARG, "alpha must be finite and >= 0");
     if (o.omega_mode != ISOCLUST_OMEGA_FULL && o.omega_mode != ISOCLUST_OMEGA_TREE)
         return fail(ISOCLUST_ERR_INVALID_ARG, "unknown omega_mode %d", o.omega_mode);
-    if (o.precision < ISOCLUST_PREC_AUTO || o.precision > ISOCLUST_PREC_FP32)
+    if (o.precision < ISOCLUST_PREC_AUTO || o.precision > ISOCLUST_PREC_BF16_TC)
         return fail(ISOCLUST_ERR_INVALID_ARG, "unknown precision %d", o.precision);
-    if (o.precision == ISOCLUST_PREC_FP32 && dtype != ISOCLUST_F32)
-        return fail(ISOCLUST_ERR_INVALID_ARG, "precision FP32 needs F32 input");
+    if ((o.precision == ISOCLUST_PREC_FP32 || o.precision == ISOCLUST_PREC_BF16_TC) && dtype != ISOCLUST_F32)
+        return fail(ISOCLUST_ERR_INVALID_ARG, "precision FP32 / BF16_TC needs F32 input");
     if (o.root < 0 || o.root >= n) return fail(ISOCLUST_ERR_INVALID_ARG, "root %d out of range", o.root);
     if (o.include_self != 0 && o.include_self != 1) return fail(ISOCLUST_ERR_INVALID_ARG, "include_self must be 0 or 1");
     return ISOCLUST_OK;
@@ -213,8 +243,21 @@ struct Events {
 
 static bool use_fp64_sweep(const isoclust_opts &o, int dtype) {
     if (o.precision == ISOCLUST_PREC_FP64) return true;
-    if (o.precision == ISOCLUST_PREC_FP32) return false;
+    if (o.precision == ISOCLUST_PREC_FP32 || o.precision == ISOCLUST_PREC_BF16_TC) return false;
     return dtype == ISOCLUST_F64;
+}
+
+// Tensor-core sweep: requested, or AUTO on F32 input on an sm_103 device.
+static isoclust_status use_tc_sweep(const isoclust_opts &o, int dtype, bool *out) {
+    *out = false;
+    if (dtype != ISOCLUST_F32) return ISOCLUST_OK;
+    if (o.precision == ISOCLUST_PREC_BF16_TC) {
+        if (!tc_supported()) return fail(ISOCLUST_ERR_INVALID_ARG, "precision BF16_TC needs an sm_103 device");
+        *out = true;
+    } else if (o.precision == ISOCLUST_PREC_AUTO) {
+        *out = tc_supported();
+    }
+    return ISOCLUST_OK;
 }
 
 // ---------------------------------------------------------------- the pipeline
@@ -235,21 +278,45 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
     }
     const bool fp64_sweep = use_fp64_sweep(o, dtype);
     const int splits = mst_splits(n);
+    bool use_tc = false;
+    if ((st = use_tc_sweep(o, dtype, &use_tc))) return st;
+    TcScratch TC;
+    const int tsplits = use_tc ? tc_splits(n) : 1;
 
     const int dev = current_device();
     std::lock_guard<std::mutex> lock(g_call_mu[dev]);
 
     // scratch layout (measured, then carved)
+    struct Perm {
+        int32_t *perm = nullptr, *vbuf = nullptr;
+        uint64_t *key = nullptr, *kbuf = nullptr;
+        float *Xp = nullptr;
+        unsigned long long *nnp = nullptr, *tiles = nullptr;
+        double *omp = nullptr, *pp = nullptr;
+    } P;
+    const bool permuted = need_labels && dtype == ISOCLUST_F32 && !fp64_sweep;
     auto carve = [&](Arena &A, MstScratch &M, TreeScratch &TS, double **phi, double **om, double **pp, double **omtmp,
                      uint32_t **status) {
         *status = A.take<uint32_t>(4);
         M.carve(A, n, splits);
+        if (use_tc) TC.carve(A, n, d, tsplits);
         if (need_labels) {
             TS.carve(A, n);
             *phi = A.take<double>(n);
             *om = A.take<double>(n);
             *pp = A.take<double>(n);
             *omtmp = A.take<double>(n);
+        }
+        if (permuted) {
+            P.perm = A.take<int32_t>(n);
+            P.vbuf = A.take<int32_t>(n);
+            P.key = A.take<uint64_t>(n);
+            P.kbuf = A.take<uint64_t>(n);
+            P.Xp = A.take<float>((size_t)n * d);
+            P.nnp = A.take<unsigned long long>(n);
+            P.tiles = A.take<unsigned long long>(2);
+            P.omp = A.take<double>(n);
+            P.pp = A.take<double>(n);
         }
     };
     MstScratch M;
@@ -279,7 +346,7 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
     ev.rec(1, s);
 
     // Section 2.2 steps 1-2: minimum spanning tree
-    ISO_CUDA(mst_build(M, X, n, d, dtype, fp64_sweep, status, s));
+    ISO_CUDA(mst_build(M, X, n, d, dtype, fp64_sweep, status, s, use_tc ? &TC : nullptr));
     k_check_edges<<<1, 1, 0, ISO_S(s)>>>(M.counters, n, status);
     if (out_eu || out_ev || out_ed2) {
         if (!(out_eu && out_ev && out_ed2)) return fail(ISOCLUST_ERR_INVALID_ARG, "edge outputs must be all or none");
@@ -288,15 +355,7 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
     ev.rec(2, s);
 
     if (need_labels) {
-        // eq. omega / eq. potential
-        const bool full = o.omega_mode == ISOCLUST_OMEGA_FULL;
-        if (full || o.alpha != 0.0) {
-            ISO_CUDA(nn_from_edges(M, M.eu, M.ev, M.ed2, s));
-            ISO_CUDA(weights_launch(X, n, d, dtype, false, sigma, o.alpha, o.include_self, M.nnbits,
-                                    full ? om : omtmp, pp, s));
-        }
-        ev.rec(3, s);
-        // Section 2.2 step 3: root the tree, BFS order; phi on tree edges
+        // Section 2.2 step 3: root the tree, BFS order
         ISO_CUDA(orient_tree(TS, M.eu, M.ev, n, o.root, nullptr, s));
         {
             uint32_t h2 = 0;
@@ -306,9 +365,31 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
             ISO_CUDA(cudaMemcpy(&h3, TS.status, sizeof(uint32_t), cudaMemcpyDeviceToHost));
             if (h2 | h3) return map_status(h2 | h3, false);
         }
+        ev.rec(3, s);
+        // eq. omega / eq. potential
+        const bool full = o.omega_mode == ISOCLUST_OMEGA_FULL;
+        if (full || o.alpha != 0.0) {
+            ISO_CUDA(nn_from_edges(M, M.eu, M.ev, M.ed2, s));
+            double *om_out = full ? om : omtmp;
+            if (permuted) {
+                const unsigned gb = (unsigned)ceil_div(n, TPB);
+                k_order_keys<<<gb, TPB, 0, ISO_S(s)>>>(TS.T.pre, M.nnbits, n, 1.0 / sigma, P.key, P.perm);
+                ISO_CUDA(sort_pairs_u64(P.key, P.perm, P.kbuf, P.vbuf, n, s));
+                k_gather_rows<<<(unsigned)ceil_div(n * (int64_t)d, TPB), TPB, 0, ISO_S(s)>>>(
+                    (const float *)X, P.perm, M.nnbits, n, d, P.Xp, P.nnp);
+                ISO_CUDA(cudaMemsetAsync(P.tiles, 0, 2 * sizeof(unsigned long long), s));
+                ISO_CUDA(weights_launch(P.Xp, n, d, dtype, false, sigma, o.alpha, o.include_self, P.nnp, P.omp, P.pp,
+                                        P.tiles, s));
+                k_scatter_rows<<<gb, TPB, 0, ISO_S(s)>>>(P.omp, P.perm, n, om_out);
+                k_scatter_rows<<<gb, TPB, 0, ISO_S(s)>>>(P.pp, P.perm, n, pp);
+            } else {
+                ISO_CUDA(weights_launch(X, n, d, dtype, false, sigma, o.alpha, o.include_self, M.nnbits, om_out, pp,
+                                        nullptr, s));
+            }
+        }
+        ev.rec(4, s);
         ISO_CUDA(phi_from_edges(TS, M.ed2, sigma, phi, s));
         if (!full) ISO_CUDA(omega_tree_mode(TS, phi, o.include_self, om, s));
-        ev.rec(4, s);
         // Algorithm 2 (search) + Algorithm 1, then Algorithm 4's labels
         ISO_CUDA(tree_search_and_label(TS, phi, om, o.alpha != 0.0 ? pp : nullptr, k, labels, residual, i_k, s));
         ev.rec(5, s);
@@ -336,15 +417,17 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
         ISO_CUDA(cudaMemcpy(&ss, TS.search, sizeof(ss), cudaMemcpyDeviceToHost));
     }
     g_prof_ms[0] = ev.ms(0, 1);
-    g_prof_ms[1] = ev.ms(2, 3);
+    g_prof_ms[1] = ev.ms(3, 4);
     g_prof_ms[2] = ev.ms(1, 2);
-    g_prof_ms[3] = ev.ms(3, 4);
+    g_prof_ms[3] = ev.ms(2, 3);
     g_prof_ms[4] = ev.ms(4, 5);
     g_prof_ms[5] = ev.ms(5, 6);
     g_prof_cnt[0] = cnt[MC_ROUNDS];
     g_prof_cnt[1] = cnt[MC_OVF_TOTAL] + cnt[MC_OVERFLOW];
     g_prof_cnt[2] = ss.passes + (need_labels ? 1 : 0);
     g_prof_cnt[3] = ss.max_depth;
+    g_prof_tiles[0] = g_prof_tiles[1] = 0;
+    if (permuted) ISO_CUDA(cudaMemcpy(g_prof_tiles, P.tiles, sizeof(g_prof_tiles), cudaMemcpyDeviceToHost));
     return map_status(fin, false);
 }
 
@@ -391,6 +474,10 @@ void isoclust_last_profile(double *t_ms6, int64_t *counts4) {
     if (counts4) for (int i = 0; i < 4; ++i) counts4[i] = g_prof_cnt[i];
 }
 
+void isoclust_last_omega_tiles(int64_t *tiles2) {
+    if (tiles2) { tiles2[0] = (int64_t)g_prof_tiles[0]; tiles2[1] = (int64_t)g_prof_tiles[1]; }
+}
+
 isoclust_status isoclust_cluster_mst(const void *X, int64_t n, int32_t d, int32_t dtype, const isoclust_opts *opts,
                                      int32_t *edge_u, int32_t *edge_v, double *edge_d2, void *stream) {
     if (!edge_u || !edge_v || !edge_d2) return fail(ISOCLUST_ERR_INVALID_ARG, "edge outputs are required");
@@ -424,6 +511,10 @@ isoclust_status isoclust_vertex_weights(const void *X, int64_t n, int32_t d, int
     cudaStream_t s = (cudaStream_t)stream;
     const bool fp64 = use_fp64_sweep(o, dtype);
     const int splits = mst_splits(n);
+    bool use_tc = false;
+    if ((st = use_tc_sweep(o, dtype, &use_tc))) return st;
+    TcScratch TC;
+    const int tsplits = use_tc ? tc_splits(n) : 1;
     const int dev = current_device();
     std::lock_guard<std::mutex> lock(g_call_mu[dev]);
     MstScratch M;
@@ -431,19 +522,21 @@ isoclust_status isoclust_vertex_weights(const void *X, int64_t n, int32_t d, int
     Arena meas;
     status = meas.take<uint32_t>(4);
     M.carve(meas, n, splits);
+    if (use_tc) TC.carve(meas, n, d, tsplits);
     void *base = scratch_acquire(meas.off, s, &st);
     if (!base) return st;
     Arena A{(char *)base, meas.off + 4096, 0, false};
     status = A.take<uint32_t>(4);
     M.carve(A, n, splits);
+    if (use_tc) TC.carve(A, n, d, tsplits);
     ISO_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t) * 4, s));
     ISO_CUDA(check_finite(X, n * (int64_t)d, dtype, status, nullptr, s));
     uint32_t hst = 0;
     ISO_CUDA(cudaMemcpyAsync(&hst, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     ISO_CUDA(cudaStreamSynchronize(s));
     if (hst) return map_status(hst, false);
-    if (!fp64) ISO_CUDA(nn_sweep(M, X, n, d, dtype, fp64, status, s));
-    ISO_CUDA(weights_launch(X, n, d, dtype, fp64, sigma, o.alpha, o.include_self, M.nnbits, omega, p, s));
+    if (!fp64) ISO_CUDA(nn_sweep(M, X, n, d, dtype, fp64, status, s, use_tc ? &TC : nullptr));
+    ISO_CUDA(weights_launch(X, n, d, dtype, fp64, sigma, o.alpha, o.include_self, M.nnbits, omega, p, nullptr, s));
     ISO_CUDA(cudaStreamSynchronize(s));
     ISO_CUDA(cudaMemcpy(&hst, status, sizeof(uint32_t), cudaMemcpyDeviceToHost));
     return map_status(hst, false);

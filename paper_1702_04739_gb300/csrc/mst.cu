@@ -474,15 +474,24 @@ static cudaError_t sweep_round(MstScratch &S, const void *X, int64_t n, int32_t 
     return cudaGetLastError();
 }
 
+__global__ void k_or_err(const uint32_t *src, uint32_t *dst) {
+    if (*src) atomicOr(dst, *src);
+}
+
 cudaError_t mst_build(MstScratch &S, const void *X, int64_t n, int32_t d, int dtype, bool sweep_fp64,
-                      uint32_t *status, cudaStream_t s) {
+                      uint32_t *status, cudaStream_t s, TcScratch *tc) {
     k_mst_init<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.comp, n, S.counters);
     const int R = log2_ceil(n) + 1;
     const int L = log2_ceil(n) + 1;
     cudaError_t e;
+    if (tc && (e = tc_prepare(*tc, (const float *)X, n, d, s))) return e;
     for (int r = 0; r < R; ++r) {
         k_round_begin<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.counters, S.cd2, S.cpair, n);
-        if ((e = sweep_round(S, X, n, d, dtype, sweep_fp64, s))) return e;
+        if (tc) {
+            if ((e = tc_sweep_round(*tc, S, (const float *)X, n, d, status, s))) return e;
+        } else if ((e = sweep_round(S, X, n, d, dtype, sweep_fp64, s))) {
+            return e;
+        }
         k_cmin_d2<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.comp, S.rowd2, S.rowj, n, S.cd2, S.counters);
         k_cmin_pair<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.comp, S.rowd2, S.rowj, n, S.cd2, S.cpair, S.counters);
         k_hook_tgt<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.comp, n, S.cd2, S.cpair, S.tgt, S.cu, S.cv, S.cdd, S.counters);
@@ -496,16 +505,22 @@ cudaError_t mst_build(MstScratch &S, const void *X, int64_t n, int32_t d, int dt
         k_relabel<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.comp, na, n, S.counters);
         k_round_end<<<1, 1, 0, ISO_S(s)>>>(S.counters);
     }
+    if (tc) k_or_err<<<1, 1, 0, ISO_S(s)>>>(tc->err, status);
     return cudaGetLastError();
 }
 
 cudaError_t nn_sweep(MstScratch &S, const void *X, int64_t n, int32_t d, int dtype, bool sweep_fp64,
-                     uint32_t *status, cudaStream_t s) {
-    (void)status;
+                     uint32_t *status, cudaStream_t s, TcScratch *tc) {
     k_mst_init<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.comp, n, S.counters);
     k_round_begin<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.counters, S.cd2, S.cpair, n);
-    cudaError_t e = sweep_round(S, X, n, d, dtype, sweep_fp64, s);
-    if (e) return e;
+    cudaError_t e;
+    if (tc) {
+        if ((e = tc_prepare(*tc, (const float *)X, n, d, s))) return e;
+        if ((e = tc_sweep_round(*tc, S, (const float *)X, n, d, status, s))) return e;
+        k_or_err<<<1, 1, 0, ISO_S(s)>>>(tc->err, status);
+    } else if ((e = sweep_round(S, X, n, d, dtype, sweep_fp64, s))) {
+        return e;
+    }
     k_nn_rows<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.rowd2, S.rowj, n, S.nnbits);
     return cudaGetLastError();
 }

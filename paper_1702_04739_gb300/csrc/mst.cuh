@@ -1,5 +1,8 @@
 // mst.cuh -- exact Euclidean minimum spanning tree by Boruvka rounds.
 #pragma once
+#include <cuda.h>
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace iso {
@@ -30,17 +33,46 @@ struct MstScratch {
 
 int mst_splits(int64_t n);
 
+// Tensor-core sweep state (mst_tc.cu): centred BF16 hi/lo copies of X padded
+// to the 128 x 64 tile grid, their TMA maps, squared norms and the best-8
+// candidate lists of every (column split, row).
+struct TcScratch {
+    int64_t n_pad = 0;
+    int32_t d_pad = 0;
+    int splits = 1;
+    __nv_bfloat16 *xh = nullptr, *xl = nullptr;   // rows in norm order: row r is point perm[r]
+    float *nrm = nullptr, *rsq = nullptr;          // |y|^2 and |y| of the represented rows
+    float *tmax = nullptr, *tsq = nullptr;         // per 128-row tile: max |y|^2 and its sqrt
+    float *mean = nullptr;
+    double *part = nullptr;
+    unsigned int *nmax_bits = nullptr;
+    int32_t *perm = nullptr, *iperm = nullptr, *vbuf = nullptr, *compp = nullptr;
+    uint64_t *keys = nullptr, *kbuf = nullptr;
+    float *tv = nullptr, *tu = nullptr;            // per (split, row): best-8 tile lower bounds, best upper bound
+    int32_t *tj = nullptr;
+    uint32_t *err = nullptr;
+    CUtensorMap map_h, map_l;
+    void carve(Arena &A, int64_t n, int32_t d, int splits);
+    static size_t bytes_needed(int64_t n, int32_t d, int splits);
+};
+int tc_splits(int64_t n);
+bool tc_supported();
+cudaError_t tc_prepare(TcScratch &T, const float *X, int64_t n, int32_t d, cudaStream_t s);
+cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t n, int32_t d, uint32_t *status,
+                           cudaStream_t s);
+
 // Builds the MST of X (n x d, dtype F32/F64) into S.eu/ev/ed2 (unsorted).
+// tc != nullptr selects the tensor-core sweep (F32 input).
 // sweep_fp64: use the exact FP64 sweep instead of FP32 + recheck.
 // rounds_out / rescans_out: host copies of the round and rescan counts are
 // written after the final stream synchronisation by the caller.
 cudaError_t mst_build(MstScratch &S, const void *X, int64_t n, int32_t d, int dtype, bool sweep_fp64,
-                      uint32_t *status, cudaStream_t s);
+                      uint32_t *status, cudaStream_t s, TcScratch *tc = nullptr);
 
 // Nearest-neighbour d2 of every row (exact key), one Boruvka-style sweep with
 // every point its own component.  Result in S.rowd2 / S.rowj.
 cudaError_t nn_sweep(MstScratch &S, const void *X, int64_t n, int32_t d, int dtype, bool sweep_fp64,
-                     uint32_t *status, cudaStream_t s);
+                     uint32_t *status, cudaStream_t s, TcScratch *tc = nullptr);
 
 // Sort S.eu/ev/ed2 by key (d2, u, v) into the output arrays (u < v).
 cudaError_t mst_sort_edges(MstScratch &S, int32_t *out_u, int32_t *out_v, double *out_d2, cudaStream_t s);

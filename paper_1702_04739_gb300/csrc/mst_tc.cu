@@ -1,0 +1,786 @@
+// mst_tc.cu -- Boruvka sweep on the 5th-generation tensor cores (tcgen05).
+//
+// Section 3.5's minimum spanning tree, one Boruvka round per launch: for
+// every row i, the candidates for its nearest point of another component.
+// The squared distance is taken from the Gram matrix,
+//     d2(i, j) = |x_i|^2 + |x_j|^2 - 2 <x_i, x_j>,
+// whose dense <x_i, x_j> tiles are the only tensor-core work: the centred
+// points are split into BF16 hi + lo parts and each 128x128 tile is
+// hi.hi + hi.lo + lo.hi (three kind::f16 MMAs per 16-wide K step) with FP32
+// accumulation in tensor memory.  Per CTA:
+//   warp 0      TMA producer: 128x64 BF16 tiles (128-byte swizzle) of the
+//               row block and the column block into a 3-stage ring,
+//   warp 1      allocates TMEM and issues the MMAs (one elected lane),
+//   warps 2..5  epilogue: tcgen05.ld of the FP32 accumulator (one row per
+//               thread), d2 = n_i + n_j - 2g, same-component mask, and a
+//               running best-8 per row in registers.
+// Two TMEM accumulators (2 x 128 columns) let the MMA of the next column
+// tile overlap the epilogue of the current one.  Every mbarrier wait is
+// bounded; on timeout the kernel raises an error flag and stops.
+// The candidates are exact-keyed in FP64 by k_recheck_tc inside a rigorous
+// error margin; rows whose margin is not closed by the best 8 are rescanned.
+#include <cuda.h>
+#include <stddef.h>
+
+#include "mst.cuh"
+
+namespace iso {
+
+namespace {
+constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64;      // BK bf16 = 128 bytes (one swizzle row)
+constexpr int TC_STAGES = 3;                              // ring depth, A and B streaming
+constexpr int TC_STAGES_B = 4;                            // ring depth, A resident
+constexpr int TC_AREG_BYTES = 4 * 128 * 64 * 2;           // A hi + lo, up to 2 K chunks (d_pad <= 128)
+constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 2;         // 16 KB
+constexpr int TC_STAGE_BYTES = 4 * TC_TILE_BYTES;        // A hi, A lo, B hi, B lo
+constexpr int TC_THREADS = 192;
+constexpr int TC_TOPK = 8;                                // best column tiles kept per row
+constexpr long long TC_WAIT_CYCLES = 4000000000LL;
+
+// Column metadata first: the epilogue reads it with 16-byte vector loads.
+struct __align__(16) TcShared {
+    float cnorm[2][TC_BN];
+    int32_t ccomp[2][TC_BN];
+    uint64_t full[4], empty[4];
+    uint64_t acc_full[2], acc_empty[2];
+    uint64_t a_full, a_empty;
+    uint32_t tmem_base;
+    uint32_t pad;
+};
+static_assert(offsetof(TcShared, cnorm) % 16 == 0, "cnorm must be 16-byte aligned");
+static_assert(offsetof(TcShared, ccomp) % 16 == 0, "ccomp must be 16-byte aligned");
+static_assert(offsetof(TcShared, full) % 8 == 0, "mbarriers must be 8-byte aligned");
+static_assert((TC_STAGES * TC_STAGE_BYTES) % 1024 == 0, "TcShared follows 1024-aligned tiles");
+static_assert(TC_STAGES <= 4 && TC_STAGES_B <= 4, "barrier arrays hold 4 stages");
+constexpr int TC_SMEM_STREAM = TC_STAGES * TC_STAGE_BYTES + 1024 + (int)sizeof(TcShared);
+constexpr int TC_SMEM_ARES = TC_AREG_BYTES + TC_STAGES_B * 2 * TC_TILE_BYTES + 1024 + (int)sizeof(TcShared);
+static_assert(TC_SMEM_STREAM <= 227 * 1024 && TC_SMEM_ARES <= 227 * 1024, "shared memory budget");
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait (about 2 s of SM cycles); false on timeout or when another
+// role has already failed.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t *err) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63u) == 63u) {
+            if (*(volatile uint32_t *)err) return false;
+            if (clock64() - t0 > TC_WAIT_CYCLES) {
+                atomicOr(err, DEV_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart; tile bases are 1024-byte aligned.
+__device__ __forceinline__ uint64_t make_sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;                  // leading byte offset (unused with this swizzle)
+    d |= (uint64_t)(1024u >> 4) << 32;       // stride byte offset
+    d |= (uint64_t)1 << 46;                  // descriptor version
+    d |= (uint64_t)2 << 61;                  // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both K-major, M=128, N=128.
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
+                              ((uint32_t)(TC_BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(TC_IDESC), "r"(accum)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void top_insert(float (&v)[TC_TOPK], int32_t (&j)[TC_TOPK], float x, int32_t c) {
+    v[TC_TOPK - 1] = x;
+    j[TC_TOPK - 1] = c;
+#pragma unroll
+    for (int q = TC_TOPK - 1; q > 0; --q) {
+        if (v[q] < v[q - 1]) {
+            float tv = v[q]; v[q] = v[q - 1]; v[q - 1] = tv;
+            int32_t tj = j[q]; j[q] = j[q - 1]; j[q - 1] = tj;
+        }
+    }
+}
+
+__device__ __forceinline__ bool mst_active(const int32_t *counters) {
+    return *((volatile const int32_t *)(counters + MC_NCOMP)) > 1;
+}
+
+// ARES: the row block's A tiles (hi, lo, every K chunk) stay resident in
+// shared memory for a whole work item and only the column blocks stream
+// through the ring (used when d_pad <= 128); otherwise A and B chunks
+// stream together.
+template <bool ARES>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUtensorMap tml,
+           const float *__restrict__ rnorm, const float *__restrict__ rsq, const float *__restrict__ tmax,
+           const float *__restrict__ tsq, float acoef, float bcoef, const int32_t *__restrict__ comp, int64_t n,
+           int ntiles, int kchunks, int splits, const int32_t *counters, float *__restrict__ out_v,
+           int32_t *__restrict__ out_j, float *__restrict__ out_u, uint32_t *err) {
+    if (!mst_active(counters)) return;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    constexpr int NST = ARES ? TC_STAGES_B : TC_STAGES;                 // ring depth
+    constexpr int SB = ARES ? 2 * TC_TILE_BYTES : TC_STAGE_BYTES;       // bytes per ring stage
+    unsigned char *areg = base;                                         // resident A (ARES)
+    unsigned char *ring = ARES ? base + TC_AREG_BYTES : base;
+    TcShared *sh = (TcShared *)(ring + NST * SB);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NST; ++s) {
+            mbar_init(&sh->full[s], 1);
+            mbar_init(&sh->empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&sh->acc_full[a], 1);
+            mbar_init(&sh->acc_empty[a], 4);
+        }
+        mbar_init(&sh->a_full, 1);
+        mbar_init(&sh->a_empty, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(&sh->tmem_base))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sh->tmem_base;
+
+    const int64_t items = (int64_t)ntiles * splits;
+    const int tiles_per_split = (ntiles + splits - 1) / splits;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            uint32_t stage = 0, phase = 0, a_phase = 0;
+            bool ok = true;
+            for (int64_t w = blockIdx.x; w < items && ok; w += gridDim.x) {
+                const int rt = (int)(w / splits), sp = (int)(w % splits);
+                const int c0 = sp * tiles_per_split, c1 = min(ntiles, c0 + tiles_per_split);
+                if (ARES) {
+                    if (!(ok = mbar_wait(&sh->a_empty, a_phase ^ 1u, err))) break;
+                    mbar_expect_tx(&sh->a_full, (uint32_t)(kchunks * 2 * TC_TILE_BYTES));
+                    for (int kc = 0; kc < kchunks; ++kc) {
+                        tma_load_2d(areg + (2 * kc) * TC_TILE_BYTES, &tmh, kc * TC_BK, rt * TC_BM, &sh->a_full);
+                        tma_load_2d(areg + (2 * kc + 1) * TC_TILE_BYTES, &tml, kc * TC_BK, rt * TC_BM, &sh->a_full);
+                    }
+                    a_phase ^= 1u;
+                }
+                for (int ct = c0; ct < c1 && ok; ++ct) {
+                    for (int kc = 0; kc < kchunks; ++kc) {
+                        if (!(ok = mbar_wait(&sh->empty[stage], phase ^ 1u, err))) break;
+                        unsigned char *st = ring + stage * SB;
+                        mbar_expect_tx(&sh->full[stage], (uint32_t)SB);
+                        if (ARES) {
+                            tma_load_2d(st, &tmh, kc * TC_BK, ct * TC_BN, &sh->full[stage]);
+                            tma_load_2d(st + TC_TILE_BYTES, &tml, kc * TC_BK, ct * TC_BN, &sh->full[stage]);
+                        } else {
+                            tma_load_2d(st, &tmh, kc * TC_BK, rt * TC_BM, &sh->full[stage]);
+                            tma_load_2d(st + TC_TILE_BYTES, &tml, kc * TC_BK, rt * TC_BM, &sh->full[stage]);
+                            tma_load_2d(st + 2 * TC_TILE_BYTES, &tmh, kc * TC_BK, ct * TC_BN, &sh->full[stage]);
+                            tma_load_2d(st + 3 * TC_TILE_BYTES, &tml, kc * TC_BK, ct * TC_BN, &sh->full[stage]);
+                        }
+                        if (++stage == NST) { stage = 0; phase ^= 1u; }
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            uint32_t stage = 0, phase = 0, acc = 0, acc_phase = 0, a_phase = 0;
+            bool ok = true;
+            for (int64_t w = blockIdx.x; w < items && ok; w += gridDim.x) {
+                const int sp = (int)(w % splits);
+                const int c0 = sp * tiles_per_split, c1 = min(ntiles, c0 + tiles_per_split);
+                if (ARES) {
+                    if (!(ok = mbar_wait(&sh->a_full, a_phase, err))) break;
+                    tc_fence_after();
+                }
+                for (int ct = c0; ct < c1 && ok; ++ct) {
+                    if (!(ok = mbar_wait(&sh->acc_empty[acc], acc_phase ^ 1u, err))) break;
+                    tc_fence_after();
+                    const uint32_t dt = tmem + acc * TC_BN;
+                    for (int kc = 0; kc < kchunks; ++kc) {
+                        if (!(ok = mbar_wait(&sh->full[stage], phase, err))) break;
+                        tc_fence_after();
+                        const uint32_t sb = smem_u32(ring + stage * SB);
+                        uint64_t ah, al, bh, bl;
+                        if (ARES) {
+                            const uint32_t sa = smem_u32(areg + (2 * kc) * TC_TILE_BYTES);
+                            ah = make_sw128_desc(sa);
+                            al = make_sw128_desc(sa + TC_TILE_BYTES);
+                            bh = make_sw128_desc(sb);
+                            bl = make_sw128_desc(sb + TC_TILE_BYTES);
+                        } else {
+                            ah = make_sw128_desc(sb);
+                            al = make_sw128_desc(sb + TC_TILE_BYTES);
+                            bh = make_sw128_desc(sb + 2 * TC_TILE_BYTES);
+                            bl = make_sw128_desc(sb + 3 * TC_TILE_BYTES);
+                        }
+#pragma unroll
+                        for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                            const uint64_t o = (uint64_t)(kk * 32) >> 4;   // 16 bf16 = 32 bytes
+                            mma_bf16(dt, ah + o, bh + o, (kc > 0 || kk > 0) ? 1u : 0u);
+                            mma_bf16(dt, ah + o, bl + o, 1u);
+                            mma_bf16(dt, al + o, bh + o, 1u);
+                        }
+                        mma_commit(&sh->empty[stage]);
+                        if (++stage == NST) { stage = 0; phase ^= 1u; }
+                    }
+                    if (!ok) break;
+                    mma_commit(&sh->acc_full[acc]);
+                    if (++acc == 2) { acc = 0; acc_phase ^= 1u; }
+                }
+                if (ARES && ok) {
+                    mma_commit(&sh->a_empty);     // A region free once this item's MMAs are done
+                    a_phase ^= 1u;
+                }
+            }
+        }
+    } else {
+        // ------------------------------------------------ epilogue (warps 2..5)
+        const int et = threadIdx.x - 64;               // 0..127
+        const int quad = warp & 3;                     // TMEM lane quadrant of this warp
+        const int trow = quad * 32 + lane;             // row within the tile = TMEM lane
+        uint32_t acc = 0, acc_phase = 0;
+        bool ok = true;
+        for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
+            const int rt = (int)(w / splits), sp = (int)(w % splits);
+            const int c0 = sp * tiles_per_split, c1 = min(ntiles, c0 + tiles_per_split);
+            const int64_t row = (int64_t)rt * TC_BM + trow;
+            const float nrow = row < n ? rnorm[row] : 0.0f;
+            const float srow = row < n ? rsq[row] : 0.0f;
+            const int32_t crow = row < n ? comp[row] : -3;
+            float ubest = INFINITY;        // smallest upper bound of a candidate's d2
+            float bv[TC_TOPK];
+            int32_t bj[TC_TOPK];
+#pragma unroll
+            for (int q = 0; q < TC_TOPK; ++q) { bv[q] = INFINITY; bj[q] = -1; }
+            // column metadata, prefetched one tile ahead
+            int64_t pcol = (int64_t)c0 * TC_BN + et;
+            float pn = pcol < n ? rnorm[pcol] : INFINITY;
+            int32_t pc = pcol < n ? comp[pcol] : -2;
+            for (int ct = c0; ct < c1; ++ct) {
+                sh->cnorm[acc][et] = pn;
+                sh->ccomp[acc][et] = pc;
+                if (ct + 1 < c1) {
+                    pcol = (int64_t)(ct + 1) * TC_BN + et;
+                    pn = pcol < n ? rnorm[pcol] : INFINITY;
+                    pc = pcol < n ? comp[pcol] : -2;
+                }
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                if (ok) ok = mbar_wait(&sh->acc_full[acc], acc_phase, err);
+                tc_fence_after();
+                float m = INFINITY;
+                if (ok) {
+                    const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + acc * TC_BN;
+#pragma unroll 1
+                    for (int cc = 0; cc < TC_BN; cc += 32) {
+                        uint32_t g[32];
+                        tmem_ld32(tbase + cc, g);
+#pragma unroll
+                        for (int q = 0; q < 32; q += 4) {
+                            const float4 nc = *reinterpret_cast<const float4 *>(&sh->cnorm[acc][cc + q]);
+                            const int4 cm = *reinterpret_cast<const int4 *>(&sh->ccomp[acc][cc + q]);
+                            const float ncv[4] = {nc.x, nc.y, nc.z, nc.w};
+                            const int32_t cmv[4] = {cm.x, cm.y, cm.z, cm.w};
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const float v = __fmaf_rn(-2.0f, __uint_as_float(g[q + u]), __fadd_rn(nrow, ncv[u]));
+                                m = fminf(m, cmv[u] != crow ? v : INFINITY);
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sh->acc_empty[acc]);
+                if (++acc == 2) { acc = 0; acc_phase ^= 1u; }
+                // rigorous bounds of the tile's smallest d2 of the represented points:
+                // accumulation + dropped lo.lo (A s_i s_j) and FP32 norm/epilogue rounding
+                const float dlt = acoef * srow * __ldg(tsq + ct) + bcoef * (nrow + __ldg(tmax + ct));
+                const float lb = m - dlt;
+                ubest = fminf(ubest, m + dlt);
+                if (lb < bv[TC_TOPK - 1]) top_insert(bv, bj, lb, ct);   // once per tile
+            }
+            if (row < n) {
+                const size_t o = ((size_t)sp * n + row) * TC_TOPK;
+#pragma unroll
+                for (int q = 0; q < TC_TOPK; ++q) { out_v[o + q] = bv[q]; out_j[o + q] = bj[q]; }
+                out_u[(size_t)sp * n + row] = ubest;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+    }
+}
+
+// Centre, split into BF16 hi + lo (zero padding to the tile grid) and the
+// squared norms of the represented points.
+__global__ void k_tc_mean_partial(const float *__restrict__ X, int64_t n, int32_t d, int64_t rows_per,
+                                  double *__restrict__ part) {
+    const int t = threadIdx.x + blockIdx.y * blockDim.x;
+    if (t >= d) return;
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per, r1 = min(n, r0 + rows_per);
+    double s = 0.0;
+    for (int64_t r = r0; r < r1; ++r) s += (double)X[r * d + t];
+    part[(int64_t)blockIdx.x * d + t] = s;
+}
+
+__global__ void k_tc_mean_final(const double *__restrict__ part, int nparts, int64_t n, int32_t d,
+                                float *__restrict__ mean) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= d) return;
+    double s = 0.0;
+    for (int p = 0; p < nparts; ++p) s += part[(int64_t)p * d + t];
+    mean[t] = (float)(s / (double)n);
+}
+
+__global__ void k_tc_prenorm_keys(const float *__restrict__ X, const float *__restrict__ mean, int64_t n,
+                                  int32_t d, uint64_t *__restrict__ keys, int32_t *__restrict__ vals) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int t = 0; t < d; ++t) {
+        const double y = (double)__fsub_rn(X[i * d + t], mean[t]);
+        s += y * y;
+    }
+    keys[i] = ((uint64_t)__float_as_uint((float)s) << 32) | (uint64_t)i;   // non-negative: bits are monotone
+    vals[i] = (int32_t)i;
+}
+
+__global__ void k_tc_inverse(const int32_t *__restrict__ perm, int64_t n, int32_t *__restrict__ iperm) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) iperm[perm[r]] = (int32_t)r;
+}
+
+// Rows in norm order: row r of the split copies is point perm[r].
+__global__ void k_tc_split(const float *__restrict__ X, const float *__restrict__ mean,
+                           const int32_t *__restrict__ perm, int64_t n, int32_t d, int64_t n_pad, int32_t d_pad,
+                           __nv_bfloat16 *__restrict__ xh, __nv_bfloat16 *__restrict__ xl) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n_pad * d_pad) return;
+    const int64_t r = idx / d_pad, t = idx - r * d_pad;
+    float y = 0.0f;
+    if (r < n && t < d) y = __fsub_rn(X[(int64_t)perm[r] * d + t], mean[t]);
+    const __nv_bfloat16 h = __float2bfloat16_rn(y);
+    const __nv_bfloat16 l = __float2bfloat16_rn(__fsub_rn(y, __bfloat162float(h)));
+    xh[idx] = h;
+    xl[idx] = l;
+}
+
+__global__ void k_tc_norms(const __nv_bfloat16 *__restrict__ xh, const __nv_bfloat16 *__restrict__ xl,
+                           int64_t n_pad, int32_t d_pad, float *__restrict__ nrm, float *__restrict__ sq,
+                           unsigned int *__restrict__ nmax_bits) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_pad) return;
+    double s = 0.0;
+    for (int t = 0; t < d_pad; ++t) {
+        const double v = (double)__bfloat162float(xh[r * d_pad + t]) + (double)__bfloat162float(xl[r * d_pad + t]);
+        s += v * v;
+    }
+    const float f = (float)s;
+    nrm[r] = f;
+    sq[r] = (float)sqrt(s);
+    atomicMax(nmax_bits, __float_as_uint(f));
+}
+
+// per 128-row tile: the largest squared norm and its square root
+__global__ void k_tc_tile_max(const float *__restrict__ nrm, int64_t n_pad, float *__restrict__ tmax,
+                              float *__restrict__ tsq) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t * TC_BM >= n_pad) return;
+    float m = 0.0f;
+    for (int r = 0; r < TC_BM; ++r) m = fmaxf(m, nrm[t * TC_BM + r]);
+    tmax[t] = m;
+    tsq[t] = sqrtf(m) * 1.0000002f;       // rounded up
+}
+
+__global__ void k_tc_gather_comp(const int32_t *__restrict__ comp, const int32_t *__restrict__ perm, int64_t n,
+                                 int32_t *__restrict__ compp, const int32_t *counters) {
+    if (!mst_active(counters)) return;
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) compp[r] = comp[perm[r]];
+}
+
+// One warp per (norm-ordered) row r, the point i = perm[r].  The column
+// splits' best-8 tile lower bounds and their best upper bound U are merged.
+// The epilogue's bounds hold for the BF16-represented points; the exact
+// points differ by the representation error rep, so a tile can hold the
+// nearest foreign point only if its lower bound is <= U + 2 rep.  Those
+// tiles' columns are filtered with FP32 direct differences and the
+// survivors keyed in FP64.  If the 8th kept tile still qualifies, the row is
+// queued for a rescan.
+__global__ void __launch_bounds__(256) k_recheck_tc(const float *__restrict__ X, int64_t n, int32_t d, int splits,
+                                                    const float *__restrict__ tv, const int32_t *__restrict__ tj,
+                                                    const float *__restrict__ tu, const float *__restrict__ rsq,
+                                                    const int32_t *__restrict__ perm, const int32_t *__restrict__ comp,
+                                                    const unsigned int *__restrict__ nmax_bits, double eps_rep,
+                                                    double e32, double *__restrict__ rowd2, int32_t *__restrict__ rowj,
+                                                    int32_t *__restrict__ ovf, int32_t *counters) {
+    if (!mst_active(counters)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (r >= n) return;
+    const int64_t i = perm[r];
+    float bv[TC_TOPK];
+    int32_t bj[TC_TOPK];
+#pragma unroll
+    for (int q = 0; q < TC_TOPK; ++q) { bv[q] = INFINITY; bj[q] = -1; }
+    float U = INFINITY;
+    for (int s = 0; s < splits; ++s) {
+        const size_t o = ((size_t)s * n + r) * TC_TOPK;
+        U = fminf(U, tu[(size_t)s * n + r]);
+        for (int q = 0; q < TC_TOPK; ++q) {
+            const float v = tv[o + q];
+            if (!(v < bv[TC_TOPK - 1])) break;          // lists are sorted
+            top_insert(bv, bj, v, tj[o + q]);
+        }
+    }
+    if (bj[0] < 0 || !(U < INFINITY)) {
+        if (lane == 0) rowj[i] = -1;
+        return;
+    }
+    // representation error: |d2(x) - d2(x~)| <= 2 e d (|y_i| + |y_j|) + e^2 (|y_i| + |y_j|)^2
+    const double si = (double)rsq[r], smax = sqrt((double)__uint_as_float(*nmax_bits));
+    const double Ud = (double)U;
+    // distances move by at most w = eps (|y_i| + |y_max|) between the exact
+    // and the represented points
+    const double w = eps_rep * (si + smax);
+    const double su = sqrt(fmax(Ud, 0.0));
+    const double hi_true = (su + w) * (su + w) * (1.0 + 1e-12);     // exact nearest foreign d2 <= this
+    const double sh = sqrt(hi_true);
+    const double tile_cut = (sh + w) * (sh + w) * (1.0 + 1e-12);   // represented d2 of any candidate <= this
+    if (bj[TC_TOPK - 1] >= 0 && (double)bv[TC_TOPK - 1] <= tile_cut) {
+        if (lane == 0) {
+            const int q = atomicAdd(counters + MC_OVERFLOW, 1);
+            ovf[q] = (int32_t)i;
+            rowj[i] = -2;
+        }
+        return;
+    }
+    const double cut32 = hi_true * (1.0 + e32) + 1e-300;
+    const int32_t ci = comp[i];
+    const float *xi = X + i * d;
+    double best = INFINITY;
+    int32_t bestj = -1;
+    for (int q = 0; q < TC_TOPK; ++q) {
+        if (bj[q] < 0 || (double)bv[q] > tile_cut) break;
+        for (int c = lane; c < TC_BN; c += 32) {
+            const int64_t jp = (int64_t)bj[q] * TC_BN + c;
+            if (jp >= n) continue;
+            const int64_t j = perm[jp];
+            if (comp[j] == ci) continue;
+            const float *xj = X + j * d;
+            float acc = 0.0f;
+            for (int t = 0; t < d; ++t) {
+                const float df = __fsub_rn(xi[t], xj[t]);
+                acc = __fmaf_rn(df, df, acc);
+            }
+            if ((double)acc <= cut32) {
+                const double e = exact_d2(xi, xj, d);
+                if (bestj < 0 || key_less(e, (int32_t)i, (int32_t)j, best, (int32_t)i, bestj)) { best = e; bestj = (int32_t)j; }
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double od = __shfl_xor_sync(0xffffffffu, best, o);
+        const int32_t oj = __shfl_xor_sync(0xffffffffu, bestj, o);
+        if (oj >= 0 && (bestj < 0 || key_less(od, (int32_t)i, oj, best, (int32_t)i, bestj))) { best = od; bestj = oj; }
+    }
+    if (lane == 0) {
+        rowd2[i] = best;
+        rowj[i] = bestj;
+    }
+}
+
+// Self-contained rescan of a queued row: FP32 direct differences give the
+// minimum m; every column within the FP32 error margin of m is keyed in FP64.
+__global__ void __launch_bounds__(256) k_rescan_tc(const float *__restrict__ X, int64_t n, int32_t d,
+                                                   const int32_t *__restrict__ comp, const int32_t *__restrict__ ovf,
+                                                   double mul, double add, double *__restrict__ rowd2,
+                                                   int32_t *__restrict__ rowj, int32_t *counters) {
+    if (!mst_active(counters)) return;
+    __shared__ float smin[256];
+    __shared__ double sd[256];
+    __shared__ int32_t sj[256];
+    const int nq = counters[MC_OVERFLOW];
+    for (int q = blockIdx.x; q < nq; q += gridDim.x) {
+        const int64_t i = ovf[q];
+        const int32_t ci = comp[i];
+        const float *xi = X + i * d;
+        float m = INFINITY;
+        for (int64_t j = threadIdx.x; j < n; j += 256) {
+            if (comp[j] == ci) continue;
+            float acc = 0.0f;
+            for (int t = 0; t < d; ++t) {
+                const float df = __fsub_rn(xi[t], X[j * d + t]);
+                acc = __fmaf_rn(df, df, acc);
+            }
+            m = fminf(m, acc);
+        }
+        smin[threadIdx.x] = m;
+        __syncthreads();
+        for (int s = 128; s > 0; s >>= 1) {
+            if (threadIdx.x < s) smin[threadIdx.x] = fminf(smin[threadIdx.x], smin[threadIdx.x + s]);
+            __syncthreads();
+        }
+        const double tau = (double)smin[0] * mul + add;
+        double bd = INFINITY;
+        int32_t bjj = -1;
+        for (int64_t j = threadIdx.x; j < n; j += 256) {
+            if (comp[j] == ci) continue;
+            float acc = 0.0f;
+            for (int t = 0; t < d; ++t) {
+                const float df = __fsub_rn(xi[t], X[j * d + t]);
+                acc = __fmaf_rn(df, df, acc);
+            }
+            if ((double)acc <= tau) {
+                const double e = exact_d2(xi, X + j * d, d);
+                if (bjj < 0 || key_less(e, (int32_t)i, (int32_t)j, bd, (int32_t)i, bjj)) { bd = e; bjj = (int32_t)j; }
+            }
+        }
+        sd[threadIdx.x] = bd;
+        sj[threadIdx.x] = bjj;
+        __syncthreads();
+        for (int s = 128; s > 0; s >>= 1) {
+            if (threadIdx.x < s) {
+                const double od = sd[threadIdx.x + s];
+                const int32_t oj = sj[threadIdx.x + s];
+                if (oj >= 0 && (sj[threadIdx.x] < 0 ||
+                                key_less(od, (int32_t)i, oj, sd[threadIdx.x], (int32_t)i, sj[threadIdx.x]))) {
+                    sd[threadIdx.x] = od;
+                    sj[threadIdx.x] = oj;
+                }
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            rowd2[i] = sd[0];
+            rowj[i] = sj[0];
+        }
+        __syncthreads();
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+cudaError_t make_map(CUtensorMap *m, const __nv_bfloat16 *base, int64_t n_pad, int32_t d_pad) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    cuuint64_t dims[2] = {(cuuint64_t)d_pad, (cuuint64_t)n_pad};
+    cuuint64_t strides[1] = {(cuuint64_t)d_pad * 2};
+    cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)TC_BM};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)base, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+}  // namespace
+
+size_t TcScratch::bytes_needed(int64_t n, int32_t d, int splits) {
+    Arena A;
+    TcScratch t;
+    t.carve(A, n, d, splits);
+    return A.off;
+}
+
+void TcScratch::carve(Arena &A, int64_t n, int32_t d, int splits_) {
+    splits = splits_;
+    n_pad = ceil_div(n, TC_BM) * TC_BM;
+    d_pad = (int32_t)(ceil_div(d, TC_BK) * TC_BK);
+    const int64_t nt = n_pad / TC_BM;
+    xh = A.take<__nv_bfloat16>((size_t)n_pad * d_pad, 1024);
+    xl = A.take<__nv_bfloat16>((size_t)n_pad * d_pad, 1024);
+    nrm = A.take<float>(n_pad);
+    rsq = A.take<float>(n_pad);
+    tmax = A.take<float>(nt);
+    tsq = A.take<float>(nt);
+    mean = A.take<float>(d);
+    part = A.take<double>((size_t)64 * d);
+    nmax_bits = A.take<unsigned int>(4);
+    perm = A.take<int32_t>(n);
+    iperm = A.take<int32_t>(n);
+    vbuf = A.take<int32_t>(n);
+    keys = A.take<uint64_t>(n);
+    kbuf = A.take<uint64_t>(n);
+    compp = A.take<int32_t>(n);
+    tv = A.take<float>((size_t)splits * n * TC_TOPK);
+    tj = A.take<int32_t>((size_t)splits * n * TC_TOPK);
+    tu = A.take<float>((size_t)splits * n);
+    err = A.take<uint32_t>(4);
+}
+
+int tc_splits(int64_t n) {
+    const int64_t rt = ceil_div(n, TC_BM);
+    int64_t s = ceil_div((int64_t)num_sms() * 16, rt > 0 ? rt : 1);
+    const int64_t max_s = rt / 4 > 1 ? rt / 4 : 1;
+    if (s > max_s) s = max_s;
+    if (s > 16) s = 16;
+    if (s < 1) s = 1;
+    return (int)s;
+}
+
+bool tc_supported() {
+    int dev = 0, major = 0, minor = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    return major == 10 && minor == 3 && encode_fn() != nullptr;
+}
+
+cudaError_t tc_prepare(TcScratch &T, const float *X, int64_t n, int32_t d, cudaStream_t s) {
+    cudaError_t e;
+    const int64_t rows_per = ceil_div(n, 64);
+    dim3 gm(64, (unsigned)ceil_div(d, 128));
+    k_tc_mean_partial<<<gm, 128, 0, ISO_S(s)>>>(X, n, d, rows_per, T.part);
+    k_tc_mean_final<<<(unsigned)ceil_div(d, 128), 128, 0, ISO_S(s)>>>(T.part, 64, n, d, T.mean);
+    // norm order: tiles of points with similar |x - c| give tight tile bounds
+    k_tc_prenorm_keys<<<(unsigned)ceil_div(n, 256), 256, 0, ISO_S(s)>>>(X, T.mean, n, d, T.keys, T.perm);
+    if ((e = sort_pairs_u64(T.keys, T.perm, T.kbuf, T.vbuf, n, s))) return e;
+    k_tc_inverse<<<(unsigned)ceil_div(n, 256), 256, 0, ISO_S(s)>>>(T.perm, n, T.iperm);
+    const int64_t tot = T.n_pad * T.d_pad;
+    k_tc_split<<<(unsigned)ceil_div(tot, 256), 256, 0, ISO_S(s)>>>(X, T.mean, T.perm, n, d, T.n_pad, T.d_pad, T.xh,
+                                                                  T.xl);
+    if ((e = cudaMemsetAsync(T.nmax_bits, 0, sizeof(unsigned int), s))) return e;
+    k_tc_norms<<<(unsigned)ceil_div(T.n_pad, 256), 256, 0, ISO_S(s)>>>(T.xh, T.xl, T.n_pad, T.d_pad, T.nrm, T.rsq,
+                                                                      T.nmax_bits);
+    k_tc_tile_max<<<(unsigned)ceil_div(T.n_pad / TC_BM, 128), 128, 0, ISO_S(s)>>>(T.nrm, T.n_pad, T.tmax, T.tsq);
+    if ((e = cudaMemsetAsync(T.err, 0, sizeof(uint32_t), s))) return e;
+    if ((e = make_map(&T.map_h, T.xh, T.n_pad, T.d_pad))) return e;
+    if ((e = make_map(&T.map_l, T.xl, T.n_pad, T.d_pad))) return e;
+    static bool attr = false;
+    if (!attr) {
+        if ((e = cudaFuncSetAttribute(k_sweep_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_STREAM)))
+            return e;
+        if ((e = cudaFuncSetAttribute(k_sweep_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_ARES)))
+            return e;
+        attr = true;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t n, int32_t d, uint32_t *status,
+                           cudaStream_t s) {
+    const int ntiles = (int)(T.n_pad / TC_BM);
+    const int kchunks = T.d_pad / TC_BK;
+    const int64_t items = (int64_t)ntiles * T.splits;
+    const int64_t nsm = (int64_t)num_sms();
+    const unsigned grid = (unsigned)(items < nsm ? items : nsm);
+    k_tc_gather_comp<<<(unsigned)ceil_div(n, 256), 256, 0, ISO_S(s)>>>(S.comp, T.perm, n, T.compp, S.counters);
+    // d2 = n_i + n_j - 2g against d2 of the represented points: tensor-core
+    // FP32 accumulation of 3 d_pad products (worst case: one rounding of the
+    // running magnitude per addition, 2^-23) and the dropped lo.lo term
+    // (2^-18), both times 2|y_i||y_j|; FP32 rounding of the norms and the
+    // epilogue, 6 x 2^-24 (n_i + n_j).  25 % headroom.
+    const double u = 1.1920928955078125e-07;   // 2^-23
+    const float acoef = (float)(1.25 * 2.0 * (3.0 * T.d_pad * u + 3.814697265625e-06));
+    const float bcoef = (float)(1.25 * 6.0 * 5.9604644775390625e-08);
+    if (kchunks <= 2)
+        k_sweep_tc<true><<<grid, TC_THREADS, TC_SMEM_ARES, ISO_S(s)>>>(
+            T.map_h, T.map_l, T.nrm, T.rsq, T.tmax, T.tsq, acoef, bcoef, T.compp, n, ntiles, kchunks, T.splits,
+            S.counters, T.tv, T.tj, T.tu, T.err);
+    else
+        k_sweep_tc<false><<<grid, TC_THREADS, TC_SMEM_STREAM, ISO_S(s)>>>(
+            T.map_h, T.map_l, T.nrm, T.rsq, T.tmax, T.tsq, acoef, bcoef, T.compp, n, ntiles, kchunks, T.splits,
+            S.counters, T.tv, T.tj, T.tu, T.err);
+    // representation error of a centred point by BF16 hi + lo: 2^-18 relative
+    // per element, plus the FP32 rounding of x - c (2^-24); 25 % headroom
+    const double eps_rep = 1.25 * (3.814697265625e-06 + 5.9604644775390625e-08);
+    const double e = 1.1 * (double)(d + 3) * 5.9604644775390625e-08;
+    k_recheck_tc<<<(unsigned)ceil_div(n * 32, 256), 256, 0, ISO_S(s)>>>(X, n, d, T.splits, T.tv, T.tj, T.tu, T.rsq,
+                                                                        T.perm, S.comp, T.nmax_bits, eps_rep, e,
+                                                                        S.rowd2, S.rowj, S.ovf_rows, S.counters);
+    const double mul = (1.0 + e) / (1.0 - e);
+    const double add = (double)(d + 1) * 1.401298464324817e-45 * 4.0;
+    k_rescan_tc<<<(unsigned)(num_sms() * 4), 256, 0, ISO_S(s)>>>(X, n, d, S.comp, S.ovf_rows, mul, add, S.rowd2, S.rowj,
+                                                                 S.counters);
+    (void)status;
+    return cudaGetLastError();
+}
+
+}  // namespace iso

@@ -612,6 +612,8 @@ cudaError_t orient_tree(TreeScratch &S, const int32_t *eu, const int32_t *ev, in
         k_fill_i32<<<1, 32, 0, ISO_S(s)>>>(T.adj_off, 2, 0);
         k_fill_i32<<<1, 32, 0, ISO_S(s)>>>(T.leaves, 1, 0);
         k_fill_i32<<<1, 32, 0, ISO_S(s)>>>(T.depth, 1, 0);
+        k_fill_i32<<<1, 32, 0, ISO_S(s)>>>(S.pre, 1, 0);
+        T.pre = S.pre;
         SearchState *SS = S.search;
         int one = 1, zero = 0;
         if ((e = cudaMemcpyAsync(&SS->nleaves, &one, sizeof(int), cudaMemcpyHostToDevice, s))) return e;
@@ -661,6 +663,7 @@ cudaError_t orient_tree(TreeScratch &S, const int32_t *eu, const int32_t *ev, in
     if (da != T.depth) {
         if ((e = cudaMemcpyAsync(T.depth, da, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s))) return e;
     }
+    T.pre = pa;
     k_bfs_keys<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(T.depth, pa, n, S.bkeys, S.ib);
     if ((e = sort_pairs_u64(S.bkeys, S.ib, S.kbuf, S.vbuf, n, s))) return e;
     k_bfs_pos<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.ib, S.bkeys, n, T.bfs_pos, S.search);

@@ -36,6 +36,7 @@ struct TreeDev {
     uint64_t *adj_key;   // [2(n-1)] (src<<32 | dst), sorted
     int32_t *leaves;     // [n]
     int32_t *depth;      // [n]
+    int32_t *pre;        // [n] preorder rank with children in ascending index (set by orient_tree)
 };
 
 struct TreeScratchSizes;

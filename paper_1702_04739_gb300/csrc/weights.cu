@@ -112,11 +112,16 @@ __device__ __forceinline__ void dw_exp_neg(float zh, float zl, const float2 *__r
     ol = __fmul_rn(pl, scale);
 }
 
-template <bool WITH_P>
+// SCREEN: before the double-word pass, each 64x64 tile pair is evaluated in
+// plain FP32; if no pair can have a term above e^-zskip of its row's
+// largest term (a rigorous lower bound on z from the FP32 error bound), the
+// tile pair is skipped.  Skipped terms total < n e^-zskip relative.
+template <bool WITH_P, bool SCREEN>
 __global__ void __launch_bounds__(TPB, 2)
 k_weights_dw(const float *__restrict__ X, int64_t n, int32_t d, const unsigned long long *__restrict__ nnbits,
              float is_h, float is_l, double inv_sigma, ExpTable tabv, double alpha, int include_self,
-             double *__restrict__ omega, double *__restrict__ pout) {
+             float zskip, float scr_shrink, double *__restrict__ omega, double *__restrict__ pout,
+             unsigned long long *__restrict__ tile_counts) {
     __shared__ __align__(16) float As[WDC][WPAD];
     __shared__ __align__(16) float Bs[WDC][WPAD];
     __shared__ float2 tab[64];
@@ -145,8 +150,58 @@ k_weights_dw(const float *__restrict__ X, int64_t n, int32_t d, const unsigned l
     for (int i = 0; i < 4; ++i) acc[i] = RowAcc{0.f, 0.f, 0.f, 0.f};
 
     const int64_t ntiles = ceil_div(n, WT);
+    unsigned long long dw_tiles = 0;
     for (int64_t ct = 0; ct < ntiles; ++ct) {
         const int64_t col0 = ct * WT;
+        if (SCREEN) {
+            float A32[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) A32[i][j] = 0.f;
+            for (int t0 = 0; t0 < d; t0 += WDC) {
+                __syncthreads();
+#pragma unroll
+                for (int q = 0; q < (WT * WDC) / TPB; ++q) {
+                    int idx = tid + q * TPB;
+                    int r = idx / WDC, t = idx % WDC;
+                    int64_t gr = row0 + r, gc = col0 + r;
+                    int gt = t0 + t;
+                    As[t][r] = (gr < n && gt < d) ? X[gr * d + gt] : 0.0f;
+                    Bs[t][r] = (gc < n && gt < d) ? X[gc * d + gt] : 0.0f;
+                }
+                __syncthreads();
+                const int tl = min(WDC, d - t0);
+                for (int t = 0; t < tl; ++t) {
+                    float4 a4 = *reinterpret_cast<const float4 *>(&As[t][ty * 4]);
+                    float4 b4 = *reinterpret_cast<const float4 *>(&Bs[t][tx * 4]);
+                    float a[4] = {a4.x, a4.y, a4.z, a4.w};
+                    float b[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            float df = __fsub_rn(a[i], b[j]);
+                            A32[i][j] = __fmaf_rn(df, df, A32[i][j]);
+                        }
+                }
+            }
+            int need = 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int64_t gr = row0 + ty * 4 + i;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int64_t gc = col0 + tx * 4 + j;
+                    if (gr >= n || gc >= n || gc == gr) continue;
+                    // d >= sqrt(d2_fp32 * (1 - e)): z >= d / sigma - y_nn
+                    float zlo = __fmul_rn(__fsqrt_rn(__fmul_rn(A32[i][j], scr_shrink)), is_h) - sh_h[i];
+                    if (!(zlo > zskip)) need = 1;
+                }
+            }
+            if (!__syncthreads_or(need)) continue;
+            ++dw_tiles;
+        }
         float S[4][4], E[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
@@ -211,12 +266,16 @@ k_weights_dw(const float *__restrict__ X, int64_t n, int32_t d, const unsigned l
                 two_sum(yh, -sh_h[i], zh, zl);
                 zl = __fadd_rn(zl, __fsub_rn(yl, sh_l[i]));
                 fast_two_sum(zh, zl, zh, zl);
-                if (zh > 87.0f) continue;      // < 2^-125 of the row's largest term
+                if (zh > zskip) continue;      // < e^-zskip of the row's largest term
                 float th, tl2;
                 dw_exp_neg(zh, zl, tab, th, tl2);
                 dw_add(acc[i].wh, acc[i].wl, th, tl2);
             }
         }
+    }
+    if (SCREEN && tid == 0) {
+        atomicAdd(tile_counts + 0, (unsigned long long)ntiles);
+        atomicAdd(tile_counts + 1, dw_tiles);
     }
     // merge the 16 column-threads of each row in fixed order
     __syncthreads();
@@ -279,7 +338,7 @@ __global__ void __launch_bounds__(TPB) k_weights_f64(const T *__restrict__ X, in
 
 cudaError_t weights_launch(const void *X, int64_t n, int32_t d, int dtype, bool fp64_path, double sigma,
                            double alpha, int include_self, const unsigned long long *nnbits, double *omega,
-                           double *p, cudaStream_t s) {
+                           double *p, unsigned long long *tile_counts, cudaStream_t s) {
     if (fp64_path || dtype == ISOCLUST_F64) {
         unsigned g = (unsigned)ceil_div(n, TPB);
         if (dtype == ISOCLUST_F64)
@@ -292,17 +351,28 @@ cudaError_t weights_launch(const void *X, int64_t n, int32_t d, int dtype, bool 
     const double is = 1.0 / sigma;
     const float is_h = (float)is;
     const float is_l = (float)(is - (double)is_h);
+    // Terms below e^-zskip of a row's largest term are dropped: their total
+    // is below n e^-zskip = e^-39 ~ 1.2e-17 of the row sum.
+    const float zskip = (float)(39.0 + log((double)n));
+    // FP32 d2 relative error <= (d+1)u (+ underflow): shrink by 1.1(d+3)u
+    // plus the rounding of the screen's own sqrt/multiply/subtract.
+    const double e = 1.1 * (double)(d + 3) * 5.9604644775390625e-08;
+    const float shrink = (float)((1.0 - e) * (1.0 - 1e-6));
     unsigned g = (unsigned)ceil_div(n, WT);
-    if (alpha != 0.0 && p)
-        k_weights_dw<true><<<g, TPB, 0, ISO_S(s)>>>((const float *)X, n, d, nnbits, is_h, is_l, is, tab, alpha, include_self,
-                                             omega, p);
-    else {
-        k_weights_dw<false><<<g, TPB, 0, ISO_S(s)>>>((const float *)X, n, d, nnbits, is_h, is_l, is, tab, alpha,
-                                              include_self, omega, p);
-        if (p) {
-            cudaError_t e = cudaMemsetAsync(p, 0, sizeof(double) * n, s);
-            if (e != cudaSuccess) return e;
-        }
+    const bool with_p = alpha != 0.0 && p;
+    const bool screen = !with_p && tile_counts != nullptr;
+    if (with_p)
+        k_weights_dw<true, false><<<g, TPB, 0, ISO_S(s)>>>((const float *)X, n, d, nnbits, is_h, is_l, is, tab, alpha,
+                                                          include_self, zskip, shrink, omega, p, tile_counts);
+    else if (screen)
+        k_weights_dw<false, true><<<g, TPB, 0, ISO_S(s)>>>((const float *)X, n, d, nnbits, is_h, is_l, is, tab, alpha,
+                                                          include_self, zskip, shrink, omega, p, tile_counts);
+    else
+        k_weights_dw<false, false><<<g, TPB, 0, ISO_S(s)>>>((const float *)X, n, d, nnbits, is_h, is_l, is, tab,
+                                                           alpha, include_self, zskip, shrink, omega, p, tile_counts);
+    if (!with_p && p) {
+        cudaError_t e2 = cudaMemsetAsync(p, 0, sizeof(double) * n, s);
+        if (e2 != cudaSuccess) return e2;
     }
     return cudaGetLastError();
 }

@@ -19,7 +19,7 @@ from . import build as _build
 
 F32, F64 = 0, 1
 OMEGA_FULL, OMEGA_TREE = 0, 1
-PREC_AUTO, PREC_FP64, PREC_FP32 = 0, 1, 2
+PREC_AUTO, PREC_FP64, PREC_FP32, PREC_BF16_TC = 0, 1, 2, 3
 
 STATUS = {
     0: "ISOCLUST_OK", 1: "ISOCLUST_ERR_INVALID_ARG", 2: "ISOCLUST_ERR_K_GT_N", 3: "ISOCLUST_ERR_NONFINITE",
@@ -82,6 +82,8 @@ def load(build_if_missing: bool = True):
                                                 _P, _P, _P, _P, _P, _P, _P, _P, _P]
         lib.isoclust_last_profile.restype = None
         lib.isoclust_last_profile.argtypes = [_P, _P]
+        lib.isoclust_last_omega_tiles.restype = None
+        lib.isoclust_last_omega_tiles.argtypes = [_P]
         _lib = lib
         return lib
 
@@ -223,7 +225,9 @@ def last_profile() -> dict:
     t = (ctypes.c_double * 6)()
     c = (ctypes.c_int64 * 4)()
     lib.isoclust_last_profile(t, c)
-    return dict(validate_ms=t[0], weights_ms=t[1], mst_ms=t[2], orient_ms=t[3], search_ms=t[4], labels_ms=t[5],
+    tl = (ctypes.c_int64 * 2)()
+    lib.isoclust_last_omega_tiles(tl)
+    return dict(omega_tiles=tl[0], omega_tiles_dw=tl[1],validate_ms=t[0], weights_ms=t[1], mst_ms=t[2], orient_ms=t[3], search_ms=t[4], labels_ms=t[5],
                 boruvka_rounds=c[0], rescanned_rows=c[1], alg1_passes=c[2], tree_depth=c[3])
 
 

@@ -142,7 +142,7 @@ def test_mst_bit_exact(iso, orc, name, X):
     assert (gd.cpu().numpy() == ed).all()
 
 
-@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("prec", [1, 2, 3])
 def test_mst_precision_paths_agree(iso, orc, prec):
     from paper_1702_04739_gb300 import workloads as W
     X = W.blobs_anisotropic(seed=9, n=2000, k=5, d=64)[0]
