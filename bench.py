@@ -168,6 +168,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mst-compare", action="store_true")
     ap.add_argument("--n", type=int, default=0,
                     help="points of the same generator (profiling of a smaller case); default: the full 100,000")
     args = ap.parse_args()
@@ -272,14 +273,41 @@ def main():
         e2e = {"value": world * n / (te / args.steps / 1000.0), "unit": UNIT,
                "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": int(n * 4 + n + 8)}
 
-    # roofline of the dominant kernel: the double-word omega sweep
+    # roofline of the dominant kernel: the screened double-word omega sweep
     peaks, src = _peaks()
     w_ms = statistics.mean(p["weights_ms"] for p in prof)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     alu_peak = sms * FP32_LANES_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12   # T instr/s
-    pairs = n * (n - 1) / 2.0
-    ops_per_pair = 21.0 * d + 75.0       # FP32-pipe instructions of one double-word pair (d2 + sqrt/exp/accumulate)
-    achieved = pairs * ops_per_pair / (w_ms / 1000.0) / 1e12
+    tiles, tiles_dw = prof[-1]["omega_tiles"], prof[-1]["omega_tiles_dw"]
+    sym = prof[-1]["omega_symmetric"]
+    screen_ops = 2.0 * d + (12.0 if sym else 8.0)            # FP32 screen of one pair (both directions if sym)
+    dw_ops = 21.0 * d + (140.0 if sym else 75.0)              # d2 (21/dim) + sqrt + exp/accumulate per direction
+    work = tiles * 4096.0 * screen_ops + tiles_dw * 4096.0 * dw_ops
+    achieved = work / (w_ms / 1000.0) / 1e12
+    # MST stage: tensor-core work and the BF16 + FP64-recheck path against the FP32 SIMT path
+    mst_ms = statistics.mean(p["mst_ms"] for p in prof)
+    rounds = prof[-1]["boruvka_rounds"]
+    n_pad = -(-n // 128) * 128
+    d_pad = -(-d // 64) * 64
+    alg_flop = rounds * 2.0 * n * n * d                  # one Gram term per round over all ordered pairs
+    exe_flop = rounds * 3 * 2.0 * n_pad * n_pad * d_pad  # hi.hi + hi.lo + lo.hi MMAs as issued
+    mst_cmp = None
+    if not args.no_mst_compare:
+        ref_edges = isoclust.cluster_mst(Xd, isoclust.opts(precision=isoclust.PREC_BF16_TC))
+        t_tc = isoclust.last_profile()["mst_ms"]
+        fp_edges = isoclust.cluster_mst(Xd, isoclust.opts(precision=isoclust.PREC_FP32))
+        t_fp = isoclust.last_profile()["mst_ms"]
+        same = all(torch.equal(a, b) for a, b in zip(ref_edges, fp_edges))
+        mst_cmp = {"bf16_tc_fp64_recheck_ms": t_tc, "fp32_simt_fp64_recheck_ms": t_fp,
+                   "speedup_vs_fp32": t_fp / t_tc if t_tc > 0 else None, "identical_edges": bool(same)}
+    mst = {"stage_ms": mst_ms, "rounds": rounds,
+           "algorithmic_tflops": alg_flop / (mst_ms / 1000.0) / 1e12,
+           "executed_tensor_tflops": exe_flop / (mst_ms / 1000.0) / 1e12,
+           "peak_bf16_tflops": peaks.get("bf16_tflops"), "peak_source": src,
+           "frac_executed_of_peak": exe_flop / (mst_ms / 1000.0) / 1e12 / peaks.get("bf16_tflops", 1900.0),
+           "note": "stage time includes the FP64 recheck and union-find; algorithmic = rounds x 2 n^2 d"}
+    if mst_cmp:
+        mst["compare"] = mst_cmp
     stages = {key: round(statistics.mean(p[key] for p in prof), 3)
               for key in ("validate_ms", "weights_ms", "mst_ms", "orient_ms", "search_ms", "labels_ms")}
     counts = {key: prof[-1][key] for key in ("boruvka_rounds", "rescanned_rows", "alg1_passes", "tree_depth")}
@@ -292,11 +320,14 @@ def main():
                    "l2": "flushed by a 256 MiB write before every step (inside the timed region)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                      "frac": achieved / alu_peak, "traffic": None,
-                     "kernel": "k_weights_dw (omega, double-word FP32)",
-                     "note": f"FP32-pipe instructions: n(n-1)/2 pairs x (21 d + 75) per pair over the omega stage's "
-                             f"event time; peak = {sms} SMs x {FP32_LANES_PER_SM} lanes x max SM clock "
-                             f"({src} sm_max_mhz)"},
-        "stages_ms": stages, "counts": counts,
+                     "kernel": "k_weights_sym (omega, double-word FP32)" if sym else "k_weights_dw (omega, double-word FP32)",
+                     "note": f"FP32-pipe instructions of the algorithm: every {'unordered' if sym else 'ordered'} "
+                             f"pair of the 64x64 tile grid screened in FP32 ({screen_ops:.0f} each, {tiles} tiles), "
+                             f"double-word evaluation ({dw_ops:.0f} per pair) of the {tiles_dw} tiles the screen "
+                             f"keeps; over the omega stage's event time; "
+                             f"peak = {sms} SMs x {FP32_LANES_PER_SM} lanes x max SM clock ({src} sm_max_mhz)"},
+        "stages_ms": stages, "counts": counts, "mst": mst,
+        "omega_tiles": {"screened": prof[-1]["omega_tiles"], "double_word": prof[-1]["omega_tiles_dw"]},
         "gpu_launches": int(launches),
         "clocks": clk,
     }

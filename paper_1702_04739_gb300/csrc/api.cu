@@ -15,6 +15,11 @@ namespace iso {
 cudaError_t weights_launch(const void *X, int64_t n, int32_t d, int dtype, bool fp64_path, double sigma,
                            double alpha, int include_self, const unsigned long long *nnbits, double *omega,
                            double *p, unsigned long long *tile_counts, cudaStream_t s);
+size_t weights_sym_bytes(int64_t n);
+cudaError_t weights_launch_sym(const float *X, int64_t n, int32_t d, double sigma, int include_self,
+                               const unsigned long long *nnbits, double *omega, void *part,
+                               unsigned long long *tile_counts, cudaStream_t s);
+constexpr size_t SYM_PART_LIMIT = size_t(16) << 30;   // symmetric sweep up to 16 GiB of partials
 
 static std::atomic<long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -24,6 +29,7 @@ static thread_local char g_err[512] = "";
 static thread_local double g_prof_ms[6] = {0, 0, 0, 0, 0, 0};
 static thread_local int64_t g_prof_cnt[4] = {0, 0, 0, 0};
 static thread_local unsigned long long g_prof_tiles[2] = {0, 0};
+static thread_local int g_prof_sym = 0;
 
 void set_error(const char *fmt, ...) {
     va_list ap;
@@ -140,13 +146,15 @@ __global__ void k_check_edges(const int32_t *counters, int64_t n, uint32_t *st) 
 __global__ void k_copy_beta(const SearchState *S, double *beta) { beta[0] = S->beta; }
 
 // Row order of the omega sweep: MST preorder (spatially coherent runs),
-// with rows whose nearest neighbour is far (y_nn > 16) moved to the end.
+// with rows whose nearest neighbour is far (y_nn > 16) moved to the front:
+// they need double-word work against most columns, so their CTAs start
+// first instead of forming the tail of the grid.
 __global__ void k_order_keys(const int32_t *__restrict__ pre, const unsigned long long *__restrict__ nnbits,
                              int64_t n, double inv_sigma, uint64_t *__restrict__ key, int32_t *__restrict__ val) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
     double y = sqrt(__longlong_as_double((long long)nnbits[v])) * inv_sigma;
-    uint64_t far = (y > 16.0) ? 1ull : 0ull;
+    uint64_t far = (y > 16.0) ? 0ull : 1ull;
     key[v] = (far << 32) | (uint64_t)(uint32_t)pre[v];
     val[v] = (int32_t)v;
 }
@@ -293,8 +301,11 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
         float *Xp = nullptr;
         unsigned long long *nnp = nullptr, *tiles = nullptr;
         double *omp = nullptr, *pp = nullptr;
+        void *sym = nullptr;
     } P;
     const bool permuted = need_labels && dtype == ISOCLUST_F32 && !fp64_sweep;
+    const bool symmetric = permuted && o.alpha == 0.0 && o.omega_mode == ISOCLUST_OMEGA_FULL &&
+                           weights_sym_bytes(n) <= SYM_PART_LIMIT;
     auto carve = [&](Arena &A, MstScratch &M, TreeScratch &TS, double **phi, double **om, double **pp, double **omtmp,
                      uint32_t **status) {
         *status = A.take<uint32_t>(4);
@@ -317,6 +328,7 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
             P.tiles = A.take<unsigned long long>(2);
             P.omp = A.take<double>(n);
             P.pp = A.take<double>(n);
+            if (symmetric) P.sym = (void *)A.take<unsigned char>(weights_sym_bytes(n));
         }
     };
     MstScratch M;
@@ -378,10 +390,16 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
                 k_gather_rows<<<(unsigned)ceil_div(n * (int64_t)d, TPB), TPB, 0, ISO_S(s)>>>(
                     (const float *)X, P.perm, M.nnbits, n, d, P.Xp, P.nnp);
                 ISO_CUDA(cudaMemsetAsync(P.tiles, 0, 2 * sizeof(unsigned long long), s));
-                ISO_CUDA(weights_launch(P.Xp, n, d, dtype, false, sigma, o.alpha, o.include_self, P.nnp, P.omp, P.pp,
-                                        P.tiles, s));
+                if (symmetric)
+                    ISO_CUDA(weights_launch_sym(P.Xp, n, d, sigma, o.include_self, P.nnp, P.omp, P.sym, P.tiles, s));
+                else
+                    ISO_CUDA(weights_launch(P.Xp, n, d, dtype, false, sigma, o.alpha, o.include_self, P.nnp, P.omp,
+                                            P.pp, P.tiles, s));
                 k_scatter_rows<<<gb, TPB, 0, ISO_S(s)>>>(P.omp, P.perm, n, om_out);
-                k_scatter_rows<<<gb, TPB, 0, ISO_S(s)>>>(P.pp, P.perm, n, pp);
+                if (symmetric)
+                    ISO_CUDA(cudaMemsetAsync(pp, 0, sizeof(double) * n, s));
+                else
+                    k_scatter_rows<<<gb, TPB, 0, ISO_S(s)>>>(P.pp, P.perm, n, pp);
             } else {
                 ISO_CUDA(weights_launch(X, n, d, dtype, false, sigma, o.alpha, o.include_self, M.nnbits, om_out, pp,
                                         nullptr, s));
@@ -428,6 +446,7 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
     g_prof_cnt[3] = ss.max_depth;
     g_prof_tiles[0] = g_prof_tiles[1] = 0;
     if (permuted) ISO_CUDA(cudaMemcpy(g_prof_tiles, P.tiles, sizeof(g_prof_tiles), cudaMemcpyDeviceToHost));
+    g_prof_sym = symmetric ? 1 : 0;
     return map_status(fin, false);
 }
 
@@ -474,8 +493,12 @@ void isoclust_last_profile(double *t_ms6, int64_t *counts4) {
     if (counts4) for (int i = 0; i < 4; ++i) counts4[i] = g_prof_cnt[i];
 }
 
-void isoclust_last_omega_tiles(int64_t *tiles2) {
-    if (tiles2) { tiles2[0] = (int64_t)g_prof_tiles[0]; tiles2[1] = (int64_t)g_prof_tiles[1]; }
+void isoclust_last_omega_tiles(int64_t *tiles3) {
+    if (tiles3) {
+        tiles3[0] = (int64_t)g_prof_tiles[0];
+        tiles3[1] = (int64_t)g_prof_tiles[1];
+        tiles3[2] = g_prof_sym;
+    }
 }
 
 isoclust_status isoclust_cluster_mst(const void *X, int64_t n, int32_t d, int32_t dtype, const isoclust_opts *opts,

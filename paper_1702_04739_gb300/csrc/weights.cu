@@ -312,6 +312,243 @@ k_weights_dw(const float *__restrict__ X, int64_t n, int32_t d, const unsigned l
     }
 }
 
+// exp(-(d / sigma - shift)) for a double-word distance (r, dl); false when
+// the term is below e^-zskip of the row's largest term (dropped).
+__device__ __forceinline__ bool dw_term(float r, float dl, float is_h, float is_l, float sh_h, float sh_l, float zskip,
+                                        const float2 *__restrict__ tab, float &th, float &tl) {
+    float yh, yl;
+    two_prod(r, is_h, yh, yl);
+    yl = __fmaf_rn(r, is_l, yl);
+    yl = __fmaf_rn(dl, is_h, yl);
+    fast_two_sum(yh, yl, yh, yl);
+    float zh, zl;
+    two_sum(yh, -sh_h, zh, zl);
+    zl = __fadd_rn(zl, __fsub_rn(yl, sh_l));
+    fast_two_sum(zh, zl, zh, zl);
+    if (zh > zskip) return false;
+    dw_exp_neg(zh, zl, tab, th, tl);
+    return true;
+}
+
+__device__ __forceinline__ void split_shift(const unsigned long long *nnbits, int64_t r, int64_t n, double inv_sigma,
+                                            float &h, float &l) {
+    double sh = 0.0;
+    if (r < n) {
+        const double nd2 = bitsd(nnbits[r]);
+        sh = isfinite(nd2) ? __dmul_rn(__dsqrt_rn(nd2), inv_sigma) : 0.0;
+    }
+    h = (float)sh;
+    l = (float)(sh - (double)h);
+}
+
+// Unordered 64x64 tile pair w = (I, J), I <= J, of the upper triangle in
+// row-major order.
+__device__ __forceinline__ void tri_item(int64_t w, int64_t T, int64_t &I, int64_t &J) {
+    const double b = 2.0 * (double)T + 1.0;
+    int64_t i = (int64_t)floor((b - sqrt(b * b - 8.0 * (double)w)) * 0.5);
+    if (i < 0) i = 0;
+    while (i > 0 && i * T - i * (i - 1) / 2 > w) --i;
+    while ((i + 1) * T - (i + 1) * i / 2 <= w) ++i;
+    I = i;
+    J = i + (w - (i * T - i * (i - 1) / 2));
+}
+
+// Symmetric omega sweep: each unordered tile pair is screened in FP32 and,
+// if any of its terms can matter in either direction, evaluated once in
+// double-word arithmetic; the pair's d2 serves both omega_i and omega_j.
+// Row partials (rows of I) and column partials (rows of J) go to fixed slots
+// of item w, so the final sums do not depend on scheduling.
+__global__ void __launch_bounds__(TPB, 2)
+k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const unsigned long long *__restrict__ nnbits,
+              float is_h, float is_l, double inv_sigma, ExpTable tabv, float zskip, float scr_shrink, int64_t T,
+              int64_t nitems, uint8_t *__restrict__ flags, float2 *__restrict__ rpart, float2 *__restrict__ cpart,
+              unsigned long long *__restrict__ tile_counts) {
+    __shared__ __align__(16) float As[WDC][WPAD];
+    __shared__ __align__(16) float Bs[WDC][WPAD];
+    __shared__ float2 tab[64];
+    __shared__ float2 mr[WT][17];
+    __shared__ float2 mc[WT][17];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    if (tid < 64) tab[tid] = tabv.t[tid];
+    unsigned long long dw_items = 0, screened = 0;
+    for (int64_t w = blockIdx.x; w < nitems; w += gridDim.x) {
+        ++screened;
+        int64_t I, J;
+        tri_item(w, T, I, J);
+        const int64_t row0 = I * WT, col0 = J * WT;
+        const bool diag = I == J;
+        float rs_h[4], rs_l[4], cs_h[4], cs_l[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            split_shift(nnbits, row0 + ty * 4 + q, n, inv_sigma, rs_h[q], rs_l[q]);
+            split_shift(nnbits, col0 + tx * 4 + q, n, inv_sigma, cs_h[q], cs_l[q]);
+        }
+        // ---- FP32 screen, both directions
+        float A32[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) A32[i][j] = 0.f;
+        for (int t0 = 0; t0 < d; t0 += WDC) {
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < (WT * WDC) / TPB; ++q) {
+                int idx = tid + q * TPB;
+                int r = idx / WDC, t = idx % WDC;
+                int64_t gr = row0 + r, gc = col0 + r;
+                int gt = t0 + t;
+                As[t][r] = (gr < n && gt < d) ? X[gr * d + gt] : 0.0f;
+                Bs[t][r] = (gc < n && gt < d) ? X[gc * d + gt] : 0.0f;
+            }
+            __syncthreads();
+            const int tl = min(WDC, d - t0);
+            for (int t = 0; t < tl; ++t) {
+                float4 a4 = *reinterpret_cast<const float4 *>(&As[t][ty * 4]);
+                float4 b4 = *reinterpret_cast<const float4 *>(&Bs[t][tx * 4]);
+                float a[4] = {a4.x, a4.y, a4.z, a4.w};
+                float b[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        float df = __fsub_rn(a[i], b[j]);
+                        A32[i][j] = __fmaf_rn(df, df, A32[i][j]);
+                    }
+            }
+        }
+        int need = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int64_t gr = row0 + ty * 4 + i;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int64_t gc = col0 + tx * 4 + j;
+                if (gr >= n || gc >= n || gc == gr) continue;
+                const float y = __fmul_rn(__fsqrt_rn(__fmul_rn(A32[i][j], scr_shrink)), is_h);
+                if (!(y - rs_h[i] > zskip) || !(y - cs_h[j] > zskip)) need = 1;
+            }
+        }
+        if (!__syncthreads_or(need)) {
+            if (tid == 0) flags[w] = 0;
+            continue;
+        }
+        ++dw_items;
+        // ---- double-word pass
+        float S[4][4], E[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) { S[i][j] = 0.f; E[i][j] = 0.f; }
+        for (int t0 = 0; t0 < d; t0 += WDC) {
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < (WT * WDC) / TPB; ++q) {
+                int idx = tid + q * TPB;
+                int r = idx / WDC, t = idx % WDC;
+                int64_t gr = row0 + r, gc = col0 + r;
+                int gt = t0 + t;
+                As[t][r] = (gr < n && gt < d) ? X[gr * d + gt] : 0.0f;
+                Bs[t][r] = (gc < n && gt < d) ? X[gc * d + gt] : 0.0f;
+            }
+            __syncthreads();
+            const int tl = min(WDC, d - t0);
+            for (int t = 0; t < tl; ++t) {
+                float4 a4 = *reinterpret_cast<const float4 *>(&As[t][ty * 4]);
+                float4 b4 = *reinterpret_cast<const float4 *>(&Bs[t][tx * 4]);
+                float a[4] = {a4.x, a4.y, a4.z, a4.w};
+                float b[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        float s1, e1;
+                        two_sum(a[i], -b[j], s1, e1);
+                        float p = __fmul_rn(s1, s1);
+                        float q2 = __fmaf_rn(s1, s1, -p);
+                        q2 = __fmaf_rn(__fadd_rn(s1, s1), e1, q2);
+                        float hs, he;
+                        two_sum(S[i][j], p, hs, he);
+                        he = __fadd_rn(he, __fadd_rn(E[i][j], q2));
+                        fast_two_sum(hs, he, S[i][j], E[i][j]);
+                    }
+            }
+        }
+        float rh[4] = {0.f, 0.f, 0.f, 0.f}, rl[4] = {0.f, 0.f, 0.f, 0.f};
+        float ch[4] = {0.f, 0.f, 0.f, 0.f}, cl[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int64_t gr = row0 + ty * 4 + i;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int64_t gc = col0 + tx * 4 + j;
+                if (gr >= n || gc >= n || gc == gr) continue;
+                const float Sh = S[i][j], El = E[i][j];
+                const float r = __fsqrt_rn(Sh);
+                float dl = 0.0f;
+                if (r > 0.0f) {
+                    const float res = __fadd_rn(__fmaf_rn(-r, r, Sh), El);
+                    dl = __fmul_rn(res, __frcp_rn(__fadd_rn(r, r)));
+                }
+                float th, tl2;
+                if (dw_term(r, dl, is_h, is_l, rs_h[i], rs_l[i], zskip, tab, th, tl2)) dw_add(rh[i], rl[i], th, tl2);
+                if (!diag && dw_term(r, dl, is_h, is_l, cs_h[j], cs_l[j], zskip, tab, th, tl2))
+                    dw_add(ch[j], cl[j], th, tl2);
+            }
+        }
+        // rows of I: merge the 16 column-threads; columns of J: merge the 16 row-threads
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            mr[ty * 4 + q][tx] = make_float2(rh[q], rl[q]);
+            mc[tx * 4 + q][ty] = make_float2(ch[q], cl[q]);
+        }
+        __syncthreads();
+        if (tid < WT) {
+            float h = 0.f, l = 0.f;
+            for (int k = 0; k < 16; ++k) dw_add(h, l, mr[tid][k].x, mr[tid][k].y);
+            rpart[w * WT + tid] = make_float2(h, l);
+        } else if (tid < 2 * WT) {
+            const int c = tid - WT;
+            float h = 0.f, l = 0.f;
+            if (!diag)
+                for (int k = 0; k < 16; ++k) dw_add(h, l, mc[c][k].x, mc[c][k].y);
+            cpart[w * WT + c] = make_float2(h, l);
+        }
+        if (tid == 0) flags[w] = 1;
+    }
+    if (tid == 0) {
+        atomicAdd(tile_counts + 0, screened);
+        atomicAdd(tile_counts + 1, dw_items);
+    }
+}
+
+// omega_r = exp(-y_nn,r) * (sum over the items of row r's tile, in item
+// order, of the row or column partial), formed in FP64.
+__global__ void k_weights_reduce(const unsigned long long *__restrict__ nnbits, int64_t n, int64_t T,
+                                 double inv_sigma, int include_self, const uint8_t *__restrict__ flags,
+                                 const float2 *__restrict__ rpart, const float2 *__restrict__ cpart,
+                                 double *__restrict__ omega) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int64_t I = r / WT, c = r - I * WT;
+    float h = 0.f, l = 0.f;
+    for (int64_t J = 0; J < T; ++J) {
+        if (J < I) {
+            const int64_t w = J * T - J * (J - 1) / 2 + (I - J);      // item (J, I): r is a column
+            if (flags[w]) dw_add(h, l, cpart[w * WT + c].x, cpart[w * WT + c].y);
+        } else {
+            const int64_t w = I * T - I * (I - 1) / 2 + (J - I);      // item (I, J): r is a row
+            if (flags[w]) dw_add(h, l, rpart[w * WT + c].x, rpart[w * WT + c].y);
+        }
+    }
+    float fh, fl;
+    split_shift(nnbits, r, n, inv_sigma, fh, fl);
+    double w2 = __dmul_rn(exp(-__dadd_rn((double)fh, (double)fl)), __dadd_rn((double)h, (double)l));
+    if (include_self) w2 = __dadd_rn(w2, 1.0);
+    omega[r] = w2;
+}
+
 // FP64 input: canonical FP64 terms, j ascending (the oracle's order).
 template <class T>
 __global__ void __launch_bounds__(TPB) k_weights_f64(const T *__restrict__ X, int64_t n, int32_t d, double sigma,
@@ -335,6 +572,37 @@ __global__ void __launch_bounds__(TPB) k_weights_f64(const T *__restrict__ X, in
     if (pout) pout[i] = alpha != 0.0 ? __dmul_rn(alpha, sd) : 0.0;
 }
 }  // namespace
+
+size_t weights_sym_bytes(int64_t n) {
+    const int64_t T = ceil_div(n, WT);
+    const int64_t items = T * (T + 1) / 2;
+    return (size_t)items * (1 + 2 * WT * sizeof(float2)) + 4096;
+}
+
+// Symmetric screened omega (F32 input, p not needed).  part must hold
+// weights_sym_bytes(n) bytes.
+cudaError_t weights_launch_sym(const float *X, int64_t n, int32_t d, double sigma, int include_self,
+                               const unsigned long long *nnbits, double *omega, void *part,
+                               unsigned long long *tile_counts, cudaStream_t s) {
+    static const ExpTable tab = make_exp_table();
+    const double is = 1.0 / sigma;
+    const float is_h = (float)is;
+    const float is_l = (float)(is - (double)is_h);
+    const float zskip = (float)(39.0 + log((double)n));
+    const double e = 1.1 * (double)(d + 3) * 5.9604644775390625e-08;
+    const float shrink = (float)((1.0 - e) * (1.0 - 1e-6));
+    const int64_t T = ceil_div(n, WT);
+    const int64_t items = T * (T + 1) / 2;
+    float2 *rpart = (float2 *)part;
+    float2 *cpart = rpart + items * WT;
+    uint8_t *flags = (uint8_t *)(cpart + items * WT);
+    const unsigned grid = (unsigned)(num_sms() * 2);
+    k_weights_sym<<<grid, TPB, 0, ISO_S(s)>>>(X, n, d, nnbits, is_h, is_l, is, tab, zskip, shrink, T, items, flags,
+                                              rpart, cpart, tile_counts);
+    k_weights_reduce<<<(unsigned)ceil_div(n, 256), 256, 0, ISO_S(s)>>>(nnbits, n, T, is, include_self, flags, rpart,
+                                                                      cpart, omega);
+    return cudaGetLastError();
+}
 
 cudaError_t weights_launch(const void *X, int64_t n, int32_t d, int dtype, bool fp64_path, double sigma,
                            double alpha, int include_self, const unsigned long long *nnbits, double *omega,

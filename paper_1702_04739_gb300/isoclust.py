@@ -225,9 +225,9 @@ def last_profile() -> dict:
     t = (ctypes.c_double * 6)()
     c = (ctypes.c_int64 * 4)()
     lib.isoclust_last_profile(t, c)
-    tl = (ctypes.c_int64 * 2)()
+    tl = (ctypes.c_int64 * 3)()
     lib.isoclust_last_omega_tiles(tl)
-    return dict(omega_tiles=tl[0], omega_tiles_dw=tl[1],validate_ms=t[0], weights_ms=t[1], mst_ms=t[2], orient_ms=t[3], search_ms=t[4], labels_ms=t[5],
+    return dict(omega_tiles=tl[0], omega_tiles_dw=tl[1], omega_symmetric=tl[2],validate_ms=t[0], weights_ms=t[1], mst_ms=t[2], orient_ms=t[3], search_ms=t[4], labels_ms=t[5],
                 boruvka_rounds=c[0], rescanned_rows=c[1], alg1_passes=c[2], tree_depth=c[3])
 
 
