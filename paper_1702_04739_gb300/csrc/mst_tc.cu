@@ -323,13 +323,17 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
             int64_t pcol = (int64_t)c0 * TC_BN + et;
             float pn = pcol < n ? rnorm[pcol] : INFINITY;
             int32_t pc = pcol < n ? comp[pcol] : -2;
+            float ptsq = __ldg(tsq + c0), ptmax = __ldg(tmax + c0);
             for (int ct = c0; ct < c1; ++ct) {
                 sh->cnorm[acc][et] = pn;
                 sh->ccomp[acc][et] = pc;
+                const float ctsq = ptsq, ctmax = ptmax;
                 if (ct + 1 < c1) {
                     pcol = (int64_t)(ct + 1) * TC_BN + et;
                     pn = pcol < n ? rnorm[pcol] : INFINITY;
                     pc = pcol < n ? comp[pcol] : -2;
+                    ptsq = __ldg(tsq + ct + 1);
+                    ptmax = __ldg(tmax + ct + 1);
                 }
                 asm volatile("bar.sync 1, 128;" ::: "memory");
                 if (ok) ok = mbar_wait(&sh->acc_full[acc], acc_phase, err);
@@ -361,7 +365,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
                 if (++acc == 2) { acc = 0; acc_phase ^= 1u; }
                 // rigorous bounds of the tile's smallest d2 of the represented points:
                 // accumulation + dropped lo.lo (A s_i s_j) and FP32 norm/epilogue rounding
-                const float dlt = acoef * srow * __ldg(tsq + ct) + bcoef * (nrow + __ldg(tmax + ct));
+                const float dlt = acoef * srow * ctsq + bcoef * (nrow + ctmax);
                 const float lb = m - dlt;
                 ubest = fminf(ubest, m + dlt);
                 if (lb < bv[TC_TOPK - 1]) top_insert(bv, bj, lb, ct);   // once per tile

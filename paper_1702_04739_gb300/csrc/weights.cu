@@ -359,8 +359,8 @@ __device__ __forceinline__ void tri_item(int64_t w, int64_t T, int64_t &I, int64
 // Row partials (rows of I) and column partials (rows of J) go to fixed slots
 // of item w, so the final sums do not depend on scheduling.
 __global__ void __launch_bounds__(TPB, 2)
-k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const unsigned long long *__restrict__ nnbits,
-              float is_h, float is_l, double inv_sigma, ExpTable tabv, float zskip, float scr_shrink, int64_t T,
+k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *__restrict__ shdw,
+              float is_h, float is_l, ExpTable tabv, float zskip, float scr_shrink, int64_t T,
               int64_t nitems, uint8_t *__restrict__ flags, float2 *__restrict__ rpart, float2 *__restrict__ cpart,
               unsigned long long *__restrict__ tile_counts) {
     __shared__ __align__(16) float As[WDC][WPAD];
@@ -368,21 +368,27 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const unsigned 
     __shared__ float2 tab[64];
     __shared__ float2 mr[WT][17];
     __shared__ float2 mc[WT][17];
+    __shared__ int64_t sIJ[2];
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     if (tid < 64) tab[tid] = tabv.t[tid];
     unsigned long long dw_items = 0, screened = 0;
     for (int64_t w = blockIdx.x; w < nitems; w += gridDim.x) {
         ++screened;
-        int64_t I, J;
-        tri_item(w, T, I, J);
+        __syncthreads();                       // previous item's readers of sIJ are done
+        if (tid == 0) tri_item(w, T, sIJ[0], sIJ[1]);
+        __syncthreads();
+        const int64_t I = sIJ[0], J = sIJ[1];
         const int64_t row0 = I * WT, col0 = J * WT;
         const bool diag = I == J;
         float rs_h[4], rs_l[4], cs_h[4], cs_l[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            split_shift(nnbits, row0 + ty * 4 + q, n, inv_sigma, rs_h[q], rs_l[q]);
-            split_shift(nnbits, col0 + tx * 4 + q, n, inv_sigma, cs_h[q], cs_l[q]);
+            const int64_t rr = row0 + ty * 4 + q, cc = col0 + tx * 4 + q;
+            const float2 a = rr < n ? shdw[rr] : make_float2(0.f, 0.f);
+            const float2 b = cc < n ? shdw[cc] : make_float2(0.f, 0.f);
+            rs_h[q] = a.x; rs_l[q] = a.y;
+            cs_h[q] = b.x; cs_l[q] = b.y;
         }
         // ---- FP32 screen, both directions
         float A32[4][4];
@@ -523,6 +529,16 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const unsigned 
     }
 }
 
+// Per row: the shift y_nn = |x - x_nn| / sigma as a double-word (once per call).
+__global__ void k_shift_dw(const unsigned long long *__restrict__ nnbits, int64_t n, double inv_sigma,
+                           float2 *__restrict__ shdw) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    float h, l;
+    split_shift(nnbits, r, n, inv_sigma, h, l);
+    shdw[r] = make_float2(h, l);
+}
+
 // omega_r = exp(-y_nn,r) * (sum over the items of row r's tile, in item
 // order, of the row or column partial), formed in FP64.
 __global__ void k_weights_reduce(const unsigned long long *__restrict__ nnbits, int64_t n, int64_t T,
@@ -576,7 +592,7 @@ __global__ void __launch_bounds__(TPB) k_weights_f64(const T *__restrict__ X, in
 size_t weights_sym_bytes(int64_t n) {
     const int64_t T = ceil_div(n, WT);
     const int64_t items = T * (T + 1) / 2;
-    return (size_t)items * (1 + 2 * WT * sizeof(float2)) + 4096;
+    return (size_t)items * (1 + 2 * WT * sizeof(float2)) + (size_t)n * sizeof(float2) + 4096;
 }
 
 // Symmetric screened omega (F32 input, p not needed).  part must hold
@@ -595,10 +611,12 @@ cudaError_t weights_launch_sym(const float *X, int64_t n, int32_t d, double sigm
     const int64_t items = T * (T + 1) / 2;
     float2 *rpart = (float2 *)part;
     float2 *cpart = rpart + items * WT;
-    uint8_t *flags = (uint8_t *)(cpart + items * WT);
+    float2 *shdw = cpart + items * WT;
+    uint8_t *flags = (uint8_t *)(shdw + n);
     const unsigned grid = (unsigned)(num_sms() * 2);
-    k_weights_sym<<<grid, TPB, 0, ISO_S(s)>>>(X, n, d, nnbits, is_h, is_l, is, tab, zskip, shrink, T, items, flags,
-                                              rpart, cpart, tile_counts);
+    k_shift_dw<<<(unsigned)ceil_div(n, 256), 256, 0, ISO_S(s)>>>(nnbits, n, is, shdw);
+    k_weights_sym<<<grid, TPB, 0, ISO_S(s)>>>(X, n, d, shdw, is_h, is_l, tab, zskip, shrink, T, items, flags, rpart,
+                                              cpart, tile_counts);
     k_weights_reduce<<<(unsigned)ceil_div(n, 256), 256, 0, ISO_S(s)>>>(nnbits, n, T, is, include_self, flags, rpart,
                                                                       cpart, omega);
     return cudaGetLastError();

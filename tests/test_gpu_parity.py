@@ -3,8 +3,8 @@
 Bars (fixed here, derived in the design notes):
   * MST edge set and d2: bit-exact (integer/index work + canonical FP64 key).
   * tree stage fed identical inputs: labels, residual and i_k bit-exact.
-  * omega: per-row relative error <= omega_tol(y_i) = 2^-45 * (y_i + 4), with
-    y_i = ||x_i - x_nn(i)|| / sigma.  Each term is evaluated in double-word
+  * omega: per-row relative error <= omega_tol(y_i) = 2^-45 max(1, sqrt(d/64))
+    (y_i + 4), with y_i = ||x_i - x_nn(i)|| / sigma.  Each term is evaluated in double-word
     FP32: d2 carries ~2^-46 relative error, so the term's exponent
     y = d / sigma carries ~2^-47 * y absolute error, and so does the term's
     relative value; the bound keeps a factor ~4 of headroom over that.
@@ -22,10 +22,11 @@ IK_RTOL = 1e-12
 
 
 def omega_tol(orc, X, sigma):
-    """Per-row bound on the double-word omega error (see module docstring)."""
+    """Per-row bound on the double-word omega error (see module docstring);
+    the d2 sum's error grows like sqrt(d), so the d = 64 constant scales."""
     nn, nd2 = orc.nn_rows(X, np.arange(X.shape[0]))
     y = np.sqrt(nd2) / sigma
-    return 2.0 ** -45 * (y + 4.0)
+    return 2.0 ** -45 * max(1.0, math.sqrt(X.shape[1] / 64.0)) * (y + 4.0)
 
 
 @pytest.fixture(scope="module")
