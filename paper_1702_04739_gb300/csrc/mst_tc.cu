@@ -482,6 +482,15 @@ __global__ void k_tc_gather_comp(const int32_t *__restrict__ comp, const int32_t
 // tiles' columns are filtered with FP32 direct differences and the
 // survivors keyed in FP64.  If the 8th kept tile still qualifies, the row is
 // queued for a rescan.
+__device__ __forceinline__ float approx_d2_f32(const float *__restrict__ a, const float *__restrict__ b, int d) {
+    float acc = 0.0f;
+    for (int t = 0; t < d; ++t) {
+        const float df = __fsub_rn(a[t], b[t]);
+        acc = __fmaf_rn(df, df, acc);
+    }
+    return acc;
+}
+
 __global__ void __launch_bounds__(256) k_recheck_tc(const float *__restrict__ X, int64_t n, int32_t d, int splits,
                                                     const float *__restrict__ tv, const int32_t *__restrict__ tj,
                                                     const float *__restrict__ tu, const float *__restrict__ rsq,
@@ -494,29 +503,63 @@ __global__ void __launch_bounds__(256) k_recheck_tc(const float *__restrict__ X,
     const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (r >= n) return;
     const int64_t i = perm[r];
+    // ---- merge: each lane holds up to 4 of the splits x 8 entries; the best 8
+    //      are selected by 8 rounds of a warp arg-min
+    const int ne = splits * TC_TOPK;
+    float ev[4];
+    int32_t ej[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int e = lane + 32 * q;
+        if (e < ne) {
+            const int sidx = e / TC_TOPK, k = e - sidx * TC_TOPK;
+            const size_t o = ((size_t)sidx * n + r) * TC_TOPK + k;
+            ev[q] = tv[o];
+            ej[q] = tj[o];
+        } else {
+            ev[q] = INFINITY;
+            ej[q] = -1;
+        }
+    }
+    float U = lane < splits ? tu[(size_t)lane * n + r] : INFINITY;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) U = fminf(U, __shfl_xor_sync(0xffffffffu, U, o));
     float bv[TC_TOPK];
     int32_t bj[TC_TOPK];
 #pragma unroll
-    for (int q = 0; q < TC_TOPK; ++q) { bv[q] = INFINITY; bj[q] = -1; }
-    float U = INFINITY;
-    for (int s = 0; s < splits; ++s) {
-        const size_t o = ((size_t)s * n + r) * TC_TOPK;
-        U = fminf(U, tu[(size_t)s * n + r]);
-        for (int q = 0; q < TC_TOPK; ++q) {
-            const float v = tv[o + q];
-            if (!(v < bv[TC_TOPK - 1])) break;          // lists are sorted
-            top_insert(bv, bj, v, tj[o + q]);
+    for (int k = 0; k < TC_TOPK; ++k) {
+        float mv = ev[0];
+        int ms = 0;
+#pragma unroll
+        for (int q = 1; q < 4; ++q)
+            if (ev[q] < mv) { mv = ev[q]; ms = q; }
+        float wv = mv;
+        int wl = lane;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, wv, o);
+            const int ol = __shfl_xor_sync(0xffffffffu, wl, o);
+            if (ov < wv || (ov == wv && ol < wl)) { wv = ov; wl = ol; }
         }
+        int32_t wj = -1;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) wj = (ms == q) ? ej[q] : wj;
+        wj = __shfl_sync(0xffffffffu, wj, wl);
+        if (lane == wl) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (ms == q) ev[q] = INFINITY;
+        }
+        bv[k] = wv;
+        bj[k] = (wv < INFINITY) ? wj : -1;
     }
     if (bj[0] < 0 || !(U < INFINITY)) {
         if (lane == 0) rowj[i] = -1;
         return;
     }
-    // representation error: |d2(x) - d2(x~)| <= 2 e d (|y_i| + |y_j|) + e^2 (|y_i| + |y_j|)^2
+    // representation error: distances move by at most w = eps (|y_i| + |y_max|)
     const double si = (double)rsq[r], smax = sqrt((double)__uint_as_float(*nmax_bits));
     const double Ud = (double)U;
-    // distances move by at most w = eps (|y_i| + |y_max|) between the exact
-    // and the represented points
     const double w = eps_rep * (si + smax);
     const double su = sqrt(fmax(Ud, 0.0));
     const double hi_true = (su + w) * (su + w) * (1.0 + 1e-12);     // exact nearest foreign d2 <= this
@@ -530,27 +573,51 @@ __global__ void __launch_bounds__(256) k_recheck_tc(const float *__restrict__ X,
         }
         return;
     }
-    const double cut32 = hi_true * (1.0 + e32) + 1e-300;
+    const float cut32 = (float)(hi_true * (1.0 + e32) * (1.0 + 1e-6));
     const int32_t ci = comp[i];
     const float *xi = X + i * d;
     double best = INFINITY;
     int32_t bestj = -1;
-    for (int q = 0; q < TC_TOPK; ++q) {
-        if (bj[q] < 0 || (double)bv[q] > tile_cut) break;
-        for (int c = lane; c < TC_BN; c += 32) {
-            const int64_t jp = (int64_t)bj[q] * TC_BN + c;
-            if (jp >= n) continue;
-            const int64_t j = perm[jp];
-            if (comp[j] == ci) continue;
-            const float *xj = X + j * d;
-            float acc = 0.0f;
-            for (int t = 0; t < d; ++t) {
-                const float df = __fsub_rn(xi[t], xj[t]);
-                acc = __fmaf_rn(df, df, acc);
+    const bool vec = (d & 3) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+    for (int k = 0; k < TC_TOPK; ++k) {
+        if (bj[k] < 0 || (double)bv[k] > tile_cut) break;
+        // four columns per lane, four independent FMA chains
+        int64_t jj[4];
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        bool live[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t jp = (int64_t)bj[k] * TC_BN + lane + 32 * u;
+            jj[u] = jp < n ? (int64_t)perm[jp] : -1;
+            live[u] = jj[u] >= 0 && comp[jj[u]] != ci;
+        }
+        if (vec) {
+            const float4 *xi4 = reinterpret_cast<const float4 *>(xi);
+            for (int t = 0; t < d / 4; ++t) {
+                const float4 a = xi4[t];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (!live[u]) continue;
+                    const float4 b = reinterpret_cast<const float4 *>(X + jj[u] * d)[t];
+                    float df = __fsub_rn(a.x, b.x); acc[u] = __fmaf_rn(df, df, acc[u]);
+                    df = __fsub_rn(a.y, b.y); acc[u] = __fmaf_rn(df, df, acc[u]);
+                    df = __fsub_rn(a.z, b.z); acc[u] = __fmaf_rn(df, df, acc[u]);
+                    df = __fsub_rn(a.w, b.w); acc[u] = __fmaf_rn(df, df, acc[u]);
+                }
             }
-            if ((double)acc <= cut32) {
-                const double e = exact_d2(xi, xj, d);
-                if (bestj < 0 || key_less(e, (int32_t)i, (int32_t)j, best, (int32_t)i, bestj)) { best = e; bestj = (int32_t)j; }
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (live[u]) acc[u] = approx_d2_f32(xi, X + jj[u] * d, d);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (live[u] && acc[u] <= cut32) {
+                const double e = exact_d2(xi, X + jj[u] * d, d);
+                if (bestj < 0 || key_less(e, (int32_t)i, (int32_t)jj[u], best, (int32_t)i, bestj)) {
+                    best = e;
+                    bestj = (int32_t)jj[u];
+                }
             }
         }
     }
