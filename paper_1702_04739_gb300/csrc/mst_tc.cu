@@ -11,9 +11,10 @@
 //   warp 0      TMA producer: 128x64 BF16 tiles (128-byte swizzle) of the
 //               row block and the column block into a 3-stage ring,
 //   warp 1      allocates TMEM and issues the MMAs (one elected lane),
-//   warps 2..5  epilogue: tcgen05.ld of the FP32 accumulator (one row per
-//               thread), d2 = n_i + n_j - 2g, same-component mask, and a
-//               running best-8 per row in registers.
+//   warps 2..9  epilogue: tcgen05.ld of the FP32 accumulator (warp w reads
+//               TMEM lane quadrant w mod 4 and one 64-column half of the
+//               tile, one row per thread), d2 = n_i + n_j - 2g, same-component
+//               mask, and a running best-8 of half-tiles per row.
 // Two TMEM accumulators (2 x 128 columns) let the MMA of the next column
 // tile overlap the epilogue of the current one.  Every mbarrier wait is
 // bounded; on timeout the kernel raises an error flag and stops.
@@ -33,8 +34,10 @@ constexpr int TC_STAGES_B = 4;                            // ring depth, A resid
 constexpr int TC_AREG_BYTES = 4 * 128 * 64 * 2;           // A hi + lo, up to 2 K chunks (d_pad <= 128)
 constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 2;         // 16 KB
 constexpr int TC_STAGE_BYTES = 4 * TC_TILE_BYTES;        // A hi, A lo, B hi, B lo
-constexpr int TC_THREADS = 192;
-constexpr int TC_TOPK = 8;                                // best column tiles kept per row
+constexpr int TC_EPI_WARPS = 8;                           // two per TMEM lane quadrant
+constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;
+constexpr int TC_TOPK = 8;                                // best half-tiles kept per (list, row)
+constexpr int TC_CW = TC_BN / 2;                          // columns per candidate (half-tile)
 constexpr long long TC_WAIT_CYCLES = 4000000000LL;
 
 // Column metadata first: the epilogue reads it with 16-byte vector loads.
@@ -145,8 +148,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void top_insert(float (&v)[TC_TOPK], int32_t (&j)[TC_TOPK], float x, int32_t c) {
     v[TC_TOPK - 1] = x;
@@ -192,7 +195,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&sh->acc_full[a], 1);
-            mbar_init(&sh->acc_empty[a], 4);
+            mbar_init(&sh->acc_empty[a], TC_EPI_WARPS);
         }
         mbar_init(&sh->a_full, 1);
         mbar_init(&sh->a_empty, 1);
@@ -301,10 +304,12 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
             }
         }
     } else {
-        // ------------------------------------------------ epilogue (warps 2..5)
-        const int et = threadIdx.x - 64;               // 0..127
+        // ------------------------------------------------ epilogue (warps 2..9)
+        const int et = threadIdx.x - 64;               // 0..255
+        const int h = et >> 7;                         // column half of the tile
         const int quad = warp & 3;                     // TMEM lane quadrant of this warp
         const int trow = quad * 32 + lane;             // row within the tile = TMEM lane
+        const int cm = et & (TC_BN - 1);               // column whose metadata this thread stages
         uint32_t acc = 0, acc_phase = 0;
         bool ok = true;
         for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
@@ -319,43 +324,61 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
             int32_t bj[TC_TOPK];
 #pragma unroll
             for (int q = 0; q < TC_TOPK; ++q) { bv[q] = INFINITY; bj[q] = -1; }
-            // column metadata, prefetched one tile ahead
-            int64_t pcol = (int64_t)c0 * TC_BN + et;
-            float pn = pcol < n ? rnorm[pcol] : INFINITY;
-            int32_t pc = pcol < n ? comp[pcol] : -2;
+            // column metadata, prefetched one tile ahead by the first half's threads
+            int64_t pcol = (int64_t)c0 * TC_BN + cm;
+            float pn = INFINITY;
+            int32_t pc = -2;
+            if (h == 0 && pcol < n) { pn = rnorm[pcol]; pc = comp[pcol]; }
             float ptsq = __ldg(tsq + c0), ptmax = __ldg(tmax + c0);
             for (int ct = c0; ct < c1; ++ct) {
-                sh->cnorm[acc][et] = pn;
-                sh->ccomp[acc][et] = pc;
+                if (h == 0) {
+                    sh->cnorm[acc][cm] = pn;
+                    sh->ccomp[acc][cm] = pc;
+                }
                 const float ctsq = ptsq, ctmax = ptmax;
                 if (ct + 1 < c1) {
-                    pcol = (int64_t)(ct + 1) * TC_BN + et;
-                    pn = pcol < n ? rnorm[pcol] : INFINITY;
-                    pc = pcol < n ? comp[pcol] : -2;
+                    pcol = (int64_t)(ct + 1) * TC_BN + cm;
+                    if (h == 0) {
+                        pn = pcol < n ? rnorm[pcol] : INFINITY;
+                        pc = pcol < n ? comp[pcol] : -2;
+                    }
                     ptsq = __ldg(tsq + ct + 1);
                     ptmax = __ldg(tmax + ct + 1);
                 }
-                asm volatile("bar.sync 1, 128;" ::: "memory");
+                asm volatile("bar.sync 1, %0;" ::"n"(32 * TC_EPI_WARPS) : "memory");
                 if (ok) ok = mbar_wait(&sh->acc_full[acc], acc_phase, err);
                 tc_fence_after();
-                float m = INFINITY;
+                float m = INFINITY;        // min over the half-tile of n_j - 2 g (foreign columns)
                 if (ok) {
-                    const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + acc * TC_BN;
-#pragma unroll 1
-                    for (int cc = 0; cc < TC_BN; cc += 32) {
-                        uint32_t g[32];
-                        tmem_ld32(tbase + cc, g);
+                    const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + acc * TC_BN + h * TC_CW;
+                    uint32_t g0[32], g1[32];
+                    tmem_ld32(tbase, g0);
+                    tmem_ld32(tbase + 32, g1);
+                    tmem_ld_wait();
+                    const float *cn = &sh->cnorm[acc][h * TC_CW];
+                    const int32_t *cc = &sh->ccomp[acc][h * TC_CW];
 #pragma unroll
-                        for (int q = 0; q < 32; q += 4) {
-                            const float4 nc = *reinterpret_cast<const float4 *>(&sh->cnorm[acc][cc + q]);
-                            const int4 cm = *reinterpret_cast<const int4 *>(&sh->ccomp[acc][cc + q]);
-                            const float ncv[4] = {nc.x, nc.y, nc.z, nc.w};
-                            const int32_t cmv[4] = {cm.x, cm.y, cm.z, cm.w};
+                    for (int q = 0; q < 32; q += 4) {
+                        const float4 nc = *reinterpret_cast<const float4 *>(cn + q);
+                        const int4 cmv4 = *reinterpret_cast<const int4 *>(cc + q);
+                        const float ncv[4] = {nc.x, nc.y, nc.z, nc.w};
+                        const int32_t cmv[4] = {cmv4.x, cmv4.y, cmv4.z, cmv4.w};
 #pragma unroll
-                            for (int u = 0; u < 4; ++u) {
-                                const float v = __fmaf_rn(-2.0f, __uint_as_float(g[q + u]), __fadd_rn(nrow, ncv[u]));
-                                m = fminf(m, cmv[u] != crow ? v : INFINITY);
-                            }
+                        for (int u = 0; u < 4; ++u) {
+                            const float v = __fmaf_rn(-2.0f, __uint_as_float(g0[q + u]), ncv[u]);
+                            m = fminf(m, cmv[u] != crow ? v : INFINITY);
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < 32; q += 4) {
+                        const float4 nc = *reinterpret_cast<const float4 *>(cn + 32 + q);
+                        const int4 cmv4 = *reinterpret_cast<const int4 *>(cc + 32 + q);
+                        const float ncv[4] = {nc.x, nc.y, nc.z, nc.w};
+                        const int32_t cmv[4] = {cmv4.x, cmv4.y, cmv4.z, cmv4.w};
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const float v = __fmaf_rn(-2.0f, __uint_as_float(g1[q + u]), ncv[u]);
+                            m = fminf(m, cmv[u] != crow ? v : INFINITY);
                         }
                     }
                 }
@@ -363,18 +386,20 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sh->acc_empty[acc]);
                 if (++acc == 2) { acc = 0; acc_phase ^= 1u; }
-                // rigorous bounds of the tile's smallest d2 of the represented points:
-                // accumulation + dropped lo.lo (A s_i s_j) and FP32 norm/epilogue rounding
+                m = __fadd_rn(m, nrow);
+                // rigorous bounds of the half-tile's smallest d2 of the represented
+                // points: accumulation + dropped lo.lo (A s_i s_j) and FP32
+                // norm/epilogue rounding
                 const float dlt = acoef * srow * ctsq + bcoef * (nrow + ctmax);
                 const float lb = m - dlt;
                 ubest = fminf(ubest, m + dlt);
-                if (lb < bv[TC_TOPK - 1]) top_insert(bv, bj, lb, ct);   // once per tile
+                if (lb < bv[TC_TOPK - 1]) top_insert(bv, bj, lb, 2 * ct + h);
             }
             if (row < n) {
-                const size_t o = ((size_t)sp * n + row) * TC_TOPK;
+                const size_t o = ((size_t)(2 * sp + h) * n + row) * TC_TOPK;
 #pragma unroll
                 for (int q = 0; q < TC_TOPK; ++q) { out_v[o + q] = bv[q]; out_j[o + q] = bj[q]; }
-                out_u[(size_t)sp * n + row] = ubest;
+                out_u[(size_t)(2 * sp + h) * n + row] = ubest;
             }
         }
     }
@@ -474,8 +499,9 @@ __global__ void k_tc_gather_comp(const int32_t *__restrict__ comp, const int32_t
     if (r < n) compp[r] = comp[perm[r]];
 }
 
-// One warp per (norm-ordered) row r, the point i = perm[r].  The column
-// splits' best-8 tile lower bounds and their best upper bound U are merged.
+// One warp per (norm-ordered) row r, the point i = perm[r].  The lists'
+// (column split x tile half) best-8 half-tile lower bounds and their best
+// upper bound U are merged.
 // The epilogue's bounds hold for the BF16-represented points; the exact
 // points differ by the representation error rep, so a tile can hold the
 // nearest foreign point only if its lower bound is <= U + 2 rep.  Those
@@ -491,7 +517,7 @@ __device__ __forceinline__ float approx_d2_f32(const float *__restrict__ a, cons
     return acc;
 }
 
-__global__ void __launch_bounds__(256) k_recheck_tc(const float *__restrict__ X, int64_t n, int32_t d, int splits,
+__global__ void __launch_bounds__(256) k_recheck_tc(const float *__restrict__ X, int64_t n, int32_t d, int lists,
                                                     const float *__restrict__ tv, const int32_t *__restrict__ tj,
                                                     const float *__restrict__ tu, const float *__restrict__ rsq,
                                                     const int32_t *__restrict__ perm, const int32_t *__restrict__ comp,
@@ -503,13 +529,14 @@ __global__ void __launch_bounds__(256) k_recheck_tc(const float *__restrict__ X,
     const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (r >= n) return;
     const int64_t i = perm[r];
-    // ---- merge: each lane holds up to 4 of the splits x 8 entries; the best 8
-    //      are selected by 8 rounds of a warp arg-min
-    const int ne = splits * TC_TOPK;
-    float ev[4];
-    int32_t ej[4];
+    // ---- merge: each lane holds up to 8 of the lists x 8 entries (lists <= 32);
+    //      the best 8 are selected by 8 rounds of a warp arg-min
+    constexpr int EPL = 8;
+    const int ne = lists * TC_TOPK;
+    float ev[EPL];
+    int32_t ej[EPL];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < EPL; ++q) {
         const int e = lane + 32 * q;
         if (e < ne) {
             const int sidx = e / TC_TOPK, k = e - sidx * TC_TOPK;
@@ -521,7 +548,7 @@ __global__ void __launch_bounds__(256) k_recheck_tc(const float *__restrict__ X,
             ej[q] = -1;
         }
     }
-    float U = lane < splits ? tu[(size_t)lane * n + r] : INFINITY;
+    float U = lane < lists ? tu[(size_t)lane * n + r] : INFINITY;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) U = fminf(U, __shfl_xor_sync(0xffffffffu, U, o));
     float bv[TC_TOPK];
@@ -531,7 +558,7 @@ __global__ void __launch_bounds__(256) k_recheck_tc(const float *__restrict__ X,
         float mv = ev[0];
         int ms = 0;
 #pragma unroll
-        for (int q = 1; q < 4; ++q)
+        for (int q = 1; q < EPL; ++q)
             if (ev[q] < mv) { mv = ev[q]; ms = q; }
         float wv = mv;
         int wl = lane;
@@ -543,11 +570,11 @@ __global__ void __launch_bounds__(256) k_recheck_tc(const float *__restrict__ X,
         }
         int32_t wj = -1;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) wj = (ms == q) ? ej[q] : wj;
+        for (int q = 0; q < EPL; ++q) wj = (ms == q) ? ej[q] : wj;
         wj = __shfl_sync(0xffffffffu, wj, wl);
         if (lane == wl) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
+            for (int q = 0; q < EPL; ++q)
                 if (ms == q) ev[q] = INFINITY;
         }
         bv[k] = wv;
@@ -579,16 +606,18 @@ __global__ void __launch_bounds__(256) k_recheck_tc(const float *__restrict__ X,
     double best = INFINITY;
     int32_t bestj = -1;
     const bool vec = (d & 3) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
-    for (int k = 0; k < TC_TOPK; ++k) {
+    for (int k = 0; k < TC_TOPK; k += 2) {
         if (bj[k] < 0 || (double)bv[k] > tile_cut) break;
-        // four columns per lane, four independent FMA chains
+        const bool second = bj[k + 1] >= 0 && (double)bv[k + 1] <= tile_cut;
+        // two half-tiles, two columns of each per lane: four independent FMA chains
         int64_t jj[4];
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
         bool live[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int64_t jp = (int64_t)bj[k] * TC_BN + lane + 32 * u;
-            jj[u] = jp < n ? (int64_t)perm[jp] : -1;
+            const int cand = (u < 2) ? bj[k] : (second ? bj[k + 1] : -1);
+            const int64_t jp = cand < 0 ? -1 : (int64_t)cand * TC_CW + lane + 32 * (u & 1);
+            jj[u] = (jp >= 0 && jp < n) ? (int64_t)perm[jp] : -1;
             live[u] = jj[u] >= 0 && comp[jj[u]] != ci;
         }
         if (vec) {
@@ -620,6 +649,7 @@ __global__ void __launch_bounds__(256) k_recheck_tc(const float *__restrict__ X,
                 }
             }
         }
+        if (!second) break;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -760,12 +790,13 @@ void TcScratch::carve(Arena &A, int64_t n, int32_t d, int splits_) {
     keys = A.take<uint64_t>(n);
     kbuf = A.take<uint64_t>(n);
     compp = A.take<int32_t>(n);
-    tv = A.take<float>((size_t)splits * n * TC_TOPK);
-    tj = A.take<int32_t>((size_t)splits * n * TC_TOPK);
-    tu = A.take<float>((size_t)splits * n);
+    tv = A.take<float>((size_t)2 * splits * n * TC_TOPK);      // lists = column split x tile half
+    tj = A.take<int32_t>((size_t)2 * splits * n * TC_TOPK);
+    tu = A.take<float>((size_t)2 * splits * n);
     err = A.take<uint32_t>(4);
 }
 
+// At most 16 splits: the recheck merges 2 x splits candidate lists in one warp.
 int tc_splits(int64_t n) {
     const int64_t rt = ceil_div(n, TC_BM);
     int64_t s = ceil_div((int64_t)num_sms() * 16, rt > 0 ? rt : 1);
@@ -826,11 +857,12 @@ cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t 
     // d2 = n_i + n_j - 2g against d2 of the represented points: tensor-core
     // FP32 accumulation of 3 d_pad products (worst case: one rounding of the
     // running magnitude per addition, 2^-23) and the dropped lo.lo term
-    // (2^-18), both times 2|y_i||y_j|; FP32 rounding of the norms and the
-    // epilogue, 6 x 2^-24 (n_i + n_j).  25 % headroom.
+    // (2^-18), both times 2|y_i||y_j|; FP32 rounding of the norms (2^-24
+    // (n_i + n_j)) and of the epilogue's fl(fl(n_j - 2g) + n_i) (at most
+    // 2^-24 (4 n_i + 5 n_j)): 8 x 2^-24 (n_i + n_j).  25 % headroom.
     const double u = 1.1920928955078125e-07;   // 2^-23
     const float acoef = (float)(1.25 * 2.0 * (3.0 * T.d_pad * u + 3.814697265625e-06));
-    const float bcoef = (float)(1.25 * 6.0 * 5.9604644775390625e-08);
+    const float bcoef = (float)(1.25 * 8.0 * 5.9604644775390625e-08);
     if (kchunks <= 2)
         k_sweep_tc<true><<<grid, TC_THREADS, TC_SMEM_ARES, ISO_S(s)>>>(
             T.map_h, T.map_l, T.nrm, T.rsq, T.tmax, T.tsq, acoef, bcoef, T.compp, n, ntiles, kchunks, T.splits,
@@ -843,7 +875,7 @@ cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t 
     // per element, plus the FP32 rounding of x - c (2^-24); 25 % headroom
     const double eps_rep = 1.25 * (3.814697265625e-06 + 5.9604644775390625e-08);
     const double e = 1.1 * (double)(d + 3) * 5.9604644775390625e-08;
-    k_recheck_tc<<<(unsigned)ceil_div(n * 32, 256), 256, 0, ISO_S(s)>>>(X, n, d, T.splits, T.tv, T.tj, T.tu, T.rsq,
+    k_recheck_tc<<<(unsigned)ceil_div(n * 32, 256), 256, 0, ISO_S(s)>>>(X, n, d, 2 * T.splits, T.tv, T.tj, T.tu, T.rsq,
                                                                         T.perm, S.comp, T.nmax_bits, eps_rep, e,
                                                                         S.rowd2, S.rowj, S.ovf_rows, S.counters);
     const double mul = (1.0 + e) / (1.0 - e);
