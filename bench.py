@@ -8,6 +8,11 @@ labels.  Inputs are resident in HBM; L2 is flushed (a 256 MiB write) before
 every step inside the timed region.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                  [--workload blobs_n100k_d64|batched_4096_d32]
+
+--workload batched_4096_d32 times isoclust_cluster_batched on 4,096
+independent sets (sizes log-uniform in [64, 8192], d = 32, 2-8 blobs each,
+k = blob count): one step = one call over all sets.
 
 N > 1 (torchrun, one rank per GPU): every rank clusters its own independent
 point set (replicas; the path has no cross-GPU exchange), value = total
@@ -33,6 +38,7 @@ import numpy as np  # noqa: E402
 METRIC = "points/s end-to-end"
 UNIT = "points/s"
 WORKLOAD = "blobs_n100k_d64"
+BATCHED = "batched_4096_d32"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP32_LANES_PER_SM = 128
 
@@ -171,9 +177,13 @@ def main():
     ap.add_argument("--no-mst-compare", action="store_true")
     ap.add_argument("--n", type=int, default=0,
                     help="points of the same generator (profiling of a smaller case); default: the full 100,000")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, BATCHED])
+    ap.add_argument("--nsets", type=int, default=0, help="batched: fewer sets of the same recipe (profiling)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         args.warmup = 3
+    if args.workload == BATCHED:
+        return main_batched(args)
 
     from paper_1702_04739_gb300 import workloads
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -335,6 +345,191 @@ def main():
         line["e2e"] = e2e
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(X, k, sigma)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+# ---------------------------------------------------------------- independent sets
+def _oracle_sets_time(X, offs, ks, sigma, sets, threads):
+    import oracle
+    oracle.build()
+    oracle.set_threads(threads)
+    t0 = time.perf_counter()
+    for b in sets:
+        oracle.cluster(np.ascontiguousarray(X[offs[b]:offs[b + 1]]), int(ks[b]), sigma)
+    return time.perf_counter() - t0
+
+
+def _sets_sample(offs, budget_pairs=1.5e9):
+    """The first sets whose n^2 sum stays within the budget (about 10-30 s of
+    oracle work on 16 cores)."""
+    sizes = np.diff(offs).astype(np.float64)
+    c = np.cumsum(sizes ** 2)
+    m = int(np.searchsorted(c, budget_pairs)) + 1
+    return list(range(min(m, sizes.size)))
+
+
+def _sets_cpu(X, offs, ks, sigma, steps=1, warmup=0):
+    sizes = np.diff(offs).astype(np.float64)
+    sets = _sets_sample(offs)
+    cores = _cpu_cores()
+    for _ in range(warmup):
+        _oracle_sets_time(X, offs, ks, sigma, sets, cores)
+    t = statistics.mean(_oracle_sets_time(X, offs, ks, sigma, sets, cores) for _ in range(max(steps, 1)))
+    scale = float((sizes ** 2).sum() / (sizes[sets] ** 2).sum())
+    value = float(offs[-1]) / (t * scale)
+    return value, t, scale, sets, cores
+
+
+def main_batched(args):
+    from paper_1702_04739_gb300 import workloads
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    X, offs, ks, sigma = workloads.make_batched(BATCHED, seed=rank, nsets=args.nsets or None)
+    N, d = X.shape
+    nsets = ks.size
+    cfg = {"workload": BATCHED, "nsets": int(nsets), "points": int(N), "d": int(d), "sigma": sigma,
+           "sizes": "log-uniform in [64, 8192]", "k": "blob count (2-8)", "storage": "f32"}
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        value, t, scale, sets, cores = _sets_cpu(X, offs, ks, sigma, args.steps, args.warmup)
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * scale * 1000.0,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": cfg,
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                 "sample": f"each step: oracle on the first {len(sets)} sets, {t:.2f} s mean; "
+                                           f"scaled to all {nsets} sets by their n^2 sum (x{scale:.1f})"},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
+
+    import torch
+    from paper_1702_04739_gb300 import isoclust
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    plan = isoclust.BatchPlan(offs, ks)
+    Xd = torch.from_numpy(X).to(dev)
+    labels = torch.empty(N, dtype=torch.int32, device=dev)
+    residual = torch.empty(N, dtype=torch.uint8, device=dev)
+    ik = torch.empty(nsets, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        flush.zero_()
+        isoclust.cluster_batched_into(Xd, plan, sigma, labels, residual, ik)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    prof = []
+    if pg is not None:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    l0 = isoclust.kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+        prof.append(isoclust.last_profile())
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    if pg is not None:
+        pg.barrier()
+    launches = isoclust.kernel_launches() - l0
+    clk = clocks.stop()
+    t_ms = ev0.elapsed_time(ev1)
+    if pg is not None:
+        tt = torch.tensor([t_ms], device=dev)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    ms_per_step = t_ms / args.steps
+    value = world * N / (ms_per_step / 1000.0)
+
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.from_numpy(X).pin_memory()
+        lh = torch.empty(N, dtype=torch.int32).pin_memory()
+        rh = torch.empty(N, dtype=torch.uint8).pin_memory()
+        ih = torch.empty(nsets, dtype=torch.float64).pin_memory()
+
+        def e2e_step():
+            flush.zero_()
+            Xd.copy_(Xh, non_blocking=True)
+            isoclust.cluster_batched_into(Xd, plan, sigma, labels, residual, ik)
+            lh.copy_(labels, non_blocking=True)
+            rh.copy_(residual, non_blocking=True)
+            ih.copy_(ik, non_blocking=True)
+        e2e_step()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        te = e0.elapsed_time(e1)
+        e2e = {"value": world * N / (te / args.steps / 1000.0), "unit": UNIT,
+               "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": int(N * 5 + nsets * 8)}
+
+    peaks, src = _peaks()
+    w_ms = statistics.mean(p["weights_ms"] for p in prof)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = sms * FP32_LANES_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    tiles, tiles_dw = prof[-1]["omega_tiles"], prof[-1]["omega_tiles_dw"]
+    screen_ops, dw_ops = 2.0 * d + 12.0, 21.0 * d + 140.0
+    work = tiles * 4096.0 * screen_ops + tiles_dw * 4096.0 * dw_ops
+    achieved = work / (w_ms / 1000.0) / 1e12
+    sizes = np.diff(offs)
+    rounds = prof[-1]["boruvka_rounds"]
+    mst_ms = statistics.mean(p["mst_ms"] for p in prof)
+    pad128 = -(-sizes // 128) * 128
+    exe_flop = rounds * 3 * 2.0 * float((pad128.astype(np.float64) ** 2).sum()) * (-(-d // 64) * 64)
+    stages = {key: round(statistics.mean(p[key] for p in prof), 3)
+              for key in ("validate_ms", "weights_ms", "mst_ms", "orient_ms", "search_ms", "labels_ms")}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": dict(cfg, parallelism=f"replicas x{world}" if world > 1 else "single GPU",
+                       l2="flushed by a 256 MiB write before every step (inside the timed region)"),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                     "frac": achieved / alu_peak, "traffic": None,
+                     "kernel": "k_weights_sym (omega over the sets' tile pairs, double-word FP32)",
+                     "note": f"FP32-pipe instructions of the algorithm ({screen_ops:.0f} per screened pair, "
+                             f"{dw_ops:.0f} per double-word pair; {tiles} tile pairs screened, {tiles_dw} kept) "
+                             f"over the omega stage's event time; peak = {sms} SMs x {FP32_LANES_PER_SM} lanes x "
+                             f"max SM clock ({src})"},
+        "stages_ms": stages,
+        "mst": {"stage_ms": mst_ms, "rounds": rounds,
+                "executed_tensor_tflops": exe_flop / (mst_ms / 1000.0) / 1e12,
+                "peak_bf16_tflops": peaks.get("bf16_tflops"), "peak_source": src},
+        "omega_tiles": {"screened": tiles, "double_word": tiles_dw},
+        "gpu_launches": int(launches), "clocks": clk,
+    }
+    if e2e is not None:
+        line["e2e"] = e2e
+    if rank == 0 and not args.no_cpu_baseline:
+        value_c, t, scale, sets, cores = _sets_cpu(X, offs, ks, sigma)
+        line["cpu_baseline"] = {"value": value_c, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"oracle on the first {len(sets)} sets took {t:.2f} s on {cores} threads; "
+                                          f"scaled to all {nsets} sets by their n^2 sum (x{scale:.1f})"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg is not None:

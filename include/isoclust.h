@@ -238,8 +238,48 @@ isoclust_status isoclust_cluster_detail(const void *X, int64_t n, int32_t d, int
                                         int32_t *edge_u, int32_t *edge_v, double *edge_d2,
                                         void *stream);
 
+/*
+ * isoclust_cluster_batched -- independent point sets in one call: set b is
+ * rows offsets[b] .. offsets[b+1]-1 of X and is clustered into ks[b] sets
+ * exactly as isoclust_cluster would cluster it alone (its own MST, omega
+ * over its own pairs, phi, statistics, threshold search and labels; the
+ * paper defines the method per point set, Section 2.2).  The sets share each
+ * launch: one Boruvka forest whose sweep never pairs points of different
+ * sets, one omega sweep over the sets' own tile pairs, and one tree pass with
+ * a search state per set.
+ *   X        N x d points, N = offsets[nsets] (device, F32 only).
+ *   offsets  [nsets+1] int64 HOST array, offsets[0] = 0, every set >= 2 points.
+ *   ks       [nsets] int32 HOST array, 1 <= ks[b] <= points of set b.
+ *   labels   [N] int32, residual [N] uint8 (device, written): row v of set b
+ *            gets its label within set b, 0 .. ks[b]-1, or -1 (residual), as
+ *            isoclust_cluster would give it on that set alone.
+ *   i_k      [nsets] double (device, written); beta [nsets] (device, may be
+ *            NULL).
+ *   opts     alpha = 0, omega_mode FULL, root 0 (each set's first point),
+ *            precision AUTO or BF16_TC; others -> ISOCLUST_ERR_INVALID_ARG.
+ * Needs an sm_103 device (tensor-core sweep).  The plan of the launch is
+ * built on the host from offsets, hence host arrays.  Errors: as
+ * isoclust_cluster, per set; a set with fewer than 2 points or ks[b] < 1 ->
+ * ISOCLUST_ERR_INVALID_ARG, ks[b] above the set's size -> ISOCLUST_ERR_K_GT_N.
+ */
+isoclust_status isoclust_cluster_batched(const void *X, const int64_t *offsets, int32_t nsets,
+                                         int32_t d, int32_t dtype, const int32_t *ks, double sigma,
+                                         const isoclust_opts *opts, int32_t *labels,
+                                         uint8_t *residual, double *i_k, double *beta,
+                                         void *stream);
+
+/* isoclust_cluster_batched that also returns, for all N points (device,
+ * NULL to skip): parent [N] int32 in global point indices (-1 at each set's
+ * first point), phi_par [N] double, omega [N] double. */
+isoclust_status isoclust_cluster_batched_detail(const void *X, const int64_t *offsets, int32_t nsets,
+                                                int32_t d, int32_t dtype, const int32_t *ks,
+                                                double sigma, const isoclust_opts *opts,
+                                                int32_t *labels, uint8_t *residual, double *i_k,
+                                                double *beta, int32_t *parent, double *phi_par,
+                                                double *omega, void *stream);
+
 /* Per-stage device times (milliseconds, CUDA events on the call's stream)
- * of the last isoclust_cluster / _detail call on this host thread:
+ * of the last isoclust_cluster / _detail / _batched call on this host thread:
  * t[0] validation, t[1] weights, t[2] MST, t[3] tree orientation + stats,
  * t[4] bisection, t[5] labels.  counts[0] = Boruvka rounds, counts[1] =
  * rows rescanned after a candidate-margin overflow, counts[2] = Algorithm-1

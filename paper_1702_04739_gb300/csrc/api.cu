@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <vector>
 #include <mutex>
 
 #include "common.cuh"
@@ -20,6 +21,12 @@ cudaError_t weights_launch_sym(const float *X, int64_t n, int32_t d, double sigm
                                const unsigned long long *nnbits, double *omega, void *part,
                                unsigned long long *tile_counts, cudaStream_t s);
 constexpr size_t SYM_PART_LIMIT = size_t(16) << 30;   // symmetric sweep up to 16 GiB of partials
+size_t weights_sym_sets_bytes(int64_t n_pad, int64_t nitems);
+cudaError_t weights_launch_sym_sets(const float *Xp, int64_t n_pad, int32_t d, double sigma, int include_self,
+                                    const unsigned long long *nnbits, double *omega, void *part, const int2 *witems,
+                                    int64_t nitems, const int32_t *tile_valid, const int32_t *tile_set,
+                                    const int64_t *tile0, const int64_t *ntl, const int64_t *item0, int64_t max_n,
+                                    unsigned long long *tile_counts, cudaStream_t s);
 
 static std::atomic<long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -450,6 +457,304 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
     return map_status(fin, false);
 }
 
+// ---------------------------------------------------------------- independent sets
+namespace {
+// upper bound search: the b with base[b] <= w < base[b + 1]
+__device__ __forceinline__ int32_t find_set(const int64_t *__restrict__ base, int32_t nsets, int64_t w) {
+    int32_t lo = 0, hi = nsets - 1;
+    while (lo < hi) {
+        const int32_t mid = (lo + hi + 1) >> 1;
+        if (base[mid] <= w) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_set_of(const int64_t *__restrict__ offs, int32_t *__restrict__ set_of) {
+    const int32_t b = blockIdx.x;
+    for (int64_t v = offs[b] + threadIdx.x; v < offs[b + 1]; v += blockDim.x) set_of[v] = b;
+}
+
+// tensor-core sweep items: set b's row tiles against the set's column tiles
+__global__ void k_tc_items(const int64_t *__restrict__ tcbase, const int64_t *__restrict__ rowbase, int32_t nsets,
+                           int4 *__restrict__ items) {
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= tcbase[nsets]) return;
+    const int32_t b = find_set(tcbase, nsets, w);
+    const int32_t t0 = (int32_t)(rowbase[b] / 128), nt = (int32_t)(tcbase[b + 1] - tcbase[b]);
+    items[w] = make_int4(t0 + (int32_t)(w - tcbase[b]), t0, t0 + nt, 0);
+}
+
+// omega items: the upper triangle of set b's 64-row tile grid, row-major
+__global__ void k_omega_items(const int64_t *__restrict__ item0, const int64_t *__restrict__ tile0,
+                              const int64_t *__restrict__ ntl, int32_t nsets, int2 *__restrict__ items) {
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= item0[nsets]) return;
+    const int32_t b = find_set(item0, nsets, w);
+    const int64_t T = ntl[b], q = w - item0[b];
+    int64_t i = 0;
+    while ((i + 1) * T - (i + 1) * i / 2 <= q) ++i;     // at most T steps (T <= max set / 64)
+    const int64_t j = i + (q - (i * T - i * (i - 1) / 2));
+    items[w] = make_int2((int32_t)(tile0[b] + i), (int32_t)(tile0[b] + j));
+}
+
+__global__ void k_omega_tiles(const int64_t *__restrict__ tile0, const int64_t *__restrict__ offs, int32_t nsets,
+                              int64_t ntiles, int32_t *__restrict__ tile_valid, int32_t *__restrict__ tile_set) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    const int32_t b = find_set(tile0, nsets, t);
+    const int64_t nb = offs[b + 1] - offs[b], lo = (t - tile0[b]) * 64;
+    const int64_t left = nb - lo;
+    tile_valid[t] = (int32_t)(left < 64 ? (left > 0 ? left : 0) : 64);
+    tile_set[t] = b;
+}
+
+// the forest's edges plus one virtual edge (nv, first point of b) per set
+__global__ void k_virtual_edges(const int64_t *__restrict__ offs, int32_t nsets, int64_t m_mst, int64_t nv,
+                                int32_t *__restrict__ eu, int32_t *__restrict__ ev, double *__restrict__ ed2) {
+    const int32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nsets) return;
+    eu[m_mst + b] = (int32_t)nv;
+    ev[m_mst + b] = (int32_t)offs[b];
+    ed2[m_mst + b] = 0.0;
+}
+
+__global__ void k_check_edges_sets(const int32_t *counters, int64_t n, int32_t nsets, uint32_t *st) {
+    if (counters[MC_NEDGES] != n - nsets || counters[MC_NCOMP] != nsets) atomicOr(st, DEV_EDGE_COUNT);
+}
+
+// padded omega row of point v: its set's first tile, plus its preorder rank
+// inside the set (the sets' subtrees are consecutive in the preorder)
+__global__ void k_pos64(const int32_t *__restrict__ pre, const int32_t *__restrict__ set_of,
+                        const int64_t *__restrict__ offs, const int64_t *__restrict__ tile0, int64_t n,
+                        int64_t *__restrict__ pos) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const int32_t b = set_of[v];
+    pos[v] = tile0[b] * 64 + (int64_t)(pre[v] - pre[offs[b]]);
+}
+
+__global__ void k_gather_pad(const float *__restrict__ X, const int64_t *__restrict__ pos,
+                             const unsigned long long *__restrict__ nnbits, int64_t n, int32_t d,
+                             float *__restrict__ Xp, unsigned long long *__restrict__ nnp) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * (int64_t)d) return;
+    const int64_t v = idx / d, t = idx - v * d;
+    const int64_t r = pos[v];
+    Xp[r * d + t] = X[idx];
+    if (t == 0) nnp[r] = nnbits[v];
+}
+
+__global__ void k_scatter_pad(const double *__restrict__ omp, const int64_t *__restrict__ pos, int64_t n,
+                              double *__restrict__ om) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) om[v] = omp[pos[v]];
+    if (v == n) om[n] = 1.0;         // the virtual root (never read)
+}
+}  // namespace
+
+static isoclust_status cluster_sets_impl(const void *X, const int64_t *offsets, int32_t nsets, int32_t d,
+                                         int32_t dtype, const int32_t *ks, double sigma, const isoclust_opts *opts_in,
+                                         int32_t *labels, uint8_t *residual, double *i_k, double *beta,
+                                         int32_t *out_parent, double *out_phi, double *out_omega, cudaStream_t s) {
+    if (!X || !offsets || !ks || !labels || !residual || !i_k)
+        return fail(ISOCLUST_ERR_INVALID_ARG, "a required pointer is NULL");
+    if (nsets < 1) return fail(ISOCLUST_ERR_INVALID_ARG, "nsets = %d must be >= 1", nsets);
+    if (dtype != ISOCLUST_F32) return fail(ISOCLUST_ERR_INVALID_ARG, "independent sets need F32 input");
+    if (d < 1) return fail(ISOCLUST_ERR_INVALID_ARG, "d = %d must be >= 1", d);
+    if (!(sigma > 0.0) || !isfinite(sigma)) return fail(ISOCLUST_ERR_INVALID_ARG, "sigma must be finite and > 0");
+    if (offsets[0] != 0) return fail(ISOCLUST_ERR_INVALID_ARG, "offsets[0] must be 0");
+    int64_t max_n = 0;
+    for (int32_t b = 0; b < nsets; ++b) {
+        const int64_t nb = offsets[b + 1] - offsets[b];
+        if (nb < 2) return fail(ISOCLUST_ERR_INVALID_ARG, "set %d has %lld points (need >= 2)", b, (long long)nb);
+        if (ks[b] < 1) return fail(ISOCLUST_ERR_INVALID_ARG, "ks[%d] = %d must be >= 1", b, ks[b]);
+        if (ks[b] > nb) return fail(ISOCLUST_ERR_K_GT_N, "ks[%d] = %d exceeds the set's %lld points", b, ks[b], (long long)nb);
+        if (nb > max_n) max_n = nb;
+    }
+    const int64_t N = offsets[nsets];
+    isoclust_status st;
+    if ((st = check_points(X, N, d, dtype, 2))) return st;
+    isoclust_opts o = resolve_opts(opts_in);
+    if ((st = check_opts(o, N, dtype))) return st;
+    if (o.alpha != 0.0 || o.omega_mode != ISOCLUST_OMEGA_FULL || o.root != 0 ||
+        (o.precision != ISOCLUST_PREC_AUTO && o.precision != ISOCLUST_PREC_BF16_TC))
+        return fail(ISOCLUST_ERR_INVALID_ARG,
+                    "independent sets support alpha = 0, omega_mode FULL, root 0 and precision AUTO / BF16_TC");
+    if (!tc_supported()) return fail(ISOCLUST_ERR_INVALID_ARG, "independent sets need an sm_103 device");
+
+    // ---- plan (host): per-set tile runs of the two padded row spaces
+    const int64_t P = nsets;
+    std::vector<int64_t> plan((size_t)(6 * P + 3));
+    int64_t *h_offs = plan.data();                  // [P + 1]
+    int64_t *h_rowbase = h_offs + (P + 1);          // [P]      first 128-row of each set (TC sweep)
+    int64_t *h_tcbase = h_rowbase + P;              // [P + 1]  first sweep item of each set
+    int64_t *h_tile0 = h_tcbase + (P + 1);          // [P]      first 64-row tile of each set (omega)
+    int64_t *h_ntl = h_tile0 + P;                   // [P]      64-row tiles of each set
+    int64_t *h_item0 = h_ntl + P;                   // [P + 1]  first omega item of each set
+    int64_t rb = 0, tc = 0, t64 = 0, it = 0;
+    for (int32_t b = 0; b < nsets; ++b) {
+        const int64_t nb = offsets[b + 1] - offsets[b];
+        h_offs[b] = offsets[b];
+        h_rowbase[b] = rb;
+        h_tcbase[b] = tc;
+        const int64_t t128 = ceil_div(nb, 128);
+        rb += t128 * 128;
+        tc += t128;
+        const int64_t T = ceil_div(nb, 64);
+        h_tile0[b] = t64;
+        h_ntl[b] = T;
+        h_item0[b] = it;
+        t64 += T;
+        it += T * (T + 1) / 2;
+    }
+    h_offs[P] = N;
+    h_tcbase[P] = tc;
+    h_item0[P] = it;
+    const int64_t n_pad128 = rb, ntc = tc, n_pad64 = t64 * 64, ntile64 = t64, nitems = it;
+
+    const int dev = current_device();
+    std::lock_guard<std::mutex> lock(g_call_mu[dev]);
+    MstScratch M;
+    TcScratch TC;
+    TreeScratch TS;
+    struct {
+        uint32_t *status;
+        int64_t *plan;
+        int32_t *ks, *set_of, *eu, *ev, *tile_valid, *tile_set;
+        int4 *titems;
+        int2 *witems;
+        double *ed2, *phi, *om, *omp;
+        SearchState *SS;
+        int64_t *pos;
+        float *Xp;
+        unsigned long long *nnp, *tiles;
+        void *sym;
+    } B;
+    auto carve = [&](Arena &A) {
+        B.status = A.take<uint32_t>(4);
+        B.plan = A.take<int64_t>(plan.size());
+        B.ks = A.take<int32_t>(P);
+        B.set_of = A.take<int32_t>(N);
+        B.titems = A.take<int4>(ntc);
+        B.witems = A.take<int2>(nitems > 0 ? nitems : 1);
+        B.tile_valid = A.take<int32_t>(ntile64);
+        B.tile_set = A.take<int32_t>(ntile64);
+        M.carve(A, N, 1);
+        TC.carve(A, N, d, 1, n_pad128, nsets, 2);
+        TS.carve(A, N + 1);
+        B.eu = A.take<int32_t>(N);
+        B.ev = A.take<int32_t>(N);
+        B.ed2 = A.take<double>(N);
+        B.phi = A.take<double>(N + 1);
+        B.om = A.take<double>(N + 1);
+        B.SS = A.take<SearchState>(P);
+        B.pos = A.take<int64_t>(N);
+        B.Xp = A.take<float>((size_t)n_pad64 * d);
+        B.nnp = A.take<unsigned long long>(n_pad64);
+        B.omp = A.take<double>(n_pad64);
+        B.tiles = A.take<unsigned long long>(2);
+        B.sym = (void *)A.take<unsigned char>(weights_sym_sets_bytes(n_pad64, nitems));
+    };
+    Arena meas;
+    carve(meas);
+    void *base = scratch_acquire(meas.off, s, &st);
+    if (!base) return st;
+    Arena A{(char *)base, meas.off + 4096, 0, false};
+    carve(A);
+    if (A.overflow) return fail(ISOCLUST_ERR_INTERNAL, "scratch carve overflow");
+    const int64_t *d_offs = B.plan, *d_rowbase = d_offs + (P + 1), *d_tcbase = d_rowbase + P;
+    const int64_t *d_tile0 = d_tcbase + (P + 1), *d_ntl = d_tile0 + P, *d_item0 = d_ntl + P;
+
+    Events ev;
+    ev.rec(0, s);
+    ISO_CUDA(cudaMemcpyAsync(B.plan, plan.data(), plan.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    ISO_CUDA(cudaMemcpyAsync(B.ks, ks, (size_t)P * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    ISO_CUDA(cudaMemsetAsync(B.status, 0, sizeof(uint32_t) * 4, s));
+    ISO_CUDA(cudaMemsetAsync(TS.status, 0, sizeof(uint32_t), s));
+    ISO_CUDA(check_finite(X, N * (int64_t)d, dtype, B.status, nullptr, s));
+    k_set_of<<<(unsigned)P, 256, 0, ISO_S(s)>>>(d_offs, B.set_of);
+    k_tc_items<<<(unsigned)ceil_div(ntc, TPB), TPB, 0, ISO_S(s)>>>(d_tcbase, d_rowbase, nsets, B.titems);
+    if (nitems > 0)
+        k_omega_items<<<(unsigned)ceil_div(nitems, TPB), TPB, 0, ISO_S(s)>>>(d_item0, d_tile0, d_ntl, nsets, B.witems);
+    k_omega_tiles<<<(unsigned)ceil_div(ntile64, TPB), TPB, 0, ISO_S(s)>>>(d_tile0, d_offs, nsets, ntile64,
+                                                                          B.tile_valid, B.tile_set);
+    uint32_t hst = 0;
+    ISO_CUDA(cudaMemcpyAsync(&hst, B.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    ISO_CUDA(cudaStreamSynchronize(s));       // also retires the pageable plan upload
+    if (hst) return map_status(hst, false);
+    ev.rec(1, s);
+
+    // Section 2.2 steps 1-2 for every set: one Boruvka forest
+    TC.items = B.titems;
+    TC.nitems = ntc;
+    TC.nsets = nsets;
+    TC.set_of = B.set_of;
+    TC.offs = d_offs;
+    TC.rowbase = d_rowbase;
+    ISO_CUDA(mst_build(M, X, N, d, dtype, false, B.status, s, &TC, nsets, max_n));
+    k_check_edges_sets<<<1, 1, 0, ISO_S(s)>>>(M.counters, N, nsets, B.status);
+    ev.rec(2, s);
+
+    // Section 2.2 step 3: the sets' trees under a virtual root (vertex N)
+    const int64_t m_mst = N - nsets;
+    ISO_CUDA(cudaMemcpyAsync(B.eu, M.eu, sizeof(int32_t) * m_mst, cudaMemcpyDeviceToDevice, s));
+    ISO_CUDA(cudaMemcpyAsync(B.ev, M.ev, sizeof(int32_t) * m_mst, cudaMemcpyDeviceToDevice, s));
+    ISO_CUDA(cudaMemcpyAsync(B.ed2, M.ed2, sizeof(double) * m_mst, cudaMemcpyDeviceToDevice, s));
+    k_virtual_edges<<<(unsigned)ceil_div(P, TPB), TPB, 0, ISO_S(s)>>>(d_offs, nsets, m_mst, N, B.eu, B.ev, B.ed2);
+    ISO_CUDA(orient_tree(TS, B.eu, B.ev, N + 1, (int32_t)N, nullptr, s, B.set_of));
+    {
+        uint32_t h2 = 0, h3 = 0;
+        ISO_CUDA(cudaMemcpyAsync(&h2, B.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        ISO_CUDA(cudaMemcpyAsync(&h3, TS.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        ISO_CUDA(cudaStreamSynchronize(s));
+        if (h2 | h3) return map_status(h2 | h3, false);
+    }
+    ISO_CUDA(fix_set_roots(TS, nsets, d_offs, s));
+    ev.rec(3, s);
+
+    // eq. omega per set, symmetric tile pairs in each set's MST preorder
+    ISO_CUDA(nn_from_edges(M, M.eu, M.ev, M.ed2, s, m_mst));
+    k_pos64<<<(unsigned)ceil_div(N, TPB), TPB, 0, ISO_S(s)>>>(TS.T.pre, B.set_of, d_offs, d_tile0, N, B.pos);
+    ISO_CUDA(cudaMemsetAsync(B.nnp, 0xff, sizeof(unsigned long long) * n_pad64, s));
+    k_gather_pad<<<(unsigned)ceil_div(N * (int64_t)d, TPB), TPB, 0, ISO_S(s)>>>((const float *)X, B.pos, M.nnbits, N, d,
+                                                                                B.Xp, B.nnp);
+    ISO_CUDA(cudaMemsetAsync(B.tiles, 0, 2 * sizeof(unsigned long long), s));
+    ISO_CUDA(weights_launch_sym_sets(B.Xp, n_pad64, d, sigma, o.include_self, B.nnp, B.omp, B.sym, B.witems, nitems,
+                                     B.tile_valid, B.tile_set, d_tile0, d_ntl, d_item0, max_n, B.tiles, s));
+    k_scatter_pad<<<(unsigned)ceil_div(N + 1, TPB), TPB, 0, ISO_S(s)>>>(B.omp, B.pos, N, B.om);
+    ev.rec(4, s);
+    ISO_CUDA(phi_from_edges(TS, B.ed2, sigma, B.phi, s));
+    // Algorithm 2 + Algorithm 1 per set, then Algorithm 4's labels
+    ISO_CUDA(tree_search_and_label_sets(TS, nsets, d_offs, B.set_of, B.ks, B.SS, B.phi, B.om, nullptr, labels, residual,
+                                        i_k, beta, s));
+    ev.rec(5, s);
+    if (out_parent) ISO_CUDA(cudaMemcpyAsync(out_parent, TS.T.parent, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, s));
+    if (out_phi) ISO_CUDA(cudaMemcpyAsync(out_phi, B.phi, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    if (out_omega) ISO_CUDA(cudaMemcpyAsync(out_omega, B.om, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    ev.rec(6, s);
+    ISO_CUDA(cudaGetLastError());
+    ISO_CUDA(cudaStreamSynchronize(s));
+    uint32_t fin = 0, tf = 0;
+    ISO_CUDA(cudaMemcpy(&fin, B.status, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    ISO_CUDA(cudaMemcpy(&tf, TS.status, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    fin |= tf;
+    int32_t cnt[8] = {0};
+    ISO_CUDA(cudaMemcpy(cnt, M.counters, sizeof(cnt), cudaMemcpyDeviceToHost));
+    g_prof_ms[0] = ev.ms(0, 1);
+    g_prof_ms[1] = ev.ms(3, 4);
+    g_prof_ms[2] = ev.ms(1, 2);
+    g_prof_ms[3] = ev.ms(2, 3);
+    g_prof_ms[4] = ev.ms(4, 5);
+    g_prof_ms[5] = ev.ms(5, 6);
+    g_prof_cnt[0] = cnt[MC_ROUNDS];
+    g_prof_cnt[1] = cnt[MC_OVF_TOTAL] + cnt[MC_OVERFLOW];
+    g_prof_cnt[2] = DP_SEARCH_PASSES + 1;
+    g_prof_cnt[3] = 0;
+    ISO_CUDA(cudaMemcpy(g_prof_tiles, B.tiles, sizeof(g_prof_tiles), cudaMemcpyDeviceToHost));
+    g_prof_sym = 1;
+    return map_status(fin, false);
+}
+
 }  // namespace iso
 
 using namespace iso;
@@ -521,6 +826,22 @@ isoclust_status isoclust_cluster_detail(const void *X, int64_t n, int32_t d, int
                                         int32_t *edge_u, int32_t *edge_v, double *edge_d2, void *stream) {
     return cluster_impl(X, n, d, dtype, k, sigma, opts, labels, residual, i_k, parent, phi_par, omega, p, beta,
                         edge_u, edge_v, edge_d2, (cudaStream_t)stream, true);
+}
+
+isoclust_status isoclust_cluster_batched(const void *X, const int64_t *offsets, int32_t nsets, int32_t d,
+                                         int32_t dtype, const int32_t *ks, double sigma, const isoclust_opts *opts,
+                                         int32_t *labels, uint8_t *residual, double *i_k, double *beta, void *stream) {
+    return cluster_sets_impl(X, offsets, nsets, d, dtype, ks, sigma, opts, labels, residual, i_k, beta, nullptr, nullptr,
+                             nullptr, (cudaStream_t)stream);
+}
+
+isoclust_status isoclust_cluster_batched_detail(const void *X, const int64_t *offsets, int32_t nsets, int32_t d,
+                                                int32_t dtype, const int32_t *ks, double sigma,
+                                                const isoclust_opts *opts, int32_t *labels, uint8_t *residual,
+                                                double *i_k, double *beta, int32_t *parent, double *phi_par,
+                                                double *omega, void *stream) {
+    return cluster_sets_impl(X, offsets, nsets, d, dtype, ks, sigma, opts, labels, residual, i_k, beta, parent, phi_par,
+                             omega, (cudaStream_t)stream);
 }
 
 isoclust_status isoclust_vertex_weights(const void *X, int64_t n, int32_t d, int32_t dtype, double sigma,

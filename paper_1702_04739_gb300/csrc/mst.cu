@@ -29,7 +29,8 @@ inline int log2_ceil(int64_t x) {
 }
 
 __device__ __forceinline__ bool active(const int32_t *counters) {
-    return *((volatile const int32_t *)(counters + MC_NCOMP)) > 1;
+    const volatile int32_t *c = counters;
+    return c[MC_NCOMP] > c[MC_TARGET];
 }
 
 // ---------------------------------------------------------------- FP32 sweep
@@ -259,10 +260,11 @@ __global__ void __launch_bounds__(TPB) k_sweep_f64(const T *__restrict__ X, int6
 }
 
 // ---------------------------------------------------------------- union-find
-__global__ void k_mst_init(int32_t *comp, int64_t n, int32_t *counters) {
+__global__ void k_mst_init(int32_t *comp, int64_t n, int32_t target, int32_t *counters) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v < n) comp[v] = (int32_t)v;
     if (v == 0) {
+        counters[MC_TARGET] = target;
         counters[MC_OVERFLOW] = 0;
         counters[MC_NEDGES] = 0;
         counters[MC_NCOMP] = (int32_t)n;
@@ -479,10 +481,14 @@ __global__ void k_or_err(const uint32_t *src, uint32_t *dst) {
 }
 
 cudaError_t mst_build(MstScratch &S, const void *X, int64_t n, int32_t d, int dtype, bool sweep_fp64,
-                      uint32_t *status, cudaStream_t s, TcScratch *tc) {
-    k_mst_init<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.comp, n, S.counters);
-    const int R = log2_ceil(n) + 1;
-    const int L = log2_ceil(n) + 1;
+                      uint32_t *status, cudaStream_t s, TcScratch *tc, int32_t target, int64_t max_n) {
+    k_mst_init<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.comp, n, target, S.counters);
+    // Boruvka at least halves every unfinished set's components per round;
+    // component chains never leave a set, so pointer jumping needs
+    // log2 of the largest set
+    const int64_t span = max_n > 0 ? max_n : n;
+    const int R = log2_ceil(span) + 1;
+    const int L = log2_ceil(span) + 1;
     cudaError_t e;
     if (tc && (e = tc_prepare(*tc, (const float *)X, n, d, s))) return e;
     for (int r = 0; r < R; ++r) {
@@ -511,7 +517,7 @@ cudaError_t mst_build(MstScratch &S, const void *X, int64_t n, int32_t d, int dt
 
 cudaError_t nn_sweep(MstScratch &S, const void *X, int64_t n, int32_t d, int dtype, bool sweep_fp64,
                      uint32_t *status, cudaStream_t s, TcScratch *tc) {
-    k_mst_init<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.comp, n, S.counters);
+    k_mst_init<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.comp, n, 1, S.counters);
     k_round_begin<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.counters, S.cd2, S.cpair, n);
     cudaError_t e;
     if (tc) {
@@ -537,8 +543,9 @@ cudaError_t mst_sort_edges(MstScratch &S, int32_t *out_u, int32_t *out_v, double
     return cudaGetLastError();
 }
 
-cudaError_t nn_from_edges(MstScratch &S, const int32_t *eu, const int32_t *ev, const double *ed2, cudaStream_t s) {
-    const int64_t m = S.n - 1;
+cudaError_t nn_from_edges(MstScratch &S, const int32_t *eu, const int32_t *ev, const double *ed2, cudaStream_t s,
+                          int64_t m) {
+    if (m < 0) m = S.n - 1;
     k_nn_init<<<blocks_for(S.n), TPB, 0, ISO_S(s)>>>(S.nnbits, S.n);
     if (m > 0) k_nn_edges<<<blocks_for(m), TPB, 0, ISO_S(s)>>>(eu, ev, ed2, m, S.nnbits);
     return cudaGetLastError();

@@ -7,7 +7,10 @@
 
 namespace iso {
 
-enum : int { MC_OVERFLOW = 0, MC_NEDGES = 1, MC_NCOMP = 2, MC_ROUNDS = 3, MC_OVF_TOTAL = 4, MC_NCOMP_NEW = 5 };
+enum : int {
+    MC_OVERFLOW = 0, MC_NEDGES = 1, MC_NCOMP = 2, MC_ROUNDS = 3, MC_OVF_TOTAL = 4, MC_NCOMP_NEW = 5,
+    MC_TARGET = 6   // components at which the forest is complete: 1, or the number of independent sets
+};
 
 struct MstScratch {
     int64_t n = 0;
@@ -33,27 +36,40 @@ struct MstScratch {
 
 int mst_splits(int64_t n);
 
-// Tensor-core sweep state (mst_tc.cu): centred BF16 hi/lo copies of X padded
-// to the 128 x 64 tile grid, their TMA maps, squared norms and the best-8
-// candidate lists of every (column split, row).
+// Tensor-core sweep state (mst_tc.cu): centred BF16 hi/lo copies of X in a
+// padded row space of 128-row tiles, their TMA maps, squared norms and the
+// best-8 candidate lists of every (list, row).  One set: rows in norm order,
+// padding after the last point.  Independent sets: each set centred on its
+// own mean, in norm order inside its own run of whole tiles.
 struct TcScratch {
-    int64_t n_pad = 0;
+    int64_t n_pad = 0;                             // padded row space (whole 128-row tiles)
     int32_t d_pad = 0;
-    int splits = 1;
-    __nv_bfloat16 *xh = nullptr, *xl = nullptr;   // rows in norm order: row r is point perm[r]
-    float *nrm = nullptr, *rsq = nullptr;          // |y|^2 and |y| of the represented rows
+    int splits = 1;                                // column splits per row tile (one set)
+    int lists = 2;                                 // candidate lists per row (2 per split: tile halves)
+    __nv_bfloat16 *xh = nullptr, *xl = nullptr;   // row r is point permp[r] (zero rows at padding)
+    float *nrm = nullptr, *rsq = nullptr;          // |y|^2 and |y| of the represented rows (0 at padding)
+    float *cnrm = nullptr;                         // |y|^2 as a column: +inf at padding
     float *tmax = nullptr, *tsq = nullptr;         // per 128-row tile: max |y|^2 and its sqrt
-    float *mean = nullptr;
+    float *mean = nullptr;                         // [nmeans][d]
     double *part = nullptr;
     unsigned int *nmax_bits = nullptr;
-    int32_t *perm = nullptr, *iperm = nullptr, *vbuf = nullptr, *compp = nullptr;
+    int32_t *perm = nullptr, *permp = nullptr, *vbuf = nullptr, *compp = nullptr;
     uint64_t *keys = nullptr, *kbuf = nullptr;
-    float *tv = nullptr, *tu = nullptr;            // per (split, row): best-8 tile lower bounds, best upper bound
+    float *tv = nullptr, *tu = nullptr;            // per (list, row): best-8 half-tile lower bounds, best upper bound
     int32_t *tj = nullptr;
     uint32_t *err = nullptr;
+    // independent sets (null for one set): sweep work items {row tile,
+    // first and end column tile, split}, set of each point, set offsets
+    // and the first padded row of each set (device arrays)
+    const int4 *items = nullptr;
+    int64_t nitems = 0;
+    int32_t nsets = 1;
+    const int32_t *set_of = nullptr;
+    const int64_t *offs = nullptr;
+    const int64_t *rowbase = nullptr;
     CUtensorMap map_h, map_l;
-    void carve(Arena &A, int64_t n, int32_t d, int splits);
-    static size_t bytes_needed(int64_t n, int32_t d, int splits);
+    // n_pad_rows / nmeans / lists: 0 = one set
+    void carve(Arena &A, int64_t n, int32_t d, int splits, int64_t n_pad_rows = 0, int nmeans = 1, int lists = 0);
 };
 int tc_splits(int64_t n);
 bool tc_supported();
@@ -66,8 +82,12 @@ cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t 
 // sweep_fp64: use the exact FP64 sweep instead of FP32 + recheck.
 // rounds_out / rescans_out: host copies of the round and rescan counts are
 // written after the final stream synchronisation by the caller.
+// target: components left when the forest is complete (1 for one point set;
+// the number of sets when X holds independent sets, whose pairs the sweep
+// never mixes); max_n bounds the rounds (the largest set).
 cudaError_t mst_build(MstScratch &S, const void *X, int64_t n, int32_t d, int dtype, bool sweep_fp64,
-                      uint32_t *status, cudaStream_t s, TcScratch *tc = nullptr);
+                      uint32_t *status, cudaStream_t s, TcScratch *tc = nullptr, int32_t target = 1,
+                      int64_t max_n = 0);
 
 // Nearest-neighbour d2 of every row (exact key), one Boruvka-style sweep with
 // every point its own component.  Result in S.rowd2 / S.rowj.
@@ -79,7 +99,8 @@ cudaError_t mst_sort_edges(MstScratch &S, int32_t *out_u, int32_t *out_v, double
 
 // nnbits[v] = min d2 over MST edges incident to v (the exact nearest
 // neighbour, which is always a tree edge).
+// m: number of edges (default n - 1; a forest of independent sets has fewer).
 cudaError_t nn_from_edges(MstScratch &S, const int32_t *eu, const int32_t *ev, const double *ed2,
-                          cudaStream_t s);
+                          cudaStream_t s, int64_t m = -1);
 
 }  // namespace iso

@@ -164,7 +164,8 @@ __device__ __forceinline__ void top_insert(float (&v)[TC_TOPK], int32_t (&j)[TC_
 }
 
 __device__ __forceinline__ bool mst_active(const int32_t *counters) {
-    return *((volatile const int32_t *)(counters + MC_NCOMP)) > 1;
+    const volatile int32_t *c = counters;
+    return c[MC_NCOMP] > c[MC_TARGET];
 }
 
 // ARES: the row block's A tiles (hi, lo, every K chunk) stay resident in
@@ -174,9 +175,10 @@ __device__ __forceinline__ bool mst_active(const int32_t *counters) {
 template <bool ARES>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUtensorMap tml,
-           const float *__restrict__ rnorm, const float *__restrict__ rsq, const float *__restrict__ tmax,
-           const float *__restrict__ tsq, float acoef, float bcoef, const int32_t *__restrict__ comp, int64_t n,
-           int ntiles, int kchunks, int splits, const int32_t *counters, float *__restrict__ out_v,
+           const float *__restrict__ rnorm, const float *__restrict__ cnorm, const float *__restrict__ rsq,
+           const float *__restrict__ tmax, const float *__restrict__ tsq, float acoef, float bcoef,
+           const int32_t *__restrict__ comp, int64_t nrows, int ntiles, int kchunks, int splits,
+           const int4 *__restrict__ witems, int64_t nwitems, const int32_t *counters, float *__restrict__ out_v,
            int32_t *__restrict__ out_j, float *__restrict__ out_u, uint32_t *err) {
     if (!mst_active(counters)) return;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -211,8 +213,21 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
     tc_fence_after();
     const uint32_t tmem = sh->tmem_base;
 
-    const int64_t items = (int64_t)ntiles * splits;
+    // work item w: row tile rt against column tiles [c0, c1), candidate list
+    // pair sp; either from the item list or row tile x column split
+    const int64_t items = witems ? nwitems : (int64_t)ntiles * splits;
     const int tiles_per_split = (ntiles + splits - 1) / splits;
+    auto item = [&](int64_t w, int &rt, int &c0, int &c1, int &sp) {
+        if (witems) {
+            const int4 it = witems[w];
+            rt = it.x; c0 = it.y; c1 = it.z; sp = it.w;
+        } else {
+            rt = (int)(w / splits);
+            sp = (int)(w % splits);
+            c0 = sp * tiles_per_split;
+            c1 = min(ntiles, c0 + tiles_per_split);
+        }
+    };
 
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
@@ -220,8 +235,8 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
             uint32_t stage = 0, phase = 0, a_phase = 0;
             bool ok = true;
             for (int64_t w = blockIdx.x; w < items && ok; w += gridDim.x) {
-                const int rt = (int)(w / splits), sp = (int)(w % splits);
-                const int c0 = sp * tiles_per_split, c1 = min(ntiles, c0 + tiles_per_split);
+                int rt, c0, c1, sp;
+                item(w, rt, c0, c1, sp);
                 if (ARES) {
                     if (!(ok = mbar_wait(&sh->a_empty, a_phase ^ 1u, err))) break;
                     mbar_expect_tx(&sh->a_full, (uint32_t)(kchunks * 2 * TC_TILE_BYTES));
@@ -256,8 +271,9 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
             uint32_t stage = 0, phase = 0, acc = 0, acc_phase = 0, a_phase = 0;
             bool ok = true;
             for (int64_t w = blockIdx.x; w < items && ok; w += gridDim.x) {
-                const int sp = (int)(w % splits);
-                const int c0 = sp * tiles_per_split, c1 = min(ntiles, c0 + tiles_per_split);
+                int rt, c0, c1, sp;
+                item(w, rt, c0, c1, sp);
+                (void)rt;
                 if (ARES) {
                     if (!(ok = mbar_wait(&sh->a_full, a_phase, err))) break;
                     tc_fence_after();
@@ -313,12 +329,12 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
         uint32_t acc = 0, acc_phase = 0;
         bool ok = true;
         for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
-            const int rt = (int)(w / splits), sp = (int)(w % splits);
-            const int c0 = sp * tiles_per_split, c1 = min(ntiles, c0 + tiles_per_split);
-            const int64_t row = (int64_t)rt * TC_BM + trow;
-            const float nrow = row < n ? rnorm[row] : 0.0f;
-            const float srow = row < n ? rsq[row] : 0.0f;
-            const int32_t crow = row < n ? comp[row] : -3;
+            int rt, c0, c1, sp;
+            item(w, rt, c0, c1, sp);
+            const int64_t row = (int64_t)rt * TC_BM + trow;      // < nrows: whole tiles
+            const float nrow = rnorm[row];
+            const float srow = rsq[row];
+            const int32_t crow = comp[row];
             float ubest = INFINITY;        // smallest upper bound of a candidate's d2
             float bv[TC_TOPK];
             int32_t bj[TC_TOPK];
@@ -328,8 +344,9 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
             int64_t pcol = (int64_t)c0 * TC_BN + cm;
             float pn = INFINITY;
             int32_t pc = -2;
-            if (h == 0 && pcol < n) { pn = rnorm[pcol]; pc = comp[pcol]; }
-            float ptsq = __ldg(tsq + c0), ptmax = __ldg(tmax + c0);
+            if (h == 0 && c0 < c1) { pn = cnorm[pcol]; pc = comp[pcol]; }
+            float ptsq = 0.f, ptmax = 0.f;
+            if (c0 < c1) { ptsq = __ldg(tsq + c0); ptmax = __ldg(tmax + c0); }
             for (int ct = c0; ct < c1; ++ct) {
                 if (h == 0) {
                     sh->cnorm[acc][cm] = pn;
@@ -339,8 +356,8 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
                 if (ct + 1 < c1) {
                     pcol = (int64_t)(ct + 1) * TC_BN + cm;
                     if (h == 0) {
-                        pn = pcol < n ? rnorm[pcol] : INFINITY;
-                        pc = pcol < n ? comp[pcol] : -2;
+                        pn = cnorm[pcol];
+                        pc = comp[pcol];
                     }
                     ptsq = __ldg(tsq + ct + 1);
                     ptmax = __ldg(tmax + ct + 1);
@@ -395,11 +412,11 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
                 ubest = fminf(ubest, m + dlt);
                 if (lb < bv[TC_TOPK - 1]) top_insert(bv, bj, lb, 2 * ct + h);
             }
-            if (row < n) {
-                const size_t o = ((size_t)(2 * sp + h) * n + row) * TC_TOPK;
+            {
+                const size_t o = ((size_t)(2 * sp + h) * nrows + row) * TC_TOPK;
 #pragma unroll
                 for (int q = 0; q < TC_TOPK; ++q) { out_v[o + q] = bv[q]; out_j[o + q] = bj[q]; }
-                out_u[(size_t)(2 * sp + h) * n + row] = ubest;
+                out_u[(size_t)(2 * sp + h) * nrows + row] = ubest;
             }
         }
     }
@@ -411,8 +428,8 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
     }
 }
 
-// Centre, split into BF16 hi + lo (zero padding to the tile grid) and the
-// squared norms of the represented points.
+// Centre, split into BF16 hi + lo (zero rows at padding) and the squared
+// norms of the represented points.
 __global__ void k_tc_mean_partial(const float *__restrict__ X, int64_t n, int32_t d, int64_t rows_per,
                                   double *__restrict__ part) {
     const int t = threadIdx.x + blockIdx.y * blockDim.x;
@@ -432,33 +449,76 @@ __global__ void k_tc_mean_final(const double *__restrict__ part, int nparts, int
     mean[t] = (float)(s / (double)n);
 }
 
-__global__ void k_tc_prenorm_keys(const float *__restrict__ X, const float *__restrict__ mean, int64_t n,
-                                  int32_t d, uint64_t *__restrict__ keys, int32_t *__restrict__ vals) {
+// One block per set: the set's mean (any centre serves; it only shrinks the
+// represented magnitudes).  8 warps x 32 dimensions per pass.
+__global__ void __launch_bounds__(256) k_tc_set_mean(const float *__restrict__ X, const int64_t *__restrict__ offs,
+                                                     int32_t d, float *__restrict__ mean) {
+    __shared__ double acc[8][33];
+    const int b = blockIdx.x, lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int64_t r0 = offs[b], r1 = offs[b + 1];
+    for (int t0 = 0; t0 < d; t0 += 32) {
+        const int t = t0 + lane;
+        double s = 0.0;
+        if (t < d)
+            for (int64_t r = r0 + wp; r < r1; r += 8) s += (double)X[r * d + t];
+        acc[wp][lane] = s;
+        __syncthreads();
+        if (wp == 0 && t < d) {
+            double tot = 0.0;
+            for (int q = 0; q < 8; ++q) tot += acc[q][lane];
+            mean[(int64_t)b * d + t] = r1 > r0 ? (float)(tot / (double)(r1 - r0)) : 0.0f;
+        }
+        __syncthreads();
+    }
+}
+
+// Sort keys: norm order (one set), or (set, norm) for independent sets.
+__global__ void k_tc_prenorm_keys(const float *__restrict__ X, const float *__restrict__ mean,
+                                  const int32_t *__restrict__ set_of, int64_t n, int32_t d,
+                                  uint64_t *__restrict__ keys, int32_t *__restrict__ vals) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const int32_t b = set_of ? set_of[i] : 0;
+    const float *mu = mean + (int64_t)b * d;
     double s = 0.0;
     for (int t = 0; t < d; ++t) {
-        const double y = (double)__fsub_rn(X[i * d + t], mean[t]);
+        const double y = (double)__fsub_rn(X[i * d + t], mu[t]);
         s += y * y;
     }
-    keys[i] = ((uint64_t)__float_as_uint((float)s) << 32) | (uint64_t)i;   // non-negative: bits are monotone
+    const uint64_t nb = (uint64_t)__float_as_uint((float)s);     // non-negative: bits are monotone
+    keys[i] = set_of ? (((uint64_t)(uint32_t)b << 32) | nb) : ((nb << 32) | (uint64_t)i);
     vals[i] = (int32_t)i;
 }
 
-__global__ void k_tc_inverse(const int32_t *__restrict__ perm, int64_t n, int32_t *__restrict__ iperm) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < n) iperm[perm[r]] = (int32_t)r;
+// Padded row of sorted position q: q itself (one set), or the set's first
+// padded row plus the rank inside the set.
+__global__ void k_tc_place(const int32_t *__restrict__ perm, int64_t n, const int32_t *__restrict__ set_of,
+                           const int64_t *__restrict__ offs, const int64_t *__restrict__ rowbase,
+                           int32_t *__restrict__ permp) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int32_t i = perm[q];
+    int64_t r = q;
+    if (set_of) {
+        const int32_t b = set_of[i];
+        r = rowbase[b] + (q - offs[b]);
+    }
+    permp[r] = i;
 }
 
-// Rows in norm order: row r of the split copies is point perm[r].
 __global__ void k_tc_split(const float *__restrict__ X, const float *__restrict__ mean,
-                           const int32_t *__restrict__ perm, int64_t n, int32_t d, int64_t n_pad, int32_t d_pad,
-                           __nv_bfloat16 *__restrict__ xh, __nv_bfloat16 *__restrict__ xl) {
+                           const int32_t *__restrict__ set_of, const int32_t *__restrict__ permp, int32_t d,
+                           int64_t n_pad, int32_t d_pad, __nv_bfloat16 *__restrict__ xh,
+                           __nv_bfloat16 *__restrict__ xl) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n_pad * d_pad) return;
     const int64_t r = idx / d_pad, t = idx - r * d_pad;
+    const int32_t i = permp[r];
     float y = 0.0f;
-    if (r < n && t < d) y = __fsub_rn(X[(int64_t)perm[r] * d + t], mean[t]);
+    if (i >= 0 && t < d) {
+        const int64_t b = set_of ? set_of[i] : 0;
+        y = __fsub_rn(X[(int64_t)i * d + t], mean[b * d + t]);
+    }
     const __nv_bfloat16 h = __float2bfloat16_rn(y);
     const __nv_bfloat16 l = __float2bfloat16_rn(__fsub_rn(y, __bfloat162float(h)));
     xh[idx] = h;
@@ -466,7 +526,8 @@ __global__ void k_tc_split(const float *__restrict__ X, const float *__restrict_
 }
 
 __global__ void k_tc_norms(const __nv_bfloat16 *__restrict__ xh, const __nv_bfloat16 *__restrict__ xl,
-                           int64_t n_pad, int32_t d_pad, float *__restrict__ nrm, float *__restrict__ sq,
+                           const int32_t *__restrict__ permp, int64_t n_pad, int32_t d_pad,
+                           float *__restrict__ nrm, float *__restrict__ cnrm, float *__restrict__ sq,
                            unsigned int *__restrict__ nmax_bits) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_pad) return;
@@ -477,6 +538,7 @@ __global__ void k_tc_norms(const __nv_bfloat16 *__restrict__ xh, const __nv_bflo
     }
     const float f = (float)s;
     nrm[r] = f;
+    cnrm[r] = permp[r] >= 0 ? f : INFINITY;
     sq[r] = (float)sqrt(s);
     atomicMax(nmax_bits, __float_as_uint(f));
 }
@@ -492,14 +554,27 @@ __global__ void k_tc_tile_max(const float *__restrict__ nrm, int64_t n_pad, floa
     tsq[t] = sqrtf(m) * 1.0000002f;       // rounded up
 }
 
-__global__ void k_tc_gather_comp(const int32_t *__restrict__ comp, const int32_t *__restrict__ perm, int64_t n,
-                                 int32_t *__restrict__ compp, const int32_t *counters) {
+__global__ void k_tc_gather_comp(const int32_t *__restrict__ comp, const int32_t *__restrict__ permp,
+                                 int64_t n_pad, int32_t *__restrict__ compp, const int32_t *counters) {
     if (!mst_active(counters)) return;
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < n) compp[r] = comp[perm[r]];
+    if (r < n_pad) {
+        const int32_t i = permp[r];
+        compp[r] = i >= 0 ? comp[i] : -2;
+    }
 }
 
-// One warp per (norm-ordered) row r, the point i = perm[r].  The lists'
+__global__ void k_tc_fill_lists(float *__restrict__ tv, int32_t *__restrict__ tj, float *__restrict__ tu,
+                                int64_t nv, int64_t nu) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nv) {
+        tv[i] = INFINITY;
+        tj[i] = -1;
+    }
+    if (i < nu) tu[i] = INFINITY;
+}
+
+// One warp per padded row r, the point i = permp[r] (none at padding).  The lists'
 // (column split x tile half) best-8 half-tile lower bounds and their best
 // upper bound U are merged.
 // The epilogue's bounds hold for the BF16-represented points; the exact
@@ -529,6 +604,7 @@ __global__ void __launch_bounds__(256) k_recheck_tc(const float *__restrict__ X,
     const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (r >= n) return;
     const int64_t i = perm[r];
+    if (i < 0) return;                     // padding row
     // ---- merge: each lane holds up to 8 of the lists x 8 entries (lists <= 32);
     //      the best 8 are selected by 8 rounds of a warp arg-min
     constexpr int EPL = 8;
@@ -665,8 +741,10 @@ __global__ void __launch_bounds__(256) k_recheck_tc(const float *__restrict__ X,
 
 // Self-contained rescan of a queued row: FP32 direct differences give the
 // minimum m; every column within the FP32 error margin of m is keyed in FP64.
+// With independent sets only the row's own set is scanned.
 __global__ void __launch_bounds__(256) k_rescan_tc(const float *__restrict__ X, int64_t n, int32_t d,
                                                    const int32_t *__restrict__ comp, const int32_t *__restrict__ ovf,
+                                                   const int32_t *__restrict__ set_of, const int64_t *__restrict__ offs,
                                                    double mul, double add, double *__restrict__ rowd2,
                                                    int32_t *__restrict__ rowj, int32_t *counters) {
     if (!mst_active(counters)) return;
@@ -678,8 +756,9 @@ __global__ void __launch_bounds__(256) k_rescan_tc(const float *__restrict__ X, 
         const int64_t i = ovf[q];
         const int32_t ci = comp[i];
         const float *xi = X + i * d;
+        const int64_t j0 = set_of ? offs[set_of[i]] : 0, j1 = set_of ? offs[set_of[i] + 1] : n;
         float m = INFINITY;
-        for (int64_t j = threadIdx.x; j < n; j += 256) {
+        for (int64_t j = j0 + threadIdx.x; j < j1; j += 256) {
             if (comp[j] == ci) continue;
             float acc = 0.0f;
             for (int t = 0; t < d; ++t) {
@@ -697,7 +776,7 @@ __global__ void __launch_bounds__(256) k_rescan_tc(const float *__restrict__ X, 
         const double tau = (double)smin[0] * mul + add;
         double bd = INFINITY;
         int32_t bjj = -1;
-        for (int64_t j = threadIdx.x; j < n; j += 256) {
+        for (int64_t j = j0 + threadIdx.x; j < j1; j += 256) {
             if (comp[j] == ci) continue;
             float acc = 0.0f;
             for (int t = 0; t < d; ++t) {
@@ -763,36 +842,31 @@ cudaError_t make_map(CUtensorMap *m, const __nv_bfloat16 *base, int64_t n_pad, i
 }
 }  // namespace
 
-size_t TcScratch::bytes_needed(int64_t n, int32_t d, int splits) {
-    Arena A;
-    TcScratch t;
-    t.carve(A, n, d, splits);
-    return A.off;
-}
-
-void TcScratch::carve(Arena &A, int64_t n, int32_t d, int splits_) {
+void TcScratch::carve(Arena &A, int64_t n, int32_t d, int splits_, int64_t n_pad_rows, int nmeans, int lists_) {
     splits = splits_;
-    n_pad = ceil_div(n, TC_BM) * TC_BM;
+    lists = lists_ > 0 ? lists_ : 2 * splits;
+    n_pad = n_pad_rows > 0 ? n_pad_rows : ceil_div(n, TC_BM) * TC_BM;
     d_pad = (int32_t)(ceil_div(d, TC_BK) * TC_BK);
     const int64_t nt = n_pad / TC_BM;
     xh = A.take<__nv_bfloat16>((size_t)n_pad * d_pad, 1024);
     xl = A.take<__nv_bfloat16>((size_t)n_pad * d_pad, 1024);
     nrm = A.take<float>(n_pad);
+    cnrm = A.take<float>(n_pad);
     rsq = A.take<float>(n_pad);
     tmax = A.take<float>(nt);
     tsq = A.take<float>(nt);
-    mean = A.take<float>(d);
+    mean = A.take<float>((size_t)(nmeans > 0 ? nmeans : 1) * d);
     part = A.take<double>((size_t)64 * d);
     nmax_bits = A.take<unsigned int>(4);
     perm = A.take<int32_t>(n);
-    iperm = A.take<int32_t>(n);
+    permp = A.take<int32_t>(n_pad);
     vbuf = A.take<int32_t>(n);
     keys = A.take<uint64_t>(n);
     kbuf = A.take<uint64_t>(n);
-    compp = A.take<int32_t>(n);
-    tv = A.take<float>((size_t)2 * splits * n * TC_TOPK);      // lists = column split x tile half
-    tj = A.take<int32_t>((size_t)2 * splits * n * TC_TOPK);
-    tu = A.take<float>((size_t)2 * splits * n);
+    compp = A.take<int32_t>(n_pad);
+    tv = A.take<float>((size_t)lists * n_pad * TC_TOPK);
+    tj = A.take<int32_t>((size_t)lists * n_pad * TC_TOPK);
+    tu = A.take<float>((size_t)lists * n_pad);
     err = A.take<uint32_t>(4);
 }
 
@@ -817,21 +891,32 @@ bool tc_supported() {
 
 cudaError_t tc_prepare(TcScratch &T, const float *X, int64_t n, int32_t d, cudaStream_t s) {
     cudaError_t e;
-    const int64_t rows_per = ceil_div(n, 64);
-    dim3 gm(64, (unsigned)ceil_div(d, 128));
-    k_tc_mean_partial<<<gm, 128, 0, ISO_S(s)>>>(X, n, d, rows_per, T.part);
-    k_tc_mean_final<<<(unsigned)ceil_div(d, 128), 128, 0, ISO_S(s)>>>(T.part, 64, n, d, T.mean);
+    const bool sets = T.set_of != nullptr;
+    if (sets) {
+        k_tc_set_mean<<<(unsigned)T.nsets, 256, 0, ISO_S(s)>>>(X, T.offs, d, T.mean);
+    } else {
+        const int64_t rows_per = ceil_div(n, 64);
+        dim3 gm(64, (unsigned)ceil_div(d, 128));
+        k_tc_mean_partial<<<gm, 128, 0, ISO_S(s)>>>(X, n, d, rows_per, T.part);
+        k_tc_mean_final<<<(unsigned)ceil_div(d, 128), 128, 0, ISO_S(s)>>>(T.part, 64, n, d, T.mean);
+    }
     // norm order: tiles of points with similar |x - c| give tight tile bounds
-    k_tc_prenorm_keys<<<(unsigned)ceil_div(n, 256), 256, 0, ISO_S(s)>>>(X, T.mean, n, d, T.keys, T.perm);
+    k_tc_prenorm_keys<<<(unsigned)ceil_div(n, 256), 256, 0, ISO_S(s)>>>(X, T.mean, T.set_of, n, d, T.keys, T.perm);
     if ((e = sort_pairs_u64(T.keys, T.perm, T.kbuf, T.vbuf, n, s))) return e;
-    k_tc_inverse<<<(unsigned)ceil_div(n, 256), 256, 0, ISO_S(s)>>>(T.perm, n, T.iperm);
+    if ((e = cudaMemsetAsync(T.permp, 0xff, sizeof(int32_t) * T.n_pad, s))) return e;     // -1: padding
+    k_tc_place<<<(unsigned)ceil_div(n, 256), 256, 0, ISO_S(s)>>>(T.perm, n, T.set_of, T.offs, T.rowbase, T.permp);
     const int64_t tot = T.n_pad * T.d_pad;
-    k_tc_split<<<(unsigned)ceil_div(tot, 256), 256, 0, ISO_S(s)>>>(X, T.mean, T.perm, n, d, T.n_pad, T.d_pad, T.xh,
-                                                                  T.xl);
+    k_tc_split<<<(unsigned)ceil_div(tot, 256), 256, 0, ISO_S(s)>>>(X, T.mean, T.set_of, T.permp, d, T.n_pad, T.d_pad,
+                                                                  T.xh, T.xl);
     if ((e = cudaMemsetAsync(T.nmax_bits, 0, sizeof(unsigned int), s))) return e;
-    k_tc_norms<<<(unsigned)ceil_div(T.n_pad, 256), 256, 0, ISO_S(s)>>>(T.xh, T.xl, T.n_pad, T.d_pad, T.nrm, T.rsq,
-                                                                      T.nmax_bits);
+    k_tc_norms<<<(unsigned)ceil_div(T.n_pad, 256), 256, 0, ISO_S(s)>>>(T.xh, T.xl, T.permp, T.n_pad, T.d_pad, T.nrm,
+                                                                      T.cnrm, T.rsq, T.nmax_bits);
     k_tc_tile_max<<<(unsigned)ceil_div(T.n_pad / TC_BM, 128), 128, 0, ISO_S(s)>>>(T.nrm, T.n_pad, T.tmax, T.tsq);
+    if (sets) {
+        // lists that no item writes (sets with fewer splits) stay empty
+        const int64_t nv = (int64_t)T.lists * T.n_pad * TC_TOPK, nu = (int64_t)T.lists * T.n_pad;
+        k_tc_fill_lists<<<(unsigned)ceil_div(nv, 256), 256, 0, ISO_S(s)>>>(T.tv, T.tj, T.tu, nv, nu);
+    }
     if ((e = cudaMemsetAsync(T.err, 0, sizeof(uint32_t), s))) return e;
     if ((e = make_map(&T.map_h, T.xh, T.n_pad, T.d_pad))) return e;
     if ((e = make_map(&T.map_l, T.xl, T.n_pad, T.d_pad))) return e;
@@ -850,10 +935,11 @@ cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t 
                            cudaStream_t s) {
     const int ntiles = (int)(T.n_pad / TC_BM);
     const int kchunks = T.d_pad / TC_BK;
-    const int64_t items = (int64_t)ntiles * T.splits;
+    const int64_t items = T.items ? T.nitems : (int64_t)ntiles * T.splits;
     const int64_t nsm = (int64_t)num_sms();
-    const unsigned grid = (unsigned)(items < nsm ? items : nsm);
-    k_tc_gather_comp<<<(unsigned)ceil_div(n, 256), 256, 0, ISO_S(s)>>>(S.comp, T.perm, n, T.compp, S.counters);
+    const unsigned grid = (unsigned)(items < nsm ? (items > 0 ? items : 1) : nsm);
+    k_tc_gather_comp<<<(unsigned)ceil_div(T.n_pad, 256), 256, 0, ISO_S(s)>>>(S.comp, T.permp, T.n_pad, T.compp,
+                                                                            S.counters);
     // d2 = n_i + n_j - 2g against d2 of the represented points: tensor-core
     // FP32 accumulation of 3 d_pad products (worst case: one rounding of the
     // running magnitude per addition, 2^-23) and the dropped lo.lo term
@@ -865,23 +951,23 @@ cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t 
     const float bcoef = (float)(1.25 * 8.0 * 5.9604644775390625e-08);
     if (kchunks <= 2)
         k_sweep_tc<true><<<grid, TC_THREADS, TC_SMEM_ARES, ISO_S(s)>>>(
-            T.map_h, T.map_l, T.nrm, T.rsq, T.tmax, T.tsq, acoef, bcoef, T.compp, n, ntiles, kchunks, T.splits,
-            S.counters, T.tv, T.tj, T.tu, T.err);
+            T.map_h, T.map_l, T.nrm, T.cnrm, T.rsq, T.tmax, T.tsq, acoef, bcoef, T.compp, T.n_pad, ntiles, kchunks,
+            T.splits, T.items, T.nitems, S.counters, T.tv, T.tj, T.tu, T.err);
     else
         k_sweep_tc<false><<<grid, TC_THREADS, TC_SMEM_STREAM, ISO_S(s)>>>(
-            T.map_h, T.map_l, T.nrm, T.rsq, T.tmax, T.tsq, acoef, bcoef, T.compp, n, ntiles, kchunks, T.splits,
-            S.counters, T.tv, T.tj, T.tu, T.err);
+            T.map_h, T.map_l, T.nrm, T.cnrm, T.rsq, T.tmax, T.tsq, acoef, bcoef, T.compp, T.n_pad, ntiles, kchunks,
+            T.splits, T.items, T.nitems, S.counters, T.tv, T.tj, T.tu, T.err);
     // representation error of a centred point by BF16 hi + lo: 2^-18 relative
     // per element, plus the FP32 rounding of x - c (2^-24); 25 % headroom
     const double eps_rep = 1.25 * (3.814697265625e-06 + 5.9604644775390625e-08);
     const double e = 1.1 * (double)(d + 3) * 5.9604644775390625e-08;
-    k_recheck_tc<<<(unsigned)ceil_div(n * 32, 256), 256, 0, ISO_S(s)>>>(X, n, d, 2 * T.splits, T.tv, T.tj, T.tu, T.rsq,
-                                                                        T.perm, S.comp, T.nmax_bits, eps_rep, e,
-                                                                        S.rowd2, S.rowj, S.ovf_rows, S.counters);
+    k_recheck_tc<<<(unsigned)ceil_div(T.n_pad * 32, 256), 256, 0, ISO_S(s)>>>(
+        X, T.n_pad, d, T.lists, T.tv, T.tj, T.tu, T.rsq, T.permp, S.comp, T.nmax_bits, eps_rep, e, S.rowd2, S.rowj,
+        S.ovf_rows, S.counters);
     const double mul = (1.0 + e) / (1.0 - e);
     const double add = (double)(d + 1) * 1.401298464324817e-45 * 4.0;
-    k_rescan_tc<<<(unsigned)(num_sms() * 4), 256, 0, ISO_S(s)>>>(X, n, d, S.comp, S.ovf_rows, mul, add, S.rowd2, S.rowj,
-                                                                 S.counters);
+    k_rescan_tc<<<(unsigned)(num_sms() * 4), 256, 0, ISO_S(s)>>>(X, n, d, S.comp, S.ovf_rows, T.set_of, T.offs, mul,
+                                                                 add, S.rowd2, S.rowj, S.counters);
     (void)status;
     return cudaGetLastError();
 }

@@ -330,6 +330,45 @@ __global__ void k_nonroot_flags(const int32_t *__restrict__ parent, int64_t n, i
     if (v < n) flag[v] = parent[v] >= 0 ? 1 : 0;
 }
 
+// Section 2.2 step 4: alpha_0, beta_0 and the thresholds of the first
+// (bracketing) pass: 0, alpha_0, beta_0, beta_0 x 2^(2^j), DBL_MAX and 18
+// points between alpha_0 and beta_0 on the bit-pattern scale.
+__device__ void init_search(SearchState *S, double phs, double phm, double wsum, double wmin, double psum,
+                            double pmin) {
+    double alpha0 = (phm + pmin) / wsum;
+    double beta0 = (phs + psum) / wmin;
+    S->stats[0] = phs; S->stats[1] = phm; S->stats[2] = wsum; S->stats[3] = wmin;
+    S->stats[4] = psum; S->stats[5] = pmin; S->stats[6] = alpha0; S->stats[7] = beta0;
+    S->have_lo = 0; S->have_hi = 0; S->done = 0; S->error = 0; S->passes = 0;
+    S->selected = 0; S->ik_bits = 0ull; S->beta = 0.0;
+    const double DMAX = 1.7976931348623157e308;
+    double b0 = (isfinite(beta0) && beta0 > 0.0) ? beta0 : 1.0;
+    double a0 = (isfinite(alpha0) && alpha0 > 0.0) ? alpha0 : 0.0;
+    double t[DP_LANES];
+    t[0] = 0.0;
+    t[1] = a0;
+    t[2] = b0;
+    double f = b0;
+    const double mult[10] = {2.0, 2.0, 4.0, 16.0, 256.0, 65536.0, 4294967296.0, 1.8446744073709552e19,
+                             3.402823669209385e38, 1.157920892373162e77};
+    for (int q = 0; q < 10; ++q) {   // b0*2, *4, *16, *256, *2^16, ..., *2^512
+        f = f * mult[q];
+        t[3 + q] = isfinite(f) ? f : DMAX;
+    }
+    t[13] = DMAX;
+    unsigned long long lb = dbits(a0), hb = dbits(b0);
+    if (hb < lb) hb = lb;
+    unsigned long long g = hb - lb;
+    for (int q = 14; q < DP_LANES; ++q) {
+        unsigned long long s = (unsigned long long)(q - 13);
+        t[q] = bitsd(lb + (g / 19ull) * s + ((g % 19ull) * s) / 19ull);
+    }
+    for (int q = 0; q < DP_LANES; ++q) {
+        S->thr[q] = t[q];
+        S->cnt[q] = 0;
+    }
+}
+
 // ------------------------------------------------------------ stats + search
 // Section 2.2 step 4 / Section 3.5: phi*, phi_* over tree edges, omega*,
 // omega_*, p*, p_* over the vertices; fixed reduction order (deterministic).
@@ -375,39 +414,65 @@ __global__ void __launch_bounds__(1024) k_stats(const int32_t *__restrict__ pare
     if (tid == 0) {
         double phs = sh[0][0], phm = n > 1 ? sh[1][0] : 0.0;
         double wsum = sh[2][0], wmin = sh[3][0], psum = sh[4][0], pmin = sh[5][0];
-        double alpha0 = (phm + pmin) / wsum;
-        double beta0 = (phs + psum) / wmin;
-        S->stats[0] = phs; S->stats[1] = phm; S->stats[2] = wsum; S->stats[3] = wmin;
-        S->stats[4] = psum; S->stats[5] = pmin; S->stats[6] = alpha0; S->stats[7] = beta0;
-        S->have_lo = 0; S->have_hi = 0; S->done = 0; S->error = 0; S->passes = 0;
-        S->selected = 0; S->ik_bits = 0ull; S->beta = 0.0;
-        const double DMAX = 1.7976931348623157e308;
-        double b0 = (isfinite(beta0) && beta0 > 0.0) ? beta0 : 1.0;
-        double a0 = (isfinite(alpha0) && alpha0 > 0.0) ? alpha0 : 0.0;
-        double t[DP_LANES];
-        t[0] = 0.0;
-        t[1] = a0;
-        t[2] = b0;
-        double f = b0;
-        const double mult[10] = {2.0, 2.0, 4.0, 16.0, 256.0, 65536.0, 4294967296.0, 1.8446744073709552e19,
-                                 3.402823669209385e38, 1.157920892373162e77};
-        for (int q = 0; q < 10; ++q) {   // b0*2, *4, *16, *256, *2^16, ..., *2^512
-            f = f * mult[q];
-            t[3 + q] = isfinite(f) ? f : DMAX;
-        }
-        t[13] = DMAX;
-        unsigned long long lb = dbits(a0), hb = dbits(b0);
-        if (hb < lb) hb = lb;
-        unsigned long long g = hb - lb;
-        for (int q = 14; q < DP_LANES; ++q) {
-            unsigned long long s = (unsigned long long)(q - 13);
-            t[q] = bitsd(lb + (g / 19ull) * s + ((g % 19ull) * s) / 19ull);
-        }
-        for (int q = 0; q < DP_LANES; ++q) {
-            S->thr[q] = t[q];
-            S->cnt[q] = 0;
+        init_search(S, phs, phm, wsum, wmin, psum, pmin);
+    }
+}
+
+// Independent sets: one block per set b (vertices offs[b] .. offs[b+1]-1),
+// the same statistics in a fixed reduction order.
+__global__ void __launch_bounds__(256) k_stats_sets(const int32_t *__restrict__ parent, const double *__restrict__ phi,
+                                                    const double *__restrict__ omega, const double *__restrict__ p,
+                                                    const int64_t *__restrict__ offs, SearchState *SS, uint32_t *st) {
+    __shared__ double sh[6][256];
+    const int tid = threadIdx.x, b = blockIdx.x;
+    const int64_t v0 = offs[b], v1 = offs[b + 1];
+    double fs = 0.0, fm = INFINITY, ws = 0.0, wm = INFINITY, ps = 0.0, pm = INFINITY;
+    uint32_t bad = 0;
+    for (int64_t v = v0 + tid; v < v1; v += 256) {
+        double w = omega[v];
+        if (!(w > 0.0) || isinf(w)) bad |= (isnan(w) || isinf(w)) ? DEV_NONFINITE : DEV_NEGATIVE;
+        ws = ws + w;
+        wm = fmin(wm, w);
+        double pv = p ? p[v] : 0.0;
+        if (!(pv >= 0.0) || isinf(pv)) bad |= (isnan(pv) || isinf(pv)) ? DEV_NONFINITE : DEV_NEGATIVE;
+        ps = ps + pv;
+        pm = fmin(pm, pv);
+        if (parent[v] >= 0) {
+            double f = phi[v];
+            if (!(f >= 0.0) || isinf(f)) bad |= (isnan(f) || isinf(f)) ? DEV_NONFINITE : DEV_NEGATIVE;
+            fs = fs + f;
+            fm = fmin(fm, f);
         }
     }
+    if (bad) flag_status(st, bad);
+    sh[0][tid] = fs; sh[1][tid] = fm; sh[2][tid] = ws; sh[3][tid] = wm; sh[4][tid] = ps; sh[5][tid] = pm;
+    __syncthreads();
+    for (int q = 128; q > 0; q >>= 1) {
+        if (tid < q) {
+            sh[0][tid] = sh[0][tid] + sh[0][tid + q];
+            sh[1][tid] = fmin(sh[1][tid], sh[1][tid + q]);
+            sh[2][tid] = sh[2][tid] + sh[2][tid + q];
+            sh[3][tid] = fmin(sh[3][tid], sh[3][tid + q]);
+            sh[4][tid] = sh[4][tid] + sh[4][tid + q];
+            sh[5][tid] = fmin(sh[5][tid], sh[5][tid + q]);
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const double phm = v1 - v0 > 1 ? sh[1][0] : 0.0;
+        init_search(SS + b, sh[0][0], phm, sh[2][0], sh[3][0], sh[4][0], sh[5][0]);
+    }
+}
+
+// The forest of independent sets is oriented as one tree under a virtual
+// root; afterwards every set's own root (its first point) becomes a root.
+__global__ void k_fix_roots(const int64_t *__restrict__ offs, int32_t nsets, int32_t *__restrict__ parent,
+                            int32_t *__restrict__ edge_of) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nsets) return;
+    const int64_t r = offs[b];
+    parent[r] = -1;
+    edge_of[r] = -1;
 }
 
 // Algorithm 1 for 32 thresholds: one lane per threshold, one warp per walk.
@@ -416,6 +481,60 @@ struct DpArgs {
     const int32_t *parent, *ch_off, *ch_list, *leaves;
     const double *phi, *omega, *p;
 };
+
+// One warp walks from leaf v towards the root, deciding each vertex for the
+// 32 thresholds of its lanes; returns this lane's cuts.
+__device__ __forceinline__ int dp_walk(const DpArgs &A, int32_t v, double N, int lane, int final_pass,
+                                       uint8_t *__restrict__ dec, double *__restrict__ wh, double *__restrict__ ph,
+                                       int32_t *__restrict__ done, double *__restrict__ rat) {
+    int cuts = 0;
+    while (true) {
+        double w = A.omega[v];
+        double pv = A.p ? A.p[v] : 0.0;
+        const int32_t c0 = A.ch_off[v], c1 = A.ch_off[v + 1];
+        for (int32_t q = c1 - 1; q >= c0; --q) {   // siblings in descending index
+            const int32_t c = A.ch_list[q];
+            const size_t cl = (size_t)c * DP_LANES + lane;
+            const uint8_t dc = ld_cg_u8(dec + cl);
+            if (dc == DEC_JOIN) {
+                w = __dadd_rn(w, ld_cg_f64(wh + cl));
+                pv = __dadd_rn(pv, ld_cg_f64(ph + cl));
+            } else {
+                pv = __dadd_rn(pv, A.phi[c]);       // cut or discarded child: boundary edge
+            }
+        }
+        const int32_t u = A.parent[v];
+        const double fe = u >= 0 ? A.phi[v] : 0.0;
+        const double nw = __dmul_rn(N, w);
+        const double fp = __dadd_rn(fe, pv);
+        uint8_t d;
+        if (fp <= nw) {
+            d = DEC_CUT;
+            ++cuts;
+            if (final_pass && lane == 0) rat[v] = __ddiv_rn(fp, w);
+        } else if (u >= 0 && __dsub_rn(pv, fe) < nw) {
+            d = DEC_JOIN;
+        } else {
+            d = DEC_DISCARD;
+        }
+        const size_t vl = (size_t)v * DP_LANES + lane;
+        dec[vl] = d;
+        wh[vl] = w;
+        ph[vl] = pv;
+        if (u < 0) break;
+        const int32_t nu = A.ch_off[u + 1] - A.ch_off[u];
+        if (nu == 1) { v = u; continue; }          // only child: no one to wait for
+        __threadfence();
+        __syncwarp();
+        int old = 0;
+        if (lane == 0) old = atomicAdd(done + u, 1);
+        old = __shfl_sync(0xffffffffu, old, 0);
+        if (old != nu - 1) break;                  // a sibling is still running
+        __threadfence();
+        v = u;
+    }
+    return cuts;
+}
 
 __global__ void __launch_bounds__(256) k_dp_pass(DpArgs A, SearchState *S, uint8_t *__restrict__ dec,
                                                  double *__restrict__ wh, double *__restrict__ ph,
@@ -428,59 +547,45 @@ __global__ void __launch_bounds__(256) k_dp_pass(DpArgs A, SearchState *S, uint8
     const double N = final_pass ? S->beta : S->thr[lane];
     const int nleaves = S->nleaves;
     int cuts = 0;
-    for (int64_t li = warp; li < nleaves; li += nwarps) {
-        int32_t v = A.leaves[li];
-        while (true) {
-            double w = A.omega[v];
-            double pv = A.p ? A.p[v] : 0.0;
-            const int32_t c0 = A.ch_off[v], c1 = A.ch_off[v + 1];
-            for (int32_t q = c1 - 1; q >= c0; --q) {   // siblings in descending index
-                const int32_t c = A.ch_list[q];
-                const size_t cl = (size_t)c * DP_LANES + lane;
-                const uint8_t dc = ld_cg_u8(dec + cl);
-                if (dc == DEC_JOIN) {
-                    w = __dadd_rn(w, ld_cg_f64(wh + cl));
-                    pv = __dadd_rn(pv, ld_cg_f64(ph + cl));
-                } else {
-                    pv = __dadd_rn(pv, A.phi[c]);       // cut or discarded child: boundary edge
-                }
-            }
-            const int32_t u = A.parent[v];
-            const double fe = u >= 0 ? A.phi[v] : 0.0;
-            const double nw = __dmul_rn(N, w);
-            const double fp = __dadd_rn(fe, pv);
-            uint8_t d;
-            if (fp <= nw) {
-                d = DEC_CUT;
-                ++cuts;
-                if (final_pass && lane == 0) rat[v] = __ddiv_rn(fp, w);
-            } else if (u >= 0 && __dsub_rn(pv, fe) < nw) {
-                d = DEC_JOIN;
-            } else {
-                d = DEC_DISCARD;
-            }
-            const size_t vl = (size_t)v * DP_LANES + lane;
-            dec[vl] = d;
-            wh[vl] = w;
-            ph[vl] = pv;
-            if (u < 0) break;
-            const int32_t nu = A.ch_off[u + 1] - A.ch_off[u];
-            if (nu == 1) { v = u; continue; }          // only child: no one to wait for
-            __threadfence();
-            __syncwarp();
-            int old = 0;
-            if (lane == 0) old = atomicAdd(done + u, 1);
-            old = __shfl_sync(0xffffffffu, old, 0);
-            if (old != nu - 1) break;                  // a sibling is still running
-            __threadfence();
-            v = u;
-        }
-    }
+    for (int64_t li = warp; li < nleaves; li += nwarps)
+        cuts += dp_walk(A, A.leaves[li], N, lane, final_pass, dec, wh, ph, done, rat);
     if (cuts) atomicAdd(&S->cnt[lane], cuts);
 }
 
-__global__ void k_search_update(SearchState *S, int32_t k, int last, uint32_t *st) {
-    if (threadIdx.x != 0 || S->done) return;
+// Independent sets (a forest whose trees are the sets): each set has its own
+// search state and thresholds.  A warp takes a contiguous run of leaves, so
+// its cut counts change set rarely and are flushed at each change.
+__global__ void __launch_bounds__(256) k_dp_pass_sets(DpArgs A, const SearchState *G, SearchState *SS,
+                                                      const int32_t *__restrict__ vset, uint8_t *__restrict__ dec,
+                                                      double *__restrict__ wh, double *__restrict__ ph,
+                                                      int32_t *__restrict__ done, double *__restrict__ rat,
+                                                      int final_pass) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nleaves = G->nleaves;
+    const int64_t chunk = (nleaves + nwarps - 1) / nwarps;
+    const int64_t l0 = warp * chunk, l1 = min(nleaves, l0 + chunk);
+    int32_t cur = -1;
+    int cuts = 0;
+    for (int64_t li = l0; li < l1; ++li) {
+        const int32_t v = A.leaves[li];
+        const int32_t b = vset[v];
+        if (b != cur) {
+            if (cuts) atomicAdd(&SS[cur].cnt[lane], cuts);
+            cuts = 0;
+            cur = b;
+        }
+        const SearchState *S = SS + b;
+        if (!final_pass && S->done) continue;
+        const double N = final_pass ? S->beta : S->thr[lane];
+        cuts += dp_walk(A, v, N, lane, final_pass, dec, wh, ph, done, rat);
+    }
+    if (cuts) atomicAdd(&SS[cur].cnt[lane], cuts);
+}
+
+__device__ void search_update(SearchState *S, int32_t k, int last, uint32_t *st) {
+    if (S->done) return;
     const unsigned long long NONE = ~0ull;
     unsigned long long hi = S->have_hi ? S->hi_bits : NONE;
     for (int t = 0; t < DP_LANES; ++t)
@@ -523,6 +628,17 @@ __global__ void k_search_update(SearchState *S, int32_t k, int last, uint32_t *s
         unsigned long long s = (unsigned long long)t;
         S->thr[t - 1] = bitsd(lo + (g / 33ull) * s + ((g % 33ull) * s) / 33ull);
     }
+}
+
+__global__ void k_search_update(SearchState *S, int32_t k, int last, uint32_t *st) {
+    if (threadIdx.x == 0) search_update(S, k, last, st);
+}
+
+// independent sets: one thread per set
+__global__ void k_search_update_sets(SearchState *SS, const int32_t *__restrict__ ks, int32_t nsets, int last,
+                                     uint32_t *st) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nsets) search_update(SS + b, ks[b], last, st);
 }
 
 // ------------------------------------------------------------ labels
@@ -570,6 +686,54 @@ __global__ void k_finish(SearchState *S, int32_t k, double *i_k, uint32_t *st) {
     i_k[0] = bitsd(S->ik_bits);
 }
 
+// Independent sets: processing positions are set-major (sets in descending
+// order, the virtual root last), so set b's cuts are counted from position
+// nv - offs[b+1] (nv = number of real vertices).
+__global__ void k_labels_sets(const uint8_t *__restrict__ dec, const int32_t *__restrict__ bfs_pos,
+                              const int32_t *__restrict__ head, const int32_t *__restrict__ cidx,
+                              const double *__restrict__ rat, int64_t nv, const int32_t *__restrict__ vset,
+                              const int64_t *__restrict__ offs, const int32_t *__restrict__ ks,
+                              int32_t *__restrict__ labels, uint8_t *__restrict__ residual, SearchState *SS) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    const int32_t b = vset[v];
+    const int32_t base = cidx[nv - offs[b + 1]];
+    const int32_t k = ks[b];
+    const int32_t h = head[v];
+    const int32_t c = dec[(size_t)h * DP_LANES] == DEC_CUT ? cidx[nv - bfs_pos[h]] - base : -1;
+    const int32_t lab = (c >= 0 && c < k) ? c : -1;
+    labels[v] = lab;
+    residual[v] = lab < 0 ? 1 : 0;
+    if (dec[(size_t)v * DP_LANES] == DEC_CUT) {
+        const int32_t cv = cidx[nv - bfs_pos[v]] - base;
+        if (cv < k) {
+            atomicMax(&SS[b].ik_bits, dbits(rat[v]));
+            atomicAdd(&SS[b].selected, 1);
+        }
+    }
+}
+
+__global__ void k_finish_sets(SearchState *SS, const int32_t *__restrict__ ks, int32_t nsets, double *i_k,
+                              double *beta, uint32_t *st) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nsets) return;
+    const SearchState *S = SS + b;
+    if (S->error) return;
+    if (S->selected != ks[b]) flag_status(st, DEV_INTERNAL);
+    i_k[b] = bitsd(S->ik_bits);
+    if (beta) beta[b] = S->beta;
+}
+
+// BFS keys of independent sets: a stable second sort by set makes the order
+// set-major with (depth, preorder) inside each set; the virtual root first.
+__global__ void k_set_keys(const int32_t *__restrict__ ib, const int32_t *__restrict__ vset, int64_t n,
+                           int64_t nv, uint64_t *__restrict__ keys) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t v = ib[i];
+    keys[i] = v < nv ? (uint64_t)(vset[v] + 1) : 0ull;
+}
+
 __global__ void k_phi_from_edges(const int32_t *__restrict__ edge_of, const double *__restrict__ ed2,
                                  int64_t n, double sigma, double *__restrict__ phi) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -599,7 +763,7 @@ __global__ void k_omega_tree(const uint64_t *__restrict__ adj_key, const int32_t
 
 // ---------------------------------------------------------------- host side
 cudaError_t orient_tree(TreeScratch &S, const int32_t *eu, const int32_t *ev, int64_t n, int32_t root,
-                        const int32_t *expect_parent, cudaStream_t s) {
+                        const int32_t *expect_parent, cudaStream_t s, const int32_t *vset) {
     TreeDev &T = S.T;
     T.n = n;
     T.root = root;
@@ -666,6 +830,11 @@ cudaError_t orient_tree(TreeScratch &S, const int32_t *eu, const int32_t *ev, in
     T.pre = pa;
     k_bfs_keys<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(T.depth, pa, n, S.bkeys, S.ib);
     if ((e = sort_pairs_u64(S.bkeys, S.ib, S.kbuf, S.vbuf, n, s))) return e;
+    if (vset) {
+        // independent sets under a virtual root (vertex n - 1): set-major order
+        k_set_keys<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.ib, vset, n, n - 1, S.bkeys);
+        if ((e = sort_pairs_u64(S.bkeys, S.ib, S.kbuf, S.vbuf, n, s))) return e;
+    }
     k_bfs_pos<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.ib, S.bkeys, n, T.bfs_pos, S.search);
     k_leaf_flags<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(T.ch_off, n, S.flag);
     if ((e = exclusive_scan_i32(S.flag, S.fpos, n, S.tmp32, s))) return e;
@@ -710,6 +879,46 @@ cudaError_t tree_search_and_label(TreeScratch &S, const double *phi_par, const d
     if ((e = exclusive_scan_i32(S.cflag, S.cidx, n, S.tmp32, s))) return e;
     k_labels<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.dec, T.bfs_pos, ha, S.cidx, S.rat, n, k, labels, residual, S.search);
     k_finish<<<1, 32, 0, ISO_S(s)>>>(S.search, k, i_k, S.status);
+    return cudaGetLastError();
+}
+
+cudaError_t tree_search_and_label_sets(TreeScratch &S, int32_t nsets, const int64_t *offs, const int32_t *vset,
+                                       const int32_t *ks, SearchState *SS, const double *phi_par, const double *omega,
+                                       const double *p, int32_t *labels, uint8_t *residual, double *i_k, double *beta,
+                                       cudaStream_t s) {
+    const TreeDev &T = S.T;
+    const int64_t n = T.n, nv = n - 1;      // vertex nv is the virtual root
+    cudaError_t e;
+    // the virtual root is never decided: mark it discarded (its own head)
+    if ((e = cudaMemsetAsync(S.dec + (size_t)nv * DP_LANES, DEC_DISCARD, DP_LANES, s))) return e;
+    k_stats_sets<<<(unsigned)nsets, 256, 0, ISO_S(s)>>>(T.parent, phi_par, omega, p, offs, SS, S.status);
+    DpArgs A{n, T.parent, T.ch_off, T.ch_list, T.leaves, phi_par, omega, p};
+    const unsigned grid = (unsigned)(num_sms() * 8);
+    const unsigned gs = (unsigned)ceil_div(nsets, 128);
+    for (int pass = 0; pass < DP_SEARCH_PASSES; ++pass) {
+        if ((e = cudaMemsetAsync(S.done, 0, sizeof(int32_t) * n, s))) return e;
+        k_dp_pass_sets<<<grid, 256, 0, ISO_S(s)>>>(A, S.search, SS, vset, S.dec, S.wh, S.ph, S.done, S.rat, 0);
+        k_search_update_sets<<<gs, 128, 0, ISO_S(s)>>>(SS, ks, nsets, pass == DP_SEARCH_PASSES - 1, S.status);
+    }
+    if ((e = cudaMemsetAsync(S.done, 0, sizeof(int32_t) * n, s))) return e;
+    k_dp_pass_sets<<<grid, 256, 0, ISO_S(s)>>>(A, S.search, SS, vset, S.dec, S.wh, S.ph, S.done, S.rat, 1);
+    k_head_init<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.dec, T.parent, n, S.head);
+    int32_t *ha = S.head, *hb = S.head2;
+    const int Ln = log2_ceil(n) + 1;
+    for (int it = 0; it < Ln; ++it) {
+        k_head_jump<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(ha, hb, n);
+        int32_t *t = ha; ha = hb; hb = t;
+    }
+    k_cut_flags<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.dec, T.bfs_pos, n, S.cflag);
+    if ((e = exclusive_scan_i32(S.cflag, S.cidx, n, S.tmp32, s))) return e;
+    k_labels_sets<<<blocks_for(nv), TPB, 0, ISO_S(s)>>>(S.dec, T.bfs_pos, ha, S.cidx, S.rat, nv, vset, offs, ks, labels,
+                                                        residual, SS);
+    k_finish_sets<<<gs, 128, 0, ISO_S(s)>>>(SS, ks, nsets, i_k, beta, S.status);
+    return cudaGetLastError();
+}
+
+cudaError_t fix_set_roots(TreeScratch &S, int32_t nsets, const int64_t *offs, cudaStream_t s) {
+    k_fix_roots<<<blocks_for(nsets), TPB, 0, ISO_S(s)>>>(offs, nsets, S.T.parent, S.T.edge_of);
     return cudaGetLastError();
 }
 

@@ -67,8 +67,11 @@ struct TreeScratch {
 // Flags DEV_BAD_TREE if the edges are not a spanning tree.  If
 // expect_parent != nullptr, also flags DEV_BAD_TREE when the orientation
 // differs from it.
+// vset != nullptr: the tree joins independent sets under a virtual root
+// (vertex n - 1, vset[v] = set of each real vertex v); the BFS order is then
+// set-major, (depth, preorder) inside each set.
 cudaError_t orient_tree(TreeScratch &S, const int32_t *eu, const int32_t *ev, int64_t n,
-                        int32_t root, const int32_t *expect_parent, cudaStream_t s);
+                        int32_t root, const int32_t *expect_parent, cudaStream_t s, const int32_t *vset = nullptr);
 
 // Edges (eu, ev) from a parent array (root entry skipped), written into
 // S.fpos/S.flag-sized buffers; returns the buffers through out pointers.
@@ -79,6 +82,19 @@ cudaError_t edges_from_parent(TreeScratch &S, const int32_t *parent, int64_t n, 
 cudaError_t tree_search_and_label(TreeScratch &S, const double *phi_par, const double *omega,
                                   const double *p, int32_t k, int32_t *labels, uint8_t *residual,
                                   double *i_k, cudaStream_t s);
+
+// After orient_tree with vset: every set's first point becomes a root
+// (parent -1, no parent edge).
+cudaError_t fix_set_roots(TreeScratch &S, int32_t nsets, const int64_t *offs, cudaStream_t s);
+
+// Independent sets on a tree oriented with vset (see orient_tree): each
+// set's own roots, statistics, search (state SS[b], k = ks[b]) and labels.
+// labels / residual cover the real vertices; i_k and beta (nullable) one
+// entry per set.
+cudaError_t tree_search_and_label_sets(TreeScratch &S, int32_t nsets, const int64_t *offs, const int32_t *vset,
+                                       const int32_t *ks, SearchState *SS, const double *phi_par, const double *omega,
+                                       const double *p, int32_t *labels, uint8_t *residual, double *i_k, double *beta,
+                                       cudaStream_t s);
 
 // phi of each oriented parent edge from the MST edge d2 (eq. phi).
 cudaError_t phi_from_edges(const TreeScratch &S, const double *edge_d2, double sigma, double *phi_par,

@@ -358,17 +358,21 @@ __device__ __forceinline__ void tri_item(int64_t w, int64_t T, int64_t &I, int64
 // double-word arithmetic; the pair's d2 serves both omega_i and omega_j.
 // Row partials (rows of I) and column partials (rows of J) go to fixed slots
 // of item w, so the final sums do not depend on scheduling.
+// Independent sets: the tile pairs come from a list (both tiles of one set)
+// and tile_valid[I] counts the real rows of tile I (padding follows them).
+template <bool SETS>
 __global__ void __launch_bounds__(TPB, 2)
 k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *__restrict__ shdw,
               float is_h, float is_l, ExpTable tabv, float zskip, float scr_shrink, int64_t T,
-              int64_t nitems, uint8_t *__restrict__ flags, float2 *__restrict__ rpart, float2 *__restrict__ cpart,
+              int64_t nitems, const int2 *__restrict__ witems, const int32_t *__restrict__ tile_valid,
+              uint8_t *__restrict__ flags, float2 *__restrict__ rpart, float2 *__restrict__ cpart,
               unsigned long long *__restrict__ tile_counts) {
     __shared__ __align__(16) float As[WDC][WPAD];
     __shared__ __align__(16) float Bs[WDC][WPAD];
     __shared__ float2 tab[64];
     __shared__ float2 mr[WT][17];
     __shared__ float2 mc[WT][17];
-    __shared__ int64_t sIJ[2];
+    __shared__ int64_t sIJ[4];
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     if (tid < 64) tab[tid] = tabv.t[tid];
@@ -376,17 +380,32 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
     for (int64_t w = blockIdx.x; w < nitems; w += gridDim.x) {
         ++screened;
         __syncthreads();                       // previous item's readers of sIJ are done
-        if (tid == 0) tri_item(w, T, sIJ[0], sIJ[1]);
+        if (tid == 0) {
+            if constexpr (SETS) {
+                const int2 it = witems[w];
+                sIJ[0] = it.x;
+                sIJ[1] = it.y;
+                sIJ[2] = tile_valid[it.x];
+                sIJ[3] = tile_valid[it.y];
+            } else {
+                tri_item(w, T, sIJ[0], sIJ[1]);
+            }
+        }
         __syncthreads();
         const int64_t I = sIJ[0], J = sIJ[1];
         const int64_t row0 = I * WT, col0 = J * WT;
         const bool diag = I == J;
+        // real rows of the two tiles (padding follows them): local row lr of
+        // tile I is real iff rok(lr)
+        const int nI = SETS ? (int)sIJ[2] : 0, nJ = SETS ? (int)sIJ[3] : 0;
+        auto rok = [&](int lr) { return SETS ? lr < nI : row0 + lr < n; };
+        auto cok = [&](int lc) { return SETS ? lc < nJ : col0 + lc < n; };
         float rs_h[4], rs_l[4], cs_h[4], cs_l[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int64_t rr = row0 + ty * 4 + q, cc = col0 + tx * 4 + q;
-            const float2 a = rr < n ? shdw[rr] : make_float2(0.f, 0.f);
-            const float2 b = cc < n ? shdw[cc] : make_float2(0.f, 0.f);
+            const int lr = ty * 4 + q, lc = tx * 4 + q;
+            const float2 a = rok(lr) ? shdw[row0 + lr] : make_float2(0.f, 0.f);
+            const float2 b = cok(lc) ? shdw[col0 + lc] : make_float2(0.f, 0.f);
             rs_h[q] = a.x; rs_l[q] = a.y;
             cs_h[q] = b.x; cs_l[q] = b.y;
         }
@@ -404,8 +423,8 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
                 int r = idx / WDC, t = idx % WDC;
                 int64_t gr = row0 + r, gc = col0 + r;
                 int gt = t0 + t;
-                As[t][r] = (gr < n && gt < d) ? X[gr * d + gt] : 0.0f;
-                Bs[t][r] = (gc < n && gt < d) ? X[gc * d + gt] : 0.0f;
+                As[t][r] = (rok(r) && gt < d) ? X[gr * d + gt] : 0.0f;
+                Bs[t][r] = (cok(r) && gt < d) ? X[gc * d + gt] : 0.0f;
             }
             __syncthreads();
             const int tl = min(WDC, d - t0);
@@ -426,11 +445,11 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
         int need = 0;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const int64_t gr = row0 + ty * 4 + i;
+            const int lr = ty * 4 + i;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const int64_t gc = col0 + tx * 4 + j;
-                if (gr >= n || gc >= n || gc == gr) continue;
+                const int lc = tx * 4 + j;
+                if (!rok(lr) || !cok(lc) || (diag && lc == lr)) continue;
                 const float y = __fmul_rn(__fsqrt_rn(__fmul_rn(A32[i][j], scr_shrink)), is_h);
                 if (!(y - rs_h[i] > zskip) || !(y - cs_h[j] > zskip)) need = 1;
             }
@@ -454,8 +473,8 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
                 int r = idx / WDC, t = idx % WDC;
                 int64_t gr = row0 + r, gc = col0 + r;
                 int gt = t0 + t;
-                As[t][r] = (gr < n && gt < d) ? X[gr * d + gt] : 0.0f;
-                Bs[t][r] = (gc < n && gt < d) ? X[gc * d + gt] : 0.0f;
+                As[t][r] = (rok(r) && gt < d) ? X[gr * d + gt] : 0.0f;
+                Bs[t][r] = (cok(r) && gt < d) ? X[gc * d + gt] : 0.0f;
             }
             __syncthreads();
             const int tl = min(WDC, d - t0);
@@ -484,11 +503,11 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
         float ch[4] = {0.f, 0.f, 0.f, 0.f}, cl[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const int64_t gr = row0 + ty * 4 + i;
+            const int lr = ty * 4 + i;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const int64_t gc = col0 + tx * 4 + j;
-                if (gr >= n || gc >= n || gc == gr) continue;
+                const int lc = tx * 4 + j;
+                if (!rok(lr) || !cok(lc) || (diag && lc == lr)) continue;
                 const float Sh = S[i][j], El = E[i][j];
                 const float r = __fsqrt_rn(Sh);
                 float dl = 0.0f;
@@ -565,6 +584,41 @@ __global__ void k_weights_reduce(const unsigned long long *__restrict__ nnbits, 
     omega[r] = w2;
 }
 
+// Independent sets: padded row r of tile I (set b = tile_set[I], tiles
+// [tile0[b], tile0[b] + ntl[b]), items from item0[b] in upper-triangle row
+// order); padding rows get 0.
+__global__ void k_weights_reduce_sets(const unsigned long long *__restrict__ nnbits, int64_t n_pad,
+                                      const int32_t *__restrict__ tile_valid, const int32_t *__restrict__ tile_set,
+                                      const int64_t *__restrict__ tile0, const int64_t *__restrict__ ntl,
+                                      const int64_t *__restrict__ item0, double inv_sigma, int include_self,
+                                      const uint8_t *__restrict__ flags, const float2 *__restrict__ rpart,
+                                      const float2 *__restrict__ cpart, double *__restrict__ omega) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_pad) return;
+    const int64_t I = r / WT, c = r - I * WT;
+    if (c >= tile_valid[I]) {
+        omega[r] = 0.0;
+        return;
+    }
+    const int32_t b = tile_set[I];
+    const int64_t T = ntl[b], base = item0[b], Il = I - tile0[b];
+    float h = 0.f, l = 0.f;
+    for (int64_t Jl = 0; Jl < T; ++Jl) {
+        if (Jl < Il) {
+            const int64_t w = base + Jl * T - Jl * (Jl - 1) / 2 + (Il - Jl);    // item (J, I): r is a column
+            if (flags[w]) dw_add(h, l, cpart[w * WT + c].x, cpart[w * WT + c].y);
+        } else {
+            const int64_t w = base + Il * T - Il * (Il - 1) / 2 + (Jl - Il);    // item (I, J): r is a row
+            if (flags[w]) dw_add(h, l, rpart[w * WT + c].x, rpart[w * WT + c].y);
+        }
+    }
+    float fh, fl;
+    split_shift(nnbits, r, n_pad, inv_sigma, fh, fl);
+    double w2 = __dmul_rn(exp(-__dadd_rn((double)fh, (double)fl)), __dadd_rn((double)h, (double)l));
+    if (include_self) w2 = __dadd_rn(w2, 1.0);
+    omega[r] = w2;
+}
+
 // FP64 input: canonical FP64 terms, j ascending (the oracle's order).
 template <class T>
 __global__ void __launch_bounds__(TPB) k_weights_f64(const T *__restrict__ X, int64_t n, int32_t d, double sigma,
@@ -615,10 +669,44 @@ cudaError_t weights_launch_sym(const float *X, int64_t n, int32_t d, double sigm
     uint8_t *flags = (uint8_t *)(shdw + n);
     const unsigned grid = (unsigned)(num_sms() * 2);
     k_shift_dw<<<(unsigned)ceil_div(n, 256), 256, 0, ISO_S(s)>>>(nnbits, n, is, shdw);
-    k_weights_sym<<<grid, TPB, 0, ISO_S(s)>>>(X, n, d, shdw, is_h, is_l, tab, zskip, shrink, T, items, flags, rpart,
-                                              cpart, tile_counts);
+    k_weights_sym<false><<<grid, TPB, 0, ISO_S(s)>>>(X, n, d, shdw, is_h, is_l, tab, zskip, shrink, T, items, nullptr,
+                                                     nullptr, flags, rpart, cpart, tile_counts);
     k_weights_reduce<<<(unsigned)ceil_div(n, 256), 256, 0, ISO_S(s)>>>(nnbits, n, T, is, include_self, flags, rpart,
                                                                       cpart, omega);
+    return cudaGetLastError();
+}
+
+size_t weights_sym_sets_bytes(int64_t n_pad, int64_t nitems) {
+    return (size_t)nitems * (1 + 2 * WT * sizeof(float2)) + (size_t)n_pad * sizeof(float2) + 4096;
+}
+
+// Symmetric screened omega over independent sets.  Xp / nnbits / omega are
+// in the padded row space (n_pad rows, sets in whole 64-row tiles); the
+// items are the upper triangles of the sets' tile grids; max_n is the
+// largest set (it bounds the number of terms per row).
+cudaError_t weights_launch_sym_sets(const float *Xp, int64_t n_pad, int32_t d, double sigma, int include_self,
+                                    const unsigned long long *nnbits, double *omega, void *part, const int2 *witems,
+                                    int64_t nitems, const int32_t *tile_valid, const int32_t *tile_set,
+                                    const int64_t *tile0, const int64_t *ntl, const int64_t *item0, int64_t max_n,
+                                    unsigned long long *tile_counts, cudaStream_t s) {
+    static const ExpTable tab = make_exp_table();
+    const double is = 1.0 / sigma;
+    const float is_h = (float)is;
+    const float is_l = (float)(is - (double)is_h);
+    const float zskip = (float)(39.0 + log((double)(max_n > 2 ? max_n : 2)));
+    const double e = 1.1 * (double)(d + 3) * 5.9604644775390625e-08;
+    const float shrink = (float)((1.0 - e) * (1.0 - 1e-6));
+    float2 *rpart = (float2 *)part;
+    float2 *cpart = rpart + nitems * WT;
+    float2 *shdw = cpart + nitems * WT;
+    uint8_t *flags = (uint8_t *)(shdw + n_pad);
+    const unsigned grid = (unsigned)(num_sms() * 2);
+    k_shift_dw<<<(unsigned)ceil_div(n_pad, 256), 256, 0, ISO_S(s)>>>(nnbits, n_pad, is, shdw);
+    if (nitems > 0)
+        k_weights_sym<true><<<grid, TPB, 0, ISO_S(s)>>>(Xp, n_pad, d, shdw, is_h, is_l, tab, zskip, shrink, 0, nitems,
+                                                        witems, tile_valid, flags, rpart, cpart, tile_counts);
+    k_weights_reduce_sets<<<(unsigned)ceil_div(n_pad, 256), 256, 0, ISO_S(s)>>>(
+        nnbits, n_pad, tile_valid, tile_set, tile0, ntl, item0, is, include_self, flags, rpart, cpart, omega);
     return cudaGetLastError();
 }
 

@@ -80,6 +80,11 @@ def load(build_if_missing: bool = True):
         lib.isoclust_cluster_detail.restype = ctypes.c_int
         lib.isoclust_cluster_detail.argtypes = [_P, _I64, _I32, _I32, _I32, _D, _P, _P, _P, _P,
                                                 _P, _P, _P, _P, _P, _P, _P, _P, _P]
+        lib.isoclust_cluster_batched.restype = ctypes.c_int
+        lib.isoclust_cluster_batched.argtypes = [_P, _P, _I32, _I32, _I32, _P, _D, _P, _P, _P, _P, _P, _P]
+        lib.isoclust_cluster_batched_detail.restype = ctypes.c_int
+        lib.isoclust_cluster_batched_detail.argtypes = [_P, _P, _I32, _I32, _I32, _P, _D, _P, _P, _P, _P, _P,
+                                                        _P, _P, _P, _P]
         lib.isoclust_last_profile.restype = None
         lib.isoclust_last_profile.argtypes = [_P, _P]
         lib.isoclust_last_omega_tiles.restype = None
@@ -211,6 +216,69 @@ def cluster_detail(X: torch.Tensor, k: int, sigma: float, o: Opts | None = None)
         xp, n, d, dt, int(k), float(sigma), _opts_ptr(o),
         *[out[key].data_ptr() for key in ("labels", "residual", "i_k", "parent", "phi_par", "omega", "p", "beta",
                                           "edge_u", "edge_v", "edge_d2")], _stream(dev)))
+    return out
+
+
+class BatchPlan:
+    """Host arrays of a batch (offsets, ks) marshalled once for repeated calls."""
+
+    def __init__(self, offsets, ks):
+        self.nsets = len(offsets) - 1
+        if len(ks) != self.nsets:
+            raise ValueError("ks must have one entry per set")
+        self.n = int(offsets[-1])
+        self.offsets = (ctypes.c_int64 * len(offsets))(*[int(v) for v in offsets])
+        self.ks = (ctypes.c_int32 * max(self.nsets, 1))(*[int(v) for v in ks])
+
+
+def cluster_batched_into(X: torch.Tensor, plan: BatchPlan, sigma: float, labels, residual, ik, beta=None,
+                         o: Opts | None = None):
+    """cluster_batched() writing into caller-provided device tensors."""
+    lib = load()
+    xp, n, d, dt = _points(X)
+    if n != plan.n:
+        raise ValueError("X rows differ from the plan's offsets[-1]")
+    _check(lib.isoclust_cluster_batched(xp, plan.offsets, plan.nsets, d, dt, plan.ks, float(sigma), _opts_ptr(o),
+                                        labels.data_ptr(), residual.data_ptr(), ik.data_ptr(),
+                                        beta.data_ptr() if beta is not None else None, _stream(X.device)))
+
+
+def cluster_batched(X: torch.Tensor, offsets, ks, sigma: float, o: Opts | None = None,
+                    detail: bool = False) -> dict:
+    """Independent point sets in one call (isoclust_cluster_batched).
+
+    X: (N, d) float32 CUDA tensor holding the sets row-wise; offsets: N+1
+    host integers (set b = rows offsets[b] .. offsets[b+1]-1); ks: the k of
+    each set.  Returns labels [N], residual [N], i_k [nsets], beta [nsets]
+    (and parent, phi_par, omega [N] with detail=True) on X's device."""
+    lib = load()
+    xp, n, d, dt = _points(X)
+    off = (ctypes.c_int64 * len(offsets))(*[int(v) for v in offsets])
+    nsets = len(offsets) - 1
+    if len(ks) != nsets:
+        raise ValueError("ks must have one entry per set")
+    kk = (ctypes.c_int32 * max(nsets, 1))(*[int(v) for v in ks])
+    if nsets >= 1 and int(offsets[-1]) != n:
+        raise ValueError("offsets[-1] must equal X.shape[0]")
+    dev = X.device
+    out = dict(
+        labels=torch.empty(n, dtype=torch.int32, device=dev),
+        residual=torch.empty(n, dtype=torch.uint8, device=dev),
+        i_k=torch.empty(max(nsets, 1), dtype=torch.float64, device=dev),
+        beta=torch.empty(max(nsets, 1), dtype=torch.float64, device=dev),
+    )
+    if detail:
+        out.update(parent=torch.empty(n, dtype=torch.int32, device=dev),
+                   phi_par=torch.empty(n, dtype=torch.float64, device=dev),
+                   omega=torch.empty(n, dtype=torch.float64, device=dev))
+        _check(lib.isoclust_cluster_batched_detail(
+            xp, off, nsets, d, dt, kk, float(sigma), _opts_ptr(o),
+            *[out[key].data_ptr() for key in ("labels", "residual", "i_k", "beta", "parent", "phi_par", "omega")],
+            _stream(dev)))
+    else:
+        _check(lib.isoclust_cluster_batched(
+            xp, off, nsets, d, dt, kk, float(sigma), _opts_ptr(o),
+            *[out[key].data_ptr() for key in ("labels", "residual", "i_k", "beta")], _stream(dev)))
     return out
 
 

@@ -14,6 +14,9 @@ input carries no ordering by cluster.
                     1% density, 10 groups sharing support pools, rows
                     L2-normalised, FP32
   table1_shape      blobs at a (n, k, d) shape of the paper's Table 1
+  batched_sets      4,096 independent sets, sizes log-uniform in [64, 8192],
+                    d = 32, each 2-8 isotropic blobs (std 1, centres
+                    U[-10,10]^32, equal split), k = its blob count, FP32
 """
 from __future__ import annotations
 
@@ -150,15 +153,45 @@ def random_rooted_tree(seed: int, n: int, shape: str = "random", max_children: i
     return parent, phi, omega, p
 
 
+def batched_sets(seed: int = 0, nsets: int = 4096, n_lo: int = 64, n_hi: int = 8192, d: int = 32,
+                 blobs_lo: int = 2, blobs_hi: int = 8, std: float = 1.0, dtype=np.float32, sizes=None):
+    """Independent point sets concatenated row-wise.
+
+    Returns (X, offsets, ks): set b is X[offsets[b]:offsets[b+1]] with
+    k = ks[b] equal to its number of blobs (at most its size).  Sizes are
+    floor(exp(U[ln n_lo, ln n_hi])) unless given; blob sizes split each set
+    as equally as possible."""
+    rng = np.random.default_rng(seed)
+    if sizes is None:
+        sizes = np.floor(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi), size=nsets))).astype(np.int64)
+        sizes = np.clip(sizes, n_lo, n_hi)
+    else:
+        sizes = np.asarray(sizes, dtype=np.int64)
+        nsets = sizes.size
+    ks = rng.integers(blobs_lo, blobs_hi + 1, size=nsets).astype(np.int32)
+    ks = np.minimum(ks, sizes).astype(np.int32)
+    parts = []
+    for b in range(nsets):
+        kb = int(ks[b])
+        centres = rng.uniform(-10.0, 10.0, size=(kb, d))
+        split = _largest_remainder(np.ones(kb), int(sizes[b]))
+        Xb = np.concatenate([c + std * rng.standard_normal((int(m), d)) for c, m in zip(centres, split)])
+        parts.append(Xb[rng.permutation(Xb.shape[0])])
+    offsets = np.zeros(nsets + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum(sizes)
+    return np.ascontiguousarray(np.concatenate(parts).astype(dtype)), offsets, ks
+
+
 CONFIGS = {
     "blobs_n2000_d8": dict(gen="blobs_isotropic", n=2000, d=8, k=5, sigma=1.0, dtype="f64"),
     "blobs_n100k_d64": dict(gen="blobs_anisotropic", n=100_000, d=64, k=20, sigma=1.0, dtype="f32"),
     "sparse_n50k_d4096": dict(gen="sparse_groups", n=50_000, d=4096, k=10, sigma=1.0, dtype="f32"),
+    "batched_4096_d32": dict(gen="batched_sets", nsets=4096, d=32, sigma=1.0, dtype="f32"),
 }
 
 
 def make(config: str, seed: int = 0):
-    """(X, k, sigma) of a named workload."""
+    """(X, k, sigma) of a named single-set workload."""
     c = CONFIGS[config]
     if c["gen"] == "blobs_isotropic":
         X, _ = blobs_isotropic(seed)
@@ -167,3 +200,15 @@ def make(config: str, seed: int = 0):
     else:
         X, _ = sparse_groups(seed)
     return X, c["k"], c["sigma"]
+
+
+def make_batched(config: str = "batched_4096_d32", seed: int = 0, nsets: int | None = None,
+                 n_hi: int | None = None):
+    """(X, offsets, ks, sigma) of a batched workload, optionally with fewer
+    or smaller sets (the same recipe)."""
+    c = CONFIGS[config]
+    kw = dict(nsets=nsets or c["nsets"], d=c["d"])
+    if n_hi is not None:
+        kw["n_hi"] = n_hi
+    X, offsets, ks = batched_sets(seed, **kw)
+    return X, offsets, ks, c["sigma"]

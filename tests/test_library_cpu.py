@@ -83,3 +83,45 @@ def test_binding_requires_cuda_tensors():
     from paper_1702_04739_gb300 import isoclust
     with pytest.raises(TypeError):
         isoclust.cluster(torch.zeros(10, 3), 2, 1.0)
+
+
+def test_batched_host_side_validation():
+    """isoclust_cluster_batched checks its host plan arrays before any CUDA call."""
+    from paper_1702_04739_gb300 import isoclust
+    L = isoclust.load()
+    fake = ctypes.c_void_p(16)
+    offs = (ctypes.c_int64 * 4)(0, 5, 9, 20)
+    ks = (ctypes.c_int32 * 3)(2, 3, 4)
+
+    def call(X=fake, o=offs, nsets=3, d=3, dtype=0, k=ks, sigma=1.0, opts=None):
+        return L.isoclust_cluster_batched(X, o, nsets, d, dtype, k, ctypes.c_double(sigma), opts,
+                                          fake, fake, fake, None, None)
+
+    assert call(X=None) == 1
+    assert call(nsets=0) == 1
+    assert call(dtype=1) == 1                                   # F32 only
+    assert call(sigma=0.0) == 1
+    assert call(o=(ctypes.c_int64 * 4)(1, 5, 9, 20)) == 1        # offsets[0] != 0
+    assert call(o=(ctypes.c_int64 * 4)(0, 1, 9, 20)) == 1        # a one-point set
+    assert call(k=(ctypes.c_int32 * 3)(2, 0, 4)) == 1            # k < 1
+    assert call(k=(ctypes.c_int32 * 3)(2, 5, 4)) == 2            # k above the set's size
+    bad = isoclust.opts(alpha=0.5)
+    assert call(opts=ctypes.byref(bad)) == 1
+    bad = isoclust.opts(omega_mode=1)
+    assert call(opts=ctypes.byref(bad)) == 1
+    bad = isoclust.opts(precision=1)
+    assert call(opts=ctypes.byref(bad)) == 1
+
+
+def test_batched_workload_recipe():
+    import numpy as np
+    from paper_1702_04739_gb300 import workloads as W
+    X, offs, ks = W.batched_sets(seed=3, nsets=64, d=32)
+    sizes = np.diff(offs)
+    assert X.dtype == np.float32 and X.shape == (offs[-1], 32)
+    assert offs[0] == 0 and (sizes >= 64).all() and (sizes <= 8192).all()
+    assert ((ks >= 2) & (ks <= 8)).all()
+    X2, offs2, ks2 = W.batched_sets(seed=3, nsets=64, d=32)
+    assert (X == X2).all() and (offs == offs2).all() and (ks == ks2).all()
+    Xs, offs_s, ks_s = W.batched_sets(seed=1, d=4, sizes=[2, 3, 70])
+    assert list(np.diff(offs_s)) == [2, 3, 70] and (ks_s <= np.diff(offs_s)).all()
