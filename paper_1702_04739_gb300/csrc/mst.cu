@@ -22,6 +22,11 @@ constexpr int SW_T = 128;      // rows and columns per tile
 constexpr int SW_DC = 16;      // dims per shared-memory chunk
 constexpr int SW_PAD = SW_T + 4;
 inline unsigned blocks_for(int64_t n) { return (unsigned)(n > 0 ? ceil_div(n, TPB) : 1); }
+// grid of the round kernels: at most 8 blocks of 256 per SM, grid-stride
+inline unsigned round_grid(int64_t n) {
+    const int64_t b = n > 0 ? ceil_div(n, 256) : 1, cap = (int64_t)num_sms() * 8;
+    return (unsigned)(b < cap ? b : cap);
+}
 inline int log2_ceil(int64_t x) {
     int l = 0;
     while ((1LL << l) < x) ++l;
@@ -274,11 +279,17 @@ __global__ void k_mst_init(int32_t *comp, int64_t n, int32_t target, int32_t *co
     }
 }
 
+// The kernels of a round loop over their elements with a grid of a few waves
+// (round_grid): once the forest is complete, the rest of the fixed round
+// budget costs a handful of blocks per launch.
 __global__ void k_round_begin(int32_t *counters, unsigned long long *cd2, unsigned long long *cpair, int64_t n) {
     if (!active(counters)) return;
-    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v < n) { cd2[v] = ~0ull; cpair[v] = ~0ull; }
-    if (v == 0) {
+    const int64_t gs = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gs) {
+        cd2[v] = ~0ull;
+        cpair[v] = ~0ull;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         counters[MC_OVF_TOTAL] += counters[MC_OVERFLOW];
         counters[MC_OVERFLOW] = 0;
         counters[MC_ROUNDS] += 1;
@@ -290,22 +301,25 @@ __global__ void k_cmin_d2(const int32_t *__restrict__ comp, const double *__rest
                           const int32_t *__restrict__ rowj, int64_t n, unsigned long long *cd2,
                           const int32_t *counters) {
     if (!active(counters)) return;
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n && rowj[i] >= 0) atomicMin(cd2 + comp[i], dbits(rowd2[i]));
+    const int64_t gs = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gs) {
+        if (rowj[i] >= 0) atomicMin(cd2 + comp[i], dbits(rowd2[i]));
+    }
 }
 
 __global__ void k_cmin_pair(const int32_t *__restrict__ comp, const double *__restrict__ rowd2,
                             const int32_t *__restrict__ rowj, int64_t n, const unsigned long long *cd2,
                             unsigned long long *cpair, const int32_t *counters) {
     if (!active(counters)) return;
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int32_t j = rowj[i];
-    if (j < 0) return;
-    int32_t c = comp[i];
-    if (dbits(rowd2[i]) != cd2[c]) return;
-    unsigned long long a = (unsigned long long)min((int32_t)i, j), b = (unsigned long long)max((int32_t)i, j);
-    atomicMin(cpair + c, (a << 32) | b);
+    const int64_t gs = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gs) {
+        int32_t j = rowj[i];
+        if (j < 0) continue;
+        int32_t c = comp[i];
+        if (dbits(rowd2[i]) != cd2[c]) continue;
+        unsigned long long a = (unsigned long long)min((int32_t)i, j), b = (unsigned long long)max((int32_t)i, j);
+        atomicMin(cpair + c, (a << 32) | b);
+    }
 }
 
 __global__ void k_hook_tgt(const int32_t *__restrict__ comp, int64_t n, const unsigned long long *__restrict__ cd2,
@@ -313,14 +327,16 @@ __global__ void k_hook_tgt(const int32_t *__restrict__ comp, int64_t n, const un
                            int32_t *__restrict__ cu, int32_t *__restrict__ cv, double *__restrict__ cdd,
                            const int32_t *counters) {
     if (!active(counters)) return;
-    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= n || comp[v] != v) return;
-    unsigned long long pr = cpair[v];
-    if (pr == ~0ull) { tgt[v] = (int32_t)v; return; }
-    int32_t a = (int32_t)(pr >> 32), b = (int32_t)(pr & 0xffffffffu);
-    int32_t outside = comp[a] == v ? b : a;
-    tgt[v] = comp[outside];
-    cu[v] = a; cv[v] = b; cdd[v] = bitsd(cd2[v]);
+    const int64_t gs = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gs) {
+        if (comp[v] != v) continue;
+        unsigned long long pr = cpair[v];
+        if (pr == ~0ull) { tgt[v] = (int32_t)v; continue; }
+        int32_t a = (int32_t)(pr >> 32), b = (int32_t)(pr & 0xffffffffu);
+        int32_t outside = comp[a] == v ? b : a;
+        tgt[v] = comp[outside];
+        cu[v] = a; cv[v] = b; cdd[v] = bitsd(cd2[v]);
+    }
 }
 
 __global__ void k_hook_resolve(const int32_t *__restrict__ comp, int64_t n, const int32_t *__restrict__ tgt,
@@ -328,33 +344,38 @@ __global__ void k_hook_resolve(const int32_t *__restrict__ comp, int64_t n, cons
                                const double *__restrict__ cdd, int32_t *__restrict__ nxt, int32_t *__restrict__ eu,
                                int32_t *__restrict__ ev, double *__restrict__ ed2, int32_t *counters, uint32_t *st) {
     if (!active(counters)) return;
-    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= n || comp[v] != v) return;
-    int32_t T = tgt[v];
-    if (T == v) { nxt[v] = (int32_t)v; return; }
-    bool mutual = tgt[T] == v;
-    nxt[v] = (mutual && v < T) ? (int32_t)v : T;
-    if (!mutual || v < T) {
-        int q = atomicAdd(counters + MC_NEDGES, 1);
-        if (q < n - 1) { eu[q] = cu[v]; ev[q] = cv[v]; ed2[q] = cdd[v]; }
-        else atomicOr(st, DEV_EDGE_COUNT);
+    const int64_t gs = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gs) {
+        if (comp[v] != v) continue;
+        int32_t T = tgt[v];
+        if (T == v) { nxt[v] = (int32_t)v; continue; }
+        bool mutual = tgt[T] == v;
+        nxt[v] = (mutual && v < T) ? (int32_t)v : T;
+        if (!mutual || v < T) {
+            int q = atomicAdd(counters + MC_NEDGES, 1);
+            if (q < n - 1) { eu[q] = cu[v]; ev[q] = cv[v]; ed2[q] = cdd[v]; }
+            else atomicOr(st, DEV_EDGE_COUNT);
+        }
     }
 }
 
 __global__ void k_jump(const int32_t *__restrict__ comp, const int32_t *__restrict__ nin, int32_t *__restrict__ nout,
                        int64_t n, const int32_t *counters) {
     if (!active(counters)) return;
-    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v < n && comp[v] == v) nout[v] = nin[nin[v]];
+    const int64_t gs = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gs) {
+        if (comp[v] == v) nout[v] = nin[nin[v]];
+    }
 }
 
 __global__ void k_relabel(int32_t *comp, const int32_t *__restrict__ nxt, int64_t n, int32_t *counters) {
     if (!active(counters)) return;
-    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= n) return;
-    int32_t r = nxt[comp[v]];
-    comp[v] = r;
-    if (r == v) atomicAdd(counters + MC_NCOMP_NEW, 1);
+    const int64_t gs = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gs) {
+        int32_t r = nxt[comp[v]];
+        comp[v] = r;
+        if (r == v) atomicAdd(counters + MC_NCOMP_NEW, 1);
+    }
 }
 
 __global__ void k_round_end(int32_t *counters) {
@@ -489,26 +510,27 @@ cudaError_t mst_build(MstScratch &S, const void *X, int64_t n, int32_t d, int dt
     const int64_t span = max_n > 0 ? max_n : n;
     const int R = log2_ceil(span) + 1;
     const int L = log2_ceil(span) + 1;
+    const unsigned rg = round_grid(n);
     cudaError_t e;
     if (tc && (e = tc_prepare(*tc, (const float *)X, n, d, s))) return e;
     for (int r = 0; r < R; ++r) {
-        k_round_begin<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.counters, S.cd2, S.cpair, n);
+        k_round_begin<<<rg, TPB, 0, ISO_S(s)>>>(S.counters, S.cd2, S.cpair, n);
         if (tc) {
             if ((e = tc_sweep_round(*tc, S, (const float *)X, n, d, status, s))) return e;
         } else if ((e = sweep_round(S, X, n, d, dtype, sweep_fp64, s))) {
             return e;
         }
-        k_cmin_d2<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.comp, S.rowd2, S.rowj, n, S.cd2, S.counters);
-        k_cmin_pair<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.comp, S.rowd2, S.rowj, n, S.cd2, S.cpair, S.counters);
-        k_hook_tgt<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.comp, n, S.cd2, S.cpair, S.tgt, S.cu, S.cv, S.cdd, S.counters);
-        k_hook_resolve<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.comp, n, S.tgt, S.cu, S.cv, S.cdd, S.nxt, S.eu, S.ev, S.ed2,
+        k_cmin_d2<<<rg, TPB, 0, ISO_S(s)>>>(S.comp, S.rowd2, S.rowj, n, S.cd2, S.counters);
+        k_cmin_pair<<<rg, TPB, 0, ISO_S(s)>>>(S.comp, S.rowd2, S.rowj, n, S.cd2, S.cpair, S.counters);
+        k_hook_tgt<<<rg, TPB, 0, ISO_S(s)>>>(S.comp, n, S.cd2, S.cpair, S.tgt, S.cu, S.cv, S.cdd, S.counters);
+        k_hook_resolve<<<rg, TPB, 0, ISO_S(s)>>>(S.comp, n, S.tgt, S.cu, S.cv, S.cdd, S.nxt, S.eu, S.ev, S.ed2,
                                                      S.counters, status);
         int32_t *na = S.nxt, *nb = S.nxt2;
         for (int it = 0; it < L; ++it) {
-            k_jump<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.comp, na, nb, n, S.counters);
+            k_jump<<<rg, TPB, 0, ISO_S(s)>>>(S.comp, na, nb, n, S.counters);
             int32_t *t = na; na = nb; nb = t;
         }
-        k_relabel<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.comp, na, n, S.counters);
+        k_relabel<<<rg, TPB, 0, ISO_S(s)>>>(S.comp, na, n, S.counters);
         k_round_end<<<1, 1, 0, ISO_S(s)>>>(S.counters);
     }
     if (tc) k_or_err<<<1, 1, 0, ISO_S(s)>>>(tc->err, status);
@@ -518,7 +540,7 @@ cudaError_t mst_build(MstScratch &S, const void *X, int64_t n, int32_t d, int dt
 cudaError_t nn_sweep(MstScratch &S, const void *X, int64_t n, int32_t d, int dtype, bool sweep_fp64,
                      uint32_t *status, cudaStream_t s, TcScratch *tc) {
     k_mst_init<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.comp, n, 1, S.counters);
-    k_round_begin<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.counters, S.cd2, S.cpair, n);
+    k_round_begin<<<round_grid(n), TPB, 0, ISO_S(s)>>>(S.counters, S.cd2, S.cpair, n);
     cudaError_t e;
     if (tc) {
         if ((e = tc_prepare(*tc, (const float *)X, n, d, s))) return e;

@@ -47,6 +47,7 @@ struct TcScratch {
     int splits = 1;                                // column splits per row tile (one set)
     int lists = 2;                                 // candidate lists per row (2 per split: tile halves)
     __nv_bfloat16 *xh = nullptr, *xl = nullptr;   // row r is point permp[r] (zero rows at padding)
+    float *xs = nullptr;                           // [n_pad][d] the points themselves in the same order
     float *nrm = nullptr, *rsq = nullptr;          // |y|^2 and |y| of the represented rows (0 at padding)
     float *cnrm = nullptr;                         // |y|^2 as a column: +inf at padding
     float *tmax = nullptr, *tsq = nullptr;         // per 128-row tile: max |y|^2 and its sqrt
@@ -57,6 +58,7 @@ struct TcScratch {
     uint64_t *keys = nullptr, *kbuf = nullptr;
     float *tv = nullptr, *tu = nullptr;            // per (list, row): best-8 half-tile lower bounds, best upper bound
     int32_t *tj = nullptr;
+    int32_t *nsurv = nullptr, *surv = nullptr;     // per row: columns to key in FP64 (padded column indices)
     uint32_t *err = nullptr;
     // independent sets (null for one set): sweep work items {row tile,
     // first and end column tile, split}, set of each point, set offsets

@@ -38,6 +38,7 @@ constexpr int TC_EPI_WARPS = 8;                           // two per TMEM lane q
 constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;
 constexpr int TC_TOPK = 8;                                // best half-tiles kept per (list, row)
 constexpr int TC_CW = TC_BN / 2;                          // columns per candidate (half-tile)
+constexpr int TC_SURV = 8;                                // FP64-keyed columns per row (more: rescan)
 constexpr long long TC_WAIT_CYCLES = 4000000000LL;
 
 // Column metadata first: the epilogue reads it with 16-byte vector loads.
@@ -506,18 +507,24 @@ __global__ void k_tc_place(const int32_t *__restrict__ perm, int64_t n, const in
     permp[r] = i;
 }
 
+// Also writes xs, the points themselves in the same row order (zero rows at
+// padding): the recheck reads candidate columns as contiguous blocks.
 __global__ void k_tc_split(const float *__restrict__ X, const float *__restrict__ mean,
                            const int32_t *__restrict__ set_of, const int32_t *__restrict__ permp, int32_t d,
                            int64_t n_pad, int32_t d_pad, __nv_bfloat16 *__restrict__ xh,
-                           __nv_bfloat16 *__restrict__ xl) {
+                           __nv_bfloat16 *__restrict__ xl, float *__restrict__ xs) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n_pad * d_pad) return;
     const int64_t r = idx / d_pad, t = idx - r * d_pad;
     const int32_t i = permp[r];
     float y = 0.0f;
-    if (i >= 0 && t < d) {
-        const int64_t b = set_of ? set_of[i] : 0;
-        y = __fsub_rn(X[(int64_t)i * d + t], mean[b * d + t]);
+    if (t < d) {
+        const float x = i >= 0 ? X[(int64_t)i * d + t] : 0.0f;
+        xs[r * d + t] = x;
+        if (i >= 0) {
+            const int64_t b = set_of ? set_of[i] : 0;
+            y = __fsub_rn(x, mean[b * d + t]);
+        }
     }
     const __nv_bfloat16 h = __float2bfloat16_rn(y);
     const __nv_bfloat16 l = __float2bfloat16_rn(__fsub_rn(y, __bfloat162float(h)));
@@ -557,8 +564,8 @@ __global__ void k_tc_tile_max(const float *__restrict__ nrm, int64_t n_pad, floa
 __global__ void k_tc_gather_comp(const int32_t *__restrict__ comp, const int32_t *__restrict__ permp,
                                  int64_t n_pad, int32_t *__restrict__ compp, const int32_t *counters) {
     if (!mst_active(counters)) return;
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < n_pad) {
+    const int64_t gs = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n_pad; r += gs) {
         const int32_t i = permp[r];
         compp[r] = i >= 0 ? comp[i] : -2;
     }
@@ -574,7 +581,10 @@ __global__ void k_tc_fill_lists(float *__restrict__ tv, int32_t *__restrict__ tj
     if (i < nu) tu[i] = INFINITY;
 }
 
-// One warp per padded row r, the point i = permp[r] (none at padding).  The lists'
+// One warp per padded row r, the point i = permp[r] (none at padding).
+// Candidate columns are read from xs (rows in the sweep's order) with their
+// components from compp, so a half-tile is one contiguous block; only the
+// survivors of the FP32 filter are mapped back to point indices.  The lists'
 // (column split x tile half) best-8 half-tile lower bounds and their best
 // upper bound U are merged.
 // The epilogue's bounds hold for the BF16-represented points; the exact
@@ -592,17 +602,15 @@ __device__ __forceinline__ float approx_d2_f32(const float *__restrict__ a, cons
     return acc;
 }
 
-__global__ void __launch_bounds__(256) k_recheck_tc(const float *__restrict__ X, int64_t n, int32_t d, int lists,
-                                                    const float *__restrict__ tv, const int32_t *__restrict__ tj,
-                                                    const float *__restrict__ tu, const float *__restrict__ rsq,
-                                                    const int32_t *__restrict__ perm, const int32_t *__restrict__ comp,
-                                                    const unsigned int *__restrict__ nmax_bits, double eps_rep,
-                                                    double e32, double *__restrict__ rowd2, int32_t *__restrict__ rowj,
-                                                    int32_t *__restrict__ ovf, int32_t *counters) {
-    if (!mst_active(counters)) return;
-    const int lane = threadIdx.x & 31;
-    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (r >= n) return;
+__device__ __forceinline__ void recheck_row(int64_t r, int lane, const float *__restrict__ xs, int64_t n, int32_t d,
+                                            int lists, const float *__restrict__ tv, const int32_t *__restrict__ tj,
+                                            const float *__restrict__ tu, const float *__restrict__ rsq,
+                                            const int32_t *__restrict__ perm, const int32_t *__restrict__ compp,
+                                            const unsigned int *__restrict__ nmax_bits, float eps_rep, float mul32,
+                                            float add32, int32_t *__restrict__ nsurv, int32_t *__restrict__ surv,
+                                            int32_t *__restrict__ rowj, int32_t *__restrict__ ovf,
+                                            int32_t *counters) {
+    if (lane == 0) nsurv[r] = 0;           // every row, padding included: k_exact_tc reads them all
     const int64_t i = perm[r];
     if (i < 0) return;                     // padding row
     // ---- merge: each lane holds up to 8 of the lists x 8 entries (lists <= 32);
@@ -660,15 +668,15 @@ __global__ void __launch_bounds__(256) k_recheck_tc(const float *__restrict__ X,
         if (lane == 0) rowj[i] = -1;
         return;
     }
-    // representation error: distances move by at most w = eps (|y_i| + |y_max|)
-    const double si = (double)rsq[r], smax = sqrt((double)__uint_as_float(*nmax_bits));
-    const double Ud = (double)U;
-    const double w = eps_rep * (si + smax);
-    const double su = sqrt(fmax(Ud, 0.0));
-    const double hi_true = (su + w) * (su + w) * (1.0 + 1e-12);     // exact nearest foreign d2 <= this
-    const double sh = sqrt(hi_true);
-    const double tile_cut = (sh + w) * (sh + w) * (1.0 + 1e-12);   // represented d2 of any candidate <= this
-    if (bj[TC_TOPK - 1] >= 0 && (double)bv[TC_TOPK - 1] <= tile_cut) {
+    // representation error: distances move by at most w = eps (|y_i| + |y_max|).
+    // FP32 bounds rounded upwards at every step, then inflated by 1e-5.
+    const float si = rsq[r], smax = __fsqrt_ru(__uint_as_float(*nmax_bits));
+    const float w = __fmul_ru(eps_rep, __fadd_ru(si, smax));
+    const float a1 = __fadd_ru(__fsqrt_ru(fmaxf(U, 0.0f)), w);
+    const float hi_true = __fmul_ru(__fmul_ru(a1, a1), 1.00001f);     // exact nearest foreign d2 <= this
+    const float a2 = __fadd_ru(__fsqrt_ru(hi_true), w);
+    const float tile_cut = __fmul_ru(__fmul_ru(a2, a2), 1.00001f);   // represented d2 of any candidate <= this
+    if (bj[TC_TOPK - 1] >= 0 && bv[TC_TOPK - 1] <= tile_cut) {
         if (lane == 0) {
             const int q = atomicAdd(counters + MC_OVERFLOW, 1);
             ovf[q] = (int32_t)i;
@@ -676,25 +684,22 @@ __global__ void __launch_bounds__(256) k_recheck_tc(const float *__restrict__ X,
         }
         return;
     }
-    const float cut32 = (float)(hi_true * (1.0 + e32) * (1.0 + 1e-6));
-    const int32_t ci = comp[i];
-    const float *xi = X + i * d;
-    double best = INFINITY;
-    int32_t bestj = -1;
-    const bool vec = (d & 3) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
-    for (int k = 0; k < TC_TOPK; k += 2) {
-        if (bj[k] < 0 || (double)bv[k] > tile_cut) break;
-        const bool second = bj[k + 1] >= 0 && (double)bv[k + 1] <= tile_cut;
-        // two half-tiles, two columns of each per lane: four independent FMA chains
-        int64_t jj[4];
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-        bool live[4];
+    // FP32 direct differences over the candidate half-tiles (two per pass, two
+    // columns of each per lane: four FMA chains).  Pass 1: the row's FP32
+    // minimum m32; the exact best has FP32 value <= m32 * mul32 + add32.
+    // Pass 2 revisits the passes that hold such columns and records them.
+    const int32_t ci = compp[r];
+    const float *xi = xs + r * d;
+    const bool vec = (d & 3) == 0 && (reinterpret_cast<uintptr_t>(xs) & 15) == 0;
+    auto scan = [&](int k, bool second, int64_t (&jp)[4], bool (&live)[4], float (&acc)[4]) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int cand = (u < 2) ? bj[k] : (second ? bj[k + 1] : -1);
-            const int64_t jp = cand < 0 ? -1 : (int64_t)cand * TC_CW + lane + 32 * (u & 1);
-            jj[u] = (jp >= 0 && jp < n) ? (int64_t)perm[jp] : -1;
-            live[u] = jj[u] >= 0 && comp[jj[u]] != ci;
+            jp[u] = cand < 0 ? -1 : (int64_t)cand * TC_CW + lane + 32 * (u & 1);
+            int32_t cj = -2;
+            if (jp[u] >= 0 && jp[u] < n) cj = compp[jp[u]];
+            live[u] = cj >= 0 && cj != ci;                                 // padding: -2
+            acc[u] = 0.0f;
         }
         if (vec) {
             const float4 *xi4 = reinterpret_cast<const float4 *>(xi);
@@ -703,7 +708,7 @@ __global__ void __launch_bounds__(256) k_recheck_tc(const float *__restrict__ X,
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     if (!live[u]) continue;
-                    const float4 b = reinterpret_cast<const float4 *>(X + jj[u] * d)[t];
+                    const float4 b = reinterpret_cast<const float4 *>(xs + jp[u] * d)[t];
                     float df = __fsub_rn(a.x, b.x); acc[u] = __fmaf_rn(df, df, acc[u]);
                     df = __fsub_rn(a.y, b.y); acc[u] = __fmaf_rn(df, df, acc[u]);
                     df = __fsub_rn(a.z, b.z); acc[u] = __fmaf_rn(df, df, acc[u]);
@@ -713,30 +718,111 @@ __global__ void __launch_bounds__(256) k_recheck_tc(const float *__restrict__ X,
         } else {
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-                if (live[u]) acc[u] = approx_d2_f32(xi, X + jj[u] * d, d);
+                if (live[u]) acc[u] = approx_d2_f32(xi, xs + jp[u] * d, d);
         }
+    };
+    float pmin[TC_TOPK / 2];
+    int npass = 0;
+    float m32 = INFINITY;
+    for (int k = 0; k < TC_TOPK; k += 2) {
+        if (bj[k] < 0 || bv[k] > tile_cut) break;
+        const bool second = bj[k + 1] >= 0 && bv[k + 1] <= tile_cut;
+        int64_t jp[4];
+        bool live[4];
+        float acc[4];
+        scan(k, second, jp, live, acc);
+        float pm = INFINITY;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            if (live[u] && acc[u] <= cut32) {
-                const double e = exact_d2(xi, X + jj[u] * d, d);
-                if (bestj < 0 || key_less(e, (int32_t)i, (int32_t)jj[u], best, (int32_t)i, bestj)) {
-                    best = e;
-                    bestj = (int32_t)jj[u];
-                }
-            }
-        }
+        for (int u = 0; u < 4; ++u)
+            if (live[u]) pm = fminf(pm, acc[u]);
+        pmin[k >> 1] = pm;
+        m32 = fminf(m32, pm);
+        ++npass;
         if (!second) break;
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const double od = __shfl_xor_sync(0xffffffffu, best, o);
-        const int32_t oj = __shfl_xor_sync(0xffffffffu, bestj, o);
-        if (oj >= 0 && (bestj < 0 || key_less(od, (int32_t)i, oj, best, (int32_t)i, bestj))) { best = od; bestj = oj; }
+    for (int o = 16; o > 0; o >>= 1) m32 = fminf(m32, __shfl_xor_sync(0xffffffffu, m32, o));
+    if (!(m32 < INFINITY)) {
+        if (lane == 0) rowj[i] = -1;
+        return;
+    }
+    const float thr = __fadd_ru(__fmul_ru(m32, mul32), add32);
+    int cnt = 0;
+    for (int p = 0; p < npass; ++p) {
+        if (!__any_sync(0xffffffffu, pmin[p] <= thr)) continue;
+        const int k = 2 * p;
+        const bool second = bj[k + 1] >= 0 && bv[k + 1] <= tile_cut;
+        int64_t jp[4];
+        bool live[4];
+        float acc[4];
+        scan(k, second, jp, live, acc);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const bool sv = live[u] && acc[u] <= thr;
+            const unsigned bal = __ballot_sync(0xffffffffu, sv);
+            const int slot = cnt + __popc(bal & ((1u << lane) - 1u));
+            if (sv && slot < TC_SURV) surv[r * TC_SURV + slot] = (int32_t)jp[u];
+            cnt += __popc(bal);
+        }
     }
     if (lane == 0) {
+        if (cnt > TC_SURV) {                     // many near-ties: exact rescan of the row
+            const int q = atomicAdd(counters + MC_OVERFLOW, 1);
+            ovf[q] = (int32_t)i;
+            rowj[i] = -2;
+        } else {
+            nsurv[r] = cnt;
+        }
+    }
+}
+
+// Exact keys of the recorded columns, one thread per row: the FP64 pipe sees
+// full warps (a warp per row would run each key on a single lane).
+__global__ void __launch_bounds__(256) k_exact_tc(const float *__restrict__ xs, int64_t n, int32_t d,
+                                                  const int32_t *__restrict__ perm, const int32_t *__restrict__ nsurv,
+                                                  const int32_t *__restrict__ surv, double *__restrict__ rowd2,
+                                                  int32_t *__restrict__ rowj, const int32_t *counters) {
+    if (!mst_active(counters)) return;
+    const int64_t gs = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gs) {
+        const int c = nsurv[r];
+        const int32_t i = perm[r];
+        if (c <= 0 || c > TC_SURV || i < 0) continue;
+        const float *xi = xs + r * d;
+        double best = INFINITY;
+        int32_t bestj = -1;
+        for (int q = 0; q < c; ++q) {
+            const int64_t jp = surv[r * TC_SURV + q];
+            if (jp < 0 || jp >= n) continue;
+            const int32_t j = perm[jp];
+            if (j < 0) continue;
+            const double e = exact_d2(xi, xs + jp * d, d);
+            if (bestj < 0 || key_less(e, i, j, best, i, bestj)) {
+                best = e;
+                bestj = j;
+            }
+        }
         rowd2[i] = best;
         rowj[i] = bestj;
     }
+}
+
+__global__ void __launch_bounds__(256, 4) k_recheck_tc(const float *__restrict__ xs, int64_t n, int32_t d, int lists,
+                                                       const float *__restrict__ tv, const int32_t *__restrict__ tj,
+                                                       const float *__restrict__ tu, const float *__restrict__ rsq,
+                                                       const int32_t *__restrict__ perm,
+                                                       const int32_t *__restrict__ compp,
+                                                       const unsigned int *__restrict__ nmax_bits, float eps_rep,
+                                                       float mul32, float add32, int32_t *__restrict__ nsurv,
+                                                       int32_t *__restrict__ surv, int32_t *__restrict__ rowj,
+                                                       int32_t *__restrict__ ovf, int32_t *counters) {
+    if (!mst_active(counters)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = w0; r < n; r += nw)
+        recheck_row(r, lane, xs, n, d, lists, tv, tj, tu, rsq, perm, compp, nmax_bits, eps_rep, mul32, add32, nsurv,
+                    surv, rowj, ovf, counters);
 }
 
 // Self-contained rescan of a queued row: FP32 direct differences give the
@@ -850,6 +936,7 @@ void TcScratch::carve(Arena &A, int64_t n, int32_t d, int splits_, int64_t n_pad
     const int64_t nt = n_pad / TC_BM;
     xh = A.take<__nv_bfloat16>((size_t)n_pad * d_pad, 1024);
     xl = A.take<__nv_bfloat16>((size_t)n_pad * d_pad, 1024);
+    xs = A.take<float>((size_t)n_pad * d, 256);
     nrm = A.take<float>(n_pad);
     cnrm = A.take<float>(n_pad);
     rsq = A.take<float>(n_pad);
@@ -864,6 +951,8 @@ void TcScratch::carve(Arena &A, int64_t n, int32_t d, int splits_, int64_t n_pad
     keys = A.take<uint64_t>(n);
     kbuf = A.take<uint64_t>(n);
     compp = A.take<int32_t>(n_pad);
+    nsurv = A.take<int32_t>(n_pad);
+    surv = A.take<int32_t>((size_t)n_pad * TC_SURV);
     tv = A.take<float>((size_t)lists * n_pad * TC_TOPK);
     tj = A.take<int32_t>((size_t)lists * n_pad * TC_TOPK);
     tu = A.take<float>((size_t)lists * n_pad);
@@ -907,7 +996,7 @@ cudaError_t tc_prepare(TcScratch &T, const float *X, int64_t n, int32_t d, cudaS
     k_tc_place<<<(unsigned)ceil_div(n, 256), 256, 0, ISO_S(s)>>>(T.perm, n, T.set_of, T.offs, T.rowbase, T.permp);
     const int64_t tot = T.n_pad * T.d_pad;
     k_tc_split<<<(unsigned)ceil_div(tot, 256), 256, 0, ISO_S(s)>>>(X, T.mean, T.set_of, T.permp, d, T.n_pad, T.d_pad,
-                                                                  T.xh, T.xl);
+                                                                  T.xh, T.xl, T.xs);
     if ((e = cudaMemsetAsync(T.nmax_bits, 0, sizeof(unsigned int), s))) return e;
     k_tc_norms<<<(unsigned)ceil_div(T.n_pad, 256), 256, 0, ISO_S(s)>>>(T.xh, T.xl, T.permp, T.n_pad, T.d_pad, T.nrm,
                                                                       T.cnrm, T.rsq, T.nmax_bits);
@@ -938,8 +1027,9 @@ cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t 
     const int64_t items = T.items ? T.nitems : (int64_t)ntiles * T.splits;
     const int64_t nsm = (int64_t)num_sms();
     const unsigned grid = (unsigned)(items < nsm ? (items > 0 ? items : 1) : nsm);
-    k_tc_gather_comp<<<(unsigned)ceil_div(T.n_pad, 256), 256, 0, ISO_S(s)>>>(S.comp, T.permp, T.n_pad, T.compp,
-                                                                            S.counters);
+    const int64_t gblocks = ceil_div(T.n_pad, 256), gcap = (int64_t)num_sms() * 8;
+    k_tc_gather_comp<<<(unsigned)(gblocks < gcap ? gblocks : gcap), 256, 0, ISO_S(s)>>>(S.comp, T.permp, T.n_pad,
+                                                                                       T.compp, S.counters);
     // d2 = n_i + n_j - 2g against d2 of the represented points: tensor-core
     // FP32 accumulation of 3 d_pad products (worst case: one rounding of the
     // running magnitude per addition, 2^-23) and the dropped lo.lo term
@@ -960,12 +1050,21 @@ cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t 
     // representation error of a centred point by BF16 hi + lo: 2^-18 relative
     // per element, plus the FP32 rounding of x - c (2^-24); 25 % headroom
     const double eps_rep = 1.25 * (3.814697265625e-06 + 5.9604644775390625e-08);
+    // FP32 direct differences: relative error <= e (and an underflow term);
+    // any column within m32 * (1+e)/(1-e) + 2 add of the row's FP32 minimum
+    // can hold the exact best
     const double e = 1.1 * (double)(d + 3) * 5.9604644775390625e-08;
-    k_recheck_tc<<<(unsigned)ceil_div(T.n_pad * 32, 256), 256, 0, ISO_S(s)>>>(
-        X, T.n_pad, d, T.lists, T.tv, T.tj, T.tu, T.rsq, T.permp, S.comp, T.nmax_bits, eps_rep, e, S.rowd2, S.rowj,
-        S.ovf_rows, S.counters);
     const double mul = (1.0 + e) / (1.0 - e);
     const double add = (double)(d + 1) * 1.401298464324817e-45 * 4.0;
+    const float mul32 = (float)(mul * (1.0 + 1e-6)), add32 = (float)(2.01 * add) + 1.401298464324817e-45f;
+    const int64_t rblocks = ceil_div(T.n_pad * 32, 256), rcap = (int64_t)num_sms() * 16;
+    k_recheck_tc<<<(unsigned)(rblocks < rcap ? rblocks : rcap), 256, 0, ISO_S(s)>>>(
+        T.xs, T.n_pad, d, T.lists, T.tv, T.tj, T.tu, T.rsq, T.permp, T.compp, T.nmax_bits, (float)(eps_rep * 1.0001),
+        mul32, add32, T.nsurv, T.surv, S.rowj, S.ovf_rows, S.counters);
+    const int64_t xblocks = ceil_div(T.n_pad, 256), xcap = (int64_t)num_sms() * 8;
+    k_exact_tc<<<(unsigned)(xblocks < xcap ? xblocks : xcap), 256, 0, ISO_S(s)>>>(T.xs, T.n_pad, d, T.permp, T.nsurv,
+                                                                                  T.surv, S.rowd2, S.rowj,
+                                                                                  S.counters);
     k_rescan_tc<<<(unsigned)(num_sms() * 4), 256, 0, ISO_S(s)>>>(X, n, d, S.comp, S.ovf_rows, T.set_of, T.offs, mul,
                                                                  add, S.rowd2, S.rowj, S.counters);
     (void)status;
