@@ -82,6 +82,10 @@ def _load():
             lib.oracle_cluster.argtypes = [_ptr, _i64, _i32, _i64, _dbl, _dbl, _i32, _i32, _i64,
                                            _ptr, _ptr, _ptr, _ptr, _ptr, _ptr, _ptr,
                                            _ptr, _ptr, _ptr, _ptr, _ptr, _ptr]
+            lib.oracle_ik_fixed.restype = ctypes.c_int
+            lib.oracle_ik_fixed.argtypes = [_ptr, _i64, _i32, _ptr, _dbl, _ptr, _ptr, _i64, _ptr, _ptr, _ptr, _ptr]
+            lib.oracle_ik_grad.restype = ctypes.c_int
+            lib.oracle_ik_grad.argtypes = [_ptr, _i64, _i32, _ptr, _dbl, _ptr, _ptr, _i32, _ptr, _ptr, _ptr, _ptr]
             lib.oracle_set_threads.restype = None
             lib.oracle_set_threads.argtypes = [ctypes.c_int]
             lib.oracle_get_threads.restype = ctypes.c_int
@@ -224,3 +228,38 @@ def cluster(X, k: int, sigma: float, alpha: float = 0.0, omega_mode: int = 0,
     return dict(edge_u=eu, edge_v=ev, edge_d2=ed2, parent=parent, phi_par=phi, omega=om, p=p,
                 labels=labels, residual=residual, i_k=float(ik[0]), beta=float(beta[0]),
                 stats=stats, calls=int(info[0]))
+
+
+def ik_fixed(X, scale, sigma: float, parent, labels, k: int) -> dict:
+    """i_k on a fixed tree and subpartition (alpha = 0): the ratio
+    phi(dA_j)/omega(A_j) of every label j < k from z = scale * x, the largest
+    (R) and its label (jstar)."""
+    X = _X(X)
+    n, d = X.shape
+    s = np.ascontiguousarray(np.asarray(scale, dtype=np.float64).reshape(d))
+    parent = np.ascontiguousarray(parent, dtype=np.int32)
+    labels = np.ascontiguousarray(labels, dtype=np.int32)
+    phk = np.zeros(k, np.float64); omk = np.zeros(k, np.float64)
+    js = np.zeros(1, np.int32); R = np.zeros(1, np.float64)
+    rc = _load().oracle_ik_fixed(_p(X), n, d, _p(s), float(sigma), _p(parent), _p(labels), int(k),
+                                 _p(phk), _p(omk), _p(js), _p(R))
+    if rc:
+        raise RuntimeError(f"oracle_ik_fixed failed: {rc}")
+    return dict(R=float(R[0]), jstar=int(js[0]), phi=phk, omega=omk)
+
+
+def ik_grad(X, scale, sigma: float, parent, labels, jstar: int) -> dict:
+    """dR/dX, dR/dscale, dR/dsigma of R = phi(dA*)/omega(A*) for the set jstar
+    on a fixed tree and subpartition."""
+    X = _X(X)
+    n, d = X.shape
+    s = np.ascontiguousarray(np.asarray(scale, dtype=np.float64).reshape(d))
+    parent = np.ascontiguousarray(parent, dtype=np.int32)
+    labels = np.ascontiguousarray(labels, dtype=np.int32)
+    dX = np.zeros((n, d), np.float64); ds = np.zeros(d, np.float64)
+    dsig = np.zeros(1, np.float64); R = np.zeros(1, np.float64)
+    rc = _load().oracle_ik_grad(_p(X), n, d, _p(s), float(sigma), _p(parent), _p(labels), int(jstar),
+                                _p(dX), _p(ds), _p(dsig), _p(R))
+    if rc:
+        raise RuntimeError(f"oracle_ik_grad failed: {rc}")
+    return dict(dX=dX, dscale=ds, dsigma=float(dsig[0]), R=float(R[0]))

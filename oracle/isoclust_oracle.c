@@ -504,3 +504,145 @@ int oracle_cluster(const double *X, int64_t n, int32_t d, int64_t k, double sigm
     return oracle_tree_stage(n, parent, phi_par, omega, alpha != 0.0 ? p : NULL, k,
                              labels, residual, i_k, beta, stats, info);
 }
+
+/* ------------------------------------------------------------------ */
+/* i_k through a fixed structure, and its derivative.
+ *
+ * With alpha = 0 (p = 0) the cost of a k-subpartition (Section 2.1) is
+ * max_j phi(dA_j) / omega(A_j): dA_j are the tree edges with exactly one
+ * end in A_j (phi of eq. phi on each), omega(A_j) is the sum of eq. omega
+ * over A_j.  The points enter as z_i = s (.) x_i, a per-feature scale s, and
+ * the bandwidth sigma enters eq. phi and eq. omega.  Holding the tree
+ * (parent) and the subpartition (labels; A_j = {v : labels[v] == j}) fixed,
+ * i_k = R = Phi / Omega for the set A* of the largest ratio, and
+ *   dR = (dPhi - R dOmega) / Omega,
+ *   phi(e) = exp(-r_e / sigma), r_e = ||z_u - z_v||,
+ *     d phi / d z_u = -phi (z_u - z_v) / (sigma r_e) = -d phi / d z_v,
+ *     d phi / d sigma = phi r_e / sigma^2,
+ *   Omega = sum_{i in A*} sum_{j != i} w_ij, w_ij = exp(-r_ij / sigma): each
+ *     ordered pair (i in A*, j) adds -w (z_i - z_j) / (sigma r) to d/dz_i,
+ *     the opposite to d/dz_j, and w r / sigma^2 to d/dsigma.
+ * Chain rule to the inputs: dR/dx_it = s_t dR/dz_it, dR/ds_t = sum_i x_it dR/dz_it.
+ * Coincident points (r = 0) are not differentiable; their terms are taken
+ * as 0 (the direction is undefined). */
+static double zdist(const double *X, const double *s, int32_t d, int64_t i, int64_t j)
+{
+    double acc = 0.0;
+    for (int32_t t = 0; t < d; ++t) {
+        double dz = s[t] * X[i * (int64_t)d + t] - s[t] * X[j * (int64_t)d + t];
+        acc = acc + dz * dz;
+    }
+    return sqrt(acc);
+}
+
+/* Phi_j, Omega_j of every label 0..k-1 and R = the largest ratio; jstar is
+ * the smallest label with that ratio. */
+int oracle_ik_fixed(const double *X, int64_t n, int32_t d, const double *s, double sigma,
+                    const int32_t *parent, const int32_t *labels, int64_t k,
+                    double *phi_k, double *omega_k, int32_t *jstar, double *R)
+{
+    if (n < 1 || d < 1 || k < 1 || !(sigma > 0.0)) return -1;
+    for (int64_t j = 0; j < k; ++j) { phi_k[j] = 0.0; omega_k[j] = 0.0; }
+    for (int64_t v = 0; v < n; ++v) {           /* boundary edges: one end in A_j */
+        int64_t u = parent[v];
+        if (u < 0) continue;
+        int32_t a = labels[v], b = labels[u];
+        if (a == b) continue;
+        double f = exp(-zdist(X, s, d, v, u) / sigma);
+        if (a >= 0 && a < k) phi_k[a] = phi_k[a] + f;
+        if (b >= 0 && b < k) phi_k[b] = phi_k[b] + f;
+    }
+    double *om = (double *)malloc(sizeof(double) * n);
+    if (!om) return -2;
+#pragma omp parallel for schedule(dynamic, 16) num_threads(g_threads)
+    for (int64_t i = 0; i < n; ++i) {            /* eq. omega of each labelled point */
+        om[i] = 0.0;
+        if (labels[i] < 0 || labels[i] >= k) continue;
+        double w = 0.0;
+        for (int64_t j = 0; j < n; ++j)
+            if (j != i) w = w + exp(-zdist(X, s, d, i, j) / sigma);
+        om[i] = w;
+    }
+    for (int64_t i = 0; i < n; ++i)
+        if (labels[i] >= 0 && labels[i] < k) omega_k[labels[i]] = omega_k[labels[i]] + om[i];
+    free(om);
+    int32_t best = 0;
+    for (int64_t j = 1; j < k; ++j)
+        if (phi_k[j] / omega_k[j] > phi_k[best] / omega_k[best]) best = (int32_t)j;
+    *jstar = best;
+    *R = phi_k[best] / omega_k[best];
+    return 0;
+}
+
+/* dR/dX (n x d), dR/ds (d), dR/dsigma for the set jstar, and R itself. */
+int oracle_ik_grad(const double *X, int64_t n, int32_t d, const double *s, double sigma,
+                   const int32_t *parent, const int32_t *labels, int32_t jstar,
+                   double *dX, double *ds, double *dsigma, double *R)
+{
+    if (n < 1 || d < 1 || !(sigma > 0.0)) return -1;
+    double *gphi = (double *)calloc((size_t)n * d, sizeof(double));   /* dPhi/dz */
+    double *gom = (double *)calloc((size_t)n * d, sizeof(double));    /* dOmega/dz */
+    double *rowsig = (double *)calloc((size_t)n, sizeof(double));
+    double *rowom = (double *)calloc((size_t)n, sizeof(double));
+    if (!gphi || !gom || !rowsig || !rowom) { free(gphi); free(gom); free(rowsig); free(rowom); return -2; }
+    double Phi = 0.0, dPhi_sig = 0.0;
+    for (int64_t v = 0; v < n; ++v) {
+        int64_t u = parent[v];
+        if (u < 0) continue;
+        if ((labels[v] == jstar) == (labels[u] == jstar)) continue;     /* not in dA* */
+        double r = zdist(X, s, d, v, u);
+        double f = exp(-r / sigma);
+        Phi = Phi + f;
+        dPhi_sig = dPhi_sig + f * r / (sigma * sigma);
+        if (r > 0.0) {
+            double c = -f / (sigma * r);
+            for (int32_t t = 0; t < d; ++t) {
+                double dz = s[t] * X[v * (int64_t)d + t] - s[t] * X[u * (int64_t)d + t];
+                gphi[v * (int64_t)d + t] = gphi[v * (int64_t)d + t] + c * dz;
+                gphi[u * (int64_t)d + t] = gphi[u * (int64_t)d + t] - c * dz;
+            }
+        }
+    }
+    /* Omega: rows of A* collect their own terms; every row collects the
+     * terms where it is the partner j (two passes keep each row's sum in a
+     * fixed order) */
+#pragma omp parallel for schedule(dynamic, 16) num_threads(g_threads)
+    for (int64_t i = 0; i < n; ++i) {
+        double *g = gom + i * (int64_t)d;
+        double sw = 0.0, sg = 0.0;
+        const int in_i = labels[i] == jstar;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            const int in_j = labels[j] == jstar;
+            if (!in_i && !in_j) continue;
+            double r = zdist(X, s, d, i, j);
+            double w = exp(-r / sigma);
+            if (in_i) { sw = sw + w; sg = sg + w * r / (sigma * sigma); }
+            if (r > 0.0) {
+                /* (i in A*, j): -w/(sigma r) (z_i - z_j) on z_i;
+                 * (j in A*, i): -w/(sigma r) (z_j - z_i) on z_i as the partner */
+                double c = -w / (sigma * r) * (double)(in_i + in_j);
+                for (int32_t t = 0; t < d; ++t) {
+                    double dz = s[t] * X[i * (int64_t)d + t] - s[t] * X[j * (int64_t)d + t];
+                    g[t] = g[t] + c * dz;
+                }
+            }
+        }
+        rowom[i] = sw;
+        rowsig[i] = sg;
+    }
+    double Omega = 0.0, dOm_sig = 0.0;
+    for (int64_t i = 0; i < n; ++i) { Omega = Omega + rowom[i]; dOm_sig = dOm_sig + rowsig[i]; }
+    double Rv = Phi / Omega;
+    for (int32_t t = 0; t < d; ++t) ds[t] = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int32_t t = 0; t < d; ++t) {
+            double gz = (gphi[i * (int64_t)d + t] - Rv * gom[i * (int64_t)d + t]) / Omega;
+            dX[i * (int64_t)d + t] = gz * s[t];
+            ds[t] = ds[t] + gz * X[i * (int64_t)d + t];
+        }
+    *dsigma = (dPhi_sig - Rv * dOm_sig) / Omega;
+    *R = Rv;
+    free(gphi); free(gom); free(rowsig); free(rowom);
+    return 0;
+}

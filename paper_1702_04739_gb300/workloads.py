@@ -14,6 +14,10 @@ input carries no ordering by cluster.
                     1% density, 10 groups sharing support pools, rows
                     L2-normalised, FP32
   table1_shape      blobs at a (n, k, d) shape of the paper's Table 1
+  moons_embedded    n = 20,000, d = 128: 3 interleaved half-circle arcs (radius
+                    1) in 2-D, embedded by the first 2 columns of a random
+                    orthogonal matrix, plus N(0, 0.1^2) noise in all 128
+                    dimensions, FP32 (the differentiation workload)
   batched_sets      4,096 independent sets, sizes log-uniform in [64, 8192],
                     d = 32, each 2-8 isotropic blobs (std 1, centres
                     U[-10,10]^32, equal split), k = its blob count, FP32
@@ -182,11 +186,37 @@ def batched_sets(seed: int = 0, nsets: int = 4096, n_lo: int = 64, n_hi: int = 8
     return np.ascontiguousarray(np.concatenate(parts).astype(dtype)), offsets, ks
 
 
+def moons_embedded(seed: int = 0, n: int = 20_000, d: int = 128, noise: float = 0.1, dtype=np.float32):
+    """Three half-circle arcs of radius 1 interleaved along x (up, down, up:
+    centres (0, 0), (1, 0.5) flipped, (2, 0)), equal sizes, embedded in d
+    dimensions by the first two columns of a sign-fixed random orthogonal
+    matrix, plus isotropic Gaussian noise.  Returns (X, true_labels)."""
+    rng = np.random.default_rng(seed)
+    sizes = _largest_remainder(np.ones(3), n)
+    parts, ys = [], []
+    for m, cnt in enumerate(sizes):
+        t = rng.uniform(0.0, np.pi, size=int(cnt))
+        if m == 1:
+            P = np.stack([1.0 - np.cos(t), 0.5 - np.sin(t)], axis=1)
+        else:
+            P = np.stack([2.0 * (m // 2) + np.cos(t), np.sin(t)], axis=1)
+        parts.append(P)
+        ys.append(np.full(int(cnt), m))
+    P = np.concatenate(parts)
+    G = rng.standard_normal((d, d))
+    Q, R = np.linalg.qr(G)
+    Q = Q * np.sign(np.diag(R))[None, :]
+    X = P @ Q[:, :2].T + noise * rng.standard_normal((P.shape[0], d))
+    X, y = _shuffle(rng, X, np.concatenate(ys))
+    return X.astype(dtype), y.astype(np.int32)
+
+
 CONFIGS = {
     "blobs_n2000_d8": dict(gen="blobs_isotropic", n=2000, d=8, k=5, sigma=1.0, dtype="f64"),
     "blobs_n100k_d64": dict(gen="blobs_anisotropic", n=100_000, d=64, k=20, sigma=1.0, dtype="f32"),
     "sparse_n50k_d4096": dict(gen="sparse_groups", n=50_000, d=4096, k=10, sigma=1.0, dtype="f32"),
     "batched_4096_d32": dict(gen="batched_sets", nsets=4096, d=32, sigma=1.0, dtype="f32"),
+    "moons_n20k_d128": dict(gen="moons_embedded", n=20_000, d=128, k=3, sigma=1.0, dtype="f32"),
 }
 
 
@@ -197,6 +227,8 @@ def make(config: str, seed: int = 0):
         X, _ = blobs_isotropic(seed)
     elif c["gen"] == "blobs_anisotropic":
         X, _ = blobs_anisotropic(seed)
+    elif c["gen"] == "moons_embedded":
+        X, _ = moons_embedded(seed)
     else:
         X, _ = sparse_groups(seed)
     return X, c["k"], c["sigma"]
