@@ -278,6 +278,41 @@ isoclust_status isoclust_cluster_batched_detail(const void *X, const int64_t *of
                                                 double *beta, int32_t *parent, double *phi_par,
                                                 double *omega, void *stream);
 
+/*
+ * isoclust_scale_features -- Z = scale (.) X per feature (z_it = scale_t x_it,
+ * formed in FP64 and stored in X's dtype): the points of a forward call with
+ * a per-feature scale.  X, Z: n x d device arrays of dtype; scale: [d]
+ * double (device).  Synchronous on `stream`.
+ */
+isoclust_status isoclust_scale_features(const void *X, int64_t n, int32_t d, int32_t dtype,
+                                        const double *scale, void *Z, void *stream);
+
+/*
+ * isoclust_ik_backward -- the derivative of i_k (alpha = 0) through the
+ * tree and the subpartition of a forward call on z = scale (.) x, held fixed
+ * (eq. phi, eq. omega; the cost of Section 2.1).  A* is the label of the
+ * largest ratio phi(dA_j) / omega(A_j), picked from the forward's phi_par /
+ * omega; everything else is recomputed in FP64 from X, scale and sigma:
+ *   i_k = Phi / Omega,  Phi = sum of phi over the tree edges with one end in
+ *   A*,  Omega = sum over A* of eq. omega,  dR = (dPhi - i_k dOmega) / Omega.
+ *   X        n x d points (device, F32 or F64) before scaling.
+ *   scale    [d] double (device); sigma > 0 (host).
+ *   parent, labels, phi_par, omega: [n] from isoclust_cluster_detail on the
+ *            scaled points (device); k as in that call.
+ *   grad_ik  upstream gradient of i_k (host scalar).
+ *   dX [n x d] double, dscale [d] double, dsigma [1] double (device, written):
+ *            grad_ik times the derivative; i_k [1] double (device, may be
+ *            NULL): the FP64 value of i_k on the fixed structure.
+ * Coincident points (zero distance) contribute no direction.  Errors:
+ * INVALID_ARG for a NULL pointer, sigma <= 0, a label in 0..k-1 without
+ * points; K_GT_N for k > n.  Synchronous on `stream`.
+ */
+isoclust_status isoclust_ik_backward(const void *X, int64_t n, int32_t d, int32_t dtype,
+                                     const double *scale, double sigma, const int32_t *parent,
+                                     const int32_t *labels, int32_t k, const double *phi_par,
+                                     const double *omega, double grad_ik, double *dX,
+                                     double *dscale, double *dsigma, double *i_k, void *stream);
+
 /* Per-stage device times (milliseconds, CUDA events on the call's stream)
  * of the last isoclust_cluster / _detail / _batched call on this host thread:
  * t[0] validation, t[1] weights, t[2] MST, t[3] tree orientation + stats,

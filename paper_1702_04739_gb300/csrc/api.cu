@@ -28,6 +28,14 @@ cudaError_t weights_launch_sym_sets(const float *Xp, int64_t n_pad, int32_t d, d
                                     const int64_t *tile0, const int64_t *ntl, const int64_t *item0, int64_t max_n,
                                     unsigned long long *tile_counts, cudaStream_t s);
 
+size_t adjoint_bytes(int64_t n, int32_t d, int32_t k);
+cudaError_t adjoint_launch(const void *X, int32_t dtype, int64_t n, int32_t d, const double *scale, double sigma,
+                           const int32_t *parent, const int32_t *labels, int32_t k, const double *phi_par,
+                           const double *omega, double grad, double *dX, double *dscale, double *dsigma, double *ik,
+                           void *ws, uint32_t *status, cudaStream_t s);
+cudaError_t scale_rows_launch(const void *X, int32_t dtype, int64_t n, int32_t d, const double *scale, void *Z,
+                              cudaStream_t s);
+
 static std::atomic<long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
@@ -842,6 +850,52 @@ isoclust_status isoclust_cluster_batched_detail(const void *X, const int64_t *of
                                                 double *omega, void *stream) {
     return cluster_sets_impl(X, offsets, nsets, d, dtype, ks, sigma, opts, labels, residual, i_k, beta, parent, phi_par,
                              omega, (cudaStream_t)stream);
+}
+
+isoclust_status isoclust_scale_features(const void *X, int64_t n, int32_t d, int32_t dtype, const double *scale,
+                                        void *Z, void *stream) {
+    isoclust_status st;
+    if ((st = check_points(X, n, d, dtype, 1))) return st;
+    if (!scale || !Z) return fail(ISOCLUST_ERR_INVALID_ARG, "scale and Z are required");
+    cudaStream_t s = (cudaStream_t)stream;
+    ISO_CUDA(scale_rows_launch(X, dtype, n, d, scale, Z, s));
+    ISO_CUDA(cudaStreamSynchronize(s));
+    return ISOCLUST_OK;
+}
+
+isoclust_status isoclust_ik_backward(const void *X, int64_t n, int32_t d, int32_t dtype, const double *scale,
+                                     double sigma, const int32_t *parent, const int32_t *labels, int32_t k,
+                                     const double *phi_par, const double *omega, double grad_ik, double *dX,
+                                     double *dscale, double *dsigma, double *i_k, void *stream) {
+    isoclust_status st;
+    if ((st = check_points(X, n, d, dtype, 2))) return st;
+    if (!scale || !parent || !labels || !phi_par || !omega || !dX || !dscale || !dsigma)
+        return fail(ISOCLUST_ERR_INVALID_ARG, "a required pointer is NULL");
+    if (k < 1) return fail(ISOCLUST_ERR_INVALID_ARG, "k = %d must be >= 1", k);
+    if (k > n) return fail(ISOCLUST_ERR_K_GT_N, "k = %d exceeds n = %lld", k, (long long)n);
+    if (!(sigma > 0.0) || !isfinite(sigma)) return fail(ISOCLUST_ERR_INVALID_ARG, "sigma must be finite and > 0");
+    if (!isfinite(grad_ik)) return fail(ISOCLUST_ERR_INVALID_ARG, "grad_ik must be finite");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int dev = current_device();
+    std::lock_guard<std::mutex> lock(g_call_mu[dev]);
+    const size_t ws_bytes = adjoint_bytes(n, d, k) + 4096;
+    void *base = scratch_acquire(ws_bytes + 256, s, &st);
+    if (!base) return st;
+    uint32_t *status = (uint32_t *)base;
+    void *ws = (char *)base + 256;
+    Events ev;
+    ev.rec(0, s);
+    ISO_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t), s));
+    ISO_CUDA(adjoint_launch(X, dtype, n, d, scale, sigma, parent, labels, k, phi_par, omega, grad_ik, dX, dscale,
+                            dsigma, i_k, ws, status, s));
+    ev.rec(1, s);
+    ISO_CUDA(cudaStreamSynchronize(s));
+    uint32_t hst = 0;
+    ISO_CUDA(cudaMemcpy(&hst, status, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < 6; ++i) g_prof_ms[i] = 0.0;
+    g_prof_ms[4] = ev.ms(0, 1);
+    if (hst & DEV_NEGATIVE) return fail(ISOCLUST_ERR_INVALID_ARG, "a label 0..k-1 has no points or no positive omega");
+    return map_status(hst, true);
 }
 
 isoclust_status isoclust_vertex_weights(const void *X, int64_t n, int32_t d, int32_t dtype, double sigma,

@@ -85,6 +85,11 @@ def load(build_if_missing: bool = True):
         lib.isoclust_cluster_batched_detail.restype = ctypes.c_int
         lib.isoclust_cluster_batched_detail.argtypes = [_P, _P, _I32, _I32, _I32, _P, _D, _P, _P, _P, _P, _P,
                                                         _P, _P, _P, _P]
+        lib.isoclust_scale_features.restype = ctypes.c_int
+        lib.isoclust_scale_features.argtypes = [_P, _I64, _I32, _I32, _P, _P, _P]
+        lib.isoclust_ik_backward.restype = ctypes.c_int
+        lib.isoclust_ik_backward.argtypes = [_P, _I64, _I32, _I32, _P, _D, _P, _P, _I32, _P, _P, _D, _P, _P, _P, _P,
+                                             _P]
         lib.isoclust_last_profile.restype = None
         lib.isoclust_last_profile.argtypes = [_P, _P]
         lib.isoclust_last_omega_tiles.restype = None
@@ -280,6 +285,67 @@ def cluster_batched(X: torch.Tensor, offsets, ks, sigma: float, o: Opts | None =
             xp, off, nsets, d, dt, kk, float(sigma), _opts_ptr(o),
             *[out[key].data_ptr() for key in ("labels", "residual", "i_k", "beta")], _stream(dev)))
     return out
+
+
+def scale_features(X: torch.Tensor, scale: torch.Tensor) -> torch.Tensor:
+    """Z = scale (.) X per feature, formed in FP64 on the device (isoclust_scale_features)."""
+    lib = load()
+    xp, n, d, dt = _points(X)
+    sp = _dev_ptr(scale, torch.float64)
+    if scale.numel() != d:
+        raise ValueError("scale must have one entry per feature")
+    Z = torch.empty_like(X)
+    _check(lib.isoclust_scale_features(xp, n, d, dt, sp, Z.data_ptr(), _stream(X.device)))
+    return Z
+
+
+def ik_backward(X: torch.Tensor, scale: torch.Tensor, sigma: float, parent, labels, k: int, phi_par, omega,
+                grad_ik: float = 1.0) -> dict:
+    """Derivative of i_k through a forward call's fixed tree and subpartition
+    (isoclust_ik_backward): dX [n, d], dscale [d], dsigma [1] in FP64, times
+    grad_ik, and the FP64 i_k of that structure."""
+    lib = load()
+    xp, n, d, dt = _points(X)
+    dev = X.device
+    out = dict(dX=torch.empty((n, d), dtype=torch.float64, device=dev),
+               dscale=torch.empty(d, dtype=torch.float64, device=dev),
+               dsigma=torch.empty(1, dtype=torch.float64, device=dev),
+               i_k=torch.empty(1, dtype=torch.float64, device=dev))
+    _check(lib.isoclust_ik_backward(
+        xp, n, d, dt, _dev_ptr(scale, torch.float64), float(sigma), _dev_ptr(parent, torch.int32),
+        _dev_ptr(labels, torch.int32), int(k), _dev_ptr(phi_par, torch.float64), _dev_ptr(omega, torch.float64),
+        float(grad_ik), out["dX"].data_ptr(), out["dscale"].data_ptr(), out["dsigma"].data_ptr(),
+        out["i_k"].data_ptr(), _stream(dev)))
+    return out
+
+
+class IsoperimetricNumber(torch.autograd.Function):
+    """i_k of the points scale (.) X (alpha = 0) as a differentiable function
+    of X, the per-feature scale and sigma, through the fixed tree and
+    subpartition of the forward pass.  Returns (i_k, labels); labels are not
+    differentiable.
+
+        ik, labels = IsoperimetricNumber.apply(X, scale, sigma, k)
+    """
+
+    @staticmethod
+    def forward(ctx, X, scale, sigma, k):
+        s64 = scale.detach().to(torch.float64).contiguous()
+        Z = scale_features(X.detach().contiguous(), s64)
+        out = cluster_detail(Z, int(k), float(sigma))
+        ctx.save_for_backward(X.detach(), s64, out["parent"], out["labels"], out["phi_par"], out["omega"])
+        ctx.sigma = float(sigma)
+        ctx.k = int(k)
+        ctx.sigma_is_tensor = isinstance(sigma, torch.Tensor)
+        ctx.mark_non_differentiable(out["labels"])
+        return out["i_k"].reshape(()).clone(), out["labels"]
+
+    @staticmethod
+    def backward(ctx, g_ik, g_labels):
+        X, s64, parent, labels, phi, omega = ctx.saved_tensors
+        g = ik_backward(X.contiguous(), s64, ctx.sigma, parent, labels, ctx.k, phi, omega, float(g_ik))
+        dsig = g["dsigma"].reshape(()) if ctx.sigma_is_tensor else None
+        return g["dX"], g["dscale"], dsig, None
 
 
 def kernel_launches() -> int:
