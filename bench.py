@@ -8,11 +8,14 @@ labels.  Inputs are resident in HBM; L2 is flushed (a 256 MiB write) before
 every step inside the timed region.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                  [--workload blobs_n100k_d64|batched_4096_d32]
+                  [--workload blobs_n100k_d64|batched_4096_d32|moons_n20k_d128]
 
 --workload batched_4096_d32 times isoclust_cluster_batched on 4,096
 independent sets (sizes log-uniform in [64, 8192], d = 32, 2-8 blobs each,
-k = blob count): one step = one call over all sets.
+k = blob count): one step = one call over all sets.  --workload
+moons_n20k_d128 times the differentiable path on 20,000 interleaved-moons
+points in 128 dimensions (k = 3): one step = the scaled forward call plus
+the FP64 backward of i_k in X, the per-feature scale and sigma.
 
 N > 1 (torchrun, one rank per GPU): every rank clusters its own independent
 point set (replicas; the path has no cross-GPU exchange), value = total
@@ -39,6 +42,8 @@ METRIC = "points/s end-to-end"
 UNIT = "points/s"
 WORKLOAD = "blobs_n100k_d64"
 BATCHED = "batched_4096_d32"
+MOONS = "moons_n20k_d128"
+FP64_PER_SM_CLK = 2          # DFMA per clock per SM (ncu peak of sm__sass_thread_inst_executed_op_dfma)
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP32_LANES_PER_SM = 128
 
@@ -177,13 +182,15 @@ def main():
     ap.add_argument("--no-mst-compare", action="store_true")
     ap.add_argument("--n", type=int, default=0,
                     help="points of the same generator (profiling of a smaller case); default: the full 100,000")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, BATCHED])
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, BATCHED, MOONS])
     ap.add_argument("--nsets", type=int, default=0, help="batched: fewer sets of the same recipe (profiling)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         args.warmup = 3
     if args.workload == BATCHED:
         return main_batched(args)
+    if args.workload == MOONS:
+        return main_moons(args)
 
     from paper_1702_04739_gb300 import workloads
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -535,6 +542,129 @@ def main_batched(args):
     if pg is not None:
         pg.barrier()
         pg.destroy_process_group()
+    return 0
+
+
+# ---------------------------------------------------------------- differentiation
+def _moons_cpu(X, k, sigma, n_sample=12000):
+    """Oracle forward + FP64 gradient on the first n_sample points, scaled to
+    n by the O(n^2) cost of both."""
+    import oracle
+    oracle.build()
+    cores = _cpu_cores()
+    oracle.set_threads(cores)
+    Xs = np.ascontiguousarray(X[:n_sample]).astype(np.float64)
+    s = np.ones(X.shape[1])
+    t0 = time.perf_counter()
+    f = oracle.cluster(Xs * s, k, sigma)
+    fx = oracle.ik_fixed(Xs, s, sigma, f["parent"], f["labels"], k)
+    oracle.ik_grad(Xs, s, sigma, f["parent"], f["labels"], fx["jstar"])
+    t = time.perf_counter() - t0
+    scale = (X.shape[0] / n_sample) ** 2
+    return X.shape[0] / (t * scale), t, cores, n_sample
+
+
+def main_moons(args):
+    from paper_1702_04739_gb300 import workloads
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    X, k, sigma = workloads.make(MOONS, seed=rank)
+    n, d = X.shape
+    cfg = {"workload": MOONS, "n": n, "d": d, "k": k, "sigma": sigma, "storage": "f32",
+           "gradient": "FP64, d i_k / d(X, scale, sigma) through the fixed tree and subpartition"}
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        vals = [_moons_cpu(X, k, sigma) for _ in range(max(args.steps, 1))]
+        value = statistics.mean(v[0] for v in vals)
+        t, cores, ns = vals[-1][1], vals[-1][2], vals[-1][3]
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": 0, "ms_per_step": n / value * 1000.0, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                 "sample": f"forward + gradient on the first {ns} points, {t:.2f} s; scaled by (n/{ns})^2"},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
+    import torch
+    from paper_1702_04739_gb300 import isoclust
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    Xd = torch.from_numpy(X).to(dev)
+    sd = torch.ones(d, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    times = {}
+
+    def step():
+        flush.zero_()
+        Z = isoclust.scale_features(Xd, sd)
+        out = isoclust.cluster_detail(Z, k, sigma)
+        times["fwd"] = isoclust.last_profile()
+        g = isoclust.ik_backward(Xd, sd, sigma, out["parent"], out["labels"], k, out["phi_par"], out["omega"], 1.0)
+        times["bwd_ms"] = isoclust.last_profile()["search_ms"]
+        return out, g
+
+    for _ in range(args.warmup):
+        out, g = step()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    l0 = isoclust.kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    bwd = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        out, g = step()
+        bwd.append(times["bwd_ms"])
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    launches = isoclust.kernel_launches() - l0
+    clk = clocks.stop()
+    ms_per_step = ev0.elapsed_time(ev1) / args.steps
+    value = world * n / (ms_per_step / 1000.0)
+    # FP64 work of the pair kernel: |A*| n + (n - |A*|) |A*| ordered pairs,
+    # each 3d (distance) + 2d (matrix product) + ~30 (sqrt, exp, quotients) flops
+    lab = out["labels"].cpu().numpy()
+    par = out["parent"].cpu().numpy()
+    phi = out["phi_par"].cpu().numpy()
+    om = out["omega"].cpu().numpy()
+    ratios = []
+    for j in range(k):
+        inj = lab == j
+        cross = (par >= 0) & (inj != inj[np.maximum(par, 0)])
+        ratios.append(phi[cross].sum() / om[inj].sum())
+    a = int((lab == int(np.argmax(ratios))).sum())
+    pairs = a * n + (n - a) * a
+    flop = pairs * (5.0 * d + 30.0)
+    b_ms = statistics.mean(bwd)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks, src = _peaks()
+    fp64_peak = sms * FP64_PER_SM_CLK * 2.0 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 forward, f64 gradient", "data": "synthetic",
+        "config": dict(cfg, l2="flushed by a 256 MiB write before every step (inside the timed region)"),
+        "roofline": {"bound": "fp64", "achieved": flop / (b_ms / 1000.0) / 1e12, "peak": fp64_peak,
+                     "unit": "TFLOP/s", "frac": flop / (b_ms / 1000.0) / 1e12 / fp64_peak, "traffic": None,
+                     "kernel": "k_omega_grad (backward pair sums, FP64)",
+                     "note": f"{pairs} ordered pairs (|A*| = {a}) x (5d + 30) flop over the backward's event time "
+                             f"({b_ms:.2f} ms); peak = {sms} SMs x {FP64_PER_SM_CLK} DFMA x 2 flop x max SM clock"},
+        "stages_ms": {"forward_ms": round(sum(times["fwd"][key] for key in ("validate_ms", "weights_ms", "mst_ms",
+                                                                          "orient_ms", "search_ms", "labels_ms")), 3),
+                      "backward_ms": round(b_ms, 3)},
+        "gpu_launches": int(launches), "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        v, t, cores, ns = _moons_cpu(X, k, sigma)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"oracle forward + FP64 gradient on the first {ns} points took {t:.2f} s "
+                                          f"on {cores} threads; scaled by (n/{ns})^2"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     return 0
 
 

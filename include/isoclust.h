@@ -316,7 +316,8 @@ isoclust_status isoclust_ik_backward(const void *X, int64_t n, int32_t d, int32_
 /* Per-stage device times (milliseconds, CUDA events on the call's stream)
  * of the last isoclust_cluster / _detail / _batched call on this host thread:
  * t[0] validation, t[1] weights, t[2] MST, t[3] tree orientation + stats,
- * t[4] bisection, t[5] labels.  counts[0] = Boruvka rounds, counts[1] =
+ * t[4] bisection, t[5] labels (after isoclust_ik_backward: t[4] is the
+ * backward's time, the others 0).  counts[0] = Boruvka rounds, counts[1] =
  * rows rescanned after a candidate-margin overflow, counts[2] = Algorithm-1
  * passes, counts[3] = tree depth.  Either pointer may be NULL. */
 void isoclust_last_profile(double *t_ms6, int64_t *counts4);
