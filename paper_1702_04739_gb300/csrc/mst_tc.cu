@@ -15,8 +15,8 @@
 //               TMEM lane quadrant w mod 4 and one 64-column half of the
 //               tile, one row per thread), d2 = n_i + n_j - 2g, same-component
 //               mask, and a running best-8 of half-tiles per row.
-// Two TMEM accumulators (2 x 128 columns) let the MMA of the next column
-// tile overlap the epilogue of the current one.  Every mbarrier wait is
+// Four TMEM accumulators (4 x 128 columns) let the MMAs of the next column
+// tiles run ahead of the epilogue of the current one.  Every mbarrier wait is
 // bounded; on timeout the kernel raises an error flag and stops.
 // The candidates are exact-keyed in FP64 by k_recheck_tc inside a rigorous
 // error margin; rows whose margin is not closed by the best 8 are rescanned.
@@ -35,6 +35,7 @@ constexpr int TC_AREG_BYTES = 4 * 128 * 64 * 2;           // A hi + lo, up to 2 
 constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 2;         // 16 KB
 constexpr int TC_STAGE_BYTES = 4 * TC_TILE_BYTES;        // A hi, A lo, B hi, B lo
 constexpr int TC_EPI_WARPS = 8;                           // two per TMEM lane quadrant
+constexpr int TC_NACC = 4;                                // TMEM accumulators (4 x 128 columns = all 512)
 constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;
 constexpr int TC_TOPK = 8;                                // best half-tiles kept per (list, row)
 constexpr int TC_CW = TC_BN / 2;                          // columns per candidate (half-tile)
@@ -43,10 +44,10 @@ constexpr long long TC_WAIT_CYCLES = 4000000000LL;
 
 // Column metadata first: the epilogue reads it with 16-byte vector loads.
 struct __align__(16) TcShared {
-    float cnorm[2][TC_BN];
-    int32_t ccomp[2][TC_BN];
+    float cnorm[TC_NACC][TC_BN];
+    int32_t ccomp[TC_NACC][TC_BN];
     uint64_t full[4], empty[4];
-    uint64_t acc_full[2], acc_empty[2];
+    uint64_t acc_full[TC_NACC], acc_empty[TC_NACC];
     uint64_t a_full, a_empty;
     uint32_t tmem_base;
     uint32_t pad;
@@ -196,7 +197,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
             mbar_init(&sh->full[s], 1);
             mbar_init(&sh->empty[s], 1);
         }
-        for (int a = 0; a < 2; ++a) {
+        for (int a = 0; a < TC_NACC; ++a) {
             mbar_init(&sh->acc_full[a], 1);
             mbar_init(&sh->acc_empty[a], TC_EPI_WARPS);
         }
@@ -205,7 +206,8 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(&sh->tmem_base))
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh->tmem_base)),
+                     "n"(TC_NACC * TC_BN)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -312,7 +314,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
                     }
                     if (!ok) break;
                     mma_commit(&sh->acc_full[acc]);
-                    if (++acc == 2) { acc = 0; acc_phase ^= 1u; }
+                    if (++acc == TC_NACC) { acc = 0; acc_phase ^= 1u; }
                 }
                 if (ARES && ok) {
                     mma_commit(&sh->a_empty);     // A region free once this item's MMAs are done
@@ -403,7 +405,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sh->acc_empty[acc]);
-                if (++acc == 2) { acc = 0; acc_phase ^= 1u; }
+                if (++acc == TC_NACC) { acc = 0; acc_phase ^= 1u; }
                 m = __fadd_rn(m, nrow);
                 // rigorous bounds of the half-tile's smallest d2 of the represented
                 // points: accumulation + dropped lo.lo (A s_i s_j) and FP32
@@ -425,7 +427,8 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TC_NACC * TC_BN)
+                     : "memory");
     }
 }
 
