@@ -489,7 +489,7 @@ __global__ void k_tc_items(const int64_t *__restrict__ tcbase, const int64_t *__
     if (w >= tcbase[nsets]) return;
     const int32_t b = find_set(tcbase, nsets, w);
     const int32_t t0 = (int32_t)(rowbase[b] / 128), nt = (int32_t)(tcbase[b + 1] - tcbase[b]);
-    items[w] = make_int4(t0 + (int32_t)(w - tcbase[b]), t0, t0 + nt, 0);
+    items[w] = make_int4(t0 + (int32_t)(w - tcbase[b]), t0, t0 + nt, b << 4);   // list pair 0, set b
 }
 
 // omega items: the upper triangle of set b's 64-row tile grid, row-major

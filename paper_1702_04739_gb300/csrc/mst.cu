@@ -513,6 +513,7 @@ cudaError_t mst_build(MstScratch &S, const void *X, int64_t n, int32_t d, int dt
     const unsigned rg = round_grid(n);
     cudaError_t e;
     if (tc && (e = tc_prepare(*tc, (const float *)X, n, d, s))) return e;
+    if (tc && (e = tc_count_sets(*tc, S.comp, n, S.counters, s))) return e;
     for (int r = 0; r < R; ++r) {
         k_round_begin<<<rg, TPB, 0, ISO_S(s)>>>(S.counters, S.cd2, S.cpair, n);
         if (tc) {
@@ -531,6 +532,7 @@ cudaError_t mst_build(MstScratch &S, const void *X, int64_t n, int32_t d, int dt
             int32_t *t = na; na = nb; nb = t;
         }
         k_relabel<<<rg, TPB, 0, ISO_S(s)>>>(S.comp, na, n, S.counters);
+        if (tc && (e = tc_count_sets(*tc, S.comp, n, S.counters, s))) return e;
         k_round_end<<<1, 1, 0, ISO_S(s)>>>(S.counters);
     }
     if (tc) k_or_err<<<1, 1, 0, ISO_S(s)>>>(tc->err, status);

@@ -69,6 +69,7 @@ struct TcScratch {
     const int32_t *set_of = nullptr;
     const int64_t *offs = nullptr;
     const int64_t *rowbase = nullptr;
+    int32_t *setcnt = nullptr;                     // components left in each set (independent sets)
     CUtensorMap map_h, map_l;
     // n_pad_rows / nmeans / lists: 0 = one set
     void carve(Arena &A, int64_t n, int32_t d, int splits, int64_t n_pad_rows = 0, int nmeans = 1, int lists = 0);
@@ -78,6 +79,8 @@ bool tc_supported();
 cudaError_t tc_prepare(TcScratch &T, const float *X, int64_t n, int32_t d, cudaStream_t s);
 cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t n, int32_t d, uint32_t *status,
                            cudaStream_t s);
+// independent sets: recount the components of every set from comp
+cudaError_t tc_count_sets(TcScratch &T, const int32_t *comp, int64_t n, const int32_t *counters, cudaStream_t s);
 
 // Builds the MST of X (n x d, dtype F32/F64) into S.eu/ev/ed2 (unsorted).
 // tc != nullptr selects the tensor-core sweep (F32 input).

@@ -180,8 +180,9 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
            const float *__restrict__ rnorm, const float *__restrict__ cnorm, const float *__restrict__ rsq,
            const float *__restrict__ tmax, const float *__restrict__ tsq, float acoef, float bcoef,
            const int32_t *__restrict__ comp, int64_t nrows, int ntiles, int kchunks, int splits,
-           const int4 *__restrict__ witems, int64_t nwitems, const int32_t *counters, float *__restrict__ out_v,
-           int32_t *__restrict__ out_j, float *__restrict__ out_u, uint32_t *err) {
+           const int4 *__restrict__ witems, int64_t nwitems, const int32_t *__restrict__ setcnt,
+           const int32_t *counters, float *__restrict__ out_v, int32_t *__restrict__ out_j, float *__restrict__ out_u,
+           uint32_t *err) {
     if (!mst_active(counters)) return;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -217,13 +218,16 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
     const uint32_t tmem = sh->tmem_base;
 
     // work item w: row tile rt against column tiles [c0, c1), candidate list
-    // pair sp; either from the item list or row tile x column split
+    // pair sp; either from the item list (sp in the low 4 bits, the set
+    // above: items of a set whose forest is complete are skipped) or row tile
+    // x column split
     const int64_t items = witems ? nwitems : (int64_t)ntiles * splits;
     const int tiles_per_split = (ntiles + splits - 1) / splits;
     auto item = [&](int64_t w, int &rt, int &c0, int &c1, int &sp) {
         if (witems) {
             const int4 it = witems[w];
-            rt = it.x; c0 = it.y; c1 = it.z; sp = it.w;
+            rt = it.x; c0 = it.y; c1 = it.z; sp = it.w & 15;
+            if (setcnt && setcnt[it.w >> 4] <= 1) c1 = c0;      // nothing left to join in this set
         } else {
             rt = (int)(w / splits);
             sp = (int)(w % splits);
@@ -574,6 +578,15 @@ __global__ void k_tc_gather_comp(const int32_t *__restrict__ comp, const int32_t
     }
 }
 
+// components of each set: the roots of comp counted per set
+__global__ void k_tc_set_roots(const int32_t *__restrict__ comp, const int32_t *__restrict__ set_of, int64_t n,
+                               int32_t *__restrict__ setcnt, const int32_t *counters) {
+    if (!mst_active(counters)) return;
+    const int64_t gs = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gs)
+        if (comp[v] == v) atomicAdd(setcnt + set_of[v], 1);
+}
+
 __global__ void k_tc_fill_lists(float *__restrict__ tv, int32_t *__restrict__ tj, float *__restrict__ tu,
                                 int64_t nv, int64_t nu) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -612,10 +625,15 @@ __device__ __forceinline__ void recheck_row(int64_t r, int lane, const float *__
                                             const unsigned int *__restrict__ nmax_bits, float eps_rep, float mul32,
                                             float add32, int32_t *__restrict__ nsurv, int32_t *__restrict__ surv,
                                             int32_t *__restrict__ rowj, int32_t *__restrict__ ovf,
+                                            const int32_t *__restrict__ set_of, const int32_t *__restrict__ setcnt,
                                             int32_t *counters) {
     if (lane == 0) nsurv[r] = 0;           // every row, padding included: k_exact_tc reads them all
     const int64_t i = perm[r];
     if (i < 0) return;                     // padding row
+    if (setcnt && setcnt[set_of[i]] <= 1) {     // the row's set is one component already
+        if (lane == 0) rowj[i] = -1;
+        return;
+    }
     // ---- merge: each lane holds up to 8 of the lists x 8 entries (lists <= 32);
     //      the best 8 are selected by 8 rounds of a warp arg-min
     constexpr int EPL = 8;
@@ -818,14 +836,15 @@ __global__ void __launch_bounds__(256, 4) k_recheck_tc(const float *__restrict__
                                                        const unsigned int *__restrict__ nmax_bits, float eps_rep,
                                                        float mul32, float add32, int32_t *__restrict__ nsurv,
                                                        int32_t *__restrict__ surv, int32_t *__restrict__ rowj,
-                                                       int32_t *__restrict__ ovf, int32_t *counters) {
+                                                       int32_t *__restrict__ ovf, const int32_t *__restrict__ set_of,
+                                                       const int32_t *__restrict__ setcnt, int32_t *counters) {
     if (!mst_active(counters)) return;
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r = w0; r < n; r += nw)
         recheck_row(r, lane, xs, n, d, lists, tv, tj, tu, rsq, perm, compp, nmax_bits, eps_rep, mul32, add32, nsurv,
-                    surv, rowj, ovf, counters);
+                    surv, rowj, ovf, set_of, setcnt, counters);
 }
 
 // Self-contained rescan of a queued row: FP32 direct differences give the
@@ -960,6 +979,16 @@ void TcScratch::carve(Arena &A, int64_t n, int32_t d, int splits_, int64_t n_pad
     tj = A.take<int32_t>((size_t)lists * n_pad * TC_TOPK);
     tu = A.take<float>((size_t)lists * n_pad);
     err = A.take<uint32_t>(4);
+    setcnt = nmeans > 1 || n_pad_rows > 0 ? A.take<int32_t>((size_t)(nmeans > 0 ? nmeans : 1)) : nullptr;
+}
+
+cudaError_t tc_count_sets(TcScratch &T, const int32_t *comp, int64_t n, const int32_t *counters, cudaStream_t s) {
+    if (!T.set_of || !T.setcnt) return cudaSuccess;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(T.setcnt, 0, sizeof(int32_t) * T.nsets, s))) return e;
+    const int64_t b = ceil_div(n, 256), cap = (int64_t)num_sms() * 8;
+    k_tc_set_roots<<<(unsigned)(b < cap ? b : cap), 256, 0, ISO_S(s)>>>(comp, T.set_of, n, T.setcnt, counters);
+    return cudaGetLastError();
 }
 
 // At most 16 splits: the recheck merges 2 x splits candidate lists in one warp.
@@ -1045,11 +1074,11 @@ cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t 
     if (kchunks <= 2)
         k_sweep_tc<true><<<grid, TC_THREADS, TC_SMEM_ARES, ISO_S(s)>>>(
             T.map_h, T.map_l, T.nrm, T.cnrm, T.rsq, T.tmax, T.tsq, acoef, bcoef, T.compp, T.n_pad, ntiles, kchunks,
-            T.splits, T.items, T.nitems, S.counters, T.tv, T.tj, T.tu, T.err);
+            T.splits, T.items, T.nitems, T.setcnt, S.counters, T.tv, T.tj, T.tu, T.err);
     else
         k_sweep_tc<false><<<grid, TC_THREADS, TC_SMEM_STREAM, ISO_S(s)>>>(
             T.map_h, T.map_l, T.nrm, T.cnrm, T.rsq, T.tmax, T.tsq, acoef, bcoef, T.compp, T.n_pad, ntiles, kchunks,
-            T.splits, T.items, T.nitems, S.counters, T.tv, T.tj, T.tu, T.err);
+            T.splits, T.items, T.nitems, T.setcnt, S.counters, T.tv, T.tj, T.tu, T.err);
     // representation error of a centred point by BF16 hi + lo: 2^-18 relative
     // per element, plus the FP32 rounding of x - c (2^-24); 25 % headroom
     const double eps_rep = 1.25 * (3.814697265625e-06 + 5.9604644775390625e-08);
@@ -1063,7 +1092,7 @@ cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t 
     const int64_t rblocks = ceil_div(T.n_pad * 32, 256), rcap = (int64_t)num_sms() * 16;
     k_recheck_tc<<<(unsigned)(rblocks < rcap ? rblocks : rcap), 256, 0, ISO_S(s)>>>(
         T.xs, T.n_pad, d, T.lists, T.tv, T.tj, T.tu, T.rsq, T.permp, T.compp, T.nmax_bits, (float)(eps_rep * 1.0001),
-        mul32, add32, T.nsurv, T.surv, S.rowj, S.ovf_rows, S.counters);
+        mul32, add32, T.nsurv, T.surv, S.rowj, S.ovf_rows, T.set_of, T.setcnt, S.counters);
     const int64_t xblocks = ceil_div(T.n_pad, 256), xcap = (int64_t)num_sms() * 8;
     k_exact_tc<<<(unsigned)(xblocks < xcap ? xblocks : xcap), 256, 0, ISO_S(s)>>>(T.xs, T.n_pad, d, T.permp, T.nsurv,
                                                                                   T.surv, S.rowd2, S.rowj,

@@ -893,7 +893,13 @@ cudaError_t tree_search_and_label_sets(TreeScratch &S, int32_t nsets, const int6
     if ((e = cudaMemsetAsync(S.dec + (size_t)nv * DP_LANES, DEC_DISCARD, DP_LANES, s))) return e;
     k_stats_sets<<<(unsigned)nsets, 256, 0, ISO_S(s)>>>(T.parent, phi_par, omega, p, offs, SS, S.status);
     DpArgs A{n, T.parent, T.ch_off, T.ch_list, T.leaves, phi_par, omega, p};
-    const unsigned grid = (unsigned)(num_sms() * 8);
+    // one full wave: every warp takes an equal run of leaves, so a partial
+    // second wave would leave SMs idle for half its length
+    static int dp_occ = 0;
+    if (dp_occ == 0 && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&dp_occ, k_dp_pass_sets, 256, 0) != cudaSuccess ||
+                        dp_occ < 1))
+        dp_occ = 4;
+    const unsigned grid = (unsigned)(num_sms() * dp_occ);
     const unsigned gs = (unsigned)ceil_div(nsets, 128);
     for (int pass = 0; pass < DP_SEARCH_PASSES; ++pass) {
         if ((e = cudaMemsetAsync(S.done, 0, sizeof(int32_t) * n, s))) return e;
