@@ -325,7 +325,7 @@ void isoclust_last_profile(double *t_ms6, int64_t *counts4);
 /* Tile pairs of the omega sweep in the last isoclust_cluster / _detail call
  * on this host thread: tiles3[0] = 64x64 tile pairs screened, tiles3[1] =
  * tile pairs evaluated in double-word arithmetic (the rest held only terms
- * below e^-(39 + ln n) of their row's largest term), tiles3[2] = 1 when the
+ * below e^-(36 + ln n) of their row's largest term), tiles3[2] = 1 when the
  * pairs were unordered (symmetric sweep, each pair once for both rows), 0
  * when ordered.  Zero counts when the screen did not run (F64 input,
  * alpha > 0, or the FP64 precision option). */

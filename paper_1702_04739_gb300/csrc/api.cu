@@ -16,12 +16,12 @@ namespace iso {
 cudaError_t weights_launch(const void *X, int64_t n, int32_t d, int dtype, bool fp64_path, double sigma,
                            double alpha, int include_self, const unsigned long long *nnbits, double *omega,
                            double *p, unsigned long long *tile_counts, cudaStream_t s);
-size_t weights_sym_bytes(int64_t n);
+size_t weights_sym_bytes(int64_t n, int32_t d);
 cudaError_t weights_launch_sym(const float *X, int64_t n, int32_t d, double sigma, int include_self,
                                const unsigned long long *nnbits, double *omega, void *part,
                                unsigned long long *tile_counts, cudaStream_t s);
 constexpr size_t SYM_PART_LIMIT = size_t(16) << 30;   // symmetric sweep up to 16 GiB of partials
-size_t weights_sym_sets_bytes(int64_t n_pad, int64_t nitems);
+size_t weights_sym_sets_bytes(int64_t n_pad, int64_t nitems, int32_t d);
 cudaError_t weights_launch_sym_sets(const float *Xp, int64_t n_pad, int32_t d, double sigma, int include_self,
                                     const unsigned long long *nnbits, double *omega, void *part, const int2 *witems,
                                     int64_t nitems, const int32_t *tile_valid, const int32_t *tile_set,
@@ -320,7 +320,7 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
     } P;
     const bool permuted = need_labels && dtype == ISOCLUST_F32 && !fp64_sweep;
     const bool symmetric = permuted && o.alpha == 0.0 && o.omega_mode == ISOCLUST_OMEGA_FULL &&
-                           weights_sym_bytes(n) <= SYM_PART_LIMIT;
+                           weights_sym_bytes(n, d) <= SYM_PART_LIMIT;
     auto carve = [&](Arena &A, MstScratch &M, TreeScratch &TS, double **phi, double **om, double **pp, double **omtmp,
                      uint32_t **status) {
         *status = A.take<uint32_t>(4);
@@ -343,7 +343,7 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
             P.tiles = A.take<unsigned long long>(2);
             P.omp = A.take<double>(n);
             P.pp = A.take<double>(n);
-            if (symmetric) P.sym = (void *)A.take<unsigned char>(weights_sym_bytes(n));
+            if (symmetric) P.sym = (void *)A.take<unsigned char>(weights_sym_bytes(n, d));
         }
     };
     MstScratch M;
@@ -661,7 +661,7 @@ static isoclust_status cluster_sets_impl(const void *X, const int64_t *offsets, 
         B.nnp = A.take<unsigned long long>(n_pad64);
         B.omp = A.take<double>(n_pad64);
         B.tiles = A.take<unsigned long long>(2);
-        B.sym = (void *)A.take<unsigned char>(weights_sym_sets_bytes(n_pad64, nitems));
+        B.sym = (void *)A.take<unsigned char>(weights_sym_sets_bytes(n_pad64, nitems, d));
     };
     Arena meas;
     carve(meas);

@@ -353,6 +353,87 @@ __device__ __forceinline__ void tri_item(int64_t w, int64_t T, int64_t &I, int64
     J = i + (w - (i * T - i * (i - 1) / 2));
 }
 
+// Per 64-row tile: centroid c (FP64 mean, stored FP32), radius r >= the
+// distance of every real row to the stored c (FP64, rounded up), and the
+// largest nearest-neighbour shift of its rows (rounded up).  By the triangle
+// inequality every pair of tiles I, J has distances >= |c_I - c_J| - r_I - r_J.
+__global__ void __launch_bounds__(64) k_tile_bounds(const float *__restrict__ X, int64_t n, int32_t d,
+                                                    const float2 *__restrict__ shdw,
+                                                    const int32_t *__restrict__ tile_valid, float *__restrict__ cen,
+                                                    float *__restrict__ rad, float *__restrict__ msh) {
+    __shared__ double red[64];
+    const int64_t I = blockIdx.x;
+    const int tid = threadIdx.x;
+    const int64_t r0 = I * WT;
+    const int nv = tile_valid ? tile_valid[I] : (int)(n - r0 < WT ? n - r0 : WT);
+    for (int32_t t = tid; t < d; t += 64) {
+        double sum = 0.0;
+        for (int q = 0; q < nv; ++q) sum += (double)X[(r0 + q) * d + t];
+        cen[I * d + t] = nv > 0 ? (float)(sum / (double)nv) : 0.0f;
+    }
+    __syncthreads();
+    double dist = 0.0, sh = 0.0;
+    if (tid < nv) {
+        double acc = 0.0;
+        for (int32_t t = 0; t < d; ++t) {
+            const double df = (double)X[(r0 + tid) * d + t] - (double)cen[I * d + t];
+            acc += df * df;
+        }
+        dist = sqrt(acc);
+        const float2 y = shdw[r0 + tid];
+        sh = (double)y.x + (double)y.y;
+    }
+    red[tid] = dist;
+    __syncthreads();
+    for (int q = 32; q > 0; q >>= 1) {
+        if (tid < q) red[tid] = fmax(red[tid], red[tid + q]);
+        __syncthreads();
+    }
+    if (tid == 0) rad[I] = (float)(red[0] * (1.0 + 1e-6)) * 1.000001f;
+    __syncthreads();
+    red[tid] = sh;
+    __syncthreads();
+    for (int q = 32; q > 0; q >>= 1) {
+        if (tid < q) red[tid] = fmax(red[tid], red[tid + q]);
+        __syncthreads();
+    }
+    if (tid == 0) msh[I] = (float)(red[0] * (1.0 + 1e-6)) * 1.000001f;
+}
+
+// One thread per tile pair w = (I, J): every distance is >= |c_I - c_J| -
+// r_I - r_J; when even that is beyond zskip of both tiles' largest shift, no
+// term of the pair of tiles can matter and the pair is skipped before the
+// per-pair screen.  The FP32 sum carries the pair screen's relative error,
+// hence its shrink; every other step rounds towards the safe side.
+template <bool SETS>
+__global__ void k_tile_pair_skip(const float *__restrict__ cen, const float *__restrict__ rad,
+                                 const float *__restrict__ msh, int32_t d, int64_t T, int64_t nitems,
+                                 const int2 *__restrict__ witems, float is_h, float zskip, float scr_shrink,
+                                 uint8_t *__restrict__ tskip) {
+    const int64_t gs = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nitems; w += gs) {
+        int64_t I, J;
+        if constexpr (SETS) {
+            I = witems[w].x;
+            J = witems[w].y;
+        } else {
+            tri_item(w, T, I, J);
+        }
+        uint8_t skip = 0;
+        if (I != J) {
+            float tot = 0.0f;
+            for (int32_t t = 0; t < d; ++t) {
+                const float df = __fsub_rn(cen[I * d + t], cen[J * d + t]);
+                tot = __fmaf_rn(df, df, tot);
+            }
+            const float lb = __fsub_rd(__fsqrt_rd(__fmul_rd(tot, scr_shrink)), __fadd_ru(rad[I], rad[J]));
+            const float ylb = __fmul_rd(__fmul_rd(lb, is_h), 0.999999f);
+            skip = ylb - fmaxf(msh[I], msh[J]) > zskip ? 1 : 0;
+        }
+        tskip[w] = skip;
+    }
+}
+
 // Symmetric omega sweep: each unordered tile pair is screened in FP32 and,
 // if any of its terms can matter in either direction, evaluated once in
 // double-word arithmetic; the pair's d2 serves both omega_i and omega_j.
@@ -365,14 +446,14 @@ __global__ void __launch_bounds__(TPB, 2)
 k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *__restrict__ shdw,
               float is_h, float is_l, ExpTable tabv, float zskip, float scr_shrink, int64_t T,
               int64_t nitems, const int2 *__restrict__ witems, const int32_t *__restrict__ tile_valid,
-              uint8_t *__restrict__ flags, float2 *__restrict__ rpart, float2 *__restrict__ cpart,
-              unsigned long long *__restrict__ tile_counts) {
+              const uint8_t *__restrict__ tskip, uint8_t *__restrict__ flags, float2 *__restrict__ rpart,
+              float2 *__restrict__ cpart, unsigned long long *__restrict__ tile_counts) {
     __shared__ __align__(16) float As[WDC][WPAD];
     __shared__ __align__(16) float Bs[WDC][WPAD];
     __shared__ float2 tab[64];
     __shared__ float2 mr[WT][17];
     __shared__ float2 mc[WT][17];
-    __shared__ int64_t sIJ[4];
+    __shared__ int64_t sIJ[5];
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     if (tid < 64) tab[tid] = tabv.t[tid];
@@ -390,8 +471,11 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
             } else {
                 tri_item(w, T, sIJ[0], sIJ[1]);
             }
+            sIJ[4] = tskip[w];
+            if (sIJ[4]) flags[w] = 0;
         }
         __syncthreads();
+        if (sIJ[4]) continue;             // the tile bound already rules the pair of tiles out
         const int64_t I = sIJ[0], J = sIJ[1];
         const int64_t row0 = I * WT, col0 = J * WT;
         const bool diag = I == J;
@@ -643,10 +727,35 @@ __global__ void __launch_bounds__(TPB) k_weights_f64(const T *__restrict__ X, in
 }
 }  // namespace
 
-size_t weights_sym_bytes(int64_t n) {
+// part: row partials, column partials [items][64] float2, shifts [rows]
+// float2, flags [items], then (256-aligned) tile centroids [T][d], radii [T]
+// and largest shifts [T]
+struct SymParts {
+    float2 *rpart, *cpart, *shdw;
+    uint8_t *flags, *tskip;
+    float *cen, *rad, *msh;
+};
+static SymParts sym_parts(void *part, int64_t items, int64_t rows, int64_t T, int32_t d) {
+    SymParts P;
+    P.rpart = (float2 *)part;
+    P.cpart = P.rpart + items * WT;
+    P.shdw = P.cpart + items * WT;
+    P.flags = (uint8_t *)(P.shdw + rows);
+    uintptr_t c = ((uintptr_t)(P.flags + items) + 255) & ~(uintptr_t)255;
+    P.cen = (float *)c;
+    P.rad = P.cen + T * d;
+    P.msh = P.rad + T;
+    P.tskip = (uint8_t *)(P.msh + T);
+    return P;
+}
+static size_t sym_bytes(int64_t items, int64_t rows, int64_t T, int32_t d) {
+    return (size_t)items * (2 + 2 * WT * sizeof(float2)) + (size_t)rows * sizeof(float2) + 256 +
+           (size_t)T * (d + 2) * sizeof(float) + 4096;
+}
+
+size_t weights_sym_bytes(int64_t n, int32_t d) {
     const int64_t T = ceil_div(n, WT);
-    const int64_t items = T * (T + 1) / 2;
-    return (size_t)items * (1 + 2 * WT * sizeof(float2)) + (size_t)n * sizeof(float2) + 4096;
+    return sym_bytes(T * (T + 1) / 2, n, T, d);
 }
 
 // Symmetric screened omega (F32 input, p not needed).  part must hold
@@ -658,26 +767,26 @@ cudaError_t weights_launch_sym(const float *X, int64_t n, int32_t d, double sigm
     const double is = 1.0 / sigma;
     const float is_h = (float)is;
     const float is_l = (float)(is - (double)is_h);
-    const float zskip = (float)(39.0 + log((double)n));
+    const float zskip = (float)(36.0 + log((double)n));
     const double e = 1.1 * (double)(d + 3) * 5.9604644775390625e-08;
     const float shrink = (float)((1.0 - e) * (1.0 - 1e-6));
     const int64_t T = ceil_div(n, WT);
     const int64_t items = T * (T + 1) / 2;
-    float2 *rpart = (float2 *)part;
-    float2 *cpart = rpart + items * WT;
-    float2 *shdw = cpart + items * WT;
-    uint8_t *flags = (uint8_t *)(shdw + n);
+    const SymParts P = sym_parts(part, items, n, T, d);
     const unsigned grid = (unsigned)(num_sms() * 2);
-    k_shift_dw<<<(unsigned)ceil_div(n, 256), 256, 0, ISO_S(s)>>>(nnbits, n, is, shdw);
-    k_weights_sym<false><<<grid, TPB, 0, ISO_S(s)>>>(X, n, d, shdw, is_h, is_l, tab, zskip, shrink, T, items, nullptr,
-                                                     nullptr, flags, rpart, cpart, tile_counts);
-    k_weights_reduce<<<(unsigned)ceil_div(n, 256), 256, 0, ISO_S(s)>>>(nnbits, n, T, is, include_self, flags, rpart,
-                                                                      cpart, omega);
+    k_shift_dw<<<(unsigned)ceil_div(n, 256), 256, 0, ISO_S(s)>>>(nnbits, n, is, P.shdw);
+    k_tile_bounds<<<(unsigned)T, 64, 0, ISO_S(s)>>>(X, n, d, P.shdw, nullptr, P.cen, P.rad, P.msh);
+    k_tile_pair_skip<false><<<(unsigned)(num_sms() * 8), 256, 0, ISO_S(s)>>>(P.cen, P.rad, P.msh, d, T, items, nullptr,
+                                                                            is_h, zskip, shrink, P.tskip);
+    k_weights_sym<false><<<grid, TPB, 0, ISO_S(s)>>>(X, n, d, P.shdw, is_h, is_l, tab, zskip, shrink, T, items, nullptr,
+                                                     nullptr, P.tskip, P.flags, P.rpart, P.cpart, tile_counts);
+    k_weights_reduce<<<(unsigned)ceil_div(n, 256), 256, 0, ISO_S(s)>>>(nnbits, n, T, is, include_self, P.flags,
+                                                                      P.rpart, P.cpart, omega);
     return cudaGetLastError();
 }
 
-size_t weights_sym_sets_bytes(int64_t n_pad, int64_t nitems) {
-    return (size_t)nitems * (1 + 2 * WT * sizeof(float2)) + (size_t)n_pad * sizeof(float2) + 4096;
+size_t weights_sym_sets_bytes(int64_t n_pad, int64_t nitems, int32_t d) {
+    return sym_bytes(nitems, n_pad, ceil_div(n_pad, WT), d);
 }
 
 // Symmetric screened omega over independent sets.  Xp / nnbits / omega are
@@ -693,20 +802,23 @@ cudaError_t weights_launch_sym_sets(const float *Xp, int64_t n_pad, int32_t d, d
     const double is = 1.0 / sigma;
     const float is_h = (float)is;
     const float is_l = (float)(is - (double)is_h);
-    const float zskip = (float)(39.0 + log((double)(max_n > 2 ? max_n : 2)));
+    const float zskip = (float)(36.0 + log((double)(max_n > 2 ? max_n : 2)));
     const double e = 1.1 * (double)(d + 3) * 5.9604644775390625e-08;
     const float shrink = (float)((1.0 - e) * (1.0 - 1e-6));
-    float2 *rpart = (float2 *)part;
-    float2 *cpart = rpart + nitems * WT;
-    float2 *shdw = cpart + nitems * WT;
-    uint8_t *flags = (uint8_t *)(shdw + n_pad);
+    const int64_t T = ceil_div(n_pad, WT);
+    const SymParts P = sym_parts(part, nitems, n_pad, T, d);
     const unsigned grid = (unsigned)(num_sms() * 2);
-    k_shift_dw<<<(unsigned)ceil_div(n_pad, 256), 256, 0, ISO_S(s)>>>(nnbits, n_pad, is, shdw);
-    if (nitems > 0)
-        k_weights_sym<true><<<grid, TPB, 0, ISO_S(s)>>>(Xp, n_pad, d, shdw, is_h, is_l, tab, zskip, shrink, 0, nitems,
-                                                        witems, tile_valid, flags, rpart, cpart, tile_counts);
+    k_shift_dw<<<(unsigned)ceil_div(n_pad, 256), 256, 0, ISO_S(s)>>>(nnbits, n_pad, is, P.shdw);
+    k_tile_bounds<<<(unsigned)T, 64, 0, ISO_S(s)>>>(Xp, n_pad, d, P.shdw, tile_valid, P.cen, P.rad, P.msh);
+    if (nitems > 0) {
+        k_tile_pair_skip<true><<<(unsigned)(num_sms() * 8), 256, 0, ISO_S(s)>>>(P.cen, P.rad, P.msh, d, T, nitems,
+                                                                               witems, is_h, zskip, shrink, P.tskip);
+        k_weights_sym<true><<<grid, TPB, 0, ISO_S(s)>>>(Xp, n_pad, d, P.shdw, is_h, is_l, tab, zskip, shrink, 0, nitems,
+                                                        witems, tile_valid, P.tskip, P.flags, P.rpart, P.cpart,
+                                                        tile_counts);
+    }
     k_weights_reduce_sets<<<(unsigned)ceil_div(n_pad, 256), 256, 0, ISO_S(s)>>>(
-        nnbits, n_pad, tile_valid, tile_set, tile0, ntl, item0, is, include_self, flags, rpart, cpart, omega);
+        nnbits, n_pad, tile_valid, tile_set, tile0, ntl, item0, is, include_self, P.flags, P.rpart, P.cpart, omega);
     return cudaGetLastError();
 }
 
@@ -726,8 +838,8 @@ cudaError_t weights_launch(const void *X, int64_t n, int32_t d, int dtype, bool 
     const float is_h = (float)is;
     const float is_l = (float)(is - (double)is_h);
     // Terms below e^-zskip of a row's largest term are dropped: their total
-    // is below n e^-zskip = e^-39 ~ 1.2e-17 of the row sum.
-    const float zskip = (float)(39.0 + log((double)n));
+    // is below n e^-zskip = e^-36 ~ 2.3e-16 of the row sum.
+    const float zskip = (float)(36.0 + log((double)n));
     // FP32 d2 relative error <= (d+1)u (+ underflow): shrink by 1.1(d+3)u
     // plus the rounding of the screen's own sqrt/multiply/subtract.
     const double e = 1.1 * (double)(d + 3) * 5.9604644775390625e-08;
