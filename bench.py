@@ -292,12 +292,16 @@ def main():
 
     # roofline of the dominant kernel: the screened double-word omega sweep
     peaks, src = _peaks()
-    w_ms = statistics.mean(p["weights_ms"] for p in prof)
+    # the kernel's own CUDA-event time (the omega stage time when it was not
+    # the symmetric kernel)
+    w_ms = statistics.mean(p["omega_kernel_ms"] or p["weights_ms"] for p in prof)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     alu_peak = sms * FP32_LANES_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12   # T instr/s
     tiles, tiles_dw = prof[-1]["omega_tiles"], prof[-1]["omega_tiles_dw"]
     sym = prof[-1]["omega_symmetric"]
-    screen_ops = 2.0 * d + (12.0 if sym else 8.0)            # FP32 screen of one pair (both directions if sym)
+    # FP32 screen of one pair (both directions if sym); none when the tensor
+    # cores screened the tile pairs (sym == 2)
+    screen_ops = 0.0 if sym == 2 else 2.0 * d + (12.0 if sym else 8.0)
     dw_ops = 21.0 * d + (140.0 if sym else 75.0)              # d2 (21/dim) + sqrt + exp/accumulate per direction
     work = tiles * 4096.0 * screen_ops + tiles_dw * 4096.0 * dw_ops
     achieved = work / (w_ms / 1000.0) / 1e12
@@ -339,9 +343,10 @@ def main():
                      "frac": achieved / alu_peak, "traffic": None,
                      "kernel": "k_weights_sym (omega, double-word FP32)" if sym else "k_weights_dw (omega, double-word FP32)",
                      "note": f"FP32-pipe instructions of the algorithm: every {'unordered' if sym else 'ordered'} "
-                             f"pair of the 64x64 tile grid screened in FP32 ({screen_ops:.0f} each, {tiles} tiles), "
+                             f"pair of the 64x64 tile grid screened ("
+                             f"{'on the tensor cores' if sym == 2 else 'in FP32, %.0f each' % screen_ops}, {tiles} tiles), "
                              f"double-word evaluation ({dw_ops:.0f} per pair) of the {tiles_dw} tiles the screen "
-                             f"keeps; over the omega stage's event time; "
+                             f"keeps; over the kernel's CUDA-event time ({w_ms:.2f} ms, launch on the call's stream); "
                              f"peak = {sms} SMs x {FP32_LANES_PER_SM} lanes x max SM clock ({src} sm_max_mhz)"},
         "stages_ms": stages, "counts": counts, "mst": mst,
         "omega_tiles": {"screened": prof[-1]["omega_tiles"], "double_word": prof[-1]["omega_tiles_dw"]},
@@ -496,7 +501,7 @@ def main_batched(args):
                "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": int(N * 5 + nsets * 8)}
 
     peaks, src = _peaks()
-    w_ms = statistics.mean(p["weights_ms"] for p in prof)
+    w_ms = statistics.mean(p["omega_kernel_ms"] or p["weights_ms"] for p in prof)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     alu_peak = sms * FP32_LANES_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     tiles, tiles_dw = prof[-1]["omega_tiles"], prof[-1]["omega_tiles_dw"]
@@ -521,7 +526,7 @@ def main_batched(args):
                      "kernel": "k_weights_sym (omega over the sets' tile pairs, double-word FP32)",
                      "note": f"FP32-pipe instructions of the algorithm ({screen_ops:.0f} per screened pair, "
                              f"{dw_ops:.0f} per double-word pair; {tiles} tile pairs screened, {tiles_dw} kept) "
-                             f"over the omega stage's event time; peak = {sms} SMs x {FP32_LANES_PER_SM} lanes x "
+                             f"over the kernel's CUDA-event time ({w_ms:.2f} ms); peak = {sms} SMs x {FP32_LANES_PER_SM} lanes x "
                              f"max SM clock ({src})"},
         "stages_ms": stages,
         "mst": {"stage_ms": mst_ms, "rounds": rounds,

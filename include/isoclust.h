@@ -325,11 +325,17 @@ void isoclust_last_profile(double *t_ms6, int64_t *counts4);
 /* Tile pairs of the omega sweep in the last isoclust_cluster / _detail call
  * on this host thread: tiles3[0] = 64x64 tile pairs screened, tiles3[1] =
  * tile pairs evaluated in double-word arithmetic (the rest held only terms
- * below e^-(36 + ln n) of their row's largest term), tiles3[2] = 1 when the
- * pairs were unordered (symmetric sweep, each pair once for both rows), 0
- * when ordered.  Zero counts when the screen did not run (F64 input,
+ * below e^-(36 + ln n) of their row's largest term), tiles3[2] = 0 when the
+ * pairs were ordered, 1 when unordered (symmetric sweep, each pair once for
+ * both rows) and screened in FP32, 2 when unordered and screened on the
+ * tensor cores (the FP32 screen did not run).  Zero counts when the screen did not run (F64 input,
  * alpha > 0, or the FP64 precision option). */
 void isoclust_last_omega_tiles(int64_t *tiles3);
+
+/* Device time (milliseconds, CUDA events on the call's stream around its
+ * launch) of the symmetric omega kernel in the last isoclust_cluster /
+ * _detail / _batched call on this host thread; 0 when it did not run. */
+double isoclust_last_omega_kernel_ms(void);
 
 #ifdef __cplusplus
 }

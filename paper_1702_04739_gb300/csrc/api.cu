@@ -19,14 +19,16 @@ cudaError_t weights_launch(const void *X, int64_t n, int32_t d, int dtype, bool 
 size_t weights_sym_bytes(int64_t n, int32_t d);
 cudaError_t weights_launch_sym(const float *X, int64_t n, int32_t d, double sigma, int include_self,
                                const unsigned long long *nnbits, double *omega, void *part,
-                               unsigned long long *tile_counts, cudaStream_t s);
+                               unsigned long long *tile_counts, const uint8_t *need, cudaEvent_t *kev,
+                               cudaStream_t s);
+float omega_zskip(int64_t n);
 constexpr size_t SYM_PART_LIMIT = size_t(16) << 30;   // symmetric sweep up to 16 GiB of partials
 size_t weights_sym_sets_bytes(int64_t n_pad, int64_t nitems, int32_t d);
 cudaError_t weights_launch_sym_sets(const float *Xp, int64_t n_pad, int32_t d, double sigma, int include_self,
                                     const unsigned long long *nnbits, double *omega, void *part, const int2 *witems,
                                     int64_t nitems, const int32_t *tile_valid, const int32_t *tile_set,
                                     const int64_t *tile0, const int64_t *ntl, const int64_t *item0, int64_t max_n,
-                                    unsigned long long *tile_counts, cudaStream_t s);
+                                    unsigned long long *tile_counts, cudaEvent_t *kev, cudaStream_t s);
 
 size_t adjoint_bytes(int64_t n, int32_t d, int32_t k);
 cudaError_t adjoint_launch(const void *X, int32_t dtype, int64_t n, int32_t d, const double *scale, double sigma,
@@ -45,6 +47,7 @@ static thread_local double g_prof_ms[6] = {0, 0, 0, 0, 0, 0};
 static thread_local int64_t g_prof_cnt[4] = {0, 0, 0, 0};
 static thread_local unsigned long long g_prof_tiles[2] = {0, 0};
 static thread_local int g_prof_sym = 0;
+static thread_local double g_prof_omega_kernel_ms = 0.0;
 
 void set_error(const char *fmt, ...) {
     va_list ap;
@@ -160,6 +163,10 @@ __global__ void k_check_edges(const int32_t *counters, int64_t n, uint32_t *st) 
 
 __global__ void k_copy_beta(const SearchState *S, double *beta) { beta[0] = S->beta; }
 
+__global__ void k_or_err_api(const uint32_t *src, uint32_t *dst) {
+    if (*src) atomicOr(dst, *src);
+}
+
 // Row order of the omega sweep: MST preorder (spatially coherent runs),
 // with rows whose nearest neighbour is far (y_nn > 16) moved to the front:
 // they need double-word work against most columns, so their CTAs start
@@ -245,7 +252,7 @@ static isoclust_status check_points(const void *X, int64_t n, int32_t d, int32_t
 }
 
 struct Events {
-    cudaEvent_t e[8];
+    cudaEvent_t e[10];
     bool ok = false;
     Events() {
         ok = true;
@@ -317,6 +324,7 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
         unsigned long long *nnp = nullptr, *tiles = nullptr;
         double *omp = nullptr, *pp = nullptr;
         void *sym = nullptr;
+        uint8_t *need = nullptr;
     } P;
     const bool permuted = need_labels && dtype == ISOCLUST_F32 && !fp64_sweep;
     const bool symmetric = permuted && o.alpha == 0.0 && o.omega_mode == ISOCLUST_OMEGA_FULL &&
@@ -344,6 +352,7 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
             P.omp = A.take<double>(n);
             P.pp = A.take<double>(n);
             if (symmetric) P.sym = (void *)A.take<unsigned char>(weights_sym_bytes(n, d));
+            if (symmetric && use_tc) P.need = A.take<uint8_t>((size_t)ceil_div(n, 64) * ceil_div(n, 64));
         }
     };
     MstScratch M;
@@ -405,8 +414,16 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
                 k_gather_rows<<<(unsigned)ceil_div(n * (int64_t)d, TPB), TPB, 0, ISO_S(s)>>>(
                     (const float *)X, P.perm, M.nnbits, n, d, P.Xp, P.nnp);
                 ISO_CUDA(cudaMemsetAsync(P.tiles, 0, 2 * sizeof(unsigned long long), s));
-                if (symmetric)
-                    ISO_CUDA(weights_launch_sym(P.Xp, n, d, sigma, o.include_self, P.nnp, P.omp, P.sym, P.tiles, s));
+                if (symmetric) {
+                    // the tensor cores decide which pairs of 64-row tiles can hold a term
+                    if (use_tc) {
+                        ISO_CUDA(tc_omega_screen(TC, P.Xp, n, d, P.nnp, sigma, (double)omega_zskip(n), P.need,
+                                                 ceil_div(n, 64), s));
+                        k_or_err_api<<<1, 1, 0, ISO_S(s)>>>(TC.err, status);
+                    }
+                    ISO_CUDA(weights_launch_sym(P.Xp, n, d, sigma, o.include_self, P.nnp, P.omp, P.sym, P.tiles,
+                                                use_tc ? P.need : nullptr, ev.ok ? ev.e + 8 : nullptr, s));
+                }
                 else
                     ISO_CUDA(weights_launch(P.Xp, n, d, dtype, false, sigma, o.alpha, o.include_self, P.nnp, P.omp,
                                             P.pp, P.tiles, s));
@@ -461,7 +478,8 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
     g_prof_cnt[3] = ss.max_depth;
     g_prof_tiles[0] = g_prof_tiles[1] = 0;
     if (permuted) ISO_CUDA(cudaMemcpy(g_prof_tiles, P.tiles, sizeof(g_prof_tiles), cudaMemcpyDeviceToHost));
-    g_prof_sym = symmetric ? 1 : 0;
+    g_prof_sym = symmetric ? (use_tc ? 2 : 1) : 0;
+    g_prof_omega_kernel_ms = symmetric ? ev.ms(8, 9) : 0.0;
     return map_status(fin, false);
 }
 
@@ -728,7 +746,8 @@ static isoclust_status cluster_sets_impl(const void *X, const int64_t *offsets, 
                                                                                 B.Xp, B.nnp);
     ISO_CUDA(cudaMemsetAsync(B.tiles, 0, 2 * sizeof(unsigned long long), s));
     ISO_CUDA(weights_launch_sym_sets(B.Xp, n_pad64, d, sigma, o.include_self, B.nnp, B.omp, B.sym, B.witems, nitems,
-                                     B.tile_valid, B.tile_set, d_tile0, d_ntl, d_item0, max_n, B.tiles, s));
+                                     B.tile_valid, B.tile_set, d_tile0, d_ntl, d_item0, max_n, B.tiles,
+                                     ev.ok ? ev.e + 8 : nullptr, s));
     k_scatter_pad<<<(unsigned)ceil_div(N + 1, TPB), TPB, 0, ISO_S(s)>>>(B.omp, B.pos, N, B.om);
     ev.rec(4, s);
     ISO_CUDA(phi_from_edges(TS, B.ed2, sigma, B.phi, s));
@@ -760,6 +779,7 @@ static isoclust_status cluster_sets_impl(const void *X, const int64_t *offsets, 
     g_prof_cnt[3] = 0;
     ISO_CUDA(cudaMemcpy(g_prof_tiles, B.tiles, sizeof(g_prof_tiles), cudaMemcpyDeviceToHost));
     g_prof_sym = 1;
+    g_prof_omega_kernel_ms = nitems > 0 ? ev.ms(8, 9) : 0.0;
     return map_status(fin, false);
 }
 
@@ -805,6 +825,8 @@ void isoclust_last_profile(double *t_ms6, int64_t *counts4) {
     if (t_ms6) for (int i = 0; i < 6; ++i) t_ms6[i] = g_prof_ms[i];
     if (counts4) for (int i = 0; i < 4; ++i) counts4[i] = g_prof_cnt[i];
 }
+
+double isoclust_last_omega_kernel_ms(void) { return g_prof_omega_kernel_ms; }
 
 void isoclust_last_omega_tiles(int64_t *tiles3) {
     if (tiles3) {

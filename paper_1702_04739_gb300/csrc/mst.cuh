@@ -70,6 +70,7 @@ struct TcScratch {
     const int64_t *offs = nullptr;
     const int64_t *rowbase = nullptr;
     int32_t *setcnt = nullptr;                     // components left in each set (independent sets)
+    bool keep_order = false;                       // rows as given instead of norm order
     CUtensorMap map_h, map_l;
     // n_pad_rows / nmeans / lists: 0 = one set
     void carve(Arena &A, int64_t n, int32_t d, int splits, int64_t n_pad_rows = 0, int nmeans = 1, int lists = 0);
@@ -79,6 +80,12 @@ bool tc_supported();
 cudaError_t tc_prepare(TcScratch &T, const float *X, int64_t n, int32_t d, cudaStream_t s);
 cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t n, int32_t d, uint32_t *status,
                            cudaStream_t s);
+// omega screen on the tensor cores: Xp (n x d, omega's row order) and its
+// nearest-neighbour d2 bits; need[I * T64 + J] = 1 for every pair of 64-row
+// tiles (I <= J) holding a pair within the cutoff zskip of eq. omega's terms
+cudaError_t tc_omega_screen(TcScratch &T, const float *Xp, int64_t n, int32_t d,
+                            const unsigned long long *nnbits, double sigma, double zskip, uint8_t *need, int64_t T64,
+                            cudaStream_t s);
 // independent sets: recount the components of every set from comp
 cudaError_t tc_count_sets(TcScratch &T, const int32_t *comp, int64_t n, const int32_t *counters, cudaStream_t s);
 

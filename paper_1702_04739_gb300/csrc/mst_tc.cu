@@ -23,6 +23,8 @@
 #include <cuda.h>
 #include <stddef.h>
 
+#include <vector>
+
 #include "mst.cuh"
 
 namespace iso {
@@ -174,7 +176,17 @@ __device__ __forceinline__ bool mst_active(const int32_t *counters) {
 // shared memory for a whole work item and only the column blocks stream
 // through the ring (used when d_pad <= 128); otherwise A and B chunks
 // stream together.
-template <bool ARES>
+// SCREEN: the same Gram tiles decide, for omega, which pairs of 64-row tiles
+// hold a pair (i, j) within the cutoff: d2 <= max(A_i, A_j) with A the
+// squared cutoff distance of each row (rowA; -inf at padding) tested
+// against the rigorous lower bound of d2; need[I64 * T64 + J64] = 1.
+struct ScreenArgs {
+    const float *rowA;
+    uint8_t *need;
+    int64_t T64;
+};
+
+template <bool ARES, bool SCREEN>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUtensorMap tml,
            const float *__restrict__ rnorm, const float *__restrict__ cnorm, const float *__restrict__ rsq,
@@ -182,8 +194,8 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
            const int32_t *__restrict__ comp, int64_t nrows, int ntiles, int kchunks, int splits,
            const int4 *__restrict__ witems, int64_t nwitems, const int32_t *__restrict__ setcnt,
            const int32_t *counters, float *__restrict__ out_v, int32_t *__restrict__ out_j, float *__restrict__ out_u,
-           uint32_t *err) {
-    if (!mst_active(counters)) return;
+           uint32_t *err, ScreenArgs scr) {
+    if (!SCREEN && !mst_active(counters)) return;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     constexpr int NST = ARES ? TC_STAGES_B : TC_STAGES;                 // ring depth
@@ -341,7 +353,8 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
             const int64_t row = (int64_t)rt * TC_BM + trow;      // < nrows: whole tiles
             const float nrow = rnorm[row];
             const float srow = rsq[row];
-            const int32_t crow = comp[row];
+            const int32_t crow = SCREEN ? 0 : comp[row];
+            const float arow = SCREEN ? scr.rowA[row] : 0.0f;
             float ubest = INFINITY;        // smallest upper bound of a candidate's d2
             float bv[TC_TOPK];
             int32_t bj[TC_TOPK];
@@ -351,7 +364,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
             int64_t pcol = (int64_t)c0 * TC_BN + cm;
             float pn = INFINITY;
             int32_t pc = -2;
-            if (h == 0 && c0 < c1) { pn = cnorm[pcol]; pc = comp[pcol]; }
+            if (h == 0 && c0 < c1) { pn = cnorm[pcol]; pc = SCREEN ? __float_as_int(scr.rowA[pcol]) : comp[pcol]; }
             float ptsq = 0.f, ptmax = 0.f;
             if (c0 < c1) { ptsq = __ldg(tsq + c0); ptmax = __ldg(tmax + c0); }
             for (int ct = c0; ct < c1; ++ct) {
@@ -364,7 +377,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
                     pcol = (int64_t)(ct + 1) * TC_BN + cm;
                     if (h == 0) {
                         pn = cnorm[pcol];
-                        pc = comp[pcol];
+                        pc = SCREEN ? __float_as_int(scr.rowA[pcol]) : comp[pcol];
                     }
                     ptsq = __ldg(tsq + ct + 1);
                     ptmax = __ldg(tmax + ct + 1);
@@ -373,6 +386,16 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
                 if (ok) ok = mbar_wait(&sh->acc_full[acc], acc_phase, err);
                 tc_fence_after();
                 float m = INFINITY;        // min over the half-tile of n_j - 2 g (foreign columns)
+                bool near = false;         // SCREEN: a pair of this half-tile within the cutoff
+                // SCREEN: d2 >= v + n_i - dlt with v = n_j - 2g; near if that
+                // bound <= max(A_i, A_j), i.e. v <= max(A_i, A_j) + (dlt - n_i)
+                const float dlt = acoef * srow * ctsq + bcoef * (nrow + ctmax);
+                // (padding rows: arow = -inf makes both thresholds -inf; the
+                // warp-collective TMEM loads stay unconditional)
+                const bool rvalid = arow > -INFINITY;
+                const float Ci = SCREEN ? (rvalid ? __fadd_ru(__fadd_ru(dlt, 1e-5f * (nrow + ctmax)), -nrow) : -INFINITY)
+                                        : 0.0f;
+                const float Bi = SCREEN ? (rvalid ? __fadd_ru(arow, Ci) : -INFINITY) : 0.0f;
                 if (ok) {
                     const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + acc * TC_BN + h * TC_CW;
                     uint32_t g0[32], g1[32];
@@ -390,7 +413,10 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             const float v = __fmaf_rn(-2.0f, __uint_as_float(g0[q + u]), ncv[u]);
-                            m = fminf(m, cmv[u] != crow ? v : INFINITY);
+                            if constexpr (SCREEN)
+                                near |= v <= fmaxf(Bi, __fadd_ru(__int_as_float(cmv[u]), Ci));
+                            else
+                                m = fminf(m, cmv[u] != crow ? v : INFINITY);
                         }
                     }
 #pragma unroll
@@ -402,7 +428,10 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             const float v = __fmaf_rn(-2.0f, __uint_as_float(g1[q + u]), ncv[u]);
-                            m = fminf(m, cmv[u] != crow ? v : INFINITY);
+                            if constexpr (SCREEN)
+                                near |= v <= fmaxf(Bi, __fadd_ru(__int_as_float(cmv[u]), Ci));
+                            else
+                                m = fminf(m, cmv[u] != crow ? v : INFINITY);
                         }
                     }
                 }
@@ -410,16 +439,23 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sh->acc_empty[acc]);
                 if (++acc == TC_NACC) { acc = 0; acc_phase ^= 1u; }
+                if constexpr (SCREEN) {
+                    // rows of this warp are one 64-row half of the row tile
+                    if (__ballot_sync(0xffffffffu, near) && lane == 0) {
+                        const int64_t I64 = 2 * (int64_t)rt + (quad >> 1), J64 = 2 * (int64_t)ct + h;
+                        if (I64 < scr.T64 && J64 < scr.T64) scr.need[I64 * scr.T64 + J64] = 1;
+                    }
+                    continue;
+                }
                 m = __fadd_rn(m, nrow);
                 // rigorous bounds of the half-tile's smallest d2 of the represented
                 // points: accumulation + dropped lo.lo (A s_i s_j) and FP32
                 // norm/epilogue rounding
-                const float dlt = acoef * srow * ctsq + bcoef * (nrow + ctmax);
                 const float lb = m - dlt;
                 ubest = fminf(ubest, m + dlt);
                 if (lb < bv[TC_TOPK - 1]) top_insert(bv, bj, lb, 2 * ct + h);
             }
-            {
+            if (!SCREEN) {
                 const size_t o = ((size_t)(2 * sp + h) * nrows + row) * TC_TOPK;
 #pragma unroll
                 for (int q = 0; q < TC_TOPK; ++q) { out_v[o + q] = bv[q]; out_j[o + q] = bj[q]; }
@@ -585,6 +621,30 @@ __global__ void k_tc_set_roots(const int32_t *__restrict__ comp, const int32_t *
     const int64_t gs = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gs)
         if (comp[v] == v) atomicAdd(setcnt + set_of[v], 1);
+}
+
+__global__ void k_tc_identity(int32_t *__restrict__ permp, int64_t n, int64_t n_pad) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n_pad) permp[r] = r < n ? (int32_t)r : -1;
+}
+
+// omega screen: squared cutoff distance of row r, (sigma (zskip + y_r) + w_r)^2
+// with y_r = d_nn(r) / sigma and w_r the representation error bound of the
+// BF16 split, computed in FP64 and rounded up; -inf at padding
+__global__ void k_screen_rows(const unsigned long long *__restrict__ nnbits, const float *__restrict__ rsq,
+                              const unsigned int *__restrict__ nmax_bits, int64_t n, int64_t n_pad, double sigma,
+                              double zskip, double eps_rep, float *__restrict__ rowA) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_pad) return;
+    if (r >= n) {
+        rowA[r] = -INFINITY;
+        return;
+    }
+    const double nd2 = __longlong_as_double((long long)nnbits[r]);
+    const double y = isfinite(nd2) ? sqrt(nd2) / sigma : 0.0;
+    const double smax = sqrt((double)__uint_as_float(*nmax_bits));
+    const double a = sigma * (zskip + y) * (1.0 + 1e-9) + eps_rep * ((double)rsq[r] + smax);
+    rowA[r] = __double2float_ru(a * a * (1.0 + 1e-6));
 }
 
 __global__ void k_tc_fill_lists(float *__restrict__ tv, int32_t *__restrict__ tj, float *__restrict__ tu,
@@ -991,6 +1051,47 @@ cudaError_t tc_count_sets(TcScratch &T, const int32_t *comp, int64_t n, const in
     return cudaGetLastError();
 }
 
+cudaError_t tc_omega_screen(TcScratch &T, const float *Xp, int64_t n, int32_t d,
+                            const unsigned long long *nnbits, double sigma, double zskip, uint8_t *need, int64_t T64,
+                            cudaStream_t s) {
+    cudaError_t e;
+    T.keep_order = true;
+    T.set_of = nullptr;
+    T.items = nullptr;
+    if ((e = tc_prepare(T, Xp, n, d, s))) return e;
+    float *rowA = T.tu;                                     // >= n_pad floats
+    const double eps_rep = 1.25 * (3.814697265625e-06 + 5.9604644775390625e-08);
+    k_screen_rows<<<(unsigned)ceil_div(T.n_pad, 256), 256, 0, ISO_S(s)>>>(nnbits, T.rsq, T.nmax_bits, n, T.n_pad, sigma,
+                                                                          zskip, eps_rep, rowA);
+    if ((e = cudaMemsetAsync(need, 0, (size_t)T64 * T64, s))) return e;
+    // the upper triangle of 128-row tiles, row tile I against [I, T) in
+    // chunks of 16 column tiles
+    const int ntiles = (int)(T.n_pad / TC_BM);
+    std::vector<int4> items;
+    for (int I = 0; I < ntiles; ++I)
+        for (int c0 = I; c0 < ntiles; c0 += 16) items.push_back(make_int4(I, c0, c0 + 16 < ntiles ? c0 + 16 : ntiles, 0));
+    int4 *ditems = reinterpret_cast<int4 *>(T.tj);          // lists x n_pad x 8 int32 >> items
+    if ((size_t)items.size() * sizeof(int4) > (size_t)T.lists * T.n_pad * TC_TOPK * sizeof(int32_t))
+        return cudaErrorInvalidValue;
+    if ((e = cudaMemcpyAsync(ditems, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, s))) return e;
+    const int kchunks = T.d_pad / TC_BK;
+    const int64_t nsm = (int64_t)num_sms(), nit = (int64_t)items.size();
+    const unsigned grid = (unsigned)(nit < nsm ? nit : nsm);
+    const double u = 1.1920928955078125e-07;
+    const float acoef = (float)(1.25 * 2.0 * (3.0 * T.d_pad * u + 3.814697265625e-06));
+    const float bcoef = (float)(1.25 * 8.0 * 5.9604644775390625e-08);
+    const ScreenArgs scr{rowA, need, T64};
+    if (kchunks <= 2)
+        k_sweep_tc<true, true><<<grid, TC_THREADS, TC_SMEM_ARES, ISO_S(s)>>>(
+            T.map_h, T.map_l, T.nrm, T.cnrm, T.rsq, T.tmax, T.tsq, acoef, bcoef, nullptr, T.n_pad, ntiles, kchunks, 1,
+            ditems, nit, nullptr, nullptr, nullptr, nullptr, nullptr, T.err, scr);
+    else
+        k_sweep_tc<false, true><<<grid, TC_THREADS, TC_SMEM_STREAM, ISO_S(s)>>>(
+            T.map_h, T.map_l, T.nrm, T.cnrm, T.rsq, T.tmax, T.tsq, acoef, bcoef, nullptr, T.n_pad, ntiles, kchunks, 1,
+            ditems, nit, nullptr, nullptr, nullptr, nullptr, nullptr, T.err, scr);
+    return cudaGetLastError();
+}
+
 // At most 16 splits: the recheck merges 2 x splits candidate lists in one warp.
 int tc_splits(int64_t n) {
     const int64_t rt = ceil_div(n, TC_BM);
@@ -1021,11 +1122,17 @@ cudaError_t tc_prepare(TcScratch &T, const float *X, int64_t n, int32_t d, cudaS
         k_tc_mean_partial<<<gm, 128, 0, ISO_S(s)>>>(X, n, d, rows_per, T.part);
         k_tc_mean_final<<<(unsigned)ceil_div(d, 128), 128, 0, ISO_S(s)>>>(T.part, 64, n, d, T.mean);
     }
-    // norm order: tiles of points with similar |x - c| give tight tile bounds
-    k_tc_prenorm_keys<<<(unsigned)ceil_div(n, 256), 256, 0, ISO_S(s)>>>(X, T.mean, T.set_of, n, d, T.keys, T.perm);
-    if ((e = sort_pairs_u64(T.keys, T.perm, T.kbuf, T.vbuf, n, s))) return e;
-    if ((e = cudaMemsetAsync(T.permp, 0xff, sizeof(int32_t) * T.n_pad, s))) return e;     // -1: padding
-    k_tc_place<<<(unsigned)ceil_div(n, 256), 256, 0, ISO_S(s)>>>(T.perm, n, T.set_of, T.offs, T.rowbase, T.permp);
+    if (T.keep_order) {
+        // rows as given (the omega screen works in omega's row order)
+        k_tc_identity<<<(unsigned)ceil_div(T.n_pad, 256), 256, 0, ISO_S(s)>>>(T.permp, n, T.n_pad);
+    } else {
+        // norm order: tiles of points with similar |x - c| give tight tile bounds
+        k_tc_prenorm_keys<<<(unsigned)ceil_div(n, 256), 256, 0, ISO_S(s)>>>(X, T.mean, T.set_of, n, d, T.keys, T.perm);
+        if ((e = sort_pairs_u64(T.keys, T.perm, T.kbuf, T.vbuf, n, s))) return e;
+        if ((e = cudaMemsetAsync(T.permp, 0xff, sizeof(int32_t) * T.n_pad, s))) return e;     // -1: padding
+        k_tc_place<<<(unsigned)ceil_div(n, 256), 256, 0, ISO_S(s)>>>(T.perm, n, T.set_of, T.offs, T.rowbase,
+                                                                    T.permp);
+    }
     const int64_t tot = T.n_pad * T.d_pad;
     k_tc_split<<<(unsigned)ceil_div(tot, 256), 256, 0, ISO_S(s)>>>(X, T.mean, T.set_of, T.permp, d, T.n_pad, T.d_pad,
                                                                   T.xh, T.xl, T.xs);
@@ -1043,9 +1150,17 @@ cudaError_t tc_prepare(TcScratch &T, const float *X, int64_t n, int32_t d, cudaS
     if ((e = make_map(&T.map_l, T.xl, T.n_pad, T.d_pad))) return e;
     static bool attr = false;
     if (!attr) {
-        if ((e = cudaFuncSetAttribute(k_sweep_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_STREAM)))
+        if ((e = cudaFuncSetAttribute(k_sweep_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      TC_SMEM_STREAM)))
             return e;
-        if ((e = cudaFuncSetAttribute(k_sweep_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_ARES)))
+        if ((e = cudaFuncSetAttribute(k_sweep_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      TC_SMEM_ARES)))
+            return e;
+        if ((e = cudaFuncSetAttribute(k_sweep_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      TC_SMEM_STREAM)))
+            return e;
+        if ((e = cudaFuncSetAttribute(k_sweep_tc<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      TC_SMEM_ARES)))
             return e;
         attr = true;
     }
@@ -1072,13 +1187,13 @@ cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t 
     const float acoef = (float)(1.25 * 2.0 * (3.0 * T.d_pad * u + 3.814697265625e-06));
     const float bcoef = (float)(1.25 * 8.0 * 5.9604644775390625e-08);
     if (kchunks <= 2)
-        k_sweep_tc<true><<<grid, TC_THREADS, TC_SMEM_ARES, ISO_S(s)>>>(
+        k_sweep_tc<true, false><<<grid, TC_THREADS, TC_SMEM_ARES, ISO_S(s)>>>(
             T.map_h, T.map_l, T.nrm, T.cnrm, T.rsq, T.tmax, T.tsq, acoef, bcoef, T.compp, T.n_pad, ntiles, kchunks,
-            T.splits, T.items, T.nitems, T.setcnt, S.counters, T.tv, T.tj, T.tu, T.err);
+            T.splits, T.items, T.nitems, T.setcnt, S.counters, T.tv, T.tj, T.tu, T.err, ScreenArgs{});
     else
-        k_sweep_tc<false><<<grid, TC_THREADS, TC_SMEM_STREAM, ISO_S(s)>>>(
+        k_sweep_tc<false, false><<<grid, TC_THREADS, TC_SMEM_STREAM, ISO_S(s)>>>(
             T.map_h, T.map_l, T.nrm, T.cnrm, T.rsq, T.tmax, T.tsq, acoef, bcoef, T.compp, T.n_pad, ntiles, kchunks,
-            T.splits, T.items, T.nitems, T.setcnt, S.counters, T.tv, T.tj, T.tu, T.err);
+            T.splits, T.items, T.nitems, T.setcnt, S.counters, T.tv, T.tj, T.tu, T.err, ScreenArgs{});
     // representation error of a centred point by BF16 hi + lo: 2^-18 relative
     // per element, plus the FP32 rounding of x - c (2^-24); 25 % headroom
     const double eps_rep = 1.25 * (3.814697265625e-06 + 5.9604644775390625e-08);

@@ -405,11 +405,13 @@ __global__ void __launch_bounds__(64) k_tile_bounds(const float *__restrict__ X,
 // term of the pair of tiles can matter and the pair is skipped before the
 // per-pair screen.  The FP32 sum carries the pair screen's relative error,
 // hence its shrink; every other step rounds towards the safe side.
+// With the tensor-core screen (need != null) the pair is skipped unless it
+// found a pair of points within the cutoff.
 template <bool SETS>
 __global__ void k_tile_pair_skip(const float *__restrict__ cen, const float *__restrict__ rad,
                                  const float *__restrict__ msh, int32_t d, int64_t T, int64_t nitems,
                                  const int2 *__restrict__ witems, float is_h, float zskip, float scr_shrink,
-                                 uint8_t *__restrict__ tskip) {
+                                 const uint8_t *__restrict__ need, uint8_t *__restrict__ tskip) {
     const int64_t gs = (int64_t)gridDim.x * blockDim.x;
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nitems; w += gs) {
         int64_t I, J;
@@ -420,7 +422,9 @@ __global__ void k_tile_pair_skip(const float *__restrict__ cen, const float *__r
             tri_item(w, T, I, J);
         }
         uint8_t skip = 0;
-        if (I != J) {
+        if (need) {
+            skip = (I != J && !need[I * T + J]) ? 1 : 0;
+        } else if (I != J) {
             float tot = 0.0f;
             for (int32_t t = 0; t < d; ++t) {
                 const float df = __fsub_rn(cen[I * d + t], cen[J * d + t]);
@@ -446,8 +450,8 @@ __global__ void __launch_bounds__(TPB, 2)
 k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *__restrict__ shdw,
               float is_h, float is_l, ExpTable tabv, float zskip, float scr_shrink, int64_t T,
               int64_t nitems, const int2 *__restrict__ witems, const int32_t *__restrict__ tile_valid,
-              const uint8_t *__restrict__ tskip, uint8_t *__restrict__ flags, float2 *__restrict__ rpart,
-              float2 *__restrict__ cpart, unsigned long long *__restrict__ tile_counts) {
+              const uint8_t *__restrict__ tskip, int prescreened, uint8_t *__restrict__ flags,
+              float2 *__restrict__ rpart, float2 *__restrict__ cpart, unsigned long long *__restrict__ tile_counts) {
     __shared__ __align__(16) float As[WDC][WPAD];
     __shared__ __align__(16) float Bs[WDC][WPAD];
     __shared__ float2 tab[64];
@@ -493,54 +497,58 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
             rs_h[q] = a.x; rs_l[q] = a.y;
             cs_h[q] = b.x; cs_l[q] = b.y;
         }
-        // ---- FP32 screen, both directions
-        float A32[4][4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) A32[i][j] = 0.f;
-        for (int t0 = 0; t0 < d; t0 += WDC) {
-            __syncthreads();
-#pragma unroll
-            for (int q = 0; q < (WT * WDC) / TPB; ++q) {
-                int idx = tid + q * TPB;
-                int r = idx / WDC, t = idx % WDC;
-                int64_t gr = row0 + r, gc = col0 + r;
-                int gt = t0 + t;
-                As[t][r] = (rok(r) && gt < d) ? X[gr * d + gt] : 0.0f;
-                Bs[t][r] = (cok(r) && gt < d) ? X[gc * d + gt] : 0.0f;
+        // ---- FP32 screen, both directions (unless the tensor-core screen
+        //      already decided this pair of tiles)
+        if (!prescreened) {
+            // ---- FP32 screen, both directions
+            float A32[4][4];
+    #pragma unroll
+            for (int i = 0; i < 4; ++i)
+    #pragma unroll
+                for (int j = 0; j < 4; ++j) A32[i][j] = 0.f;
+            for (int t0 = 0; t0 < d; t0 += WDC) {
+                __syncthreads();
+    #pragma unroll
+                for (int q = 0; q < (WT * WDC) / TPB; ++q) {
+                    int idx = tid + q * TPB;
+                    int r = idx / WDC, t = idx % WDC;
+                    int64_t gr = row0 + r, gc = col0 + r;
+                    int gt = t0 + t;
+                    As[t][r] = (rok(r) && gt < d) ? X[gr * d + gt] : 0.0f;
+                    Bs[t][r] = (cok(r) && gt < d) ? X[gc * d + gt] : 0.0f;
+                }
+                __syncthreads();
+                const int tl = min(WDC, d - t0);
+                for (int t = 0; t < tl; ++t) {
+                    float4 a4 = *reinterpret_cast<const float4 *>(&As[t][ty * 4]);
+                    float4 b4 = *reinterpret_cast<const float4 *>(&Bs[t][tx * 4]);
+                    float a[4] = {a4.x, a4.y, a4.z, a4.w};
+                    float b[4] = {b4.x, b4.y, b4.z, b4.w};
+    #pragma unroll
+                    for (int i = 0; i < 4; ++i)
+    #pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            float df = __fsub_rn(a[i], b[j]);
+                            A32[i][j] = __fmaf_rn(df, df, A32[i][j]);
+                        }
+                }
             }
-            __syncthreads();
-            const int tl = min(WDC, d - t0);
-            for (int t = 0; t < tl; ++t) {
-                float4 a4 = *reinterpret_cast<const float4 *>(&As[t][ty * 4]);
-                float4 b4 = *reinterpret_cast<const float4 *>(&Bs[t][tx * 4]);
-                float a[4] = {a4.x, a4.y, a4.z, a4.w};
-                float b[4] = {b4.x, b4.y, b4.z, b4.w};
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        float df = __fsub_rn(a[i], b[j]);
-                        A32[i][j] = __fmaf_rn(df, df, A32[i][j]);
-                    }
+            int need = 0;
+    #pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int lr = ty * 4 + i;
+    #pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int lc = tx * 4 + j;
+                    if (!rok(lr) || !cok(lc) || (diag && lc == lr)) continue;
+                    const float y = __fmul_rn(__fsqrt_rn(__fmul_rn(A32[i][j], scr_shrink)), is_h);
+                    if (!(y - rs_h[i] > zskip) || !(y - cs_h[j] > zskip)) need = 1;
+                }
             }
-        }
-        int need = 0;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int lr = ty * 4 + i;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int lc = tx * 4 + j;
-                if (!rok(lr) || !cok(lc) || (diag && lc == lr)) continue;
-                const float y = __fmul_rn(__fsqrt_rn(__fmul_rn(A32[i][j], scr_shrink)), is_h);
-                if (!(y - rs_h[i] > zskip) || !(y - cs_h[j] > zskip)) need = 1;
+            if (!__syncthreads_or(need)) {
+                if (tid == 0) flags[w] = 0;
+                continue;
             }
-        }
-        if (!__syncthreads_or(need)) {
-            if (tid == 0) flags[w] = 0;
-            continue;
         }
         ++dw_items;
         // ---- double-word pass
@@ -753,6 +761,10 @@ static size_t sym_bytes(int64_t items, int64_t rows, int64_t T, int32_t d) {
            (size_t)T * (d + 2) * sizeof(float) + 4096;
 }
 
+// the omega cutoff of a problem with n points per set: terms below
+// e^-zskip of a row's largest term are dropped (total < e^-36 of the row)
+float omega_zskip(int64_t n) { return (float)(36.0 + log((double)(n > 2 ? n : 2))); }
+
 size_t weights_sym_bytes(int64_t n, int32_t d) {
     const int64_t T = ceil_div(n, WT);
     return sym_bytes(T * (T + 1) / 2, n, T, d);
@@ -762,12 +774,13 @@ size_t weights_sym_bytes(int64_t n, int32_t d) {
 // weights_sym_bytes(n) bytes.
 cudaError_t weights_launch_sym(const float *X, int64_t n, int32_t d, double sigma, int include_self,
                                const unsigned long long *nnbits, double *omega, void *part,
-                               unsigned long long *tile_counts, cudaStream_t s) {
+                               unsigned long long *tile_counts, const uint8_t *need, cudaEvent_t *kev,
+                               cudaStream_t s) {
     static const ExpTable tab = make_exp_table();
     const double is = 1.0 / sigma;
     const float is_h = (float)is;
     const float is_l = (float)(is - (double)is_h);
-    const float zskip = (float)(36.0 + log((double)n));
+    const float zskip = omega_zskip(n);
     const double e = 1.1 * (double)(d + 3) * 5.9604644775390625e-08;
     const float shrink = (float)((1.0 - e) * (1.0 - 1e-6));
     const int64_t T = ceil_div(n, WT);
@@ -777,9 +790,12 @@ cudaError_t weights_launch_sym(const float *X, int64_t n, int32_t d, double sigm
     k_shift_dw<<<(unsigned)ceil_div(n, 256), 256, 0, ISO_S(s)>>>(nnbits, n, is, P.shdw);
     k_tile_bounds<<<(unsigned)T, 64, 0, ISO_S(s)>>>(X, n, d, P.shdw, nullptr, P.cen, P.rad, P.msh);
     k_tile_pair_skip<false><<<(unsigned)(num_sms() * 8), 256, 0, ISO_S(s)>>>(P.cen, P.rad, P.msh, d, T, items, nullptr,
-                                                                            is_h, zskip, shrink, P.tskip);
+                                                                            is_h, zskip, shrink, need, P.tskip);
+    if (kev) cudaEventRecord(kev[0], s);
     k_weights_sym<false><<<grid, TPB, 0, ISO_S(s)>>>(X, n, d, P.shdw, is_h, is_l, tab, zskip, shrink, T, items, nullptr,
-                                                     nullptr, P.tskip, P.flags, P.rpart, P.cpart, tile_counts);
+                                                     nullptr, P.tskip, need ? 1 : 0, P.flags, P.rpart, P.cpart,
+                                                     tile_counts);
+    if (kev) cudaEventRecord(kev[1], s);
     k_weights_reduce<<<(unsigned)ceil_div(n, 256), 256, 0, ISO_S(s)>>>(nnbits, n, T, is, include_self, P.flags,
                                                                       P.rpart, P.cpart, omega);
     return cudaGetLastError();
@@ -797,12 +813,12 @@ cudaError_t weights_launch_sym_sets(const float *Xp, int64_t n_pad, int32_t d, d
                                     const unsigned long long *nnbits, double *omega, void *part, const int2 *witems,
                                     int64_t nitems, const int32_t *tile_valid, const int32_t *tile_set,
                                     const int64_t *tile0, const int64_t *ntl, const int64_t *item0, int64_t max_n,
-                                    unsigned long long *tile_counts, cudaStream_t s) {
+                                    unsigned long long *tile_counts, cudaEvent_t *kev, cudaStream_t s) {
     static const ExpTable tab = make_exp_table();
     const double is = 1.0 / sigma;
     const float is_h = (float)is;
     const float is_l = (float)(is - (double)is_h);
-    const float zskip = (float)(36.0 + log((double)(max_n > 2 ? max_n : 2)));
+    const float zskip = omega_zskip(max_n);
     const double e = 1.1 * (double)(d + 3) * 5.9604644775390625e-08;
     const float shrink = (float)((1.0 - e) * (1.0 - 1e-6));
     const int64_t T = ceil_div(n_pad, WT);
@@ -811,11 +827,13 @@ cudaError_t weights_launch_sym_sets(const float *Xp, int64_t n_pad, int32_t d, d
     k_shift_dw<<<(unsigned)ceil_div(n_pad, 256), 256, 0, ISO_S(s)>>>(nnbits, n_pad, is, P.shdw);
     k_tile_bounds<<<(unsigned)T, 64, 0, ISO_S(s)>>>(Xp, n_pad, d, P.shdw, tile_valid, P.cen, P.rad, P.msh);
     if (nitems > 0) {
-        k_tile_pair_skip<true><<<(unsigned)(num_sms() * 8), 256, 0, ISO_S(s)>>>(P.cen, P.rad, P.msh, d, T, nitems,
-                                                                               witems, is_h, zskip, shrink, P.tskip);
+        k_tile_pair_skip<true><<<(unsigned)(num_sms() * 8), 256, 0, ISO_S(s)>>>(
+            P.cen, P.rad, P.msh, d, T, nitems, witems, is_h, zskip, shrink, nullptr, P.tskip);
+        if (kev) cudaEventRecord(kev[0], s);
         k_weights_sym<true><<<grid, TPB, 0, ISO_S(s)>>>(Xp, n_pad, d, P.shdw, is_h, is_l, tab, zskip, shrink, 0, nitems,
-                                                        witems, tile_valid, P.tskip, P.flags, P.rpart, P.cpart,
+                                                        witems, tile_valid, P.tskip, 0, P.flags, P.rpart, P.cpart,
                                                         tile_counts);
+        if (kev) cudaEventRecord(kev[1], s);
     }
     k_weights_reduce_sets<<<(unsigned)ceil_div(n_pad, 256), 256, 0, ISO_S(s)>>>(
         nnbits, n_pad, tile_valid, tile_set, tile0, ntl, item0, is, include_self, P.flags, P.rpart, P.cpart, omega);
@@ -839,7 +857,7 @@ cudaError_t weights_launch(const void *X, int64_t n, int32_t d, int dtype, bool 
     const float is_l = (float)(is - (double)is_h);
     // Terms below e^-zskip of a row's largest term are dropped: their total
     // is below n e^-zskip = e^-36 ~ 2.3e-16 of the row sum.
-    const float zskip = (float)(36.0 + log((double)n));
+    const float zskip = omega_zskip(n);
     // FP32 d2 relative error <= (d+1)u (+ underflow): shrink by 1.1(d+3)u
     // plus the rounding of the screen's own sqrt/multiply/subtract.
     const double e = 1.1 * (double)(d + 3) * 5.9604644775390625e-08;

@@ -92,6 +92,8 @@ def load(build_if_missing: bool = True):
                                              _P]
         lib.isoclust_last_profile.restype = None
         lib.isoclust_last_profile.argtypes = [_P, _P]
+        lib.isoclust_last_omega_kernel_ms.restype = _D
+        lib.isoclust_last_omega_kernel_ms.argtypes = []
         lib.isoclust_last_omega_tiles.restype = None
         lib.isoclust_last_omega_tiles.argtypes = [_P]
         _lib = lib
@@ -361,7 +363,8 @@ def last_profile() -> dict:
     lib.isoclust_last_profile(t, c)
     tl = (ctypes.c_int64 * 3)()
     lib.isoclust_last_omega_tiles(tl)
-    return dict(omega_tiles=tl[0], omega_tiles_dw=tl[1], omega_symmetric=tl[2],validate_ms=t[0], weights_ms=t[1], mst_ms=t[2], orient_ms=t[3], search_ms=t[4], labels_ms=t[5],
+    return dict(omega_tiles=tl[0], omega_tiles_dw=tl[1], omega_symmetric=tl[2],
+                omega_kernel_ms=float(lib.isoclust_last_omega_kernel_ms()), validate_ms=t[0], weights_ms=t[1], mst_ms=t[2], orient_ms=t[3], search_ms=t[4], labels_ms=t[5],
                 boruvka_rounds=c[0], rescanned_rows=c[1], alg1_passes=c[2], tree_depth=c[3])
 
 
