@@ -32,8 +32,7 @@ namespace iso {
 namespace {
 constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64;      // BK bf16 = 128 bytes (one swizzle row)
 constexpr int TC_STAGES = 3;                              // ring depth, A and B streaming
-constexpr int TC_STAGES_B = 4;                            // ring depth, A resident
-constexpr int TC_AREG_BYTES = 4 * 128 * 64 * 2;           // A hi + lo, up to 2 K chunks (d_pad <= 128)
+constexpr int TC_MAXST = 6;                               // barrier slots for the ring
 constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 2;         // 16 KB
 constexpr int TC_STAGE_BYTES = 4 * TC_TILE_BYTES;        // A hi, A lo, B hi, B lo
 constexpr int TC_EPI_WARPS = 8;                           // two per TMEM lane quadrant
@@ -48,7 +47,7 @@ constexpr long long TC_WAIT_CYCLES = 4000000000LL;
 struct __align__(16) TcShared {
     float cnorm[TC_NACC][TC_BN];
     int32_t ccomp[TC_NACC][TC_BN];
-    uint64_t full[4], empty[4];
+    uint64_t full[TC_MAXST], empty[TC_MAXST];
     uint64_t acc_full[TC_NACC], acc_empty[TC_NACC];
     uint64_t a_full, a_empty;
     uint32_t tmem_base;
@@ -58,10 +57,18 @@ static_assert(offsetof(TcShared, cnorm) % 16 == 0, "cnorm must be 16-byte aligne
 static_assert(offsetof(TcShared, ccomp) % 16 == 0, "ccomp must be 16-byte aligned");
 static_assert(offsetof(TcShared, full) % 8 == 0, "mbarriers must be 8-byte aligned");
 static_assert((TC_STAGES * TC_STAGE_BYTES) % 1024 == 0, "TcShared follows 1024-aligned tiles");
-static_assert(TC_STAGES <= 4 && TC_STAGES_B <= 4, "barrier arrays hold 4 stages");
-constexpr int TC_SMEM_STREAM = TC_STAGES * TC_STAGE_BYTES + 1024 + (int)sizeof(TcShared);
-constexpr int TC_SMEM_ARES = TC_AREG_BYTES + TC_STAGES_B * 2 * TC_TILE_BYTES + 1024 + (int)sizeof(TcShared);
-static_assert(TC_SMEM_STREAM <= 227 * 1024 && TC_SMEM_ARES <= 227 * 1024, "shared memory budget");
+// AK = K chunks of a resident row block (0: A and B stream together).  A
+// resident block of one chunk (d_pad = 64) leaves room for a deeper B ring:
+// its depth is what hides the TMA latency of the column blocks.
+__host__ __device__ constexpr int tc_areg_bytes(int AK) { return AK * 2 * TC_TILE_BYTES; }
+__host__ __device__ constexpr int tc_nst(int AK) { return AK == 0 ? TC_STAGES : (AK == 1 ? 5 : 4); }
+__host__ __device__ constexpr int tc_smem(int AK) {
+    return AK == 0 ? TC_STAGES * TC_STAGE_BYTES + 1024 + (int)sizeof(TcShared)
+                   : tc_areg_bytes(AK) + tc_nst(AK) * 2 * TC_TILE_BYTES + 1024 + (int)sizeof(TcShared);
+}
+static_assert(tc_nst(0) <= TC_MAXST && tc_nst(1) <= TC_MAXST && tc_nst(2) <= TC_MAXST, "barrier slots");
+static_assert(tc_smem(0) <= 227 * 1024 && tc_smem(1) <= 227 * 1024 && tc_smem(2) <= 227 * 1024,
+              "shared memory budget");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -186,7 +193,7 @@ struct ScreenArgs {
     int64_t T64;
 };
 
-template <bool ARES, bool SCREEN>
+template <int AK, bool SCREEN>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUtensorMap tml,
            const float *__restrict__ rnorm, const float *__restrict__ cnorm, const float *__restrict__ rsq,
@@ -198,10 +205,11 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
     if (!SCREEN && !mst_active(counters)) return;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    constexpr int NST = ARES ? TC_STAGES_B : TC_STAGES;                 // ring depth
+    constexpr bool ARES = AK > 0;
+    constexpr int NST = tc_nst(AK);                                     // ring depth
     constexpr int SB = ARES ? 2 * TC_TILE_BYTES : TC_STAGE_BYTES;       // bytes per ring stage
     unsigned char *areg = base;                                         // resident A (ARES)
-    unsigned char *ring = ARES ? base + TC_AREG_BYTES : base;
+    unsigned char *ring = base + tc_areg_bytes(AK);
     TcShared *sh = (TcShared *)(ring + NST * SB);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -1081,14 +1089,17 @@ cudaError_t tc_omega_screen(TcScratch &T, const float *Xp, int64_t n, int32_t d,
     const float acoef = (float)(1.25 * 2.0 * (3.0 * T.d_pad * u + 3.814697265625e-06));
     const float bcoef = (float)(1.25 * 8.0 * 5.9604644775390625e-08);
     const ScreenArgs scr{rowA, need, T64};
-    if (kchunks <= 2)
-        k_sweep_tc<true, true><<<grid, TC_THREADS, TC_SMEM_ARES, ISO_S(s)>>>(
-            T.map_h, T.map_l, T.nrm, T.cnrm, T.rsq, T.tmax, T.tsq, acoef, bcoef, nullptr, T.n_pad, ntiles, kchunks, 1,
-            ditems, nit, nullptr, nullptr, nullptr, nullptr, nullptr, T.err, scr);
+#define ISO_SCREEN_LAUNCH(AKV)                                                                                    \
+    k_sweep_tc<AKV, true><<<grid, TC_THREADS, tc_smem(AKV), ISO_S(s)>>>(                                          \
+        T.map_h, T.map_l, T.nrm, T.cnrm, T.rsq, T.tmax, T.tsq, acoef, bcoef, nullptr, T.n_pad, ntiles, kchunks, 1,   \
+        ditems, nit, nullptr, nullptr, nullptr, nullptr, nullptr, T.err, scr)
+    if (kchunks == 1)
+        ISO_SCREEN_LAUNCH(1);
+    else if (kchunks == 2)
+        ISO_SCREEN_LAUNCH(2);
     else
-        k_sweep_tc<false, true><<<grid, TC_THREADS, TC_SMEM_STREAM, ISO_S(s)>>>(
-            T.map_h, T.map_l, T.nrm, T.cnrm, T.rsq, T.tmax, T.tsq, acoef, bcoef, nullptr, T.n_pad, ntiles, kchunks, 1,
-            ditems, nit, nullptr, nullptr, nullptr, nullptr, nullptr, T.err, scr);
+        ISO_SCREEN_LAUNCH(0);
+#undef ISO_SCREEN_LAUNCH
     return cudaGetLastError();
 }
 
@@ -1150,18 +1161,16 @@ cudaError_t tc_prepare(TcScratch &T, const float *X, int64_t n, int32_t d, cudaS
     if ((e = make_map(&T.map_l, T.xl, T.n_pad, T.d_pad))) return e;
     static bool attr = false;
     if (!attr) {
-        if ((e = cudaFuncSetAttribute(k_sweep_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      TC_SMEM_STREAM)))
-            return e;
-        if ((e = cudaFuncSetAttribute(k_sweep_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      TC_SMEM_ARES)))
-            return e;
-        if ((e = cudaFuncSetAttribute(k_sweep_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      TC_SMEM_STREAM)))
-            return e;
-        if ((e = cudaFuncSetAttribute(k_sweep_tc<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      TC_SMEM_ARES)))
-            return e;
+#define ISO_SMEM_ATTR(AKV, SCR)                                                                                   \
+    if ((e = cudaFuncSetAttribute(k_sweep_tc<AKV, SCR>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(AKV))))  \
+        return e;
+        ISO_SMEM_ATTR(0, false)
+        ISO_SMEM_ATTR(1, false)
+        ISO_SMEM_ATTR(2, false)
+        ISO_SMEM_ATTR(0, true)
+        ISO_SMEM_ATTR(1, true)
+        ISO_SMEM_ATTR(2, true)
+#undef ISO_SMEM_ATTR
         attr = true;
     }
     return cudaGetLastError();
@@ -1186,14 +1195,17 @@ cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t 
     const double u = 1.1920928955078125e-07;   // 2^-23
     const float acoef = (float)(1.25 * 2.0 * (3.0 * T.d_pad * u + 3.814697265625e-06));
     const float bcoef = (float)(1.25 * 8.0 * 5.9604644775390625e-08);
-    if (kchunks <= 2)
-        k_sweep_tc<true, false><<<grid, TC_THREADS, TC_SMEM_ARES, ISO_S(s)>>>(
-            T.map_h, T.map_l, T.nrm, T.cnrm, T.rsq, T.tmax, T.tsq, acoef, bcoef, T.compp, T.n_pad, ntiles, kchunks,
-            T.splits, T.items, T.nitems, T.setcnt, S.counters, T.tv, T.tj, T.tu, T.err, ScreenArgs{});
+#define ISO_SWEEP_LAUNCH(AKV)                                                                                     \
+    k_sweep_tc<AKV, false><<<grid, TC_THREADS, tc_smem(AKV), ISO_S(s)>>>(                                         \
+        T.map_h, T.map_l, T.nrm, T.cnrm, T.rsq, T.tmax, T.tsq, acoef, bcoef, T.compp, T.n_pad, ntiles, kchunks,      \
+        T.splits, T.items, T.nitems, T.setcnt, S.counters, T.tv, T.tj, T.tu, T.err, ScreenArgs{})
+    if (kchunks == 1)
+        ISO_SWEEP_LAUNCH(1);
+    else if (kchunks == 2)
+        ISO_SWEEP_LAUNCH(2);
     else
-        k_sweep_tc<false, false><<<grid, TC_THREADS, TC_SMEM_STREAM, ISO_S(s)>>>(
-            T.map_h, T.map_l, T.nrm, T.cnrm, T.rsq, T.tmax, T.tsq, acoef, bcoef, T.compp, T.n_pad, ntiles, kchunks,
-            T.splits, T.items, T.nitems, T.setcnt, S.counters, T.tv, T.tj, T.tu, T.err, ScreenArgs{});
+        ISO_SWEEP_LAUNCH(0);
+#undef ISO_SWEEP_LAUNCH
     // representation error of a centred point by BF16 hi + lo: 2^-18 relative
     // per element, plus the FP32 rounding of x - c (2^-24); 25 % headroom
     const double eps_rep = 1.25 * (3.814697265625e-06 + 5.9604644775390625e-08);
