@@ -631,7 +631,7 @@ def main_moons(args):
     ms_per_step = ev0.elapsed_time(ev1) / args.steps
     value = world * n / (ms_per_step / 1000.0)
     # FP64 work of the pair kernel: |A*| n + (n - |A*|) |A*| ordered pairs,
-    # each 3d (distance) + 2d (matrix product) + ~30 (sqrt, exp, quotients) flops
+    # each 2d (dot product) + 2d (matrix product) + ~30 (sqrt, exp, quotients) flops
     lab = out["labels"].cpu().numpy()
     par = out["parent"].cpu().numpy()
     phi = out["phi_par"].cpu().numpy()
@@ -643,7 +643,7 @@ def main_moons(args):
         ratios.append(phi[cross].sum() / om[inj].sum())
     a = int((lab == int(np.argmax(ratios))).sum())
     pairs = a * n + (n - a) * a
-    flop = pairs * (5.0 * d + 30.0)
+    flop = pairs * (4.0 * d + 30.0)
     b_ms = statistics.mean(bwd)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peaks, src = _peaks()
@@ -655,8 +655,8 @@ def main_moons(args):
         "config": dict(cfg, l2="flushed by a 256 MiB write before every step (inside the timed region)"),
         "roofline": {"bound": "fp64", "achieved": flop / (b_ms / 1000.0) / 1e12, "peak": fp64_peak,
                      "unit": "TFLOP/s", "frac": flop / (b_ms / 1000.0) / 1e12 / fp64_peak, "traffic": None,
-                     "kernel": "k_omega_grad (backward pair sums, FP64)",
-                     "note": f"{pairs} ordered pairs (|A*| = {a}) x (5d + 30) flop over the backward's event time "
+                     "kernel": "k_pair_grad (backward pair sums, FP64)",
+                     "note": f"{pairs} ordered pairs (|A*| = {a}) x (4d + 30) flop over the backward's event time "
                              f"({b_ms:.2f} ms); peak = {sms} SMs x {FP64_PER_SM_CLK} DFMA x 2 flop x max SM clock"},
         "stages_ms": {"forward_ms": round(sum(times["fwd"][key] for key in ("validate_ms", "weights_ms", "mst_ms",
                                                                           "orient_ms", "search_ms", "labels_ms")), 3),

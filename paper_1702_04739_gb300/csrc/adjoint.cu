@@ -13,11 +13,14 @@
 //   adds -w (z_i - z_j) / (sigma r) to d/dz_i, the opposite to d/dz_j and
 //   w r / sigma^2 to d/dsigma.
 // Everything is FP64 (the derivative is compared with FP64 finite
-// differences).  The pair sums are tiled: 32 rows x 32 columns per step, the
-// pair coefficients in shared memory, then applied to the column points as a
-// small matrix product; every row's sums run in a fixed order, so the result
-// is deterministic.  Rows of A* pair with every point, the other rows with
-// the points of A* only.
+// differences).  The pair sums run in 64 x 64 tiles with 4 x 4 register
+// blocks: squared distances from dot products, the pair coefficients in
+// shared memory, then applied to the column points as a small matrix
+// product; partial sums per work item are added in a fixed order, so the
+// result is deterministic.  Rows of A* pair with every point, the other rows
+// with the points of A* only.
+#include <vector>
+
 #include "common.cuh"
 
 namespace iso {
@@ -25,8 +28,6 @@ cudaError_t exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, int32
 
 namespace {
 constexpr int TPB = 256;
-constexpr int AT = 32;        // rows and columns per pair tile
-constexpr int ADC = 32;       // dimensions per shared-memory chunk (static shared memory < 48 KB)
 
 inline unsigned grid_for(int64_t n) {
     const int64_t b = n > 0 ? ceil_div(n, TPB) : 1, cap = (int64_t)num_sms() * 16;
@@ -141,142 +142,235 @@ __global__ void __launch_bounds__(TPB) k_phi_grad(const T *__restrict__ X, const
     }
 }
 
-// Omega's pair sums for the rows in rlist (32 per block-step) against the
-// columns in clist (all points when clist is null).  A pair (i, j) counts
-// once per end in A* (in_i + in_j); rows of A* also sum w (-> omega_i) and
-// w r / sigma^2.  gom[i] = C_i z_i - V_i with C_i = sum_j c_ij,
-// V_i = sum_j c_ij z_j, c_ij = -(in_i + in_j) w / (sigma r).  V is held in
-// registers for 128 dimensions at a time (larger d: the pairs are revisited
-// per 128-dimension chunk).
+// Omega's pair sums.  Work item = (row group, 64-row
+// tile of the group's list, chunk of GC columns): group 0 = rows of A*
+// against every point, group 1 = the other rows against A*.  Per 64 x 64
+// pair tile: squared distances from dot products, |z_i|^2 + |z_j|^2 -
+// 2 z_i.z_j (4 x 4 pairs per thread, FP64), with a direct recomputation
+// where that cancels (d2 < 2^-20 (|z_i|^2 + |z_j|^2)); the coefficients in
+// shared memory; then V_i += sum_j c_ij z_j for 128 dimensions at a time
+// (4 rows x 1 dimension per thread and 16-dimension chunk).  Each item
+// writes its partial sums to its own slot; k_pair_reduce adds the slots of a
+// row in chunk order.
+constexpr int GT = 64;              // rows / columns per pair tile
+constexpr int GDC = 16;             // dimensions per shared-memory chunk
+constexpr int GVD = 128;            // dimensions of V per pass
+constexpr int GC = 4096;            // columns per work item
+
+struct PairItem {
+    int32_t group, tile, chunk, pad;
+};
+
 template <class T>
-__global__ void __launch_bounds__(TPB) k_omega_grad(const T *__restrict__ X, const double *__restrict__ s, int64_t n,
-                                                    int32_t d, const int32_t *__restrict__ rlist,
-                                                    const int32_t *__restrict__ rcount,
-                                                    const int32_t *__restrict__ clist,
-                                                    const int32_t *__restrict__ ccount,
-                                                    const int32_t *__restrict__ inA, double sigma,
-                                                    double *__restrict__ gom, double *__restrict__ rowom,
-                                                    double *__restrict__ rowsig) {
-    constexpr int VQ = (AT * 128) / TPB;      // accumulators per thread: (row, dimension) pairs
-    __shared__ double Zr[AT][ADC + 1];
-    __shared__ double Zc[AT][ADC + 1];
-    __shared__ double C[AT][AT + 1];          // squared distances, then the pair coefficients
-    __shared__ double W[AT][AT + 1];
-    __shared__ double WR[AT][AT + 1];
-    __shared__ int32_t ri[AT], ci[AT], rin[AT], cin[AT];
-    __shared__ double Cs[AT];
-    const int tid = threadIdx.x;
-    const int64_t nr = *rcount, nc = clist ? (int64_t)*ccount : n;
-    const int64_t ntr = (nr + AT - 1) / AT, ntc = (nc + AT - 1) / AT;
-    const int32_t dchunks = (d + 127) / 128;
-    for (int64_t tr = blockIdx.x; tr < ntr; tr += gridDim.x) {
+__global__ void __launch_bounds__(TPB, 1)
+k_pair_grad(const T *__restrict__ X, const double *__restrict__ s, int64_t n, int32_t d,
+            const double *__restrict__ N2, const int32_t *__restrict__ inA, const int32_t *__restrict__ alist,
+            const int32_t *__restrict__ blist, const int32_t *__restrict__ cnt, const PairItem *__restrict__ items,
+            int64_t nitems, double sigma, double *__restrict__ Vp, double *__restrict__ Cp, double *__restrict__ Op,
+            double *__restrict__ Sp) {
+    extern __shared__ __align__(16) double gsm[];
+    double *Zr = gsm;                                  // [GDC][GT]
+    double *Zc = Zr + GDC * GT;                        // [GDC][GT]
+    double *Cm = Zc + GDC * GT;                        // [GT][GT + 1]
+    __shared__ int32_t ri[GT], ci[GT], rin[GT], cin[GT];
+    __shared__ double rn[GT], cn[GT];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int32_t na = cnt[1], nb = cnt[2];
+    for (int64_t w = blockIdx.x; w < nitems; w += gridDim.x) {
+        const PairItem it = items[w];
+        const int32_t *rlist = it.group == 0 ? alist : blist;
+        const int64_t nr = it.group == 0 ? na : nb;
+        const int64_t ncol = it.group == 0 ? n : na;
+        const int64_t q0 = (int64_t)it.chunk * GC, q1 = min(ncol, q0 + GC);
         __syncthreads();
-        if (tid < AT) {
-            const int64_t q = tr * AT + tid;
+        if (tid < GT) {
+            const int64_t q = (int64_t)it.tile * GT + tid;
             ri[tid] = q < nr ? rlist[q] : -1;
-            rin[tid] = q < nr ? inA[ri[tid]] : 0;
+            rin[tid] = ri[tid] >= 0 ? inA[ri[tid]] : 0;
+            rn[tid] = ri[tid] >= 0 ? N2[ri[tid]] : 0.0;
         }
-        double cs = 0.0, os = 0.0, ss = 0.0;   // row tid < AT: C_i, omega_i, sigma term
-        for (int32_t dc = 0; dc < dchunks; ++dc) {
-            const int32_t t0 = dc * 128, tl = min(128, d - t0);
-            double vacc[VQ];
+        double csum[4] = {0, 0, 0, 0}, osum[4] = {0, 0, 0, 0}, ssum[4] = {0, 0, 0, 0};
+        for (int32_t v0 = 0; v0 < d; v0 += GVD) {
+            const int32_t vl = min(GVD, d - v0);
+            double V[4][GVD / GDC];
 #pragma unroll
-            for (int q = 0; q < VQ; ++q) vacc[q] = 0.0;
-            for (int64_t tc = 0; tc < ntc; ++tc) {
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int c = 0; c < GVD / GDC; ++c) V[i][c] = 0.0;
+            for (int64_t c0 = q0; c0 < q1; c0 += GT) {
                 __syncthreads();
-                if (tid < AT) {
-                    const int64_t q = tc * AT + tid;
-                    const int64_t j = q < nc ? (clist ? (int64_t)clist[q] : q) : -1;
+                if (tid < GT) {
+                    const int64_t q = c0 + tid;
+                    const int64_t j = q < q1 ? (it.group == 0 ? q : (int64_t)alist[q]) : -1;
                     ci[tid] = (int32_t)j;
                     cin[tid] = j >= 0 ? inA[j] : 0;
+                    cn[tid] = j >= 0 ? N2[j] : 0.0;
                 }
-                for (int e = tid; e < AT * AT; e += TPB) C[e / AT][e % AT] = 0.0;
-                __syncthreads();
-                // squared distances of the 32 x 32 pairs over all dimensions
-                for (int32_t u0 = 0; u0 < d; u0 += ADC) {
-                    const int ul = min(ADC, d - u0);
-                    for (int e = tid; e < AT * ADC; e += TPB) {
-                        const int r = e / ADC, t = e % ADC;
-                        Zr[r][t] = (t < ul && ri[r] >= 0) ? zv(X, s, ri[r], u0 + t, d) : 0.0;
-                        Zc[r][t] = (t < ul && ci[r] >= 0) ? zv(X, s, ci[r], u0 + t, d) : 0.0;
-                    }
-                    __syncthreads();
-                    for (int e = tid; e < AT * AT; e += TPB) {
-                        const int r = e / AT, c = e % AT;
-                        double acc = C[r][c];
-                        for (int t = 0; t < ul; ++t) {
-                            const double dz = __dsub_rn(Zr[r][t], Zc[c][t]);
-                            acc = __fma_rn(dz, dz, acc);
-                        }
-                        C[r][c] = acc;
-                    }
-                    __syncthreads();
-                }
-                // pair coefficients
-                for (int e = tid; e < AT * AT; e += TPB) {
-                    const int r = e / AT, c = e % AT;
-                    const int32_t i = ri[r], j = ci[c];
-                    double cc = 0.0, w = 0.0, wr = 0.0;
-                    const int mult = rin[r] + cin[c];
-                    if (i >= 0 && j >= 0 && i != j && mult > 0) {
-                        const double rr = sqrt(C[r][c]);
-                        const double ww = exp(-rr / sigma);
-                        if (rr > 0.0) cc = -(double)mult * ww / (sigma * rr);
-                        if (rin[r]) {
-                            w = ww;
-                            wr = ww * rr / (sigma * sigma);
-                        }
-                    }
-                    C[r][c] = cc;
-                    W[r][c] = w;
-                    WR[r][c] = wr;
-                }
-                __syncthreads();
-                if (dc == 0 && tid < AT) {
-                    for (int c = 0; c < AT; ++c) {
-                        cs = __dadd_rn(cs, C[tid][c]);
-                        os = __dadd_rn(os, W[tid][c]);
-                        ss = __dadd_rn(ss, WR[tid][c]);
-                    }
-                }
-                // V[r][t] += sum_c C[r][c] z_c[t] over this chunk's dimensions
-                for (int32_t h = 0; h < tl; h += ADC) {
-                    const int hl = min(ADC, tl - h);
-                    __syncthreads();
-                    for (int e = tid; e < AT * ADC; e += TPB) {
-                        const int c = e / ADC, t = e % ADC;
-                        Zc[c][t] = (t < hl && ci[c] >= 0) ? zv(X, s, ci[c], t0 + h + t, d) : 0.0;
-                    }
-                    __syncthreads();
+                // ---- dot products z_i . z_j, 4 x 4 per thread
+                double acc[4][4];
 #pragma unroll
-                    for (int q = 0; q < VQ; ++q) {
-                        const int e = tid + q * TPB;
-                        const int r = e / 128, t = e % 128;
-                        if (t >= h && t < h + hl) {
-                            double a = vacc[q];
-                            for (int c = 0; c < AT; ++c) a = __fma_rn(C[r][c], Zc[c][t - h], a);
-                            vacc[q] = a;
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+                for (int32_t t0 = 0; t0 < d; t0 += GDC) {
+                    __syncthreads();
+                    for (int e = tid; e < GDC * GT; e += TPB) {
+                        const int t = e / GT, r = e % GT;
+                        const bool ok = t0 + t < d;
+                        Zr[e] = (ok && ri[r] >= 0) ? zv(X, s, ri[r], t0 + t, d) : 0.0;
+                        Zc[e] = (ok && ci[r] >= 0) ? zv(X, s, ci[r], t0 + t, d) : 0.0;
+                    }
+                    __syncthreads();
+#pragma unroll 4
+                    for (int t = 0; t < GDC; ++t) {
+                        double a[4], b[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) a[i] = Zr[t * GT + ty * 4 + i];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) b[j] = Zc[t * GT + tx * 4 + j];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) acc[i][j] = __fma_rn(a[i], b[j], acc[i][j]);
+                    }
+                }
+                // ---- pair coefficients
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int r = ty * 4 + i;
+                    double cs = 0.0, os = 0.0, ss = 0.0;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int c = tx * 4 + j;
+                        const int32_t gi = ri[r], gj = ci[c];
+                        const int mult = rin[r] + cin[c];
+                        double cc = 0.0;
+                        if (gi >= 0 && gj >= 0 && gi != gj && mult > 0) {
+                            const double nsum = rn[r] + cn[c];
+                            double r2 = __fma_rn(-2.0, acc[i][j], nsum);
+                            if (r2 < nsum * 9.5367431640625e-07) {      // cancellation: direct differences
+                                double dd = 0.0;
+                                for (int32_t t = 0; t < d; ++t) {
+                                    const double df = __dsub_rn(zv(X, s, gi, t, d), zv(X, s, gj, t, d));
+                                    dd = __fma_rn(df, df, dd);
+                                }
+                                r2 = dd;
+                            }
+                            const double rr = sqrt(fmax(r2, 0.0));
+                            const double ww = exp(-rr / sigma);
+                            if (rr > 0.0) cc = -(double)mult * ww / (sigma * rr);
+                            if (rin[r] && v0 == 0) {
+                                os = os + ww;
+                                ss = ss + ww * rr / (sigma * sigma);
+                            }
+                        }
+                        Cm[r * (GT + 1) + c] = cc;
+                        cs = cs + cc;
+                    }
+                    // rows' sums over this tile's 64 columns: the 16 threads of a row, in order
+#pragma unroll
+                    for (int o = 8; o > 0; o >>= 1) {
+                        cs = cs + __shfl_down_sync(0xffffffffu, cs, o, 16);
+                        os = os + __shfl_down_sync(0xffffffffu, os, o, 16);
+                        ss = ss + __shfl_down_sync(0xffffffffu, ss, o, 16);
+                    }
+                    if (v0 == 0) {
+                        csum[i] = csum[i] + cs;
+                        osum[i] = osum[i] + os;
+                        ssum[i] = ssum[i] + ss;
+                    }
+                }
+                // ---- V[r][t] += sum_c C[r][c] z_c[t], t in [v0, v0 + vl)
+                for (int32_t h = 0; h < vl; h += GDC) {
+                    __syncthreads();
+                    for (int e = tid; e < GDC * GT; e += TPB) {
+                        const int t = e / GT, c = e % GT;
+                        Zc[e] = (h + t < vl && ci[c] >= 0) ? zv(X, s, ci[c], v0 + h + t, d) : 0.0;
+                    }
+                    __syncthreads();
+                    const int hc = h / GDC;
+#pragma unroll
+                    for (int hh = 0; hh < GVD / GDC; ++hh) {
+                        if (hh != hc) continue;
+#pragma unroll 8
+                        for (int c = 0; c < GT; ++c) {
+                            const double zc = Zc[tx * GT + c];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) V[i][hh] = __fma_rn(Cm[(ty * 4 + i) * (GT + 1) + c], zc, V[i][hh]);
                         }
                     }
                 }
             }
-            // gom[i][t] = C_i z_i[t] - V_i[t]
-            __syncthreads();
-            if (tid < AT) Cs[tid] = cs;
-            __syncthreads();
+            // partial V of this item: rows ty*4+i, dimension v0 + hh*16 + tx
 #pragma unroll
-            for (int q = 0; q < VQ; ++q) {
-                const int e = tid + q * TPB;
-                const int r = e / 128, t = e % 128;
-                const int32_t i = ri[r];
-                if (i >= 0 && t < tl)
-                    gom[(int64_t)i * d + t0 + t] = __fma_rn(Cs[r], zv(X, s, i, t0 + t, d), -vacc[q]);
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int hh = 0; hh < GVD / GDC; ++hh) {
+                    const int32_t t = v0 + hh * GDC + tx;
+                    if (t < d) Vp[(w * GT + ty * 4 + i) * (int64_t)d + t] = V[i][hh];
+                }
+        }
+        if (tx == 0) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int r = ty * 4 + i;
+                Cp[w * GT + r] = csum[i];
+                Op[w * GT + r] = osum[i];
+                Sp[w * GT + r] = ssum[i];
             }
         }
-        if (tid < AT && ri[tid] >= 0) {
-            rowom[ri[tid]] = os;
-            rowsig[ri[tid]] = ss;
+    }
+}
+
+// gom[i] = C_i z_i - V_i, omega_i and the sigma term of every listed row:
+// the item slots of its row tile added in chunk order.
+template <class T>
+__global__ void k_pair_reduce(const T *__restrict__ X, const double *__restrict__ s, int64_t n, int32_t d,
+                              const int32_t *__restrict__ alist, const int32_t *__restrict__ blist,
+                              const int32_t *__restrict__ cnt, int64_t itemsA, int64_t chunksA, int64_t chunksB,
+                              const double *__restrict__ Vp, const double *__restrict__ Cp,
+                              const double *__restrict__ Op, const double *__restrict__ Sp, double *__restrict__ gom,
+                              double *__restrict__ rowom, double *__restrict__ rowsig) {
+    const int32_t na = cnt[1], nb = cnt[2];
+    const int64_t total = (int64_t)na + nb;
+    const int64_t gs = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total * (int64_t)d; e += gs) {
+        const int64_t q = e / d;
+        const int32_t t = (int32_t)(e - q * d);
+        const bool ga = q < na;
+        const int64_t qq = ga ? q : q - na;
+        const int32_t i = ga ? alist[qq] : blist[qq];
+        const int64_t tile = qq / GT, r = qq - tile * GT;
+        const int64_t nch = ga ? chunksA : chunksB;
+        const int64_t w0 = ga ? tile * chunksA : itemsA + tile * chunksB;
+        double cs = 0.0, vs = 0.0;
+        for (int64_t k = 0; k < nch; ++k) {
+            cs = cs + Cp[(w0 + k) * GT + r];
+            vs = vs + Vp[((w0 + k) * GT + r) * (int64_t)d + t];
         }
+        gom[(int64_t)i * d + t] = __fma_rn(cs, zv(X, s, i, t, d), -vs);
+        if (t == 0) {
+            double os = 0.0, ss = 0.0;
+            for (int64_t k = 0; k < nch; ++k) {
+                os = os + Op[(w0 + k) * GT + r];
+                ss = ss + Sp[(w0 + k) * GT + r];
+            }
+            rowom[i] = os;
+            rowsig[i] = ss;
+        }
+    }
+}
+
+__global__ void k_row_norms(const float *__restrict__ Xf, const double *__restrict__ Xd, const double *__restrict__ s,
+                            int64_t n, int32_t d, double *__restrict__ N2) {
+    const int64_t gs = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gs) {
+        double acc = 0.0;
+        for (int32_t t = 0; t < d; ++t) {
+            const double z = Xf ? zv(Xf, s, i, t, d) : zv(Xd, s, i, t, d);
+            acc = __fma_rn(z, z, acc);
+        }
+        N2[i] = acc;
     }
 }
 
@@ -353,8 +447,17 @@ __global__ void k_scale_rows(const T *__restrict__ X, const double *__restrict__
 }
 }  // namespace
 
+static int64_t pair_items_bound(int64_t n) {
+    return 2 * ceil_div(n, GT) * ceil_div(n, GC) + 2;
+}
+
 size_t adjoint_bytes(int64_t n, int32_t d, int32_t k) {
     Arena A;
+    const int64_t mi = pair_items_bound(n);
+    A.take<double>(n);
+    A.take<PairItem>(mi);
+    A.take<double>((size_t)mi * GT * d);
+    A.take<double>((size_t)mi * GT * 3);
     A.take<double>((size_t)n * d);
     A.take<double>((size_t)n * d);
     A.take<double>(n);
@@ -382,6 +485,12 @@ cudaError_t adjoint_launch(const void *X, int32_t dtype, int64_t n, int32_t d, c
                            const double *omega, double grad, double *dX, double *dscale, double *dsigma, double *ik,
                            void *ws, uint32_t *status, cudaStream_t s) {
     Arena A{(char *)ws, adjoint_bytes(n, d, k) + 4096, 0, false};
+    const int64_t mi = pair_items_bound(n);
+    double *N2 = A.take<double>(n);
+    PairItem *pitems = A.take<PairItem>(mi);
+    double *Vp = A.take<double>((size_t)mi * GT * d);
+    double *Cp = A.take<double>((size_t)mi * GT * 3);
+    double *Op = Cp + mi * GT, *Sp = Op + mi * GT;
     double *gphi = A.take<double>((size_t)n * d);
     double *gom = A.take<double>((size_t)n * d);
     double *rowom = A.take<double>(n);
@@ -417,14 +526,43 @@ cudaError_t adjoint_launch(const void *X, int32_t dtype, int64_t n, int32_t d, c
     k_compact<<<g, TPB, 0, ISO_S(s)>>>(fb, pb, n, blist, cnt + 2);
     if ((e = exclusive_scan_i32(fe, pe, n, tmp, s))) return e;
     k_compact<<<g, TPB, 0, ISO_S(s)>>>(fe, pe, n, elist, cnt + 3);
-    const unsigned gp = (unsigned)(num_sms() * 2);
+    // list sizes on the host: they shape the work items of the pair sums
+    int32_t hc[4] = {0, 0, 0, 0};
+    if ((e = cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, s))) return e;
+    if ((e = cudaStreamSynchronize(s))) return e;
+    const int64_t na = hc[1], nb = hc[2];
+    const int64_t chunksA = ceil_div(n, GC), chunksB = na > 0 ? ceil_div(na, GC) : 0;
+    const int64_t tilesA = ceil_div(na, GT), tilesB = na > 0 ? ceil_div(nb, GT) : 0;
+    std::vector<PairItem> items;
+    for (int64_t t = 0; t < tilesA; ++t)
+        for (int64_t c = 0; c < chunksA; ++c) items.push_back(PairItem{0, (int32_t)t, (int32_t)c, 0});
+    for (int64_t t = 0; t < tilesB; ++t)
+        for (int64_t c = 0; c < chunksB; ++c) items.push_back(PairItem{1, (int32_t)t, (int32_t)c, 0});
+    const int64_t nit = (int64_t)items.size();
+    if (nit > mi) return cudaErrorInvalidValue;
+    if (nit > 0 &&
+        (e = cudaMemcpyAsync(pitems, items.data(), sizeof(PairItem) * nit, cudaMemcpyHostToDevice, s)))
+        return e;
+    const size_t gsm = sizeof(double) * (2 * GDC * GT + GT * (GT + 1));
+    const unsigned gp = (unsigned)(nit < num_sms() ? (nit > 0 ? nit : 1) : num_sms());
+    const unsigned gr = grid_for((na + nb) * d);
+    static bool attr = false;
+    if (!attr) {
+        if ((e = cudaFuncSetAttribute(k_pair_grad<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm)))
+            return e;
+        if ((e = cudaFuncSetAttribute(k_pair_grad<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm)))
+            return e;
+        attr = true;
+    }
     if (dtype == ISOCLUST_F64) {
         const double *Xd = (const double *)X;
         k_phi_grad<double><<<1, TPB, 0, ISO_S(s)>>>(Xd, scale, d, parent, elist, cnt + 3, sigma, gphi, sums);
-        k_omega_grad<double><<<gp, TPB, 0, ISO_S(s)>>>(Xd, scale, n, d, alist, cnt + 1, nullptr, nullptr, fa, sigma,
-                                                        gom, rowom, rowsig);
-        k_omega_grad<double><<<gp, TPB, 0, ISO_S(s)>>>(Xd, scale, n, d, blist, cnt + 2, alist, cnt + 1, fa, sigma,
-                                                        gom, rowom, rowsig);
+        k_row_norms<<<g, TPB, 0, ISO_S(s)>>>(nullptr, Xd, scale, n, d, N2);
+        if (nit > 0)
+            k_pair_grad<double><<<gp, TPB, gsm, ISO_S(s)>>>(Xd, scale, n, d, N2, fa, alist, blist, cnt, pitems, nit,
+                                                             sigma, Vp, Cp, Op, Sp);
+        k_pair_reduce<double><<<gr, TPB, 0, ISO_S(s)>>>(Xd, scale, n, d, alist, blist, cnt, tilesA * chunksA, chunksA,
+                                                         chunksB, Vp, Cp, Op, Sp, gom, rowom, rowsig);
         k_omega_total<<<1, TPB, 0, ISO_S(s)>>>(alist, cnt + 1, rowom, rowsig, sums + 2);
         k_grad_out<double><<<grid_for(n * d), TPB, 0, ISO_S(s)>>>(Xd, scale, n, d, gphi, gom, sums, sums + 2, grad, dX);
         k_grad_scale<double><<<(unsigned)ceil_div(d, 128), 128, 0, ISO_S(s)>>>(Xd, scale, n, d, gphi, gom, sums,
@@ -432,10 +570,12 @@ cudaError_t adjoint_launch(const void *X, int32_t dtype, int64_t n, int32_t d, c
     } else {
         const float *Xf = (const float *)X;
         k_phi_grad<float><<<1, TPB, 0, ISO_S(s)>>>(Xf, scale, d, parent, elist, cnt + 3, sigma, gphi, sums);
-        k_omega_grad<float><<<gp, TPB, 0, ISO_S(s)>>>(Xf, scale, n, d, alist, cnt + 1, nullptr, nullptr, fa, sigma,
-                                                       gom, rowom, rowsig);
-        k_omega_grad<float><<<gp, TPB, 0, ISO_S(s)>>>(Xf, scale, n, d, blist, cnt + 2, alist, cnt + 1, fa, sigma,
-                                                       gom, rowom, rowsig);
+        k_row_norms<<<g, TPB, 0, ISO_S(s)>>>(Xf, nullptr, scale, n, d, N2);
+        if (nit > 0)
+            k_pair_grad<float><<<gp, TPB, gsm, ISO_S(s)>>>(Xf, scale, n, d, N2, fa, alist, blist, cnt, pitems, nit,
+                                                            sigma, Vp, Cp, Op, Sp);
+        k_pair_reduce<float><<<gr, TPB, 0, ISO_S(s)>>>(Xf, scale, n, d, alist, blist, cnt, tilesA * chunksA, chunksA,
+                                                        chunksB, Vp, Cp, Op, Sp, gom, rowom, rowsig);
         k_omega_total<<<1, TPB, 0, ISO_S(s)>>>(alist, cnt + 1, rowom, rowsig, sums + 2);
         k_grad_out<float><<<grid_for(n * d), TPB, 0, ISO_S(s)>>>(Xf, scale, n, d, gphi, gom, sums, sums + 2, grad, dX);
         k_grad_scale<float><<<(unsigned)ceil_div(d, 128), 128, 0, ISO_S(s)>>>(Xf, scale, n, d, gphi, gom, sums,
