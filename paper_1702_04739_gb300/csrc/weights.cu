@@ -830,8 +830,12 @@ cudaError_t weights_launch_sym_sets(const float *Xp, int64_t n_pad, int32_t d, d
         k_tile_pair_skip<true><<<(unsigned)(num_sms() * 8), 256, 0, ISO_S(s)>>>(
             P.cen, P.rad, P.msh, d, T, nitems, witems, is_h, zskip, shrink, nullptr, P.tskip);
         if (kev) cudaEventRecord(kev[0], s);
+        // independent sets: the tile bound is the only screen; tile pairs it
+        // keeps go straight to the double-word pass (for sets of a few
+        // thousand points nearly every pair of tiles holds terms, so the FP32
+        // pair screen would cost more than the double-word work it saves)
         k_weights_sym<true><<<grid, TPB, 0, ISO_S(s)>>>(Xp, n_pad, d, P.shdw, is_h, is_l, tab, zskip, shrink, 0, nitems,
-                                                        witems, tile_valid, P.tskip, 0, P.flags, P.rpart, P.cpart,
+                                                        witems, tile_valid, P.tskip, 1, P.flags, P.rpart, P.cpart,
                                                         tile_counts);
         if (kev) cudaEventRecord(kev[1], s);
     }
