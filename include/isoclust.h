@@ -333,8 +333,10 @@ void isoclust_last_profile(double *t_ms6, int64_t *counts4);
 void isoclust_last_omega_tiles(int64_t *tiles3);
 
 /* Device time (milliseconds, CUDA events on the call's stream around its
- * launch) of the symmetric omega kernel in the last isoclust_cluster /
- * _detail / _batched call on this host thread; 0 when it did not run. */
+ * launch) of the dominant pair kernel of the last call on this host thread:
+ * the symmetric omega kernel after isoclust_cluster / _detail / _batched (0
+ * when it did not run), the FP64 pair-sum kernel of dOmega after
+ * isoclust_ik_backward. */
 double isoclust_last_omega_kernel_ms(void);
 
 #ifdef __cplusplus

@@ -483,7 +483,7 @@ size_t adjoint_bytes(int64_t n, int32_t d, int32_t k) {
 cudaError_t adjoint_launch(const void *X, int32_t dtype, int64_t n, int32_t d, const double *scale, double sigma,
                            const int32_t *parent, const int32_t *labels, int32_t k, const double *phi_par,
                            const double *omega, double grad, double *dX, double *dscale, double *dsigma, double *ik,
-                           void *ws, uint32_t *status, cudaStream_t s) {
+                           void *ws, uint32_t *status, cudaEvent_t *kev, cudaStream_t s) {
     Arena A{(char *)ws, adjoint_bytes(n, d, k) + 4096, 0, false};
     const int64_t mi = pair_items_bound(n);
     double *N2 = A.take<double>(n);
@@ -558,9 +558,11 @@ cudaError_t adjoint_launch(const void *X, int32_t dtype, int64_t n, int32_t d, c
         const double *Xd = (const double *)X;
         k_phi_grad<double><<<1, TPB, 0, ISO_S(s)>>>(Xd, scale, d, parent, elist, cnt + 3, sigma, gphi, sums);
         k_row_norms<<<g, TPB, 0, ISO_S(s)>>>(nullptr, Xd, scale, n, d, N2);
+        if (kev) cudaEventRecord(kev[0], s);
         if (nit > 0)
             k_pair_grad<double><<<gp, TPB, gsm, ISO_S(s)>>>(Xd, scale, n, d, N2, fa, alist, blist, cnt, pitems, nit,
                                                              sigma, Vp, Cp, Op, Sp);
+        if (kev) cudaEventRecord(kev[1], s);
         k_pair_reduce<double><<<gr, TPB, 0, ISO_S(s)>>>(Xd, scale, n, d, alist, blist, cnt, tilesA * chunksA, chunksA,
                                                          chunksB, Vp, Cp, Op, Sp, gom, rowom, rowsig);
         k_omega_total<<<1, TPB, 0, ISO_S(s)>>>(alist, cnt + 1, rowom, rowsig, sums + 2);
@@ -571,9 +573,11 @@ cudaError_t adjoint_launch(const void *X, int32_t dtype, int64_t n, int32_t d, c
         const float *Xf = (const float *)X;
         k_phi_grad<float><<<1, TPB, 0, ISO_S(s)>>>(Xf, scale, d, parent, elist, cnt + 3, sigma, gphi, sums);
         k_row_norms<<<g, TPB, 0, ISO_S(s)>>>(Xf, nullptr, scale, n, d, N2);
+        if (kev) cudaEventRecord(kev[0], s);
         if (nit > 0)
             k_pair_grad<float><<<gp, TPB, gsm, ISO_S(s)>>>(Xf, scale, n, d, N2, fa, alist, blist, cnt, pitems, nit,
                                                             sigma, Vp, Cp, Op, Sp);
+        if (kev) cudaEventRecord(kev[1], s);
         k_pair_reduce<float><<<gr, TPB, 0, ISO_S(s)>>>(Xf, scale, n, d, alist, blist, cnt, tilesA * chunksA, chunksA,
                                                         chunksB, Vp, Cp, Op, Sp, gom, rowom, rowsig);
         k_omega_total<<<1, TPB, 0, ISO_S(s)>>>(alist, cnt + 1, rowom, rowsig, sums + 2);

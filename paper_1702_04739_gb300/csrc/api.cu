@@ -34,7 +34,7 @@ size_t adjoint_bytes(int64_t n, int32_t d, int32_t k);
 cudaError_t adjoint_launch(const void *X, int32_t dtype, int64_t n, int32_t d, const double *scale, double sigma,
                            const int32_t *parent, const int32_t *labels, int32_t k, const double *phi_par,
                            const double *omega, double grad, double *dX, double *dscale, double *dsigma, double *ik,
-                           void *ws, uint32_t *status, cudaStream_t s);
+                           void *ws, uint32_t *status, cudaEvent_t *kev, cudaStream_t s);
 cudaError_t scale_rows_launch(const void *X, int32_t dtype, int64_t n, int32_t d, const double *scale, void *Z,
                               cudaStream_t s);
 
@@ -909,13 +909,14 @@ isoclust_status isoclust_ik_backward(const void *X, int64_t n, int32_t d, int32_
     ev.rec(0, s);
     ISO_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t), s));
     ISO_CUDA(adjoint_launch(X, dtype, n, d, scale, sigma, parent, labels, k, phi_par, omega, grad_ik, dX, dscale,
-                            dsigma, i_k, ws, status, s));
+                            dsigma, i_k, ws, status, ev.ok ? ev.e + 8 : nullptr, s));
     ev.rec(1, s);
     ISO_CUDA(cudaStreamSynchronize(s));
     uint32_t hst = 0;
     ISO_CUDA(cudaMemcpy(&hst, status, sizeof(uint32_t), cudaMemcpyDeviceToHost));
     for (int i = 0; i < 6; ++i) g_prof_ms[i] = 0.0;
     g_prof_ms[4] = ev.ms(0, 1);
+    g_prof_omega_kernel_ms = ev.ms(8, 9);
     if (hst & DEV_NEGATIVE) return fail(ISOCLUST_ERR_INVALID_ARG, "a label 0..k-1 has no points or no positive omega");
     return map_status(hst, true);
 }
