@@ -260,7 +260,9 @@ isoclust_status isoclust_cluster_detail(const void *X, int64_t n, int32_t d, int
  * Needs an sm_103 device (tensor-core sweep).  The plan of the launch is
  * built on the host from offsets, hence host arrays.  Errors: as
  * isoclust_cluster, per set; a set with fewer than 2 points or ks[b] < 1 ->
- * ISOCLUST_ERR_INVALID_ARG, ks[b] above the set's size -> ISOCLUST_ERR_K_GT_N.
+ * ISOCLUST_ERR_INVALID_ARG, ks[b] above the set's size -> ISOCLUST_ERR_K_GT_N;
+ * more than 2^31 rows once every set is rounded up to a multiple of 128 ->
+ * ISOCLUST_ERR_INVALID_ARG.
  */
 isoclust_status isoclust_cluster_batched(const void *X, const int64_t *offsets, int32_t nsets,
                                          int32_t d, int32_t dtype, const int32_t *ks, double sigma,

@@ -637,6 +637,9 @@ static isoclust_status cluster_sets_impl(const void *X, const int64_t *offsets, 
     h_tcbase[P] = tc;
     h_item0[P] = it;
     const int64_t n_pad128 = rb, ntc = tc, n_pad64 = t64 * 64, ntile64 = t64, nitems = it;
+    // the sweep addresses padded rows with 32-bit column indices
+    if (n_pad128 > 2147483648LL)
+        return fail(ISOCLUST_ERR_INVALID_ARG, "the sets' padded rows (%lld) exceed 2^31", (long long)n_pad128);
 
     const int dev = current_device();
     std::lock_guard<std::mutex> lock(g_call_mu[dev]);

@@ -31,12 +31,13 @@ namespace iso {
 
 namespace {
 constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64;      // BK bf16 = 128 bytes (one swizzle row)
-constexpr int TC_STAGES = 3;                              // ring depth, A and B streaming
-constexpr int TC_MAXST = 6;                               // barrier slots for the ring
-constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 2;         // 16 KB
-constexpr int TC_STAGE_BYTES = 4 * TC_TILE_BYTES;        // A hi, A lo, B hi, B lo
+constexpr int TC_NP = 2;                                  // column tiles per MMA (N = 256)
+constexpr int TC_BNP = TC_NP * TC_BN;
+constexpr int TC_NST = 2;                                 // ring depth
+constexpr int TC_MAXST = TC_NST;                          // barrier slots for the ring
+constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 2;         // 16 KB: 128 rows x one K chunk
 constexpr int TC_EPI_WARPS = 8;                           // two per TMEM lane quadrant
-constexpr int TC_NACC = 4;                                // TMEM accumulators (4 x 128 columns = all 512)
+constexpr int TC_NACC = 2;                                // TMEM accumulators (2 x 256 columns = all 512)
 constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;
 constexpr int TC_TOPK = 8;                                // best half-tiles kept per (list, row)
 constexpr int TC_CW = TC_BN / 2;                          // columns per candidate (half-tile)
@@ -45,8 +46,8 @@ constexpr long long TC_WAIT_CYCLES = 4000000000LL;
 
 // Column metadata first: the epilogue reads it with 16-byte vector loads.
 struct __align__(16) TcShared {
-    float cnorm[TC_NACC][TC_BN];
-    int32_t ccomp[TC_NACC][TC_BN];
+    float cnorm[TC_NACC][TC_BNP];
+    int32_t ccomp[TC_NACC][TC_BNP];
     uint64_t full[TC_MAXST], empty[TC_MAXST];
     uint64_t acc_full[TC_NACC], acc_empty[TC_NACC];
     uint64_t a_full, a_empty;
@@ -56,17 +57,16 @@ struct __align__(16) TcShared {
 static_assert(offsetof(TcShared, cnorm) % 16 == 0, "cnorm must be 16-byte aligned");
 static_assert(offsetof(TcShared, ccomp) % 16 == 0, "ccomp must be 16-byte aligned");
 static_assert(offsetof(TcShared, full) % 8 == 0, "mbarriers must be 8-byte aligned");
-static_assert((TC_STAGES * TC_STAGE_BYTES) % 1024 == 0, "TcShared follows 1024-aligned tiles");
 // AK = K chunks of a resident row block (0: A and B stream together).  A
-// resident block of one chunk (d_pad = 64) leaves room for a deeper B ring:
-// its depth is what hides the TMA latency of the column blocks.
+// ring stage holds one K chunk of a pair of column tiles, hi and lo (B hi
+// 256 rows, B lo 256 rows), preceded by the row tile's chunk (A hi, A lo)
+// when A streams.
 __host__ __device__ constexpr int tc_areg_bytes(int AK) { return AK * 2 * TC_TILE_BYTES; }
-__host__ __device__ constexpr int tc_nst(int AK) { return AK == 0 ? TC_STAGES : (AK == 1 ? 5 : 4); }
+__host__ __device__ constexpr int tc_sb(int AK) { return (AK > 0 ? 2 * TC_NP : 2 + 2 * TC_NP) * TC_TILE_BYTES; }
 __host__ __device__ constexpr int tc_smem(int AK) {
-    return AK == 0 ? TC_STAGES * TC_STAGE_BYTES + 1024 + (int)sizeof(TcShared)
-                   : tc_areg_bytes(AK) + tc_nst(AK) * 2 * TC_TILE_BYTES + 1024 + (int)sizeof(TcShared);
+    return tc_areg_bytes(AK) + TC_NST * tc_sb(AK) + 1024 + (int)sizeof(TcShared);
 }
-static_assert(tc_nst(0) <= TC_MAXST && tc_nst(1) <= TC_MAXST && tc_nst(2) <= TC_MAXST, "barrier slots");
+static_assert(tc_sb(0) % 1024 == 0 && tc_sb(1) % 1024 == 0, "TcShared follows 1024-aligned tiles");
 static_assert(tc_smem(0) <= 227 * 1024 && tc_smem(1) <= 227 * 1024 && tc_smem(2) <= 227 * 1024,
               "shared memory budget");
 
@@ -132,16 +132,20 @@ __device__ __forceinline__ uint64_t make_sw128_desc(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both K-major, M=128, N=128.
-constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
-                              ((uint32_t)(TC_BM >> 4) << 24);
+// Instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both K-major, M=128,
+// N = 256 (a pair of column tiles) or 128 (the last tile of an odd range).
+__host__ __device__ constexpr uint32_t tc_idesc(int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+}
+static_assert(TC_BNP % 16 == 0 && TC_BNP <= 256, "N of one MMA");
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accum) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(TC_IDESC), "r"(accum)
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
         : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
@@ -161,6 +165,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// m = min(m, v) unless the column's component is the row's (a predicated
+// min: compare + min per element)
+__device__ __forceinline__ void min_foreign(float &m, float v, int32_t ccol, int32_t crow) {
+    asm("{\n\t.reg .pred p;\n\t"
+        "setp.ne.s32 p, %1, %2;\n\t"
+        "@p min.f32 %0, %0, %3;\n\t}"
+        : "+f"(m)
+        : "r"(ccol), "r"(crow), "f"(v));
+}
 
 __device__ __forceinline__ void top_insert(float (&v)[TC_TOPK], int32_t (&j)[TC_TOPK], float x, int32_t c) {
     v[TC_TOPK - 1] = x;
@@ -206,8 +220,8 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     constexpr bool ARES = AK > 0;
-    constexpr int NST = tc_nst(AK);                                     // ring depth
-    constexpr int SB = ARES ? 2 * TC_TILE_BYTES : TC_STAGE_BYTES;       // bytes per ring stage
+    constexpr int NST = TC_NST;                                         // ring depth
+    constexpr int SB = tc_sb(AK);                                       // bytes per ring stage
     unsigned char *areg = base;                                         // resident A (ARES)
     unsigned char *ring = base + tc_areg_bytes(AK);
     TcShared *sh = (TcShared *)(ring + NST * SB);
@@ -228,7 +242,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh->tmem_base)),
-                     "n"(TC_NACC * TC_BN)
+                     "n"(TC_NACC * TC_BNP)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -273,19 +287,22 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
                     }
                     a_phase ^= 1u;
                 }
-                for (int ct = c0; ct < c1 && ok; ++ct) {
+                for (int ct = c0; ct < c1 && ok; ct += TC_NP) {
+                    const int nct = min(TC_NP, c1 - ct);
                     for (int kc = 0; kc < kchunks; ++kc) {
                         if (!(ok = mbar_wait(&sh->empty[stage], phase ^ 1u, err))) break;
                         unsigned char *st = ring + stage * SB;
-                        mbar_expect_tx(&sh->full[stage], (uint32_t)SB);
-                        if (ARES) {
-                            tma_load_2d(st, &tmh, kc * TC_BK, ct * TC_BN, &sh->full[stage]);
-                            tma_load_2d(st + TC_TILE_BYTES, &tml, kc * TC_BK, ct * TC_BN, &sh->full[stage]);
-                        } else {
+                        // stage: [A hi][A lo] (streaming A) then [B hi: NP tiles][B lo: NP tiles]
+                        unsigned char *sbh = st + (ARES ? 0 : 2 * TC_TILE_BYTES);
+                        unsigned char *sbl = sbh + TC_NP * TC_TILE_BYTES;
+                        mbar_expect_tx(&sh->full[stage], (uint32_t)((ARES ? 0 : 2) + 2 * nct) * TC_TILE_BYTES);
+                        if (!ARES) {
                             tma_load_2d(st, &tmh, kc * TC_BK, rt * TC_BM, &sh->full[stage]);
                             tma_load_2d(st + TC_TILE_BYTES, &tml, kc * TC_BK, rt * TC_BM, &sh->full[stage]);
-                            tma_load_2d(st + 2 * TC_TILE_BYTES, &tmh, kc * TC_BK, ct * TC_BN, &sh->full[stage]);
-                            tma_load_2d(st + 3 * TC_TILE_BYTES, &tml, kc * TC_BK, ct * TC_BN, &sh->full[stage]);
+                        }
+                        for (int q = 0; q < nct; ++q) {
+                            tma_load_2d(sbh + q * TC_TILE_BYTES, &tmh, kc * TC_BK, (ct + q) * TC_BN, &sh->full[stage]);
+                            tma_load_2d(sbl + q * TC_TILE_BYTES, &tml, kc * TC_BK, (ct + q) * TC_BN, &sh->full[stage]);
                         }
                         if (++stage == NST) { stage = 0; phase ^= 1u; }
                     }
@@ -305,33 +322,25 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
                     if (!(ok = mbar_wait(&sh->a_full, a_phase, err))) break;
                     tc_fence_after();
                 }
-                for (int ct = c0; ct < c1 && ok; ++ct) {
+                for (int ct = c0; ct < c1 && ok; ct += TC_NP) {
+                    const uint32_t idesc = tc_idesc(min(TC_NP, c1 - ct) * TC_BN);
                     if (!(ok = mbar_wait(&sh->acc_empty[acc], acc_phase ^ 1u, err))) break;
                     tc_fence_after();
-                    const uint32_t dt = tmem + acc * TC_BN;
+                    const uint32_t dt = tmem + acc * TC_BNP;
                     for (int kc = 0; kc < kchunks; ++kc) {
                         if (!(ok = mbar_wait(&sh->full[stage], phase, err))) break;
                         tc_fence_after();
                         const uint32_t sb = smem_u32(ring + stage * SB);
-                        uint64_t ah, al, bh, bl;
-                        if (ARES) {
-                            const uint32_t sa = smem_u32(areg + (2 * kc) * TC_TILE_BYTES);
-                            ah = make_sw128_desc(sa);
-                            al = make_sw128_desc(sa + TC_TILE_BYTES);
-                            bh = make_sw128_desc(sb);
-                            bl = make_sw128_desc(sb + TC_TILE_BYTES);
-                        } else {
-                            ah = make_sw128_desc(sb);
-                            al = make_sw128_desc(sb + TC_TILE_BYTES);
-                            bh = make_sw128_desc(sb + 2 * TC_TILE_BYTES);
-                            bl = make_sw128_desc(sb + 3 * TC_TILE_BYTES);
-                        }
+                        const uint32_t sbh = sb + (ARES ? 0 : 2 * TC_TILE_BYTES), sbl = sbh + TC_NP * TC_TILE_BYTES;
+                        const uint32_t sa = ARES ? smem_u32(areg + (2 * kc) * TC_TILE_BYTES) : sb;
+                        const uint64_t ah = make_sw128_desc(sa), al = make_sw128_desc(sa + TC_TILE_BYTES);
+                        const uint64_t bh = make_sw128_desc(sbh), bl = make_sw128_desc(sbl);
 #pragma unroll
                         for (int kk = 0; kk < TC_BK / 16; ++kk) {
                             const uint64_t o = (uint64_t)(kk * 32) >> 4;   // 16 bf16 = 32 bytes
-                            mma_bf16(dt, ah + o, bh + o, (kc > 0 || kk > 0) ? 1u : 0u);
-                            mma_bf16(dt, ah + o, bl + o, 1u);
-                            mma_bf16(dt, al + o, bh + o, 1u);
+                            mma_bf16(dt, ah + o, bh + o, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                            mma_bf16(dt, ah + o, bl + o, idesc, 1u);
+                            mma_bf16(dt, al + o, bh + o, idesc, 1u);
                         }
                         mma_commit(&sh->empty[stage]);
                         if (++stage == NST) { stage = 0; phase ^= 1u; }
@@ -348,11 +357,14 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
         }
     } else {
         // ------------------------------------------------ epilogue (warps 2..9)
+        // warps 2..5 take the first column tile of a pair, 6..9 the second;
+        // each warp covers its tile's 128 columns as two 64-column candidate
+        // blocks, for the 32 rows of its TMEM lane quadrant
         const int et = threadIdx.x - 64;               // 0..255
-        const int h = et >> 7;                         // column half of the tile
+        const int h = et >> 7;                         // column tile of the pair
         const int quad = warp & 3;                     // TMEM lane quadrant of this warp
         const int trow = quad * 32 + lane;             // row within the tile = TMEM lane
-        const int cm = et & (TC_BN - 1);               // column whose metadata this thread stages
+        const int cm = et;                             // column of the pair whose metadata this thread stages
         uint32_t acc = 0, acc_phase = 0;
         bool ok = true;
         for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
@@ -368,100 +380,109 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
             int32_t bj[TC_TOPK];
 #pragma unroll
             for (int q = 0; q < TC_TOPK; ++q) { bv[q] = INFINITY; bj[q] = -1; }
-            // column metadata, prefetched one tile ahead by the first half's threads
-            int64_t pcol = (int64_t)c0 * TC_BN + cm;
+            // column metadata, prefetched one pair of tiles ahead (columns of
+            // a missing second tile: +inf norm, no component)
             float pn = INFINITY;
             int32_t pc = -2;
-            if (h == 0 && c0 < c1) { pn = cnorm[pcol]; pc = SCREEN ? __float_as_int(scr.rowA[pcol]) : comp[pcol]; }
+            if (c0 < c1 && cm < min(TC_NP, c1 - c0) * TC_BN) {
+                const int64_t pcol = (int64_t)c0 * TC_BN + cm;
+                pn = cnorm[pcol];
+                pc = SCREEN ? __float_as_int(scr.rowA[pcol]) : comp[pcol];
+            }
             float ptsq = 0.f, ptmax = 0.f;
-            if (c0 < c1) { ptsq = __ldg(tsq + c0); ptmax = __ldg(tmax + c0); }
-            for (int ct = c0; ct < c1; ++ct) {
-                if (h == 0) {
-                    sh->cnorm[acc][cm] = pn;
-                    sh->ccomp[acc][cm] = pc;
-                }
+            if (c0 + h < c1) { ptsq = __ldg(tsq + c0 + h); ptmax = __ldg(tmax + c0 + h); }
+            for (int ct = c0; ct < c1; ct += TC_NP) {
+                sh->cnorm[acc][cm] = pn;
+                sh->ccomp[acc][cm] = pc;
                 const float ctsq = ptsq, ctmax = ptmax;
-                if (ct + 1 < c1) {
-                    pcol = (int64_t)(ct + 1) * TC_BN + cm;
-                    if (h == 0) {
+                const bool mine = ct + h < c1;          // this warp's column tile exists (warp-uniform)
+                const int cn2 = ct + TC_NP;
+                if (cn2 < c1) {
+                    pn = INFINITY;
+                    pc = -2;
+                    if (cm < min(TC_NP, c1 - cn2) * TC_BN) {
+                        const int64_t pcol = (int64_t)cn2 * TC_BN + cm;
                         pn = cnorm[pcol];
                         pc = SCREEN ? __float_as_int(scr.rowA[pcol]) : comp[pcol];
                     }
-                    ptsq = __ldg(tsq + ct + 1);
-                    ptmax = __ldg(tmax + ct + 1);
+                    if (cn2 + h < c1) { ptsq = __ldg(tsq + cn2 + h); ptmax = __ldg(tmax + cn2 + h); }
                 }
                 asm volatile("bar.sync 1, %0;" ::"n"(32 * TC_EPI_WARPS) : "memory");
                 if (ok) ok = mbar_wait(&sh->acc_full[acc], acc_phase, err);
                 tc_fence_after();
-                float m = INFINITY;        // min over the half-tile of n_j - 2 g (foreign columns)
-                bool near = false;         // SCREEN: a pair of this half-tile within the cutoff
                 // SCREEN: d2 >= v + n_i - dlt with v = n_j - 2g; near if that
                 // bound <= max(A_i, A_j), i.e. v <= max(A_i, A_j) + (dlt - n_i)
                 const float dlt = acoef * srow * ctsq + bcoef * (nrow + ctmax);
                 // (padding rows: arow = -inf makes both thresholds -inf; the
-                // warp-collective TMEM loads stay unconditional)
+                // warp-collective TMEM loads stay unconditional within a warp)
                 const bool rvalid = arow > -INFINITY;
                 const float Ci = SCREEN ? (rvalid ? __fadd_ru(__fadd_ru(dlt, 1e-5f * (nrow + ctmax)), -nrow) : -INFINITY)
                                         : 0.0f;
                 const float Bi = SCREEN ? (rvalid ? __fadd_ru(arow, Ci) : -INFINITY) : 0.0f;
-                if (ok) {
-                    const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + acc * TC_BN + h * TC_CW;
-                    uint32_t g0[32], g1[32];
-                    tmem_ld32(tbase, g0);
-                    tmem_ld32(tbase + 32, g1);
-                    tmem_ld_wait();
-                    const float *cn = &sh->cnorm[acc][h * TC_CW];
-                    const int32_t *cc = &sh->ccomp[acc][h * TC_CW];
+#pragma unroll 1
+                for (int sub = 0; sub < 2; ++sub) {
+                    float m = INFINITY;        // min over the block of n_j - 2 g (foreign columns)
+                    bool near = false;         // SCREEN: a pair of this block within the cutoff
+                    if (ok && mine) {
+                        const int cofs = h * TC_BN + sub * TC_CW;
+                        const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + acc * TC_BNP + cofs;
+                        uint32_t g0[32], g1[32];
+                        tmem_ld32(tbase, g0);
+                        tmem_ld32(tbase + 32, g1);
+                        tmem_ld_wait();
+                        const float *cn = &sh->cnorm[acc][cofs];
+                        const int32_t *cc = &sh->ccomp[acc][cofs];
 #pragma unroll
-                    for (int q = 0; q < 32; q += 4) {
-                        const float4 nc = *reinterpret_cast<const float4 *>(cn + q);
-                        const int4 cmv4 = *reinterpret_cast<const int4 *>(cc + q);
-                        const float ncv[4] = {nc.x, nc.y, nc.z, nc.w};
-                        const int32_t cmv[4] = {cmv4.x, cmv4.y, cmv4.z, cmv4.w};
+                        for (int q = 0; q < 32; q += 4) {
+                            const float4 nc = *reinterpret_cast<const float4 *>(cn + q);
+                            const int4 cmv4 = *reinterpret_cast<const int4 *>(cc + q);
+                            const float ncv[4] = {nc.x, nc.y, nc.z, nc.w};
+                            const int32_t cmv[4] = {cmv4.x, cmv4.y, cmv4.z, cmv4.w};
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const float v = __fmaf_rn(-2.0f, __uint_as_float(g0[q + u]), ncv[u]);
-                            if constexpr (SCREEN)
-                                near |= v <= fmaxf(Bi, __fadd_ru(__int_as_float(cmv[u]), Ci));
-                            else
-                                m = fminf(m, cmv[u] != crow ? v : INFINITY);
+                            for (int u = 0; u < 4; ++u) {
+                                const float v = __fmaf_rn(-2.0f, __uint_as_float(g0[q + u]), ncv[u]);
+                                if constexpr (SCREEN)
+                                    near |= v <= fmaxf(Bi, __fadd_ru(__int_as_float(cmv[u]), Ci));
+                                else
+                                    min_foreign(m, v, cmv[u], crow);
+                            }
+                        }
+#pragma unroll
+                        for (int q = 0; q < 32; q += 4) {
+                            const float4 nc = *reinterpret_cast<const float4 *>(cn + 32 + q);
+                            const int4 cmv4 = *reinterpret_cast<const int4 *>(cc + 32 + q);
+                            const float ncv[4] = {nc.x, nc.y, nc.z, nc.w};
+                            const int32_t cmv[4] = {cmv4.x, cmv4.y, cmv4.z, cmv4.w};
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const float v = __fmaf_rn(-2.0f, __uint_as_float(g1[q + u]), ncv[u]);
+                                if constexpr (SCREEN)
+                                    near |= v <= fmaxf(Bi, __fadd_ru(__int_as_float(cmv[u]), Ci));
+                                else
+                                    min_foreign(m, v, cmv[u], crow);
+                            }
                         }
                     }
-#pragma unroll
-                    for (int q = 0; q < 32; q += 4) {
-                        const float4 nc = *reinterpret_cast<const float4 *>(cn + 32 + q);
-                        const int4 cmv4 = *reinterpret_cast<const int4 *>(cc + 32 + q);
-                        const float ncv[4] = {nc.x, nc.y, nc.z, nc.w};
-                        const int32_t cmv[4] = {cmv4.x, cmv4.y, cmv4.z, cmv4.w};
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const float v = __fmaf_rn(-2.0f, __uint_as_float(g1[q + u]), ncv[u]);
-                            if constexpr (SCREEN)
-                                near |= v <= fmaxf(Bi, __fadd_ru(__int_as_float(cmv[u]), Ci));
-                            else
-                                m = fminf(m, cmv[u] != crow ? v : INFINITY);
+                    if constexpr (SCREEN) {
+                        // rows of this warp are one 64-row half of the row tile
+                        if (__ballot_sync(0xffffffffu, near) && lane == 0) {
+                            const int64_t I64 = 2 * (int64_t)rt + (quad >> 1), J64 = 2 * (int64_t)(ct + h) + sub;
+                            if (I64 < scr.T64 && J64 < scr.T64) scr.need[I64 * scr.T64 + J64] = 1;
                         }
+                    } else if (mine) {
+                        m = __fadd_rn(m, nrow);
+                        // rigorous bounds of the block's smallest d2 of the represented
+                        // points: accumulation + dropped lo.lo (A s_i s_j) and FP32
+                        // norm/epilogue rounding
+                        const float lb = m - dlt;
+                        ubest = fminf(ubest, m + dlt);
+                        if (lb < bv[TC_TOPK - 1]) top_insert(bv, bj, lb, 2 * (ct + h) + sub);
                     }
                 }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sh->acc_empty[acc]);
                 if (++acc == TC_NACC) { acc = 0; acc_phase ^= 1u; }
-                if constexpr (SCREEN) {
-                    // rows of this warp are one 64-row half of the row tile
-                    if (__ballot_sync(0xffffffffu, near) && lane == 0) {
-                        const int64_t I64 = 2 * (int64_t)rt + (quad >> 1), J64 = 2 * (int64_t)ct + h;
-                        if (I64 < scr.T64 && J64 < scr.T64) scr.need[I64 * scr.T64 + J64] = 1;
-                    }
-                    continue;
-                }
-                m = __fadd_rn(m, nrow);
-                // rigorous bounds of the half-tile's smallest d2 of the represented
-                // points: accumulation + dropped lo.lo (A s_i s_j) and FP32
-                // norm/epilogue rounding
-                const float lb = m - dlt;
-                ubest = fminf(ubest, m + dlt);
-                if (lb < bv[TC_TOPK - 1]) top_insert(bv, bj, lb, 2 * ct + h);
             }
             if (!SCREEN) {
                 const size_t o = ((size_t)(2 * sp + h) * nrows + row) * TC_TOPK;
@@ -475,7 +496,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TC_NACC * TC_BN)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TC_NACC * TC_BNP)
                      : "memory");
     }
 }
@@ -780,11 +801,11 @@ __device__ __forceinline__ void recheck_row(int64_t r, int lane, const float *__
     const int32_t ci = compp[r];
     const float *xi = xs + r * d;
     const bool vec = (d & 3) == 0 && (reinterpret_cast<uintptr_t>(xs) & 15) == 0;
-    auto scan = [&](int k, bool second, int64_t (&jp)[4], bool (&live)[4], float (&acc)[4]) {
+    auto scan = [&](int k, bool second, int32_t (&jp)[4], bool (&live)[4], float (&acc)[4]) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int cand = (u < 2) ? bj[k] : (second ? bj[k + 1] : -1);
-            jp[u] = cand < 0 ? -1 : (int64_t)cand * TC_CW + lane + 32 * (u & 1);
+            jp[u] = cand < 0 ? -1 : cand * TC_CW + lane + 32 * (u & 1);   // padded column (< n_pad < 2^31)
             int32_t cj = -2;
             if (jp[u] >= 0 && jp[u] < n) cj = compp[jp[u]];
             live[u] = cj >= 0 && cj != ci;                                 // padding: -2
@@ -797,7 +818,7 @@ __device__ __forceinline__ void recheck_row(int64_t r, int lane, const float *__
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     if (!live[u]) continue;
-                    const float4 b = reinterpret_cast<const float4 *>(xs + jp[u] * d)[t];
+                    const float4 b = reinterpret_cast<const float4 *>(xs + (int64_t)jp[u] * d)[t];
                     float df = __fsub_rn(a.x, b.x); acc[u] = __fmaf_rn(df, df, acc[u]);
                     df = __fsub_rn(a.y, b.y); acc[u] = __fmaf_rn(df, df, acc[u]);
                     df = __fsub_rn(a.z, b.z); acc[u] = __fmaf_rn(df, df, acc[u]);
@@ -807,27 +828,36 @@ __device__ __forceinline__ void recheck_row(int64_t r, int lane, const float *__
         } else {
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-                if (live[u]) acc[u] = approx_d2_f32(xi, xs + jp[u] * d, d);
+                if (live[u]) acc[u] = approx_d2_f32(xi, xs + (int64_t)jp[u] * d, d);
         }
     };
-    float pmin[TC_TOPK / 2];
+    // pass 1 keeps its distances in registers; pass 2 filters them against
+    // the threshold without reading the columns again
+    constexpr int NPASS = TC_TOPK / 2;
+    float pmin[NPASS];
+    float accs[NPASS][4];
+    int32_t jps[NPASS][4];
+    bool lives[NPASS][4];
     int npass = 0;
     float m32 = INFINITY;
-    for (int k = 0; k < TC_TOPK; k += 2) {
-        if (bj[k] < 0 || bv[k] > tile_cut) break;
+    bool more = true;
+#pragma unroll
+    for (int p = 0; p < NPASS; ++p) {
+        pmin[p] = INFINITY;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) { accs[p][u] = INFINITY; jps[p][u] = -1; lives[p][u] = false; }
+        const int k = 2 * p;
+        if (!more || bj[k] < 0 || bv[k] > tile_cut) { more = false; continue; }
         const bool second = bj[k + 1] >= 0 && bv[k + 1] <= tile_cut;
-        int64_t jp[4];
-        bool live[4];
-        float acc[4];
-        scan(k, second, jp, live, acc);
+        scan(k, second, jps[p], lives[p], accs[p]);
         float pm = INFINITY;
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-            if (live[u]) pm = fminf(pm, acc[u]);
-        pmin[k >> 1] = pm;
+            if (lives[p][u]) pm = fminf(pm, accs[p][u]);
+        pmin[p] = pm;
         m32 = fminf(m32, pm);
         ++npass;
-        if (!second) break;
+        if (!second) more = false;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m32 = fminf(m32, __shfl_xor_sync(0xffffffffu, m32, o));
@@ -837,20 +867,15 @@ __device__ __forceinline__ void recheck_row(int64_t r, int lane, const float *__
     }
     const float thr = __fadd_ru(__fmul_ru(m32, mul32), add32);
     int cnt = 0;
-    for (int p = 0; p < npass; ++p) {
-        if (!__any_sync(0xffffffffu, pmin[p] <= thr)) continue;
-        const int k = 2 * p;
-        const bool second = bj[k + 1] >= 0 && bv[k + 1] <= tile_cut;
-        int64_t jp[4];
-        bool live[4];
-        float acc[4];
-        scan(k, second, jp, live, acc);
+#pragma unroll
+    for (int p = 0; p < NPASS; ++p) {
+        if (p >= npass || !__any_sync(0xffffffffu, pmin[p] <= thr)) continue;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const bool sv = live[u] && acc[u] <= thr;
+            const bool sv = lives[p][u] && accs[p][u] <= thr;
             const unsigned bal = __ballot_sync(0xffffffffu, sv);
             const int slot = cnt + __popc(bal & ((1u << lane) - 1u));
-            if (sv && slot < TC_SURV) surv[r * TC_SURV + slot] = (int32_t)jp[u];
+            if (sv && slot < TC_SURV) surv[r * TC_SURV + slot] = jps[p][u];
             cnt += __popc(bal);
         }
     }
@@ -896,7 +921,7 @@ __global__ void __launch_bounds__(256) k_exact_tc(const float *__restrict__ xs, 
     }
 }
 
-__global__ void __launch_bounds__(256, 4) k_recheck_tc(const float *__restrict__ xs, int64_t n, int32_t d, int lists,
+__global__ void __launch_bounds__(256, 3) k_recheck_tc(const float *__restrict__ xs, int64_t n, int32_t d, int lists,
                                                        const float *__restrict__ tv, const int32_t *__restrict__ tj,
                                                        const float *__restrict__ tu, const float *__restrict__ rsq,
                                                        const int32_t *__restrict__ perm,
