@@ -45,7 +45,8 @@ struct TcScratch {
     int64_t n_pad = 0;                             // padded row space (whole 128-row tiles)
     int32_t d_pad = 0;
     int splits = 1;                                // column splits per row tile (one set)
-    int lists = 2;                                 // candidate lists per row (2 per split: tile halves)
+    int lists = 2;                                 // candidate lists per row (2 per split: tiles of a pair)
+    int cw = 64;                                   // columns per candidate block (64 or 32; set by tc_prepare)
     __nv_bfloat16 *xh = nullptr, *xl = nullptr;   // row r is point permp[r] (zero rows at padding)
     float *xs = nullptr;                           // [n_pad][d] the points themselves in the same order
     float *nrm = nullptr, *rsq = nullptr;          // |y|^2 and |y| of the represented rows (0 at padding)

@@ -5,19 +5,20 @@
 // The squared distance is taken from the Gram matrix,
 //     d2(i, j) = |x_i|^2 + |x_j|^2 - 2 <x_i, x_j>,
 // whose dense <x_i, x_j> tiles are the only tensor-core work: the centred
-// points are split into BF16 hi + lo parts and each 128x128 tile is
-// hi.hi + hi.lo + lo.hi (three kind::f16 MMAs per 16-wide K step) with FP32
-// accumulation in tensor memory.  Per CTA:
+// points are split into BF16 hi + lo parts and each 128-row tile against a
+// pair of 128-column tiles is hi.hi + hi.lo + lo.hi (three kind::f16 MMAs of
+// N = 256 per 16-wide K step) with FP32 accumulation in tensor memory.  Per CTA:
 //   warp 0      TMA producer: 128x64 BF16 tiles (128-byte swizzle) of the
-//               row block and the column block into a 3-stage ring,
+//               column blocks (and of the row block when it streams) into
+//               a 2-stage ring,
 //   warp 1      allocates TMEM and issues the MMAs (one elected lane),
 //   warps 2..9  epilogue: tcgen05.ld of the FP32 accumulator (warp w reads
-//               TMEM lane quadrant w mod 4 and one 64-column half of the
-//               tile, one row per thread), d2 = n_i + n_j - 2g, same-component
-//               mask, and a running best-8 of half-tiles per row.
-// Four TMEM accumulators (4 x 128 columns) let the MMAs of the next column
-// tiles run ahead of the epilogue of the current one.  Every mbarrier wait is
-// bounded; on timeout the kernel raises an error flag and stops.
+//               TMEM lane quadrant w mod 4 and one 128-column tile of the
+//               pair, one row per thread), d2 = n_i + n_j - 2g, same-component
+//               mask, and a running best-8 of 32-column blocks per row.
+// Two TMEM accumulators (2 x 256 columns) let the MMAs of the next pair of
+// column tiles run ahead of the epilogue of the current one.  Every mbarrier
+// wait is bounded; on timeout the kernel raises an error flag and stops.
 // The candidates are exact-keyed in FP64 by k_recheck_tc inside a rigorous
 // error margin; rows whose margin is not closed by the best 8 are rescanned.
 #include <cuda.h>
@@ -39,8 +40,10 @@ constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 2;         // 16 KB: 128 rows x on
 constexpr int TC_EPI_WARPS = 8;                           // two per TMEM lane quadrant
 constexpr int TC_NACC = 2;                                // TMEM accumulators (2 x 256 columns = all 512)
 constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;
-constexpr int TC_TOPK = 8;                                // best half-tiles kept per (list, row)
-constexpr int TC_CW = TC_BN / 2;                          // columns per candidate (half-tile)
+constexpr int TC_TOPK = 8;                                // best candidate blocks kept per (list, row)
+// Columns per candidate block: 64 (one set, d_pad <= 64: the epilogue is
+// the sweep's limit) or 32 (independent sets or wider rows: the recheck's
+// column reads are the limit).
 constexpr int TC_SURV = 8;                                // FP64-keyed columns per row (more: rescan)
 constexpr long long TC_WAIT_CYCLES = 4000000000LL;
 
@@ -207,7 +210,7 @@ struct ScreenArgs {
     int64_t T64;
 };
 
-template <int AK, bool SCREEN>
+template <int AK, bool SCREEN, int CW>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUtensorMap tml,
            const float *__restrict__ rnorm, const float *__restrict__ cnorm, const float *__restrict__ rsq,
@@ -419,12 +422,16 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
                 const float Ci = SCREEN ? (rvalid ? __fadd_ru(__fadd_ru(dlt, 1e-5f * (nrow + ctmax)), -nrow) : -INFINITY)
                                         : 0.0f;
                 const float Bi = SCREEN ? (rvalid ? __fadd_ru(arow, Ci) : -INFINITY) : 0.0f;
+                // two 64-column halves of the warp's tile; each half is one
+                // TMEM load pair and 64 / CW candidate blocks
+                static_assert(CW == 32 || CW == 64, "candidate block width");
+                constexpr int NB = 64 / CW;
 #pragma unroll 1
-                for (int sub = 0; sub < 2; ++sub) {
-                    float m = INFINITY;        // min over the block of n_j - 2 g (foreign columns)
-                    bool near = false;         // SCREEN: a pair of this block within the cutoff
+                for (int hf = 0; hf < 2; ++hf) {
+                    float m0 = INFINITY, m1 = INFINITY;   // min over each block of n_j - 2 g (foreign columns)
+                    bool near = false;                   // SCREEN: a pair of this half within the cutoff
                     if (ok && mine) {
-                        const int cofs = h * TC_BN + sub * TC_CW;
+                        const int cofs = h * TC_BN + hf * 64;
                         const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + acc * TC_BNP + cofs;
                         uint32_t g0[32], g1[32];
                         tmem_ld32(tbase, g0);
@@ -444,7 +451,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
                                 if constexpr (SCREEN)
                                     near |= v <= fmaxf(Bi, __fadd_ru(__int_as_float(cmv[u]), Ci));
                                 else
-                                    min_foreign(m, v, cmv[u], crow);
+                                    min_foreign(m0, v, cmv[u], crow);
                             }
                         }
 #pragma unroll
@@ -459,24 +466,35 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
                                 if constexpr (SCREEN)
                                     near |= v <= fmaxf(Bi, __fadd_ru(__int_as_float(cmv[u]), Ci));
                                 else
-                                    min_foreign(m, v, cmv[u], crow);
+                                    min_foreign(NB == 2 ? m1 : m0, v, cmv[u], crow);
                             }
                         }
                     }
                     if constexpr (SCREEN) {
                         // rows of this warp are one 64-row half of the row tile
                         if (__ballot_sync(0xffffffffu, near) && lane == 0) {
-                            const int64_t I64 = 2 * (int64_t)rt + (quad >> 1), J64 = 2 * (int64_t)(ct + h) + sub;
+                            const int64_t I64 = 2 * (int64_t)rt + (quad >> 1), J64 = 2 * (int64_t)(ct + h) + hf;
                             if (I64 < scr.T64 && J64 < scr.T64) scr.need[I64 * scr.T64 + J64] = 1;
                         }
                     } else if (mine) {
-                        m = __fadd_rn(m, nrow);
-                        // rigorous bounds of the block's smallest d2 of the represented
-                        // points: accumulation + dropped lo.lo (A s_i s_j) and FP32
-                        // norm/epilogue rounding
-                        const float lb = m - dlt;
-                        ubest = fminf(ubest, m + dlt);
-                        if (lb < bv[TC_TOPK - 1]) top_insert(bv, bj, lb, 2 * (ct + h) + sub);
+                        // rigorous bounds of each block's smallest d2 of the
+                        // represented points: accumulation + dropped lo.lo
+                        // (A s_i s_j) and FP32 norm/epilogue rounding
+                        const int blk = (TC_BN / CW) * (ct + h) + NB * hf;
+                        m0 = __fadd_rn(m0, nrow);
+                        if constexpr (NB == 2) {
+                            m1 = __fadd_rn(m1, nrow);
+                            ubest = fminf(ubest, fminf(m0, m1) + dlt);
+#pragma unroll 1
+                            for (int e = 0; e < NB; ++e) {
+                                const float lb = (e ? m1 : m0) - dlt;
+                                if (lb < bv[TC_TOPK - 1]) top_insert(bv, bj, lb, blk + e);
+                            }
+                        } else {
+                            ubest = fminf(ubest, m0 + dlt);
+                            const float lb = m0 - dlt;
+                            if (lb < bv[TC_TOPK - 1]) top_insert(bv, bj, lb, blk);
+                        }
                     }
                 }
                 tc_fence_before();
@@ -688,15 +706,15 @@ __global__ void k_tc_fill_lists(float *__restrict__ tv, int32_t *__restrict__ tj
 
 // One warp per padded row r, the point i = permp[r] (none at padding).
 // Candidate columns are read from xs (rows in the sweep's order) with their
-// components from compp, so a half-tile is one contiguous block; only the
-// survivors of the FP32 filter are mapped back to point indices.  The lists'
-// (column split x tile half) best-8 half-tile lower bounds and their best
-// upper bound U are merged.
+// components from compp, so a candidate block is 32 contiguous rows of xs;
+// only the survivors of the FP32 filter are mapped back to point indices.
+// The lists' (column split x tile of the pair) best-8 block lower bounds and
+// their best upper bound U are merged.
 // The epilogue's bounds hold for the BF16-represented points; the exact
-// points differ by the representation error rep, so a tile can hold the
+// points differ by the representation error rep, so a block can hold the
 // nearest foreign point only if its lower bound is <= U + 2 rep.  Those
-// tiles' columns are filtered with FP32 direct differences and the
-// survivors keyed in FP64.  If the 8th kept tile still qualifies, the row is
+// blocks' columns are filtered with FP32 direct differences and the
+// survivors keyed in FP64.  If the 8th kept block still qualifies, the row is
 // queued for a rescan.
 __device__ __forceinline__ float approx_d2_f32(const float *__restrict__ a, const float *__restrict__ b, int d) {
     float acc = 0.0f;
@@ -707,6 +725,7 @@ __device__ __forceinline__ float approx_d2_f32(const float *__restrict__ a, cons
     return acc;
 }
 
+template <int EPL, int CW>
 __device__ __forceinline__ void recheck_row(int64_t r, int lane, const float *__restrict__ xs, int64_t n, int32_t d,
                                             int lists, const float *__restrict__ tv, const int32_t *__restrict__ tj,
                                             const float *__restrict__ tu, const float *__restrict__ rsq,
@@ -723,9 +742,8 @@ __device__ __forceinline__ void recheck_row(int64_t r, int lane, const float *__
         if (lane == 0) rowj[i] = -1;
         return;
     }
-    // ---- merge: each lane holds up to 8 of the lists x 8 entries (lists <= 32);
-    //      the best 8 are selected by 8 rounds of a warp arg-min
-    constexpr int EPL = 8;
+    // ---- merge: each lane holds EPL of the lists x 8 entries (lists x 8 <=
+    //      32 EPL); the best 8 are selected by 8 rounds of a warp arg-min
     const int ne = lists * TC_TOPK;
     float ev[EPL];
     int32_t ej[EPL];
@@ -794,31 +812,41 @@ __device__ __forceinline__ void recheck_row(int64_t r, int lane, const float *__
         }
         return;
     }
-    // FP32 direct differences over the candidate half-tiles (two per pass, two
-    // columns of each per lane: four FMA chains).  Pass 1: the row's FP32
+    // FP32 direct differences over the candidate blocks (four per pass, one
+    // column of each per lane: four FMA chains).  Pass 1: the row's FP32
     // minimum m32; the exact best has FP32 value <= m32 * mul32 + add32.
-    // Pass 2 revisits the passes that hold such columns and records them.
+    // Pass 2 filters the first pass's distances and records those columns.
     const int32_t ci = compp[r];
     const float *xi = xs + r * d;
     const bool vec = (d & 3) == 0 && (reinterpret_cast<uintptr_t>(xs) & 15) == 0;
-    auto scan = [&](int k, bool second, int32_t (&jp)[4], bool (&live)[4], float (&acc)[4]) {
+    // a pass covers four columns per lane: SPB of each of BPP blocks
+    constexpr int SPB = CW / 32, BPP = 4 / SPB;
+    // block q of the sorted list qualifies if its lower bound is within the cut
+    auto qual = [&](int q) { return q < TC_TOPK && bj[q] >= 0 && bv[q] <= tile_cut; };
+    auto scan = [&](int k, int32_t (&jp)[4], bool (&live)[4], float (&acc)[4]) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int cand = (u < 2) ? bj[k] : (second ? bj[k + 1] : -1);
-            jp[u] = cand < 0 ? -1 : cand * TC_CW + lane + 32 * (u & 1);   // padded column (< n_pad < 2^31)
+            const int q = k + u / SPB;
+            const int cand = qual(q) ? bj[q] : -1;
+            jp[u] = cand < 0 ? -1 : cand * CW + lane + 32 * (u % SPB);   // padded column (< n_pad <= 2^31)
             int32_t cj = -2;
             if (jp[u] >= 0 && jp[u] < n) cj = compp[jp[u]];
             live[u] = cj >= 0 && cj != ci;                                 // padding: -2
             acc[u] = 0.0f;
         }
         if (vec) {
+            // every slot loads (a dead slot reads the row itself and is
+            // ignored), so the four columns' loads issue together
             const float4 *xi4 = reinterpret_cast<const float4 *>(xi);
+            const float4 *b4[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) b4[u] = reinterpret_cast<const float4 *>(xs + (live[u] ? (int64_t)jp[u] : r) * d);
+#pragma unroll 1
             for (int t = 0; t < d / 4; ++t) {
                 const float4 a = xi4[t];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    if (!live[u]) continue;
-                    const float4 b = reinterpret_cast<const float4 *>(xs + (int64_t)jp[u] * d)[t];
+                    const float4 b = b4[u][t];
                     float df = __fsub_rn(a.x, b.x); acc[u] = __fmaf_rn(df, df, acc[u]);
                     df = __fsub_rn(a.y, b.y); acc[u] = __fmaf_rn(df, df, acc[u]);
                     df = __fsub_rn(a.z, b.z); acc[u] = __fmaf_rn(df, df, acc[u]);
@@ -831,33 +859,34 @@ __device__ __forceinline__ void recheck_row(int64_t r, int lane, const float *__
                 if (live[u]) acc[u] = approx_d2_f32(xi, xs + (int64_t)jp[u] * d, d);
         }
     };
-    // pass 1 keeps its distances in registers; pass 2 filters them against
-    // the threshold without reading the columns again
-    constexpr int NPASS = TC_TOPK / 2;
+    // pass 1 keeps the distances of its first KEEP passes in registers; pass
+    // 2 filters those against the threshold without reading the columns
+    // again (later passes, rare, are scanned again).  Qualifying blocks are
+    // a prefix of the sorted list, so a pass runs only if its first one does.
+    constexpr int NPASS = TC_TOPK / BPP, KEEP = NPASS < 2 ? NPASS : 2;
     float pmin[NPASS];
-    float accs[NPASS][4];
-    int32_t jps[NPASS][4];
-    bool lives[NPASS][4];
-    int npass = 0;
+    float accs[KEEP][4];
+    int32_t jps[KEEP][4];
+    uint32_t livem = 0;                 // bit 4p + u: slot u of kept pass p is a live foreign point
     float m32 = INFINITY;
-    bool more = true;
 #pragma unroll
     for (int p = 0; p < NPASS; ++p) {
         pmin[p] = INFINITY;
+        if (!qual(BPP * p)) continue;
+        int32_t jp[4];
+        bool live[4];
+        float acc[4];
+        scan(BPP * p, jp, live, acc);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) { accs[p][u] = INFINITY; jps[p][u] = -1; lives[p][u] = false; }
-        const int k = 2 * p;
-        if (!more || bj[k] < 0 || bv[k] > tile_cut) { more = false; continue; }
-        const bool second = bj[k + 1] >= 0 && bv[k + 1] <= tile_cut;
-        scan(k, second, jps[p], lives[p], accs[p]);
-        float pm = INFINITY;
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (lives[p][u]) pm = fminf(pm, accs[p][u]);
-        pmin[p] = pm;
-        m32 = fminf(m32, pm);
-        ++npass;
-        if (!second) more = false;
+        for (int u = 0; u < 4; ++u) {
+            if (live[u]) pmin[p] = fminf(pmin[p], acc[u]);
+            if (p < KEEP) {
+                accs[p < KEEP ? p : 0][u] = acc[u];
+                jps[p < KEEP ? p : 0][u] = jp[u];
+                if (live[u]) livem |= 1u << (4 * p + u);
+            }
+        }
+        m32 = fminf(m32, pmin[p]);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m32 = fminf(m32, __shfl_xor_sync(0xffffffffu, m32, o));
@@ -869,13 +898,26 @@ __device__ __forceinline__ void recheck_row(int64_t r, int lane, const float *__
     int cnt = 0;
 #pragma unroll
     for (int p = 0; p < NPASS; ++p) {
-        if (p >= npass || !__any_sync(0xffffffffu, pmin[p] <= thr)) continue;
+        if (!__any_sync(0xffffffffu, pmin[p] <= thr)) continue;
+        int32_t jp[4];
+        bool live[4];
+        float acc[4];
+        if (p < KEEP) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                acc[u] = accs[p < KEEP ? p : 0][u];
+                jp[u] = jps[p < KEEP ? p : 0][u];
+                live[u] = (livem >> (4 * p + u)) & 1u;
+            }
+        } else {
+            scan(BPP * p, jp, live, acc);
+        }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const bool sv = lives[p][u] && accs[p][u] <= thr;
+            const bool sv = live[u] && acc[u] <= thr;
             const unsigned bal = __ballot_sync(0xffffffffu, sv);
             const int slot = cnt + __popc(bal & ((1u << lane) - 1u));
-            if (sv && slot < TC_SURV) surv[r * TC_SURV + slot] = jps[p][u];
+            if (sv && slot < TC_SURV) surv[r * TC_SURV + slot] = jp[u];
             cnt += __popc(bal);
         }
     }
@@ -921,7 +963,8 @@ __global__ void __launch_bounds__(256) k_exact_tc(const float *__restrict__ xs, 
     }
 }
 
-__global__ void __launch_bounds__(256, 3) k_recheck_tc(const float *__restrict__ xs, int64_t n, int32_t d, int lists,
+template <int EPL, int CW>
+__global__ void __launch_bounds__(256, 4) k_recheck_tc(const float *__restrict__ xs, int64_t n, int32_t d, int lists,
                                                        const float *__restrict__ tv, const int32_t *__restrict__ tj,
                                                        const float *__restrict__ tu, const float *__restrict__ rsq,
                                                        const int32_t *__restrict__ perm,
@@ -936,7 +979,7 @@ __global__ void __launch_bounds__(256, 3) k_recheck_tc(const float *__restrict__
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r = w0; r < n; r += nw)
-        recheck_row(r, lane, xs, n, d, lists, tv, tj, tu, rsq, perm, compp, nmax_bits, eps_rep, mul32, add32, nsurv,
+        recheck_row<EPL, CW>(r, lane, xs, n, d, lists, tv, tj, tu, rsq, perm, compp, nmax_bits, eps_rep, mul32, add32, nsurv,
                     surv, rowj, ovf, set_of, setcnt, counters);
 }
 
@@ -1115,7 +1158,7 @@ cudaError_t tc_omega_screen(TcScratch &T, const float *Xp, int64_t n, int32_t d,
     const float bcoef = (float)(1.25 * 8.0 * 5.9604644775390625e-08);
     const ScreenArgs scr{rowA, need, T64};
 #define ISO_SCREEN_LAUNCH(AKV)                                                                                    \
-    k_sweep_tc<AKV, true><<<grid, TC_THREADS, tc_smem(AKV), ISO_S(s)>>>(                                          \
+    k_sweep_tc<AKV, true, 64><<<grid, TC_THREADS, tc_smem(AKV), ISO_S(s)>>>(                                          \
         T.map_h, T.map_l, T.nrm, T.cnrm, T.rsq, T.tmax, T.tsq, acoef, bcoef, nullptr, T.n_pad, ntiles, kchunks, 1,   \
         ditems, nit, nullptr, nullptr, nullptr, nullptr, nullptr, T.err, scr)
     if (kchunks == 1)
@@ -1169,6 +1212,7 @@ cudaError_t tc_prepare(TcScratch &T, const float *X, int64_t n, int32_t d, cudaS
         k_tc_place<<<(unsigned)ceil_div(n, 256), 256, 0, ISO_S(s)>>>(T.perm, n, T.set_of, T.offs, T.rowbase,
                                                                     T.permp);
     }
+    T.cw = (sets || T.d_pad > 64) ? 32 : 64;
     const int64_t tot = T.n_pad * T.d_pad;
     k_tc_split<<<(unsigned)ceil_div(tot, 256), 256, 0, ISO_S(s)>>>(X, T.mean, T.set_of, T.permp, d, T.n_pad, T.d_pad,
                                                                   T.xh, T.xl, T.xs);
@@ -1186,15 +1230,19 @@ cudaError_t tc_prepare(TcScratch &T, const float *X, int64_t n, int32_t d, cudaS
     if ((e = make_map(&T.map_l, T.xl, T.n_pad, T.d_pad))) return e;
     static bool attr = false;
     if (!attr) {
-#define ISO_SMEM_ATTR(AKV, SCR)                                                                                   \
-    if ((e = cudaFuncSetAttribute(k_sweep_tc<AKV, SCR>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(AKV))))  \
+#define ISO_SMEM_ATTR(AKV, SCR, CWV)                                                                              \
+    if ((e = cudaFuncSetAttribute(k_sweep_tc<AKV, SCR, CWV>, cudaFuncAttributeMaxDynamicSharedMemorySize,         \
+                                  tc_smem(AKV))))                                                                 \
         return e;
-        ISO_SMEM_ATTR(0, false)
-        ISO_SMEM_ATTR(1, false)
-        ISO_SMEM_ATTR(2, false)
-        ISO_SMEM_ATTR(0, true)
-        ISO_SMEM_ATTR(1, true)
-        ISO_SMEM_ATTR(2, true)
+        ISO_SMEM_ATTR(0, false, 32)
+        ISO_SMEM_ATTR(1, false, 32)
+        ISO_SMEM_ATTR(2, false, 32)
+        ISO_SMEM_ATTR(0, false, 64)
+        ISO_SMEM_ATTR(1, false, 64)
+        ISO_SMEM_ATTR(2, false, 64)
+        ISO_SMEM_ATTR(0, true, 64)
+        ISO_SMEM_ATTR(1, true, 64)
+        ISO_SMEM_ATTR(2, true, 64)
 #undef ISO_SMEM_ATTR
         attr = true;
     }
@@ -1220,16 +1268,25 @@ cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t 
     const double u = 1.1920928955078125e-07;   // 2^-23
     const float acoef = (float)(1.25 * 2.0 * (3.0 * T.d_pad * u + 3.814697265625e-06));
     const float bcoef = (float)(1.25 * 8.0 * 5.9604644775390625e-08);
-#define ISO_SWEEP_LAUNCH(AKV)                                                                                     \
-    k_sweep_tc<AKV, false><<<grid, TC_THREADS, tc_smem(AKV), ISO_S(s)>>>(                                         \
+#define ISO_SWEEP_LAUNCH(AKV, CWV)                                                                                \
+    k_sweep_tc<AKV, false, CWV><<<grid, TC_THREADS, tc_smem(AKV), ISO_S(s)>>>(                                         \
         T.map_h, T.map_l, T.nrm, T.cnrm, T.rsq, T.tmax, T.tsq, acoef, bcoef, T.compp, T.n_pad, ntiles, kchunks,      \
         T.splits, T.items, T.nitems, T.setcnt, S.counters, T.tv, T.tj, T.tu, T.err, ScreenArgs{})
     if (kchunks == 1)
-        ISO_SWEEP_LAUNCH(1);
+        {
+        if (T.cw == 32) ISO_SWEEP_LAUNCH(1, 32);
+        else ISO_SWEEP_LAUNCH(1, 64);
+    }
     else if (kchunks == 2)
-        ISO_SWEEP_LAUNCH(2);
+        {
+        if (T.cw == 32) ISO_SWEEP_LAUNCH(2, 32);
+        else ISO_SWEEP_LAUNCH(2, 64);
+    }
     else
-        ISO_SWEEP_LAUNCH(0);
+        {
+        if (T.cw == 32) ISO_SWEEP_LAUNCH(0, 32);
+        else ISO_SWEEP_LAUNCH(0, 64);
+    }
 #undef ISO_SWEEP_LAUNCH
     // representation error of a centred point by BF16 hi + lo: 2^-18 relative
     // per element, plus the FP32 rounding of x - c (2^-24); 25 % headroom
@@ -1242,9 +1299,32 @@ cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t 
     const double add = (double)(d + 1) * 1.401298464324817e-45 * 4.0;
     const float mul32 = (float)(mul * (1.0 + 1e-6)), add32 = (float)(2.01 * add) + 1.401298464324817e-45f;
     const int64_t rblocks = ceil_div(T.n_pad * 32, 256), rcap = (int64_t)num_sms() * 16;
-    k_recheck_tc<<<(unsigned)(rblocks < rcap ? rblocks : rcap), 256, 0, ISO_S(s)>>>(
-        T.xs, T.n_pad, d, T.lists, T.tv, T.tj, T.tu, T.rsq, T.permp, T.compp, T.nmax_bits, (float)(eps_rep * 1.0001),
-        mul32, add32, T.nsurv, T.surv, S.rowj, S.ovf_rows, T.set_of, T.setcnt, S.counters);
+    // entries per lane of the list merge: lists x 8 <= 32 EPL (lists <= 32)
+#define ISO_RECHECK_LAUNCH(EPLV, CWV)                                                                                \
+    k_recheck_tc<EPLV, CWV><<<(unsigned)(rblocks < rcap ? rblocks : rcap), 256, 0, ISO_S(s)>>>(                        \
+        T.xs, T.n_pad, d, T.lists, T.tv, T.tj, T.tu, T.rsq, T.permp, T.compp, T.nmax_bits, (float)(eps_rep * 1.0001),  \
+        mul32, add32, T.nsurv, T.surv, S.rowj, S.ovf_rows, T.set_of, T.setcnt, S.counters)
+    if (T.lists <= 4)
+        {
+        if (T.cw == 32) ISO_RECHECK_LAUNCH(1, 32);
+        else ISO_RECHECK_LAUNCH(1, 64);
+    }
+    else if (T.lists <= 8)
+        {
+        if (T.cw == 32) ISO_RECHECK_LAUNCH(2, 32);
+        else ISO_RECHECK_LAUNCH(2, 64);
+    }
+    else if (T.lists <= 16)
+        {
+        if (T.cw == 32) ISO_RECHECK_LAUNCH(4, 32);
+        else ISO_RECHECK_LAUNCH(4, 64);
+    }
+    else
+        {
+        if (T.cw == 32) ISO_RECHECK_LAUNCH(8, 32);
+        else ISO_RECHECK_LAUNCH(8, 64);
+    }
+#undef ISO_RECHECK_LAUNCH
     const int64_t xblocks = ceil_div(T.n_pad, 256), xcap = (int64_t)num_sms() * 8;
     k_exact_tc<<<(unsigned)(xblocks < xcap ? xblocks : xcap), 256, 0, ISO_S(s)>>>(T.xs, T.n_pad, d, T.permp, T.nsurv,
                                                                                   T.surv, S.rowd2, S.rowj,
