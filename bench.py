@@ -8,7 +8,11 @@ labels.  Inputs are resident in HBM; L2 is flushed (a 256 MiB write) before
 every step inside the timed region.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                  [--workload blobs_n100k_d64|batched_4096_d32|moons_n20k_d128]
+                  [--workload blobs_n100k_d64|sparse_n50k_d4096|batched_4096_d32|moons_n20k_d128]
+
+--workload sparse_n50k_d4096 times the same call on 50,000 sparse-like rows
+of 4,096 features (L2-normalised log-normal values at 1 % density, 10
+groups, k = 10), where the sweep's Gram tiles dominate the MST stage.
 
 --workload batched_4096_d32 times isoclust_cluster_batched on 4,096
 independent sets (sizes log-uniform in [64, 8192], d = 32, 2-8 blobs each,
@@ -41,6 +45,7 @@ import numpy as np  # noqa: E402
 METRIC = "points/s end-to-end"
 UNIT = "points/s"
 WORKLOAD = "blobs_n100k_d64"
+SPARSE = "sparse_n50k_d4096"
 BATCHED = "batched_4096_d32"
 MOONS = "moons_n20k_d128"
 FP64_PER_SM_CLK = 2          # DFMA per clock per SM (ncu peak of sm__sass_thread_inst_executed_op_dfma)
@@ -131,10 +136,18 @@ def _cpu_cores():
         return os.cpu_count() or 1
 
 
-def cpu_baseline(X, k, sigma, n_sample=30000):
+def _sample_rows(d, base=30000):
+    """Oracle sample size: about the cost of 30,000 points at d = 64 (the
+    path costs n^2 d)."""
+    return int(max(2000, min(base, base * (64.0 / max(d, 1)) ** 0.5)))
+
+
+def cpu_baseline(X, k, sigma, n_sample=None):
     """The oracle as it stands, on a bounded sample, scaled to full n by the
     O(n^2) cost of the path (all pairs for omega, Prim's n min-reductions)."""
     n = X.shape[0]
+    if n_sample is None:
+        n_sample = _sample_rows(X.shape[1])
     cores = _cpu_cores()
     t = _oracle_time(X, k, sigma, n_sample, cores)
     t_full = t * (n / n_sample) ** 2
@@ -149,7 +162,7 @@ def run_reference(args, X, k, sigma):
         return 0
     steps_total = args.steps + args.warmup
     n = X.shape[0]
-    n_sample = int(min(30000, max(5000, 30000 * (8.0 / max(steps_total, 1)) ** 0.5)))
+    n_sample = int(max(2000, _sample_rows(X.shape[1]) * min(1.0, (8.0 / max(steps_total, 1)) ** 0.5)))
     cores = _cpu_cores()
     for _ in range(args.warmup):
         _oracle_time(X, k, sigma, n_sample, cores)
@@ -160,7 +173,7 @@ def run_reference(args, X, k, sigma):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1000.0 * (n / n_sample) ** 2,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "d": X.shape[1], "k": k, "sigma": sigma},
+        "config": {"workload": args.workload, "n": n, "d": X.shape[1], "k": k, "sigma": sigma},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"each step: oracle on the first {n_sample} points, {t:.2f} s mean; "
                                    f"scaled to n={n} by the O(n^2) cost law"},
@@ -182,7 +195,7 @@ def main():
     ap.add_argument("--no-mst-compare", action="store_true")
     ap.add_argument("--n", type=int, default=0,
                     help="points of the same generator (profiling of a smaller case); default: the full 100,000")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, BATCHED, MOONS])
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, SPARSE, BATCHED, MOONS])
     ap.add_argument("--nsets", type=int, default=0, help="batched: fewer sets of the same recipe (profiling)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
@@ -196,9 +209,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    X, k, sigma = workloads.make(WORKLOAD, seed=rank)
+    X, k, sigma = workloads.make(args.workload, seed=rank)
     if args.n:
-        X = workloads.blobs_anisotropic(seed=rank, n=args.n)[0]
+        X = workloads.blobs_anisotropic(seed=rank, n=args.n)[0] if args.workload == WORKLOAD else X[:args.n]
     if args.impl == "reference":
         return run_reference(args, X, k, sigma)
 
@@ -336,7 +349,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "d": d, "k": k, "sigma": sigma, "storage": "f32",
+        "config": {"workload": args.workload, "n": n, "d": d, "k": k, "sigma": sigma, "storage": "f32",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "flushed by a 256 MiB write before every step (inside the timed region)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
