@@ -261,6 +261,7 @@ def main():
     barrier()
     launches = isoclust.kernel_launches() - l0
     clk = clocks.stop()
+    sweep_variant = isoclust.last_sweep_variant()
     t_ms = ev0.elapsed_time(ev1)
     if pg is not None:
         tt = torch.tensor([t_ms], device=dev)
@@ -334,7 +335,7 @@ def main():
         same = all(torch.equal(a, b) for a, b in zip(ref_edges, fp_edges))
         mst_cmp = {"bf16_tc_fp64_recheck_ms": t_tc, "fp32_simt_fp64_recheck_ms": t_fp,
                    "speedup_vs_fp32": t_fp / t_tc if t_tc > 0 else None, "identical_edges": bool(same)}
-    mst = {"stage_ms": mst_ms, "rounds": rounds,
+    mst = {"stage_ms": mst_ms, "rounds": rounds, "sweep_variant": sweep_variant,
            "algorithmic_tflops": alg_flop / (mst_ms / 1000.0) / 1e12,
            "executed_tensor_tflops": exe_flop / (mst_ms / 1000.0) / 1e12,
            "peak_bf16_tflops": peaks.get("bf16_tflops"), "peak_source": src,
@@ -478,6 +479,7 @@ def main_batched(args):
         pg.barrier()
     launches = isoclust.kernel_launches() - l0
     clk = clocks.stop()
+    sweep_variant = isoclust.last_sweep_variant()
     t_ms = ev0.elapsed_time(ev1)
     if pg is not None:
         tt = torch.tensor([t_ms], device=dev)
@@ -545,7 +547,7 @@ def main_batched(args):
                              f"over the kernel's CUDA-event time ({w_ms:.2f} ms); peak = {sms} SMs x {FP32_LANES_PER_SM} lanes x "
                              f"max SM clock ({src})"},
         "stages_ms": stages,
-        "mst": {"stage_ms": mst_ms, "rounds": rounds,
+        "mst": {"stage_ms": mst_ms, "rounds": rounds, "sweep_variant": sweep_variant,
                 "executed_tensor_tflops": exe_flop / (mst_ms / 1000.0) / 1e12,
                 "peak_bf16_tflops": peaks.get("bf16_tflops"), "peak_source": src},
         "omega_tiles": {"screened": tiles, "double_word": tiles_dw},

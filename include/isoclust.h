@@ -341,6 +341,24 @@ void isoclust_last_omega_tiles(int64_t *tiles3);
  * isoclust_ik_backward. */
 double isoclust_last_omega_kernel_ms(void);
 
+/* Tile variant of the tensor-core Boruvka sweep (Section 3.5's MST step
+ * with the tiled Gram sweep): bit 0 set = 32-column candidate blocks (else
+ * 64), bit 1 set = the row block streams with the column blocks (else it
+ * stays resident in shared memory when the padded row length is <= 128).
+ * variant -1 (the default) lets the library pick: on the first call of a
+ * shape class (device, one set or independent sets, padded row length, and
+ * the powers of two of the padded rows and work items) it times one trial
+ * round of each variant on the round-1 state and caches the fastest; small
+ * problems take a fixed rule.  0..3 force a variant for every later call of
+ * the process.  Results do not depend on the variant (the minimum spanning
+ * tree under the edge key is unique); only the speed does.  Other values ->
+ * ISOCLUST_ERR_INVALID_ARG.  Process-wide setting; no device work. */
+isoclust_status isoclust_set_sweep_variant(int32_t variant);
+
+/* The sweep variant of the last minimum-spanning-tree build on this host
+ * thread (0..3), or -1 when none ran (FP32/FP64 sweep, F64 input). */
+int32_t isoclust_last_sweep_variant(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -831,6 +831,14 @@ void isoclust_last_profile(double *t_ms6, int64_t *counts4) {
 
 double isoclust_last_omega_kernel_ms(void) { return g_prof_omega_kernel_ms; }
 
+isoclust_status isoclust_set_sweep_variant(int32_t variant) {
+    if (variant < -1 || variant > 3) return fail(ISOCLUST_ERR_INVALID_ARG, "sweep variant %d is not in -1..3", variant);
+    tc_force_variant(variant);
+    return ISOCLUST_OK;
+}
+
+int32_t isoclust_last_sweep_variant(void) { return tc_last_variant(); }
+
 void isoclust_last_omega_tiles(int64_t *tiles3) {
     if (tiles3) {
         tiles3[0] = (int64_t)g_prof_tiles[0];

@@ -514,6 +514,8 @@ cudaError_t mst_build(MstScratch &S, const void *X, int64_t n, int32_t d, int dt
     cudaError_t e;
     if (tc && (e = tc_prepare(*tc, (const float *)X, n, d, s))) return e;
     if (tc && (e = tc_count_sets(*tc, S.comp, n, S.counters, s))) return e;
+    if (tc && (e = tc_autotune(*tc, S, (const float *)X, n, d, status, s))) return e;
+    if (!tc) tc_clear_last_variant();
     for (int r = 0; r < R; ++r) {
         k_round_begin<<<rg, TPB, 0, ISO_S(s)>>>(S.counters, S.cd2, S.cpair, n);
         if (tc) {

@@ -46,7 +46,8 @@ struct TcScratch {
     int32_t d_pad = 0;
     int splits = 1;                                // column splits per row tile (one set)
     int lists = 2;                                 // candidate lists per row (2 per split: tiles of a pair)
-    int cw = 64;                                   // columns per candidate block (64 or 32; set by tc_prepare)
+    int cw = 64;                                   // columns per candidate block (64 or 32)
+    bool resident = true;                          // row block resident in shared memory when d_pad <= 128
     __nv_bfloat16 *xh = nullptr, *xl = nullptr;   // row r is point permp[r] (zero rows at padding)
     float *xs = nullptr;                           // [n_pad][d] the points themselves in the same order
     float *nrm = nullptr, *rsq = nullptr;          // |y|^2 and |y| of the represented rows (0 at padding)
@@ -87,6 +88,15 @@ cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t 
 cudaError_t tc_omega_screen(TcScratch &T, const float *Xp, int64_t n, int32_t d,
                             const unsigned long long *nnbits, double sigma, double zskip, uint8_t *need, int64_t T64,
                             cudaStream_t s);
+// Sweep variant (bit 0: 32-column candidate blocks, bit 1: streamed row
+// block): forced by tc_force_variant, else the fastest of one timed trial
+// round per variant, cached per device and shape class.  Runs on the
+// round-1 state before the first round and restores the round counters.
+cudaError_t tc_autotune(TcScratch &T, MstScratch &S, const float *X, int64_t n, int32_t d, uint32_t *status,
+                        cudaStream_t s);
+void tc_force_variant(int variant);     // -1: tune
+int tc_last_variant();                  // this thread's last variant (-1: none)
+void tc_clear_last_variant();           // a build without the tensor-core sweep
 // independent sets: recount the components of every set from comp
 cudaError_t tc_count_sets(TcScratch &T, const int32_t *comp, int64_t n, const int32_t *counters, cudaStream_t s);
 

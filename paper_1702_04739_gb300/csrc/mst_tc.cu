@@ -24,6 +24,10 @@
 #include <cuda.h>
 #include <stddef.h>
 
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "mst.cuh"
@@ -1118,6 +1122,110 @@ void TcScratch::carve(Arena &A, int64_t n, int32_t d, int splits_, int64_t n_pad
     setcnt = nmeans > 1 || n_pad_rows > 0 ? A.take<int32_t>((size_t)(nmeans > 0 ? nmeans : 1)) : nullptr;
 }
 
+namespace {
+struct TuneKey {
+    int dev, sets, d_pad, lg_rows, lg_items;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(dev, sets, d_pad, lg_rows, lg_items) < std::tie(o.dev, o.sets, o.d_pad, o.lg_rows, o.lg_items);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune;           // shape class -> fastest variant
+std::atomic<int> g_force{-1};
+thread_local int g_last_variant = -1;
+int ilog2(int64_t x) {
+    int l = 0;
+    while (x > 1) { x >>= 1; ++l; }
+    return l;
+}
+void apply_variant(TcScratch &T, int v) {
+    T.cw = (v & 1) ? 32 : 64;
+    T.resident = (v & 2) == 0;
+}
+}  // namespace
+
+void tc_force_variant(int variant) { g_force.store(variant); }
+int tc_last_variant() { return g_last_variant; }
+void tc_clear_last_variant() { g_last_variant = -1; }
+
+cudaError_t tc_autotune(TcScratch &T, MstScratch &S, const float *X, int64_t n, int32_t d, uint32_t *status,
+                        cudaStream_t s) {
+    const int heuristic = (T.cw == 32 ? 1 : 0) | (T.resident ? 0 : 2);
+    const int forced = g_force.load();
+    if (forced >= 0) {
+        apply_variant(T, forced);
+        g_last_variant = forced;
+        return cudaSuccess;
+    }
+    const int kchunks = T.d_pad / TC_BK;
+    const int64_t items = T.items ? T.nitems : (T.n_pad / TC_BM) * T.splits;
+    int dev = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev))) return e;
+    const TuneKey key{dev, T.set_of != nullptr, T.d_pad, ilog2(T.n_pad), ilog2(items > 0 ? items : 1)};
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            apply_variant(T, it->second);
+            g_last_variant = it->second;
+            return cudaSuccess;
+        }
+    }
+    // small problems: a trial round costs more than any difference
+    if (T.n_pad < 8192) {
+        g_last_variant = heuristic;
+        return cudaSuccess;
+    }
+    int cand[4], nc = 0;
+    cand[nc++] = 0;
+    cand[nc++] = 1;
+    if (kchunks <= 2) {
+        cand[nc++] = 2;
+        cand[nc++] = 3;
+    }
+    int32_t saved[8];
+    if ((e = cudaMemcpyAsync(saved, S.counters, sizeof(saved), cudaMemcpyDeviceToHost, s))) return e;
+    if ((e = cudaStreamSynchronize(s))) return e;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if ((e = cudaEventCreate(&e0)) || (e = cudaEventCreate(&e1))) {
+        if (e0) cudaEventDestroy(e0);
+        return e;
+    }
+    int best = heuristic;
+    float best_ms = INFINITY;
+    for (int c = 0; c < nc && e == cudaSuccess; ++c) {
+        apply_variant(T, cand[c]);
+        // two trial rounds on the round-1 state, the second timed; the
+        // rescan queue is emptied before each (it indexes by its count)
+        float ms = 0.f;
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+            if ((e = cudaMemsetAsync(S.counters + MC_OVERFLOW, 0, sizeof(int32_t), s))) break;
+            if ((e = cudaEventRecord(e0, s))) break;
+            if ((e = tc_sweep_round(T, S, X, n, d, status, s))) break;
+            if ((e = cudaEventRecord(e1, s))) break;
+            if ((e = cudaEventSynchronize(e1))) break;
+            if ((e = cudaEventElapsedTime(&ms, e0, e1))) break;
+        }
+        if (e == cudaSuccess && ms < best_ms) {
+            best_ms = ms;
+            best = cand[c];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e) return e;
+    // restore the round counters (the trials only touched the rescan queue)
+    if ((e = cudaMemcpy(S.counters, saved, sizeof(saved), cudaMemcpyHostToDevice))) return e;
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        g_tune[key] = best;
+    }
+    apply_variant(T, best);
+    g_last_variant = best;
+    return cudaSuccess;
+}
+
 cudaError_t tc_count_sets(TcScratch &T, const int32_t *comp, int64_t n, const int32_t *counters, cudaStream_t s) {
     if (!T.set_of || !T.setcnt) return cudaSuccess;
     cudaError_t e;
@@ -1212,7 +1320,8 @@ cudaError_t tc_prepare(TcScratch &T, const float *X, int64_t n, int32_t d, cudaS
         k_tc_place<<<(unsigned)ceil_div(n, 256), 256, 0, ISO_S(s)>>>(T.perm, n, T.set_of, T.offs, T.rowbase,
                                                                     T.permp);
     }
-    T.cw = (sets || T.d_pad > 64) ? 32 : 64;
+    T.cw = (sets || T.d_pad > 64) ? 32 : 64;      // heuristic variant (see tc_autotune)
+    T.resident = true;
     const int64_t tot = T.n_pad * T.d_pad;
     k_tc_split<<<(unsigned)ceil_div(tot, 256), 256, 0, ISO_S(s)>>>(X, T.mean, T.set_of, T.permp, d, T.n_pad, T.d_pad,
                                                                   T.xh, T.xl, T.xs);
@@ -1272,12 +1381,12 @@ cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t 
     k_sweep_tc<AKV, false, CWV><<<grid, TC_THREADS, tc_smem(AKV), ISO_S(s)>>>(                                         \
         T.map_h, T.map_l, T.nrm, T.cnrm, T.rsq, T.tmax, T.tsq, acoef, bcoef, T.compp, T.n_pad, ntiles, kchunks,      \
         T.splits, T.items, T.nitems, T.setcnt, S.counters, T.tv, T.tj, T.tu, T.err, ScreenArgs{})
-    if (kchunks == 1)
+    if (kchunks == 1 && T.resident)
         {
         if (T.cw == 32) ISO_SWEEP_LAUNCH(1, 32);
         else ISO_SWEEP_LAUNCH(1, 64);
     }
-    else if (kchunks == 2)
+    else if (kchunks == 2 && T.resident)
         {
         if (T.cw == 32) ISO_SWEEP_LAUNCH(2, 32);
         else ISO_SWEEP_LAUNCH(2, 64);

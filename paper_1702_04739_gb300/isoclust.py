@@ -94,6 +94,10 @@ def load(build_if_missing: bool = True):
         lib.isoclust_last_profile.argtypes = [_P, _P]
         lib.isoclust_last_omega_kernel_ms.restype = _D
         lib.isoclust_last_omega_kernel_ms.argtypes = []
+        lib.isoclust_set_sweep_variant.restype = ctypes.c_int
+        lib.isoclust_set_sweep_variant.argtypes = [ctypes.c_int32]
+        lib.isoclust_last_sweep_variant.restype = ctypes.c_int32
+        lib.isoclust_last_sweep_variant.argtypes = []
         lib.isoclust_last_omega_tiles.restype = None
         lib.isoclust_last_omega_tiles.argtypes = [_P]
         _lib = lib
@@ -348,6 +352,18 @@ class IsoperimetricNumber(torch.autograd.Function):
         g = ik_backward(X.contiguous(), s64, ctx.sigma, parent, labels, ctx.k, phi, omega, float(g_ik))
         dsig = g["dsigma"].reshape(()) if ctx.sigma_is_tensor else None
         return g["dX"], g["dscale"], dsig, None
+
+
+def set_sweep_variant(variant: int) -> None:
+    """Force the tensor-core sweep's tile variant (0..3: bit 0 = 32-column
+    candidate blocks, bit 1 = streamed row block) or let the library time and
+    cache the fastest per shape class (-1, the default) -- isoclust_set_sweep_variant."""
+    _check(load().isoclust_set_sweep_variant(int(variant)))
+
+
+def last_sweep_variant() -> int:
+    """Sweep variant of the last MST build on this thread (-1: none)."""
+    return int(load().isoclust_last_sweep_variant())
 
 
 def kernel_launches() -> int:

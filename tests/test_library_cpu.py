@@ -76,6 +76,9 @@ def test_host_side_validation_without_device_work():
     assert L.isoclust_tree_isoperimetric(5, fake, fake, fake, None, 6, None, fake, fake, fake, None) == 2
     assert L.isoclust_tree_isoperimetric(5, None, fake, fake, None, 2, None, fake, fake, fake, None) == 1
     assert b"exceeds" in L.isoclust_last_error() or b"NULL" in L.isoclust_last_error()
+    # the sweep-variant setting is host state only
+    assert L.isoclust_set_sweep_variant(4) == 1 and L.isoclust_set_sweep_variant(-2) == 1
+    assert L.isoclust_set_sweep_variant(2) == 0 and L.isoclust_set_sweep_variant(-1) == 0
 
 
 def test_binding_requires_cuda_tensors():
