@@ -359,6 +359,16 @@ isoclust_status isoclust_set_sweep_variant(int32_t variant);
  * thread (0..3), or -1 when none ran (FP32/FP64 sweep, F64 input). */
 int32_t isoclust_last_sweep_variant(void);
 
+/* How the last isoclust_cluster_batched / _batched_detail call on this
+ * process ran its device work: 0 launched kernel by kernel, 1 captured into
+ * CUDA graphs and launched them, 2 replayed the graphs of the previous call.
+ * A call replays when its arguments (pointers, sizes, offsets and ks
+ * contents, sigma, options) match the previous batched call on the device
+ * (the first call of a signature runs kernel by kernel, the second is
+ * captured); the environment variable ISOCLUST_GRAPHS=0 keeps every call
+ * kernel by kernel.  Results are identical in every mode. */
+int32_t isoclust_last_batched_graph_mode(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -558,11 +558,11 @@ cudaError_t adjoint_launch(const void *X, int32_t dtype, int64_t n, int32_t d, c
         const double *Xd = (const double *)X;
         k_phi_grad<double><<<1, TPB, 0, ISO_S(s)>>>(Xd, scale, d, parent, elist, cnt + 3, sigma, gphi, sums);
         k_row_norms<<<g, TPB, 0, ISO_S(s)>>>(nullptr, Xd, scale, n, d, N2);
-        if (kev) cudaEventRecord(kev[0], s);
+        if (kev) record_event(kev[0], s);
         if (nit > 0)
             k_pair_grad<double><<<gp, TPB, gsm, ISO_S(s)>>>(Xd, scale, n, d, N2, fa, alist, blist, cnt, pitems, nit,
                                                              sigma, Vp, Cp, Op, Sp);
-        if (kev) cudaEventRecord(kev[1], s);
+        if (kev) record_event(kev[1], s);
         k_pair_reduce<double><<<gr, TPB, 0, ISO_S(s)>>>(Xd, scale, n, d, alist, blist, cnt, tilesA * chunksA, chunksA,
                                                          chunksB, Vp, Cp, Op, Sp, gom, rowom, rowsig);
         k_omega_total<<<1, TPB, 0, ISO_S(s)>>>(alist, cnt + 1, rowom, rowsig, sums + 2);
@@ -573,11 +573,11 @@ cudaError_t adjoint_launch(const void *X, int32_t dtype, int64_t n, int32_t d, c
         const float *Xf = (const float *)X;
         k_phi_grad<float><<<1, TPB, 0, ISO_S(s)>>>(Xf, scale, d, parent, elist, cnt + 3, sigma, gphi, sums);
         k_row_norms<<<g, TPB, 0, ISO_S(s)>>>(Xf, nullptr, scale, n, d, N2);
-        if (kev) cudaEventRecord(kev[0], s);
+        if (kev) record_event(kev[0], s);
         if (nit > 0)
             k_pair_grad<float><<<gp, TPB, gsm, ISO_S(s)>>>(Xf, scale, n, d, N2, fa, alist, blist, cnt, pitems, nit,
                                                             sigma, Vp, Cp, Op, Sp);
-        if (kev) cudaEventRecord(kev[1], s);
+        if (kev) record_event(kev[1], s);
         k_pair_reduce<float><<<gr, TPB, 0, ISO_S(s)>>>(Xf, scale, n, d, alist, blist, cnt, tilesA * chunksA, chunksA,
                                                         chunksB, Vp, Cp, Op, Sp, gom, rowom, rowsig);
         k_omega_total<<<1, TPB, 0, ISO_S(s)>>>(alist, cnt + 1, rowom, rowsig, sums + 2);

@@ -40,6 +40,7 @@ cudaError_t scale_rows_launch(const void *X, int32_t dtype, int64_t n, int32_t d
 
 static std::atomic<long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static void note_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------- errors
 static thread_local char g_err[512] = "";
@@ -252,23 +253,76 @@ static isoclust_status check_points(const void *X, int64_t n, int32_t d, int32_t
 }
 
 struct Events {
-    cudaEvent_t e[10];
+    cudaEvent_t e[10] = {};
     bool ok = false;
     Events() {
         ok = true;
         for (auto &x : e) ok = ok && cudaEventCreate(&x) == cudaSuccess;
     }
     ~Events() {
-        for (auto &x : e) cudaEventDestroy(x);
+        for (auto &x : e)
+            if (x) cudaEventDestroy(x);
     }
     void rec(int i, cudaStream_t s) {
-        if (ok) cudaEventRecord(e[i], s);
+        if (ok) record_event(e[i], s);
     }
     double ms(int a, int b) {
         float t = 0.f;
-        if (!ok || cudaEventElapsedTime(&t, e[a], e[b]) != cudaSuccess) return 0.0;
+        if (!ok) return 0.0;
+        if (cudaEventElapsedTime(&t, e[a], e[b]) != cudaSuccess) {
+            cudaGetLastError();              // a pair never recorded: no time, no pending error
+            return 0.0;
+        }
         return (double)t;
     }
+};
+
+// ---- CUDA graphs of repeated batched calls.  A batched call whose
+// arguments (pointers, sizes, the plan's offsets and ks, sigma, options),
+// scratch base and sweep-variant setting all match the previous batched call
+// on this device replays the two graphs captured from that call's device
+// work (before and after the host check of the trees) instead of launching
+// every kernel again.  The first call of a signature runs eagerly (the sweep
+// variant is tuned there), the second is captured, later ones replay.  The
+// graphs run on a library-owned stream; the call stays synchronous.
+// ISOCLUST_GRAPHS=0 in the environment keeps every call eager.
+struct SetsGraph {
+    uint64_t key = 0;
+    int seen = 0;                                  // consecutive calls with this key
+    bool broken = false;                           // capture failed for this key: eager
+    cudaGraphExec_t g[2] = {nullptr, nullptr};
+    long long nk[2] = {0, 0};                      // kernels in each graph
+    Events *ev = nullptr;                          // the events the graphs record
+    void reset(uint64_t k) {
+        for (auto &x : g)
+            if (x) { cudaGraphExecDestroy(x); x = nullptr; }
+        delete ev;
+        ev = nullptr;
+        key = k;
+        seen = 0;
+        broken = false;
+        nk[0] = nk[1] = 0;
+    }
+};
+static SetsGraph g_sets_graph[MAX_DEV];
+static cudaStream_t g_graph_stream[MAX_DEV] = {nullptr};
+static int g_last_graph_mode = 0;                  // 0 eager, 1 captured, 2 replayed (last batched call)
+
+static bool graphs_enabled() {
+    static const bool on = [] {
+        const char *v = getenv("ISOCLUST_GRAPHS");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
+struct Fnv {
+    uint64_t h = 1469598103934665603ull;
+    void add(const void *p, size_t n) {
+        const unsigned char *c = (const unsigned char *)p;
+        for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
+    }
+    template <class T> void val(const T &v) { add(&v, sizeof(v)); }
 };
 
 static bool use_fp64_sweep(const isoclust_opts &o, int dtype) {
@@ -713,57 +767,129 @@ static isoclust_status cluster_sets_impl(const void *X, const int64_t *offsets, 
     if (hst) return map_status(hst, false);
     ev.rec(1, s);
 
-    // Section 2.2 steps 1-2 for every set: one Boruvka forest
-    TC.items = B.titems;
-    TC.nitems = ntc;
-    TC.nsets = nsets;
-    TC.set_of = B.set_of;
-    TC.offs = d_offs;
-    TC.rowbase = d_rowbase;
-    ISO_CUDA(mst_build(M, X, N, d, dtype, false, B.status, s, &TC, nsets, max_n));
-    k_check_edges_sets<<<1, 1, 0, ISO_S(s)>>>(M.counters, N, nsets, B.status);
-    ev.rec(2, s);
+    // Section 2.2 steps 1-3 up to the host check of the trees (phase 0),
+    // then steps 3-4 and Algorithms 1, 2 and 4 (phase 1)
+    auto phase0 = [&](cudaStream_t q, Events &E) -> cudaError_t {
+        cudaError_t e;
+        E.rec(1, q);
+        // one Boruvka forest for every set
+        TC.items = B.titems;
+        TC.nitems = ntc;
+        TC.nsets = nsets;
+        TC.set_of = B.set_of;
+        TC.offs = d_offs;
+        TC.rowbase = d_rowbase;
+        if ((e = mst_build(M, X, N, d, dtype, false, B.status, q, &TC, nsets, max_n))) return e;
+        k_check_edges_sets<<<1, 1, 0, ISO_S(q)>>>(M.counters, N, nsets, B.status);
+        E.rec(2, q);
+        // the sets' trees under a virtual root (vertex N)
+        const int64_t m_mst = N - nsets;
+        if ((e = cudaMemcpyAsync(B.eu, M.eu, sizeof(int32_t) * m_mst, cudaMemcpyDeviceToDevice, q))) return e;
+        if ((e = cudaMemcpyAsync(B.ev, M.ev, sizeof(int32_t) * m_mst, cudaMemcpyDeviceToDevice, q))) return e;
+        if ((e = cudaMemcpyAsync(B.ed2, M.ed2, sizeof(double) * m_mst, cudaMemcpyDeviceToDevice, q))) return e;
+        k_virtual_edges<<<(unsigned)ceil_div(P, TPB), TPB, 0, ISO_S(q)>>>(d_offs, nsets, m_mst, N, B.eu, B.ev, B.ed2);
+        return orient_tree(TS, B.eu, B.ev, N + 1, (int32_t)N, nullptr, q, B.set_of, 1);
+    };
+    auto phase1 = [&](cudaStream_t q, Events &E) -> cudaError_t {
+        cudaError_t e;
+        const int64_t m_mst = N - nsets;
+        if ((e = orient_tree(TS, B.eu, B.ev, N + 1, (int32_t)N, nullptr, q, B.set_of, 2))) return e;
+        if ((e = fix_set_roots(TS, nsets, d_offs, q))) return e;
+        E.rec(3, q);
+        // eq. omega per set, symmetric tile pairs in each set's MST preorder
+        if ((e = nn_from_edges(M, M.eu, M.ev, M.ed2, q, m_mst))) return e;
+        k_pos64<<<(unsigned)ceil_div(N, TPB), TPB, 0, ISO_S(q)>>>(TS.T.pre, B.set_of, d_offs, d_tile0, N, B.pos);
+        if ((e = cudaMemsetAsync(B.nnp, 0xff, sizeof(unsigned long long) * n_pad64, q))) return e;
+        k_gather_pad<<<(unsigned)ceil_div(N * (int64_t)d, TPB), TPB, 0, ISO_S(q)>>>((const float *)X, B.pos, M.nnbits, N,
+                                                                                    d, B.Xp, B.nnp);
+        if ((e = cudaMemsetAsync(B.tiles, 0, 2 * sizeof(unsigned long long), q))) return e;
+        if ((e = weights_launch_sym_sets(B.Xp, n_pad64, d, sigma, o.include_self, B.nnp, B.omp, B.sym, B.witems,
+                                         nitems, B.tile_valid, B.tile_set, d_tile0, d_ntl, d_item0, max_n, B.tiles,
+                                         E.ok ? E.e + 8 : nullptr, q)))
+            return e;
+        k_scatter_pad<<<(unsigned)ceil_div(N + 1, TPB), TPB, 0, ISO_S(q)>>>(B.omp, B.pos, N, B.om);
+        E.rec(4, q);
+        if ((e = phi_from_edges(TS, B.ed2, sigma, B.phi, q))) return e;
+        // Algorithm 2 + Algorithm 1 per set, then Algorithm 4's labels
+        if ((e = tree_search_and_label_sets(TS, nsets, d_offs, B.set_of, B.ks, B.SS, B.phi, B.om, nullptr, labels,
+                                            residual, i_k, beta, q)))
+            return e;
+        E.rec(5, q);
+        if (out_parent &&
+            (e = cudaMemcpyAsync(out_parent, TS.T.parent, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, q)))
+            return e;
+        if (out_phi && (e = cudaMemcpyAsync(out_phi, B.phi, sizeof(double) * N, cudaMemcpyDeviceToDevice, q)))
+            return e;
+        if (out_omega && (e = cudaMemcpyAsync(out_omega, B.om, sizeof(double) * N, cudaMemcpyDeviceToDevice, q)))
+            return e;
+        E.rec(6, q);
+        return cudaGetLastError();
+    };
 
-    // Section 2.2 step 3: the sets' trees under a virtual root (vertex N)
-    const int64_t m_mst = N - nsets;
-    ISO_CUDA(cudaMemcpyAsync(B.eu, M.eu, sizeof(int32_t) * m_mst, cudaMemcpyDeviceToDevice, s));
-    ISO_CUDA(cudaMemcpyAsync(B.ev, M.ev, sizeof(int32_t) * m_mst, cudaMemcpyDeviceToDevice, s));
-    ISO_CUDA(cudaMemcpyAsync(B.ed2, M.ed2, sizeof(double) * m_mst, cudaMemcpyDeviceToDevice, s));
-    k_virtual_edges<<<(unsigned)ceil_div(P, TPB), TPB, 0, ISO_S(s)>>>(d_offs, nsets, m_mst, N, B.eu, B.ev, B.ed2);
-    ISO_CUDA(orient_tree(TS, B.eu, B.ev, N + 1, (int32_t)N, nullptr, s, B.set_of));
-    {
-        uint32_t h2 = 0, h3 = 0;
-        ISO_CUDA(cudaMemcpyAsync(&h2, B.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-        ISO_CUDA(cudaMemcpyAsync(&h3, TS.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-        ISO_CUDA(cudaStreamSynchronize(s));
-        if (h2 | h3) return map_status(h2 | h3, false);
+    SetsGraph &G = g_sets_graph[dev];
+    bool replay = false, capture = false;
+    if (graphs_enabled()) {
+        Fnv f;
+        f.val(X); f.val(N); f.val(d); f.val(dtype); f.val(nsets); f.val(sigma);
+        f.val(o.alpha); f.val(o.omega_mode); f.val(o.precision); f.val(o.root); f.val(o.include_self);
+        f.add(offsets, sizeof(int64_t) * (size_t)(P + 1));
+        f.add(ks, sizeof(int32_t) * (size_t)P);
+        f.val(labels); f.val(residual); f.val(i_k); f.val(beta);
+        f.val(out_parent); f.val(out_phi); f.val(out_omega);
+        f.val(base); f.val(meas.off);
+        const int fv = tc_forced_variant();
+        f.val(fv);
+        if (G.key != f.h) G.reset(f.h);
+        ++G.seen;
+        replay = !G.broken && G.g[0] && G.g[1];
+        capture = !G.broken && !replay && G.seen >= 2;
+        if ((replay || capture) && !g_graph_stream[dev] &&
+            cudaStreamCreateWithFlags(&g_graph_stream[dev], cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            replay = capture = false;
+        }
+        if ((replay || capture) && !G.ev) G.ev = new Events;
     }
-    ISO_CUDA(fix_set_roots(TS, nsets, d_offs, s));
-    ev.rec(3, s);
-
-    // eq. omega per set, symmetric tile pairs in each set's MST preorder
-    ISO_CUDA(nn_from_edges(M, M.eu, M.ev, M.ed2, s, m_mst));
-    k_pos64<<<(unsigned)ceil_div(N, TPB), TPB, 0, ISO_S(s)>>>(TS.T.pre, B.set_of, d_offs, d_tile0, N, B.pos);
-    ISO_CUDA(cudaMemsetAsync(B.nnp, 0xff, sizeof(unsigned long long) * n_pad64, s));
-    k_gather_pad<<<(unsigned)ceil_div(N * (int64_t)d, TPB), TPB, 0, ISO_S(s)>>>((const float *)X, B.pos, M.nnbits, N, d,
-                                                                                B.Xp, B.nnp);
-    ISO_CUDA(cudaMemsetAsync(B.tiles, 0, 2 * sizeof(unsigned long long), s));
-    ISO_CUDA(weights_launch_sym_sets(B.Xp, n_pad64, d, sigma, o.include_self, B.nnp, B.omp, B.sym, B.witems, nitems,
-                                     B.tile_valid, B.tile_set, d_tile0, d_ntl, d_item0, max_n, B.tiles,
-                                     ev.ok ? ev.e + 8 : nullptr, s));
-    k_scatter_pad<<<(unsigned)ceil_div(N + 1, TPB), TPB, 0, ISO_S(s)>>>(B.omp, B.pos, N, B.om);
-    ev.rec(4, s);
-    ISO_CUDA(phi_from_edges(TS, B.ed2, sigma, B.phi, s));
-    // Algorithm 2 + Algorithm 1 per set, then Algorithm 4's labels
-    ISO_CUDA(tree_search_and_label_sets(TS, nsets, d_offs, B.set_of, B.ks, B.SS, B.phi, B.om, nullptr, labels, residual,
-                                        i_k, beta, s));
-    ev.rec(5, s);
-    if (out_parent) ISO_CUDA(cudaMemcpyAsync(out_parent, TS.T.parent, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, s));
-    if (out_phi) ISO_CUDA(cudaMemcpyAsync(out_phi, B.phi, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
-    if (out_omega) ISO_CUDA(cudaMemcpyAsync(out_omega, B.om, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
-    ev.rec(6, s);
+    cudaStream_t q = (replay || capture) ? g_graph_stream[dev] : s;
+    Events &E = (replay || capture) ? *G.ev : ev;
+    for (int ph = 0; ph < 2; ++ph) {
+        if (replay) {
+            ISO_CUDA(cudaGraphLaunch(G.g[ph], q));
+            note_launches(G.nk[ph]);
+        } else if (capture && !G.broken) {
+            const long long c0 = g_launches.load();
+            ISO_CUDA(cudaStreamBeginCapture(q, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = ph == 0 ? phase0(q, E) : phase1(q, E);
+            cudaGraph_t graph = nullptr;
+            const cudaError_t ee = cudaStreamEndCapture(q, &graph);
+            if (e == cudaSuccess) e = ee;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&G.g[ph], graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (e == cudaSuccess) {
+                G.nk[ph] = g_launches.load() - c0;
+                ISO_CUDA(cudaGraphLaunch(G.g[ph], q));
+            } else {
+                // not capturable: this call from here on, and later calls
+                // with this signature, run kernel by kernel
+                cudaGetLastError();
+                G.broken = true;
+                ISO_CUDA(ph == 0 ? phase0(q, E) : phase1(q, E));
+            }
+        } else {
+            ISO_CUDA(ph == 0 ? phase0(q, E) : phase1(q, E));
+        }
+        if (ph == 0) {
+            // the trees are checked before anything walks them
+            uint32_t h2 = 0, h3 = 0;
+            ISO_CUDA(cudaMemcpyAsync(&h2, B.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, q));
+            ISO_CUDA(cudaMemcpyAsync(&h3, TS.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, q));
+            ISO_CUDA(cudaStreamSynchronize(q));
+            if (h2 | h3) return map_status(h2 | h3, false);
+        }
+    }
+    g_last_graph_mode = replay ? 2 : (capture && !G.broken ? 1 : 0);
     ISO_CUDA(cudaGetLastError());
-    ISO_CUDA(cudaStreamSynchronize(s));
+    ISO_CUDA(cudaStreamSynchronize(q));
     uint32_t fin = 0, tf = 0;
     ISO_CUDA(cudaMemcpy(&fin, B.status, sizeof(uint32_t), cudaMemcpyDeviceToHost));
     ISO_CUDA(cudaMemcpy(&tf, TS.status, sizeof(uint32_t), cudaMemcpyDeviceToHost));
@@ -771,18 +897,18 @@ static isoclust_status cluster_sets_impl(const void *X, const int64_t *offsets, 
     int32_t cnt[8] = {0};
     ISO_CUDA(cudaMemcpy(cnt, M.counters, sizeof(cnt), cudaMemcpyDeviceToHost));
     g_prof_ms[0] = ev.ms(0, 1);
-    g_prof_ms[1] = ev.ms(3, 4);
-    g_prof_ms[2] = ev.ms(1, 2);
-    g_prof_ms[3] = ev.ms(2, 3);
-    g_prof_ms[4] = ev.ms(4, 5);
-    g_prof_ms[5] = ev.ms(5, 6);
+    g_prof_ms[1] = E.ms(3, 4);
+    g_prof_ms[2] = E.ms(1, 2);
+    g_prof_ms[3] = E.ms(2, 3);
+    g_prof_ms[4] = E.ms(4, 5);
+    g_prof_ms[5] = E.ms(5, 6);
     g_prof_cnt[0] = cnt[MC_ROUNDS];
     g_prof_cnt[1] = cnt[MC_OVF_TOTAL] + cnt[MC_OVERFLOW];
     g_prof_cnt[2] = DP_SEARCH_PASSES + 1;
     g_prof_cnt[3] = 0;
     ISO_CUDA(cudaMemcpy(g_prof_tiles, B.tiles, sizeof(g_prof_tiles), cudaMemcpyDeviceToHost));
     g_prof_sym = 1;
-    g_prof_omega_kernel_ms = nitems > 0 ? ev.ms(8, 9) : 0.0;
+    g_prof_omega_kernel_ms = nitems > 0 ? E.ms(8, 9) : 0.0;
     return map_status(fin, false);
 }
 
@@ -838,6 +964,8 @@ isoclust_status isoclust_set_sweep_variant(int32_t variant) {
 }
 
 int32_t isoclust_last_sweep_variant(void) { return tc_last_variant(); }
+
+int32_t isoclust_last_batched_graph_mode(void) { return g_last_graph_mode; }
 
 void isoclust_last_omega_tiles(int64_t *tiles3) {
     if (tiles3) {

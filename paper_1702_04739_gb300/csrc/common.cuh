@@ -43,6 +43,16 @@ isoclust_status cuda_fail(cudaError_t e, const char *what);
 void note_launch();
 #define ISO_S(s) (::iso::note_launch(), (s))
 
+// Timing event on s.  Under stream capture a plain record only orders work
+// inside the graph; the external flag makes the graph record the event
+// itself when it runs, so its time can be read afterwards.
+inline cudaError_t record_event(cudaEvent_t e, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        return cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    return cudaEventRecord(e, s);
+}
+
 // ---------------------------------------------------------------- arena
 // Bump allocator over one device buffer.  In measure mode (base == nullptr)
 // it only adds up the bytes a stage needs, so the same carving code both

@@ -95,6 +95,7 @@ cudaError_t tc_omega_screen(TcScratch &T, const float *Xp, int64_t n, int32_t d,
 cudaError_t tc_autotune(TcScratch &T, MstScratch &S, const float *X, int64_t n, int32_t d, uint32_t *status,
                         cudaStream_t s);
 void tc_force_variant(int variant);     // -1: tune
+int tc_forced_variant();                // the setting (-1: tune)
 int tc_last_variant();                  // this thread's last variant (-1: none)
 void tc_clear_last_variant();           // a build without the tensor-core sweep
 // independent sets: recount the components of every set from comp

@@ -1145,6 +1145,7 @@ void apply_variant(TcScratch &T, int v) {
 }  // namespace
 
 void tc_force_variant(int variant) { g_force.store(variant); }
+int tc_forced_variant() { return g_force.load(); }
 int tc_last_variant() { return g_last_variant; }
 void tc_clear_last_variant() { g_last_variant = -1; }
 

@@ -763,7 +763,7 @@ __global__ void k_omega_tree(const uint64_t *__restrict__ adj_key, const int32_t
 
 // ---------------------------------------------------------------- host side
 cudaError_t orient_tree(TreeScratch &S, const int32_t *eu, const int32_t *ev, int64_t n, int32_t root,
-                        const int32_t *expect_parent, cudaStream_t s, const int32_t *vset) {
+                        const int32_t *expect_parent, cudaStream_t s, const int32_t *vset, int part) {
     TreeDev &T = S.T;
     T.n = n;
     T.root = root;
@@ -785,26 +785,31 @@ cudaError_t orient_tree(TreeScratch &S, const int32_t *eu, const int32_t *ev, in
         return cudaStreamSynchronize(s);
     }
     const int64_t m = n - 1, M = 2 * m;
-    k_dir_keys<<<blocks_for(m), TPB, 0, ISO_S(s)>>>(eu, ev, m, n, T.adj_key, S.vals, S.status);
-    if ((e = sort_pairs_u64(T.adj_key, S.vals, S.kbuf, S.vbuf, M, s))) return e;
-    k_fill_i32<<<blocks_for(n + 1), TPB, 0, ISO_S(s)>>>(T.adj_off, n + 1, -1);
-    k_adj_off<<<blocks_for(M), TPB, 0, ISO_S(s)>>>(T.adj_key, M, n, T.adj_off, S.status);
-    k_check_adj<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(T.adj_off, n, S.status);
-    k_rev_succ<<<blocks_for(M), TPB, 0, ISO_S(s)>>>(T.adj_key, T.adj_off, M, n, S.rev, S.succ, S.status);
-    k_break_tour<<<1, 1, 0, ISO_S(s)>>>(T.adj_off, S.rev, S.succ, root, M, S.status);
-    k_fill_i32<<<blocks_for(M), TPB, 0, ISO_S(s)>>>(S.rnk, M, 1);
-    int32_t *sa = S.succ, *sb = S.succ2, *ra = S.rnk, *rb = S.rnk2;
     const int L = log2_ceil(M) + 1;
-    for (int it = 0; it < L; ++it) {
-        k_wyllie<<<blocks_for(M), TPB, 0, ISO_S(s)>>>(sa, ra, sb, rb, M);
-        int32_t *t = sa; sa = sb; sb = t;
-        t = ra; ra = rb; rb = t;
+    // the ranks end in rnk after an even number of Wyllie steps, else rnk2
+    int32_t *ra = (L % 2 == 0) ? S.rnk : S.rnk2;
+    if (part != 2) {
+        k_dir_keys<<<blocks_for(m), TPB, 0, ISO_S(s)>>>(eu, ev, m, n, T.adj_key, S.vals, S.status);
+        if ((e = sort_pairs_u64(T.adj_key, S.vals, S.kbuf, S.vbuf, M, s))) return e;
+        k_fill_i32<<<blocks_for(n + 1), TPB, 0, ISO_S(s)>>>(T.adj_off, n + 1, -1);
+        k_adj_off<<<blocks_for(M), TPB, 0, ISO_S(s)>>>(T.adj_key, M, n, T.adj_off, S.status);
+        k_check_adj<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(T.adj_off, n, S.status);
+        k_rev_succ<<<blocks_for(M), TPB, 0, ISO_S(s)>>>(T.adj_key, T.adj_off, M, n, S.rev, S.succ, S.status);
+        k_break_tour<<<1, 1, 0, ISO_S(s)>>>(T.adj_off, S.rev, S.succ, root, M, S.status);
+        k_fill_i32<<<blocks_for(M), TPB, 0, ISO_S(s)>>>(S.rnk, M, 1);
+        int32_t *sa = S.succ, *sb = S.succ2, *rk = S.rnk, *rb = S.rnk2;
+        for (int it = 0; it < L; ++it) {
+            k_wyllie<<<blocks_for(M), TPB, 0, ISO_S(s)>>>(sa, rk, sb, rb, M);
+            int32_t *t = sa; sa = sb; sb = t;
+            t = rk; rk = rb; rb = t;
+        }
+        k_check_ranked<<<blocks_for(M), TPB, 0, ISO_S(s)>>>(sa, rk, M, S.status);
+        if (part == 1) return cudaGetLastError();
+        uint32_t hst = 0;
+        if ((e = cudaMemcpyAsync(&hst, S.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s))) return e;
+        if ((e = cudaStreamSynchronize(s))) return e;
+        if (hst & DEV_BAD_TREE) return cudaSuccess;   // caller reads the status word
     }
-    k_check_ranked<<<blocks_for(M), TPB, 0, ISO_S(s)>>>(sa, ra, M, S.status);
-    uint32_t hst = 0;
-    if ((e = cudaMemcpyAsync(&hst, S.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s))) return e;
-    if ((e = cudaStreamSynchronize(s))) return e;
-    if (hst & DEV_BAD_TREE) return cudaSuccess;   // caller reads the status word
 
     k_orient<<<blocks_for(M), TPB, 0, ISO_S(s)>>>(T.adj_key, S.vals, S.rev, ra, M, n, root, T.parent, S.size, T.edge_of,
                                            S.flag);

@@ -70,8 +70,13 @@ struct TreeScratch {
 // vset != nullptr: the tree joins independent sets under a virtual root
 // (vertex n - 1, vset[v] = set of each real vertex v); the BFS order is then
 // set-major, (depth, preorder) inside each set.
+// part 0: the whole orientation, with a host check of the Euler tour (a bad
+// tree returns before the tour is used); part 1: the tour and its ranking up
+// to that check (no host synchronisation: the caller reads S.status); part
+// 2: the rest (call only after the caller has seen no DEV_BAD_TREE).
 cudaError_t orient_tree(TreeScratch &S, const int32_t *eu, const int32_t *ev, int64_t n,
-                        int32_t root, const int32_t *expect_parent, cudaStream_t s, const int32_t *vset = nullptr);
+                        int32_t root, const int32_t *expect_parent, cudaStream_t s, const int32_t *vset = nullptr,
+                        int part = 0);
 
 // Edges (eu, ev) from a parent array (root entry skipped), written into
 // S.fpos/S.flag-sized buffers; returns the buffers through out pointers.

@@ -791,11 +791,11 @@ cudaError_t weights_launch_sym(const float *X, int64_t n, int32_t d, double sigm
     k_tile_bounds<<<(unsigned)T, 64, 0, ISO_S(s)>>>(X, n, d, P.shdw, nullptr, P.cen, P.rad, P.msh);
     k_tile_pair_skip<false><<<(unsigned)(num_sms() * 8), 256, 0, ISO_S(s)>>>(P.cen, P.rad, P.msh, d, T, items, nullptr,
                                                                             is_h, zskip, shrink, need, P.tskip);
-    if (kev) cudaEventRecord(kev[0], s);
+    if (kev) record_event(kev[0], s);
     k_weights_sym<false><<<grid, TPB, 0, ISO_S(s)>>>(X, n, d, P.shdw, is_h, is_l, tab, zskip, shrink, T, items, nullptr,
                                                      nullptr, P.tskip, need ? 1 : 0, P.flags, P.rpart, P.cpart,
                                                      tile_counts);
-    if (kev) cudaEventRecord(kev[1], s);
+    if (kev) record_event(kev[1], s);
     k_weights_reduce<<<(unsigned)ceil_div(n, 256), 256, 0, ISO_S(s)>>>(nnbits, n, T, is, include_self, P.flags,
                                                                       P.rpart, P.cpart, omega);
     return cudaGetLastError();
@@ -829,7 +829,7 @@ cudaError_t weights_launch_sym_sets(const float *Xp, int64_t n_pad, int32_t d, d
     if (nitems > 0) {
         k_tile_pair_skip<true><<<(unsigned)(num_sms() * 8), 256, 0, ISO_S(s)>>>(
             P.cen, P.rad, P.msh, d, T, nitems, witems, is_h, zskip, shrink, nullptr, P.tskip);
-        if (kev) cudaEventRecord(kev[0], s);
+        if (kev) record_event(kev[0], s);
         // independent sets: the tile bound is the only screen; tile pairs it
         // keeps go straight to the double-word pass (for sets of a few
         // thousand points nearly every pair of tiles holds terms, so the FP32
@@ -837,7 +837,7 @@ cudaError_t weights_launch_sym_sets(const float *Xp, int64_t n_pad, int32_t d, d
         k_weights_sym<true><<<grid, TPB, 0, ISO_S(s)>>>(Xp, n_pad, d, P.shdw, is_h, is_l, tab, zskip, shrink, 0, nitems,
                                                         witems, tile_valid, P.tskip, 1, P.flags, P.rpart, P.cpart,
                                                         tile_counts);
-        if (kev) cudaEventRecord(kev[1], s);
+        if (kev) record_event(kev[1], s);
     }
     k_weights_reduce_sets<<<(unsigned)ceil_div(n_pad, 256), 256, 0, ISO_S(s)>>>(
         nnbits, n_pad, tile_valid, tile_set, tile0, ntl, item0, is, include_self, P.flags, P.rpart, P.cpart, omega);

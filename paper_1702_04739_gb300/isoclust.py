@@ -98,6 +98,8 @@ def load(build_if_missing: bool = True):
         lib.isoclust_set_sweep_variant.argtypes = [ctypes.c_int32]
         lib.isoclust_last_sweep_variant.restype = ctypes.c_int32
         lib.isoclust_last_sweep_variant.argtypes = []
+        lib.isoclust_last_batched_graph_mode.restype = ctypes.c_int32
+        lib.isoclust_last_batched_graph_mode.argtypes = []
         lib.isoclust_last_omega_tiles.restype = None
         lib.isoclust_last_omega_tiles.argtypes = [_P]
         _lib = lib
@@ -364,6 +366,12 @@ def set_sweep_variant(variant: int) -> None:
 def last_sweep_variant() -> int:
     """Sweep variant of the last MST build on this thread (-1: none)."""
     return int(load().isoclust_last_sweep_variant())
+
+
+def last_batched_graph_mode() -> int:
+    """0 kernel by kernel, 1 captured into CUDA graphs, 2 replayed graphs
+    (the last batched call; isoclust_last_batched_graph_mode)."""
+    return int(load().isoclust_last_batched_graph_mode())
 
 
 def kernel_launches() -> int:

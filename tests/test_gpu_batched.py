@@ -144,3 +144,32 @@ def test_full_batch_properties(full):
         assert ((L >= -1) & (L < ks[b])).all()
         assert np.unique(L[L >= 0]).size == ks[b]
         assert (om[lo:hi] > 0).all()
+
+
+def test_repeated_calls_replay_cuda_graphs(iso):
+    """Identical batched calls: the first launches kernel by kernel, the
+    second captures CUDA graphs, the third replays them; every output is
+    bit-identical and each call launches the same number of kernels."""
+    X, offs, ks = _small_batch(3)
+    Xd = torch.from_numpy(X).cuda()
+    plan = iso.BatchPlan(offs, ks)
+    n = X.shape[0]
+    outs, modes, launches = [], [], []
+    labels = torch.empty(n, dtype=torch.int32, device="cuda")
+    residual = torch.empty(n, dtype=torch.uint8, device="cuda")
+    ik = torch.empty(len(ks), dtype=torch.float64, device="cuda")
+    for _ in range(4):
+        l0 = iso.kernel_launches()
+        iso.cluster_batched_into(Xd, plan, 1.0, labels, residual, ik)
+        launches.append(iso.kernel_launches() - l0)
+        modes.append(iso.last_batched_graph_mode())
+        outs.append((labels.cpu().numpy().copy(), residual.cpu().numpy().copy(), ik.cpu().numpy().copy()))
+    assert modes == [0, 1, 2, 2], modes
+    assert len(set(launches)) == 1, launches
+    for o in outs[1:]:
+        for a, b in zip(o, outs[0]):
+            assert (a == b).all()
+    # another signature (different ks) starts again kernel by kernel
+    ks2 = np.maximum(1, np.asarray(ks) - 1).astype(np.int32)
+    iso.cluster_batched_into(Xd, iso.BatchPlan(offs, ks2), 1.0, labels, residual, ik)
+    assert iso.last_batched_graph_mode() == 0
