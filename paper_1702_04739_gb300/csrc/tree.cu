@@ -484,7 +484,9 @@ struct DpArgs {
 
 // One warp walks from leaf v towards the root, deciding each vertex for the
 // 32 thresholds of its lanes; returns this lane's cuts.
-__device__ __forceinline__ int dp_walk(const DpArgs &A, int32_t v, double N, int lane, int final_pass,
+// One warp walks from leaf v towards the root, deciding each vertex for the
+// 32 thresholds of its lanes; returns this lane's cuts.
+__device__ __forceinline__ int dp_walk_tree(const DpArgs &A, int32_t v, double N, int lane, int final_pass,
                                        uint8_t *__restrict__ dec, double *__restrict__ wh, double *__restrict__ ph,
                                        int32_t *__restrict__ done, double *__restrict__ rat) {
     int cuts = 0;
@@ -536,6 +538,81 @@ __device__ __forceinline__ int dp_walk(const DpArgs &A, int32_t v, double N, int
     return cuts;
 }
 
+// The same walk for the independent sets' pass, which has millions of short
+// walks in flight: a vertex's own data (its child range, parent, omega, p,
+// phi of its parent edge) does not change during a pass, so the parent's is
+// loaded while the current vertex's children are folded.  (One large tree's
+// pass is bound by its longest walk and measured faster with dp_walk_tree.)
+__device__ __forceinline__ int dp_walk_sets(const DpArgs &A, int32_t v, double N, int lane, int final_pass,
+                                       uint8_t *__restrict__ dec, double *__restrict__ wh, double *__restrict__ ph,
+                                       int32_t *__restrict__ done, double *__restrict__ rat) {
+    int cuts = 0;
+    int32_t c0 = A.ch_off[v], c1 = A.ch_off[v + 1];
+    int32_t u = A.parent[v];
+    double w0 = A.omega[v];
+    double p0 = A.p ? A.p[v] : 0.0;
+    double fe = u >= 0 ? A.phi[v] : 0.0;
+    while (true) {
+        int32_t uc0 = 0, uc1 = 0, uu = -1;
+        double uw = 0.0, up = 0.0, ufe = 0.0;
+        if (u >= 0) {
+            uc0 = A.ch_off[u];
+            uc1 = A.ch_off[u + 1];
+            uu = A.parent[u];
+            uw = A.omega[u];
+            up = A.p ? A.p[u] : 0.0;
+            ufe = A.phi[u];
+        }
+        double w = w0, pv = p0;
+        for (int32_t q = c1 - 1; q >= c0; --q) {   // siblings in descending index
+            const int32_t c = A.ch_list[q];
+            const size_t cl = (size_t)c * DP_LANES + lane;
+            const uint8_t dc = ld_cg_u8(dec + cl);
+            if (dc == DEC_JOIN) {
+                w = __dadd_rn(w, ld_cg_f64(wh + cl));
+                pv = __dadd_rn(pv, ld_cg_f64(ph + cl));
+            } else {
+                pv = __dadd_rn(pv, A.phi[c]);       // cut or discarded child: boundary edge
+            }
+        }
+        const double nw = __dmul_rn(N, w);
+        const double fp = __dadd_rn(fe, pv);
+        uint8_t d;
+        if (fp <= nw) {
+            d = DEC_CUT;
+            ++cuts;
+            if (final_pass && lane == 0) rat[v] = __ddiv_rn(fp, w);
+        } else if (u >= 0 && __dsub_rn(pv, fe) < nw) {
+            d = DEC_JOIN;
+        } else {
+            d = DEC_DISCARD;
+        }
+        const size_t vl = (size_t)v * DP_LANES + lane;
+        dec[vl] = d;
+        wh[vl] = w;
+        ph[vl] = pv;
+        if (u < 0) break;
+        const int32_t nu = uc1 - uc0;
+        if (nu != 1) {                             // an only child has no one to wait for
+            __threadfence();
+            __syncwarp();
+            int old = 0;
+            if (lane == 0) old = atomicAdd(done + u, 1);
+            old = __shfl_sync(0xffffffffu, old, 0);
+            if (old != nu - 1) break;              // a sibling is still running
+            __threadfence();
+        }
+        v = u;
+        c0 = uc0;
+        c1 = uc1;
+        u = uu;
+        w0 = uw;
+        p0 = up;
+        fe = uu >= 0 ? ufe : 0.0;
+    }
+    return cuts;
+}
+
 __global__ void __launch_bounds__(256) k_dp_pass(DpArgs A, SearchState *S, uint8_t *__restrict__ dec,
                                                  double *__restrict__ wh, double *__restrict__ ph,
                                                  int32_t *__restrict__ done, double *__restrict__ rat,
@@ -548,7 +625,7 @@ __global__ void __launch_bounds__(256) k_dp_pass(DpArgs A, SearchState *S, uint8
     const int nleaves = S->nleaves;
     int cuts = 0;
     for (int64_t li = warp; li < nleaves; li += nwarps)
-        cuts += dp_walk(A, A.leaves[li], N, lane, final_pass, dec, wh, ph, done, rat);
+        cuts += dp_walk_tree(A, A.leaves[li], N, lane, final_pass, dec, wh, ph, done, rat);
     if (cuts) atomicAdd(&S->cnt[lane], cuts);
 }
 
@@ -579,7 +656,7 @@ __global__ void __launch_bounds__(256) k_dp_pass_sets(DpArgs A, const SearchStat
         const SearchState *S = SS + b;
         if (!final_pass && S->done) continue;
         const double N = final_pass ? S->beta : S->thr[lane];
-        cuts += dp_walk(A, v, N, lane, final_pass, dec, wh, ph, done, rat);
+        cuts += dp_walk_sets(A, v, N, lane, final_pass, dec, wh, ph, done, rat);
     }
     if (cuts) atomicAdd(&SS[cur].cnt[lane], cuts);
 }
