@@ -458,6 +458,7 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
     __shared__ float2 mr[WT][17];
     __shared__ float2 mc[WT][17];
     __shared__ int64_t sIJ[5];
+    __shared__ float sred[TPB / 32][2];        // per warp: smallest and largest shift of its real rows
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     if (tid < 64) tab[tid] = tabv.t[tid];
@@ -496,6 +497,21 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
             const float2 b = cok(lc) ? shdw[col0 + lc] : make_float2(0.f, 0.f);
             rs_h[q] = a.x; rs_l[q] = a.y;
             cs_h[q] = b.x; cs_l[q] = b.y;
+        }
+        {
+            // the tile pair's range of shifts (read after the next barrier)
+            float mn = INFINITY, mx = -INFINITY;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (rok(ty * 4 + q)) { mn = fminf(mn, rs_h[q]); mx = fmaxf(mx, rs_h[q]); }
+                if (cok(tx * 4 + q)) { mn = fminf(mn, cs_h[q]); mx = fmaxf(mx, cs_h[q]); }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+                mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            }
+            if ((tid & 31) == 0) { sred[tid >> 5][0] = mn; sred[tid >> 5][1] = mx; }
         }
         // ---- FP32 screen, both directions (unless the tensor-core screen
         //      already decided this pair of tiles)
@@ -593,6 +609,20 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
         }
         float rh[4] = {0.f, 0.f, 0.f, 0.f}, rl[4] = {0.f, 0.f, 0.f, 0.f};
         float ch[4] = {0.f, 0.f, 0.f, 0.f}, cl[4] = {0.f, 0.f, 0.f, 0.f};
+        // One exponential per pair for both of its rows: terms are taken
+        // against a shift sref shared by the tile pair, exp(-(y - sref)), and
+        // each row's partial is scaled by exp(sh - sref) in the merge.  sref
+        // keeps every kept term's exponent in [-75, 70] (double-word FP32
+        // stays normal and the partials finite); otherwise each direction
+        // takes its own shift as on the diagonal.
+        float smin = INFINITY, smax = -INFINITY;
+#pragma unroll
+        for (int q = 0; q < TPB / 32; ++q) { smin = fminf(smin, sred[q][0]); smax = fmaxf(smax, sred[q][1]); }
+        const float sref = fmaxf(smin, smax + zskip - 70.0f);
+        const bool one_exp = !diag && sref - smin <= 75.0f;
+        float ar[4], ac[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { ar[q] = rs_h[q] - sref; ac[q] = cs_h[q] - sref; }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int lr = ty * 4 + i;
@@ -608,9 +638,28 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
                     dl = __fmul_rn(res, __frcp_rn(__fadd_rn(r, r)));
                 }
                 float th, tl2;
-                if (dw_term(r, dl, is_h, is_l, rs_h[i], rs_l[i], zskip, tab, th, tl2)) dw_add(rh[i], rl[i], th, tl2);
-                if (!diag && dw_term(r, dl, is_h, is_l, cs_h[j], cs_l[j], zskip, tab, th, tl2))
+                if (one_exp) {
+                    float yh, yl;
+                    two_prod(r, is_h, yh, yl);
+                    yl = __fmaf_rn(r, is_l, yl);
+                    yl = __fmaf_rn(dl, is_h, yl);
+                    fast_two_sum(yh, yl, yh, yl);
+                    float zh, zl;
+                    two_sum(yh, -sref, zh, zl);
+                    zl = __fadd_rn(zl, yl);
+                    fast_two_sum(zh, zl, zh, zl);
+                    // below e^-zskip of the largest term of both rows (the
+                    // margin covers the FP32 shift differences): dropped
+                    if (zh > zskip + fmaxf(ar[i], ac[j]) + 0.01f) continue;
+                    dw_exp_neg(zh, zl, tab, th, tl2);
+                    dw_add(rh[i], rl[i], th, tl2);
                     dw_add(ch[j], cl[j], th, tl2);
+                } else {
+                    if (dw_term(r, dl, is_h, is_l, rs_h[i], rs_l[i], zskip, tab, th, tl2))
+                        dw_add(rh[i], rl[i], th, tl2);
+                    if (!diag && dw_term(r, dl, is_h, is_l, cs_h[j], cs_l[j], zskip, tab, th, tl2))
+                        dw_add(ch[j], cl[j], th, tl2);
+                }
             }
         }
         // rows of I: merge the 16 column-threads; columns of J: merge the 16 row-threads
@@ -621,15 +670,31 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
             mc[tx * 4 + q][ty] = make_float2(ch[q], cl[q]);
         }
         __syncthreads();
+        // partials leave in each row's own shift: sum exp(-(y - sh))
+        auto to_own_shift = [&](float &h, float &l, float2 sh) {
+            float zh, zl, fh, fl;
+            two_sum(sref, -sh.x, zh, zl);          // sref - sh as a double-word
+            zl = __fsub_rn(zl, sh.y);
+            fast_two_sum(zh, zl, zh, zl);
+            dw_exp_neg(zh, zl, tab, fh, fl);       // exp(sh - sref)
+            float p, e;
+            two_prod(h, fh, p, e);
+            e = __fmaf_rn(h, fl, e);
+            e = __fmaf_rn(l, fh, e);
+            fast_two_sum(p, e, h, l);
+        };
         if (tid < WT) {
             float h = 0.f, l = 0.f;
             for (int k = 0; k < 16; ++k) dw_add(h, l, mr[tid][k].x, mr[tid][k].y);
+            if (one_exp && rok(tid)) to_own_shift(h, l, shdw[row0 + tid]);
             rpart[w * WT + tid] = make_float2(h, l);
         } else if (tid < 2 * WT) {
             const int c = tid - WT;
             float h = 0.f, l = 0.f;
-            if (!diag)
+            if (!diag) {
                 for (int k = 0; k < 16; ++k) dw_add(h, l, mc[c][k].x, mc[c][k].y);
+                if (one_exp && cok(c)) to_own_shift(h, l, shdw[col0 + c]);
+            }
             cpart[w * WT + c] = make_float2(h, l);
         }
         if (tid == 0) flags[w] = 1;
