@@ -146,12 +146,16 @@ __global__ void __launch_bounds__(TPB) k_phi_grad(const T *__restrict__ X, const
 // tile of the group's list, chunk of GC columns): group 0 = rows of A*
 // against every point, group 1 = the other rows against A*.  Per 64 x 64
 // pair tile: squared distances from dot products, |z_i|^2 + |z_j|^2 -
-// 2 z_i.z_j (4 x 4 pairs per thread, FP64), with a direct recomputation
-// where that cancels (d2 < 2^-20 (|z_i|^2 + |z_j|^2)); the coefficients in
-// shared memory; then V_i += sum_j c_ij z_j for 128 dimensions at a time
-// (4 rows x 1 dimension per thread and 16-dimension chunk).  Each item
-// writes its partial sums to its own slot; k_pair_reduce adds the slots of a
-// row in chunk order.
+// 2 z_i.z_j (4 x 4 pairs per thread), with a direct FP64 recomputation
+// where that cancels (d2 < 2^-20 (|z_i|^2 + |z_j|^2)); the coefficients
+// (FP64: sqrt, exp) in shared memory; then V_i += sum_j c_ij z_j for 128
+// dimensions at a time (4 rows x 1 dimension per thread and 16-dimension
+// chunk).  The two d-long sums run in double-word FP32 on z's double-word
+// copy (exact products by FMA, TwoSum of the high parts, low parts summed
+// in FP32 and renormalised every 16 dimensions or 64 columns: relative
+// error ~ d 2^-48), where GB300's FP32 pipe has 64 times the FP64 rate.
+// Each item writes its partial sums to its own slot; k_pair_reduce adds the
+// slots of a row in chunk order.
 constexpr int GT = 64;              // rows / columns per pair tile
 constexpr int GDC = 16;             // dimensions per shared-memory chunk
 constexpr int GVD = 128;            // dimensions of V per pass
@@ -161,17 +165,54 @@ struct PairItem {
     int32_t group, tile, chunk, pad;
 };
 
+// (sh, sl) += (ah + al)(bh + bl): the product's error by FMA, the cross
+// terms rounded (the lo.lo term is below 2^-48 of the product), the high
+// parts added by TwoSum, everything else gathered in sl (renormalised by
+// the caller)
+__device__ __forceinline__ void dw_mac(float ah, float al, float bh, float bl, float &sh, float &sl) {
+    const float p = __fmul_rn(ah, bh);
+    float e = __fmaf_rn(ah, bh, -p);
+    e = __fmaf_rn(ah, bl, e);
+    e = __fmaf_rn(al, bh, e);
+    const float t = __fadd_rn(sh, p);
+    const float bb = __fsub_rn(t, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+    sh = t;
+    sl = __fadd_rn(sl, __fadd_rn(err, e));
+}
+__device__ __forceinline__ void dw_norm(float &h, float &l) {
+    const float t = __fadd_rn(h, l);
+    l = __fsub_rn(l, __fsub_rn(t, h));
+    h = t;
+}
+__device__ __forceinline__ float2 dw_of(double z) {
+    const float h = __double2float_rn(z);
+    return make_float2(h, __double2float_rn(__dsub_rn(z, (double)h)));
+}
+
+// z = s (.) x of every point as double-words, once per call
+template <class T>
+__global__ void k_z_dw(const T *__restrict__ X, const double *__restrict__ s, int64_t n, int32_t d,
+                       float2 *__restrict__ Zd) {
+    const int64_t tot = n * (int64_t)d, gs = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += gs) {
+        const int32_t t = (int32_t)(e % d);
+        Zd[e] = dw_of(__dmul_rn(s[t], (double)X[e]));
+    }
+}
+
 template <class T>
 __global__ void __launch_bounds__(TPB, 1)
 k_pair_grad(const T *__restrict__ X, const double *__restrict__ s, int64_t n, int32_t d,
             const double *__restrict__ N2, const int32_t *__restrict__ inA, const int32_t *__restrict__ alist,
             const int32_t *__restrict__ blist, const int32_t *__restrict__ cnt, const PairItem *__restrict__ items,
-            int64_t nitems, double sigma, double *__restrict__ Vp, double *__restrict__ Cp, double *__restrict__ Op,
-            double *__restrict__ Sp) {
-    extern __shared__ __align__(16) double gsm[];
-    double *Zr = gsm;                                  // [GDC][GT]
-    double *Zc = Zr + GDC * GT;                        // [GDC][GT]
-    double *Cm = Zc + GDC * GT;                        // [GT][GT + 1]
+            int64_t nitems, double sigma, const float2 *__restrict__ Zd, double *__restrict__ Vp,
+            double *__restrict__ Cp, double *__restrict__ Op, double *__restrict__ Sp) {
+    extern __shared__ __align__(16) float2 gsm[];
+    const double isg = 1.0 / sigma, isg2 = isg * isg;
+    float2 *Zr = gsm;                                  // [GDC][GT] double-word z of the rows
+    float2 *Zc = Zr + GDC * GT;                        // [GDC][GT] of the columns
+    float2 *Cm = Zc + GDC * GT;                        // [GT][GT + 1] double-word coefficients
     __shared__ int32_t ri[GT], ci[GT], rin[GT], cin[GT];
     __shared__ double rn[GT], cn[GT];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -192,11 +233,11 @@ k_pair_grad(const T *__restrict__ X, const double *__restrict__ s, int64_t n, in
         double csum[4] = {0, 0, 0, 0}, osum[4] = {0, 0, 0, 0}, ssum[4] = {0, 0, 0, 0};
         for (int32_t v0 = 0; v0 < d; v0 += GVD) {
             const int32_t vl = min(GVD, d - v0);
-            double V[4][GVD / GDC];
+            float Vh[4][GVD / GDC], Vl[4][GVD / GDC];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int c = 0; c < GVD / GDC; ++c) V[i][c] = 0.0;
+                for (int c = 0; c < GVD / GDC; ++c) { Vh[i][c] = 0.f; Vl[i][c] = 0.f; }
             for (int64_t c0 = q0; c0 < q1; c0 += GT) {
                 __syncthreads();
                 if (tid < GT) {
@@ -206,24 +247,25 @@ k_pair_grad(const T *__restrict__ X, const double *__restrict__ s, int64_t n, in
                     cin[tid] = j >= 0 ? inA[j] : 0;
                     cn[tid] = j >= 0 ? N2[j] : 0.0;
                 }
-                // ---- dot products z_i . z_j, 4 x 4 per thread
-                double acc[4][4];
+                // ---- dot products z_i . z_j, 4 x 4 per thread (double-word)
+                float gh[4][4], gl[4][4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+                    for (int j = 0; j < 4; ++j) { gh[i][j] = 0.f; gl[i][j] = 0.f; }
+                const float2 zero2 = make_float2(0.f, 0.f);
                 for (int32_t t0 = 0; t0 < d; t0 += GDC) {
                     __syncthreads();
                     for (int e = tid; e < GDC * GT; e += TPB) {
                         const int t = e / GT, r = e % GT;
                         const bool ok = t0 + t < d;
-                        Zr[e] = (ok && ri[r] >= 0) ? zv(X, s, ri[r], t0 + t, d) : 0.0;
-                        Zc[e] = (ok && ci[r] >= 0) ? zv(X, s, ci[r], t0 + t, d) : 0.0;
+                        Zr[e] = (ok && ri[r] >= 0) ? Zd[(int64_t)ri[r] * d + t0 + t] : zero2;
+                        Zc[e] = (ok && ci[r] >= 0) ? Zd[(int64_t)ci[r] * d + t0 + t] : zero2;
                     }
                     __syncthreads();
 #pragma unroll 4
                     for (int t = 0; t < GDC; ++t) {
-                        double a[4], b[4];
+                        float2 a[4], b[4];
 #pragma unroll
                         for (int i = 0; i < 4; ++i) a[i] = Zr[t * GT + ty * 4 + i];
 #pragma unroll
@@ -231,8 +273,12 @@ k_pair_grad(const T *__restrict__ X, const double *__restrict__ s, int64_t n, in
 #pragma unroll
                         for (int i = 0; i < 4; ++i)
 #pragma unroll
-                            for (int j = 0; j < 4; ++j) acc[i][j] = __fma_rn(a[i], b[j], acc[i][j]);
+                            for (int j = 0; j < 4; ++j) dw_mac(a[i].x, a[i].y, b[j].x, b[j].y, gh[i][j], gl[i][j]);
                     }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) dw_norm(gh[i][j], gl[i][j]);
                 }
                 // ---- pair coefficients
 #pragma unroll
@@ -247,7 +293,8 @@ k_pair_grad(const T *__restrict__ X, const double *__restrict__ s, int64_t n, in
                         double cc = 0.0;
                         if (gi >= 0 && gj >= 0 && gi != gj && mult > 0) {
                             const double nsum = rn[r] + cn[c];
-                            double r2 = __fma_rn(-2.0, acc[i][j], nsum);
+                            const double g = __dadd_rn((double)gh[i][j], (double)gl[i][j]);
+                            double r2 = __fma_rn(-2.0, g, nsum);
                             if (r2 < nsum * 9.5367431640625e-07) {      // cancellation: direct differences
                                 double dd = 0.0;
                                 for (int32_t t = 0; t < d; ++t) {
@@ -256,15 +303,20 @@ k_pair_grad(const T *__restrict__ X, const double *__restrict__ s, int64_t n, in
                                 }
                                 r2 = dd;
                             }
-                            const double rr = sqrt(fmax(r2, 0.0));
-                            const double ww = exp(-rr / sigma);
-                            if (rr > 0.0) cc = -(double)mult * ww / (sigma * rr);
+                            // r and 1/r from one reciprocal square root; 1/sigma
+                            // and 1/sigma^2 precomputed (no FP64 division, the
+                            // costliest part of a pair on the FP64 pipe)
+                            const double r2c = fmax(r2, 0.0);
+                            const double irr = r2c > 0.0 ? rsqrt(r2c) : 0.0;
+                            const double rr = r2c * irr;
+                            const double ww = exp(-rr * isg);
+                            if (rr > 0.0) cc = -(double)mult * ww * (isg * irr);
                             if (rin[r] && v0 == 0) {
                                 os = os + ww;
-                                ss = ss + ww * rr / (sigma * sigma);
+                                ss = ss + ww * rr * isg2;
                             }
                         }
-                        Cm[r * (GT + 1) + c] = cc;
+                        Cm[r * (GT + 1) + c] = dw_of(cc);
                         cs = cs + cc;
                     }
                     // rows' sums over this tile's 64 columns: the 16 threads of a row, in order
@@ -285,7 +337,7 @@ k_pair_grad(const T *__restrict__ X, const double *__restrict__ s, int64_t n, in
                     __syncthreads();
                     for (int e = tid; e < GDC * GT; e += TPB) {
                         const int t = e / GT, c = e % GT;
-                        Zc[e] = (h + t < vl && ci[c] >= 0) ? zv(X, s, ci[c], v0 + h + t, d) : 0.0;
+                        Zc[e] = (h + t < vl && ci[c] >= 0) ? Zd[(int64_t)ci[c] * d + v0 + h + t] : make_float2(0.f, 0.f);
                     }
                     __syncthreads();
                     const int hc = h / GDC;
@@ -294,10 +346,15 @@ k_pair_grad(const T *__restrict__ X, const double *__restrict__ s, int64_t n, in
                         if (hh != hc) continue;
 #pragma unroll 8
                         for (int c = 0; c < GT; ++c) {
-                            const double zc = Zc[tx * GT + c];
+                            const float2 zc = Zc[tx * GT + c];
 #pragma unroll
-                            for (int i = 0; i < 4; ++i) V[i][hh] = __fma_rn(Cm[(ty * 4 + i) * (GT + 1) + c], zc, V[i][hh]);
+                            for (int i = 0; i < 4; ++i) {
+                                const float2 cf = Cm[(ty * 4 + i) * (GT + 1) + c];
+                                dw_mac(cf.x, cf.y, zc.x, zc.y, Vh[i][hh], Vl[i][hh]);
+                            }
                         }
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) dw_norm(Vh[i][hh], Vl[i][hh]);
                     }
                 }
             }
@@ -307,7 +364,7 @@ k_pair_grad(const T *__restrict__ X, const double *__restrict__ s, int64_t n, in
 #pragma unroll
                 for (int hh = 0; hh < GVD / GDC; ++hh) {
                     const int32_t t = v0 + hh * GDC + tx;
-                    if (t < d) Vp[(w * GT + ty * 4 + i) * (int64_t)d + t] = V[i][hh];
+                    if (t < d) Vp[(w * GT + ty * 4 + i) * (int64_t)d + t] = __dadd_rn((double)Vh[i][hh], (double)Vl[i][hh]);
                 }
         }
         if (tx == 0) {
@@ -460,6 +517,7 @@ size_t adjoint_bytes(int64_t n, int32_t d, int32_t k) {
     A.take<double>((size_t)mi * GT * 3);
     A.take<double>((size_t)n * d);
     A.take<double>((size_t)n * d);
+    A.take<float2>((size_t)n * d);
     A.take<double>(n);
     A.take<double>(n);
     A.take<int32_t>(n);
@@ -493,6 +551,7 @@ cudaError_t adjoint_launch(const void *X, int32_t dtype, int64_t n, int32_t d, c
     double *Op = Cp + mi * GT, *Sp = Op + mi * GT;
     double *gphi = A.take<double>((size_t)n * d);
     double *gom = A.take<double>((size_t)n * d);
+    float2 *Zd = A.take<float2>((size_t)n * d);
     double *rowom = A.take<double>(n);
     double *rowsig = A.take<double>(n);
     int32_t *fa = A.take<int32_t>(n);
@@ -543,7 +602,8 @@ cudaError_t adjoint_launch(const void *X, int32_t dtype, int64_t n, int32_t d, c
     if (nit > 0 &&
         (e = cudaMemcpyAsync(pitems, items.data(), sizeof(PairItem) * nit, cudaMemcpyHostToDevice, s)))
         return e;
-    const size_t gsm = sizeof(double) * (2 * GDC * GT + GT * (GT + 1));
+    static_assert(sizeof(float2) == sizeof(double), "pair tiles hold one 8-byte value per entry");
+    const size_t gsm = sizeof(float2) * (2 * GDC * GT + GT * (GT + 1));
     const unsigned gp = (unsigned)(nit < num_sms() ? (nit > 0 ? nit : 1) : num_sms());
     const unsigned gr = grid_for((na + nb) * d);
     static bool attr = false;
@@ -558,10 +618,11 @@ cudaError_t adjoint_launch(const void *X, int32_t dtype, int64_t n, int32_t d, c
         const double *Xd = (const double *)X;
         k_phi_grad<double><<<1, TPB, 0, ISO_S(s)>>>(Xd, scale, d, parent, elist, cnt + 3, sigma, gphi, sums);
         k_row_norms<<<g, TPB, 0, ISO_S(s)>>>(nullptr, Xd, scale, n, d, N2);
+        k_z_dw<double><<<grid_for(n * d), TPB, 0, ISO_S(s)>>>(Xd, scale, n, d, Zd);
         if (kev) record_event(kev[0], s);
         if (nit > 0)
             k_pair_grad<double><<<gp, TPB, gsm, ISO_S(s)>>>(Xd, scale, n, d, N2, fa, alist, blist, cnt, pitems, nit,
-                                                             sigma, Vp, Cp, Op, Sp);
+                                                             sigma, Zd, Vp, Cp, Op, Sp);
         if (kev) record_event(kev[1], s);
         k_pair_reduce<double><<<gr, TPB, 0, ISO_S(s)>>>(Xd, scale, n, d, alist, blist, cnt, tilesA * chunksA, chunksA,
                                                          chunksB, Vp, Cp, Op, Sp, gom, rowom, rowsig);
@@ -573,10 +634,11 @@ cudaError_t adjoint_launch(const void *X, int32_t dtype, int64_t n, int32_t d, c
         const float *Xf = (const float *)X;
         k_phi_grad<float><<<1, TPB, 0, ISO_S(s)>>>(Xf, scale, d, parent, elist, cnt + 3, sigma, gphi, sums);
         k_row_norms<<<g, TPB, 0, ISO_S(s)>>>(Xf, nullptr, scale, n, d, N2);
+        k_z_dw<float><<<grid_for(n * d), TPB, 0, ISO_S(s)>>>(Xf, scale, n, d, Zd);
         if (kev) record_event(kev[0], s);
         if (nit > 0)
             k_pair_grad<float><<<gp, TPB, gsm, ISO_S(s)>>>(Xf, scale, n, d, N2, fa, alist, blist, cnt, pitems, nit,
-                                                            sigma, Vp, Cp, Op, Sp);
+                                                            sigma, Zd, Vp, Cp, Op, Sp);
         if (kev) record_event(kev[1], s);
         k_pair_reduce<float><<<gr, TPB, 0, ISO_S(s)>>>(Xf, scale, n, d, alist, blist, cnt, tilesA * chunksA, chunksA,
                                                         chunksB, Vp, Cp, Op, Sp, gom, rowom, rowsig);
