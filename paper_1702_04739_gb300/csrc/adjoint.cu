@@ -157,8 +157,8 @@ __global__ void __launch_bounds__(TPB) k_phi_grad(const T *__restrict__ X, const
 // Each item writes its partial sums to its own slot; k_pair_reduce adds the
 // slots of a row in chunk order.
 constexpr int GT = 64;              // rows / columns per pair tile
-constexpr int GDC = 16;             // dimensions per shared-memory chunk
-constexpr int GVD = 128;            // dimensions of V per pass
+constexpr int GK = 128;             // dimensions per shared-memory block (and of V per pass)
+constexpr int GS = GT + 1;          // padded stride of the shared-memory blocks (bank-conflict free)
 constexpr int GC = 4096;            // columns per work item
 
 struct PairItem {
@@ -210,13 +210,22 @@ k_pair_grad(const T *__restrict__ X, const double *__restrict__ s, int64_t n, in
             double *__restrict__ Cp, double *__restrict__ Op, double *__restrict__ Sp) {
     extern __shared__ __align__(16) float2 gsm[];
     const double isg = 1.0 / sigma, isg2 = isg * isg;
-    float2 *Zr = gsm;                                  // [GDC][GT] double-word z of the rows
-    float2 *Zc = Zr + GDC * GT;                        // [GDC][GT] of the columns
-    float2 *Cm = Zc + GDC * GT;                        // [GT][GT + 1] double-word coefficients
+    float2 *Zr = gsm;                                  // [GK][GS] double-word z of the rows (dimension-major)
+    float2 *Zc = Zr + GK * GS;                         // [GK][GS] of the columns
+    float2 *Cm = Zc + GK * GS;                         // [GT][GS] double-word coefficients
     __shared__ int32_t ri[GT], ci[GT], rin[GT], cin[GT];
     __shared__ double rn[GT], cn[GT];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int32_t na = cnt[1], nb = cnt[2];
+    const float2 zero2 = make_float2(0.f, 0.f);
+    // dimensions [k0, k0 + GK) of the 64 listed points idx[] into Z (GS-strided rows of dims)
+    auto load_block = [&](float2 *Z, const int32_t *idx, int32_t k0) {
+        const int32_t kl = min(GK, d - k0);
+        for (int e = tid; e < GK * GT; e += TPB) {
+            const int c = e / GK, t = e % GK;
+            Z[t * GS + c] = (t < kl && idx[c] >= 0) ? Zd[(int64_t)idx[c] * d + k0 + t] : zero2;
+        }
+    };
     for (int64_t w = blockIdx.x; w < nitems; w += gridDim.x) {
         const PairItem it = items[w];
         const int32_t *rlist = it.group == 0 ? alist : blist;
@@ -230,16 +239,18 @@ k_pair_grad(const T *__restrict__ X, const double *__restrict__ s, int64_t n, in
             rin[tid] = ri[tid] >= 0 ? inA[ri[tid]] : 0;
             rn[tid] = ri[tid] >= 0 ? N2[ri[tid]] : 0.0;
         }
+        __syncthreads();
+        int32_t zr_k0 = -1;                            // chunk of dimensions held in Zr
         double csum[4] = {0, 0, 0, 0}, osum[4] = {0, 0, 0, 0}, ssum[4] = {0, 0, 0, 0};
-        for (int32_t v0 = 0; v0 < d; v0 += GVD) {
-            const int32_t vl = min(GVD, d - v0);
-            float Vh[4][GVD / GDC], Vl[4][GVD / GDC];
+        for (int32_t v0 = 0; v0 < d; v0 += GK) {
+            // thread (ty, tx): rows ty*4+i, dimensions v0 + hh*16 + tx
+            float Vh[4][GK / 16], Vl[4][GK / 16];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int c = 0; c < GVD / GDC; ++c) { Vh[i][c] = 0.f; Vl[i][c] = 0.f; }
+                for (int c = 0; c < GK / 16; ++c) { Vh[i][c] = 0.f; Vl[i][c] = 0.f; }
             for (int64_t c0 = q0; c0 < q1; c0 += GT) {
-                __syncthreads();
+                __syncthreads();                       // readers of ci, Zc and Cm of the last tile are done
                 if (tid < GT) {
                     const int64_t q = c0 + tid;
                     const int64_t j = q < q1 ? (it.group == 0 ? q : (int64_t)alist[q]) : -1;
@@ -247,47 +258,51 @@ k_pair_grad(const T *__restrict__ X, const double *__restrict__ s, int64_t n, in
                     cin[tid] = j >= 0 ? inA[j] : 0;
                     cn[tid] = j >= 0 ? N2[j] : 0.0;
                 }
-                // ---- dot products z_i . z_j, 4 x 4 per thread (double-word)
+                __syncthreads();
+                // ---- dot products z_i . z_j (double-word): thread (ty, tx) takes
+                //      rows ty*4+i and columns j*16+tx (conflict-free loads)
                 float gh[4][4], gl[4][4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
                     for (int j = 0; j < 4; ++j) { gh[i][j] = 0.f; gl[i][j] = 0.f; }
-                const float2 zero2 = make_float2(0.f, 0.f);
-                for (int32_t t0 = 0; t0 < d; t0 += GDC) {
+                int32_t zc_k0 = -1;
+                for (int32_t k0 = 0; k0 < d; k0 += GK) {
+                    if (k0 > 0) __syncthreads();
+                    if (zr_k0 != k0) load_block(Zr, ri, k0);
+                    load_block(Zc, ci, k0);
+                    zr_k0 = k0;
+                    zc_k0 = k0;
                     __syncthreads();
-                    for (int e = tid; e < GDC * GT; e += TPB) {
-                        const int t = e / GT, r = e % GT;
-                        const bool ok = t0 + t < d;
-                        Zr[e] = (ok && ri[r] >= 0) ? Zd[(int64_t)ri[r] * d + t0 + t] : zero2;
-                        Zc[e] = (ok && ci[r] >= 0) ? Zd[(int64_t)ci[r] * d + t0 + t] : zero2;
-                    }
-                    __syncthreads();
+                    const int32_t kl = min(GK, d - k0);
+                    for (int32_t t0 = 0; t0 < kl; t0 += 16) {
+                        const int32_t tl = min(16, kl - t0);
 #pragma unroll 4
-                    for (int t = 0; t < GDC; ++t) {
-                        float2 a[4], b[4];
+                        for (int t = t0; t < t0 + tl; ++t) {
+                            float2 a[4], b[4];
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) a[i] = Zr[t * GT + ty * 4 + i];
+                            for (int i = 0; i < 4; ++i) a[i] = Zr[t * GS + ty * 4 + i];
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) b[j] = Zc[t * GT + tx * 4 + j];
+                            for (int j = 0; j < 4; ++j) b[j] = Zc[t * GS + j * 16 + tx];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                                for (int j = 0; j < 4; ++j) dw_mac(a[i].x, a[i].y, b[j].x, b[j].y, gh[i][j], gl[i][j]);
+                        }
 #pragma unroll
                         for (int i = 0; i < 4; ++i)
 #pragma unroll
-                            for (int j = 0; j < 4; ++j) dw_mac(a[i].x, a[i].y, b[j].x, b[j].y, gh[i][j], gl[i][j]);
+                            for (int j = 0; j < 4; ++j) dw_norm(gh[i][j], gl[i][j]);
                     }
-#pragma unroll
-                    for (int i = 0; i < 4; ++i)
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) dw_norm(gh[i][j], gl[i][j]);
                 }
-                // ---- pair coefficients
+                // ---- pair coefficients (FP64)
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const int r = ty * 4 + i;
                     double cs = 0.0, os = 0.0, ss = 0.0;
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        const int c = tx * 4 + j;
+                        const int c = j * 16 + tx;
                         const int32_t gi = ri[r], gj = ci[c];
                         const int mult = rin[r] + cin[c];
                         double cc = 0.0;
@@ -304,8 +319,7 @@ k_pair_grad(const T *__restrict__ X, const double *__restrict__ s, int64_t n, in
                                 r2 = dd;
                             }
                             // r and 1/r from one reciprocal square root; 1/sigma
-                            // and 1/sigma^2 precomputed (no FP64 division, the
-                            // costliest part of a pair on the FP64 pipe)
+                            // and 1/sigma^2 precomputed (no FP64 division)
                             const double r2c = fmax(r2, 0.0);
                             const double irr = r2c > 0.0 ? rsqrt(r2c) : 0.0;
                             const double rr = r2c * irr;
@@ -316,7 +330,7 @@ k_pair_grad(const T *__restrict__ X, const double *__restrict__ s, int64_t n, in
                                 ss = ss + ww * rr * isg2;
                             }
                         }
-                        Cm[r * (GT + 1) + c] = dw_of(cc);
+                        Cm[r * GS + c] = dw_of(cc);
                         cs = cs + cc;
                     }
                     // rows' sums over this tile's 64 columns: the 16 threads of a row, in order
@@ -332,38 +346,37 @@ k_pair_grad(const T *__restrict__ X, const double *__restrict__ s, int64_t n, in
                         ssum[i] = ssum[i] + ss;
                     }
                 }
-                // ---- V[r][t] += sum_c C[r][c] z_c[t], t in [v0, v0 + vl)
-                for (int32_t h = 0; h < vl; h += GDC) {
+                // ---- V[r][t] += sum_c C[r][c] z_c[t], t in [v0, v0 + GK): the
+                //      columns' chunk v0 is in Zc unless d > GK moved past it
+                if (zc_k0 != v0) {
                     __syncthreads();
-                    for (int e = tid; e < GDC * GT; e += TPB) {
-                        const int t = e / GT, c = e % GT;
-                        Zc[e] = (h + t < vl && ci[c] >= 0) ? Zd[(int64_t)ci[c] * d + v0 + h + t] : make_float2(0.f, 0.f);
-                    }
-                    __syncthreads();
-                    const int hc = h / GDC;
-#pragma unroll
-                    for (int hh = 0; hh < GVD / GDC; ++hh) {
-                        if (hh != hc) continue;
-#pragma unroll 8
-                        for (int c = 0; c < GT; ++c) {
-                            const float2 zc = Zc[tx * GT + c];
-#pragma unroll
-                            for (int i = 0; i < 4; ++i) {
-                                const float2 cf = Cm[(ty * 4 + i) * (GT + 1) + c];
-                                dw_mac(cf.x, cf.y, zc.x, zc.y, Vh[i][hh], Vl[i][hh]);
-                            }
-                        }
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) dw_norm(Vh[i][hh], Vl[i][hh]);
-                    }
+                    load_block(Zc, ci, v0);
                 }
+                __syncthreads();                       // Cm (and Zc) complete
+#pragma unroll 2
+                for (int c = 0; c < GT; ++c) {
+                    float2 zc[GK / 16], cf[4];
+#pragma unroll
+                    for (int hh = 0; hh < GK / 16; ++hh) zc[hh] = Zc[(hh * 16 + tx) * GS + c];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) cf[i] = Cm[(ty * 4 + i) * GS + c];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int hh = 0; hh < GK / 16; ++hh)
+                            dw_mac(cf[i].x, cf[i].y, zc[hh].x, zc[hh].y, Vh[i][hh], Vl[i][hh]);
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int hh = 0; hh < GK / 16; ++hh) dw_norm(Vh[i][hh], Vl[i][hh]);
             }
             // partial V of this item: rows ty*4+i, dimension v0 + hh*16 + tx
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int hh = 0; hh < GVD / GDC; ++hh) {
-                    const int32_t t = v0 + hh * GDC + tx;
+                for (int hh = 0; hh < GK / 16; ++hh) {
+                    const int32_t t = v0 + hh * 16 + tx;
                     if (t < d) Vp[(w * GT + ty * 4 + i) * (int64_t)d + t] = __dadd_rn((double)Vh[i][hh], (double)Vl[i][hh]);
                 }
         }
@@ -602,8 +615,7 @@ cudaError_t adjoint_launch(const void *X, int32_t dtype, int64_t n, int32_t d, c
     if (nit > 0 &&
         (e = cudaMemcpyAsync(pitems, items.data(), sizeof(PairItem) * nit, cudaMemcpyHostToDevice, s)))
         return e;
-    static_assert(sizeof(float2) == sizeof(double), "pair tiles hold one 8-byte value per entry");
-    const size_t gsm = sizeof(float2) * (2 * GDC * GT + GT * (GT + 1));
+    const size_t gsm = sizeof(float2) * (2 * GK * GS + GT * GS);
     const unsigned gp = (unsigned)(nit < num_sms() ? (nit > 0 ? nit : 1) : num_sms());
     const unsigned gr = grid_for((na + nb) * d);
     static bool attr = false;
