@@ -689,8 +689,8 @@ def main_moons(args):
                "d2h_bytes_per_step": int(lh.numel() * 4 + gh.numel() * 8 + sh.numel() * 8)}
     # work of the pair kernel: |A*| n + (n - |A*|) |A*| ordered pairs, each a
     # d-long dot product and a d-long accumulation in double-word FP32 (12
-    # FP32-pipe instructions per step); the per-pair FP64 tail (rsqrt, exp)
-    # is not counted
+    # FP32-pipe instructions per step) and the pair's coefficient (norms,
+    # root, reciprocal, exp, products: ~115 double-word FP32 instructions)
     lab = out["labels"].cpu().numpy()
     par = out["parent"].cpu().numpy()
     phi = out["phi_par"].cpu().numpy()
@@ -702,7 +702,7 @@ def main_moons(args):
         ratios.append(phi[cross].sum() / om[inj].sum())
     a = int((lab == int(np.argmax(ratios))).sum())
     pairs = a * n + (n - a) * a
-    ops = pairs * (24.0 * d)
+    ops = pairs * (24.0 * d + 115.0)
     b_ms = statistics.mean(bwd)
     k_ms = statistics.mean(pair)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -715,11 +715,11 @@ def main_moons(args):
         "config": dict(cfg, l2="flushed by a 256 MiB write before every step (inside the timed region)"),
         "roofline": {"bound": "alu", "achieved": ops / (k_ms / 1000.0) / 1e12, "peak": alu_peak,
                      "unit": "TFLOP/s", "frac": ops / (k_ms / 1000.0) / 1e12 / alu_peak, "traffic": None,
-                     "kernel": "k_pair_grad (backward pair sums, double-word FP32 with an FP64 tail)",
-                     "note": f"{pairs} ordered pairs (|A*| = {a}) x 24 d FP32-pipe instructions (two d-long "
-                             f"double-word sums) over the kernel's CUDA-event time ({k_ms:.2f} ms of the "
-                             f"backward's {b_ms:.2f} ms); the per-pair FP64 sqrt/exp tail is not counted; peak = "
-                             f"{sms} SMs x {FP32_LANES_PER_SM} lanes x max SM clock ({src})"},
+                     "kernel": "k_pair_grad (backward pair sums, double-word FP32)",
+                     "note": f"{pairs} ordered pairs (|A*| = {a}) x (24 d + 115) FP32-pipe instructions (two "
+                             f"d-long double-word sums and the pair's coefficient) over the kernel's CUDA-event "
+                             f"time ({k_ms:.2f} ms of the backward's {b_ms:.2f} ms); peak = {sms} SMs x "
+                             f"{FP32_LANES_PER_SM} lanes x max SM clock ({src})"},
         "stages_ms": {"forward_ms": round(sum(times["fwd"][key] for key in ("validate_ms", "weights_ms", "mst_ms",
                                                                           "orient_ms", "search_ms", "labels_ms")), 3),
                       "backward_ms": round(b_ms, 3)},

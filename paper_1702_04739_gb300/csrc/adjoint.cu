@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "dwmath.cuh"
 
 namespace iso {
 cudaError_t exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, int32_t *tmp, cudaStream_t s);
@@ -145,17 +146,22 @@ __global__ void __launch_bounds__(TPB) k_phi_grad(const T *__restrict__ X, const
 // Omega's pair sums.  Work item = (row group, 64-row
 // tile of the group's list, chunk of GC columns): group 0 = rows of A*
 // against every point, group 1 = the other rows against A*.  Per 64 x 64
-// pair tile: squared distances from dot products, |z_i|^2 + |z_j|^2 -
-// 2 z_i.z_j (4 x 4 pairs per thread), with a direct FP64 recomputation
-// where that cancels (d2 < 2^-20 (|z_i|^2 + |z_j|^2)); the coefficients
-// (FP64: sqrt, exp) in shared memory; then V_i += sum_j c_ij z_j for 128
-// dimensions at a time (4 rows x 1 dimension per thread and 16-dimension
-// chunk).  The two d-long sums run in double-word FP32 on z's double-word
-// copy (exact products by FMA, TwoSum of the high parts, low parts summed
-// in FP32 and renormalised every 16 dimensions or 64 columns: relative
-// error ~ d 2^-48), where GB300's FP32 pipe has 64 times the FP64 rate.
-// Each item writes its partial sums to its own slot; k_pair_reduce adds the
-// slots of a row in chunk order.
+// pair tile (all of a point's first 128 dimensions in shared memory at
+// once): squared distances from dot products, |z_i|^2 + |z_j|^2 - 2 z_i.z_j
+// (4 x 4 pairs per thread), with a direct FP64 recomputation where that
+// cancels (d2 < 2^-20 (|z_i|^2 + |z_j|^2)); the coefficients
+// c_ij = -m w / (sigma r), w = exp(-r / sigma), in shared memory; then
+// V_i += sum_j c_ij z_j (4 rows x 8 dimensions per thread).  Everything
+// runs in double-word FP32, where GB300's FP32 pipe has 64 times the FP64
+// rate: the two d-long sums on z's double-word copy (exact products by FMA,
+// TwoSum of the high parts, low parts summed in FP32 and renormalised every
+// 16 dimensions or 64 columns: relative error ~ d 2^-48), the root and
+// reciprocal by one correction of their FP32 values, the exp by the
+// table-driven double-word exp of the omega sweep.  A pair whose r / sigma
+// exceeds 80 (past FP32's exponent range) takes the FP64 path; omega's own
+// sums (w and w r / sigma^2) are added in FP64.  Each item writes its
+// partial sums to its own slot; k_pair_reduce adds the slots of a row in
+// chunk order.
 constexpr int GT = 64;              // rows / columns per pair tile
 constexpr int GK = 128;             // dimensions per shared-memory block (and of V per pass)
 constexpr int GS = GT + 1;          // padded stride of the shared-memory blocks (bank-conflict free)
@@ -189,6 +195,14 @@ __device__ __forceinline__ float2 dw_of(double z) {
     const float h = __double2float_rn(z);
     return make_float2(h, __double2float_rn(__dsub_rn(z, (double)h)));
 }
+// (ah + al)(bh + bl) as a double-word (the lo.lo term dropped)
+__device__ __forceinline__ void dw_mul(float ah, float al, float bh, float bl, float &ph, float &pl) {
+    const float p = __fmul_rn(ah, bh);
+    float e = __fmaf_rn(ah, bh, -p);
+    e = __fmaf_rn(ah, bl, e);
+    e = __fmaf_rn(al, bh, e);
+    fast_two_sum(p, e, ph, pl);
+}
 
 // z = s (.) x of every point as double-words, once per call
 template <class T>
@@ -206,15 +220,18 @@ __global__ void __launch_bounds__(TPB, 1)
 k_pair_grad(const T *__restrict__ X, const double *__restrict__ s, int64_t n, int32_t d,
             const double *__restrict__ N2, const int32_t *__restrict__ inA, const int32_t *__restrict__ alist,
             const int32_t *__restrict__ blist, const int32_t *__restrict__ cnt, const PairItem *__restrict__ items,
-            int64_t nitems, double sigma, const float2 *__restrict__ Zd, double *__restrict__ Vp,
+            int64_t nitems, double sigma, const float2 *__restrict__ Zd, ExpTable tabv, double *__restrict__ Vp,
             double *__restrict__ Cp, double *__restrict__ Op, double *__restrict__ Sp) {
     extern __shared__ __align__(16) float2 gsm[];
     const double isg = 1.0 / sigma, isg2 = isg * isg;
+    const float2 isw = dw_of(isg);                     // 1/sigma as a double-word
+    __shared__ float2 tab[64];
+    if (threadIdx.x < 64) tab[threadIdx.x] = tabv.t[threadIdx.x];
     float2 *Zr = gsm;                                  // [GK][GS] double-word z of the rows (dimension-major)
     float2 *Zc = Zr + GK * GS;                         // [GK][GS] of the columns
     float2 *Cm = Zc + GK * GS;                         // [GT][GS] double-word coefficients
     __shared__ int32_t ri[GT], ci[GT], rin[GT], cin[GT];
-    __shared__ double rn[GT], cn[GT];
+    __shared__ float2 rn[GT], cn[GT];                  // |z|^2 as double-words
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int32_t na = cnt[1], nb = cnt[2];
     const float2 zero2 = make_float2(0.f, 0.f);
@@ -237,7 +254,7 @@ k_pair_grad(const T *__restrict__ X, const double *__restrict__ s, int64_t n, in
             const int64_t q = (int64_t)it.tile * GT + tid;
             ri[tid] = q < nr ? rlist[q] : -1;
             rin[tid] = ri[tid] >= 0 ? inA[ri[tid]] : 0;
-            rn[tid] = ri[tid] >= 0 ? N2[ri[tid]] : 0.0;
+            rn[tid] = ri[tid] >= 0 ? dw_of(N2[ri[tid]]) : zero2;
         }
         __syncthreads();
         int32_t zr_k0 = -1;                            // chunk of dimensions held in Zr
@@ -256,7 +273,7 @@ k_pair_grad(const T *__restrict__ X, const double *__restrict__ s, int64_t n, in
                     const int64_t j = q < q1 ? (it.group == 0 ? q : (int64_t)alist[q]) : -1;
                     ci[tid] = (int32_t)j;
                     cin[tid] = j >= 0 ? inA[j] : 0;
-                    cn[tid] = j >= 0 ? N2[j] : 0.0;
+                    cn[tid] = j >= 0 ? dw_of(N2[j]) : zero2;
                 }
                 __syncthreads();
                 // ---- dot products z_i . z_j (double-word): thread (ty, tx) takes
@@ -295,53 +312,85 @@ k_pair_grad(const T *__restrict__ X, const double *__restrict__ s, int64_t n, in
                             for (int j = 0; j < 4; ++j) dw_norm(gh[i][j], gl[i][j]);
                     }
                 }
-                // ---- pair coefficients (FP64)
+                // ---- pair coefficients c_ij = -m w / (sigma r) with w = exp(-r / sigma),
+                //      in double-word FP32; omega's sums (w, w r / sigma^2) in FP64
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const int r = ty * 4 + i;
-                    double cs = 0.0, os = 0.0, ss = 0.0;
+                    float csh = 0.f, csl = 0.f;
+                    double os = 0.0, ss = 0.0;
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         const int c = j * 16 + tx;
                         const int32_t gi = ri[r], gj = ci[c];
                         const int mult = rin[r] + cin[c];
-                        double cc = 0.0;
+                        float cch = 0.f, ccl = 0.f;
                         if (gi >= 0 && gj >= 0 && gi != gj && mult > 0) {
-                            const double nsum = rn[r] + cn[c];
-                            const double g = __dadd_rn((double)gh[i][j], (double)gl[i][j]);
-                            double r2 = __fma_rn(-2.0, g, nsum);
-                            if (r2 < nsum * 9.5367431640625e-07) {      // cancellation: direct differences
+                            float nh = rn[r].x, nl = rn[r].y;
+                            dw_add(nh, nl, cn[c].x, cn[c].y);              // |z_i|^2 + |z_j|^2
+                            float r2h = nh, r2l = nl;
+                            dw_add(r2h, r2l, -2.0f * gh[i][j], -2.0f * gl[i][j]);
+                            if (r2h < nh * 9.5367431640625e-07f) {      // cancellation: direct FP64 differences
                                 double dd = 0.0;
                                 for (int32_t t = 0; t < d; ++t) {
                                     const double df = __dsub_rn(zv(X, s, gi, t, d), zv(X, s, gj, t, d));
                                     dd = __fma_rn(df, df, dd);
                                 }
-                                r2 = dd;
+                                const float2 q = dw_of(dd);
+                                r2h = q.x;
+                                r2l = q.y;
                             }
-                            // r and 1/r from one reciprocal square root; 1/sigma
-                            // and 1/sigma^2 precomputed (no FP64 division)
-                            const double r2c = fmax(r2, 0.0);
-                            const double irr = r2c > 0.0 ? rsqrt(r2c) : 0.0;
-                            const double rr = r2c * irr;
-                            const double ww = exp(-rr * isg);
-                            if (rr > 0.0) cc = -(double)mult * ww * (isg * irr);
+                            if (!(r2h > 0.f)) { r2h = 0.f; r2l = 0.f; }
+                            // r by one correction of the FP32 root; 1/r likewise
+                            const float rh = __fsqrt_rn(r2h);
+                            float rl = 0.f, qh = 0.f, ql = 0.f;
+                            if (rh > 0.f) {
+                                rl = __fmul_rn(__fadd_rn(__fmaf_rn(-rh, rh, r2h), r2l), __frcp_rn(__fadd_rn(rh, rh)));
+                                qh = __frcp_rn(rh);
+                                float t = __fmaf_rn(-rh, qh, 1.0f);
+                                t = __fmaf_rn(-rl, qh, t);
+                                ql = __fmul_rn(t, qh);
+                            }
+                            float zh, zl;
+                            dw_mul(rh, rl, isw.x, isw.y, zh, zl);          // r / sigma
+                            double wwd;
+                            if (zh <= 80.0f) {
+                                float wh, wl, ah, al, bh, bl;
+                                dw_exp_neg(zh, zl, tab, wh, wl);
+                                dw_mul(isw.x, isw.y, qh, ql, ah, al);     // 1 / (sigma r)
+                                dw_mul(wh, wl, ah, al, bh, bl);
+                                if (rh > 0.f) {
+                                    cch = -(float)mult * bh;                // mult is 1 or 2: exact
+                                    ccl = -(float)mult * bl;
+                                }
+                                wwd = __dadd_rn((double)wh, (double)wl);
+                            } else {
+                                // past FP32's exponent range: the pair in FP64
+                                const double rd = __dadd_rn((double)rh, (double)rl);
+                                wwd = exp(-rd * isg);
+                                const float2 q = dw_of(-(double)mult * wwd * (isg / rd));
+                                cch = q.x;
+                                ccl = q.y;
+                            }
                             if (rin[r] && v0 == 0) {
-                                os = os + ww;
-                                ss = ss + ww * rr * isg2;
+                                os = os + wwd;
+                                ss = ss + wwd * __dadd_rn((double)rh, (double)rl) * isg2;
                             }
                         }
-                        Cm[r * GS + c] = dw_of(cc);
-                        cs = cs + cc;
+                        Cm[r * GS + c] = make_float2(cch, ccl);
+                        dw_add(csh, csl, cch, ccl);
                     }
                     // rows' sums over this tile's 64 columns: the 16 threads of a row, in order
 #pragma unroll
                     for (int o = 8; o > 0; o >>= 1) {
-                        cs = cs + __shfl_down_sync(0xffffffffu, cs, o, 16);
+                        const float oh = __shfl_down_sync(0xffffffffu, csh, o, 16);
+                        const float ol = __shfl_down_sync(0xffffffffu, csl, o, 16);
+                        dw_add(csh, csl, oh, ol);
                         os = os + __shfl_down_sync(0xffffffffu, os, o, 16);
                         ss = ss + __shfl_down_sync(0xffffffffu, ss, o, 16);
                     }
                     if (v0 == 0) {
-                        csum[i] = csum[i] + cs;
+                        csum[i] = csum[i] + __dadd_rn((double)csh, (double)csl);
                         osum[i] = osum[i] + os;
                         ssum[i] = ssum[i] + ss;
                     }
@@ -616,6 +665,7 @@ cudaError_t adjoint_launch(const void *X, int32_t dtype, int64_t n, int32_t d, c
         (e = cudaMemcpyAsync(pitems, items.data(), sizeof(PairItem) * nit, cudaMemcpyHostToDevice, s)))
         return e;
     const size_t gsm = sizeof(float2) * (2 * GK * GS + GT * GS);
+    static const ExpTable tab = make_exp_table();
     const unsigned gp = (unsigned)(nit < num_sms() ? (nit > 0 ? nit : 1) : num_sms());
     const unsigned gr = grid_for((na + nb) * d);
     static bool attr = false;
@@ -634,7 +684,7 @@ cudaError_t adjoint_launch(const void *X, int32_t dtype, int64_t n, int32_t d, c
         if (kev) record_event(kev[0], s);
         if (nit > 0)
             k_pair_grad<double><<<gp, TPB, gsm, ISO_S(s)>>>(Xd, scale, n, d, N2, fa, alist, blist, cnt, pitems, nit,
-                                                             sigma, Zd, Vp, Cp, Op, Sp);
+                                                             sigma, Zd, tab, Vp, Cp, Op, Sp);
         if (kev) record_event(kev[1], s);
         k_pair_reduce<double><<<gr, TPB, 0, ISO_S(s)>>>(Xd, scale, n, d, alist, blist, cnt, tilesA * chunksA, chunksA,
                                                          chunksB, Vp, Cp, Op, Sp, gom, rowom, rowsig);
@@ -650,7 +700,7 @@ cudaError_t adjoint_launch(const void *X, int32_t dtype, int64_t n, int32_t d, c
         if (kev) record_event(kev[0], s);
         if (nit > 0)
             k_pair_grad<float><<<gp, TPB, gsm, ISO_S(s)>>>(Xf, scale, n, d, N2, fa, alist, blist, cnt, pitems, nit,
-                                                            sigma, Zd, Vp, Cp, Op, Sp);
+                                                            sigma, Zd, tab, Vp, Cp, Op, Sp);
         if (kev) record_event(kev[1], s);
         k_pair_reduce<float><<<gr, TPB, 0, ISO_S(s)>>>(Xf, scale, n, d, alist, blist, cnt, tilesA * chunksA, chunksA,
                                                         chunksB, Vp, Cp, Op, Sp, gom, rowom, rowsig);
