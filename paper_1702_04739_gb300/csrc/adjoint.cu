@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(TPB) k_phi_grad(const T *__restrict__ X, const
 // (4 x 4 pairs per thread), with a direct FP64 recomputation where that
 // cancels (d2 < 2^-20 (|z_i|^2 + |z_j|^2)); the coefficients
 // c_ij = -m w / (sigma r), w = exp(-r / sigma), in shared memory; then
-// V_i += sum_j c_ij z_j (4 rows x 8 dimensions per thread).  Everything
+// V_i += sum_j c_ij z_j (512 threads, 2 rows x 8 dimensions each).  Everything
 // runs in double-word FP32, where GB300's FP32 pipe has 64 times the FP64
 // rate: the two d-long sums on z's double-word copy (exact products by FMA,
 // TwoSum of the high parts, low parts summed in FP32 and renormalised every
@@ -165,6 +165,8 @@ __global__ void __launch_bounds__(TPB) k_phi_grad(const T *__restrict__ X, const
 constexpr int GT = 64;              // rows / columns per pair tile
 constexpr int GK = 128;             // dimensions per shared-memory block (and of V per pass)
 constexpr int GS = GT + 1;          // padded stride of the shared-memory blocks (bank-conflict free)
+constexpr int GP = 512;             // threads of the pair kernel: 32 x 16
+constexpr int GR = GT / (GP / 16);  // rows per thread (2)
 constexpr int GC = 4096;            // columns per work item
 
 struct PairItem {
@@ -216,7 +218,7 @@ __global__ void k_z_dw(const T *__restrict__ X, const double *__restrict__ s, in
 }
 
 template <class T>
-__global__ void __launch_bounds__(TPB, 1)
+__global__ void __launch_bounds__(GP, 1)
 k_pair_grad(const T *__restrict__ X, const double *__restrict__ s, int64_t n, int32_t d,
             const double *__restrict__ N2, const int32_t *__restrict__ inA, const int32_t *__restrict__ alist,
             const int32_t *__restrict__ blist, const int32_t *__restrict__ cnt, const PairItem *__restrict__ items,
@@ -238,7 +240,7 @@ k_pair_grad(const T *__restrict__ X, const double *__restrict__ s, int64_t n, in
     // dimensions [k0, k0 + GK) of the 64 listed points idx[] into Z (GS-strided rows of dims)
     auto load_block = [&](float2 *Z, const int32_t *idx, int32_t k0) {
         const int32_t kl = min(GK, d - k0);
-        for (int e = tid; e < GK * GT; e += TPB) {
+        for (int e = tid; e < GK * GT; e += GP) {
             const int c = e / GK, t = e % GK;
             Z[t * GS + c] = (t < kl && idx[c] >= 0) ? Zd[(int64_t)idx[c] * d + k0 + t] : zero2;
         }
@@ -258,12 +260,14 @@ k_pair_grad(const T *__restrict__ X, const double *__restrict__ s, int64_t n, in
         }
         __syncthreads();
         int32_t zr_k0 = -1;                            // chunk of dimensions held in Zr
-        double csum[4] = {0, 0, 0, 0}, osum[4] = {0, 0, 0, 0}, ssum[4] = {0, 0, 0, 0};
-        for (int32_t v0 = 0; v0 < d; v0 += GK) {
-            // thread (ty, tx): rows ty*4+i, dimensions v0 + hh*16 + tx
-            float Vh[4][GK / 16], Vl[4][GK / 16];
+        double csum[GR], osum[GR], ssum[GR];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < GR; ++i) { csum[i] = 0.0; osum[i] = 0.0; ssum[i] = 0.0; }
+        for (int32_t v0 = 0; v0 < d; v0 += GK) {
+            // thread (ty, tx): rows ty*GR+i, dimensions v0 + hh*16 + tx
+            float Vh[GR][GK / 16], Vl[GR][GK / 16];
+#pragma unroll
+            for (int i = 0; i < GR; ++i)
 #pragma unroll
                 for (int c = 0; c < GK / 16; ++c) { Vh[i][c] = 0.f; Vl[i][c] = 0.f; }
             for (int64_t c0 = q0; c0 < q1; c0 += GT) {
@@ -277,10 +281,10 @@ k_pair_grad(const T *__restrict__ X, const double *__restrict__ s, int64_t n, in
                 }
                 __syncthreads();
                 // ---- dot products z_i . z_j (double-word): thread (ty, tx) takes
-                //      rows ty*4+i and columns j*16+tx (conflict-free loads)
-                float gh[4][4], gl[4][4];
+                //      rows ty*GR+i and columns j*16+tx (conflict-free loads)
+                float gh[GR][4], gl[GR][4];
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < GR; ++i)
 #pragma unroll
                     for (int j = 0; j < 4; ++j) { gh[i][j] = 0.f; gl[i][j] = 0.f; }
                 int32_t zc_k0 = -1;
@@ -296,18 +300,18 @@ k_pair_grad(const T *__restrict__ X, const double *__restrict__ s, int64_t n, in
                         const int32_t tl = min(16, kl - t0);
 #pragma unroll 4
                         for (int t = t0; t < t0 + tl; ++t) {
-                            float2 a[4], b[4];
+                            float2 a[GR], b[4];
 #pragma unroll
-                            for (int i = 0; i < 4; ++i) a[i] = Zr[t * GS + ty * 4 + i];
+                            for (int i = 0; i < GR; ++i) a[i] = Zr[t * GS + ty * GR + i];
 #pragma unroll
                             for (int j = 0; j < 4; ++j) b[j] = Zc[t * GS + j * 16 + tx];
 #pragma unroll
-                            for (int i = 0; i < 4; ++i)
+                            for (int i = 0; i < GR; ++i)
 #pragma unroll
                                 for (int j = 0; j < 4; ++j) dw_mac(a[i].x, a[i].y, b[j].x, b[j].y, gh[i][j], gl[i][j]);
                         }
 #pragma unroll
-                        for (int i = 0; i < 4; ++i)
+                        for (int i = 0; i < GR; ++i)
 #pragma unroll
                             for (int j = 0; j < 4; ++j) dw_norm(gh[i][j], gl[i][j]);
                     }
@@ -315,8 +319,8 @@ k_pair_grad(const T *__restrict__ X, const double *__restrict__ s, int64_t n, in
                 // ---- pair coefficients c_ij = -m w / (sigma r) with w = exp(-r / sigma),
                 //      in double-word FP32; omega's sums (w, w r / sigma^2) in FP64
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int r = ty * 4 + i;
+                for (int i = 0; i < GR; ++i) {
+                    const int r = ty * GR + i;
                     float csh = 0.f, csl = 0.f;
                     double os = 0.0, ss = 0.0;
 #pragma unroll
@@ -404,35 +408,35 @@ k_pair_grad(const T *__restrict__ X, const double *__restrict__ s, int64_t n, in
                 __syncthreads();                       // Cm (and Zc) complete
 #pragma unroll 2
                 for (int c = 0; c < GT; ++c) {
-                    float2 zc[GK / 16], cf[4];
+                    float2 zc[GK / 16], cf[GR];
 #pragma unroll
                     for (int hh = 0; hh < GK / 16; ++hh) zc[hh] = Zc[(hh * 16 + tx) * GS + c];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) cf[i] = Cm[(ty * 4 + i) * GS + c];
+                    for (int i = 0; i < GR; ++i) cf[i] = Cm[(ty * GR + i) * GS + c];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
+                    for (int i = 0; i < GR; ++i)
 #pragma unroll
                         for (int hh = 0; hh < GK / 16; ++hh)
                             dw_mac(cf[i].x, cf[i].y, zc[hh].x, zc[hh].y, Vh[i][hh], Vl[i][hh]);
                 }
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < GR; ++i)
 #pragma unroll
                     for (int hh = 0; hh < GK / 16; ++hh) dw_norm(Vh[i][hh], Vl[i][hh]);
             }
-            // partial V of this item: rows ty*4+i, dimension v0 + hh*16 + tx
+            // partial V of this item: rows ty*GR+i, dimension v0 + hh*16 + tx
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < GR; ++i)
 #pragma unroll
                 for (int hh = 0; hh < GK / 16; ++hh) {
                     const int32_t t = v0 + hh * 16 + tx;
-                    if (t < d) Vp[(w * GT + ty * 4 + i) * (int64_t)d + t] = __dadd_rn((double)Vh[i][hh], (double)Vl[i][hh]);
+                    if (t < d) Vp[(w * GT + ty * GR + i) * (int64_t)d + t] = __dadd_rn((double)Vh[i][hh], (double)Vl[i][hh]);
                 }
         }
         if (tx == 0) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int r = ty * 4 + i;
+            for (int i = 0; i < GR; ++i) {
+                const int r = ty * GR + i;
                 Cp[w * GT + r] = csum[i];
                 Op[w * GT + r] = osum[i];
                 Sp[w * GT + r] = ssum[i];
@@ -683,7 +687,7 @@ cudaError_t adjoint_launch(const void *X, int32_t dtype, int64_t n, int32_t d, c
         k_z_dw<double><<<grid_for(n * d), TPB, 0, ISO_S(s)>>>(Xd, scale, n, d, Zd);
         if (kev) record_event(kev[0], s);
         if (nit > 0)
-            k_pair_grad<double><<<gp, TPB, gsm, ISO_S(s)>>>(Xd, scale, n, d, N2, fa, alist, blist, cnt, pitems, nit,
+            k_pair_grad<double><<<gp, GP, gsm, ISO_S(s)>>>(Xd, scale, n, d, N2, fa, alist, blist, cnt, pitems, nit,
                                                              sigma, Zd, tab, Vp, Cp, Op, Sp);
         if (kev) record_event(kev[1], s);
         k_pair_reduce<double><<<gr, TPB, 0, ISO_S(s)>>>(Xd, scale, n, d, alist, blist, cnt, tilesA * chunksA, chunksA,
@@ -699,7 +703,7 @@ cudaError_t adjoint_launch(const void *X, int32_t dtype, int64_t n, int32_t d, c
         k_z_dw<float><<<grid_for(n * d), TPB, 0, ISO_S(s)>>>(Xf, scale, n, d, Zd);
         if (kev) record_event(kev[0], s);
         if (nit > 0)
-            k_pair_grad<float><<<gp, TPB, gsm, ISO_S(s)>>>(Xf, scale, n, d, N2, fa, alist, blist, cnt, pitems, nit,
+            k_pair_grad<float><<<gp, GP, gsm, ISO_S(s)>>>(Xf, scale, n, d, N2, fa, alist, blist, cnt, pitems, nit,
                                                             sigma, Zd, tab, Vp, Cp, Op, Sp);
         if (kev) record_event(kev[1], s);
         k_pair_reduce<float><<<gr, TPB, 0, ISO_S(s)>>>(Xf, scale, n, d, alist, blist, cnt, tilesA * chunksA, chunksA,
