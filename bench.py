@@ -196,6 +196,9 @@ def main():
                     help="points of the same generator (profiling of a smaller case); default: the full 100,000")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, SPARSE, BATCHED, MOONS])
     ap.add_argument("--nsets", type=int, default=0, help="batched: fewer sets of the same recipe (profiling)")
+    ap.add_argument("--sweep-variant", type=int, default=-1,
+                    help="force the MST sweep's tile variant 0..3 (profiling: a profiler distorts the autotuner's "
+                         "trial timings); -1 = the library's own choice")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         args.warmup = 3
@@ -217,6 +220,7 @@ def main():
     import torch
     from paper_1702_04739_gb300 import isoclust
     torch.cuda.set_device(local_rank)
+    isoclust.set_sweep_variant(args.sweep_variant)
     dev = torch.device("cuda", local_rank)
     pg = None
     if world > 1:
@@ -440,6 +444,7 @@ def main_batched(args):
     import torch
     from paper_1702_04739_gb300 import isoclust
     torch.cuda.set_device(local_rank)
+    isoclust.set_sweep_variant(args.sweep_variant)
     dev = torch.device("cuda", local_rank)
     pg = None
     if world > 1:
@@ -614,6 +619,7 @@ def main_moons(args):
     import torch
     from paper_1702_04739_gb300 import isoclust
     torch.cuda.set_device(local_rank)
+    isoclust.set_sweep_variant(args.sweep_variant)
     dev = torch.device("cuda", local_rank)
     Xd = torch.from_numpy(X).to(dev)
     sd = torch.ones(d, dtype=torch.float64, device=dev)
@@ -724,6 +730,7 @@ def main_moons(args):
                                                                           "orient_ms", "search_ms", "labels_ms")), 3),
                       "backward_ms": round(b_ms, 3)},
         "gpu_launches": int(launches), "clocks": clk, "e2e": e2e,
+        "mst_sweep_variant": isoclust.last_sweep_variant(),
     }
     if rank == 0 and not args.no_cpu_baseline:
         v, t, cores, ns = _moons_cpu(X, k, sigma)

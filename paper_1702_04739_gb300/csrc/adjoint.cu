@@ -540,20 +540,44 @@ __global__ void k_grad_out(const T *__restrict__ X, const double *__restrict__ s
     }
 }
 
+// d i_k / d scale_t = g / Omega sum_i (gphi_it - R gom_it) x_it: rows in
+// GS_CHUNKS chunks (block (t-group, chunk), 32 dimensions x 8 row lanes,
+// lanes added in order), then the chunks added in order by k_grad_scale.
+constexpr int GS_CHUNKS = 64;
 template <class T>
-__global__ void k_grad_scale(const T *__restrict__ X, const double *__restrict__ s, int64_t n, int32_t d,
-                             const double *__restrict__ gphi, const double *__restrict__ gom,
-                             const double *__restrict__ phi2, const double *__restrict__ om2, double g,
-                             double *__restrict__ dscale, double *__restrict__ dsigma, double *__restrict__ ik) {
+__global__ void __launch_bounds__(256) k_grad_scale_part(const T *__restrict__ X, int64_t n, int32_t d,
+                                                         const double *__restrict__ gphi,
+                                                         const double *__restrict__ gom,
+                                                         const double *__restrict__ phi2,
+                                                         const double *__restrict__ om2, double *__restrict__ part) {
+    __shared__ double red[8][33];
+    const double R = phi2[0] / om2[0];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int32_t t = blockIdx.x * 32 + tx;
+    const int64_t per = (n + GS_CHUNKS - 1) / GS_CHUNKS;
+    const int64_t i0 = (int64_t)blockIdx.y * per, i1 = min(n, i0 + per);
+    double acc = 0.0;
+    if (t < d)
+        for (int64_t i = i0 + ty; i < i1; i += 8)
+            acc = __fma_rn(__fma_rn(-R, gom[i * d + t], gphi[i * d + t]), (double)X[i * d + t], acc);
+    red[ty][tx] = acc;
+    __syncthreads();
+    if (ty == 0 && t < d) {
+        double sum = 0.0;
+        for (int q = 0; q < 8; ++q) sum = sum + red[q][tx];
+        part[(int64_t)blockIdx.y * d + t] = sum;
+    }
+}
+
+__global__ void k_grad_scale(int32_t d, const double *__restrict__ part, const double *__restrict__ phi2,
+                             const double *__restrict__ om2, double g, double *__restrict__ dscale,
+                             double *__restrict__ dsigma, double *__restrict__ ik) {
     const double Omega = om2[0], R = phi2[0] / Omega;
     const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < d) {
         double acc = 0.0;
-        for (int64_t i = 0; i < n; ++i) {
-            const double gz = (gphi[i * d + t] - R * gom[i * d + t]) / Omega;
-            acc = __fma_rn(gz, (double)X[i * d + t], acc);
-        }
-        dscale[t] = g * acc;
+        for (int c = 0; c < GS_CHUNKS; ++c) acc = acc + part[(int64_t)c * d + t];
+        dscale[t] = g * acc / Omega;
     }
     if (t == 0) {
         dsigma[0] = g * (phi2[1] - R * om2[1]) / Omega;
@@ -600,6 +624,7 @@ size_t adjoint_bytes(int64_t n, int32_t d, int32_t k) {
     A.take<double>(k);
     A.take<double>(4);
     A.take<int32_t>(8);
+    A.take<double>((size_t)GS_CHUNKS * d);
     return A.off;
 }
 
@@ -634,6 +659,7 @@ cudaError_t adjoint_launch(const void *X, int32_t dtype, int64_t n, int32_t d, c
     double *omk = A.take<double>(k);
     double *sums = A.take<double>(4);      // Phi, Phi_sigma, Omega, Omega_sigma
     int32_t *cnt = A.take<int32_t>(8);     // jstar, |A*|, |rest|, |boundary|
+    double *gpart = A.take<double>((size_t)GS_CHUNKS * d);
     if (A.overflow) return cudaErrorInvalidValue;
     cudaError_t e;
     if ((e = cudaMemsetAsync(gphi, 0, sizeof(double) * n * d, s))) return e;
@@ -694,8 +720,10 @@ cudaError_t adjoint_launch(const void *X, int32_t dtype, int64_t n, int32_t d, c
                                                          chunksB, Vp, Cp, Op, Sp, gom, rowom, rowsig);
         k_omega_total<<<1, TPB, 0, ISO_S(s)>>>(alist, cnt + 1, rowom, rowsig, sums + 2);
         k_grad_out<double><<<grid_for(n * d), TPB, 0, ISO_S(s)>>>(Xd, scale, n, d, gphi, gom, sums, sums + 2, grad, dX);
-        k_grad_scale<double><<<(unsigned)ceil_div(d, 128), 128, 0, ISO_S(s)>>>(Xd, scale, n, d, gphi, gom, sums,
-                                                                               sums + 2, grad, dscale, dsigma, ik);
+        k_grad_scale_part<double><<<dim3((unsigned)ceil_div(d, 32), GS_CHUNKS), 256, 0, ISO_S(s)>>>(
+            Xd, n, d, gphi, gom, sums, sums + 2, gpart);
+        k_grad_scale<<<(unsigned)ceil_div(d, 128), 128, 0, ISO_S(s)>>>(d, gpart, sums, sums + 2, grad, dscale, dsigma,
+                                                                      ik);
     } else {
         const float *Xf = (const float *)X;
         k_phi_grad<float><<<1, TPB, 0, ISO_S(s)>>>(Xf, scale, d, parent, elist, cnt + 3, sigma, gphi, sums);
@@ -710,8 +738,10 @@ cudaError_t adjoint_launch(const void *X, int32_t dtype, int64_t n, int32_t d, c
                                                         chunksB, Vp, Cp, Op, Sp, gom, rowom, rowsig);
         k_omega_total<<<1, TPB, 0, ISO_S(s)>>>(alist, cnt + 1, rowom, rowsig, sums + 2);
         k_grad_out<float><<<grid_for(n * d), TPB, 0, ISO_S(s)>>>(Xf, scale, n, d, gphi, gom, sums, sums + 2, grad, dX);
-        k_grad_scale<float><<<(unsigned)ceil_div(d, 128), 128, 0, ISO_S(s)>>>(Xf, scale, n, d, gphi, gom, sums,
-                                                                              sums + 2, grad, dscale, dsigma, ik);
+        k_grad_scale_part<float><<<dim3((unsigned)ceil_div(d, 32), GS_CHUNKS), 256, 0, ISO_S(s)>>>(
+            Xf, n, d, gphi, gom, sums, sums + 2, gpart);
+        k_grad_scale<<<(unsigned)ceil_div(d, 128), 128, 0, ISO_S(s)>>>(d, gpart, sums, sums + 2, grad, dscale, dsigma,
+                                                                      ik);
     }
     return cudaGetLastError();
 }
