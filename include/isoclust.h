@@ -294,7 +294,9 @@ isoclust_status isoclust_scale_features(const void *X, int64_t n, int32_t d, int
  * tree and the subpartition of a forward call on z = scale (.) x, held fixed
  * (eq. phi, eq. omega; the cost of Section 2.1).  A* is the label of the
  * largest ratio phi(dA_j) / omega(A_j), picked from the forward's phi_par /
- * omega; everything else is recomputed in FP64 from X, scale and sigma:
+ * omega; everything else is recomputed from X, scale and sigma (results in
+ * FP64; Omega's pair sums in double-word FP32, relative error ~ d 2^-48,
+ * with FP64 past FP32's exponent range):
  *   i_k = Phi / Omega,  Phi = sum of phi over the tree edges with one end in
  *   A*,  Omega = sum over A* of eq. omega,  dR = (dPhi - i_k dOmega) / Omega.
  *   X        n x d points (device, F32 or F64) before scaling.
@@ -337,7 +339,7 @@ void isoclust_last_omega_tiles(int64_t *tiles3);
 /* Device time (milliseconds, CUDA events on the call's stream around its
  * launch) of the dominant pair kernel of the last call on this host thread:
  * the symmetric omega kernel after isoclust_cluster / _detail / _batched (0
- * when it did not run), the FP64 pair-sum kernel of dOmega after
+ * when it did not run), the pair-sum kernel of dOmega after
  * isoclust_ik_backward. */
 double isoclust_last_omega_kernel_ms(void);
 
