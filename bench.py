@@ -319,9 +319,10 @@ def main():
     # FP32 screen of one pair (both directions if sym); none when the tensor
     # cores screened the tile pairs (sym == 2)
     screen_ops = 0.0 if sym == 2 else 2.0 * d + (12.0 if sym else 8.0)
-    # d2 (21/dim), then sqrt and one double-word exp per pair: accumulated
-    # in one direction (ordered sweep) or both (symmetric sweep)
-    dw_ops = 21.0 * d + (95.0 if sym else 75.0)
+    # d2 (18.75/dim in the symmetric sweep: renormalised every 4 dimensions;
+    # 21/dim in the ordered one), then sqrt and one double-word exp per pair,
+    # accumulated in one direction (ordered sweep) or both (symmetric sweep)
+    dw_ops = (18.75 * d + 95.0) if sym else (21.0 * d + 75.0)
     work = tiles * 4096.0 * screen_ops + tiles_dw * 4096.0 * dw_ops
     achieved = work / (w_ms / 1000.0) / 1e12
     # MST stage: tensor-core work and the BF16 + FP64-recheck path against the FP32 SIMT path
@@ -528,7 +529,7 @@ def main_batched(args):
     tiles, tiles_dw = prof[-1]["omega_tiles"], prof[-1]["omega_tiles_dw"]
     # independent sets: the tile bound is the only screen (no FP32 pair screen
     # runs), so only the double-word pass counts
-    dw_ops = 21.0 * d + 95.0
+    dw_ops = 18.75 * d + 95.0
     work = tiles_dw * 4096.0 * dw_ops
     achieved = work / (w_ms / 1000.0) / 1e12
     sizes = np.diff(offs)

@@ -520,6 +520,10 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
             }
             __syncthreads();
             const int tl = min(WDC, d - t0);
+            // S takes each square's high part by TwoSum; the rounding errors
+            // and the squares' low parts gather in E, renormalised every 4
+            // dimensions (E stays below 2^-21 of S between renormalisations)
+#pragma unroll 4
             for (int t = 0; t < tl; ++t) {
                 float4 a4 = *reinterpret_cast<const float4 *>(&As[t][ty * 4]);
                 float4 b4 = *reinterpret_cast<const float4 *>(&Bs[t][tx * 4]);
@@ -536,10 +540,20 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
                         q2 = __fmaf_rn(__fadd_rn(s1, s1), e1, q2);
                         float hs, he;
                         two_sum(S[i][j], p, hs, he);
-                        he = __fadd_rn(he, __fadd_rn(E[i][j], q2));
-                        fast_two_sum(hs, he, S[i][j], E[i][j]);
+                        S[i][j] = hs;
+                        E[i][j] = __fadd_rn(E[i][j], __fadd_rn(he, q2));
                     }
+                if ((t & 3) == 3) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) fast_two_sum(S[i][j], E[i][j], S[i][j], E[i][j]);
+                }
             }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) fast_two_sum(S[i][j], E[i][j], S[i][j], E[i][j]);
         }
         float rh[4] = {0.f, 0.f, 0.f, 0.f}, rl[4] = {0.f, 0.f, 0.f, 0.f};
         float ch[4] = {0.f, 0.f, 0.f, 0.f}, cl[4] = {0.f, 0.f, 0.f, 0.f};
