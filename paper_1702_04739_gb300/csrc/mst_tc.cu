@@ -738,7 +738,8 @@ __device__ __forceinline__ void recheck_row(int64_t r, int lane, const float *__
                                             float add32, int32_t *__restrict__ nsurv, int32_t *__restrict__ surv,
                                             int32_t *__restrict__ rowj, int32_t *__restrict__ ovf,
                                             const int32_t *__restrict__ set_of, const int32_t *__restrict__ setcnt,
-                                            int32_t *counters) {
+                                            int32_t *counters, float *__restrict__ wv_s, float *__restrict__ bv_s,
+                                            int32_t *__restrict__ bj_s) {
     if (lane == 0) nsurv[r] = 0;           // every row, padding included: k_exact_tc reads them all
     const int64_t i = perm[r];
     if (i < 0) return;                     // padding row
@@ -769,32 +770,59 @@ __device__ __forceinline__ void recheck_row(int64_t r, int lane, const float *__
     for (int o = 16; o > 0; o >>= 1) U = fminf(U, __shfl_xor_sync(0xffffffffu, U, o));
     float bv[TC_TOPK];
     int32_t bj[TC_TOPK];
+    if constexpr (EPL == 1) {
+        // one entry per lane: its rank in the order (value, lane) - the
+        // order of repeated arg-mins - from all 32 values in shared memory;
+        // the 8 first scatter themselves, every lane reads them back
+        __syncwarp();
+        wv_s[lane] = ev[0];
+        __syncwarp();
+        int rk0 = 0, rk1 = 0;
 #pragma unroll
-    for (int k = 0; k < TC_TOPK; ++k) {
-        float mv = ev[0];
-        int ms = 0;
-#pragma unroll
-        for (int q = 1; q < EPL; ++q)
-            if (ev[q] < mv) { mv = ev[q]; ms = q; }
-        float wv = mv;
-        int wl = lane;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ov = __shfl_xor_sync(0xffffffffu, wv, o);
-            const int ol = __shfl_xor_sync(0xffffffffu, wl, o);
-            if (ov < wv || (ov == wv && ol < wl)) { wv = ov; wl = ol; }
+        for (int q = 0; q < 32; q += 2) {
+            const float w0 = wv_s[q], w1 = wv_s[q + 1];
+            rk0 += (w0 < ev[0] || (w0 == ev[0] && q < lane)) ? 1 : 0;
+            rk1 += (w1 < ev[0] || (w1 == ev[0] && q + 1 < lane)) ? 1 : 0;
         }
-        int32_t wj = -1;
-#pragma unroll
-        for (int q = 0; q < EPL; ++q) wj = (ms == q) ? ej[q] : wj;
-        wj = __shfl_sync(0xffffffffu, wj, wl);
-        if (lane == wl) {
-#pragma unroll
-            for (int q = 0; q < EPL; ++q)
-                if (ms == q) ev[q] = INFINITY;
+        const int rk = rk0 + rk1;
+        if (rk < TC_TOPK) {
+            bv_s[rk] = ev[0];
+            bj_s[rk] = ej[0];
         }
-        bv[k] = wv;
-        bj[k] = (wv < INFINITY) ? wj : -1;
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < TC_TOPK; ++k) {
+            bv[k] = bv_s[k];
+            bj[k] = bv[k] < INFINITY ? bj_s[k] : -1;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < TC_TOPK; ++k) {
+            float mv = ev[0];
+            int ms = 0;
+#pragma unroll
+            for (int q = 1; q < EPL; ++q)
+                if (ev[q] < mv) { mv = ev[q]; ms = q; }
+            float wv = mv;
+            int wl = lane;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ov = __shfl_xor_sync(0xffffffffu, wv, o);
+                const int ol = __shfl_xor_sync(0xffffffffu, wl, o);
+                if (ov < wv || (ov == wv && ol < wl)) { wv = ov; wl = ol; }
+            }
+            int32_t wj = -1;
+#pragma unroll
+            for (int q = 0; q < EPL; ++q) wj = (ms == q) ? ej[q] : wj;
+            wj = __shfl_sync(0xffffffffu, wj, wl);
+            if (lane == wl) {
+#pragma unroll
+                for (int q = 0; q < EPL; ++q)
+                    if (ms == q) ev[q] = INFINITY;
+            }
+            bv[k] = wv;
+            bj[k] = (wv < INFINITY) ? wj : -1;
+        }
     }
     if (bj[0] < 0 || !(U < INFINITY)) {
         if (lane == 0) rowj[i] = -1;
@@ -979,12 +1007,14 @@ __global__ void __launch_bounds__(256, 4) k_recheck_tc(const float *__restrict__
                                                        int32_t *__restrict__ ovf, const int32_t *__restrict__ set_of,
                                                        const int32_t *__restrict__ setcnt, int32_t *counters) {
     if (!mst_active(counters)) return;
-    const int lane = threadIdx.x & 31;
+    __shared__ float wv_s[8][32], bv_s[8][TC_TOPK];
+    __shared__ int32_t bj_s[8][TC_TOPK];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r = w0; r < n; r += nw)
         recheck_row<EPL, CW>(r, lane, xs, n, d, lists, tv, tj, tu, rsq, perm, compp, nmax_bits, eps_rep, mul32, add32, nsurv,
-                    surv, rowj, ovf, set_of, setcnt, counters);
+                             surv, rowj, ovf, set_of, setcnt, counters, wv_s[wib], bv_s[wib], bj_s[wib]);
 }
 
 // Self-contained rescan of a queued row: FP32 direct differences give the
