@@ -58,7 +58,7 @@ struct TcScratch {
     unsigned int *nmax_bits = nullptr;
     int32_t *perm = nullptr, *permp = nullptr, *vbuf = nullptr, *compp = nullptr;
     uint64_t *keys = nullptr, *kbuf = nullptr;
-    float *tv = nullptr, *tu = nullptr;            // per (list, row): best-8 half-tile lower bounds, best upper bound
+    float *tv = nullptr, *tu = nullptr;            // per (list, row): best-8 candidate-block lower bounds, best upper bound
     int32_t *tj = nullptr;
     int32_t *nsurv = nullptr, *surv = nullptr;     // per row: columns to key in FP64 (padded column indices)
     uint32_t *err = nullptr;
