@@ -49,6 +49,10 @@ SPARSE = "sparse_n50k_d4096"
 BATCHED = "batched_4096_d32"
 MOONS = "moons_n20k_d128"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# DRAM bytes (read + write) of one launch of the roofline kernel, from the
+# ncu capture summarised in profiles/traffic_k_weights_sym_blobs_n100k_d64.md
+# (taken on the kernel as it stands; other workloads report null)
+OMEGA_TRAFFIC = {"blobs_n100k_d64": 51293952 + 242455808}
 FP32_LANES_PER_SM = 128
 
 
@@ -360,7 +364,8 @@ def main():
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "flushed by a 256 MiB write before every step (inside the timed region)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                     "frac": achieved / alu_peak, "traffic": None,
+                     "frac": achieved / alu_peak,
+                     "traffic": OMEGA_TRAFFIC.get(args.workload) if (sym and not args.n) else None,
                      "kernel": "k_weights_sym (omega, double-word FP32)" if sym else "k_weights_dw (omega, double-word FP32)",
                      "note": f"FP32-pipe instructions of the algorithm: every {'unordered' if sym else 'ordered'} "
                              f"pair of the 64x64 tile grid screened ("
