@@ -49,9 +49,9 @@ SPARSE = "sparse_n50k_d4096"
 BATCHED = "batched_4096_d32"
 MOONS = "moons_n20k_d128"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# DRAM bytes (read + write) of one launch of the roofline kernel, from the
-# ncu capture summarised in profiles/traffic_k_weights_sym_blobs_n100k_d64.md
-# (taken on the kernel as it stands; other workloads report null)
+# DRAM bytes (read + write) of one full-size launch of the roofline kernel,
+# measured by a one-pass ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) of the kernel as it stands; other workloads report null
 OMEGA_TRAFFIC = {"blobs_n100k_d64": 51293952 + 242455808}
 FP32_LANES_PER_SM = 128
 
