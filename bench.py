@@ -151,6 +151,7 @@ def cpu_baseline(X, k, sigma, n_sample=None):
     n = X.shape[0]
     if n_sample is None:
         n_sample = _sample_rows(X.shape[1])
+    n_sample = min(n_sample, n)
     cores = _cpu_cores()
     t = _oracle_time(X, k, sigma, n_sample, cores)
     t_full = t * (n / n_sample) ** 2
@@ -165,7 +166,7 @@ def run_reference(args, X, k, sigma):
         return 0
     steps_total = args.steps + args.warmup
     n = X.shape[0]
-    n_sample = int(max(2000, _sample_rows(X.shape[1]) * min(1.0, (8.0 / max(steps_total, 1)) ** 0.5)))
+    n_sample = min(n, int(max(2000, _sample_rows(X.shape[1]) * min(1.0, (8.0 / max(steps_total, 1)) ** 0.5))))
     cores = _cpu_cores()
     for _ in range(args.warmup):
         _oracle_time(X, k, sigma, n_sample, cores)

@@ -1,0 +1,45 @@
+"""The benchmark's reference arm (the FP64 oracle on the host cores) keeps the
+JSON-line contract; small inputs keep these runs to a few seconds."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+KEYS = {"impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+        "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"}
+
+
+def _run(args):
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference"] + args,
+                         capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1, out.stdout
+    return json.loads(lines[0])
+
+
+def _check(line, workload):
+    assert KEYS <= set(line), KEYS - set(line)
+    assert line["impl"] == "reference" and line["config"]["workload"] == workload
+    assert line["value"] > 0 and line["unit"] == "points/s" and line["higher_is_better"] is True
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    assert line["e2e"]["value"] == line["value"] and line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_reference_arm_one_set():
+    line = _run(["--n", "2500", "--steps", "1", "--warmup", "0"])
+    _check(line, "blobs_n100k_d64")
+    # the sample never exceeds the points: no O(n^2) scaling below one
+    assert "first 2500 points" in line["cpu_baseline"]["sample"]
+    n = line["config"]["n"]
+    assert n == 2500 and line["ms_per_step"] == pytest.approx(n / line["value"] * 1000.0, rel=1e-9)
+
+
+def test_reference_arm_batched():
+    line = _run(["--workload", "batched_4096_d32", "--nsets", "6", "--steps", "1", "--warmup", "0"])
+    _check(line, "batched_4096_d32")
+    assert line["config"]["nsets"] == 6
