@@ -15,6 +15,8 @@ Functions and the passages they follow:
   flow         eq. phi
   bfs_order    Section 2.2 step 3 (BFS order, children ascending)
   decision     Algorithm 1
+  decision_detail  Algorithm 1 with each visited vertex's branch and the
+               two critical thresholds of its tests (decision margins)
   tree_stage   Algorithm 2 (bisection to the last bit) + final Algorithm 1
   cluster      Section 2.2 steps 1-5 end to end
 """
@@ -75,6 +77,8 @@ def _load():
             lib.oracle_bfs_order.argtypes = [_i64, _ptr, _ptr]
             lib.oracle_decision.restype = _i64
             lib.oracle_decision.argtypes = [_i64, _ptr, _ptr, _ptr, _ptr, _i64, _dbl]
+            lib.oracle_decision_detail.restype = _i64
+            lib.oracle_decision_detail.argtypes = [_i64, _ptr, _ptr, _ptr, _ptr, _i64, _dbl, _ptr, _ptr, _ptr]
             lib.oracle_tree_stage.restype = ctypes.c_int
             lib.oracle_tree_stage.argtypes = [_i64, _ptr, _ptr, _ptr, _ptr, _i64,
                                               _ptr, _ptr, _ptr, _ptr, _ptr, _ptr]
@@ -190,6 +194,23 @@ def decision(parent, phi_par, omega, p, k: int, N: float) -> int:
     if r < 0:
         raise ValueError("parent[] is not a rooted tree")
     return int(r)
+
+
+def decision_detail(parent, phi_par, omega, p, k: int, N: float) -> dict:
+    """Algorithm 1 at N with its early stop: per vertex the branch taken
+    (0 cut, 1 join, 2 discard, -1 not visited) and the thresholds at which
+    its cut test ((phi(e) + p-hat) / omega-hat) and join test
+    ((p-hat - phi(e)) / omega-hat) change; cuts = the number of cuts made."""
+    parent, phi_par, omega, p = _tree_args(parent, phi_par, omega, p)
+    n = parent.size
+    code = np.zeros(n, np.int8)
+    ncut = np.zeros(n, np.float64)
+    njoin = np.zeros(n, np.float64)
+    r = _load().oracle_decision_detail(n, _p(parent), _p(phi_par), _p(omega), _p(p), int(k), float(N),
+                                       _p(code), _p(ncut), _p(njoin))
+    if r < 0:
+        raise ValueError("parent[] is not a rooted tree")
+    return dict(code=code, ncut=ncut, njoin=njoin, cuts=int(r))
 
 
 def tree_stage(parent, phi_par, omega, p, k: int) -> dict:

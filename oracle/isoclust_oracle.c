@@ -352,6 +352,59 @@ int64_t oracle_decision(int64_t n, const int32_t *parent, const double *phi_par,
     return r;
 }
 
+/* Algorithm 1 at threshold N, reporting how close each decision was.
+ * Same walk and early stop as decision() (x_1..x_n = reversed BFS order,
+ * stop after the k-th cut).  For every vertex x visited, with e its parent
+ * edge and omega-hat, p-hat the working values at x's turn:
+ *   code[x]  = 0 cut, 1 join, 2 discard (the branch Algorithm 1 took);
+ *   ncut[x]  = (phi(e) + p-hat(x)) / omega-hat(x): the cut test holds iff
+ *              N reaches this value (up to the rounding of N * omega-hat);
+ *   njoin[x] = (p-hat(x) - phi(e)) / omega-hat(x): the join test holds iff
+ *              N exceeds it.
+ * Vertices not visited (after the k-th cut) get code -1 and NaN ratios.
+ * Returns the number of cuts made, or -1 if parent[] is not a rooted tree. */
+int64_t oracle_decision_detail(int64_t n, const int32_t *parent, const double *phi_par,
+                               const double *omega, const double *p, int64_t k, double N,
+                               int8_t *code, double *ncut, double *njoin)
+{
+    int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (n > 0 ? n : 1));
+    double *w = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+    double *pp = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+    int64_t j = -1;
+    if (!order || !w || !pp || oracle_bfs_order(n, parent, order) != 0) goto out;
+    for (int64_t v = 0; v < n; ++v) {
+        w[v] = omega[v];
+        pp[v] = p ? p[v] : 0.0;
+        code[v] = -1;
+        ncut[v] = NAN;
+        njoin[v] = NAN;
+    }
+    j = 0;
+    for (int64_t i = 0; j < k && i < n; ++i) {
+        int32_t x = order[n - 1 - i];
+        int32_t u = parent[x];
+        double fe = u >= 0 ? phi_par[x] : 0.0;
+        double pv = pp[x], wv = w[x];
+        double nw = N * wv;
+        ncut[x] = (fe + pv) / wv;
+        njoin[x] = (pv - fe) / wv;
+        if (fe + pv <= nw) {
+            code[x] = 0;
+            j = j + 1;
+            if (u >= 0) pp[u] = pp[u] + fe;
+        } else if (pv - fe < nw) {
+            code[x] = 1;
+            if (u >= 0) { w[u] = w[u] + wv; pp[u] = pp[u] + pv; }
+        } else {
+            code[x] = 2;
+            if (u >= 0) pp[u] = pp[u] + fe;
+        }
+    }
+out:
+    free(order); free(w); free(pp);
+    return j;
+}
+
 static uint64_t dbits(double x) { uint64_t u; memcpy(&u, &x, 8); return u; }
 static double bitsd(uint64_t u) { double x; memcpy(&x, &u, 8); return x; }
 

@@ -372,3 +372,89 @@ def test_malformed_tree_rejected(oracle_lib):
         oracle_lib.bfs_order([1, 0, -1])          # cycle 0 <-> 1 disconnected from root 2
     with pytest.raises(ValueError):
         oracle_lib.bfs_order([-1, -1, 0])         # two roots
+
+
+# ---------------------------------------------------------------- label order (readings A5-A8)
+def _label_order_cases():
+    with open(os.path.join(HERE, "golden", "label_order_trees.json")) as f:
+        return json.load(f)
+
+
+def test_bfs_order_hand_written(oracle_lib):
+    """A hand-written breadth-first order (children ascending) on an unsorted
+    tree: a depth-first order or descending children fail it."""
+    for c in _label_order_cases()["bfs_cases"]:
+        assert oracle_lib.bfs_order(c["parent"]).tolist() == c["bfs"], c["name"]
+
+
+@pytest.mark.parametrize("case", [c["name"] for c in _label_order_cases()["label_cases"]])
+def test_label_order_hand_derived(oracle_lib, case):
+    """Which k sets Algorithm 1 returns and how they are numbered: ascending
+    children in the BFS, the reversed walk, the first k cuts numbered j-1,
+    and the descending-index fold of omega-hat (hand-derived expectations)."""
+    c = next(x for x in _label_order_cases()["label_cases"] if x["name"] == case)
+    r = oracle_lib.tree_stage(c["parent"], c["phi_par"], c["omega"], None, c["k"])
+    assert r["labels"].tolist() == c["labels"]
+    assert r["i_k"] == c["i_k"]
+    if "beta" in c:
+        assert r["beta"] == c["beta"]
+
+
+# ---------------------------------------------------------------- decision margins
+def _set_ratio(parent, phi, om, p, A):
+    n = parent.size
+    bnd = sum(phi[v] for v in range(n) if parent[v] >= 0 and A[v] != A[parent[v]])
+    return (bnd + (p[A].sum() if p is not None else 0.0)) / om[A].sum()
+
+
+@pytest.mark.parametrize("with_p", [False, True])
+def test_decision_detail_agrees_with_definitions(oracle_lib, with_p):
+    """At beta: the cut vertices, in walking order, head the sets 0..k-1; a
+    cut vertex's critical ratio is its set's ratio from the definitions
+    (eq. cost); every branch taken agrees with its critical ratios; some
+    vertex sits at beta (beta is the YES/NO boundary)."""
+    rng = np.random.default_rng(20 + with_p)
+    for _ in range(20):
+        n = int(rng.integers(2, 70))
+        parent = random_tree(rng, n, "random")
+        phi, om, p = _random_weights(rng, parent, with_p)
+        k = int(rng.integers(1, min(n, 9) + 1))
+        r = oracle_lib.tree_stage(parent, phi, om, p, k)
+        beta, lab = r["beta"], r["labels"]
+        det = oracle_lib.decision_detail(parent, phi, om, p, k, beta)
+        assert det["cuts"] == k
+        order = oracle_lib.bfs_order(parent)[::-1]
+        visited = [int(x) for x in order if det["code"][x] >= 0]
+        cuts = [x for x in visited if det["code"][x] == 0]
+        assert len(cuts) == k
+        for j, x in enumerate(cuts):
+            assert lab[x] == j
+            want = _set_ratio(parent, phi, om, p, lab == j)
+            assert math.isclose(det["ncut"][x], want, rel_tol=1e-13)
+        eps = 4e-16
+        closest = np.inf
+        for x in visited:
+            c, nc, nj = det["code"][x], det["ncut"][x], det["njoin"][x]
+            if c == 0:
+                assert nc <= beta * (1 + eps)
+            elif c == 1:
+                assert nc > beta * (1 - eps) and nj < beta * (1 + eps)
+                assert parent[x] >= 0 and lab[x] == lab[parent[x]]
+            else:
+                assert nc > beta * (1 - eps) and nj >= beta * (1 - eps)
+            if beta > 0:
+                closest = min(closest, abs(nc - beta) / beta, abs(nj - beta) / beta)
+        if beta > 0:
+            assert closest <= 1e-15
+        assert (det["code"][[v for v in range(n) if v not in visited]] == -1).all()
+
+
+def test_decision_detail_hand_trees(oracle_lib):
+    """The two-level hand tree at beta = 1/2: leaves 6, 5, 4 cut with ratio
+    exactly 1/2 (phi 1 over omega 2); the walk stops after the third cut."""
+    c = next(x for x in _label_order_cases()["label_cases"] if x["name"] == "two_levels_bfs_not_dfs")
+    det = oracle_lib.decision_detail(c["parent"], c["phi_par"], c["omega"], None, c["k"], c["beta"])
+    assert det["cuts"] == 3
+    assert det["code"].tolist() == [-1, -1, -1, -1, 0, 0, 0]
+    assert det["ncut"][4] == det["ncut"][5] == det["ncut"][6] == 0.5
+    assert det["njoin"][6] == -0.5
