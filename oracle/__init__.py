@@ -13,6 +13,7 @@ Functions and the passages they follow:
   nn_rows      exact nearest neighbour (smallest key) of sampled rows
   weights      eq. omega and eq. potential
   flow         eq. phi
+  parent_flow  eq. phi on the parent edge of every vertex of a rooted tree
   bfs_order    Section 2.2 step 3 (BFS order, children ascending)
   decision     Algorithm 1
   decision_detail  Algorithm 1 with each visited vertex's branch and the
@@ -65,6 +66,8 @@ def _load():
             lib.oracle_d2.argtypes = [_ptr, _i64, _i32, _i64, _i64]
             lib.oracle_flow.restype = _dbl
             lib.oracle_flow.argtypes = [_dbl, _dbl]
+            lib.oracle_parent_flow.restype = ctypes.c_int
+            lib.oracle_parent_flow.argtypes = [_ptr, _i64, _i32, _ptr, _dbl, _ptr]
             lib.oracle_mst_prim.restype = ctypes.c_int
             lib.oracle_mst_prim.argtypes = [_ptr, _i64, _i32, _i64, _ptr, _ptr, _ptr, _ptr, _ptr]
             lib.oracle_mst_kruskal.restype = ctypes.c_int
@@ -121,6 +124,16 @@ def d2(X, i: int, j: int) -> float:
 
 def flow(d2v: float, sigma: float) -> float:
     return float(_load().oracle_flow(float(d2v), float(sigma)))
+
+
+def parent_flow(X, parent, sigma: float):
+    """phi of every vertex's parent edge (eq. phi), 0 at the root."""
+    X = _X(X)
+    parent = np.ascontiguousarray(np.asarray(parent, dtype=np.int32))
+    out = np.zeros(parent.size, np.float64)
+    if _load().oracle_parent_flow(_p(X), X.shape[0], X.shape[1], _p(parent), float(sigma), _p(out)):
+        raise ValueError("parent index out of range")
+    return out
 
 
 def mst_prim(X, root: int = 0):

@@ -213,6 +213,18 @@ static double flow_of_d2(double d2, double sigma)
 
 double oracle_flow(double d2, double sigma) { return flow_of_d2(d2, sigma); }
 
+/* eq. phi on the parent edge of every vertex: phi_par[v] = phi(x_v,
+ * x_parent[v]) (0 at the root), as the pipeline of oracle_cluster forms it. */
+int oracle_parent_flow(const double *X, int64_t n, int32_t d, const int32_t *parent, double sigma,
+                       double *phi_par)
+{
+    for (int64_t v = 0; v < n; ++v) {
+        if (parent[v] >= n) return -1;
+        phi_par[v] = parent[v] >= 0 ? flow_of_d2(oracle_d2(X, n, d, v, parent[v]), sigma) : 0.0;
+    }
+    return 0;
+}
+
 /* eq. omega and eq. potential for the listed rows (all rows when rows is
  * NULL): omega_i = sum_j phi(x_i,x_j), p_i = alpha * sum_j ||x_i - x_j||,
  * j ascending, j = i skipped unless include_self (reading R2). */

@@ -10,10 +10,26 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 if HERE not in sys.path:
     sys.path.insert(0, HERE)
 
+# measured errors against the oracle, printed at the end of the run
+_REPORT: list[str] = []
+
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: longer CPU test")
+
+
+def pytest_terminal_summary(terminalreporter, exitstatus, config):
+    if _REPORT:
+        terminalreporter.write_sep("-", "measured error against the FP64 oracle")
+        for line in _REPORT:
+            terminalreporter.write_line(line)
+
+
+@pytest.fixture(scope="session")
+def parity_report():
+    """Append one line to the end-of-run report."""
+    return _REPORT.append
 
 
 @pytest.fixture(scope="session")

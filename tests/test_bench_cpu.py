@@ -33,13 +33,21 @@ def _check(line, workload):
 def test_reference_arm_one_set():
     line = _run(["--n", "2500", "--steps", "1", "--warmup", "0"])
     _check(line, "blobs_n100k_d64")
-    # the sample never exceeds the points: no O(n^2) scaling below one
-    assert "first 2500 points" in line["cpu_baseline"]["sample"]
+    # one measured oracle run on the whole workload: no scaling law
+    assert "the whole workload" in line["cpu_baseline"]["sample"] and "not scaled" in line["cpu_baseline"]["sample"]
     n = line["config"]["n"]
     assert n == 2500 and line["ms_per_step"] == pytest.approx(n / line["value"] * 1000.0, rel=1e-9)
+    assert line["steps"] == 1 and line["warmup"] == 0
 
 
 def test_reference_arm_batched():
     line = _run(["--workload", "batched_4096_d32", "--nsets", "6", "--steps", "1", "--warmup", "0"])
     _check(line, "batched_4096_d32")
     assert line["config"]["nsets"] == 6
+    assert "not scaled" in line["cpu_baseline"]["sample"]
+
+
+def test_reference_arm_moons_is_measured_whole():
+    line = _run(["--workload", "moons_n20k_d128", "--n", "600", "--steps", "2", "--warmup", "1"])
+    _check(line, "moons_n20k_d128")
+    assert line["config"]["n"] == 600 and "not scaled" in line["cpu_baseline"]["sample"]

@@ -458,3 +458,15 @@ def test_decision_detail_hand_trees(oracle_lib):
     assert det["code"].tolist() == [-1, -1, -1, -1, 0, 0, 0]
     assert det["ncut"][4] == det["ncut"][5] == det["ncut"][6] == 0.5
     assert det["njoin"][6] == -0.5
+
+
+def test_parent_flow_matches_the_pipeline(oracle_lib):
+    """phi on parent edges equals the per-pair flow of the same d2 and the
+    pipeline's own phi_par."""
+    rng = np.random.default_rng(22)
+    X = rng.normal(size=(90, 5)).astype(np.float32)
+    c = oracle_lib.cluster(X, 3, 0.7)
+    pf = oracle_lib.parent_flow(X, c["parent"], 0.7)
+    assert (pf == c["phi_par"]).all()
+    v = int(np.nonzero(c["parent"] >= 0)[0][0])
+    assert pf[v] == math.exp(-math.sqrt(oracle_lib.d2(X, v, int(c["parent"][v]))) / 0.7)
