@@ -92,8 +92,27 @@ typedef struct {
     int32_t precision;          /* ISOCLUST_PREC_*, default AUTO                        */
     int32_t root;               /* root vertex of the tree (default 0)                  */
     int32_t include_self;       /* 1: omega and p include the j = i term (default 0)   */
-    uint64_t spin_limit;        /* bound on every device-side wait loop (0 = default)  */
+    uint64_t spin_limit;        /* bound of every device-side wait, SM clock cycles
+                                   (0 = default, 4e9: about 2 s); see below         */
 } isoclust_opts;
+
+/* spin_limit: the library's only device-side waits are the mbarrier waits
+ * of the tensor-core Boruvka sweep (and of the omega screen, which reuses
+ * it), between its copy, MMA and epilogue roles.  Each wait gives up after
+ * spin_limit SM clock cycles: the kernel raises a timeout flag, lets the
+ * copies and MMAs it already issued finish, frees its tensor memory and
+ * returns; the call then returns ISOCLUST_ERR_TIMEOUT without walking the
+ * unfinished tree, and the device stays usable.  A small value can make
+ * calls fail on a healthy device.  Calls without the tensor-core sweep
+ * never wait. */
+
+/* Test hook of the timeout path (no paper counterpart): while on (1), the
+ * epilogue of every tensor-core sweep launch first waits for a barrier that
+ * nothing arrives at, so that wait runs out after spin_limit cycles and the
+ * call returns ISOCLUST_ERR_TIMEOUT through the same teardown as a real
+ * timeout (in-flight copies and MMAs drained, tensor memory freed).  0 (the
+ * default) turns it off.  Process-wide; other values -> INVALID_ARG. */
+isoclust_status isoclust_set_test_stalled_wait(int32_t on);
 
 /* Default options (alpha 0, full-graph omega, AUTO precision, root 0). */
 isoclust_opts isoclust_opts_default(void);
@@ -182,16 +201,20 @@ isoclust_status isoclust_tree_isoperimetric(int64_t n, const int32_t *parent,
  * pool's accounting; or a latency-bound loop that cannot afford cudaMalloc /
  * cudaFree, which may synchronise the whole device.  This entry point calls
  * neither, nor any other allocating routine: its scratch is a fixed 13 MiB
- * array in the library's device memory, reserved on every GPU that loads
- * the library until the process exits.  The caller still provides every
+ * array in the library's device code.  The caller still provides every
  * input and output buffer.
  *
  * Limits and behaviour:
  *   - n <= ISOCLUST_NOALLOC_MAX_N; larger trees are rejected with
  *     ISOCLUST_ERR_INVALID_ARG and a message naming the limit.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *   - The array is placed in a device's memory when the first call on that
+ *     device sets up (the CUDA runtime loads the module holding it lazily,
+ *     and this call looks up the array's device address with
+ *     cudaGetSymbolAddress, that device current); from then on it stays
+ *     there until the process exits.  Make that first call (any small tree
+ *     will do) on each device before a memory pool reserves the device's
+ *     free memory and before any stream capture; it may synchronise the
+ *     device.
  *   - All calls share the one array, which keeps the previous call's
  *     contents (the call clears what must start at zero).  Calls from this
  *     process are serialised and each completes before it returns; work that
@@ -367,9 +390,14 @@ int32_t isoclust_last_sweep_variant(void);
  * A call replays when its arguments (pointers, sizes, offsets and ks
  * contents, sigma, options) match the previous batched call on the device
  * (the first call of a signature runs kernel by kernel, the second is
- * captured); the environment variable ISOCLUST_GRAPHS=0 keeps every call
- * kernel by kernel.  Results are identical in every mode. */
+ * captured).  Results are identical in every mode. */
 int32_t isoclust_last_batched_graph_mode(void);
+
+/* Whether repeated batched calls may capture and replay CUDA graphs: 1 (the
+ * default) allows it, 0 keeps every later batched call kernel by kernel.
+ * Process-wide setting, no device work; other values -> INVALID_ARG.  A
+ * batched call with a non-zero opts->spin_limit never uses graphs. */
+isoclust_status isoclust_set_batched_graphs(int32_t enable);
 
 #ifdef __cplusplus
 }

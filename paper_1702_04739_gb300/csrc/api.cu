@@ -213,15 +213,17 @@ cudaError_t check_finite(const void *X, int64_t count, int dtype, uint32_t *stat
 }
 
 // ---------------------------------------------------------------- helpers
-static isoclust_status map_status(uint32_t st, bool user_tree) {
+isoclust_status map_status(uint32_t st, bool user_tree) {
     if (st & DEV_NONFINITE) return fail(ISOCLUST_ERR_NONFINITE, "non-finite value in an input array");
+    // a wait that ran out leaves the stages after it without their input:
+    // it is reported before anything that follows from it
+    if (st & DEV_TIMEOUT) return fail(ISOCLUST_ERR_TIMEOUT, "a bounded device wait ran out");
     if (st & DEV_BAD_TREE)
         return user_tree ? fail(ISOCLUST_ERR_INVALID_ARG, "parent[] does not describe a rooted tree")
                          : fail(ISOCLUST_ERR_INTERNAL, "internal: the spanning tree is malformed");
     if (st & DEV_NEGATIVE)
         return user_tree ? fail(ISOCLUST_ERR_INVALID_ARG, "omega must be > 0, phi and p >= 0")
                          : fail(ISOCLUST_ERR_INTERNAL, "internal: a vertex weight is not positive");
-    if (st & DEV_TIMEOUT) return fail(ISOCLUST_ERR_TIMEOUT, "a bounded device wait ran out");
     if (st & DEV_NO_SOLUTION) return fail(ISOCLUST_ERR_NO_SOLUTION, "no finite threshold gives k sets");
     if (st & (DEV_INTERNAL | DEV_EDGE_COUNT)) return fail(ISOCLUST_ERR_INTERNAL, "internal consistency check failed (0x%x)", st);
     return ISOCLUST_OK;
@@ -285,7 +287,7 @@ struct Events {
 // every kernel again.  The first call of a signature runs eagerly (the sweep
 // variant is tuned there), the second is captured, later ones replay.  The
 // graphs run on a library-owned stream; the call stays synchronous.
-// ISOCLUST_GRAPHS=0 in the environment keeps every call eager.
+// isoclust_set_batched_graphs(0) keeps every call eager.
 struct SetsGraph {
     uint64_t key = 0;
     int seen = 0;                                  // consecutive calls with this key
@@ -308,13 +310,9 @@ static SetsGraph g_sets_graph[MAX_DEV];
 static cudaStream_t g_graph_stream[MAX_DEV] = {nullptr};
 static int g_last_graph_mode = 0;                  // 0 eager, 1 captured, 2 replayed (last batched call)
 
-static bool graphs_enabled() {
-    static const bool on = [] {
-        const char *v = getenv("ISOCLUST_GRAPHS");
-        return !(v && v[0] == '0');
-    }();
-    return on;
-}
+static std::atomic<int> g_graphs_on{1};          // isoclust_set_batched_graphs
+static std::atomic<int> g_stall_test{0};         // isoclust_set_test_stalled_wait
+static bool graphs_enabled() { return g_graphs_on.load(std::memory_order_relaxed) != 0; }
 
 struct Fnv {
     uint64_t h = 1469598103934665603ull;
@@ -365,6 +363,8 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
     bool use_tc = false;
     if ((st = use_tc_sweep(o, dtype, &use_tc))) return st;
     TcScratch TC;
+    TC.wait_cycles = o.spin_limit;
+    TC.stall_test = g_stall_test.load(std::memory_order_relaxed);
     const int tsplits = use_tc ? tc_splits(n) : 1;
 
     const int dev = current_device();
@@ -445,6 +445,13 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
     ev.rec(2, s);
 
     if (need_labels) {
+        // the tree is complete (no wait ran out, n - 1 edges) before anything walks it
+        {
+            uint32_t h1 = 0;
+            ISO_CUDA(cudaMemcpyAsync(&h1, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+            ISO_CUDA(cudaStreamSynchronize(s));
+            if (h1) return map_status(h1, false);
+        }
         // Section 2.2 step 3: root the tree, BFS order
         ISO_CUDA(orient_tree(TS, M.eu, M.ev, n, o.root, nullptr, s));
         {
@@ -748,6 +755,8 @@ static isoclust_status cluster_sets_impl(const void *X, const int64_t *offsets, 
     const int64_t *d_offs = B.plan, *d_rowbase = d_offs + (P + 1), *d_tcbase = d_rowbase + P;
     const int64_t *d_tile0 = d_tcbase + (P + 1), *d_ntl = d_tile0 + P, *d_item0 = d_ntl + P;
 
+    TC.wait_cycles = o.spin_limit;
+    TC.stall_test = g_stall_test.load(std::memory_order_relaxed);
     Events ev;
     ev.rec(0, s);
     ISO_CUDA(cudaMemcpyAsync(B.plan, plan.data(), plan.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
@@ -769,6 +778,7 @@ static isoclust_status cluster_sets_impl(const void *X, const int64_t *offsets, 
 
     // Section 2.2 steps 1-3 up to the host check of the trees (phase 0),
     // then steps 3-4 and Algorithms 1, 2 and 4 (phase 1)
+    const bool mid_check = o.spin_limit != 0 || TC.stall_test != 0;
     auto phase0 = [&](cudaStream_t q, Events &E) -> cudaError_t {
         cudaError_t e;
         E.rec(1, q);
@@ -782,6 +792,14 @@ static isoclust_status cluster_sets_impl(const void *X, const int64_t *offsets, 
         if ((e = mst_build(M, X, N, d, dtype, false, B.status, q, &TC, nsets, max_n))) return e;
         k_check_edges_sets<<<1, 1, 0, ISO_S(q)>>>(M.counters, N, nsets, B.status);
         E.rec(2, q);
+        if (mid_check) {
+            // a caller's spin limit can run out: the forest is checked before
+            // anything walks it (kernel by kernel only, no graphs then)
+            uint32_t h1 = 0;
+            if ((e = cudaMemcpyAsync(&h1, B.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, q))) return e;
+            if ((e = cudaStreamSynchronize(q))) return e;
+            if (h1) return cudaSuccess;            // the host check after this phase reports it
+        }
         // the sets' trees under a virtual root (vertex N)
         const int64_t m_mst = N - nsets;
         if ((e = cudaMemcpyAsync(B.eu, M.eu, sizeof(int32_t) * m_mst, cudaMemcpyDeviceToDevice, q))) return e;
@@ -828,7 +846,7 @@ static isoclust_status cluster_sets_impl(const void *X, const int64_t *offsets, 
 
     SetsGraph &G = g_sets_graph[dev];
     bool replay = false, capture = false;
-    if (graphs_enabled()) {
+    if (graphs_enabled() && !mid_check) {
         Fnv f;
         f.val(X); f.val(N); f.val(d); f.val(dtype); f.val(nsets); f.val(sigma);
         f.val(o.alpha); f.val(o.omega_mode); f.val(o.precision); f.val(o.root); f.val(o.include_self);
@@ -967,6 +985,18 @@ int32_t isoclust_last_sweep_variant(void) { return tc_last_variant(); }
 
 int32_t isoclust_last_batched_graph_mode(void) { return g_last_graph_mode; }
 
+isoclust_status isoclust_set_test_stalled_wait(int32_t on) {
+    if (on != 0 && on != 1) return fail(ISOCLUST_ERR_INVALID_ARG, "on must be 0 or 1");
+    g_stall_test.store(on, std::memory_order_relaxed);
+    return ISOCLUST_OK;
+}
+
+isoclust_status isoclust_set_batched_graphs(int32_t enable) {
+    if (enable != 0 && enable != 1) return fail(ISOCLUST_ERR_INVALID_ARG, "enable must be 0 or 1");
+    g_graphs_on.store(enable, std::memory_order_relaxed);
+    return ISOCLUST_OK;
+}
+
 void isoclust_last_omega_tiles(int64_t *tiles3) {
     if (tiles3) {
         tiles3[0] = (int64_t)g_prof_tiles[0];
@@ -1074,6 +1104,8 @@ isoclust_status isoclust_vertex_weights(const void *X, int64_t n, int32_t d, int
     bool use_tc = false;
     if ((st = use_tc_sweep(o, dtype, &use_tc))) return st;
     TcScratch TC;
+    TC.wait_cycles = o.spin_limit;
+    TC.stall_test = g_stall_test.load(std::memory_order_relaxed);
     const int tsplits = use_tc ? tc_splits(n) : 1;
     const int dev = current_device();
     std::lock_guard<std::mutex> lock(g_call_mu[dev]);

@@ -24,6 +24,9 @@ enum : uint32_t {
 void set_error(const char *fmt, ...);
 isoclust_status fail(isoclust_status s, const char *fmt, ...);
 isoclust_status cuda_fail(cudaError_t e, const char *what);
+// Status word of a call's device checks -> its status code (and message);
+// user_tree: the tree came from the caller (a malformed one is INVALID_ARG).
+isoclust_status map_status(uint32_t st, bool user_tree);
 
 #define ISO_CUDA(expr)                                              \
     do {                                                            \

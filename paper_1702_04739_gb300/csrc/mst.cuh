@@ -73,6 +73,8 @@ struct TcScratch {
     const int64_t *rowbase = nullptr;
     int32_t *setcnt = nullptr;                     // components left in each set (independent sets)
     bool keep_order = false;                       // rows as given instead of norm order
+    uint64_t wait_cycles = 0;                      // bound of each sweep wait in SM cycles (0: default)
+    int stall_test = 0;                            // test hook: the epilogue's first wait cannot complete
     CUtensorMap map_h, map_l;
     // n_pad_rows / nmeans / lists: 0 = one set
     void carve(Arena &A, int64_t n, int32_t d, int splits, int64_t n_pad_rows = 0, int nmeans = 1, int lists = 0);

@@ -49,7 +49,7 @@ constexpr int TC_TOPK = 8;                                // best candidate bloc
 // the sweep's limit) or 32 (independent sets or wider rows: the recheck's
 // column reads are the limit).
 constexpr int TC_SURV = 8;                                // FP64-keyed columns per row (more: rescan)
-constexpr long long TC_WAIT_CYCLES = 4000000000LL;
+constexpr long long TC_WAIT_CYCLES = 4000000000LL;         // default bound of one wait (about 2 s)
 
 // Column metadata first: the epilogue reads it with 16-byte vector loads.
 struct __align__(16) TcShared {
@@ -58,6 +58,8 @@ struct __align__(16) TcShared {
     uint64_t full[TC_MAXST], empty[TC_MAXST];
     uint64_t acc_full[TC_NACC], acc_empty[TC_NACC];
     uint64_t a_full, a_empty;
+    uint64_t drain;                                       // completion of the issued MMAs at exit
+    uint64_t stall;                                       // test hook: a barrier nothing arrives at
     uint32_t tmem_base;
     uint32_t pad;
 };
@@ -99,21 +101,40 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait (about 2 s of SM cycles); false on timeout or when another
-// role has already failed.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t *err) {
+// Bounded wait of at most `limit` SM cycles; false on timeout or when
+// another role has already failed.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t *err, long long limit) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     for (uint32_t it = 0;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 63u) == 63u) {
             if (*(volatile uint32_t *)err) return false;
-            if (clock64() - t0 > TC_WAIT_CYCLES) {
+            if (clock64() - t0 > limit) {
                 atomicOr(err, DEV_TIMEOUT);
                 return false;
             }
         }
     }
+}
+// Wait for work this CTA itself issued (TMA copies, MMAs) before it exits:
+// such work finishes by itself, so the default bound applies whatever the
+// caller's limit, and an error raised elsewhere does not cut it short.
+__device__ __forceinline__ void mbar_drain(uint64_t *bar, uint32_t parity, uint32_t *err) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > TC_WAIT_CYCLES) {
+            atomicOr(err, DEV_TIMEOUT);
+            return;
+        }
+    }
+}
+
+// The bound of every wait in the sweep: the caller's spin limit (SM cycles),
+// or the default.
+static long long tc_wait_limit(const TcScratch &T) {
+    return T.wait_cycles > 0 ? (long long)(T.wait_cycles < (1ull << 62) ? T.wait_cycles : (1ull << 62))
+                             : TC_WAIT_CYCLES;
 }
 
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
@@ -222,7 +243,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
            const int32_t *__restrict__ comp, int64_t nrows, int ntiles, int kchunks, int splits,
            const int4 *__restrict__ witems, int64_t nwitems, const int32_t *__restrict__ setcnt,
            const int32_t *counters, float *__restrict__ out_v, int32_t *__restrict__ out_j, float *__restrict__ out_u,
-           uint32_t *err, ScreenArgs scr) {
+           uint32_t *err, ScreenArgs scr, long long wait_limit, int stall_test) {
     if (!SCREEN && !mst_active(counters)) return;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -245,6 +266,8 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
         }
         mbar_init(&sh->a_full, 1);
         mbar_init(&sh->a_empty, 1);
+        mbar_init(&sh->drain, 1);
+        mbar_init(&sh->stall, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -281,23 +304,25 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
             uint32_t stage = 0, phase = 0, a_phase = 0;
+            uint32_t fills = 0, a_fills = 0;         // ring stages / A blocks whose copies were issued
             bool ok = true;
             for (int64_t w = blockIdx.x; w < items && ok; w += gridDim.x) {
                 int rt, c0, c1, sp;
                 item(w, rt, c0, c1, sp);
                 if (ARES) {
-                    if (!(ok = mbar_wait(&sh->a_empty, a_phase ^ 1u, err))) break;
+                    if (!(ok = mbar_wait(&sh->a_empty, a_phase ^ 1u, err, wait_limit))) break;
                     mbar_expect_tx(&sh->a_full, (uint32_t)(kchunks * 2 * TC_TILE_BYTES));
                     for (int kc = 0; kc < kchunks; ++kc) {
                         tma_load_2d(areg + (2 * kc) * TC_TILE_BYTES, &tmh, kc * TC_BK, rt * TC_BM, &sh->a_full);
                         tma_load_2d(areg + (2 * kc + 1) * TC_TILE_BYTES, &tml, kc * TC_BK, rt * TC_BM, &sh->a_full);
                     }
+                    ++a_fills;
                     a_phase ^= 1u;
                 }
                 for (int ct = c0; ct < c1 && ok; ct += TC_NP) {
                     const int nct = min(TC_NP, c1 - ct);
                     for (int kc = 0; kc < kchunks; ++kc) {
-                        if (!(ok = mbar_wait(&sh->empty[stage], phase ^ 1u, err))) break;
+                        if (!(ok = mbar_wait(&sh->empty[stage], phase ^ 1u, err, wait_limit))) break;
                         unsigned char *st = ring + stage * SB;
                         // stage: [A hi][A lo] (streaming A) then [B hi: NP tiles][B lo: NP tiles]
                         unsigned char *sbh = st + (ARES ? 0 : 2 * TC_TILE_BYTES);
@@ -311,10 +336,18 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
                             tma_load_2d(sbh + q * TC_TILE_BYTES, &tmh, kc * TC_BK, (ct + q) * TC_BN, &sh->full[stage]);
                             tma_load_2d(sbl + q * TC_TILE_BYTES, &tml, kc * TC_BK, (ct + q) * TC_BN, &sh->full[stage]);
                         }
+                        ++fills;
                         if (++stage == NST) { stage = 0; phase ^= 1u; }
                     }
                 }
             }
+            // before the CTA exits (also after a timeout), the copies it
+            // issued land: the last fill of each ring stage and of the A block
+            for (uint32_t st = 0; st < (uint32_t)NST && st < fills; ++st) {
+                const uint32_t f = (fills - 1u) - ((fills - 1u - st) % (uint32_t)NST);   // last fill of stage st
+                mbar_drain(&sh->full[st], (f / (uint32_t)NST) & 1u, err);
+            }
+            if (ARES && a_fills > 0) mbar_drain(&sh->a_full, (a_fills - 1u) & 1u, err);
         }
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
@@ -326,16 +359,16 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
                 item(w, rt, c0, c1, sp);
                 (void)rt;
                 if (ARES) {
-                    if (!(ok = mbar_wait(&sh->a_full, a_phase, err))) break;
+                    if (!(ok = mbar_wait(&sh->a_full, a_phase, err, wait_limit))) break;
                     tc_fence_after();
                 }
                 for (int ct = c0; ct < c1 && ok; ct += TC_NP) {
                     const uint32_t idesc = tc_idesc(min(TC_NP, c1 - ct) * TC_BN);
-                    if (!(ok = mbar_wait(&sh->acc_empty[acc], acc_phase ^ 1u, err))) break;
+                    if (!(ok = mbar_wait(&sh->acc_empty[acc], acc_phase ^ 1u, err, wait_limit))) break;
                     tc_fence_after();
                     const uint32_t dt = tmem + acc * TC_BNP;
                     for (int kc = 0; kc < kchunks; ++kc) {
-                        if (!(ok = mbar_wait(&sh->full[stage], phase, err))) break;
+                        if (!(ok = mbar_wait(&sh->full[stage], phase, err, wait_limit))) break;
                         tc_fence_after();
                         const uint32_t sb = smem_u32(ring + stage * SB);
                         const uint32_t sbh = sb + (ARES ? 0 : 2 * TC_TILE_BYTES), sbl = sbh + TC_NP * TC_TILE_BYTES;
@@ -361,6 +394,10 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
                     a_phase ^= 1u;
                 }
             }
+            // every MMA this thread issued completes before TMEM is freed
+            // (also after a timeout): one more commit, and its arrival
+            mma_commit(&sh->drain);
+            mbar_drain(&sh->drain, 0u, err);
         }
     } else {
         // ------------------------------------------------ epilogue (warps 2..9)
@@ -415,7 +452,10 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
                     if (cn2 + h < c1) { ptsq = __ldg(tsq + cn2 + h); ptmax = __ldg(tmax + cn2 + h); }
                 }
                 asm volatile("bar.sync 1, %0;" ::"n"(32 * TC_EPI_WARPS) : "memory");
-                if (ok) ok = mbar_wait(&sh->acc_full[acc], acc_phase, err);
+                // test hook: the epilogue first waits for a barrier that no
+                // role arrives at, so the bounded wait runs out (timeout path)
+                if (stall_test && ok) ok = mbar_wait(&sh->stall, 0u, err, wait_limit);
+                if (ok) ok = mbar_wait(&sh->acc_full[acc], acc_phase, err, wait_limit);
                 tc_fence_after();
                 // SCREEN: d2 >= v + n_i - dlt with v = n_j - 2g; near if that
                 // bound <= max(A_i, A_j), i.e. v <= max(A_i, A_j) + (dlt - n_i)
@@ -1299,7 +1339,7 @@ cudaError_t tc_omega_screen(TcScratch &T, const float *Xp, int64_t n, int32_t d,
 #define ISO_SCREEN_LAUNCH(AKV)                                                                                    \
     k_sweep_tc<AKV, true, 64><<<grid, TC_THREADS, tc_smem(AKV), ISO_S(s)>>>(                                          \
         T.map_h, T.map_l, T.nrm, T.cnrm, T.rsq, T.tmax, T.tsq, acoef, bcoef, nullptr, T.n_pad, ntiles, kchunks, 1,   \
-        ditems, nit, nullptr, nullptr, nullptr, nullptr, nullptr, T.err, scr)
+        ditems, nit, nullptr, nullptr, nullptr, nullptr, nullptr, T.err, scr, tc_wait_limit(T), T.stall_test)
     if (kchunks == 1)
         ISO_SCREEN_LAUNCH(1);
     else if (kchunks == 2)
@@ -1411,7 +1451,8 @@ cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t 
 #define ISO_SWEEP_LAUNCH(AKV, CWV)                                                                                \
     k_sweep_tc<AKV, false, CWV><<<grid, TC_THREADS, tc_smem(AKV), ISO_S(s)>>>(                                         \
         T.map_h, T.map_l, T.nrm, T.cnrm, T.rsq, T.tmax, T.tsq, acoef, bcoef, T.compp, T.n_pad, ntiles, kchunks,      \
-        T.splits, T.items, T.nitems, T.setcnt, S.counters, T.tv, T.tj, T.tu, T.err, ScreenArgs{})
+        T.splits, T.items, T.nitems, T.setcnt, S.counters, T.tv, T.tj, T.tu, T.err, ScreenArgs{},           \
+        tc_wait_limit(T), T.stall_test)
     if (kchunks == 1 && T.resident)
         {
         if (T.cw == 32) ISO_SWEEP_LAUNCH(1, 32);

@@ -8,9 +8,13 @@
 // loop on one stream that cannot afford cudaMalloc/cudaFree, which may
 // synchronise the whole device.  The regular entry points grow a cached
 // scratch buffer with cudaMalloc; this one never does.  Its scratch is the
-// array below, reserved on every GPU that loads the library until the
-// process exits, which bounds the tree it accepts to ISOCLUST_NOALLOC_MAX_N
-// vertices.
+// array below, which bounds the tree it accepts to ISOCLUST_NOALLOC_MAX_N
+// vertices.  The array lives in this file's own device module, which the
+// CUDA runtime loads lazily: it takes its place in a device's memory when
+// the first call on that device looks up its address, and stays there until
+// the process exits.  So that first call (any small tree) belongs before the
+// caller's pool reserves the device's free memory, and before any stream
+// capture; loading the module may synchronise the device.
 #include <mutex>
 
 #include "common.cuh"
@@ -48,15 +52,6 @@ __global__ void k_na_tree_input(const int32_t *__restrict__ parent, int64_t n, i
     }
 }
 
-isoclust_status na_map(uint32_t st) {
-    if (st & DEV_NONFINITE) return fail(ISOCLUST_ERR_NONFINITE, "non-finite value in an input array");
-    if (st & DEV_BAD_TREE) return fail(ISOCLUST_ERR_INVALID_ARG, "parent[] does not describe a rooted tree");
-    if (st & DEV_NEGATIVE) return fail(ISOCLUST_ERR_INVALID_ARG, "omega must be > 0, phi and p >= 0");
-    if (st & DEV_NO_SOLUTION) return fail(ISOCLUST_ERR_NO_SOLUTION, "no finite threshold gives k sets");
-    if (st & (DEV_INTERNAL | DEV_EDGE_COUNT | DEV_TIMEOUT))
-        return fail(ISOCLUST_ERR_INTERNAL, "internal consistency check failed (0x%x)", st);
-    return ISOCLUST_OK;
-}
 }  // namespace
 
 }  // namespace iso
@@ -85,7 +80,8 @@ extern "C" isoclust_status isoclust_tree_isoperimetric_noalloc(int64_t n, const 
     std::lock_guard<std::mutex> lock(g_na_mu[dev]);
 
     // Set-up, once per device, with that device current: the device address
-    // of the static array (the host-side name is not a device pointer).
+    // of the static array (the host-side name is not a device pointer).  This
+    // loads the module that holds the array, placing it in device memory.
     if (!g_na_ptr[dev]) {
         void *ptr = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
@@ -113,15 +109,15 @@ extern "C" isoclust_status isoclust_tree_isoperimetric_noalloc(int64_t n, const 
     ISO_CUDA(cudaMemcpyAsync(info, TS.hostinfo, sizeof(info), cudaMemcpyDeviceToHost, s));
     ISO_CUDA(cudaMemcpyAsync(&hst, TS.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     ISO_CUDA(cudaStreamSynchronize(s));
-    if (hst) return na_map(hst);
+    if (hst) return map_status(hst, true);
     if (info[0] != 1) return fail(ISOCLUST_ERR_INVALID_ARG, "parent[] has %d roots (need exactly 1)", info[0]);
     if (n > 1) ISO_CUDA(edges_from_parent(TS, parent, n, eu, ev, s));
     ISO_CUDA(orient_tree(TS, eu, ev, n, info[1], parent, s));
     ISO_CUDA(cudaMemcpyAsync(&hst, TS.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     ISO_CUDA(cudaStreamSynchronize(s));
-    if (hst) return na_map(hst);
+    if (hst) return map_status(hst, true);
     ISO_CUDA(tree_search_and_label(TS, phi_par, omega, p, k, labels, residual, i_k, s));
     ISO_CUDA(cudaMemcpyAsync(&hst, TS.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     ISO_CUDA(cudaStreamSynchronize(s));
-    return na_map(hst);
+    return map_status(hst, true);
 }

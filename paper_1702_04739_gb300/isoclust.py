@@ -100,6 +100,10 @@ def load(build_if_missing: bool = True):
         lib.isoclust_last_sweep_variant.argtypes = []
         lib.isoclust_last_batched_graph_mode.restype = ctypes.c_int32
         lib.isoclust_last_batched_graph_mode.argtypes = []
+        lib.isoclust_set_batched_graphs.restype = ctypes.c_int
+        lib.isoclust_set_batched_graphs.argtypes = [ctypes.c_int32]
+        lib.isoclust_set_test_stalled_wait.restype = ctypes.c_int
+        lib.isoclust_set_test_stalled_wait.argtypes = [ctypes.c_int32]
         lib.isoclust_last_omega_tiles.restype = None
         lib.isoclust_last_omega_tiles.argtypes = [_P]
         _lib = lib
@@ -372,6 +376,19 @@ def last_batched_graph_mode() -> int:
     """0 kernel by kernel, 1 captured into CUDA graphs, 2 replayed graphs
     (the last batched call; isoclust_last_batched_graph_mode)."""
     return int(load().isoclust_last_batched_graph_mode())
+
+
+def set_batched_graphs(enable: bool) -> None:
+    """Allow (True, the default) or forbid CUDA-graph capture and replay of
+    repeated batched calls (isoclust_set_batched_graphs)."""
+    _check(load().isoclust_set_batched_graphs(int(bool(enable))))
+
+
+def set_test_stalled_wait(on: bool) -> None:
+    """Test hook of the timeout path (isoclust_set_test_stalled_wait): while
+    on, every tensor-core sweep's epilogue waits for a barrier nothing
+    arrives at, so calls run into their spin limit."""
+    _check(load().isoclust_set_test_stalled_wait(int(bool(on))))
 
 
 def kernel_launches() -> int:

@@ -128,3 +128,11 @@ def test_batched_workload_recipe():
     assert (X == X2).all() and (offs == offs2).all() and (ks == ks2).all()
     Xs, offs_s, ks_s = W.batched_sets(seed=1, d=4, sizes=[2, 3, 70])
     assert list(np.diff(offs_s)) == [2, 3, 70] and (ks_s <= np.diff(offs_s)).all()
+
+
+def test_process_settings_validate_their_argument():
+    """The graph and test-hook switches take 0 or 1 (no device work)."""
+    from paper_1702_04739_gb300 import isoclust
+    L = isoclust.load()
+    assert L.isoclust_set_batched_graphs(2) == 1 and L.isoclust_set_test_stalled_wait(-1) == 1
+    assert L.isoclust_set_batched_graphs(1) == 0 and L.isoclust_set_test_stalled_wait(0) == 0
