@@ -63,7 +63,8 @@ typedef enum {
     ISOCLUST_ERR_CUDA = 5,          /* a CUDA runtime call failed               */
     ISOCLUST_ERR_TIMEOUT = 6,       /* a bounded device wait ran out            */
     ISOCLUST_ERR_NO_SOLUTION = 7,   /* no finite N makes Algorithm 1 answer YES */
-    ISOCLUST_ERR_INTERNAL = 8       /* an internal consistency check failed     */
+    ISOCLUST_ERR_INTERNAL = 8,      /* an internal consistency check failed     */
+    ISOCLUST_ERR_COMM = 9           /* a sharded call's all-reduce callback failed */
 } isoclust_status;
 
 /* Element type of X. */
@@ -340,6 +341,54 @@ isoclust_status isoclust_ik_backward(const void *X, int64_t n, int32_t d, int32_
                                      const double *omega, double grad_ik, double *dX,
                                      double *dscale, double *dsigma, double *i_k, void *stream);
 
+/*
+ * isoclust_cluster_sharded -- isoclust_cluster on one point set whose
+ * pairwise work is split across `comm->world` processes, one GPU each
+ * (Section 3.5's MST rounds and eq. omega are sums and minima over the rows
+ * of X, so rows shard; the tree stage is O(n) and runs on every rank).
+ * Every rank calls it with the same X (replicated in its own device memory),
+ * sizes, k, sigma and options, and gets the same labels, residual and i_k.
+ *   - Boruvka rounds: rank r sweeps the 128-row tiles t of the norm-ordered
+ *     rows with t mod world == r (tensor-core sweep, FP64 recheck of its own
+ *     rows); the per-component minimum keys are combined by two all-reduce
+ *     MIN calls per round (the d2 bits, then the packed (min, max) pair among
+ *     the rows that reach that d2), each over n uint64 values; the
+ *     union-find that follows is identical on every rank.
+ *   - eq. omega: rank r evaluates the 64-row tile pairs w of the symmetric
+ *     sweep with w mod world == r; each rank's per-row partial sums (FP64)
+ *     are combined by one all-reduce SUM over n doubles.
+ * comm->allreduce(ctx, buf, count, op, stream) must reduce the `count`
+ * elements at device address `buf` in place across all ranks with `op`
+ * (ISOCLUST_REDUCE_MIN_U64: unsigned 64-bit minimum - all ones marks "no
+ * key", so a signed minimum needs the sign bit flipped before and after;
+ * ISOCLUST_REDUCE_SUM_F64)
+ * ordered on `stream` (a cudaStream_t): it is called from the host between
+ * kernel launches, with earlier work queued, not finished; the library's
+ * kernels that follow are queued after it returns.  It returns 0 on success;
+ * anything else makes the call return ISOCLUST_ERR_COMM.  rank in [0,
+ * world), world >= 1; world == 1 runs the single-GPU work through the same
+ * path.  The omega sums of different ranks are added in FP64 after the
+ * double-word per-rank sums, so omega (and i_k) can differ from
+ * isoclust_cluster's in the last bits, within its error bound; the tree is
+ * the same unique MST.
+ * Needs F32 input, an sm_103 device, alpha = 0, full-graph omega and the
+ * AUTO or BF16_TC precision; other options -> ISOCLUST_ERR_INVALID_ARG.
+ */
+enum { ISOCLUST_REDUCE_MIN_U64 = 0, ISOCLUST_REDUCE_SUM_F64 = 1 };
+typedef int32_t (*isoclust_allreduce_fn)(void *ctx, void *buf, int64_t count, int32_t op, void *stream);
+typedef struct {
+    int32_t rank;                     /* this process, 0 .. world-1       */
+    int32_t world;                    /* processes sharing the work       */
+    isoclust_allreduce_fn allreduce;  /* the caller's collective          */
+    void *ctx;                        /* passed back to allreduce         */
+} isoclust_comm;
+
+isoclust_status isoclust_cluster_sharded(const void *X, int64_t n, int32_t d, int32_t dtype,
+                                         int32_t k, double sigma, const isoclust_opts *opts,
+                                         const isoclust_comm *comm,
+                                         int32_t *labels, uint8_t *residual, double *i_k,
+                                         void *stream);
+
 /* Per-stage device times (milliseconds, CUDA events on the call's stream)
  * of the last isoclust_cluster / _detail / _batched call on this host thread:
  * t[0] validation, t[1] weights, t[2] MST, t[3] tree orientation + stats,
@@ -355,7 +404,8 @@ void isoclust_last_profile(double *t_ms6, int64_t *counts4);
  * below e^-(36 + ln n) of their row's largest term), tiles3[2] = 0 when the
  * pairs were ordered, 1 when unordered (symmetric sweep, each pair once for
  * both rows) and screened in FP32, 2 when unordered and screened on the
- * tensor cores (the FP32 screen did not run).  Zero counts when the screen did not run (F64 input,
+ * tensor cores (the FP32 screen did not run), 3 as 2 with the kept pairs'
+ * Gram on the tensor cores (isoclust_set_omega_gram).  Zero counts when the screen did not run (F64 input,
  * alpha > 0, or the FP64 precision option). */
 void isoclust_last_omega_tiles(int64_t *tiles3);
 
@@ -392,6 +442,16 @@ int32_t isoclust_last_sweep_variant(void);
  * (the first call of a signature runs kernel by kernel, the second is
  * captured).  Results are identical in every mode. */
 int32_t isoclust_last_batched_graph_mode(void);
+
+/* Arithmetic of eq. omega's pair sums in one-set calls (F32 input, sm_103,
+ * alpha = 0, full-graph omega): 1 (the default) forms each kept tile pair's
+ * Gram <y_i, y_j> of the tile-centred points exactly on the tensor cores (7
+ * balanced base-256 digit planes per row, BF16 products summed exactly in
+ * FP32 accumulators) and the rest of d2 and the terms in double-word FP32;
+ * 0 forms d2 by double-word FP32 sums of squared differences.  Both keep
+ * d2 to about 2^-46; omega agrees to within the library's error bound, not
+ * bit for bit.  Process-wide; other values -> INVALID_ARG. */
+isoclust_status isoclust_set_omega_gram(int32_t on);
 
 /* Whether repeated batched calls may capture and replay CUDA graphs: 1 (the
  * default) allows it, 0 keeps every later batched call kernel by kernel.

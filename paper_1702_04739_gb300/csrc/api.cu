@@ -20,7 +20,8 @@ size_t weights_sym_bytes(int64_t n, int32_t d);
 cudaError_t weights_launch_sym(const float *X, int64_t n, int32_t d, double sigma, int include_self,
                                const unsigned long long *nnbits, double *omega, void *part,
                                unsigned long long *tile_counts, const uint8_t *need, cudaEvent_t *kev,
-                               cudaStream_t s);
+                               cudaStream_t s, const Shard *sh = nullptr, double *part64 = nullptr,
+                               OmegaGram *og = nullptr, uint32_t *status = nullptr, uint64_t wait_cycles = 0);
 float omega_zskip(int64_t n);
 constexpr size_t SYM_PART_LIMIT = size_t(16) << 30;   // symmetric sweep up to 16 GiB of partials
 size_t weights_sym_sets_bytes(int64_t n_pad, int64_t nitems, int32_t d);
@@ -65,9 +66,29 @@ isoclust_status fail(isoclust_status s, const char *fmt, ...) {
     return s;
 }
 
+static thread_local int g_comm_rc = 0;            // a failed all-reduce callback (sharded calls)
+
 isoclust_status cuda_fail(cudaError_t e, const char *what) {
+    if (g_comm_rc) {
+        const int rc = g_comm_rc;
+        g_comm_rc = 0;
+        return fail(ISOCLUST_ERR_COMM, "the all-reduce callback returned %d", rc);
+    }
     snprintf(g_err, sizeof(g_err), "CUDA error %d (%s) at %s", (int)e, cudaGetErrorString(e), what);
     return e == cudaErrorMemoryAllocation ? ISOCLUST_ERR_OOM : ISOCLUST_ERR_CUDA;
+}
+
+cudaError_t shard_allreduce(const Shard &sh, void *buf, int64_t count, int32_t op, cudaStream_t s) {
+    const cudaError_t pending = cudaGetLastError();     // launches queued before the collective
+    if (pending != cudaSuccess) return pending;
+    const int32_t rc = sh.fn(sh.ctx, buf, count, op, (void *)s);
+    if (rc != 0) {
+        g_comm_rc = rc;
+        cudaStreamSynchronize(s);         // the call returns with none of its work in flight
+        cudaGetLastError();
+        return cudaErrorUnknown;
+    }
+    return cudaSuccess;
 }
 
 // ---------------------------------------------------------------- device info
@@ -122,6 +143,35 @@ void *scratch_acquire(size_t bytes, cudaStream_t stream, isoclust_status *st) {
     }
     g_scratch[dev] = p;
     g_scratch_cap[dev] = want;
+    return p;
+}
+
+static void *g_gram[MAX_DEV] = {nullptr};
+static size_t g_gram_cap[MAX_DEV] = {0};
+
+// Caller holds g_call_mu[dev] (one call per device at a time).
+void *gram_acquire(size_t bytes) {
+    int dev = current_device();
+    if (g_gram_cap[dev] >= bytes && g_gram[dev]) return g_gram[dev];
+    if (g_gram[dev]) {
+        cudaDeviceSynchronize();
+        cudaFree(g_gram[dev]);
+        g_gram[dev] = nullptr;
+        g_gram_cap[dev] = 0;
+    }
+    size_t want = bytes + bytes / 8 + (1u << 20);
+    void *p = nullptr;
+    if (cudaMalloc(&p, want) != cudaSuccess) {
+        cudaGetLastError();
+        want = bytes;
+        if (cudaMalloc(&p, want) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cannot allocate %zu bytes for the omega Gram tiles", bytes);
+            return nullptr;
+        }
+    }
+    g_gram[dev] = p;
+    g_gram_cap[dev] = want;
     return p;
 }
 
@@ -312,6 +362,7 @@ static int g_last_graph_mode = 0;                  // 0 eager, 1 captured, 2 rep
 
 static std::atomic<int> g_graphs_on{1};          // isoclust_set_batched_graphs
 static std::atomic<int> g_stall_test{0};         // isoclust_set_test_stalled_wait
+static std::atomic<int> g_omega_gram{1};         // isoclust_set_omega_gram
 static bool graphs_enabled() { return g_graphs_on.load(std::memory_order_relaxed) != 0; }
 
 struct Fnv {
@@ -347,8 +398,9 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
                                     const isoclust_opts *opts_in, int32_t *labels, uint8_t *residual, double *i_k,
                                     int32_t *out_parent, double *out_phi, double *out_omega, double *out_p,
                                     double *out_beta, int32_t *out_eu, int32_t *out_ev, double *out_ed2,
-                                    cudaStream_t s, bool need_labels) {
+                                    cudaStream_t s, bool need_labels, const Shard *sh = nullptr) {
     isoclust_status st;
+    g_comm_rc = 0;
     if ((st = check_points(X, n, d, dtype, 2))) return st;
     isoclust_opts o = resolve_opts(opts_in);
     if ((st = check_opts(o, n, dtype))) return st;
@@ -366,6 +418,15 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
     TC.wait_cycles = o.spin_limit;
     TC.stall_test = g_stall_test.load(std::memory_order_relaxed);
     const int tsplits = use_tc ? tc_splits(n) : 1;
+    if (sh) {
+        // the sharded work: the tensor-core sweep and the symmetric omega sweep
+        if (!use_tc || fp64_sweep || o.alpha != 0.0 || o.omega_mode != ISOCLUST_OMEGA_FULL || !need_labels ||
+            weights_sym_bytes(n, d) > SYM_PART_LIMIT)
+            return fail(ISOCLUST_ERR_INVALID_ARG, "a sharded call needs F32 input on an sm_103 device, alpha = 0, "
+                                                  "full-graph omega and precision AUTO or BF16_TC");
+        TC.shard_rank = sh->rank;
+        TC.shard_world = sh->world;
+    }
 
     const int dev = current_device();
     std::lock_guard<std::mutex> lock(g_call_mu[dev]);
@@ -379,10 +440,15 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
         double *omp = nullptr, *pp = nullptr;
         void *sym = nullptr;
         uint8_t *need = nullptr;
+        double *part64 = nullptr;
+        void *gram = nullptr;
     } P;
     const bool permuted = need_labels && dtype == ISOCLUST_F32 && !fp64_sweep;
     const bool symmetric = permuted && o.alpha == 0.0 && o.omega_mode == ISOCLUST_OMEGA_FULL &&
                            weights_sym_bytes(n, d) <= SYM_PART_LIMIT;
+    // eq. omega's Gram on the tensor cores (with the tensor-core screen)
+    const bool gram = symmetric && use_tc && g_omega_gram.load(std::memory_order_relaxed) != 0 &&
+                      ceil_div(n, 128) <= 65535;
     auto carve = [&](Arena &A, MstScratch &M, TreeScratch &TS, double **phi, double **om, double **pp, double **omtmp,
                      uint32_t **status) {
         *status = A.take<uint32_t>(4);
@@ -407,6 +473,8 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
             P.pp = A.take<double>(n);
             if (symmetric) P.sym = (void *)A.take<unsigned char>(weights_sym_bytes(n, d));
             if (symmetric && use_tc) P.need = A.take<uint8_t>((size_t)ceil_div(n, 64) * ceil_div(n, 64));
+            if (sh) P.part64 = A.take<double>(n);
+            if (gram) P.gram = (void *)A.take<unsigned char>(omega_gram_bytes(n, d), 1024);
         }
     };
     MstScratch M;
@@ -436,7 +504,7 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
     ev.rec(1, s);
 
     // Section 2.2 steps 1-2: minimum spanning tree
-    ISO_CUDA(mst_build(M, X, n, d, dtype, fp64_sweep, status, s, use_tc ? &TC : nullptr));
+    ISO_CUDA(mst_build(M, X, n, d, dtype, fp64_sweep, status, s, use_tc ? &TC : nullptr, 1, 0, sh));
     k_check_edges<<<1, 1, 0, ISO_S(s)>>>(M.counters, n, status);
     if (out_eu || out_ev || out_ed2) {
         if (!(out_eu && out_ev && out_ed2)) return fail(ISOCLUST_ERR_INVALID_ARG, "edge outputs must be all or none");
@@ -482,8 +550,12 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
                                                  ceil_div(n, 64), s));
                         k_or_err_api<<<1, 1, 0, ISO_S(s)>>>(TC.err, status);
                     }
+                    OmegaGram og;
+                    og.scratch = P.gram;
+                    og.scratch_bytes = gram ? omega_gram_bytes(n, d) : 0;
                     ISO_CUDA(weights_launch_sym(P.Xp, n, d, sigma, o.include_self, P.nnp, P.omp, P.sym, P.tiles,
-                                                use_tc ? P.need : nullptr, ev.ok ? ev.e + 8 : nullptr, s));
+                                                use_tc ? P.need : nullptr, ev.ok ? ev.e + 8 : nullptr, s, sh,
+                                                P.part64, gram ? &og : nullptr, status, o.spin_limit));
                 }
                 else
                     ISO_CUDA(weights_launch(P.Xp, n, d, dtype, false, sigma, o.alpha, o.include_self, P.nnp, P.omp,
@@ -539,7 +611,7 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
     g_prof_cnt[3] = ss.max_depth;
     g_prof_tiles[0] = g_prof_tiles[1] = 0;
     if (permuted) ISO_CUDA(cudaMemcpy(g_prof_tiles, P.tiles, sizeof(g_prof_tiles), cudaMemcpyDeviceToHost));
-    g_prof_sym = symmetric ? (use_tc ? 2 : 1) : 0;
+    g_prof_sym = symmetric ? (gram ? 3 : (use_tc ? 2 : 1)) : 0;
     g_prof_omega_kernel_ms = symmetric ? ev.ms(8, 9) : 0.0;
     return map_status(fin, false);
 }
@@ -985,6 +1057,12 @@ int32_t isoclust_last_sweep_variant(void) { return tc_last_variant(); }
 
 int32_t isoclust_last_batched_graph_mode(void) { return g_last_graph_mode; }
 
+isoclust_status isoclust_set_omega_gram(int32_t on) {
+    if (on != 0 && on != 1) return fail(ISOCLUST_ERR_INVALID_ARG, "on must be 0 or 1");
+    g_omega_gram.store(on, std::memory_order_relaxed);
+    return ISOCLUST_OK;
+}
+
 isoclust_status isoclust_set_test_stalled_wait(int32_t on) {
     if (on != 0 && on != 1) return fail(ISOCLUST_ERR_INVALID_ARG, "on must be 0 or 1");
     g_stall_test.store(on, std::memory_order_relaxed);
@@ -1017,6 +1095,21 @@ isoclust_status isoclust_cluster(const void *X, int64_t n, int32_t d, int32_t dt
                                  void *stream) {
     return cluster_impl(X, n, d, dtype, k, sigma, opts, labels, residual, i_k, nullptr, nullptr, nullptr, nullptr,
                         nullptr, nullptr, nullptr, nullptr, (cudaStream_t)stream, true);
+}
+
+isoclust_status isoclust_cluster_sharded(const void *X, int64_t n, int32_t d, int32_t dtype, int32_t k, double sigma,
+                                         const isoclust_opts *opts, const isoclust_comm *comm, int32_t *labels,
+                                         uint8_t *residual, double *i_k, void *stream) {
+    if (!comm || !comm->allreduce) return fail(ISOCLUST_ERR_INVALID_ARG, "comm and comm->allreduce are required");
+    if (comm->world < 1 || comm->rank < 0 || comm->rank >= comm->world)
+        return fail(ISOCLUST_ERR_INVALID_ARG, "rank %d of world %d", comm->rank, comm->world);
+    Shard sh;
+    sh.rank = comm->rank;
+    sh.world = comm->world;
+    sh.fn = comm->allreduce;
+    sh.ctx = comm->ctx;
+    return cluster_impl(X, n, d, dtype, k, sigma, opts, labels, residual, i_k, nullptr, nullptr, nullptr, nullptr,
+                        nullptr, nullptr, nullptr, nullptr, (cudaStream_t)stream, true, &sh);
 }
 
 isoclust_status isoclust_cluster_detail(const void *X, int64_t n, int32_t d, int32_t dtype, int32_t k, double sigma,

@@ -21,6 +21,17 @@ enum : uint32_t {
     DEV_EDGE_COUNT = 1u << 6,   // Boruvka did not produce n-1 edges
 };
 
+// A sharded call's collectives (isoclust_comm): rank r of world processes
+// and the caller's all-reduce.  A null Shard pointer: nothing is sharded.
+struct Shard {
+    int32_t rank = 0, world = 1;
+    isoclust_allreduce_fn fn = nullptr;
+    void *ctx = nullptr;
+};
+// Runs the caller's all-reduce; a failure is reported as ISOCLUST_ERR_COMM
+// by the next cuda_fail of this thread (the returned error is cudaErrorUnknown).
+cudaError_t shard_allreduce(const Shard &sh, void *buf, int64_t count, int32_t op, cudaStream_t s);
+
 void set_error(const char *fmt, ...);
 isoclust_status fail(isoclust_status s, const char *fmt, ...);
 isoclust_status cuda_fail(cudaError_t e, const char *what);
@@ -80,6 +91,26 @@ struct Arena {
 // Per-device cached scratch (grow-only).  Returns nullptr on failure.
 void *scratch_acquire(size_t bytes, cudaStream_t stream, isoclust_status *st);
 void scratch_release();
+// A second per-device cached buffer (grow-only) for the omega Gram tiles,
+// whose size is known only after the screen.  nullptr on failure.
+void *gram_acquire(size_t bytes);
+
+// The Gram of eq. omega's tile pairs on the tensor cores (omega_tc.cu).
+// scratch / scratch_bytes: omega_gram_bytes(n, d) bytes of the call's
+// scratch; the launch fills the rest (rows of the omega order padded to 128).
+struct OmegaGram {
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    float *yh = nullptr, *yl = nullptr;   // [n_pad][d] y = x - c_T as a double-word
+    int32_t *rexp = nullptr;              // [n_pad] E of each row
+    float2 *rnorm = nullptr;              // [n_pad] |y|^2 as a double-word
+    int32_t *item_slot = nullptr;         // [items] 2 x block + half, -1 when the screen drops the item
+    float2 *gbuf = nullptr;               // [blocks][128][64] G in units of 2^(E_i + E_j - 14)
+    int64_t nblocks = 0;
+};
+size_t omega_gram_bytes(int64_t n, int32_t d);
+cudaError_t omega_gram_launch(OmegaGram &G, const float *Xp, int64_t n, int32_t d, const float *cen,
+                              const uint8_t *tskip, uint32_t *err, uint64_t wait_cycles, cudaStream_t s);
 
 // ---------------------------------------------------------------- helpers
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

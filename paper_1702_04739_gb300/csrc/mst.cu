@@ -325,7 +325,7 @@ __global__ void k_cmin_pair(const int32_t *__restrict__ comp, const double *__re
 __global__ void k_hook_tgt(const int32_t *__restrict__ comp, int64_t n, const unsigned long long *__restrict__ cd2,
                            const unsigned long long *__restrict__ cpair, int32_t *__restrict__ tgt,
                            int32_t *__restrict__ cu, int32_t *__restrict__ cv, double *__restrict__ cdd,
-                           const int32_t *counters) {
+                           const int32_t *counters, uint32_t *st) {
     if (!active(counters)) return;
     const int64_t gs = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gs) {
@@ -333,6 +333,12 @@ __global__ void k_hook_tgt(const int32_t *__restrict__ comp, int64_t n, const un
         unsigned long long pr = cpair[v];
         if (pr == ~0ull) { tgt[v] = (int32_t)v; continue; }
         int32_t a = (int32_t)(pr >> 32), b = (int32_t)(pr & 0xffffffffu);
+        if (a < 0 || b < 0 || a >= n || b >= n) {
+            // not a pair of points (a sharded call's all-reduce returned garbage): no hook
+            atomicOr(st, DEV_INTERNAL);
+            tgt[v] = (int32_t)v;
+            continue;
+        }
         int32_t outside = comp[a] == v ? b : a;
         tgt[v] = comp[outside];
         cu[v] = a; cv[v] = b; cdd[v] = bitsd(cd2[v]);
@@ -502,7 +508,8 @@ __global__ void k_or_err(const uint32_t *src, uint32_t *dst) {
 }
 
 cudaError_t mst_build(MstScratch &S, const void *X, int64_t n, int32_t d, int dtype, bool sweep_fp64,
-                      uint32_t *status, cudaStream_t s, TcScratch *tc, int32_t target, int64_t max_n) {
+                      uint32_t *status, cudaStream_t s, TcScratch *tc, int32_t target, int64_t max_n,
+                      const Shard *sh) {
     k_mst_init<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.comp, n, target, S.counters);
     // Boruvka at least halves every unfinished set's components per round;
     // component chains never leave a set, so pointer jumping needs
@@ -524,8 +531,11 @@ cudaError_t mst_build(MstScratch &S, const void *X, int64_t n, int32_t d, int dt
             return e;
         }
         k_cmin_d2<<<rg, TPB, 0, ISO_S(s)>>>(S.comp, S.rowd2, S.rowj, n, S.cd2, S.counters);
+        // sharded: each rank saw only its own rows; the minima over all rows
+        if (sh && (e = shard_allreduce(*sh, S.cd2, n, ISOCLUST_REDUCE_MIN_U64, s))) return e;
         k_cmin_pair<<<rg, TPB, 0, ISO_S(s)>>>(S.comp, S.rowd2, S.rowj, n, S.cd2, S.cpair, S.counters);
-        k_hook_tgt<<<rg, TPB, 0, ISO_S(s)>>>(S.comp, n, S.cd2, S.cpair, S.tgt, S.cu, S.cv, S.cdd, S.counters);
+        if (sh && (e = shard_allreduce(*sh, S.cpair, n, ISOCLUST_REDUCE_MIN_U64, s))) return e;
+        k_hook_tgt<<<rg, TPB, 0, ISO_S(s)>>>(S.comp, n, S.cd2, S.cpair, S.tgt, S.cu, S.cv, S.cdd, S.counters, status);
         k_hook_resolve<<<rg, TPB, 0, ISO_S(s)>>>(S.comp, n, S.tgt, S.cu, S.cv, S.cdd, S.nxt, S.eu, S.ev, S.ed2,
                                                      S.counters, status);
         int32_t *na = S.nxt, *nb = S.nxt2;

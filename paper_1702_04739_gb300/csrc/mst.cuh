@@ -75,6 +75,7 @@ struct TcScratch {
     bool keep_order = false;                       // rows as given instead of norm order
     uint64_t wait_cycles = 0;                      // bound of each sweep wait in SM cycles (0: default)
     int stall_test = 0;                            // test hook: the epilogue's first wait cannot complete
+    int shard_rank = 0, shard_world = 1;           // sharded call: this rank sweeps row tiles t = rank mod world
     CUtensorMap map_h, map_l;
     // n_pad_rows / nmeans / lists: 0 = one set
     void carve(Arena &A, int64_t n, int32_t d, int splits, int64_t n_pad_rows = 0, int nmeans = 1, int lists = 0);
@@ -111,9 +112,12 @@ cudaError_t tc_count_sets(TcScratch &T, const int32_t *comp, int64_t n, const in
 // target: components left when the forest is complete (1 for one point set;
 // the number of sets when X holds independent sets, whose pairs the sweep
 // never mixes); max_n bounds the rounds (the largest set).
+// sh != nullptr (sharded call, tensor-core sweep only): each rank's rows
+// give the per-component minima, combined across ranks by the caller's
+// all-reduce before the union-find.
 cudaError_t mst_build(MstScratch &S, const void *X, int64_t n, int32_t d, int dtype, bool sweep_fp64,
                       uint32_t *status, cudaStream_t s, TcScratch *tc = nullptr, int32_t target = 1,
-                      int64_t max_n = 0);
+                      int64_t max_n = 0, const Shard *sh = nullptr);
 
 // Nearest-neighbour d2 of every row (exact key), one Boruvka-style sweep with
 // every point its own component.  Result in S.rowd2 / S.rowj.

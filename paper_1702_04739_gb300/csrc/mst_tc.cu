@@ -31,8 +31,11 @@
 #include <vector>
 
 #include "mst.cuh"
+#include "tcgen05.cuh"
 
 namespace iso {
+
+using namespace tcx;
 
 namespace {
 constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64;      // BK bf16 = 128 bytes (one swizzle row)
@@ -70,6 +73,7 @@ static_assert(offsetof(TcShared, full) % 8 == 0, "mbarriers must be 8-byte align
 // ring stage holds one K chunk of a pair of column tiles, hi and lo (B hi
 // 256 rows, B lo 256 rows), preceded by the row tile's chunk (A hi, A lo)
 // when A streams.
+static_assert(TC_BNP % 16 == 0 && TC_BNP <= 256, "N of one MMA");
 __host__ __device__ constexpr int tc_areg_bytes(int AK) { return AK * 2 * TC_TILE_BYTES; }
 __host__ __device__ constexpr int tc_sb(int AK) { return (AK > 0 ? 2 * TC_NP : 2 + 2 * TC_NP) * TC_TILE_BYTES; }
 __host__ __device__ constexpr int tc_smem(int AK) {
@@ -79,56 +83,6 @@ static_assert(tc_sb(0) % 1024 == 0 && tc_sb(1) % 1024 == 0, "TcShared follows 10
 static_assert(tc_smem(0) <= 227 * 1024 && tc_smem(1) <= 227 * 1024 && tc_smem(2) <= 227 * 1024,
               "shared memory budget");
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait of at most `limit` SM cycles; false on timeout or when
-// another role has already failed.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t *err, long long limit) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const long long t0 = clock64();
-    for (uint32_t it = 0;; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 63u) == 63u) {
-            if (*(volatile uint32_t *)err) return false;
-            if (clock64() - t0 > limit) {
-                atomicOr(err, DEV_TIMEOUT);
-                return false;
-            }
-        }
-    }
-}
-// Wait for work this CTA itself issued (TMA copies, MMAs) before it exits:
-// such work finishes by itself, so the default bound applies whatever the
-// caller's limit, and an error raised elsewhere does not cut it short.
-__device__ __forceinline__ void mbar_drain(uint64_t *bar, uint32_t parity, uint32_t *err) {
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > TC_WAIT_CYCLES) {
-            atomicOr(err, DEV_TIMEOUT);
-            return;
-        }
-    }
-}
 
 // The bound of every wait in the sweep: the caller's spin limit (SM cycles),
 // or the default.
@@ -136,63 +90,6 @@ static long long tc_wait_limit(const TcScratch &T) {
     return T.wait_cycles > 0 ? (long long)(T.wait_cycles < (1ull << 62) ? T.wait_cycles : (1ull << 62))
                              : TC_WAIT_CYCLES;
 }
-
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
-            "r"(smem_u32(dst)),
-        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart; tile bases are 1024-byte aligned.
-__device__ __forceinline__ uint64_t make_sw128_desc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;                  // leading byte offset (unused with this swizzle)
-    d |= (uint64_t)(1024u >> 4) << 32;       // stride byte offset
-    d |= (uint64_t)1 << 46;                  // descriptor version
-    d |= (uint64_t)2 << 61;                  // 128-byte swizzle
-    return d;
-}
-
-// Instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both K-major, M=128,
-// N = 256 (a pair of column tiles) or 128 (the last tile of an odd range).
-__host__ __device__ constexpr uint32_t tc_idesc(int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
-}
-static_assert(TC_BNP % 16 == 0 && TC_BNP <= 256, "N of one MMA");
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accum) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
-        : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // m = min(m, v) unless the column's component is the row's (a predicated
 // min: compare + min per element)
@@ -243,7 +140,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
            const int32_t *__restrict__ comp, int64_t nrows, int ntiles, int kchunks, int splits,
            const int4 *__restrict__ witems, int64_t nwitems, const int32_t *__restrict__ setcnt,
            const int32_t *counters, float *__restrict__ out_v, int32_t *__restrict__ out_j, float *__restrict__ out_u,
-           uint32_t *err, ScreenArgs scr, long long wait_limit, int stall_test) {
+           uint32_t *err, ScreenArgs scr, long long wait_limit, int stall_test, int rt_stride, int rt_off) {
     if (!SCREEN && !mst_active(counters)) return;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -293,7 +190,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
             rt = it.x; c0 = it.y; c1 = it.z; sp = it.w & 15;
             if (setcnt && setcnt[it.w >> 4] <= 1) c1 = c0;      // nothing left to join in this set
         } else {
-            rt = (int)(w / splits);
+            rt = (int)(w / splits) * rt_stride + rt_off;      // row tiles of this rank (sharded calls)
             sp = (int)(w % splits);
             c0 = sp * tiles_per_split;
             c1 = min(ntiles, c0 + tiles_per_split);
@@ -456,6 +353,9 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
                 // role arrives at, so the bounded wait runs out (timeout path)
                 if (stall_test && ok) ok = mbar_wait(&sh->stall, 0u, err, wait_limit);
                 if (ok) ok = mbar_wait(&sh->acc_full[acc], acc_phase, err, wait_limit);
+                // lanes may part on a wait that runs out; the warp-collective
+                // TMEM loads below need one answer for the whole warp
+                ok = __all_sync(0xffffffffu, ok);
                 tc_fence_after();
                 // SCREEN: d2 >= v + n_i - dlt with v = n_j - 2g; near if that
                 // bound <= max(A_i, A_j), i.e. v <= max(A_i, A_j) + (dlt - n_i)
@@ -779,10 +679,14 @@ __device__ __forceinline__ void recheck_row(int64_t r, int lane, const float *__
                                             int32_t *__restrict__ rowj, int32_t *__restrict__ ovf,
                                             const int32_t *__restrict__ set_of, const int32_t *__restrict__ setcnt,
                                             int32_t *counters, float *__restrict__ wv_s, float *__restrict__ bv_s,
-                                            int32_t *__restrict__ bj_s) {
+                                            int32_t *__restrict__ bj_s, int shard_rank, int shard_world) {
     if (lane == 0) nsurv[r] = 0;           // every row, padding included: k_exact_tc reads them all
     const int64_t i = perm[r];
     if (i < 0) return;                     // padding row
+    if (shard_world > 1 && (int)((r / TC_BM) % shard_world) != shard_rank) {
+        if (lane == 0) rowj[i] = -1;       // another rank's row (sharded calls)
+        return;
+    }
     if (setcnt && setcnt[set_of[i]] <= 1) {     // the row's set is one component already
         if (lane == 0) rowj[i] = -1;
         return;
@@ -1045,7 +949,8 @@ __global__ void __launch_bounds__(256, 4) k_recheck_tc(const float *__restrict__
                                                        float mul32, float add32, int32_t *__restrict__ nsurv,
                                                        int32_t *__restrict__ surv, int32_t *__restrict__ rowj,
                                                        int32_t *__restrict__ ovf, const int32_t *__restrict__ set_of,
-                                                       const int32_t *__restrict__ setcnt, int32_t *counters) {
+                                                       const int32_t *__restrict__ setcnt, int32_t *counters,
+                                                       int shard_rank, int shard_world) {
     if (!mst_active(counters)) return;
     __shared__ float wv_s[8][32], bv_s[8][TC_TOPK];
     __shared__ int32_t bj_s[8][TC_TOPK];
@@ -1054,7 +959,8 @@ __global__ void __launch_bounds__(256, 4) k_recheck_tc(const float *__restrict__
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r = w0; r < n; r += nw)
         recheck_row<EPL, CW>(r, lane, xs, n, d, lists, tv, tj, tu, rsq, perm, compp, nmax_bits, eps_rep, mul32, add32, nsurv,
-                             surv, rowj, ovf, set_of, setcnt, counters, wv_s[wib], bv_s[wib], bj_s[wib]);
+                             surv, rowj, ovf, set_of, setcnt, counters, wv_s[wib], bv_s[wib], bj_s[wib], shard_rank,
+                             shard_world);
 }
 
 // Self-contained rescan of a queued row: FP32 direct differences give the
@@ -1146,6 +1052,19 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
+cudaError_t make_map_rows(CUtensorMap *m, const void *base, int64_t n_pad, int32_t d_pad, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    cuuint64_t dims[2] = {(cuuint64_t)d_pad, (cuuint64_t)n_pad};
+    cuuint64_t strides[1] = {(cuuint64_t)d_pad * 2};
+    cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 cudaError_t make_map(CUtensorMap *m, const __nv_bfloat16 *base, int64_t n_pad, int32_t d_pad) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return cudaErrorNotSupported;
@@ -1159,6 +1078,10 @@ cudaError_t make_map(CUtensorMap *m, const __nv_bfloat16 *base, int64_t n_pad, i
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 }  // namespace
+
+cudaError_t tc_map_bf16(CUtensorMap *m, const void *base, int64_t rows, int32_t cols, int box_rows) {
+    return make_map_rows(m, base, rows, cols, box_rows);
+}
 
 void TcScratch::carve(Arena &A, int64_t n, int32_t d, int splits_, int64_t n_pad_rows, int nmeans, int lists_) {
     splits = splits_;
@@ -1339,7 +1262,7 @@ cudaError_t tc_omega_screen(TcScratch &T, const float *Xp, int64_t n, int32_t d,
 #define ISO_SCREEN_LAUNCH(AKV)                                                                                    \
     k_sweep_tc<AKV, true, 64><<<grid, TC_THREADS, tc_smem(AKV), ISO_S(s)>>>(                                          \
         T.map_h, T.map_l, T.nrm, T.cnrm, T.rsq, T.tmax, T.tsq, acoef, bcoef, nullptr, T.n_pad, ntiles, kchunks, 1,   \
-        ditems, nit, nullptr, nullptr, nullptr, nullptr, nullptr, T.err, scr, tc_wait_limit(T), T.stall_test)
+        ditems, nit, nullptr, nullptr, nullptr, nullptr, nullptr, T.err, scr, tc_wait_limit(T), T.stall_test, 1, 0)
     if (kchunks == 1)
         ISO_SCREEN_LAUNCH(1);
     else if (kchunks == 2)
@@ -1433,7 +1356,10 @@ cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t 
                            cudaStream_t s) {
     const int ntiles = (int)(T.n_pad / TC_BM);
     const int kchunks = T.d_pad / TC_BK;
-    const int64_t items = T.items ? T.nitems : (int64_t)ntiles * T.splits;
+    // a sharded call sweeps the row tiles t with t mod world == rank
+    const int64_t own_tiles = T.shard_rank < ntiles
+                                  ? ((int64_t)ntiles - T.shard_rank + T.shard_world - 1) / T.shard_world : 0;
+    const int64_t items = T.items ? T.nitems : own_tiles * T.splits;
     const int64_t nsm = (int64_t)num_sms();
     const unsigned grid = (unsigned)(items < nsm ? (items > 0 ? items : 1) : nsm);
     const int64_t gblocks = ceil_div(T.n_pad, 256), gcap = (int64_t)num_sms() * 8;
@@ -1452,7 +1378,7 @@ cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t 
     k_sweep_tc<AKV, false, CWV><<<grid, TC_THREADS, tc_smem(AKV), ISO_S(s)>>>(                                         \
         T.map_h, T.map_l, T.nrm, T.cnrm, T.rsq, T.tmax, T.tsq, acoef, bcoef, T.compp, T.n_pad, ntiles, kchunks,      \
         T.splits, T.items, T.nitems, T.setcnt, S.counters, T.tv, T.tj, T.tu, T.err, ScreenArgs{},           \
-        tc_wait_limit(T), T.stall_test)
+        tc_wait_limit(T), T.stall_test, T.items ? 1 : T.shard_world, T.items ? 0 : T.shard_rank)
     if (kchunks == 1 && T.resident)
         {
         if (T.cw == 32) ISO_SWEEP_LAUNCH(1, 32);
@@ -1484,7 +1410,8 @@ cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t 
 #define ISO_RECHECK_LAUNCH(EPLV, CWV)                                                                                \
     k_recheck_tc<EPLV, CWV><<<(unsigned)(rblocks < rcap ? rblocks : rcap), 256, 0, ISO_S(s)>>>(                        \
         T.xs, T.n_pad, d, T.lists, T.tv, T.tj, T.tu, T.rsq, T.permp, T.compp, T.nmax_bits, (float)(eps_rep * 1.0001),  \
-        mul32, add32, T.nsurv, T.surv, S.rowj, S.ovf_rows, T.set_of, T.setcnt, S.counters)
+        mul32, add32, T.nsurv, T.surv, S.rowj, S.ovf_rows, T.set_of, T.setcnt, S.counters, T.shard_rank,           \
+        T.shard_world)
     if (T.lists <= 4)
         {
         if (T.cw == 32) ISO_RECHECK_LAUNCH(1, 32);

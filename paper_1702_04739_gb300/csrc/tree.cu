@@ -68,6 +68,7 @@ void TreeScratch::carve(Arena &A, int64_t n) {
     head2 = A.take<int32_t>(n);
     cflag = A.take<int32_t>(n + 1);
     cidx = A.take<int32_t>(n + 1);
+    hist = A.take<uint32_t>(CAND_BUCKETS);
     search = A.take<SearchState>(1);
     status = A.take<uint32_t>(1);
     hostinfo = A.take<int32_t>(16);
@@ -341,6 +342,7 @@ __device__ void init_search(SearchState *S, double phs, double phm, double wsum,
     S->stats[4] = psum; S->stats[5] = pmin; S->stats[6] = alpha0; S->stats[7] = beta0;
     S->have_lo = 0; S->have_hi = 0; S->done = 0; S->error = 0; S->passes = 0;
     S->selected = 0; S->ik_bits = 0ull; S->beta = 0.0;
+    S->lane_lo = -1; S->mode = 0; S->cand_passes = 0; S->ncand = 0u;
     const double DMAX = 1.7976931348623157e308;
     double b0 = (isfinite(beta0) && beta0 > 0.0) ? beta0 : 1.0;
     double a0 = (isfinite(alpha0) && alpha0 > 0.0) ? alpha0 : 0.0;
@@ -676,10 +678,15 @@ __device__ void search_update(SearchState *S, int32_t k, int last, uint32_t *st)
     }
     bool have_lo = S->have_lo;
     unsigned long long lo = S->lo_bits;
+    int lane_lo = -1;
     for (int t = 0; t < DP_LANES; ++t) {
         unsigned long long b = dbits(S->thr[t]);
-        if (S->cnt[t] < k && b < hi && (!have_lo || b > lo)) { lo = b; have_lo = true; }
+        if (S->cnt[t] < k && b < hi && (!have_lo || b > lo)) { lo = b; have_lo = true; lane_lo = t; }
     }
+    if (lane_lo < 0 && have_lo)          // lo unchanged: a lane that re-evaluated it
+        for (int t = 0; t < DP_LANES; ++t)
+            if (S->cnt[t] < k && dbits(S->thr[t]) == lo) { lane_lo = t; break; }
+    S->lane_lo = lane_lo;
     S->hi_bits = hi; S->have_hi = 1;
     S->lo_bits = lo; S->have_lo = have_lo ? 1 : 0;
     for (int t = 0; t < DP_LANES; ++t) S->cnt[t] = 0;
@@ -709,6 +716,135 @@ __device__ void search_update(SearchState *S, int32_t k, int last, uint32_t *st)
 
 __global__ void k_search_update(SearchState *S, int32_t k, int last, uint32_t *st) {
     if (threadIdx.x == 0) search_update(S, k, last, st);
+}
+
+// ---- thresholds from critical ratios (one tree).  As N grows from lo, the
+// first decision of Algorithm 1 to change is that of a vertex whose
+// descendants keep theirs, so it changes where N reaches the vertex's own
+// critical ratio in lo's state: (phi(e) + p-hat) / omega-hat for the cut
+// test, (p-hat - phi(e)) / omega-hat for the join test.  The ratios inside
+// the bracket (lo, hi) of every vertex, read from the lane that evaluated lo
+// in the last pass, are counted per bucket of the bracket's bit patterns;
+// the next pass splits them into 32 groups of equal count (or, when at most
+// CAND_EXACT remain, tries each of them and its neighbouring doubles).  Any
+// threshold inside the bracket keeps the search correct (the bracket only
+// shrinks); these choices only make it shorter.  lo itself is re-evaluated
+// in lane 0 so that its state is always available.
+__device__ __forceinline__ int cand_bucket(unsigned long long b, unsigned long long lo, double inv_w) {
+    int j = (int)((double)(b - lo) * inv_w);
+    return j < 0 ? 0 : (j >= CAND_BUCKETS ? CAND_BUCKETS - 1 : j);
+}
+
+__device__ __forceinline__ bool cand_active(const SearchState *S) {
+    return !S->done && S->mode == 0 && S->lane_lo >= 0 && S->cand_passes < DP_CAND_PASSES;
+}
+
+__global__ void __launch_bounds__(256) k_cand_hist(DpArgs A, SearchState *S, const double *__restrict__ wh,
+                                                   const double *__restrict__ ph, uint32_t *__restrict__ hist) {
+    if (!cand_active(S)) return;
+    const unsigned long long lo = S->lo_bits, hi = S->hi_bits;
+    const int L = S->lane_lo;
+    const double inv_w = (double)CAND_BUCKETS / (double)(hi - lo);
+    auto add = [&](double c) {
+        const unsigned long long b = dbits(c);
+        if (!(c > 0.0) || b <= lo || b >= hi) return;
+        atomicAdd(hist + cand_bucket(b, lo, inv_w), 1u);
+        const unsigned q = atomicAdd(&S->ncand, 1u);
+        if (q < (unsigned)CAND_EXACT) S->cand[q] = b;
+    };
+    const int64_t gs = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < A.n; v += gs) {
+        const size_t vl = (size_t)v * DP_LANES + L;
+        const double w = wh[vl], pv = ph[vl];
+        const int32_t u = A.parent[v];
+        const double fe = u >= 0 ? A.phi[v] : 0.0;
+        add(__ddiv_rn(__dadd_rn(fe, pv), w));
+        if (u >= 0) add(__ddiv_rn(__dsub_rn(pv, fe), w));
+    }
+}
+
+// One block: the next pass's thresholds (lane 0 = lo), or the switch to the
+// 33-ary bit search already written by k_search_update.
+__global__ void __launch_bounds__(1024) k_cand_select(SearchState *S, uint32_t *__restrict__ hist) {
+    __shared__ unsigned int pre[CAND_BUCKETS];
+    __shared__ unsigned int warp_sum[32];
+    __shared__ int active;
+    const int tid = threadIdx.x;
+    if (tid == 0) active = cand_active(S) ? 1 : 0;
+    __syncthreads();
+    if (!active) {
+        if (tid == 0 && !S->done) S->mode = 1;       // k_search_update's bit-search thresholds stand
+        for (int j = tid; j < CAND_BUCKETS; j += blockDim.x) hist[j] = 0u;
+        return;
+    }
+    // inclusive prefix sums of the buckets: 4 per thread, then across threads
+    constexpr int PER = CAND_BUCKETS / 1024;
+    unsigned int loc[PER], run = 0;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) { run += hist[tid * PER + q]; loc[q] = run; }
+    const int lane = tid & 31, wp = tid >> 5;
+    unsigned int x = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sum[wp] = x;
+    __syncthreads();
+    if (wp == 0) {
+        unsigned int z = warp_sum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int y = __shfl_up_sync(0xffffffffu, z, o);
+            if (lane >= o) z += y;
+        }
+        warp_sum[lane] = z;
+    }
+    __syncthreads();
+    const unsigned int before = (x - run) + (wp > 0 ? warp_sum[wp - 1] : 0u);
+#pragma unroll
+    for (int q = 0; q < PER; ++q) pre[tid * PER + q] = before + loc[q];
+    __syncthreads();
+    for (int j = tid; j < CAND_BUCKETS; j += blockDim.x) hist[j] = 0u;     // ready for the next pass
+    if (tid != 0) return;
+    const unsigned long long lo = S->lo_bits, hi = S->hi_bits;
+    const unsigned int m = pre[CAND_BUCKETS - 1];
+    const unsigned int nc = S->ncand;
+    S->ncand = 0u;
+    double t[DP_LANES];
+    t[0] = bitsd(lo);
+    int used = 1;
+    if (hi - lo <= (unsigned long long)DP_LANES) {
+        // every double of the bracket
+        for (int q = 1; q < DP_LANES; ++q) t[q] = bitsd(lo + (unsigned long long)q < hi ? lo + q : hi);
+        used = DP_LANES;
+    } else if (m == 0u) {
+        S->mode = 1;                                  // nothing to aim at: bit search
+        return;
+    } else if (nc <= (unsigned)CAND_EXACT) {
+        // each remaining critical ratio and its neighbouring doubles
+        for (unsigned q = 0; q < nc && used + 3 <= DP_LANES; ++q) {
+            const unsigned long long b = S->cand[q];
+            const unsigned long long c[3] = {b - 1ull, b, b + 1ull};
+            for (int r = 0; r < 3; ++r)
+                if (c[r] > lo && c[r] < hi) t[used++] = bitsd(c[r]);
+        }
+    } else {
+        // 31 thresholds splitting the ratios into groups of equal count
+        const double wdt = (double)(hi - lo) / (double)CAND_BUCKETS;
+        int j = 0;
+        for (int q = 1; q < DP_LANES; ++q) {
+            const unsigned long long r = ((unsigned long long)m * (unsigned long long)q) / DP_LANES;
+            while (j < CAND_BUCKETS - 1 && pre[j] < r) ++j;
+            unsigned long long b = lo + (unsigned long long)((double)(j + 1) * wdt);
+            if (b <= lo) b = lo + 1ull;
+            if (b >= hi) b = hi - 1ull;
+            t[used++] = bitsd(b);
+        }
+    }
+    for (int q = used; q < DP_LANES; ++q) t[q] = t[used - 1];
+    for (int q = 0; q < DP_LANES; ++q) S->thr[q] = t[q];
+    S->cand_passes += 1;
 }
 
 // independent sets: one thread per set
@@ -941,10 +1077,16 @@ cudaError_t tree_search_and_label(TreeScratch &S, const double *phi_par, const d
     k_stats<<<1, 1024, 0, ISO_S(s)>>>(T.parent, phi_par, omega, p, n, S.search, S.status);
     DpArgs A{n, T.parent, T.ch_off, T.ch_list, T.leaves, phi_par, omega, p};
     const unsigned grid = (unsigned)(num_sms() * 8);
-    for (int pass = 0; pass < DP_SEARCH_PASSES; ++pass) {
+    if ((e = cudaMemsetAsync(S.hist, 0, sizeof(uint32_t) * CAND_BUCKETS, s))) return e;
+    for (int pass = 0; pass < DP_TREE_PASSES; ++pass) {
         if ((e = cudaMemsetAsync(S.done, 0, sizeof(int32_t) * n, s))) return e;
         k_dp_pass<<<grid, 256, 0, ISO_S(s)>>>(A, S.search, S.dec, S.wh, S.ph, S.done, S.rat, 0);
-        k_search_update<<<1, 32, 0, ISO_S(s)>>>(S.search, k, pass == DP_SEARCH_PASSES - 1, S.status);
+        k_search_update<<<1, 32, 0, ISO_S(s)>>>(S.search, k, pass == DP_TREE_PASSES - 1, S.status);
+        if (pass + 1 < DP_TREE_PASSES) {
+            // the next pass's thresholds from the critical ratios in lo's state
+            k_cand_hist<<<grid, 256, 0, ISO_S(s)>>>(A, S.search, S.wh, S.ph, S.hist);
+            k_cand_select<<<1, 1024, 0, ISO_S(s)>>>(S.search, S.hist);
+        }
     }
     // Final call of Algorithm 1 at beta: Cut, eta and the set ratios.
     if ((e = cudaMemsetAsync(S.done, 0, sizeof(int32_t) * n, s))) return e;

@@ -6,6 +6,14 @@ namespace iso {
 
 constexpr int DP_LANES = 32;          // thresholds evaluated per Algorithm-1 pass
 constexpr int DP_SEARCH_PASSES = 14;  // 1 bracketing pass + 13 passes of 33-ary search
+// One tree: after the bracketing pass, up to DP_CAND_PASSES passes take their
+// thresholds from the critical ratios of the vertices (see
+// tree_search_and_label), then 33-ary search of the bit patterns finishes
+// whatever remains (at most 13 passes).
+constexpr int DP_CAND_PASSES = 8;
+constexpr int DP_TREE_PASSES = 1 + DP_CAND_PASSES + 13;
+constexpr int CAND_BUCKETS = 4096;    // histogram of critical ratios over the bracket's bit patterns
+constexpr int CAND_EXACT = 10;        // at most this many left: they are tried exactly (+-1 ulp)
 enum : uint8_t { DEC_DISCARD = 0, DEC_CUT = 1, DEC_JOIN = 2 };
 
 // Device-resident search state of reading S (bisection to the last bit).
@@ -21,6 +29,11 @@ struct SearchState {
     int nleaves;
     int selected;             // cuts among the first k (must equal k)
     unsigned long long ik_bits;
+    int lane_lo;              // lane of the last pass whose threshold is lo (-1: none)
+    int mode;                 // 0: thresholds from critical ratios, 1: 33-ary bit search
+    int cand_passes;          // passes that took their thresholds from critical ratios
+    unsigned int ncand;       // critical ratios inside the bracket (this pass)
+    unsigned long long cand[CAND_EXACT];
 };
 
 // Rooted tree in device scratch.
@@ -55,6 +68,7 @@ struct TreeScratch {
     uint8_t *dec;
     double *wh, *ph, *rat;
     int32_t *done, *head, *head2, *cflag, *cidx;
+    uint32_t *hist;      // [CAND_BUCKETS] critical ratios per bucket of the bracket
     SearchState *search;
     uint32_t *status;
     int32_t *hostinfo;   // small device block read back by the host

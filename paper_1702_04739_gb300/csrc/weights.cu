@@ -372,6 +372,37 @@ __global__ void k_tile_pair_skip(const float *__restrict__ cen, const float *__r
     }
 }
 
+// d2 of rows of the omega order from the tensor-core Gram (omega_tc.cu).
+struct GramArgs {
+    const float2 *gbuf;          // [blocks][128][64] G in units of 2^(E_i + E_j - 14)
+    const int32_t *item_slot;    // per item: 2 x block + half
+    const float *yh, *yl;        // y = x - c_T, double-word
+    const int32_t *rexp;         // E of each row
+    const float2 *rnorm;         // |y|^2, double-word
+    const float *cen;            // tile centroids c_T
+};
+
+// Renormalised double-word sum of squared exact differences (the sweep's own
+// d2, for the pairs whose Gram form cancels).
+__device__ __forceinline__ void direct_d2(const float *__restrict__ a, const float *__restrict__ b, int d, float &S,
+                                          float &E) {
+    S = 0.f;
+    E = 0.f;
+    for (int t = 0; t < d; ++t) {
+        float s1, e1;
+        two_sum(a[t], -b[t], s1, e1);
+        const float p = __fmul_rn(s1, s1);
+        float q2 = __fmaf_rn(s1, s1, -p);
+        q2 = __fmaf_rn(__fadd_rn(s1, s1), e1, q2);
+        float hs, he;
+        two_sum(S, p, hs, he);
+        S = hs;
+        E = __fadd_rn(E, __fadd_rn(he, q2));
+        if ((t & 3) == 3) fast_two_sum(S, E, S, E);
+    }
+    fast_two_sum(S, E, S, E);
+}
+
 // Symmetric omega sweep: each unordered tile pair is screened in FP32 and,
 // if any of its terms can matter in either direction, evaluated once in
 // double-word arithmetic; the pair's d2 serves both omega_i and omega_j.
@@ -379,13 +410,14 @@ __global__ void k_tile_pair_skip(const float *__restrict__ cen, const float *__r
 // of item w, so the final sums do not depend on scheduling.
 // Independent sets: the tile pairs come from a list (both tiles of one set)
 // and tile_valid[I] counts the real rows of tile I (padding follows them).
-template <bool SETS>
+template <bool SETS, bool GRAM = false>
 __global__ void __launch_bounds__(TPB, 2)
 k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *__restrict__ shdw,
               float is_h, float is_l, ExpTable tabv, float zskip, float scr_shrink, int64_t T,
               int64_t nitems, const int2 *__restrict__ witems, const int32_t *__restrict__ tile_valid,
               const uint8_t *__restrict__ tskip, int prescreened, uint8_t *__restrict__ flags,
-              float2 *__restrict__ rpart, float2 *__restrict__ cpart, unsigned long long *__restrict__ tile_counts) {
+              float2 *__restrict__ rpart, float2 *__restrict__ cpart, unsigned long long *__restrict__ tile_counts,
+              int shard_rank, int shard_world, GramArgs ga) {
     __shared__ __align__(16) float As[WDC][WPAD];
     __shared__ __align__(16) float Bs[WDC][WPAD];
     __shared__ float2 tab[64];
@@ -393,11 +425,16 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
     __shared__ float2 mc[WT][17];
     __shared__ int64_t sIJ[5];
     __shared__ float sred[TPB / 32][2];        // per warp: smallest and largest shift of its real rows
+    __shared__ float2 sUV[GRAM ? 2 * WT : 1];  // GRAM: |y|^2 +- 2 <y, D> of the rows of I, then of J
+    __shared__ float sSc[GRAM ? 2 * WT : 1];   // GRAM: 2^(E - 7) of the rows of I, 2^(E - 6) of J
+    __shared__ float2 sC;                      // GRAM: |D|^2
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     if (tid < 64) tab[tid] = tabv.t[tid];
     unsigned long long dw_items = 0, screened = 0;
-    for (int64_t w = blockIdx.x; w < nitems; w += gridDim.x) {
+    // a sharded call evaluates the items w with w mod world == rank
+    for (int64_t w = (int64_t)blockIdx.x * shard_world + shard_rank; w < nitems;
+         w += (int64_t)gridDim.x * shard_world) {
         ++screened;
         __syncthreads();                       // previous item's readers of sIJ are done
         if (tid == 0) {
@@ -507,6 +544,96 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) { S[i][j] = 0.f; E[i][j] = 0.f; }
+        if constexpr (GRAM) {
+            // d2 = (|y_i|^2 + 2 <y_i, D> + |D|^2) + (|y_j|^2 - 2 <y_j, D>) - 2 G_ij, y = x - c_T,
+            // D = c_I - c_J: the cross terms of the 64 rows of I (products 0..63)
+            // and of J (64..127), two threads per product
+            const int dp = tid >> 1, part = tid & 1;
+            const int64_t gr = dp < WT ? row0 + dp : col0 + (dp - WT);
+            float xh = 0.f, xl = 0.f;
+            if (!diag) {
+                const float *cI = ga.cen + I * d, *cJ = ga.cen + J * d;
+                const float *ryh = ga.yh + gr * d, *ryl = ga.yl + gr * d;
+                for (int t = part; t < d; t += 2) {
+                    float Dh, Dl;
+                    two_sum(cI[t], -cJ[t], Dh, Dl);
+                    const float a = ryh[t], al = ryl[t];
+                    float p, e;
+                    two_prod(a, Dh, p, e);
+                    e = __fmaf_rn(a, Dl, __fmaf_rn(al, Dh, e));
+                    dw_add(xh, xl, p, e);
+                }
+            }
+            {
+                const float oh = __shfl_xor_sync(0xffffffffu, xh, 1), ol = __shfl_xor_sync(0xffffffffu, xl, 1);
+                dw_add(xh, xl, oh, ol);
+            }
+            if (part == 0) {
+                const float2 rn = ga.rnorm[gr];
+                float uh = rn.x, ul = rn.y;
+                const float sg = dp < WT ? 2.0f : -2.0f;
+                dw_add(uh, ul, __fmul_rn(sg, xh), __fmul_rn(sg, xl));
+                sUV[dp] = make_float2(uh, ul);
+                sSc[dp] = ldexpf(1.0f, ga.rexp[gr] - (dp < WT ? 7 : 6));
+            }
+            if (tid < 32) {
+                float ch = 0.f, cl = 0.f;
+                if (!diag) {
+                    const float *cI = ga.cen + I * d, *cJ = ga.cen + J * d;
+                    for (int t = tid; t < d; t += 32) {
+                        float Dh, Dl;
+                        two_sum(cI[t], -cJ[t], Dh, Dl);
+                        float p, e;
+                        two_prod(Dh, Dh, p, e);
+                        e = __fmaf_rn(__fadd_rn(Dh, Dh), Dl, e);
+                        dw_add(ch, cl, p, e);
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float oh = __shfl_xor_sync(0xffffffffu, ch, o), ol = __shfl_xor_sync(0xffffffffu, cl, o);
+                    dw_add(ch, cl, oh, ol);
+                }
+                if (tid == 0) sC = make_float2(ch, cl);
+            }
+            __syncthreads();
+            const int32_t slot = ga.item_slot[w];
+            // (every kept item has a Gram block; should one lack it, its pairs
+            // take the direct sums below)
+            const float2 *Gp = ga.gbuf + ((size_t)(slot >= 0 ? slot >> 1 : 0) * (2 * WT) + (size_t)(slot & 1) * WT) * WT;
+            const float2 C = sC;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int lr = ty * 4 + i;
+                float uh = sUV[lr].x, ul = sUV[lr].y;
+                dw_add(uh, ul, C.x, C.y);
+                float4 g01 = make_float4(0.f, 0.f, 0.f, 0.f), g23 = g01;
+                if (slot >= 0) {
+                    g01 = *reinterpret_cast<const float4 *>(Gp + lr * WT + tx * 4);
+                    g23 = *reinterpret_cast<const float4 *>(Gp + lr * WT + tx * 4 + 2);
+                }
+                const float gv[4][2] = {{g01.x, g01.y}, {g01.z, g01.w}, {g23.x, g23.y}, {g23.z, g23.w}};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int lc = tx * 4 + j;
+                    if (!rok(lr) || !cok(lc) || (diag && lc == lr)) continue;
+                    const float sc = __fmul_rn(sSc[lr], sSc[WT + lc]);      // 2^(E_i + E_j - 13), exact
+                    const float gh = __fmul_rn(gv[j][0], sc), gl = __fmul_rn(gv[j][1], sc);
+                    const float2 V = sUV[WT + lc];
+                    float h = uh, l = ul;
+                    dw_add(h, l, V.x, V.y);
+                    dw_add(h, l, -gh, -gl);
+                    // the Gram form's error is about 2^-46 of the addends' size:
+                    // where they cancel to under a quarter of it, take the
+                    // direct sum of squared differences instead
+                    const float M = fabsf(uh) + fabsf(V.x) + fabsf(gh);
+                    if (slot < 0 || !(__fmul_rn(h, 4.0f) >= M))
+                        direct_d2(X + (row0 + lr) * d, X + (col0 + lc) * d, d, h, l);
+                    S[i][j] = h;
+                    E[i][j] = l;
+                }
+            }
+        } else
         for (int t0 = 0; t0 < d; t0 += WDC) {
             __syncthreads();
 #pragma unroll
@@ -668,7 +795,7 @@ __global__ void k_shift_dw(const unsigned long long *__restrict__ nnbits, int64_
 __global__ void k_weights_reduce(const unsigned long long *__restrict__ nnbits, int64_t n, int64_t T,
                                  double inv_sigma, int include_self, const uint8_t *__restrict__ flags,
                                  const float2 *__restrict__ rpart, const float2 *__restrict__ cpart,
-                                 double *__restrict__ omega) {
+                                 double *__restrict__ omega, double *__restrict__ part64) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     const int64_t I = r / WT, c = r - I * WT;
@@ -682,9 +809,25 @@ __global__ void k_weights_reduce(const unsigned long long *__restrict__ nnbits, 
             if (flags[w]) dw_add(h, l, rpart[w * WT + c].x, rpart[w * WT + c].y);
         }
     }
+    if (part64) {                 // sharded call: this rank's share, combined across ranks first
+        part64[r] = __dadd_rn((double)h, (double)l);
+        return;
+    }
     float fh, fl;
     split_shift(nnbits, r, n, inv_sigma, fh, fl);
     double w2 = __dmul_rn(exp(-__dadd_rn((double)fh, (double)fl)), __dadd_rn((double)h, (double)l));
+    if (include_self) w2 = __dadd_rn(w2, 1.0);
+    omega[r] = w2;
+}
+
+// Sharded call: omega_r from the sum over the ranks of their shares.
+__global__ void k_weights_finish(const unsigned long long *__restrict__ nnbits, int64_t n, double inv_sigma,
+                                 int include_self, const double *__restrict__ part64, double *__restrict__ omega) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    float fh, fl;
+    split_shift(nnbits, r, n, inv_sigma, fh, fl);
+    double w2 = __dmul_rn(exp(-__dadd_rn((double)fh, (double)fl)), part64[r]);
     if (include_self) w2 = __dadd_rn(w2, 1.0);
     omega[r] = w2;
 }
@@ -788,7 +931,8 @@ size_t weights_sym_bytes(int64_t n, int32_t d) {
 cudaError_t weights_launch_sym(const float *X, int64_t n, int32_t d, double sigma, int include_self,
                                const unsigned long long *nnbits, double *omega, void *part,
                                unsigned long long *tile_counts, const uint8_t *need, cudaEvent_t *kev,
-                               cudaStream_t s) {
+                               cudaStream_t s, const Shard *sh, double *part64, OmegaGram *og, uint32_t *status,
+                               uint64_t wait_cycles) {
     static const ExpTable tab = make_exp_table();
     const double is = 1.0 / sigma;
     const float is_h = (float)is;
@@ -804,13 +948,31 @@ cudaError_t weights_launch_sym(const float *X, int64_t n, int32_t d, double sigm
     k_tile_bounds<<<(unsigned)T, 64, 0, ISO_S(s)>>>(X, n, d, P.shdw, nullptr, P.cen, P.rad, P.msh);
     k_tile_pair_skip<false><<<(unsigned)(num_sms() * 8), 256, 0, ISO_S(s)>>>(P.cen, P.rad, P.msh, d, T, items, nullptr,
                                                                             is_h, zskip, shrink, need, P.tskip);
+    cudaError_t err;
+    // sharded: the items of other ranks hold nothing here
+    if (sh && (err = cudaMemsetAsync(P.flags, 0, (size_t)items, s))) return err;
     if (kev) record_event(kev[0], s);
-    k_weights_sym<false><<<grid, TPB, 0, ISO_S(s)>>>(X, n, d, P.shdw, is_h, is_l, tab, zskip, shrink, T, items, nullptr,
-                                                     nullptr, P.tskip, need ? 1 : 0, P.flags, P.rpart, P.cpart,
-                                                     tile_counts);
+    if (og && need) {
+        // the kept tile pairs' Gram on the tensor cores, then the terms
+        if ((err = omega_gram_launch(*og, X, n, d, P.cen, P.tskip, status, wait_cycles, s))) return err;
+        const GramArgs ga{og->gbuf, og->item_slot, og->yh, og->yl, og->rexp, og->rnorm, P.cen};
+        k_weights_sym<false, true><<<grid, TPB, 0, ISO_S(s)>>>(X, n, d, P.shdw, is_h, is_l, tab, zskip, shrink, T,
+                                                               items, nullptr, nullptr, P.tskip, 1, P.flags, P.rpart,
+                                                               P.cpart, tile_counts, sh ? sh->rank : 0,
+                                                               sh ? sh->world : 1, ga);
+    } else {
+        k_weights_sym<false><<<grid, TPB, 0, ISO_S(s)>>>(X, n, d, P.shdw, is_h, is_l, tab, zskip, shrink, T, items,
+                                                         nullptr, nullptr, P.tskip, need ? 1 : 0, P.flags, P.rpart,
+                                                         P.cpart, tile_counts, sh ? sh->rank : 0, sh ? sh->world : 1,
+                                                         GramArgs{});
+    }
     if (kev) record_event(kev[1], s);
     k_weights_reduce<<<(unsigned)ceil_div(n, 256), 256, 0, ISO_S(s)>>>(nnbits, n, T, is, include_self, P.flags,
-                                                                      P.rpart, P.cpart, omega);
+                                                                      P.rpart, P.cpart, omega, sh ? part64 : nullptr);
+    if (sh) {
+        if ((err = shard_allreduce(*sh, part64, n, ISOCLUST_REDUCE_SUM_F64, s))) return err;
+        k_weights_finish<<<(unsigned)ceil_div(n, 256), 256, 0, ISO_S(s)>>>(nnbits, n, is, include_self, part64, omega);
+    }
     return cudaGetLastError();
 }
 
@@ -849,7 +1011,7 @@ cudaError_t weights_launch_sym_sets(const float *Xp, int64_t n_pad, int32_t d, d
         // pair screen would cost more than the double-word work it saves)
         k_weights_sym<true><<<grid, TPB, 0, ISO_S(s)>>>(Xp, n_pad, d, P.shdw, is_h, is_l, tab, zskip, shrink, 0, nitems,
                                                         witems, tile_valid, P.tskip, 1, P.flags, P.rpart, P.cpart,
-                                                        tile_counts);
+                                                        tile_counts, 0, 1, GramArgs{});
         if (kev) record_event(kev[1], s);
     }
     k_weights_reduce_sets<<<(unsigned)ceil_div(n_pad, 256), 256, 0, ISO_S(s)>>>(

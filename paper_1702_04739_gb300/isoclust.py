@@ -24,8 +24,17 @@ PREC_AUTO, PREC_FP64, PREC_FP32, PREC_BF16_TC = 0, 1, 2, 3
 STATUS = {
     0: "ISOCLUST_OK", 1: "ISOCLUST_ERR_INVALID_ARG", 2: "ISOCLUST_ERR_K_GT_N", 3: "ISOCLUST_ERR_NONFINITE",
     4: "ISOCLUST_ERR_OOM", 5: "ISOCLUST_ERR_CUDA", 6: "ISOCLUST_ERR_TIMEOUT", 7: "ISOCLUST_ERR_NO_SOLUTION",
-    8: "ISOCLUST_ERR_INTERNAL",
+    8: "ISOCLUST_ERR_INTERNAL", 9: "ISOCLUST_ERR_COMM",
 }
+REDUCE_MIN_U64, REDUCE_SUM_F64 = 0, 1
+# int32 allreduce(void *ctx, void *buf, int64 count, int32 op, void *stream)
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                ctypes.c_void_p)
+
+
+class Comm(ctypes.Structure):
+    _fields_ = [("rank", ctypes.c_int32), ("world", ctypes.c_int32), ("allreduce", ALLREDUCE_FN),
+                ("ctx", ctypes.c_void_p)]
 
 
 class IsoclustError(RuntimeError):
@@ -77,6 +86,8 @@ def load(build_if_missing: bool = True):
         lib.isoclust_tree_isoperimetric.argtypes = [_I64, _P, _P, _P, _P, _I32, _P, _P, _P, _P, _P]
         lib.isoclust_cluster.restype = ctypes.c_int
         lib.isoclust_cluster.argtypes = [_P, _I64, _I32, _I32, _I32, _D, _P, _P, _P, _P, _P]
+        lib.isoclust_cluster_sharded.restype = ctypes.c_int
+        lib.isoclust_cluster_sharded.argtypes = [_P, _I64, _I32, _I32, _I32, _D, _P, _P, _P, _P, _P, _P]
         lib.isoclust_cluster_detail.restype = ctypes.c_int
         lib.isoclust_cluster_detail.argtypes = [_P, _I64, _I32, _I32, _I32, _D, _P, _P, _P, _P,
                                                 _P, _P, _P, _P, _P, _P, _P, _P, _P]
@@ -102,6 +113,8 @@ def load(build_if_missing: bool = True):
         lib.isoclust_last_batched_graph_mode.argtypes = []
         lib.isoclust_set_batched_graphs.restype = ctypes.c_int
         lib.isoclust_set_batched_graphs.argtypes = [ctypes.c_int32]
+        lib.isoclust_set_omega_gram.restype = ctypes.c_int
+        lib.isoclust_set_omega_gram.argtypes = [ctypes.c_int32]
         lib.isoclust_set_test_stalled_wait.restype = ctypes.c_int
         lib.isoclust_set_test_stalled_wait.argtypes = [ctypes.c_int32]
         lib.isoclust_last_omega_tiles.restype = None
@@ -210,6 +223,39 @@ def cluster_into(X: torch.Tensor, k: int, sigma: float, labels, residual, ik, o:
     xp, n, d, dt = _points(X)
     _check(lib.isoclust_cluster(xp, n, d, dt, int(k), float(sigma), _opts_ptr(o), labels.data_ptr(),
                                 residual.data_ptr(), ik.data_ptr(), _stream(X.device)))
+
+
+def cluster_sharded(X: torch.Tensor, k: int, sigma: float, rank: int, world: int, allreduce,
+                    o: Opts | None = None):
+    """isoclust_cluster_sharded: the pairwise work split across `world`
+    processes (this one is `rank`); every rank passes the same X and gets the
+    same (labels, residual, i_k).  allreduce(buf, count, op, stream) reduces
+    `count` elements at device address `buf` in place across the ranks
+    (op REDUCE_MIN_U64 or REDUCE_SUM_F64), ordered on `stream`; it raises
+    on failure.  See sharded.torch_allreduce for one over torch.distributed."""
+    lib = load()
+    xp, n, d, dt = _points(X)
+    dev = X.device
+    labels = torch.empty(n, dtype=torch.int32, device=dev)
+    residual = torch.empty(n, dtype=torch.uint8, device=dev)
+    ik = torch.empty(1, dtype=torch.float64, device=dev)
+    failure = []
+
+    def cb(ctx, buf, count, op, stream):
+        try:
+            allreduce(int(buf), int(count), int(op), int(stream or 0))
+            return 0
+        except Exception as e:      # reported as ISOCLUST_ERR_COMM; the exception is re-raised below
+            failure.append(e)
+            return 1
+    fn = ALLREDUCE_FN(cb)
+    comm = Comm(int(rank), int(world), fn, None)
+    code = lib.isoclust_cluster_sharded(xp, n, d, dt, int(k), float(sigma), _opts_ptr(o), ctypes.byref(comm),
+                                        labels.data_ptr(), residual.data_ptr(), ik.data_ptr(), _stream(dev))
+    if failure:
+        raise IsoclustError(code, f"all-reduce callback failed: {failure[0]!r}") from failure[0]
+    _check(code)
+    return labels, residual, ik
 
 
 def cluster_detail(X: torch.Tensor, k: int, sigma: float, o: Opts | None = None) -> dict:
@@ -382,6 +428,12 @@ def set_batched_graphs(enable: bool) -> None:
     """Allow (True, the default) or forbid CUDA-graph capture and replay of
     repeated batched calls (isoclust_set_batched_graphs)."""
     _check(load().isoclust_set_batched_graphs(int(bool(enable))))
+
+
+def set_omega_gram(on: bool) -> None:
+    """eq. omega's Gram on the tensor cores (True, the default) or double-word
+    sums of squared differences on the CUDA cores (isoclust_set_omega_gram)."""
+    _check(load().isoclust_set_omega_gram(int(bool(on))))
 
 
 def set_test_stalled_wait(on: bool) -> None:

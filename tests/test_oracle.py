@@ -470,3 +470,40 @@ def test_parent_flow_matches_the_pipeline(oracle_lib):
     assert (pf == c["phi_par"]).all()
     v = int(np.nonzero(c["parent"] >= 0)[0][0])
     assert pf[v] == math.exp(-math.sqrt(oracle_lib.d2(X, v, int(c["parent"][v]))) / 0.7)
+
+
+def test_min_foreign_is_nearest_neighbour_then_boruvka_equals_prim(oracle_lib):
+    """With every point its own component the step gives the nearest
+    neighbours; Boruvka rounds built on it give Prim's tree."""
+    rng = np.random.default_rng(23)
+    X = rng.normal(size=(70, 3))
+    n = X.shape[0]
+    rows = np.arange(n)
+    j, d2 = oracle_lib.min_foreign(X, np.arange(n), rows)
+    nn, nd = oracle_lib.nn_rows(X, rows)
+    assert (j == nn).all() and (d2 == nd).all()
+    comp = np.arange(n)
+    edges = set()
+    while len(set(comp.tolist())) > 1:
+        j, d2 = oracle_lib.min_foreign(X, comp, rows)
+        best = {}
+        for i in range(n):
+            key = (d2[i], min(i, j[i]), max(i, j[i]))
+            if comp[i] not in best or key < best[comp[i]]:
+                best[comp[i]] = key
+        for _, a, b in best.values():
+            edges.add((a, b))
+        # merge along the chosen edges
+        p = {c: c for c in set(comp.tolist())}
+
+        def f(x):
+            while p[x] != x:
+                x = p[x]
+            return x
+        for _, a, b in best.values():
+            ra, rb = f(comp[a]), f(comp[b])
+            if ra != rb:
+                p[max(ra, rb)] = min(ra, rb)
+        comp = np.array([f(c) for c in comp])
+    eu, ev, _, _, _ = oracle_lib.mst_prim(X)
+    assert edges == set(zip(eu.tolist(), ev.tolist()))
