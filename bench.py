@@ -205,11 +205,13 @@ def omega_roofline(torch, dev, prof, n_pairs_alg, d, workload, sets=False):
     sms, alu_peak = _alu_peak(torch, dev, peaks)
     w_ms = statistics.mean(p["omega_kernel_ms"] or p["weights_ms"] for p in prof)
     tiles, tiles_dw, sym = prof[-1]["omega_tiles"], prof[-1]["omega_tiles_dw"], prof[-1]["omega_symmetric"]
+    alg_flop = n_pairs_alg * (2.0 * d + 25.0)
+    if sym == 3:
+        return omega_gram_roofline(prof, peaks, src, alu_peak, sms, w_ms, tiles_dw, d, alg_flop)
     screen_ops = 0.0 if (sym == 2 or sets) else 2.0 * d + (12.0 if sym else 8.0)
     dw_ops = (18.75 * d + 95.0) if (sym or sets) else (21.0 * d + 75.0)
     work = tiles * 4096.0 * screen_ops + tiles_dw * 4096.0 * dw_ops
     achieved = work / (w_ms / 1000.0) / 1e12
-    alg_flop = n_pairs_alg * (2.0 * d + 25.0)
     alg = alg_flop / (w_ms / 1000.0) / 1e12
     return {
         "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
@@ -229,6 +231,42 @@ def omega_roofline(torch, dev, prof, n_pairs_alg, d, workload, sets=False):
                                 f"this unit (native FP64 is {FP64_NOMINAL_TFLOPS} TFLOP/s nominal, "
                                 f"{alg / FP64_NOMINAL_TFLOPS:.1f}x of it)"},
     }
+
+
+def omega_gram_roofline(prof, peaks, src, alu_peak, sms, sweep_ms, items, d, alg_flop):
+    """omega with the Gram on the tensor cores: two kernels.  The Gram kernel
+    (tensor-bound: 34 BF16 digit-plane products of 2 x 128 x 64 x d_pad
+    flop per 128 x 64 block, executed) and the sweep that reads it
+    (ALU-bound: per kept 64 x 64 tile pair, 4096 pairs x ~150 FP32-pipe
+    instructions (d2 from G, root, exp, accumulation) plus 128 cross terms of
+    21 d + 2400 lane instructions; pairs that fall back to direct sums are
+    not counted).  The line's roofline is the slower of the two."""
+    g_ms = statistics.mean(p["omega_gram_ms"] for p in prof)
+    blocks = prof[-1]["omega_gram_blocks"]
+    d_pad = -(-d // 64) * 64
+    tc_flop = blocks * 34 * 2.0 * 128 * 64 * d_pad
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    tc = tc_flop / (g_ms / 1000.0) / 1e12 if g_ms > 0 else 0.0
+    sw_ops = items * (4096.0 * 150.0 + 128.0 * (21.0 * d + 2400.0))
+    sw = sw_ops / (sweep_ms / 1000.0) / 1e12 if sweep_ms > 0 else 0.0
+    gram_k = {"kernel": "k_oz_gram (omega Gram, tcgen05 BF16 digit planes)", "bound": "tensor", "kernel_ms": g_ms,
+              "achieved": tc, "peak": bf16, "unit": "TFLOP/s", "frac": tc / bf16, "blocks": blocks}
+    sweep_k = {"kernel": "k_weights_sym<GRAM> (omega terms from the Gram, double-word FP32)", "bound": "alu",
+               "kernel_ms": sweep_ms, "achieved": sw, "peak": alu_peak, "unit": "TFLOP/s", "frac": sw / alu_peak}
+    top, other = (gram_k, sweep_k) if g_ms >= sweep_ms else (sweep_k, gram_k)
+    both_ms = g_ms + sweep_ms
+    alg = alg_flop / (both_ms / 1000.0) / 1e12
+    out = dict(top, traffic=None,
+               note=f"omega's Gram on the tensor cores: the Gram kernel {g_ms:.2f} ms ({blocks} blocks of 128 x 64, 34 "
+                    f"digit-plane MMAs per 16 dimensions, executed flop over the measured BF16 peak, {src}) and the "
+                    f"sweep reading it {sweep_ms:.2f} ms (FP32-pipe instructions of the algorithm as built over "
+                    f"{sms} SMs x 128 lanes x max SM clock); the line reports the slower one",
+               other_kernel=other,
+               algorithmic={"achieved": alg, "unit": "FP64-equivalent TFLOP/s", "peak": None,
+                            "flop_per_launch": alg_flop,
+                            "note": "the method's work (eq. omega over all pairs, (2d + 25) FP64-equivalent flop each) "
+                                    "over both kernels' time; no measured peak exists in this unit"})
+    return out
 
 
 def mst_summary(prof, n_pairs_alg, pad_pairs_exe, d, sweep_variant):

@@ -412,9 +412,16 @@ void isoclust_last_omega_tiles(int64_t *tiles3);
 /* Device time (milliseconds, CUDA events on the call's stream around its
  * launch) of the dominant pair kernel of the last call on this host thread:
  * the symmetric omega kernel after isoclust_cluster / _detail / _batched (0
- * when it did not run), the pair-sum kernel of dOmega after
- * isoclust_ik_backward. */
+ * when it did not run; with the Gram on the tensor cores, the sweep that
+ * reads it), the pair-sum kernel of dOmega after isoclust_ik_backward. */
 double isoclust_last_omega_kernel_ms(void);
+
+/* Device time (milliseconds, CUDA events on the call's stream) of the
+ * tensor-core Gram kernel of omega in the last one-set call on this host
+ * thread (isoclust_set_omega_gram), 0 when it did not run; *blocks (may be
+ * NULL) gets its number of 128 x 64 blocks (each 34 BF16 digit-plane MMA
+ * products of 2 x 128 x 64 x d_pad flop, d_pad = d rounded up to 64). */
+double isoclust_last_omega_gram_ms(int64_t *blocks);
 
 /* Tile variant of the tensor-core Boruvka sweep (Section 3.5's MST step
  * with the tiled Gram sweep): bit 0 set = 32-column candidate blocks (else
@@ -444,14 +451,18 @@ int32_t isoclust_last_sweep_variant(void);
 int32_t isoclust_last_batched_graph_mode(void);
 
 /* Arithmetic of eq. omega's pair sums in one-set calls (F32 input, sm_103,
- * alpha = 0, full-graph omega): 1 (the default) forms each kept tile pair's
- * Gram <y_i, y_j> of the tile-centred points exactly on the tensor cores (7
- * balanced base-256 digit planes per row, BF16 products summed exactly in
- * FP32 accumulators) and the rest of d2 and the terms in double-word FP32;
- * 0 forms d2 by double-word FP32 sums of squared differences.  Both keep
- * d2 to about 2^-46; omega agrees to within the library's error bound, not
- * bit for bit.  Process-wide; other values -> INVALID_ARG. */
-isoclust_status isoclust_set_omega_gram(int32_t on);
+ * alpha = 0, full-graph omega).  Tensor-core Gram: each kept tile pair's
+ * Gram <y_i, y_j> of the tile-centred points is formed exactly on the tensor
+ * cores (7 balanced base-256 digit planes per row, BF16 products summed
+ * exactly in FP32 accumulators), the rest of d2 and the terms in double-word
+ * FP32, and pairs whose Gram form cancels (its parts more than twice d2)
+ * take the double-word sum of squared differences.  Otherwise every pair's
+ * d2 is that double-word sum.  Both keep d2 to about 2^-46 relative; omega
+ * agrees to within the library's error bound, not bit for bit.
+ * mode -1 (the default): the Gram on the tensor cores for rows longer than
+ * 128 dimensions; 1: always; 0: never.  Process-wide; other values ->
+ * INVALID_ARG. */
+isoclust_status isoclust_set_omega_gram(int32_t mode);
 
 /* Whether repeated batched calls may capture and replay CUDA graphs: 1 (the
  * default) allows it, 0 keeps every later batched call kernel by kernel.

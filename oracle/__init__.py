@@ -11,6 +11,7 @@ Functions and the passages they follow:
   mst_prim     Algorithm 3 (Prim with min-reduction), key (d2, min, max)
   mst_kruskal  textbook Kruskal over all pairs (self-check of mst_prim)
   nn_rows      exact nearest neighbour (smallest key) of sampled rows
+  min_foreign  one Boruvka step: each row's smallest-key edge to another component
   weights      eq. omega and eq. potential
   flow         eq. phi
   parent_flow  eq. phi on the parent edge of every vertex of a rooted tree
@@ -74,6 +75,8 @@ def _load():
             lib.oracle_mst_kruskal.argtypes = [_ptr, _i64, _i32, _ptr, _ptr, _ptr]
             lib.oracle_nn_rows.restype = ctypes.c_int
             lib.oracle_nn_rows.argtypes = [_ptr, _i64, _i32, _ptr, _i64, _ptr, _ptr]
+            lib.oracle_min_foreign.restype = ctypes.c_int
+            lib.oracle_min_foreign.argtypes = [_ptr, _i64, _i32, _ptr, _ptr, _i64, _ptr, _ptr]
             lib.oracle_weights.restype = ctypes.c_int
             lib.oracle_weights.argtypes = [_ptr, _i64, _i32, _dbl, _dbl, _i32, _ptr, _i64, _ptr, _ptr]
             lib.oracle_bfs_order.restype = ctypes.c_int
@@ -166,6 +169,16 @@ def nn_rows(X, rows):
     nn = np.zeros(rows.size, np.int32); nd = np.zeros(rows.size, np.float64)
     _load().oracle_nn_rows(_p(X), X.shape[0], X.shape[1], _p(rows), rows.size, _p(nn), _p(nd))
     return nn, nd
+
+
+def min_foreign(X, comp, rows):
+    """For each row, (j, d2) of its smallest-key edge to another component."""
+    X = _X(X)
+    comp = np.ascontiguousarray(np.asarray(comp, dtype=np.int32))
+    rows = np.ascontiguousarray(np.asarray(rows, dtype=np.int64))
+    j = np.zeros(rows.size, np.int32); d2v = np.zeros(rows.size, np.float64)
+    _load().oracle_min_foreign(_p(X), X.shape[0], X.shape[1], _p(comp), _p(rows), rows.size, _p(j), _p(d2v))
+    return j, d2v
 
 
 def weights(X, sigma: float, alpha: float = 0.0, include_self: bool = False, rows=None):

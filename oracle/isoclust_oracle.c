@@ -202,6 +202,29 @@ int oracle_nn_rows(const double *X, int64_t n, int32_t d, const int64_t *rows, i
     return 0;
 }
 
+/* One step of Boruvka's method (Section 3.5's MST, the rounds that replace
+ * Prim's loop): for each listed row i, its smallest-key edge (d2, min, max)
+ * to a point of another component (comp[j] != comp[i]); -1 / INFINITY when
+ * every point is in i's component. */
+int oracle_min_foreign(const double *X, int64_t n, int32_t d, const int32_t *comp,
+                       const int64_t *rows, int64_t nrows, int32_t *out_j, double *out_d2)
+{
+#pragma omp parallel for num_threads(g_threads) schedule(dynamic, 1)
+    for (int64_t r = 0; r < nrows; ++r) {
+        int64_t i = rows[r];
+        int64_t best = -1;
+        double bd = INFINITY;
+        for (int64_t j = 0; j < n; ++j) {
+            if (comp[j] == comp[i]) continue;
+            double c = oracle_d2(X, n, d, i, j);
+            if (best < 0 || key_less(c, i, j, bd, i, best)) { best = j; bd = c; }
+        }
+        out_j[r] = (int32_t)best;
+        out_d2[r] = bd;
+    }
+    return 0;
+}
+
 /* ------------------------------------------------------------------ */
 /* eq. phi: phi(x_i,x_j) = exp(-||x_i - x_j||_2 / sigma)                */
 static double flow_of_d2(double d2, double sigma)

@@ -24,6 +24,10 @@ cudaError_t weights_launch_sym(const float *X, int64_t n, int32_t d, double sigm
                                OmegaGram *og = nullptr, uint32_t *status = nullptr, uint64_t wait_cycles = 0);
 float omega_zskip(int64_t n);
 constexpr size_t SYM_PART_LIMIT = size_t(16) << 30;   // symmetric sweep up to 16 GiB of partials
+// the omega Gram goes to the tensor cores by default for rows longer than
+// this (measured: 3.3x faster on 50,000 x 4,096; slower at d = 64, where the
+// per-pair cross terms and cancelling pairs outweigh the d-long sums)
+constexpr int32_t OMEGA_GRAM_MIN_D = 128;
 size_t weights_sym_sets_bytes(int64_t n_pad, int64_t nitems, int32_t d);
 cudaError_t weights_launch_sym_sets(const float *Xp, int64_t n_pad, int32_t d, double sigma, int include_self,
                                     const unsigned long long *nnbits, double *omega, void *part, const int2 *witems,
@@ -50,6 +54,8 @@ static thread_local int64_t g_prof_cnt[4] = {0, 0, 0, 0};
 static thread_local unsigned long long g_prof_tiles[2] = {0, 0};
 static thread_local int g_prof_sym = 0;
 static thread_local double g_prof_omega_kernel_ms = 0.0;
+static thread_local double g_prof_omega_gram_ms = 0.0;
+static thread_local int64_t g_prof_omega_gram_blocks = 0;
 
 void set_error(const char *fmt, ...) {
     va_list ap;
@@ -305,7 +311,7 @@ static isoclust_status check_points(const void *X, int64_t n, int32_t d, int32_t
 }
 
 struct Events {
-    cudaEvent_t e[10] = {};
+    cudaEvent_t e[12] = {};
     bool ok = false;
     Events() {
         ok = true;
@@ -362,7 +368,7 @@ static int g_last_graph_mode = 0;                  // 0 eager, 1 captured, 2 rep
 
 static std::atomic<int> g_graphs_on{1};          // isoclust_set_batched_graphs
 static std::atomic<int> g_stall_test{0};         // isoclust_set_test_stalled_wait
-static std::atomic<int> g_omega_gram{1};         // isoclust_set_omega_gram
+static std::atomic<int> g_omega_gram{-1};        // isoclust_set_omega_gram (-1: by row length)
 static bool graphs_enabled() { return g_graphs_on.load(std::memory_order_relaxed) != 0; }
 
 struct Fnv {
@@ -447,8 +453,10 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
     const bool symmetric = permuted && o.alpha == 0.0 && o.omega_mode == ISOCLUST_OMEGA_FULL &&
                            weights_sym_bytes(n, d) <= SYM_PART_LIMIT;
     // eq. omega's Gram on the tensor cores (with the tensor-core screen)
-    const bool gram = symmetric && use_tc && g_omega_gram.load(std::memory_order_relaxed) != 0 &&
-                      ceil_div(n, 128) <= 65535;
+    int64_t gram_blocks = 0;
+    const int gram_mode = g_omega_gram.load(std::memory_order_relaxed);
+    const bool gram = symmetric && use_tc && ceil_div(n, 128) <= 65535 &&
+                      (gram_mode == 1 || (gram_mode < 0 && d > OMEGA_GRAM_MIN_D));
     auto carve = [&](Arena &A, MstScratch &M, TreeScratch &TS, double **phi, double **om, double **pp, double **omtmp,
                      uint32_t **status) {
         *status = A.take<uint32_t>(4);
@@ -556,6 +564,7 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
                     ISO_CUDA(weights_launch_sym(P.Xp, n, d, sigma, o.include_self, P.nnp, P.omp, P.sym, P.tiles,
                                                 use_tc ? P.need : nullptr, ev.ok ? ev.e + 8 : nullptr, s, sh,
                                                 P.part64, gram ? &og : nullptr, status, o.spin_limit));
+                    gram_blocks = og.nblocks;
                 }
                 else
                     ISO_CUDA(weights_launch(P.Xp, n, d, dtype, false, sigma, o.alpha, o.include_self, P.nnp, P.omp,
@@ -612,7 +621,10 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
     g_prof_tiles[0] = g_prof_tiles[1] = 0;
     if (permuted) ISO_CUDA(cudaMemcpy(g_prof_tiles, P.tiles, sizeof(g_prof_tiles), cudaMemcpyDeviceToHost));
     g_prof_sym = symmetric ? (gram ? 3 : (use_tc ? 2 : 1)) : 0;
-    g_prof_omega_kernel_ms = symmetric ? ev.ms(8, 9) : 0.0;
+    // the symmetric sweep kernel (after the Gram kernel when that ran), and the Gram kernel
+    g_prof_omega_kernel_ms = symmetric ? (gram ? ev.ms(11, 9) : ev.ms(8, 9)) : 0.0;
+    g_prof_omega_gram_ms = (symmetric && gram) ? ev.ms(10, 11) : 0.0;
+    g_prof_omega_gram_blocks = (symmetric && gram) ? gram_blocks : 0;
     return map_status(fin, false);
 }
 
@@ -999,6 +1011,8 @@ static isoclust_status cluster_sets_impl(const void *X, const int64_t *offsets, 
     ISO_CUDA(cudaMemcpy(g_prof_tiles, B.tiles, sizeof(g_prof_tiles), cudaMemcpyDeviceToHost));
     g_prof_sym = 1;
     g_prof_omega_kernel_ms = nitems > 0 ? E.ms(8, 9) : 0.0;
+    g_prof_omega_gram_ms = 0.0;
+    g_prof_omega_gram_blocks = 0;
     return map_status(fin, false);
 }
 
@@ -1047,6 +1061,11 @@ void isoclust_last_profile(double *t_ms6, int64_t *counts4) {
 
 double isoclust_last_omega_kernel_ms(void) { return g_prof_omega_kernel_ms; }
 
+double isoclust_last_omega_gram_ms(int64_t *blocks) {
+    if (blocks) *blocks = g_prof_omega_gram_blocks;
+    return g_prof_omega_gram_ms;
+}
+
 isoclust_status isoclust_set_sweep_variant(int32_t variant) {
     if (variant < -1 || variant > 3) return fail(ISOCLUST_ERR_INVALID_ARG, "sweep variant %d is not in -1..3", variant);
     tc_force_variant(variant);
@@ -1057,9 +1076,9 @@ int32_t isoclust_last_sweep_variant(void) { return tc_last_variant(); }
 
 int32_t isoclust_last_batched_graph_mode(void) { return g_last_graph_mode; }
 
-isoclust_status isoclust_set_omega_gram(int32_t on) {
-    if (on != 0 && on != 1) return fail(ISOCLUST_ERR_INVALID_ARG, "on must be 0 or 1");
-    g_omega_gram.store(on, std::memory_order_relaxed);
+isoclust_status isoclust_set_omega_gram(int32_t mode) {
+    if (mode < -1 || mode > 1) return fail(ISOCLUST_ERR_INVALID_ARG, "mode must be -1, 0 or 1");
+    g_omega_gram.store(mode, std::memory_order_relaxed);
     return ISOCLUST_OK;
 }
 
@@ -1179,6 +1198,8 @@ isoclust_status isoclust_ik_backward(const void *X, int64_t n, int32_t d, int32_
     for (int i = 0; i < 6; ++i) g_prof_ms[i] = 0.0;
     g_prof_ms[4] = ev.ms(0, 1);
     g_prof_omega_kernel_ms = ev.ms(8, 9);
+    g_prof_omega_gram_ms = 0.0;
+    g_prof_omega_gram_blocks = 0;
     if (hst & DEV_NEGATIVE) return fail(ISOCLUST_ERR_INVALID_ARG, "a label 0..k-1 has no points or no positive omega");
     return map_status(hst, true);
 }

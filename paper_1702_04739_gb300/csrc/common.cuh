@@ -109,8 +109,10 @@ struct OmegaGram {
     int64_t nblocks = 0;
 };
 size_t omega_gram_bytes(int64_t n, int32_t d);
+// kev (may be null): two events recorded around the Gram kernel
 cudaError_t omega_gram_launch(OmegaGram &G, const float *Xp, int64_t n, int32_t d, const float *cen,
-                              const uint8_t *tskip, uint32_t *err, uint64_t wait_cycles, cudaStream_t s);
+                              const uint8_t *tskip, uint32_t *err, uint64_t wait_cycles, cudaStream_t s,
+                              cudaEvent_t *kev = nullptr);
 
 // ---------------------------------------------------------------- helpers
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

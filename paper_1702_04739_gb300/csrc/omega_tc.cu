@@ -383,7 +383,8 @@ size_t omega_gram_bytes(int64_t n, int32_t d) {
 }
 
 cudaError_t omega_gram_launch(OmegaGram &G, const float *Xp, int64_t n, int32_t d, const float *cen,
-                              const uint8_t *tskip, uint32_t *err, uint64_t wait_cycles, cudaStream_t s) {
+                              const uint8_t *tskip, uint32_t *err, uint64_t wait_cycles, cudaStream_t s,
+                              cudaEvent_t *kev) {
     cudaError_t e;
     const int64_t T64 = ceil_div(n, 64), T128 = ceil_div(n, 128);
     const int64_t n_pad = T128 * 128;
@@ -421,7 +422,10 @@ cudaError_t omega_gram_launch(OmegaGram &G, const float *Xp, int64_t n, int32_t 
     // the Gram buffer: 128 x 64 double-words per block
     const size_t gbytes = (size_t)(nb > 0 ? nb : 1) * OZ_BM * OZ_BN * sizeof(float2);
     if (!(G.gbuf = (float2 *)gram_acquire(gbytes))) return cudaErrorMemoryAllocation;
-    if (nb == 0) return cudaGetLastError();
+    if (nb == 0) {
+        if (kev) { record_event(kev[0], s); record_event(kev[1], s); }
+        return cudaGetLastError();
+    }
     CUtensorMap mapA, mapB;
     if ((e = tc_map_bf16(&mapA, planes, (int64_t)OZ_S * n_pad, d_pad, OZ_BM))) return e;
     if ((e = tc_map_bf16(&mapB, planes, (int64_t)OZ_S * n_pad, d_pad, OZ_BN))) return e;
@@ -438,12 +442,14 @@ cudaError_t omega_gram_launch(OmegaGram &G, const float *Xp, int64_t n, int32_t 
     const unsigned grid = (unsigned)(nb < nsm ? nb : nsm);
     const long long lim = wait_cycles > 0 ? (long long)(wait_cycles < (1ull << 62) ? wait_cycles : (1ull << 62))
                                           : OZ_WAIT_CYCLES;
+    if (kev) record_event(kev[0], s);
     if (ares)
         k_oz_gram<true><<<grid, OZ_THREADS, oz_smem(true), ISO_S(s)>>>(mapA, mapB, n_pad, d_pad / OZ_BK, blocks, nb,
                                                                        G.gbuf, err, lim);
     else
         k_oz_gram<false><<<grid, OZ_THREADS, oz_smem(false), ISO_S(s)>>>(mapA, mapB, n_pad, d_pad / OZ_BK, blocks, nb,
                                                                          G.gbuf, err, lim);
+    if (kev) record_event(kev[1], s);
     return cudaGetLastError();
 }
 

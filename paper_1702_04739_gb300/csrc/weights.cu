@@ -382,27 +382,6 @@ struct GramArgs {
     const float *cen;            // tile centroids c_T
 };
 
-// Renormalised double-word sum of squared exact differences (the sweep's own
-// d2, for the pairs whose Gram form cancels).
-__device__ __forceinline__ void direct_d2(const float *__restrict__ a, const float *__restrict__ b, int d, float &S,
-                                          float &E) {
-    S = 0.f;
-    E = 0.f;
-    for (int t = 0; t < d; ++t) {
-        float s1, e1;
-        two_sum(a[t], -b[t], s1, e1);
-        const float p = __fmul_rn(s1, s1);
-        float q2 = __fmaf_rn(s1, s1, -p);
-        q2 = __fmaf_rn(__fadd_rn(s1, s1), e1, q2);
-        float hs, he;
-        two_sum(S, p, hs, he);
-        S = hs;
-        E = __fadd_rn(E, __fadd_rn(he, q2));
-        if ((t & 3) == 3) fast_two_sum(S, E, S, E);
-    }
-    fast_two_sum(S, E, S, E);
-}
-
 // Symmetric omega sweep: each unordered tile pair is screened in FP32 and,
 // if any of its terms can matter in either direction, evaluated once in
 // double-word arithmetic; the pair's d2 serves both omega_i and omega_j.
@@ -428,6 +407,7 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
     __shared__ float2 sUV[GRAM ? 2 * WT : 1];  // GRAM: |y|^2 +- 2 <y, D> of the rows of I, then of J
     __shared__ float sSc[GRAM ? 2 * WT : 1];   // GRAM: 2^(E - 7) of the rows of I, 2^(E - 6) of J
     __shared__ float2 sC;                      // GRAM: |D|^2
+    __shared__ float sMg[GRAM ? 2 * WT : 1];   // GRAM: |y|^2 + 2 |<y, D>| (+ |D|^2 for I): the parts' size
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     if (tid < 64) tab[tid] = tabv.t[tid];
@@ -547,54 +527,63 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
         if constexpr (GRAM) {
             // d2 = (|y_i|^2 + 2 <y_i, D> + |D|^2) + (|y_j|^2 - 2 <y_j, D>) - 2 G_ij, y = x - c_T,
             // D = c_I - c_J: the cross terms of the 64 rows of I (products 0..63)
-            // and of J (64..127), two threads per product
-            const int dp = tid >> 1, part = tid & 1;
-            const int64_t gr = dp < WT ? row0 + dp : col0 + (dp - WT);
-            float xh = 0.f, xl = 0.f;
-            if (!diag) {
-                const float *cI = ga.cen + I * d, *cJ = ga.cen + J * d;
-                const float *ryh = ga.yh + gr * d, *ryl = ga.yl + gr * d;
-                for (int t = part; t < d; t += 2) {
-                    float Dh, Dl;
-                    two_sum(cI[t], -cJ[t], Dh, Dl);
-                    const float a = ryh[t], al = ryl[t];
-                    float p, e;
-                    two_prod(a, Dh, p, e);
-                    e = __fmaf_rn(a, Dl, __fmaf_rn(al, Dh, e));
-                    dw_add(xh, xl, p, e);
-                }
-            }
+            // and of J (64..127); warp w takes products w, w + 8, ..., its lanes
+            // the dimensions (coalesced rows), folded in a fixed shuffle tree.
+            // Warp 0 also forms |D|^2.
             {
-                const float oh = __shfl_xor_sync(0xffffffffu, xh, 1), ol = __shfl_xor_sync(0xffffffffu, xl, 1);
-                dw_add(xh, xl, oh, ol);
-            }
-            if (part == 0) {
-                const float2 rn = ga.rnorm[gr];
-                float uh = rn.x, ul = rn.y;
-                const float sg = dp < WT ? 2.0f : -2.0f;
-                dw_add(uh, ul, __fmul_rn(sg, xh), __fmul_rn(sg, xl));
-                sUV[dp] = make_float2(uh, ul);
-                sSc[dp] = ldexpf(1.0f, ga.rexp[gr] - (dp < WT ? 7 : 6));
-            }
-            if (tid < 32) {
-                float ch = 0.f, cl = 0.f;
-                if (!diag) {
-                    const float *cI = ga.cen + I * d, *cJ = ga.cen + J * d;
-                    for (int t = tid; t < d; t += 32) {
-                        float Dh, Dl;
-                        two_sum(cI[t], -cJ[t], Dh, Dl);
-                        float p, e;
-                        two_prod(Dh, Dh, p, e);
-                        e = __fmaf_rn(__fadd_rn(Dh, Dh), Dl, e);
-                        dw_add(ch, cl, p, e);
+                const int lane = tid & 31, wq = tid >> 5;
+                const float *cI = ga.cen + I * d, *cJ = ga.cen + J * d;
+                for (int dp = wq; dp < 2 * WT; dp += TPB / 32) {
+                    const int64_t gr = dp < WT ? row0 + dp : col0 + (dp - WT);
+                    float xh = 0.f, xl = 0.f;
+                    if (!diag) {
+                        const float *ryh = ga.yh + gr * d, *ryl = ga.yl + gr * d;
+                        for (int t = lane; t < d; t += 32) {
+                            float Dh, Dl;
+                            two_sum(cI[t], -cJ[t], Dh, Dl);
+                            const float a = ryh[t], al = ryl[t];
+                            float p, e;
+                            two_prod(a, Dh, p, e);
+                            e = __fmaf_rn(a, Dl, __fmaf_rn(al, Dh, e));
+                            dw_add(xh, xl, p, e);
+                        }
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) {
+                            const float oh = __shfl_xor_sync(0xffffffffu, xh, o);
+                            const float ol = __shfl_xor_sync(0xffffffffu, xl, o);
+                            dw_add(xh, xl, oh, ol);
+                        }
+                    }
+                    if (lane == 0) {
+                        const float2 rn = ga.rnorm[gr];
+                        float uh = rn.x, ul = rn.y;
+                        const float sg = dp < WT ? 2.0f : -2.0f;
+                        dw_add(uh, ul, __fmul_rn(sg, xh), __fmul_rn(sg, xl));
+                        sUV[dp] = make_float2(uh, ul);
+                        sMg[dp] = __fadd_rn(rn.x, fabsf(__fmul_rn(2.0f, xh)));
+                        sSc[dp] = ldexpf(1.0f, ga.rexp[gr] - (dp < WT ? 7 : 6));
                     }
                 }
+                if (wq == 0) {
+                    float ch = 0.f, cl = 0.f;
+                    if (!diag) {
+                        for (int t = lane; t < d; t += 32) {
+                            float Dh, Dl;
+                            two_sum(cI[t], -cJ[t], Dh, Dl);
+                            float p, e;
+                            two_prod(Dh, Dh, p, e);
+                            e = __fmaf_rn(__fadd_rn(Dh, Dh), Dl, e);
+                            dw_add(ch, cl, p, e);
+                        }
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const float oh = __shfl_xor_sync(0xffffffffu, ch, o), ol = __shfl_xor_sync(0xffffffffu, cl, o);
-                    dw_add(ch, cl, oh, ol);
+                        for (int o = 16; o > 0; o >>= 1) {
+                            const float oh = __shfl_xor_sync(0xffffffffu, ch, o);
+                            const float ol = __shfl_xor_sync(0xffffffffu, cl, o);
+                            dw_add(ch, cl, oh, ol);
+                        }
+                    }
+                    if (lane == 0) sC = make_float2(ch, cl);
                 }
-                if (tid == 0) sC = make_float2(ch, cl);
             }
             __syncthreads();
             const int32_t slot = ga.item_slot[w];
@@ -602,6 +591,7 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
             // take the direct sums below)
             const float2 *Gp = ga.gbuf + ((size_t)(slot >= 0 ? slot >> 1 : 0) * (2 * WT) + (size_t)(slot & 1) * WT) * WT;
             const float2 C = sC;
+            unsigned fb = 0u;                  // pairs whose Gram form cancels (bit 4i + j)
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int lr = ty * 4 + i;
@@ -626,11 +616,50 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
                     // the Gram form's error is about 2^-46 of the addends' size:
                     // where they cancel to under a quarter of it, take the
                     // direct sum of squared differences instead
-                    const float M = fabsf(uh) + fabsf(V.x) + fabsf(gh);
-                    if (slot < 0 || !(__fmul_rn(h, 4.0f) >= M))
-                        direct_d2(X + (row0 + lr) * d, X + (col0 + lc) * d, d, h, l);
+                    // size of the addends before they cancel (the Gram form's error scales with it)
+                    const float M = sMg[lr] + C.x + sMg[WT + lc] + fabsf(gh);
+                    if (slot < 0 || !(__fmul_rn(h, 2.0f) >= M)) fb |= 1u << (4 * i + j);
                     S[i][j] = h;
                     E[i][j] = l;
+                }
+            }
+            // the pairs whose Gram form cancels take the direct sum of squared
+            // differences, one pair at a time by the whole warp (a lane per
+            // dimension, the lanes' double-word partial sums folded in a fixed
+            // tree); a rolled loop over the 16 slots keeps the code small
+            const int lane = tid & 31;
+#pragma unroll 1
+            for (int k = 0; k < 16; ++k) {
+                unsigned todo = __ballot_sync(0xffffffffu, (fb >> k) & 1u);
+                while (todo) {
+                    const int src = __ffs(todo) - 1;
+                    todo &= todo - 1u;
+                    const int slr = __shfl_sync(0xffffffffu, ty * 4 + (k >> 2), src);
+                    const int slc = __shfl_sync(0xffffffffu, tx * 4 + (k & 3), src);
+                    const float *xa = X + (row0 + slr) * d, *xb = X + (col0 + slc) * d;
+                    float ph = 0.f, pl = 0.f;
+                    for (int t = lane; t < d; t += 32) {
+                        float s1, e1;
+                        two_sum(xa[t], -xb[t], s1, e1);
+                        const float p = __fmul_rn(s1, s1);
+                        float q2 = __fmaf_rn(s1, s1, -p);
+                        q2 = __fmaf_rn(__fadd_rn(s1, s1), e1, q2);
+                        dw_add(ph, pl, p, q2);
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const float oh = __shfl_xor_sync(0xffffffffu, ph, o);
+                        const float ol = __shfl_xor_sync(0xffffffffu, pl, o);
+                        dw_add(ph, pl, oh, ol);
+                    }
+                    if (lane == src) {
+#pragma unroll
+                        for (int kk = 0; kk < 16; ++kk)
+                            if (kk == k) {
+                                S[kk >> 2][kk & 3] = ph;
+                                E[kk >> 2][kk & 3] = pl;
+                            }
+                    }
                 }
             }
         } else
@@ -954,7 +983,8 @@ cudaError_t weights_launch_sym(const float *X, int64_t n, int32_t d, double sigm
     if (kev) record_event(kev[0], s);
     if (og && need) {
         // the kept tile pairs' Gram on the tensor cores, then the terms
-        if ((err = omega_gram_launch(*og, X, n, d, P.cen, P.tskip, status, wait_cycles, s))) return err;
+        if ((err = omega_gram_launch(*og, X, n, d, P.cen, P.tskip, status, wait_cycles, s, kev ? kev + 2 : nullptr)))
+            return err;
         const GramArgs ga{og->gbuf, og->item_slot, og->yh, og->yl, og->rexp, og->rnorm, P.cen};
         k_weights_sym<false, true><<<grid, TPB, 0, ISO_S(s)>>>(X, n, d, P.shdw, is_h, is_l, tab, zskip, shrink, T,
                                                                items, nullptr, nullptr, P.tskip, 1, P.flags, P.rpart,

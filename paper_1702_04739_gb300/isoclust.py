@@ -105,6 +105,8 @@ def load(build_if_missing: bool = True):
         lib.isoclust_last_profile.argtypes = [_P, _P]
         lib.isoclust_last_omega_kernel_ms.restype = _D
         lib.isoclust_last_omega_kernel_ms.argtypes = []
+        lib.isoclust_last_omega_gram_ms.restype = _D
+        lib.isoclust_last_omega_gram_ms.argtypes = [_P]
         lib.isoclust_set_sweep_variant.restype = ctypes.c_int
         lib.isoclust_set_sweep_variant.argtypes = [ctypes.c_int32]
         lib.isoclust_last_sweep_variant.restype = ctypes.c_int32
@@ -430,10 +432,11 @@ def set_batched_graphs(enable: bool) -> None:
     _check(load().isoclust_set_batched_graphs(int(bool(enable))))
 
 
-def set_omega_gram(on: bool) -> None:
-    """eq. omega's Gram on the tensor cores (True, the default) or double-word
-    sums of squared differences on the CUDA cores (isoclust_set_omega_gram)."""
-    _check(load().isoclust_set_omega_gram(int(bool(on))))
+def set_omega_gram(mode) -> None:
+    """eq. omega's Gram on the tensor cores: True / 1 always, False / 0 never
+    (double-word sums of squared differences), -1 by row length, the
+    default (isoclust_set_omega_gram)."""
+    _check(load().isoclust_set_omega_gram(int(mode)))
 
 
 def set_test_stalled_wait(on: bool) -> None:
@@ -456,8 +459,11 @@ def last_profile() -> dict:
     lib.isoclust_last_profile(t, c)
     tl = (ctypes.c_int64 * 3)()
     lib.isoclust_last_omega_tiles(tl)
+    gb = ctypes.c_int64(0)
+    gms = float(lib.isoclust_last_omega_gram_ms(ctypes.byref(gb)))
     return dict(omega_tiles=tl[0], omega_tiles_dw=tl[1], omega_symmetric=tl[2],
-                omega_kernel_ms=float(lib.isoclust_last_omega_kernel_ms()), validate_ms=t[0], weights_ms=t[1], mst_ms=t[2], orient_ms=t[3], search_ms=t[4], labels_ms=t[5],
+                omega_kernel_ms=float(lib.isoclust_last_omega_kernel_ms()),
+                omega_gram_ms=gms, omega_gram_blocks=int(gb.value), validate_ms=t[0], weights_ms=t[1], mst_ms=t[2], orient_ms=t[3], search_ms=t[4], labels_ms=t[5],
                 boruvka_rounds=c[0], rescanned_rows=c[1], alg1_passes=c[2], tree_depth=c[3])
 
 

@@ -46,7 +46,10 @@ def _view(ptr: int, count: int, op: int, stream: int, device_buffers: bool, devi
     else:
         raise ValueError(f"unknown reduction {op}")
     if device_buffers:
-        return torch.as_tensor(_DeviceBuffer(ptr, count, typestr, stream), device=device)
+        t = torch.as_tensor(_DeviceBuffer(ptr, count, typestr, stream), device=device)
+        if t.data_ptr() != ptr:
+            raise RuntimeError("the device buffer was copied, not viewed")
+        return t
     import ctypes
     import numpy as np
     buf = (ctypes.c_byte * (8 * count)).from_address(ptr)

@@ -87,16 +87,36 @@ def boruvka_rank(rank, world, port, out, tile_rows):
 
 def gpu_cluster_rank(rank, world, port, out, n):
     """isoclust_cluster_sharded on one GPU per rank (here both ranks share
-    cuda:0), the exchange through gloo on host copies."""
+    cuda:0), the exchange through gloo on host copies.  Each rank logs its
+    collectives (op, count) and keeps its own error, so a failure names the
+    rank that caused it (the other rank only sees the lost peer)."""
+    import faulthandler
+    import traceback
     import torch
     from paper_1702_04739_gb300 import isoclust, sharded, workloads
-    dist = _init(rank, world, port)
-    torch.cuda.set_device(0)
-    X, _ = workloads.blobs_anisotropic(seed=11, n=n, k=8)
-    Xd = torch.from_numpy(X).cuda()
-    lab, res, ik = isoclust.cluster_sharded(Xd, 8, 1.0, rank, world,
-                                            sharded.torch_allreduce(device_buffers=True, device=Xd.device))
-    np.save(os.path.join(out, f"gpu{rank}.npy"), np.concatenate([lab.cpu().numpy().astype(np.float64),
-                                                                 res.cpu().numpy().astype(np.float64),
-                                                                 ik.cpu().numpy()]))
-    dist.destroy_process_group()
+    trace = open(os.path.join(out, f"gpu{rank}.trace"), "w")
+    faulthandler.enable(file=trace)
+    log = open(os.path.join(out, f"gpu{rank}.log"), "w")
+    try:
+        dist = _init(rank, world, port)
+        torch.cuda.set_device(0)
+        X, _ = workloads.blobs_anisotropic(seed=11, n=n, k=8)
+        Xd = torch.from_numpy(X).cuda()
+        inner = sharded.torch_allreduce(device_buffers=True, device=Xd.device)
+
+        def logged(ptr, count, op, stream):
+            log.write(f"{op} {count}\n")
+            log.flush()
+            inner(ptr, count, op, stream)
+        lab, res, ik = isoclust.cluster_sharded(Xd, 8, 1.0, rank, world, logged)
+        np.save(os.path.join(out, f"gpu{rank}.npy"), np.concatenate([lab.cpu().numpy().astype(np.float64),
+                                                                     res.cpu().numpy().astype(np.float64),
+                                                                     ik.cpu().numpy()]))
+        log.write("done\n")
+        log.flush()
+        dist.barrier()
+        dist.destroy_process_group()
+    except BaseException:
+        with open(os.path.join(out, f"gpu{rank}.err"), "w") as f:
+            f.write(traceback.format_exc())
+        raise

@@ -21,7 +21,7 @@ def iso():
     from paper_1702_04739_gb300 import isoclust
     isoclust.load()
     yield isoclust
-    isoclust.set_omega_gram(True)
+    isoclust.set_omega_gram(-1)
 
 
 def _bound(orc, X, sigma):
@@ -56,7 +56,7 @@ def test_gram_omega_against_oracle_and_cuda_cores(iso, oracle_lib, parity_report
     iso.set_omega_gram(False)
     c = {key: v.cpu().numpy() for key, v in iso.cluster_detail(Xd, k, sigma).items()}
     assert iso.last_profile()["omega_symmetric"] == 2
-    iso.set_omega_gram(True)
+    iso.set_omega_gram(-1)
     om, _ = oracle_lib.weights(X, sigma)
     bound = _bound(oracle_lib, X, sigma)
     rel_g = np.abs(g["omega"] - om) / om

@@ -11,6 +11,7 @@ so omega can differ from the one-GPU sum in the last bits).  A failing
 callback gives ISOCLUST_ERR_COMM and leaves the library usable.
 """
 import os
+import time
 import socket
 
 import numpy as np
@@ -70,8 +71,23 @@ def test_two_ranks_on_one_gpu_through_gloo(iso, oracle_lib, tmp_path):
     import torch.multiprocessing as mp
     from paper_1702_04739_gb300 import workloads
     n = 6000
-    mp.start_processes(_sharded_ranks.gpu_cluster_rank, args=(2, _free_port(), str(tmp_path), n), nprocs=2,
-                       join=True, start_method="spawn")
+    ctx = mp.start_processes(_sharded_ranks.gpu_cluster_rank, args=(2, _free_port(), str(tmp_path), n), nprocs=2,
+                             join=False, start_method="spawn")
+    deadline = time.monotonic() + 300.0
+    for p in ctx.processes:
+        p.join(max(1.0, deadline - time.monotonic()))
+    for p in ctx.processes:
+        if p.is_alive():
+            p.terminate()
+            p.join(30.0)
+    codes = [p.exitcode for p in ctx.processes]
+    if codes != [0, 0]:
+        def read(name):
+            f = os.path.join(tmp_path, name)
+            return open(f).read()[-3000:] if os.path.exists(f) else "(none)"
+        report = "\n".join(f"rank {r}: exit {codes[r]}\n log:\n{read(f'gpu{r}.log')}\n error:\n{read(f'gpu{r}.err')}"
+                           f"\n fault trace:\n{read(f'gpu{r}.trace')}" for r in range(2))
+        raise AssertionError("a rank failed\n" + report)
     r0, r1 = (np.load(os.path.join(tmp_path, f"gpu{r}.npy")) for r in range(2))
     assert (r0 == r1).all()
     lab, res, ik = r0[:n].astype(np.int32), r0[n:2 * n].astype(np.uint8), float(r0[2 * n])
