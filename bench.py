@@ -249,10 +249,12 @@ def omega_gram_roofline(prof, peaks, src, alu_peak, sms, sweep_ms, items, d, alg
     tc = tc_flop / (g_ms / 1000.0) / 1e12 if g_ms > 0 else 0.0
     sw_ops = items * (4096.0 * 150.0 + 128.0 * (21.0 * d + 2400.0))
     sw = sw_ops / (sweep_ms / 1000.0) / 1e12 if sweep_ms > 0 else 0.0
+    direct = prof[-1].get("omega_gram_direct_pairs", 0)
     gram_k = {"kernel": "k_oz_gram (omega Gram, tcgen05 BF16 digit planes)", "bound": "tensor", "kernel_ms": g_ms,
               "achieved": tc, "peak": bf16, "unit": "TFLOP/s", "frac": tc / bf16, "blocks": blocks}
     sweep_k = {"kernel": "k_weights_sym<GRAM> (omega terms from the Gram, double-word FP32)", "bound": "alu",
-               "kernel_ms": sweep_ms, "achieved": sw, "peak": alu_peak, "unit": "TFLOP/s", "frac": sw / alu_peak}
+               "kernel_ms": sweep_ms, "achieved": sw, "peak": alu_peak, "unit": "TFLOP/s", "frac": sw / alu_peak,
+               "direct_pairs": direct, "direct_share": direct / max(1.0, items * 4096.0)}
     top, other = (gram_k, sweep_k) if g_ms >= sweep_ms else (sweep_k, gram_k)
     both_ms = g_ms + sweep_ms
     alg = alg_flop / (both_ms / 1000.0) / 1e12

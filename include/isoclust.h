@@ -420,8 +420,10 @@ double isoclust_last_omega_kernel_ms(void);
  * tensor-core Gram kernel of omega in the last one-set call on this host
  * thread (isoclust_set_omega_gram), 0 when it did not run; *blocks (may be
  * NULL) gets its number of 128 x 64 blocks (each 34 BF16 digit-plane MMA
- * products of 2 x 128 x 64 x d_pad flop, d_pad = d rounded up to 64). */
-double isoclust_last_omega_gram_ms(int64_t *blocks);
+ * products of 2 x 128 x 64 x d_pad flop, d_pad = d rounded up to 64), and
+ * *direct_pairs (may be NULL) the number of pairs whose Gram form cancelled
+ * and which took the direct sum of squared differences instead. */
+double isoclust_last_omega_gram_ms(int64_t *blocks, int64_t *direct_pairs);
 
 /* Tile variant of the tensor-core Boruvka sweep (Section 3.5's MST step
  * with the tiled Gram sweep): bit 0 set = 32-column candidate blocks (else

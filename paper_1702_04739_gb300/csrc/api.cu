@@ -51,7 +51,7 @@ static void note_launches(long long k) { g_launches.fetch_add(k, std::memory_ord
 static thread_local char g_err[512] = "";
 static thread_local double g_prof_ms[6] = {0, 0, 0, 0, 0, 0};
 static thread_local int64_t g_prof_cnt[4] = {0, 0, 0, 0};
-static thread_local unsigned long long g_prof_tiles[2] = {0, 0};
+static thread_local unsigned long long g_prof_tiles[3] = {0, 0, 0};
 static thread_local int g_prof_sym = 0;
 static thread_local double g_prof_omega_kernel_ms = 0.0;
 static thread_local double g_prof_omega_gram_ms = 0.0;
@@ -281,7 +281,7 @@ isoclust_status map_status(uint32_t st, bool user_tree) {
         return user_tree ? fail(ISOCLUST_ERR_INVALID_ARG, "omega must be > 0, phi and p >= 0")
                          : fail(ISOCLUST_ERR_INTERNAL, "internal: a vertex weight is not positive");
     if (st & DEV_NO_SOLUTION) return fail(ISOCLUST_ERR_NO_SOLUTION, "no finite threshold gives k sets");
-    if (st & (DEV_INTERNAL | DEV_EDGE_COUNT)) return fail(ISOCLUST_ERR_INTERNAL, "internal consistency check failed (0x%x)", st);
+    if (st) return fail(ISOCLUST_ERR_INTERNAL, "internal consistency check failed (0x%x)", st);
     return ISOCLUST_OK;
 }
 
@@ -476,7 +476,7 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
             P.kbuf = A.take<uint64_t>(n);
             P.Xp = A.take<float>((size_t)n * d);
             P.nnp = A.take<unsigned long long>(n);
-            P.tiles = A.take<unsigned long long>(2);
+            P.tiles = A.take<unsigned long long>(3);
             P.omp = A.take<double>(n);
             P.pp = A.take<double>(n);
             if (symmetric) P.sym = (void *)A.take<unsigned char>(weights_sym_bytes(n, d));
@@ -550,7 +550,7 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
                 ISO_CUDA(sort_pairs_u64(P.key, P.perm, P.kbuf, P.vbuf, n, s));
                 k_gather_rows<<<(unsigned)ceil_div(n * (int64_t)d, TPB), TPB, 0, ISO_S(s)>>>(
                     (const float *)X, P.perm, M.nnbits, n, d, P.Xp, P.nnp);
-                ISO_CUDA(cudaMemsetAsync(P.tiles, 0, 2 * sizeof(unsigned long long), s));
+                ISO_CUDA(cudaMemsetAsync(P.tiles, 0, 3 * sizeof(unsigned long long), s));
                 if (symmetric) {
                     // the tensor cores decide which pairs of 64-row tiles can hold a term
                     if (use_tc) {
@@ -618,7 +618,7 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
     g_prof_cnt[1] = cnt[MC_OVF_TOTAL] + cnt[MC_OVERFLOW];
     g_prof_cnt[2] = ss.passes + (need_labels ? 1 : 0);
     g_prof_cnt[3] = ss.max_depth;
-    g_prof_tiles[0] = g_prof_tiles[1] = 0;
+    g_prof_tiles[0] = g_prof_tiles[1] = g_prof_tiles[2] = 0;
     if (permuted) ISO_CUDA(cudaMemcpy(g_prof_tiles, P.tiles, sizeof(g_prof_tiles), cudaMemcpyDeviceToHost));
     g_prof_sym = symmetric ? (gram ? 3 : (use_tc ? 2 : 1)) : 0;
     // the symmetric sweep kernel (after the Gram kernel when that ran), and the Gram kernel
@@ -826,7 +826,7 @@ static isoclust_status cluster_sets_impl(const void *X, const int64_t *offsets, 
         B.Xp = A.take<float>((size_t)n_pad64 * d);
         B.nnp = A.take<unsigned long long>(n_pad64);
         B.omp = A.take<double>(n_pad64);
-        B.tiles = A.take<unsigned long long>(2);
+        B.tiles = A.take<unsigned long long>(3);
         B.sym = (void *)A.take<unsigned char>(weights_sym_sets_bytes(n_pad64, nitems, d));
     };
     Arena meas;
@@ -904,7 +904,7 @@ static isoclust_status cluster_sets_impl(const void *X, const int64_t *offsets, 
         if ((e = cudaMemsetAsync(B.nnp, 0xff, sizeof(unsigned long long) * n_pad64, q))) return e;
         k_gather_pad<<<(unsigned)ceil_div(N * (int64_t)d, TPB), TPB, 0, ISO_S(q)>>>((const float *)X, B.pos, M.nnbits, N,
                                                                                     d, B.Xp, B.nnp);
-        if ((e = cudaMemsetAsync(B.tiles, 0, 2 * sizeof(unsigned long long), q))) return e;
+        if ((e = cudaMemsetAsync(B.tiles, 0, 3 * sizeof(unsigned long long), q))) return e;
         if ((e = weights_launch_sym_sets(B.Xp, n_pad64, d, sigma, o.include_self, B.nnp, B.omp, B.sym, B.witems,
                                          nitems, B.tile_valid, B.tile_set, d_tile0, d_ntl, d_item0, max_n, B.tiles,
                                          E.ok ? E.e + 8 : nullptr, q)))
@@ -1061,8 +1061,9 @@ void isoclust_last_profile(double *t_ms6, int64_t *counts4) {
 
 double isoclust_last_omega_kernel_ms(void) { return g_prof_omega_kernel_ms; }
 
-double isoclust_last_omega_gram_ms(int64_t *blocks) {
+double isoclust_last_omega_gram_ms(int64_t *blocks, int64_t *direct_pairs) {
     if (blocks) *blocks = g_prof_omega_gram_blocks;
+    if (direct_pairs) *direct_pairs = g_prof_omega_gram_blocks ? (int64_t)g_prof_tiles[2] : 0;
     return g_prof_omega_gram_ms;
 }
 

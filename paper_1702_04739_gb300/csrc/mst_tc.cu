@@ -182,7 +182,9 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
     // pair sp; either from the item list (sp in the low 4 bits, the set
     // above: items of a set whose forest is complete are skipped) or row tile
     // x column split
-    const int64_t items = witems ? nwitems : (int64_t)ntiles * splits;
+    // (a sharded call: only the row tiles rt_off, rt_off + rt_stride, ... of this rank)
+    const int64_t own_tiles = rt_off < ntiles ? ((int64_t)ntiles - rt_off + rt_stride - 1) / rt_stride : 0;
+    const int64_t items = witems ? nwitems : own_tiles * splits;
     const int tiles_per_split = (ntiles + splits - 1) / splits;
     auto item = [&](int64_t w, int &rt, int &c0, int &c1, int &sp) {
         if (witems) {

@@ -411,7 +411,7 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     if (tid < 64) tab[tid] = tabv.t[tid];
-    unsigned long long dw_items = 0, screened = 0;
+    unsigned long long dw_items = 0, screened = 0, fallbacks = 0;
     // a sharded call evaluates the items w with w mod world == rank
     for (int64_t w = (int64_t)blockIdx.x * shard_world + shard_rank; w < nitems;
          w += (int64_t)gridDim.x * shard_world) {
@@ -623,6 +623,7 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
                     E[i][j] = l;
                 }
             }
+            fallbacks += (unsigned)__popc(fb);
             // the pairs whose Gram form cancels take the direct sum of squared
             // differences, one pair at a time by the whole warp (a lane per
             // dimension, the lanes' double-word partial sums folded in a fixed
@@ -806,6 +807,12 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
     if (tid == 0) {
         atomicAdd(tile_counts + 0, screened);
         atomicAdd(tile_counts + 1, dw_items);
+    }
+    if constexpr (GRAM) {
+        // pairs that took the direct sums (tile_counts[2])
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) fallbacks += __shfl_xor_sync(0xffffffffu, fallbacks, o);
+        if ((tid & 31) == 0 && fallbacks) atomicAdd(tile_counts + 2, fallbacks);
     }
 }
 

@@ -106,7 +106,7 @@ def load(build_if_missing: bool = True):
         lib.isoclust_last_omega_kernel_ms.restype = _D
         lib.isoclust_last_omega_kernel_ms.argtypes = []
         lib.isoclust_last_omega_gram_ms.restype = _D
-        lib.isoclust_last_omega_gram_ms.argtypes = [_P]
+        lib.isoclust_last_omega_gram_ms.argtypes = [_P, _P]
         lib.isoclust_set_sweep_variant.restype = ctypes.c_int
         lib.isoclust_set_sweep_variant.argtypes = [ctypes.c_int32]
         lib.isoclust_last_sweep_variant.restype = ctypes.c_int32
@@ -459,11 +459,11 @@ def last_profile() -> dict:
     lib.isoclust_last_profile(t, c)
     tl = (ctypes.c_int64 * 3)()
     lib.isoclust_last_omega_tiles(tl)
-    gb = ctypes.c_int64(0)
-    gms = float(lib.isoclust_last_omega_gram_ms(ctypes.byref(gb)))
+    gb, gf = ctypes.c_int64(0), ctypes.c_int64(0)
+    gms = float(lib.isoclust_last_omega_gram_ms(ctypes.byref(gb), ctypes.byref(gf)))
     return dict(omega_tiles=tl[0], omega_tiles_dw=tl[1], omega_symmetric=tl[2],
                 omega_kernel_ms=float(lib.isoclust_last_omega_kernel_ms()),
-                omega_gram_ms=gms, omega_gram_blocks=int(gb.value), validate_ms=t[0], weights_ms=t[1], mst_ms=t[2], orient_ms=t[3], search_ms=t[4], labels_ms=t[5],
+                omega_gram_ms=gms, omega_gram_blocks=int(gb.value), omega_gram_direct_pairs=int(gf.value), validate_ms=t[0], weights_ms=t[1], mst_ms=t[2], orient_ms=t[3], search_ms=t[4], labels_ms=t[5],
                 boruvka_rounds=c[0], rescanned_rows=c[1], alg1_passes=c[2], tree_depth=c[3])
 
 

@@ -13,8 +13,11 @@ for p in (ROOT, HERE):
 
 
 def _init(rank, world, port):
+    import datetime
     import torch.distributed as dist
-    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    # a rank that leaves early ends the other's next collective within a minute
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=60))
     return dist
 
 
