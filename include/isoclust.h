@@ -461,8 +461,11 @@ int32_t isoclust_last_batched_graph_mode(void);
  * take the double-word sum of squared differences.  Otherwise every pair's
  * d2 is that double-word sum.  Both keep d2 to about 2^-46 relative; omega
  * agrees to within the library's error bound, not bit for bit.
- * mode -1 (the default): the Gram on the tensor cores for rows longer than
- * 128 dimensions; 1: always; 0: never.  Process-wide; other values ->
+ * Rows of 1,024 dimensions or more are centred on one point for the Gram
+ * (the mean of the 64-row tiles' centroids), shorter ones on their tile's
+ * centroid.
+ * mode -1 (the default): the Gram on the tensor cores for rows of 64
+ * dimensions or more; 1: always; 0: never.  Process-wide; other values ->
  * INVALID_ARG. */
 isoclust_status isoclust_set_omega_gram(int32_t mode);
 

@@ -24,10 +24,10 @@ cudaError_t weights_launch_sym(const float *X, int64_t n, int32_t d, double sigm
                                OmegaGram *og = nullptr, uint32_t *status = nullptr, uint64_t wait_cycles = 0);
 float omega_zskip(int64_t n);
 constexpr size_t SYM_PART_LIMIT = size_t(16) << 30;   // symmetric sweep up to 16 GiB of partials
-// the omega Gram goes to the tensor cores by default for rows longer than
-// this (measured: 3.3x faster on 50,000 x 4,096; slower at d = 64, where the
-// per-pair cross terms and cancelling pairs outweigh the d-long sums)
-constexpr int32_t OMEGA_GRAM_MIN_D = 128;
+// the omega Gram goes to the tensor cores by default for rows at least this
+// long (measured on GB300: 1.23x faster at d = 64, 1.3x at d = 128, 5x at
+// d = 4,096 than the double-word CUDA-core sums)
+constexpr int32_t OMEGA_GRAM_MIN_D = 64;
 size_t weights_sym_sets_bytes(int64_t n_pad, int64_t nitems, int32_t d);
 cudaError_t weights_launch_sym_sets(const float *Xp, int64_t n_pad, int32_t d, double sigma, int include_self,
                                     const unsigned long long *nnbits, double *omega, void *part, const int2 *witems,
@@ -456,7 +456,7 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
     int64_t gram_blocks = 0;
     const int gram_mode = g_omega_gram.load(std::memory_order_relaxed);
     const bool gram = symmetric && use_tc && ceil_div(n, 128) <= 65535 &&
-                      (gram_mode == 1 || (gram_mode < 0 && d > OMEGA_GRAM_MIN_D));
+                      (gram_mode == 1 || (gram_mode < 0 && d >= OMEGA_GRAM_MIN_D));
     auto carve = [&](Arena &A, MstScratch &M, TreeScratch &TS, double **phi, double **om, double **pp, double **omtmp,
                      uint32_t **status) {
         *status = A.take<uint32_t>(4);

@@ -107,7 +107,10 @@ struct OmegaGram {
     int32_t *item_slot = nullptr;         // [items] 2 x block + half, -1 when the screen drops the item
     float2 *gbuf = nullptr;               // [blocks][128][64] G in units of 2^(E_i + E_j - 14)
     int64_t nblocks = 0;
+    int one_centre = 0;                   // every row centred on one point instead of its tile's centroid
 };
+// Rows at least this long are centred on one point for the Gram (no cross terms).
+constexpr int32_t OMEGA_ONE_CENTRE_MIN_D = 1024;
 size_t omega_gram_bytes(int64_t n, int32_t d);
 // kev (may be null): two events recorded around the Gram kernel
 cudaError_t omega_gram_launch(OmegaGram &G, const float *Xp, int64_t n, int32_t d, const float *cen,

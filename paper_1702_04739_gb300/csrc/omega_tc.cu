@@ -74,9 +74,19 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
 
 // ---- digits: one warp per padded row r of the omega order (rows past n and
 // dimensions past d are zero).  Also the row's y = x - c_T as a double-word,
-// its exponent E and |y|^2 as a double-word.
+// its exponent E and |y|^2 as a double-word.  cen_stride = 0: every row is
+// centred on the same point cen[0 .. d).
+// The mean of the tile centroids (the single centre of long rows).
+__global__ void k_oz_centre(const float *__restrict__ cen, int64_t T64, int32_t d, float *__restrict__ out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= d) return;
+    double s = 0.0;
+    for (int64_t T = 0; T < T64; ++T) s += (double)cen[T * d + t];
+    out[t] = (float)(s / (double)T64);
+}
+
 __global__ void __launch_bounds__(256) k_oz_digits(const float *__restrict__ X, int64_t n, int32_t d, int32_t d_pad,
-                                                   int64_t n_pad, const float *__restrict__ cen,
+                                                   int64_t n_pad, const float *__restrict__ cen, int64_t cen_stride,
                                                    __nv_bfloat16 *__restrict__ planes, float *__restrict__ yh_out,
                                                    float *__restrict__ yl_out, int32_t *__restrict__ rexp,
                                                    float2 *__restrict__ rnorm) {
@@ -90,7 +100,7 @@ __global__ void __launch_bounds__(256) k_oz_digits(const float *__restrict__ X, 
     float nh = 0.f, nl = 0.f;
     for (int t = lane; t < d; t += 32) {
         float yh = 0.f, yl = 0.f;
-        if (real) two_sum(X[r * d + t], -cen[T * d + t], yh, yl);
+        if (real) two_sum(X[r * d + t], -cen[T * cen_stride + t], yh, yl);
         if (yh != 0.f) emax = max(emax, ilogbf(yh) + 1);         // |yh| < 2^(ilogb + 1)
         float p, e;
         two_prod(yh, yh, p, e);
@@ -379,7 +389,8 @@ size_t omega_gram_bytes(int64_t n, int32_t d) {
     const int64_t ncand = T128 * T64;               // >= the candidate blocks
     const int64_t items = T64 * (T64 + 1) / 2;
     return (size_t)OZ_S * n_pad * d_pad * 2 + 2 * (size_t)n_pad * d * 4 + (size_t)n_pad * (4 + 8) +
-           (size_t)ncand * (4 + 4 + 4 + 16) + (size_t)items * 4 + (size_t)scan_tmp_elems(ncand + 1) * 4 + 8 * 1024;
+           (size_t)ncand * (4 + 4 + 4 + 16) + (size_t)items * 4 + (size_t)scan_tmp_elems(ncand + 1) * 4 +
+           (size_t)d * 4 + 9 * 1024;
 }
 
 cudaError_t omega_gram_launch(OmegaGram &G, const float *Xp, int64_t n, int32_t d, const float *cen,
@@ -404,10 +415,15 @@ cudaError_t omega_gram_launch(OmegaGram &G, const float *Xp, int64_t n, int32_t 
     int4 *blocks = A.take<int4>(ncand);
     G.item_slot = A.take<int32_t>(items);
     int32_t *tmp = A.take<int32_t>(scan_tmp_elems(ncand + 1));
+    float *one = A.take<float>(d);
     if (A.overflow) return cudaErrorInvalidValue;
 
-    k_oz_digits<<<(unsigned)ceil_div(n_pad * 32, 256), 256, 0, ISO_S(s)>>>(Xp, n, d, d_pad, n_pad, cen, planes, G.yh,
-                                                                           G.yl, G.rexp, G.rnorm);
+    // long rows share one centre: their tile-centred cross terms <y, c_I -
+    // c_J> would cost O(d) per row and tile pair
+    G.one_centre = d >= OMEGA_ONE_CENTRE_MIN_D ? 1 : 0;
+    if (G.one_centre) k_oz_centre<<<(unsigned)ceil_div(d, 128), 128, 0, ISO_S(s)>>>(cen, T64, d, one);
+    k_oz_digits<<<(unsigned)ceil_div(n_pad * 32, 256), 256, 0, ISO_S(s)>>>(
+        Xp, n, d, d_pad, n_pad, G.one_centre ? one : cen, G.one_centre ? 0 : d, planes, G.yh, G.yl, G.rexp, G.rnorm);
     if ((e = cudaMemsetAsync(flag, 0, sizeof(int32_t) * (ncand + 1), s))) return e;
     if ((e = cudaMemsetAsync(bits, 0, sizeof(int32_t) * ncand, s))) return e;
     if ((e = cudaMemsetAsync(G.item_slot, 0xff, sizeof(int32_t) * items, s))) return e;

@@ -41,6 +41,8 @@ constexpr int TPB = 256;
 constexpr int WT = 64;        // rows / columns per tile
 constexpr int WDC = 32;       // dims per shared-memory chunk
 constexpr int WPAD = WT + 4;
+constexpr int GR_DCH = (WDC * WPAD) / 2;    // dimensions of D per chunk (a double-word each, in As)
+constexpr int GR_FCAP = (WDC * WPAD) / 2;   // cancelling pairs per round (indices in Bs, results in As)
 
 struct RowAcc {
     float wh, wl, ph, pl;
@@ -380,6 +382,7 @@ struct GramArgs {
     const int32_t *rexp;         // E of each row
     const float2 *rnorm;         // |y|^2, double-word
     const float *cen;            // tile centroids c_T
+    int one_centre;              // 1: every row was centred on the same point (D = 0)
 };
 
 // Symmetric omega sweep: each unordered tile pair is screened in FP32 and,
@@ -408,6 +411,7 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
     __shared__ float sSc[GRAM ? 2 * WT : 1];   // GRAM: 2^(E - 7) of the rows of I, 2^(E - 6) of J
     __shared__ float2 sC;                      // GRAM: |D|^2
     __shared__ float sMg[GRAM ? 2 * WT : 1];   // GRAM: |y|^2 + 2 |<y, D>| (+ |D|^2 for I): the parts' size
+    __shared__ int sFb;                        // GRAM: cancelling pairs of the item
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     if (tid < 64) tab[tid] = tabv.t[tid];
@@ -526,63 +530,75 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
             for (int j = 0; j < 4; ++j) { S[i][j] = 0.f; E[i][j] = 0.f; }
         if constexpr (GRAM) {
             // d2 = (|y_i|^2 + 2 <y_i, D> + |D|^2) + (|y_j|^2 - 2 <y_j, D>) - 2 G_ij, y = x - c_T,
-            // D = c_I - c_J: the cross terms of the 64 rows of I (products 0..63)
-            // and of J (64..127); warp w takes products w, w + 8, ..., its lanes
-            // the dimensions (coalesced rows), folded in a fixed shuffle tree.
-            // Warp 0 also forms |D|^2.
+            // D = c_I - c_J (zero on the diagonal and when every row shares one centre)
+            const int lane = tid & 31, wq = tid >> 5;
+            const bool cross = !diag && !ga.one_centre;
+            float2 *sD = reinterpret_cast<float2 *>(&As[0][0]);          // D chunk, double-word
+            float2 *sX = reinterpret_cast<float2 *>(&Bs[0][0]);          // upper half's partial products
             {
-                const int lane = tid & 31, wq = tid >> 5;
-                const float *cI = ga.cen + I * d, *cJ = ga.cen + J * d;
-                for (int dp = wq; dp < 2 * WT; dp += TPB / 32) {
-                    const int64_t gr = dp < WT ? row0 + dp : col0 + (dp - WT);
-                    float xh = 0.f, xl = 0.f;
-                    if (!diag) {
-                        const float *ryh = ga.yh + gr * d, *ryl = ga.yl + gr * d;
-                        for (int t = lane; t < d; t += 32) {
+                // products p = 0..63 (rows of I) and 64..127 (rows of J), one
+                // thread each; the two halves of the block take alternate
+                // dimensions of every chunk of D
+                const int pr = tid & 127, hh = tid >> 7;
+                const int64_t gr = pr < WT ? row0 + pr : col0 + (pr - WT);
+                float xh = 0.f, xl = 0.f, ch = 0.f, cl = 0.f;
+                if (cross) {
+                    const float *cI = ga.cen + I * d, *cJ = ga.cen + J * d;
+                    const float *ryh = ga.yh + gr * d, *ryl = ga.yl + gr * d;
+                    for (int t0 = 0; t0 < d; t0 += GR_DCH) {
+                        const int tl = min(GR_DCH, d - t0);
+                        __syncthreads();                       // previous chunk's readers are done
+                        for (int t = tid; t < tl; t += TPB) {
                             float Dh, Dl;
-                            two_sum(cI[t], -cJ[t], Dh, Dl);
-                            const float a = ryh[t], al = ryl[t];
-                            float p, e;
-                            two_prod(a, Dh, p, e);
-                            e = __fmaf_rn(a, Dl, __fmaf_rn(al, Dh, e));
-                            dw_add(xh, xl, p, e);
-                        }
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) {
-                            const float oh = __shfl_xor_sync(0xffffffffu, xh, o);
-                            const float ol = __shfl_xor_sync(0xffffffffu, xl, o);
-                            dw_add(xh, xl, oh, ol);
-                        }
-                    }
-                    if (lane == 0) {
-                        const float2 rn = ga.rnorm[gr];
-                        float uh = rn.x, ul = rn.y;
-                        const float sg = dp < WT ? 2.0f : -2.0f;
-                        dw_add(uh, ul, __fmul_rn(sg, xh), __fmul_rn(sg, xl));
-                        sUV[dp] = make_float2(uh, ul);
-                        sMg[dp] = __fadd_rn(rn.x, fabsf(__fmul_rn(2.0f, xh)));
-                        sSc[dp] = ldexpf(1.0f, ga.rexp[gr] - (dp < WT ? 7 : 6));
-                    }
-                }
-                if (wq == 0) {
-                    float ch = 0.f, cl = 0.f;
-                    if (!diag) {
-                        for (int t = lane; t < d; t += 32) {
-                            float Dh, Dl;
-                            two_sum(cI[t], -cJ[t], Dh, Dl);
+                            two_sum(cI[t0 + t], -cJ[t0 + t], Dh, Dl);
+                            sD[t] = make_float2(Dh, Dl);
                             float p, e;
                             two_prod(Dh, Dh, p, e);
                             e = __fmaf_rn(__fadd_rn(Dh, Dh), Dl, e);
                             dw_add(ch, cl, p, e);
                         }
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) {
-                            const float oh = __shfl_xor_sync(0xffffffffu, ch, o);
-                            const float ol = __shfl_xor_sync(0xffffffffu, cl, o);
-                            dw_add(ch, cl, oh, ol);
+                        __syncthreads();
+                        for (int t = hh; t < tl; t += 2) {
+                            const float2 D = sD[t];
+                            const float a = ryh[t0 + t], al = ryl[t0 + t];
+                            float p, e;
+                            two_prod(a, D.x, p, e);
+                            e = __fmaf_rn(a, D.y, __fmaf_rn(al, D.x, e));
+                            dw_add(xh, xl, p, e);
                         }
                     }
-                    if (lane == 0) sC = make_float2(ch, cl);
+                    // |D|^2: the threads' chunk partials, folded in a fixed order
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const float oh = __shfl_xor_sync(0xffffffffu, ch, o);
+                        const float ol = __shfl_xor_sync(0xffffffffu, cl, o);
+                        dw_add(ch, cl, oh, ol);
+                    }
+                    if (hh) sX[pr] = make_float2(xh, xl);
+                }
+                __syncthreads();
+                if (cross && lane == 0) sX[128 + wq] = make_float2(ch, cl);
+                __syncthreads();
+                if (tid < 2 * WT) {
+                    const float2 rn = ga.rnorm[gr];
+                    float uh = rn.x, ul = rn.y;
+                    float mg = rn.x;
+                    if (cross) {
+                        const float2 o = sX[pr];
+                        dw_add(xh, xl, o.x, o.y);
+                        const float sg = pr < WT ? 2.0f : -2.0f;
+                        dw_add(uh, ul, __fmul_rn(sg, xh), __fmul_rn(sg, xl));
+                        mg = __fadd_rn(rn.x, fabsf(__fmul_rn(2.0f, xh)));
+                    }
+                    sUV[pr] = make_float2(uh, ul);
+                    sMg[pr] = mg;
+                    sSc[pr] = ldexpf(1.0f, ga.rexp[gr] - (pr < WT ? 7 : 6));
+                }
+                if (tid == 0) {
+                    float h = 0.f, l = 0.f;
+                    if (cross)
+                        for (int q = 0; q < TPB / 32; ++q) dw_add(h, l, sX[128 + q].x, sX[128 + q].y);
+                    sC = make_float2(h, l);
                 }
             }
             __syncthreads();
@@ -597,6 +613,7 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
                 const int lr = ty * 4 + i;
                 float uh = sUV[lr].x, ul = sUV[lr].y;
                 dw_add(uh, ul, C.x, C.y);
+                const float mi = sMg[lr] + C.x, si = sSc[lr];
                 float4 g01 = make_float4(0.f, 0.f, 0.f, 0.f), g23 = g01;
                 if (slot >= 0) {
                     g01 = *reinterpret_cast<const float4 *>(Gp + lr * WT + tx * 4);
@@ -606,62 +623,95 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const int lc = tx * 4 + j;
-                    if (!rok(lr) || !cok(lc) || (diag && lc == lr)) continue;
-                    const float sc = __fmul_rn(sSc[lr], sSc[WT + lc]);      // 2^(E_i + E_j - 13), exact
+                    const float sc = __fmul_rn(si, sSc[WT + lc]);      // 2^(E_i + E_j - 13), exact
                     const float gh = __fmul_rn(gv[j][0], sc), gl = __fmul_rn(gv[j][1], sc);
                     const float2 V = sUV[WT + lc];
                     float h = uh, l = ul;
                     dw_add(h, l, V.x, V.y);
                     dw_add(h, l, -gh, -gl);
-                    // the Gram form's error is about 2^-46 of the addends' size:
-                    // where they cancel to under a quarter of it, take the
-                    // direct sum of squared differences instead
-                    // size of the addends before they cancel (the Gram form's error scales with it)
-                    const float M = sMg[lr] + C.x + sMg[WT + lc] + fabsf(gh);
-                    if (slot < 0 || !(__fmul_rn(h, 2.0f) >= M)) fb |= 1u << (4 * i + j);
+                    // the Gram form's error is about 2^-46 of the addends'
+                    // size M: where they cancel to under half of it, the
+                    // pair takes the direct sum of squared differences
+                    const float M = mi + sMg[WT + lc] + fabsf(gh);
+                    const bool real = rok(lr) && cok(lc) && !(diag && lc == lr);
+                    if (real && (slot < 0 || !(__fmul_rn(h, 2.0f) >= M))) fb |= 1u << (4 * i + j);
                     S[i][j] = h;
                     E[i][j] = l;
                 }
             }
             fallbacks += (unsigned)__popc(fb);
-            // the pairs whose Gram form cancels take the direct sum of squared
-            // differences, one pair at a time by the whole warp (a lane per
-            // dimension, the lanes' double-word partial sums folded in a fixed
-            // tree); a rolled loop over the 16 slots keeps the code small
-            const int lane = tid & 31;
-#pragma unroll 1
-            for (int k = 0; k < 16; ++k) {
-                unsigned todo = __ballot_sync(0xffffffffu, (fb >> k) & 1u);
-                while (todo) {
-                    const int src = __ffs(todo) - 1;
-                    todo &= todo - 1u;
-                    const int slr = __shfl_sync(0xffffffffu, ty * 4 + (k >> 2), src);
-                    const int slc = __shfl_sync(0xffffffffu, tx * 4 + (k & 3), src);
-                    const float *xa = X + (row0 + slr) * d, *xb = X + (col0 + slc) * d;
-                    float ph = 0.f, pl = 0.f;
-                    for (int t = lane; t < d; t += 32) {
-                        float s1, e1;
-                        two_sum(xa[t], -xb[t], s1, e1);
-                        const float p = __fmul_rn(s1, s1);
-                        float q2 = __fmaf_rn(s1, s1, -p);
-                        q2 = __fmaf_rn(__fadd_rn(s1, s1), e1, q2);
-                        dw_add(ph, pl, p, q2);
-                    }
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        const float oh = __shfl_xor_sync(0xffffffffu, ph, o);
-                        const float ol = __shfl_xor_sync(0xffffffffu, pl, o);
-                        dw_add(ph, pl, oh, ol);
-                    }
-                    if (lane == src) {
-#pragma unroll
-                        for (int kk = 0; kk < 16; ++kk)
-                            if (kk == k) {
-                                S[kk >> 2][kk & 3] = ph;
-                                E[kk >> 2][kk & 3] = pl;
-                            }
+            // the cancelling pairs go to a block-wide list (pair index lr * 64
+            // + lc), evaluated by groups of GL lanes (a lane per GL-th
+            // dimension, the group's double-word partials folded in a fixed
+            // tree); results come back through shared memory
+            uint16_t *flist = reinterpret_cast<uint16_t *>(&Bs[0][0]);
+            float2 *fres = reinterpret_cast<float2 *>(&As[0][0]);
+            if (tid == 0) sFb = 0;
+            __syncthreads();
+            const int nmine = __popc(fb);
+            const int fbase = nmine ? atomicAdd(&sFb, nmine) : 0;
+            __syncthreads();
+            const int ftotal = sFb;
+            const int GL = d >= 256 ? 32 : 8;
+            const int ngroups = (TPB / 32) * (32 / GL);      // groups in the block
+            for (int r0 = 0; r0 < ftotal; r0 += GR_FCAP) {
+                const int rn = min(GR_FCAP, ftotal - r0);
+                {
+                    unsigned m = fb;
+                    for (int q = 0; m; ++q) {
+                        const int b = __ffs(m) - 1;
+                        m &= m - 1u;
+                        const int e = fbase + q - r0;
+                        if (e >= 0 && e < rn) flist[e] = (uint16_t)((ty * 4 + (b >> 2)) * WT + tx * 4 + (b & 3));
                     }
                 }
+                __syncthreads();
+                {
+                    // warp-uniform trip count: the groups of a warp take
+                    // consecutive entries, the whole warp shuffles
+                    const int gpw = 32 / GL, wg = lane / GL, gl = lane % GL;
+                    for (int eb = wq * gpw; eb < rn; eb += ngroups) {
+                        const int e = eb + wg;
+                        float ph = 0.f, pl = 0.f;
+                        if (e < rn) {
+                            const int pi = flist[e];
+                            const float *xa = X + (row0 + (pi >> 6)) * d, *xb = X + (col0 + (pi & 63)) * d;
+                            for (int t = gl; t < d; t += GL) {
+                                float s1, e1;
+                                two_sum(xa[t], -xb[t], s1, e1);
+                                const float p = __fmul_rn(s1, s1);
+                                float q2 = __fmaf_rn(s1, s1, -p);
+                                q2 = __fmaf_rn(__fadd_rn(s1, s1), e1, q2);
+                                dw_add(ph, pl, p, q2);
+                            }
+                        }
+                        for (int o = GL >> 1; o > 0; o >>= 1) {
+                            const float oh = __shfl_xor_sync(0xffffffffu, ph, o);
+                            const float ol = __shfl_xor_sync(0xffffffffu, pl, o);
+                            dw_add(ph, pl, oh, ol);
+                        }
+                        if (e < rn && gl == 0) fres[e] = make_float2(ph, pl);
+                    }
+                }
+                __syncthreads();
+                {
+                    unsigned m = fb;
+                    for (int q = 0; m; ++q) {
+                        const int b = __ffs(m) - 1;
+                        m &= m - 1u;
+                        const int e = fbase + q - r0;
+                        if (e >= 0 && e < rn) {
+                            const float2 v = fres[e];
+#pragma unroll
+                            for (int kk = 0; kk < 16; ++kk)
+                                if (kk == b) {
+                                    S[kk >> 2][kk & 3] = v.x;
+                                    E[kk >> 2][kk & 3] = v.y;
+                                }
+                        }
+                    }
+                }
+                __syncthreads();
             }
         } else
         for (int t0 = 0; t0 < d; t0 += WDC) {
@@ -992,7 +1042,7 @@ cudaError_t weights_launch_sym(const float *X, int64_t n, int32_t d, double sigm
         // the kept tile pairs' Gram on the tensor cores, then the terms
         if ((err = omega_gram_launch(*og, X, n, d, P.cen, P.tskip, status, wait_cycles, s, kev ? kev + 2 : nullptr)))
             return err;
-        const GramArgs ga{og->gbuf, og->item_slot, og->yh, og->yl, og->rexp, og->rnorm, P.cen};
+        const GramArgs ga{og->gbuf, og->item_slot, og->yh, og->yl, og->rexp, og->rnorm, P.cen, og->one_centre};
         k_weights_sym<false, true><<<grid, TPB, 0, ISO_S(s)>>>(X, n, d, P.shdw, is_h, is_l, tab, zskip, shrink, T,
                                                                items, nullptr, nullptr, P.tskip, 1, P.flags, P.rpart,
                                                                P.cpart, tile_counts, sh ? sh->rank : 0,

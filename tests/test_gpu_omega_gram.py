@@ -4,7 +4,9 @@ double-word CUDA-core sums (isoclust_set_omega_gram(0)): per-row omega within
 the library's bound, the MST unchanged, labels equal.  Cases cover the
 resident-row kernel (d <= 64) and the streamed one (d > 64, several 64-wide
 chunks), ragged tiles, exact duplicates and near-duplicates (where the Gram
-form cancels and the direct sums take over)."""
+form cancels and the direct sums take over, by groups of 8 lanes for short
+rows and of 32 for long ones), and rows long enough (d >= 1024) to be centred
+on one point instead of their tile's centroid."""
 import math
 
 import numpy as np
@@ -43,16 +45,23 @@ def _cases():
     out.append(("blobs_d8_dups", X, 4, 1.0))
     X = (rng.normal(size=(3001, 37)) * np.exp(rng.uniform(-4, 4, size=37))).astype(np.float32)
     out.append(("scaled_d37_ragged", X, 5, 3.0))
+    X = workloads.blobs_isotropic(seed=24, n_per=500, k=3, d=1100, dtype=np.float32)[0]
+    X[10] = X[3]                                          # an exact duplicate of a long row
+    X[400] = X[401] + np.float32(1e-5)                    # and a near-duplicate
+    out.append(("blobs_d1100_one_centre_dups", X, 3, 4.0))
     return out
 
 
-@pytest.mark.parametrize("case", range(4))
+@pytest.mark.parametrize("case", range(5))
 def test_gram_omega_against_oracle_and_cuda_cores(iso, oracle_lib, parity_report, case):
     name, X, k, sigma = _cases()[case]
     Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
     iso.set_omega_gram(True)
     g = {key: v.cpu().numpy() for key, v in iso.cluster_detail(Xd, k, sigma).items()}
-    assert iso.last_profile()["omega_symmetric"] == 3
+    prof = iso.last_profile()
+    assert prof["omega_symmetric"] == 3
+    if "dups" in name:
+        assert prof["omega_gram_direct_pairs"] > 0         # the duplicates took the direct sums
     iso.set_omega_gram(False)
     c = {key: v.cpu().numpy() for key, v in iso.cluster_detail(Xd, k, sigma).items()}
     assert iso.last_profile()["omega_symmetric"] == 2
