@@ -558,13 +558,30 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
                             dw_add(ch, cl, p, e);
                         }
                         __syncthreads();
-                        for (int t = hh; t < tl; t += 2) {
-                            const float2 D = sD[t];
-                            const float a = ryh[t0 + t], al = ryl[t0 + t];
+                        // the lower half of the block takes the chunk's first
+                        // h4 dimensions, the upper half the rest (4 at a time
+                        // when rows are 16-byte aligned)
+                        const int h4 = ((tl + 7) >> 3) << 2;
+                        const int ta = hh ? min(h4, tl) : 0, tb = hh ? tl : min(h4, tl);
+                        auto term = [&](float a, float al, float2 D) {
                             float p, e;
                             two_prod(a, D.x, p, e);
                             e = __fmaf_rn(a, D.y, __fmaf_rn(al, D.x, e));
                             dw_add(xh, xl, p, e);
+                        };
+                        if ((d & 3) == 0) {
+                            for (int t = ta; t < tb; t += 4) {
+                                const float4 a4 = *reinterpret_cast<const float4 *>(ryh + t0 + t);
+                                const float4 l4 = *reinterpret_cast<const float4 *>(ryl + t0 + t);
+                                const float4 d01 = *reinterpret_cast<const float4 *>(sD + t);
+                                const float4 d23 = *reinterpret_cast<const float4 *>(sD + t + 2);
+                                term(a4.x, l4.x, make_float2(d01.x, d01.y));
+                                term(a4.y, l4.y, make_float2(d01.z, d01.w));
+                                term(a4.z, l4.z, make_float2(d23.x, d23.y));
+                                term(a4.w, l4.w, make_float2(d23.z, d23.w));
+                            }
+                        } else {
+                            for (int t = ta; t < tb; ++t) term(ryh[t0 + t], ryl[t0 + t], sD[t]);
                         }
                     }
                     // |D|^2: the threads' chunk partials, folded in a fixed order
@@ -676,13 +693,26 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
                         if (e < rn) {
                             const int pi = flist[e];
                             const float *xa = X + (row0 + (pi >> 6)) * d, *xb = X + (col0 + (pi & 63)) * d;
-                            for (int t = gl; t < d; t += GL) {
+                            auto sq = [&](float a, float b) {
                                 float s1, e1;
-                                two_sum(xa[t], -xb[t], s1, e1);
+                                two_sum(a, -b, s1, e1);
                                 const float p = __fmul_rn(s1, s1);
                                 float q2 = __fmaf_rn(s1, s1, -p);
                                 q2 = __fmaf_rn(__fadd_rn(s1, s1), e1, q2);
                                 dw_add(ph, pl, p, q2);
+                            };
+                            if ((d & 3) == 0) {
+                                // 4 consecutive dimensions per lane and step
+                                for (int t = 4 * gl; t < d; t += 4 * GL) {
+                                    const float4 a = *reinterpret_cast<const float4 *>(xa + t);
+                                    const float4 b = *reinterpret_cast<const float4 *>(xb + t);
+                                    sq(a.x, b.x);
+                                    sq(a.y, b.y);
+                                    sq(a.z, b.z);
+                                    sq(a.w, b.w);
+                                }
+                            } else {
+                                for (int t = gl; t < d; t += GL) sq(xa[t], xb[t]);
                             }
                         }
                         for (int o = GL >> 1; o > 0; o >>= 1) {
