@@ -398,6 +398,12 @@ isoclust_status isoclust_cluster_sharded(const void *X, int64_t n, int32_t d, in
  * passes, counts[3] = tree depth.  Either pointer may be NULL. */
 void isoclust_last_profile(double *t_ms6, int64_t *counts4);
 
+/* The last one-set call's tensor-core sweep on this host thread: tiles2[0]
+ * = pairs of 128-row tiles swept over all Boruvka rounds (row tile x column
+ * tile; the pruned rounds' near and far tiles), tiles2[1] = the pairs a full
+ * sweep of every round takes (rounds x tiles^2); both 0 without that sweep. */
+void isoclust_last_mst_tiles(int64_t *tiles2);
+
 /* Tile pairs of the omega sweep in the last isoclust_cluster / _detail call
  * on this host thread: tiles3[0] = 64x64 tile pairs screened, tiles3[1] =
  * tile pairs evaluated in double-word arithmetic (the rest held only terms
@@ -468,6 +474,18 @@ int32_t isoclust_last_batched_graph_mode(void);
  * dimensions or more; 1: always; 0: never.  Process-wide; other values ->
  * INVALID_ARG. */
 isoclust_status isoclust_set_omega_gram(int32_t mode);
+
+/* Pruned Boruvka rounds for one-set calls (Section 3.5's minimum spanning
+ * tree): rows in a recursive-bisection order whose 128-row tiles are
+ * compact; each round first sweeps every tile against its near tiles, which
+ * bounds each component's lightest outgoing edge from above, and then sweeps
+ * only the pairs of tiles whose distance lower bound (centroid distance less
+ * both radii) is within the bound of some component of the row tile, and
+ * never two tiles wholly inside one component.  The tree is the same edge
+ * for edge.  mode -1 (the default): pruned for n >= 65,536 and d <= 256;
+ * 1: whenever the tensor-core sweep runs a one-set call; 0: never.
+ * Process-wide; other values -> INVALID_ARG. */
+isoclust_status isoclust_set_mst_prune(int32_t mode);
 
 /* Whether repeated batched calls may capture and replay CUDA graphs: 1 (the
  * default) allows it, 0 keeps every later batched call kernel by kernel.

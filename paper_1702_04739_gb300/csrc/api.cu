@@ -51,6 +51,7 @@ static void note_launches(long long k) { g_launches.fetch_add(k, std::memory_ord
 static thread_local char g_err[512] = "";
 static thread_local double g_prof_ms[6] = {0, 0, 0, 0, 0, 0};
 static thread_local int64_t g_prof_cnt[4] = {0, 0, 0, 0};
+static thread_local int64_t g_prof_mst_tiles[2] = {0, 0};     // tile pairs swept, and a full sweep's
 static thread_local unsigned long long g_prof_tiles[3] = {0, 0, 0};
 static thread_local int g_prof_sym = 0;
 static thread_local double g_prof_omega_kernel_ms = 0.0;
@@ -433,6 +434,12 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
         TC.shard_rank = sh->rank;
         TC.shard_world = sh->world;
     }
+    // pruned Boruvka rounds (one set, not sharded); their candidate lists
+    // (2 per slot) are all written by the first, full round too, which then
+    // sweeps PRUNE_SLOTS column splits
+    TC.prune = use_tc && !sh && prune_wanted(n, d);
+    const int tlists = TC.prune ? 2 * PRUNE_SLOTS : 0;
+    const int tsplits_used = TC.prune ? PRUNE_SLOTS : tsplits;
 
     const int dev = current_device();
     std::lock_guard<std::mutex> lock(g_call_mu[dev]);
@@ -461,7 +468,7 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
                      uint32_t **status) {
         *status = A.take<uint32_t>(4);
         M.carve(A, n, splits);
-        if (use_tc) TC.carve(A, n, d, tsplits);
+        if (use_tc) TC.carve(A, n, d, tsplits_used, 0, 1, tlists);
         if (need_labels) {
             TS.carve(A, n);
             *phi = A.take<double>(n);
@@ -513,6 +520,12 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
 
     // Section 2.2 steps 1-2: minimum spanning tree
     ISO_CUDA(mst_build(M, X, n, d, dtype, fp64_sweep, status, s, use_tc ? &TC : nullptr, 1, 0, sh));
+    const bool mst_pruned = TC.prune && TC.prune_ready;     // (the omega screen re-prepares TC later)
+    unsigned long long mst_swept = 0;
+    if (mst_pruned) {
+        ISO_CUDA(cudaMemcpyAsync(&mst_swept, TC.swept, sizeof(mst_swept), cudaMemcpyDeviceToHost, s));
+        ISO_CUDA(cudaStreamSynchronize(s));
+    }
     k_check_edges<<<1, 1, 0, ISO_S(s)>>>(M.counters, n, status);
     if (out_eu || out_ev || out_ed2) {
         if (!(out_eu && out_ev && out_ed2)) return fail(ISOCLUST_ERR_INVALID_ARG, "edge outputs must be all or none");
@@ -618,6 +631,14 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
     g_prof_cnt[1] = cnt[MC_OVF_TOTAL] + cnt[MC_OVERFLOW];
     g_prof_cnt[2] = ss.passes + (need_labels ? 1 : 0);
     g_prof_cnt[3] = ss.max_depth;
+    g_prof_mst_tiles[0] = g_prof_mst_tiles[1] = 0;
+    if (use_tc) {
+        const int64_t nt = TC.n_pad / 128;
+        g_prof_mst_tiles[1] = (int64_t)cnt[MC_ROUNDS] * nt * nt;
+        g_prof_mst_tiles[0] = g_prof_mst_tiles[1];
+        // the first round swept every tile pair, the pruned ones counted theirs
+        if (mst_pruned) g_prof_mst_tiles[0] = nt * nt + (int64_t)mst_swept;
+    }
     g_prof_tiles[0] = g_prof_tiles[1] = g_prof_tiles[2] = 0;
     if (permuted) ISO_CUDA(cudaMemcpy(g_prof_tiles, P.tiles, sizeof(g_prof_tiles), cudaMemcpyDeviceToHost));
     g_prof_sym = symmetric ? (gram ? 3 : (use_tc ? 2 : 1)) : 0;
@@ -1054,6 +1075,13 @@ int32_t isoclust_abi_version(void) { return ISOCLUST_ABI_VERSION; }
 
 int64_t isoclust_kernel_launches(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
 
+void isoclust_last_mst_tiles(int64_t *tiles2) {
+    if (tiles2) {
+        tiles2[0] = g_prof_mst_tiles[0];
+        tiles2[1] = g_prof_mst_tiles[1];
+    }
+}
+
 void isoclust_last_profile(double *t_ms6, int64_t *counts4) {
     if (t_ms6) for (int i = 0; i < 6; ++i) t_ms6[i] = g_prof_ms[i];
     if (counts4) for (int i = 0; i < 4; ++i) counts4[i] = g_prof_cnt[i];
@@ -1076,6 +1104,12 @@ isoclust_status isoclust_set_sweep_variant(int32_t variant) {
 int32_t isoclust_last_sweep_variant(void) { return tc_last_variant(); }
 
 int32_t isoclust_last_batched_graph_mode(void) { return g_last_graph_mode; }
+
+isoclust_status isoclust_set_mst_prune(int32_t mode) {
+    if (mode < -1 || mode > 1) return fail(ISOCLUST_ERR_INVALID_ARG, "mst prune mode %d is not -1, 0 or 1", mode);
+    prune_set_mode(mode);
+    return ISOCLUST_OK;
+}
 
 isoclust_status isoclust_set_omega_gram(int32_t mode) {
     if (mode < -1 || mode > 1) return fail(ISOCLUST_ERR_INVALID_ARG, "mode must be -1, 0 or 1");

@@ -76,11 +76,44 @@ struct TcScratch {
     uint64_t wait_cycles = 0;                      // bound of each sweep wait in SM cycles (0: default)
     int stall_test = 0;                            // test hook: the epilogue's first wait cannot complete
     int shard_rank = 0, shard_world = 1;           // sharded call: this rank sweeps row tiles t = rank mod world
+    // Pruned rounds (one set, set before carve): rows in a bisection order
+    // whose 128-row tiles are compact, each tile's centroid and radius, and
+    // per round the pairs of tiles that can hold a component's lightest
+    // outgoing edge (mst_prune.cu)
+    bool prune = false;
+    bool prune_ready = false;                      // the pruned row order is in place (after the first round)
+    float *tcen = nullptr;                         // [ntiles][d] tile centroids
+    float *trad = nullptr;                         // [ntiles] radii (rounded up)
+    float *tlb2 = nullptr;                         // [ntiles][ntiles] lower bound of d2 between two tiles' points
+    unsigned int *cub = nullptr;                   // [n] per component: upper bound of its lightest outgoing d2 (bits)
+    float *tmu = nullptr;                          // [ntiles] largest bound over the components of a tile's rows
+    int32_t *tcomp = nullptr;                      // [ntiles] the one component of a tile's rows, or -1
+    int4 *items_a = nullptr, *items_b = nullptr;   // [ntiles] near items, [ntiles][PRUNE_SLOTS - 1] far items
+    unsigned long long *far = nullptr;             // [2][ntiles] order construction: farthest points per node
+    unsigned long long *swept = nullptr;           // [1] tile pairs swept by the pruned rounds so far
     CUtensorMap map_h, map_l;
     // n_pad_rows / nmeans / lists: 0 = one set
     void carve(Arena &A, int64_t n, int32_t d, int splits, int64_t n_pad_rows = 0, int nmeans = 1, int lists = 0);
 };
 int tc_splits(int64_t n);
+// Pruned rounds: candidate-list slots per row (slot 0: the near tiles,
+// 1..PRUNE_SLOTS-1: the far items of the row tile) and near window (tiles).
+constexpr int PRUNE_SLOTS = 16;
+constexpr int PRUNE_NEAR = 2;
+// Whether a one-set call of n points in d dimensions prunes its rounds
+// (isoclust_set_mst_prune: -1 auto, 0 never, 1 whenever supported).
+bool prune_wanted(int64_t n, int32_t d);
+void prune_set_mode(int mode);
+int prune_mode();
+// After the first (full) round, whose keys are every point's exact nearest
+// neighbour: rows re-ordered for the pruned rounds (points whose nearest
+// neighbour is more than 4x the median distance away at the end, the others
+// in bisection order), the sweep's row data re-placed, the tile geometry.
+cudaError_t prune_reorder(TcScratch &T, const double *rowd2, const float *X, int64_t n, int32_t d, cudaStream_t s);
+// Re-place the sweep's rows (hi/lo split, norms, tile maxima) in T.perm's order.
+cudaError_t tc_place_rows(TcScratch &T, const float *X, int64_t n, int32_t d, cudaStream_t s);
+// Per round, after the near sweep: component bounds and the far items.
+cudaError_t prune_far_items(TcScratch &T, const int32_t *comp, int64_t n, const int32_t *counters, cudaStream_t s);
 bool tc_supported();
 cudaError_t tc_prepare(TcScratch &T, const float *X, int64_t n, int32_t d, cudaStream_t s);
 cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t n, int32_t d, uint32_t *status,

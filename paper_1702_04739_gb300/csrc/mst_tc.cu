@@ -208,7 +208,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
             for (int64_t w = blockIdx.x; w < items && ok; w += gridDim.x) {
                 int rt, c0, c1, sp;
                 item(w, rt, c0, c1, sp);
-                if (ARES) {
+                if (ARES && c0 < c1) {          // (an empty item only writes its rows' empty lists)
                     if (!(ok = mbar_wait(&sh->a_empty, a_phase ^ 1u, err, wait_limit))) break;
                     mbar_expect_tx(&sh->a_full, (uint32_t)(kchunks * 2 * TC_TILE_BYTES));
                     for (int kc = 0; kc < kchunks; ++kc) {
@@ -257,7 +257,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
                 int rt, c0, c1, sp;
                 item(w, rt, c0, c1, sp);
                 (void)rt;
-                if (ARES) {
+                if (ARES && c0 < c1) {
                     if (!(ok = mbar_wait(&sh->a_full, a_phase, err, wait_limit))) break;
                     tc_fence_after();
                 }
@@ -288,7 +288,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
                     mma_commit(&sh->acc_full[acc]);
                     if (++acc == TC_NACC) { acc = 0; acc_phase ^= 1u; }
                 }
-                if (ARES && ok) {
+                if (ARES && ok && c0 < c1) {
                     mma_commit(&sh->a_empty);     // A region free once this item's MMAs are done
                     a_phase ^= 1u;
                 }
@@ -1115,6 +1115,18 @@ void TcScratch::carve(Arena &A, int64_t n, int32_t d, int splits_, int64_t n_pad
     tu = A.take<float>((size_t)lists * n_pad);
     err = A.take<uint32_t>(4);
     setcnt = nmeans > 1 || n_pad_rows > 0 ? A.take<int32_t>((size_t)(nmeans > 0 ? nmeans : 1)) : nullptr;
+    if (prune) {
+        tcen = A.take<float>((size_t)nt * d);
+        trad = A.take<float>(nt);
+        tlb2 = A.take<float>((size_t)nt * nt);
+        cub = A.take<unsigned int>(n);
+        tmu = A.take<float>(nt);
+        tcomp = A.take<int32_t>(nt);
+        items_a = A.take<int4>(nt);
+        items_b = A.take<int4>((size_t)nt * (PRUNE_SLOTS - 1));
+        far = A.take<unsigned long long>((size_t)4 * nt);
+        swept = A.take<unsigned long long>(1);
+    }
 }
 
 namespace {
@@ -1158,7 +1170,8 @@ cudaError_t tc_autotune(TcScratch &T, MstScratch &S, const float *X, int64_t n, 
     int dev = 0;
     cudaError_t e;
     if ((e = cudaGetDevice(&dev))) return e;
-    const TuneKey key{dev, T.set_of != nullptr, T.d_pad, ilog2(T.n_pad), ilog2(items > 0 ? items : 1)};
+    const TuneKey key{dev, (T.set_of != nullptr ? 1 : 0) | (T.prune ? 2 : 0), T.d_pad, ilog2(T.n_pad),
+                      ilog2(items > 0 ? items : 1)};
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
         auto it = g_tune.find(key);
@@ -1213,6 +1226,7 @@ cudaError_t tc_autotune(TcScratch &T, MstScratch &S, const float *X, int64_t n, 
     if (e) return e;
     // restore the round counters (the trials only touched the rescan queue)
     if ((e = cudaMemcpy(S.counters, saved, sizeof(saved), cudaMemcpyHostToDevice))) return e;
+    if (T.swept && (e = cudaMemsetAsync(T.swept, 0, sizeof(unsigned long long), s))) return e;
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
         g_tune[key] = best;
@@ -1305,6 +1319,7 @@ cudaError_t tc_prepare(TcScratch &T, const float *X, int64_t n, int32_t d, cudaS
         k_tc_mean_partial<<<gm, 128, 0, ISO_S(s)>>>(X, n, d, rows_per, T.part);
         k_tc_mean_final<<<(unsigned)ceil_div(d, 128), 128, 0, ISO_S(s)>>>(T.part, 64, n, d, T.mean);
     }
+    T.prune_ready = false;           // (pruned rounds start after the first, in their own row order)
     if (T.keep_order) {
         // rows as given (the omega screen works in omega's row order)
         k_tc_identity<<<(unsigned)ceil_div(T.n_pad, 256), 256, 0, ISO_S(s)>>>(T.permp, n, T.n_pad);
@@ -1325,6 +1340,7 @@ cudaError_t tc_prepare(TcScratch &T, const float *X, int64_t n, int32_t d, cudaS
     k_tc_norms<<<(unsigned)ceil_div(T.n_pad, 256), 256, 0, ISO_S(s)>>>(T.xh, T.xl, T.permp, T.n_pad, T.d_pad, T.nrm,
                                                                       T.cnrm, T.rsq, T.nmax_bits);
     k_tc_tile_max<<<(unsigned)ceil_div(T.n_pad / TC_BM, 128), 128, 0, ISO_S(s)>>>(T.nrm, T.n_pad, T.tmax, T.tsq);
+    if (T.swept && (e = cudaMemsetAsync(T.swept, 0, sizeof(unsigned long long), s))) return e;
     if (sets) {
         // lists that no item writes (sets with fewer splits) stay empty
         const int64_t nv = (int64_t)T.lists * T.n_pad * TC_TOPK, nu = (int64_t)T.lists * T.n_pad;
@@ -1354,6 +1370,20 @@ cudaError_t tc_prepare(TcScratch &T, const float *X, int64_t n, int32_t d, cudaS
     return cudaGetLastError();
 }
 
+cudaError_t tc_place_rows(TcScratch &T, const float *X, int64_t n, int32_t d, cudaStream_t s) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(T.permp, 0xff, sizeof(int32_t) * T.n_pad, s))) return e;     // -1: padding
+    k_tc_place<<<(unsigned)ceil_div(n, 256), 256, 0, ISO_S(s)>>>(T.perm, n, nullptr, nullptr, nullptr, T.permp);
+    const int64_t tot = T.n_pad * T.d_pad;
+    k_tc_split<<<(unsigned)ceil_div(tot, 256), 256, 0, ISO_S(s)>>>(X, T.mean, nullptr, T.permp, d, T.n_pad, T.d_pad,
+                                                                  T.xh, T.xl, T.xs);
+    if ((e = cudaMemsetAsync(T.nmax_bits, 0, sizeof(unsigned int), s))) return e;
+    k_tc_norms<<<(unsigned)ceil_div(T.n_pad, 256), 256, 0, ISO_S(s)>>>(T.xh, T.xl, T.permp, T.n_pad, T.d_pad, T.nrm,
+                                                                      T.cnrm, T.rsq, T.nmax_bits);
+    k_tc_tile_max<<<(unsigned)ceil_div(T.n_pad / TC_BM, 128), 128, 0, ISO_S(s)>>>(T.nrm, T.n_pad, T.tmax, T.tsq);
+    return cudaGetLastError();
+}
+
 cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t n, int32_t d, uint32_t *status,
                            cudaStream_t s) {
     const int ntiles = (int)(T.n_pad / TC_BM);
@@ -1361,9 +1391,8 @@ cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t 
     // a sharded call sweeps the row tiles t with t mod world == rank
     const int64_t own_tiles = T.shard_rank < ntiles
                                   ? ((int64_t)ntiles - T.shard_rank + T.shard_world - 1) / T.shard_world : 0;
-    const int64_t items = T.items ? T.nitems : own_tiles * T.splits;
     const int64_t nsm = (int64_t)num_sms();
-    const unsigned grid = (unsigned)(items < nsm ? (items > 0 ? items : 1) : nsm);
+    const bool pruned = T.prune && T.prune_ready && !T.items && T.shard_world == 1;
     const int64_t gblocks = ceil_div(T.n_pad, 256), gcap = (int64_t)num_sms() * 8;
     k_tc_gather_comp<<<(unsigned)(gblocks < gcap ? gblocks : gcap), 256, 0, ISO_S(s)>>>(S.comp, T.permp, T.n_pad,
                                                                                        T.compp, S.counters);
@@ -1376,27 +1405,38 @@ cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t 
     const double u = 1.1920928955078125e-07;   // 2^-23
     const float acoef = (float)(1.25 * 2.0 * (3.0 * T.d_pad * u + 3.814697265625e-06));
     const float bcoef = (float)(1.25 * 8.0 * 5.9604644775390625e-08);
+    // one sweep launch over an item list (null: row tile x column split)
+    auto sweep = [&](const int4 *wit, int64_t nwit) {
+        const int64_t items = wit ? nwit : own_tiles * T.splits;
+        const unsigned grid = (unsigned)(items < nsm ? (items > 0 ? items : 1) : nsm);
 #define ISO_SWEEP_LAUNCH(AKV, CWV)                                                                                \
     k_sweep_tc<AKV, false, CWV><<<grid, TC_THREADS, tc_smem(AKV), ISO_S(s)>>>(                                         \
         T.map_h, T.map_l, T.nrm, T.cnrm, T.rsq, T.tmax, T.tsq, acoef, bcoef, T.compp, T.n_pad, ntiles, kchunks,      \
-        T.splits, T.items, T.nitems, T.setcnt, S.counters, T.tv, T.tj, T.tu, T.err, ScreenArgs{},           \
-        tc_wait_limit(T), T.stall_test, T.items ? 1 : T.shard_world, T.items ? 0 : T.shard_rank)
-    if (kchunks == 1 && T.resident)
-        {
-        if (T.cw == 32) ISO_SWEEP_LAUNCH(1, 32);
-        else ISO_SWEEP_LAUNCH(1, 64);
-    }
-    else if (kchunks == 2 && T.resident)
-        {
-        if (T.cw == 32) ISO_SWEEP_LAUNCH(2, 32);
-        else ISO_SWEEP_LAUNCH(2, 64);
-    }
-    else
-        {
-        if (T.cw == 32) ISO_SWEEP_LAUNCH(0, 32);
-        else ISO_SWEEP_LAUNCH(0, 64);
-    }
+        T.splits, wit, nwit, T.setcnt, S.counters, T.tv, T.tj, T.tu, T.err, ScreenArgs{},                        \
+        tc_wait_limit(T), T.stall_test, wit ? 1 : T.shard_world, wit ? 0 : T.shard_rank)
+        if (kchunks == 1 && T.resident) {
+            if (T.cw == 32) ISO_SWEEP_LAUNCH(1, 32);
+            else ISO_SWEEP_LAUNCH(1, 64);
+        } else if (kchunks == 2 && T.resident) {
+            if (T.cw == 32) ISO_SWEEP_LAUNCH(2, 32);
+            else ISO_SWEEP_LAUNCH(2, 64);
+        } else {
+            if (T.cw == 32) ISO_SWEEP_LAUNCH(0, 32);
+            else ISO_SWEEP_LAUNCH(0, 64);
+        }
 #undef ISO_SWEEP_LAUNCH
+    };
+    if (pruned) {
+        // near tiles first (candidate list slot 0); their candidates bound
+        // each component's lightest edge, which decides the far items
+        // (slots 1 .. PRUNE_SLOTS - 1)
+        sweep(T.items_a, ntiles);
+        cudaError_t pe = prune_far_items(T, S.comp, n, S.counters, s);
+        if (pe != cudaSuccess) return pe;
+        sweep(T.items_b, (int64_t)ntiles * (PRUNE_SLOTS - 1));
+    } else {
+        sweep(T.items, T.nitems);
+    }
     // representation error of a centred point by BF16 hi + lo: 2^-18 relative
     // per element, plus the FP32 rounding of x - c (2^-24); 25 % headroom
     const double eps_rep = 1.25 * (3.814697265625e-06 + 5.9604644775390625e-08);

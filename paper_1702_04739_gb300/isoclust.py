@@ -117,8 +117,12 @@ def load(build_if_missing: bool = True):
         lib.isoclust_set_batched_graphs.argtypes = [ctypes.c_int32]
         lib.isoclust_set_omega_gram.restype = ctypes.c_int
         lib.isoclust_set_omega_gram.argtypes = [ctypes.c_int32]
+        lib.isoclust_set_mst_prune.restype = ctypes.c_int
+        lib.isoclust_set_mst_prune.argtypes = [ctypes.c_int32]
         lib.isoclust_set_test_stalled_wait.restype = ctypes.c_int
         lib.isoclust_set_test_stalled_wait.argtypes = [ctypes.c_int32]
+        lib.isoclust_last_mst_tiles.restype = None
+        lib.isoclust_last_mst_tiles.argtypes = [_P]
         lib.isoclust_last_omega_tiles.restype = None
         lib.isoclust_last_omega_tiles.argtypes = [_P]
         _lib = lib
@@ -439,6 +443,13 @@ def set_omega_gram(mode) -> None:
     _check(load().isoclust_set_omega_gram(int(mode)))
 
 
+def set_mst_prune(mode) -> None:
+    """Pruned Boruvka rounds of one-set calls: True / 1 whenever supported,
+    False / 0 never, -1 by size and dimension, the default
+    (isoclust_set_mst_prune)."""
+    _check(load().isoclust_set_mst_prune(int(mode)))
+
+
 def set_test_stalled_wait(on: bool) -> None:
     """Test hook of the timeout path (isoclust_set_test_stalled_wait): while
     on, every tensor-core sweep's epilogue waits for a barrier nothing
@@ -459,11 +470,14 @@ def last_profile() -> dict:
     lib.isoclust_last_profile(t, c)
     tl = (ctypes.c_int64 * 3)()
     lib.isoclust_last_omega_tiles(tl)
+    mt = (ctypes.c_int64 * 2)()
+    lib.isoclust_last_mst_tiles(mt)
     gb, gf = ctypes.c_int64(0), ctypes.c_int64(0)
     gms = float(lib.isoclust_last_omega_gram_ms(ctypes.byref(gb), ctypes.byref(gf)))
     return dict(omega_tiles=tl[0], omega_tiles_dw=tl[1], omega_symmetric=tl[2],
                 omega_kernel_ms=float(lib.isoclust_last_omega_kernel_ms()),
-                omega_gram_ms=gms, omega_gram_blocks=int(gb.value), omega_gram_direct_pairs=int(gf.value), validate_ms=t[0], weights_ms=t[1], mst_ms=t[2], orient_ms=t[3], search_ms=t[4], labels_ms=t[5],
+                omega_gram_ms=gms, omega_gram_blocks=int(gb.value), omega_gram_direct_pairs=int(gf.value),
+                mst_tiles_swept=mt[0], mst_tiles_full=mt[1], validate_ms=t[0], weights_ms=t[1], mst_ms=t[2], orient_ms=t[3], search_ms=t[4], labels_ms=t[5],
                 boruvka_rounds=c[0], rescanned_rows=c[1], alg1_passes=c[2], tree_depth=c[3])
 
 

@@ -137,3 +137,4 @@ def test_process_settings_validate_their_argument():
     assert L.isoclust_set_batched_graphs(2) == 1 and L.isoclust_set_test_stalled_wait(-1) == 1
     assert L.isoclust_set_batched_graphs(1) == 0 and L.isoclust_set_test_stalled_wait(0) == 0
     assert L.isoclust_set_omega_gram(2) == 1 and L.isoclust_set_omega_gram(-1) == 0
+    assert L.isoclust_set_mst_prune(-2) == 1 and L.isoclust_set_mst_prune(-1) == 0
