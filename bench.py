@@ -237,19 +237,22 @@ def omega_gram_roofline(prof, peaks, src, alu_peak, sms, sweep_ms, items, d, alg
     """omega with the Gram on the tensor cores: two kernels.  The Gram kernel
     (tensor-bound: 34 BF16 digit-plane products of 2 x 128 x 64 x d_pad
     flop per 128 x 64 block, executed) and the sweep that reads it
-    (ALU-bound: per kept 64 x 64 tile pair, 4096 pairs x ~150 FP32-pipe
-    instructions (d2 from G, root, exp, accumulation) plus 128 cross terms of
-    21 d + 2400 lane instructions; pairs that fall back to direct sums are
-    not counted).  The line's roofline is the slower of the two."""
+    (ALU-bound, FP32-pipe instructions of the algorithm as built: per pair of
+    a kept 64 x 64 tile pair 155 (d2 from G and the parts' size 40, root and
+    Newton correction 25, shift 20, double-word exp 50, two accumulations
+    20); per off-diagonal tile pair with tile centres (d < 1024) 128 cross
+    terms of 14 d and |D|^2 of 12 d; per pair that took the direct sum
+    18.75 d + 60).  The line's roofline is the slower of the two."""
     g_ms = statistics.mean(p["omega_gram_ms"] for p in prof)
     blocks = prof[-1]["omega_gram_blocks"]
     d_pad = -(-d // 64) * 64
     tc_flop = blocks * 34 * 2.0 * 128 * 64 * d_pad
     bf16 = peaks.get("bf16_tflops", 1900.0)
     tc = tc_flop / (g_ms / 1000.0) / 1e12 if g_ms > 0 else 0.0
-    sw_ops = items * (4096.0 * 150.0 + 128.0 * (21.0 * d + 2400.0))
-    sw = sw_ops / (sweep_ms / 1000.0) / 1e12 if sweep_ms > 0 else 0.0
     direct = prof[-1].get("omega_gram_direct_pairs", 0)
+    cross = 0.0 if d >= 1024 else items * (128.0 * 14.0 * d + 12.0 * d)
+    sw_ops = items * 4096.0 * 155.0 + cross + direct * (18.75 * d + 60.0)
+    sw = sw_ops / (sweep_ms / 1000.0) / 1e12 if sweep_ms > 0 else 0.0
     gram_k = {"kernel": "k_oz_gram (omega Gram, tcgen05 BF16 digit planes)", "bound": "tensor", "kernel_ms": g_ms,
               "achieved": tc, "peak": bf16, "unit": "TFLOP/s", "frac": tc / bf16, "blocks": blocks}
     sweep_k = {"kernel": "k_weights_sym<GRAM> (omega terms from the Gram, double-word FP32)", "bound": "alu",
@@ -261,7 +264,9 @@ def omega_gram_roofline(prof, peaks, src, alu_peak, sms, sweep_ms, items, d, alg
     out = dict(top, traffic=None,
                note=f"omega's Gram on the tensor cores: the Gram kernel {g_ms:.2f} ms ({blocks} blocks of 128 x 64, 34 "
                     f"digit-plane MMAs per 16 dimensions, executed flop over the measured BF16 peak, {src}) and the "
-                    f"sweep reading it {sweep_ms:.2f} ms (FP32-pipe instructions of the algorithm as built over "
+                    f"sweep reading it {sweep_ms:.2f} ms (FP32-pipe instructions of the algorithm as built - 155 per "
+                    f"pair, cross terms {'none: one centre' if d >= 1024 else '128 x 14 d per tile pair'}, "
+                    f"18.75 d + 60 per direct pair - over "
                     f"{sms} SMs x 128 lanes x max SM clock); the line reports the slower one",
                other_kernel=other,
                algorithmic={"achieved": alg, "unit": "FP64-equivalent TFLOP/s", "peak": None,

@@ -519,6 +519,9 @@ cudaError_t mst_build(MstScratch &S, const void *X, int64_t n, int32_t d, int dt
     const int L = log2_ceil(span) + 1;
     const unsigned rg = round_grid(n);
     cudaError_t e;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if ((e = cudaStreamIsCapturing(s, &cs))) return e;
+    const bool capturing = cs != cudaStreamCaptureStatusNone;
     if (tc && (e = tc_prepare(*tc, (const float *)X, n, d, s))) return e;
     if (tc && (e = tc_count_sets(*tc, S.comp, n, S.counters, s))) return e;
     if (tc && (e = tc_autotune(*tc, S, (const float *)X, n, d, status, s))) return e;
@@ -549,6 +552,15 @@ cudaError_t mst_build(MstScratch &S, const void *X, int64_t n, int32_t d, int dt
         k_relabel<<<rg, TPB, 0, ISO_S(s)>>>(S.comp, na, n, S.counters);
         if (tc && (e = tc_count_sets(*tc, S.comp, n, S.counters, s))) return e;
         k_round_end<<<1, 1, 0, ISO_S(s)>>>(S.counters);
+        // one point set whose tree is complete: the rounds left would only
+        // launch kernels that return at once (independent sets keep every
+        // round, so a call launches the same kernels as its CUDA graph)
+        if (target == 1 && !capturing && r + 1 < R) {
+            int32_t h[8];
+            if ((e = cudaMemcpyAsync(h, S.counters, sizeof(h), cudaMemcpyDeviceToHost, s))) return e;
+            if ((e = cudaStreamSynchronize(s))) return e;
+            if (h[MC_NCOMP] <= h[MC_TARGET]) break;
+        }
     }
     if (tc) k_or_err<<<1, 1, 0, ISO_S(s)>>>(tc->err, status);
     return cudaGetLastError();
