@@ -354,7 +354,12 @@ k_oz_gram(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                             for (int m = 0; m < OZ_G; ++m) Q[m] = __uint_as_float(q[m][c]);
                             float h, l;
                             oz_fold(Q, h, l);
-                            dw_add(gh[cg * 8 + c], gl[cg * 8 + c], h, l);
+                            if (kc == 0) {          // (h, l) is normalised: the same as adding it to zero
+                                gh[cg * 8 + c] = h;
+                                gl[cg * 8 + c] = l;
+                            } else {
+                                dw_add(gh[cg * 8 + c], gl[cg * 8 + c], h, l);
+                            }
                         }
                     }
                 }

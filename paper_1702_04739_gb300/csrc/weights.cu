@@ -912,19 +912,32 @@ __global__ void k_weights_reduce(const unsigned long long *__restrict__ nnbits, 
                                  double inv_sigma, int include_self, const uint8_t *__restrict__ flags,
                                  const float2 *__restrict__ rpart, const float2 *__restrict__ cpart,
                                  double *__restrict__ omega, double *__restrict__ part64) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    const int64_t I = r / WT, c = r - I * WT;
+    // a warp is 32 rows of one 64-row tile I (blocks of 256 rows): its lanes
+    // read the flags of 32 tile pairs at once; the kept pairs' partials are
+    // then added in ascending J, the order of a plain loop over J
+    const int64_t r0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+    if (r0 >= n) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t r = r0 + lane;
+    const int64_t I = r0 / WT, c = r - I * WT;
+    auto item = [&](int64_t J) {
+        return J < I ? J * T - J * (J - 1) / 2 + (I - J)      // item (J, I): r is a column
+                     : I * T - I * (I - 1) / 2 + (J - I);     // item (I, J): r is a row
+    };
     float h = 0.f, l = 0.f;
-    for (int64_t J = 0; J < T; ++J) {
-        if (J < I) {
-            const int64_t w = J * T - J * (J - 1) / 2 + (I - J);      // item (J, I): r is a column
-            if (flags[w]) dw_add(h, l, cpart[w * WT + c].x, cpart[w * WT + c].y);
-        } else {
-            const int64_t w = I * T - I * (I - 1) / 2 + (J - I);      // item (I, J): r is a row
-            if (flags[w]) dw_add(h, l, rpart[w * WT + c].x, rpart[w * WT + c].y);
+    for (int64_t J0 = 0; J0 < T; J0 += 32) {
+        const int64_t Jl = J0 + lane;
+        const bool kept = Jl < T && flags[item(Jl)];
+        unsigned m = __ballot_sync(0xffffffffu, kept);
+        while (m) {
+            const int64_t J = J0 + (__ffs(m) - 1);
+            m &= m - 1u;
+            const int64_t w = item(J);
+            const float2 v = J < I ? cpart[w * WT + c] : rpart[w * WT + c];
+            dw_add(h, l, v.x, v.y);
         }
     }
+    if (r >= n) return;
     if (part64) {                 // sharded call: this rank's share, combined across ranks first
         part64[r] = __dadd_rn((double)h, (double)l);
         return;
