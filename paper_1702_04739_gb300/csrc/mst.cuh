@@ -113,7 +113,8 @@ cudaError_t prune_reorder(TcScratch &T, const double *rowd2, const float *X, int
 // Re-place the sweep's rows (hi/lo split, norms, tile maxima) in T.perm's order.
 cudaError_t tc_place_rows(TcScratch &T, const float *X, int64_t n, int32_t d, cudaStream_t s);
 // Per round, after the near sweep: component bounds and the far items.
-cudaError_t prune_far_items(TcScratch &T, const int32_t *comp, int64_t n, const int32_t *counters, cudaStream_t s);
+cudaError_t prune_far_items(TcScratch &T, const int32_t *comp, const double *rowd2, const int32_t *rowj, int64_t n,
+                            const int32_t *counters, cudaStream_t s);
 bool tc_supported();
 cudaError_t tc_prepare(TcScratch &T, const float *X, int64_t n, int32_t d, cudaStream_t s);
 cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t n, int32_t d, uint32_t *status,

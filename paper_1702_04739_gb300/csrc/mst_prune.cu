@@ -9,7 +9,8 @@
 // PRUNE_NEAR tiles on either side in a bisection order whose tiles are
 // compact); the candidates found there bound each component's lightest
 // outgoing d2 from above (UB, rigorous: the sweep's upper bound of the
-// represented d2 plus the BF16 representation error).  A far tile pair is
+// represented d2 plus the BF16 representation error, or the exact d2 of a
+// row's best pair of the previous round whose points are still apart).  A far tile pair is
 // then swept only if LB(R, C) <= max over R's rows of their component's UB,
 // and not when both tiles lie wholly inside one component.  Pairs left out
 // have every d2 > UB of each component of R's rows, so no component's
@@ -63,22 +64,35 @@ __device__ __forceinline__ float pr_d2_warp(const float *__restrict__ x, const f
 }
 
 // PASS 0: farthest point of each node from its first point; PASS 1: from
-// that point.  far[node] = max (d2 bits, index).  One warp per position.
+// that point.  far[node] = max (d2 bits, index).  A warp takes PR_FAR_ROWS
+// consecutive positions (lanes over dimensions) and keeps the running
+// maximum of its current node, so the top levels' nodes see one atomic per
+// run of positions instead of one per point.
+constexpr int PR_FAR_ROWS = 32;
 template <int PASS>
 __global__ void k_pr_far(const float *__restrict__ X, int64_t n, int32_t d, const int32_t *__restrict__ perm,
                          int64_t T, int l, const unsigned long long *__restrict__ far0,
                          unsigned long long *__restrict__ far) {
-    const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t p0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * PR_FAR_ROWS;
     const int lane = threadIdx.x & 31;
-    if (p >= n) return;
-    int64_t a, b;
-    const uint32_t id = pr_node(p / PR_BM, T, l, a, b);
-    if (b - a <= 1) return;                                  // a single tile: not split further
-    const int32_t i = perm[p];
-    const int64_t ref = PASS == 0 ? (int64_t)perm[a * PR_BM] : (int64_t)(uint32_t)(far0[id] & 0xffffffffull);
-    const float v = pr_d2_warp(X + (int64_t)i * d, X + ref * d, d, lane);
-    if (lane == 0)
-        atomicMax(far + id, ((unsigned long long)__float_as_uint(v) << 32) | (unsigned long long)(uint32_t)i);
+    uint32_t cur = 0xffffffffu;
+    unsigned long long best = 0;
+    for (int64_t p = p0; p < p0 + PR_FAR_ROWS && p < n; ++p) {
+        int64_t a, b;
+        const uint32_t id = pr_node(p / PR_BM, T, l, a, b);
+        if (b - a <= 1) continue;                            // a single tile: not split further
+        if (id != cur) {
+            if (cur != 0xffffffffu && lane == 0) atomicMax(far + cur, best);
+            cur = id;
+            best = 0;
+        }
+        const int32_t i = perm[p];
+        const int64_t ref = PASS == 0 ? (int64_t)perm[a * PR_BM] : (int64_t)(uint32_t)(far0[id] & 0xffffffffull);
+        const float v = pr_d2_warp(X + (int64_t)i * d, X + ref * d, d, lane);
+        const unsigned long long key = ((unsigned long long)__float_as_uint(v) << 32) | (unsigned long long)(uint32_t)i;
+        best = key > best ? key : best;
+    }
+    if (cur != 0xffffffffu && lane == 0) atomicMax(far + cur, best);
 }
 
 // sort key of position p: (node, projection on the node's far pair's line)
@@ -210,22 +224,36 @@ __device__ __forceinline__ bool pr_active(const int32_t *counters) {
 // the near sweep: per row, the smallest upper bound of a candidate's
 // represented d2 (lists 0 and 1), widened by the representation error as
 // the recheck does, then the minimum over the component's rows.
+// Also, the row's exact best pair of the previous round (rowd2, rowj), when
+// its other point is still in another component: a real outgoing edge, so
+// its exact d2 (rounded up) bounds the component's lightest one too; this is
+// what keeps the bound tight for large components, whose rows see only
+// their own component among their near tiles.
 __global__ void k_pr_comp_ub(const float *__restrict__ tu, const int32_t *__restrict__ permp,
                              const int32_t *__restrict__ comp, const float *__restrict__ rsq,
-                             const unsigned int *__restrict__ nmax_bits, int64_t n_pad, float eps_rep,
+                             const unsigned int *__restrict__ nmax_bits, const double *__restrict__ rowd2,
+                             const int32_t *__restrict__ rowj, int64_t n_pad, float eps_rep,
                              unsigned int *__restrict__ cub, const int32_t *counters) {
     if (!pr_active(counters)) return;
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_pad) return;
     const int32_t i = permp[r];
     if (i < 0) return;
+    const int32_t ci = comp[i];
+    float ub = INFINITY;
     const float U = fminf(tu[r], tu[n_pad + r]);
-    if (!(U < INFINITY)) return;
-    const float smax = __fsqrt_ru(__uint_as_float(*nmax_bits));
-    const float w = __fmul_ru(eps_rep, __fadd_ru(rsq[r], smax));
-    const float a1 = __fadd_ru(__fsqrt_ru(fmaxf(U, 0.0f)), w);
-    const float ub = __fmul_ru(__fmul_ru(a1, a1), 1.00001f);
-    atomicMin(cub + comp[i], __float_as_uint(ub));           // non-negative: bits are monotone
+    if (U < INFINITY) {
+        const float smax = __fsqrt_ru(__uint_as_float(*nmax_bits));
+        const float w = __fmul_ru(eps_rep, __fadd_ru(rsq[r], smax));
+        const float a1 = __fadd_ru(__fsqrt_ru(fmaxf(U, 0.0f)), w);
+        ub = __fmul_ru(__fmul_ru(a1, a1), 1.00001f);
+    }
+    const int32_t j = rowj[i];
+    if (j >= 0 && comp[j] != ci) {
+        const double d2 = rowd2[i];
+        if (d2 < INFINITY) ub = fminf(ub, __double2float_ru(d2));
+    }
+    if (ub < INFINITY) atomicMin(cub + ci, __float_as_uint(ub));   // non-negative: bits are monotone
 }
 
 // Per tile: the largest bound over its rows' components (+inf when one has
@@ -381,14 +409,15 @@ static cudaError_t prune_geometry(TcScratch &T, const float *X, int64_t n, int32
 static cudaError_t prune_bisect(TcScratch &T, const float *X, int64_t m, int32_t d, cudaStream_t s) {
     const int64_t nt = ceil_div(m, PR_BM);
     const unsigned gw = (unsigned)ceil_div(m * 32, 256);          // a warp per position
+    const unsigned gf = (unsigned)ceil_div(ceil_div(m, PR_FAR_ROWS) * 32, 256);   // a warp per PR_FAR_ROWS positions
     int levels = 0;
     while (((int64_t)1 << levels) < nt) ++levels;
     cudaError_t e;
     unsigned long long *far0 = T.far, *far1 = T.far + 2 * nt;
     for (int l = 0; l < levels; ++l) {
         if ((e = cudaMemsetAsync(T.far, 0, sizeof(unsigned long long) * 4 * nt, s))) return e;
-        k_pr_far<0><<<gw, 256, 0, ISO_S(s)>>>(X, m, d, T.perm, nt, l, nullptr, far0);
-        k_pr_far<1><<<gw, 256, 0, ISO_S(s)>>>(X, m, d, T.perm, nt, l, far0, far1);
+        k_pr_far<0><<<gf, 256, 0, ISO_S(s)>>>(X, m, d, T.perm, nt, l, nullptr, far0);
+        k_pr_far<1><<<gf, 256, 0, ISO_S(s)>>>(X, m, d, T.perm, nt, l, far0, far1);
         k_pr_keys<<<gw, 256, 0, ISO_S(s)>>>(X, m, d, T.perm, nt, l, far0, far1, T.keys);
         // stable: ties keep the previous level's order
         if ((e = sort_pairs_u64(T.keys, T.perm, T.kbuf, T.vbuf, m, s))) return e;
@@ -427,15 +456,16 @@ static cudaError_t prune_geometry(TcScratch &T, const float *X, int64_t n, int32
     return cudaGetLastError();
 }
 
-cudaError_t prune_far_items(TcScratch &T, const int32_t *comp, int64_t n, const int32_t *counters, cudaStream_t s) {
+cudaError_t prune_far_items(TcScratch &T, const int32_t *comp, const double *rowd2, const int32_t *rowj, int64_t n,
+                            const int32_t *counters, cudaStream_t s) {
     const int64_t nt = T.n_pad / PR_BM;
     (void)n;
     cudaError_t e;
     if ((e = cudaMemsetAsync(T.cub, 0xff, sizeof(unsigned int) * n, s))) return e;
     const double eps_rep = 1.25 * (3.814697265625e-06 + 5.9604644775390625e-08);
     k_pr_comp_ub<<<(unsigned)ceil_div(T.n_pad, 256), 256, 0, ISO_S(s)>>>(T.tu, T.permp, comp, T.rsq, T.nmax_bits,
-                                                                        T.n_pad, (float)(eps_rep * 1.0001), T.cub,
-                                                                        counters);
+                                                                        rowd2, rowj, T.n_pad,
+                                                                        (float)(eps_rep * 1.0001), T.cub, counters);
     k_pr_tile_mu<<<(unsigned)nt, 128, 0, ISO_S(s)>>>(T.permp, comp, T.cub, T.tmu, T.tcomp, counters);
     k_pr_far_items<<<(unsigned)nt, 256, sizeof(uint32_t) * ceil_div(nt, 32), ISO_S(s)>>>(T.tlb2, T.tmu, T.tcomp, nt,
                                                                                        T.items_b, T.swept, counters);

@@ -1431,7 +1431,7 @@ cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t 
         // each component's lightest edge, which decides the far items
         // (slots 1 .. PRUNE_SLOTS - 1)
         sweep(T.items_a, ntiles);
-        cudaError_t pe = prune_far_items(T, S.comp, n, S.counters, s);
+        cudaError_t pe = prune_far_items(T, S.comp, S.rowd2, S.rowj, n, S.counters, s);
         if (pe != cudaSuccess) return pe;
         sweep(T.items_b, (int64_t)ntiles * (PRUNE_SLOTS - 1));
     } else {
