@@ -486,18 +486,69 @@ struct DpArgs {
 
 // One warp walks from leaf v towards the root, deciding each vertex for the
 // 32 thresholds of its lanes; returns this lane's cuts.
+// Folds the children [c0, c1) of a vertex into (w, pv) for this lane's
+// threshold, in descending index: a joined child adds its omega-hat and
+// p-hat, any other its parent edge's phi.  With up to DP_FEW children their
+// indices are loaded in one round and their states in the next (a walk's
+// steps are latency-bound); more children are folded one by one.
+constexpr int DP_FEW = 4;
+__device__ __forceinline__ void dp_fold_children(const DpArgs &A, int32_t c0, int32_t c1, int lane,
+                                                 const uint8_t *__restrict__ dec, const double *__restrict__ wh,
+                                                 const double *__restrict__ ph, double &w, double &pv) {
+    const int32_t nc = c1 - c0;
+    if (nc <= DP_FEW) {
+        int32_t ch[DP_FEW];
+#pragma unroll
+        for (int q = 0; q < DP_FEW; ++q) ch[q] = q < nc ? A.ch_list[c0 + q] : 0;
+        uint8_t dcv[DP_FEW];
+        double cw[DP_FEW], cp[DP_FEW], cf[DP_FEW];
+#pragma unroll
+        for (int q = 0; q < DP_FEW; ++q) {
+            dcv[q] = DEC_DISCARD;
+            cw[q] = cp[q] = cf[q] = 0.0;
+            if (q < nc) {
+                const size_t cl = (size_t)ch[q] * DP_LANES + lane;
+                dcv[q] = ld_cg_u8(dec + cl);
+                cw[q] = ld_cg_f64(wh + cl);
+                cp[q] = ld_cg_f64(ph + cl);
+                cf[q] = A.phi[ch[q]];
+            }
+        }
+#pragma unroll
+        for (int q = DP_FEW - 1; q >= 0; --q) {       // siblings in descending index
+            if (q < nc) {
+                if (dcv[q] == DEC_JOIN) {
+                    w = __dadd_rn(w, cw[q]);
+                    pv = __dadd_rn(pv, cp[q]);
+                } else {
+                    pv = __dadd_rn(pv, cf[q]);          // cut or discarded child: boundary edge
+                }
+            }
+        }
+    } else {
+        for (int32_t q = c1 - 1; q >= c0; --q) {       // siblings in descending index
+            const int32_t c = A.ch_list[q];
+            const size_t cl = (size_t)c * DP_LANES + lane;
+            const uint8_t dc = ld_cg_u8(dec + cl);
+            if (dc == DEC_JOIN) {
+                w = __dadd_rn(w, ld_cg_f64(wh + cl));
+                pv = __dadd_rn(pv, ld_cg_f64(ph + cl));
+            } else {
+                pv = __dadd_rn(pv, A.phi[c]);
+            }
+        }
+    }
+}
+
 // One warp walks from leaf v towards the root, deciding each vertex for the
 // 32 thresholds of its lanes; returns this lane's cuts.
 __device__ __forceinline__ int dp_walk_tree(const DpArgs &A, int32_t v, double N, int lane, int final_pass,
                                        uint8_t *__restrict__ dec, double *__restrict__ wh, double *__restrict__ ph,
                                        int32_t *__restrict__ done, double *__restrict__ rat) {
     // The walk's critical path is the tree's longest chain of handoffs, and
-    // each step's memory round trips are its latency: a vertex with up to
-    // DP_FEW children issues all of their indices at once, then all of their
-    // states (decision, omega-hat, p-hat, phi) at once, then folds them in
-    // descending index as before (every sum in the same order); the parent's
-    // child range is fetched with the vertex's own data.
-    constexpr int DP_FEW = 4;
+    // each step's memory round trips are its latency: the children are folded
+    // in two rounds of loads (dp_fold_children); the parent's child range is
+    // fetched with the vertex's own data.
     int cuts = 0;
     while (true) {
         const int32_t c0 = A.ch_off[v], c1 = A.ch_off[v + 1];
@@ -506,49 +557,7 @@ __device__ __forceinline__ int dp_walk_tree(const DpArgs &A, int32_t v, double N
         double pv = A.p ? A.p[v] : 0.0;
         const double phv = A.phi[v];
         const int32_t uc0 = u >= 0 ? A.ch_off[u] : 0, uc1 = u >= 0 ? A.ch_off[u + 1] : 0;
-        const int32_t nc = c1 - c0;
-        if (nc <= DP_FEW) {
-            int32_t ch[DP_FEW];
-#pragma unroll
-            for (int q = 0; q < DP_FEW; ++q) ch[q] = q < nc ? A.ch_list[c0 + q] : 0;
-            uint8_t dcv[DP_FEW];
-            double cw[DP_FEW], cp[DP_FEW], cf[DP_FEW];
-#pragma unroll
-            for (int q = 0; q < DP_FEW; ++q) {
-                dcv[q] = DEC_DISCARD;
-                cw[q] = cp[q] = cf[q] = 0.0;
-                if (q < nc) {
-                    const size_t cl = (size_t)ch[q] * DP_LANES + lane;
-                    dcv[q] = ld_cg_u8(dec + cl);
-                    cw[q] = ld_cg_f64(wh + cl);
-                    cp[q] = ld_cg_f64(ph + cl);
-                    cf[q] = A.phi[ch[q]];
-                }
-            }
-#pragma unroll
-            for (int q = DP_FEW - 1; q >= 0; --q) {   // siblings in descending index
-                if (q < nc) {
-                    if (dcv[q] == DEC_JOIN) {
-                        w = __dadd_rn(w, cw[q]);
-                        pv = __dadd_rn(pv, cp[q]);
-                    } else {
-                        pv = __dadd_rn(pv, cf[q]);      // cut or discarded child: boundary edge
-                    }
-                }
-            }
-        } else {
-            for (int32_t q = c1 - 1; q >= c0; --q) {   // siblings in descending index
-                const int32_t c = A.ch_list[q];
-                const size_t cl = (size_t)c * DP_LANES + lane;
-                const uint8_t dc = ld_cg_u8(dec + cl);
-                if (dc == DEC_JOIN) {
-                    w = __dadd_rn(w, ld_cg_f64(wh + cl));
-                    pv = __dadd_rn(pv, ld_cg_f64(ph + cl));
-                } else {
-                    pv = __dadd_rn(pv, A.phi[c]);       // cut or discarded child: boundary edge
-                }
-            }
-        }
+        dp_fold_children(A, c0, c1, lane, dec, wh, ph, w, pv);
         const double fe = u >= 0 ? phv : 0.0;
         const double nw = __dmul_rn(N, w);
         const double fp = __dadd_rn(fe, pv);
@@ -607,17 +616,7 @@ __device__ __forceinline__ int dp_walk_sets(const DpArgs &A, int32_t v, double N
             ufe = A.phi[u];
         }
         double w = w0, pv = p0;
-        for (int32_t q = c1 - 1; q >= c0; --q) {   // siblings in descending index
-            const int32_t c = A.ch_list[q];
-            const size_t cl = (size_t)c * DP_LANES + lane;
-            const uint8_t dc = ld_cg_u8(dec + cl);
-            if (dc == DEC_JOIN) {
-                w = __dadd_rn(w, ld_cg_f64(wh + cl));
-                pv = __dadd_rn(pv, ld_cg_f64(ph + cl));
-            } else {
-                pv = __dadd_rn(pv, A.phi[c]);       // cut or discarded child: boundary edge
-            }
-        }
+        dp_fold_children(A, c0, c1, lane, dec, wh, ph, w, pv);
         const double nw = __dmul_rn(N, w);
         const double fp = __dadd_rn(fe, pv);
         uint8_t d;
