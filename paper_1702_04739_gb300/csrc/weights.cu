@@ -808,6 +808,46 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
         float ar[4], ac[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) { ar[q] = rs_h[q] - sref; ac[q] = cs_h[q] - sref; }
+        if (one_exp) {
+            // off the diagonal with one shift: the 16 pairs without branches
+            // (a dropped or padding pair adds an exact zero, which leaves the
+            // double-word sums unchanged), so their dependent double-word
+            // chains can interleave
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int lr = ty * 4 + i;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int lc = tx * 4 + j;
+                    const bool real = rok(lr) && cok(lc);
+                    const float Sh = real ? S[i][j] : 1.0f, El = real ? E[i][j] : 0.0f;
+                    const float r = __fsqrt_rn(Sh);
+                    float dl = 0.0f;
+                    if (r > 0.0f) {
+                        const float res = __fadd_rn(__fmaf_rn(-r, r, Sh), El);
+                        dl = __fmul_rn(res, __frcp_rn(__fadd_rn(r, r)));
+                    }
+                    float yh, yl;
+                    two_prod(r, is_h, yh, yl);
+                    yl = __fmaf_rn(r, is_l, yl);
+                    yl = __fmaf_rn(dl, is_h, yl);
+                    fast_two_sum(yh, yl, yh, yl);
+                    float zh, zl;
+                    two_sum(yh, -sref, zh, zl);
+                    zl = __fadd_rn(zl, yl);
+                    fast_two_sum(zh, zl, zh, zl);
+                    // below e^-zskip of the largest term of both rows (the
+                    // margin covers the FP32 shift differences): dropped
+                    const bool keep = real && !(zh > zskip + fmaxf(ar[i], ac[j]) + 0.01f);
+                    float th, tl2;
+                    dw_exp_neg(keep ? zh : 0.0f, keep ? zl : 0.0f, tab, th, tl2);
+                    th = keep ? th : 0.0f;
+                    tl2 = keep ? tl2 : 0.0f;
+                    dw_add(rh[i], rl[i], th, tl2);
+                    dw_add(ch[j], cl[j], th, tl2);
+                }
+            }
+        } else
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int lr = ty * 4 + i;
