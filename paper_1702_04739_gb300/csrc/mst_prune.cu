@@ -51,56 +51,51 @@ __device__ __forceinline__ uint32_t pr_node(int64_t t, int64_t T, int l, int64_t
     return id;
 }
 
-// warp-wide FP32 d2 (lanes over dimensions; every lane gets the sum)
-__device__ __forceinline__ float pr_d2_warp(const float *__restrict__ x, const float *__restrict__ y, int d, int lane) {
-    float s = 0.0f;
-    for (int t = lane; t < d; t += 32) {
-        const float df = x[t] - y[t];
-        s = fmaf(df, df, s);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    return s;
-}
-
 // PASS 0: farthest point of each node from its first point; PASS 1: from
-// that point.  far[node] = max (d2 bits, index).  A warp takes PR_FAR_ROWS
-// consecutive positions (lanes over dimensions) and keeps the running
-// maximum of its current node, so the top levels' nodes see one atomic per
-// run of positions instead of one per point.
-constexpr int PR_FAR_ROWS = 32;
+// that point.  far[node] = max (d2 bits, index).  A thread per position (its
+// row's loads in flight together); the lanes of a warp that share a node
+// fold their keys first, so a node sees one atomic per warp.
 template <int PASS>
 __global__ void k_pr_far(const float *__restrict__ X, int64_t n, int32_t d, const int32_t *__restrict__ perm,
                          int64_t T, int l, const unsigned long long *__restrict__ far0,
                          unsigned long long *__restrict__ far) {
-    const int64_t p0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * PR_FAR_ROWS;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    uint32_t cur = 0xffffffffu;
-    unsigned long long best = 0;
-    for (int64_t p = p0; p < p0 + PR_FAR_ROWS && p < n; ++p) {
+    uint32_t id = 0xffffffffu;
+    unsigned long long key = 0;
+    if (p < n) {
         int64_t a, b;
-        const uint32_t id = pr_node(p / PR_BM, T, l, a, b);
-        if (b - a <= 1) continue;                            // a single tile: not split further
-        if (id != cur) {
-            if (cur != 0xffffffffu && lane == 0) atomicMax(far + cur, best);
-            cur = id;
-            best = 0;
+        id = pr_node(p / PR_BM, T, l, a, b);
+        if (b - a > 1) {
+            const int32_t i = perm[p];
+            const int64_t ref = PASS == 0 ? (int64_t)perm[a * PR_BM] : (int64_t)(uint32_t)(far0[id] & 0xffffffffull);
+            const float *x = X + (int64_t)i * d, *y = X + ref * d;
+            float s2 = 0.0f;
+            for (int t = 0; t < d; ++t) {
+                const float df = x[t] - y[t];
+                s2 = fmaf(df, df, s2);
+            }
+            key = ((unsigned long long)__float_as_uint(s2) << 32) | (unsigned long long)(uint32_t)i;
+        } else {
+            id = 0xffffffffu;                                // a single tile: not split further
         }
-        const int32_t i = perm[p];
-        const int64_t ref = PASS == 0 ? (int64_t)perm[a * PR_BM] : (int64_t)(uint32_t)(far0[id] & 0xffffffffull);
-        const float v = pr_d2_warp(X + (int64_t)i * d, X + ref * d, d, lane);
-        const unsigned long long key = ((unsigned long long)__float_as_uint(v) << 32) | (unsigned long long)(uint32_t)i;
-        best = key > best ? key : best;
     }
-    if (cur != 0xffffffffu && lane == 0) atomicMax(far + cur, best);
+    // lanes of the same node: the largest key goes to the lowest such lane
+    const unsigned same = __match_any_sync(0xffffffffu, id);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long k2 = __shfl_down_sync(0xffffffffu, key, o);
+        const int src = lane + o;
+        if (src < 32 && ((same >> src) & 1u) && k2 > key) key = k2;
+    }
+    if (id != 0xffffffffu && lane == __ffs(same) - 1) atomicMax(far + id, key);
 }
 
 // sort key of position p: (node, projection on the node's far pair's line)
 __global__ void k_pr_keys(const float *__restrict__ X, int64_t n, int32_t d, const int32_t *__restrict__ perm,
                           int64_t T, int l, const unsigned long long *__restrict__ far0,
                           const unsigned long long *__restrict__ far1, uint64_t *__restrict__ keys) {
-    const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     int64_t a, b;
     const uint32_t id = pr_node(p / PR_BM, T, l, a, b);
@@ -110,15 +105,11 @@ __global__ void k_pr_keys(const float *__restrict__ X, int64_t n, int32_t d, con
         const int64_t pb = (int64_t)(uint32_t)(far0[id] & 0xffffffffull);
         const int64_t pc = (int64_t)(uint32_t)(far1[id] & 0xffffffffull);
         const float *xi = X + (int64_t)i * d, *xb = X + pb * d, *xc = X + pc * d;
-        for (int t = lane; t < d; t += 32) proj = fmaf(xi[t] - xb[t], xc[t] - xb[t], proj);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) proj += __shfl_xor_sync(0xffffffffu, proj, o);
+        for (int t = 0; t < d; ++t) proj = fmaf(xi[t] - xb[t], xc[t] - xb[t], proj);
     }
-    if (lane == 0) {
-        uint32_t u = __float_as_uint(proj);
-        u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);         // order-preserving bits
-        keys[p] = ((uint64_t)id << 32) | (uint64_t)u;
-    }
+    uint32_t u = __float_as_uint(proj);
+    u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);             // order-preserving bits
+    keys[p] = ((uint64_t)id << 32) | (uint64_t)u;
 }
 
 __global__ void k_pr_nn_keys(const double *__restrict__ rowd2, int64_t n, uint64_t *__restrict__ keys,
@@ -408,17 +399,16 @@ static cudaError_t prune_geometry(TcScratch &T, const float *X, int64_t n, int32
 // recursive bisection of positions [0, m) of T.perm (whole tiles from 0)
 static cudaError_t prune_bisect(TcScratch &T, const float *X, int64_t m, int32_t d, cudaStream_t s) {
     const int64_t nt = ceil_div(m, PR_BM);
-    const unsigned gw = (unsigned)ceil_div(m * 32, 256);          // a warp per position
-    const unsigned gf = (unsigned)ceil_div(ceil_div(m, PR_FAR_ROWS) * 32, 256);   // a warp per PR_FAR_ROWS positions
+    const unsigned g = (unsigned)ceil_div(m, 256);                 // a thread per position
     int levels = 0;
     while (((int64_t)1 << levels) < nt) ++levels;
     cudaError_t e;
     unsigned long long *far0 = T.far, *far1 = T.far + 2 * nt;
     for (int l = 0; l < levels; ++l) {
         if ((e = cudaMemsetAsync(T.far, 0, sizeof(unsigned long long) * 4 * nt, s))) return e;
-        k_pr_far<0><<<gf, 256, 0, ISO_S(s)>>>(X, m, d, T.perm, nt, l, nullptr, far0);
-        k_pr_far<1><<<gf, 256, 0, ISO_S(s)>>>(X, m, d, T.perm, nt, l, far0, far1);
-        k_pr_keys<<<gw, 256, 0, ISO_S(s)>>>(X, m, d, T.perm, nt, l, far0, far1, T.keys);
+        k_pr_far<0><<<g, 256, 0, ISO_S(s)>>>(X, m, d, T.perm, nt, l, nullptr, far0);
+        k_pr_far<1><<<g, 256, 0, ISO_S(s)>>>(X, m, d, T.perm, nt, l, far0, far1);
+        k_pr_keys<<<g, 256, 0, ISO_S(s)>>>(X, m, d, T.perm, nt, l, far0, far1, T.keys);
         // stable: ties keep the previous level's order
         if ((e = sort_pairs_u64(T.keys, T.perm, T.kbuf, T.vbuf, m, s))) return e;
     }
