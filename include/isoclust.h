@@ -483,7 +483,8 @@ isoclust_status isoclust_set_omega_gram(int32_t mode);
  * both radii) is within the bound of some component of the row tile, and
  * never two tiles wholly inside one component.  The tree is the same edge
  * for edge.  mode -1 (the default): pruned for n >= 65,536 and d <= 256;
- * 1: whenever the tensor-core sweep runs a one-set call; 0: never.
+ * 1: whenever the tensor-core sweep runs a one-set call of 64 points or
+ * more and at most 256 dimensions, a multiple of 4; 0: never.
  * Process-wide; other values -> INVALID_ARG. */
 isoclust_status isoclust_set_mst_prune(int32_t mode);
 

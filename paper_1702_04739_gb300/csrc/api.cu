@@ -636,8 +636,7 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
         const int64_t nt = TC.n_pad / 128;
         g_prof_mst_tiles[1] = (int64_t)cnt[MC_ROUNDS] * nt * nt;
         g_prof_mst_tiles[0] = g_prof_mst_tiles[1];
-        // the first round swept every tile pair, the pruned ones counted theirs
-        if (mst_pruned) g_prof_mst_tiles[0] = nt * nt + (int64_t)mst_swept;
+        if (mst_pruned) g_prof_mst_tiles[0] = (int64_t)mst_swept;     // every round pruned
     }
     g_prof_tiles[0] = g_prof_tiles[1] = g_prof_tiles[2] = 0;
     if (permuted) ISO_CUDA(cudaMemcpy(g_prof_tiles, P.tiles, sizeof(g_prof_tiles), cudaMemcpyDeviceToHost));

@@ -523,13 +523,16 @@ cudaError_t mst_build(MstScratch &S, const void *X, int64_t n, int32_t d, int dt
     if ((e = cudaStreamIsCapturing(s, &cs))) return e;
     const bool capturing = cs != cudaStreamCaptureStatusNone;
     if (tc && (e = tc_prepare(*tc, (const float *)X, n, d, s))) return e;
+    if (tc && tc->prune) {
+        // pruned rounds (one set): the rows take the pruning's order; no row
+        // has a previous round's pair yet
+        if ((e = prune_reorder(*tc, S.rowd2, (const float *)X, n, d, s))) return e;
+        if ((e = cudaMemsetAsync(S.rowj, 0xff, sizeof(int32_t) * n, s))) return e;
+    }
     if (tc && (e = tc_count_sets(*tc, S.comp, n, S.counters, s))) return e;
     if (tc && (e = tc_autotune(*tc, S, (const float *)X, n, d, status, s))) return e;
     if (!tc) tc_clear_last_variant();
     for (int r = 0; r < R; ++r) {
-        // pruned rounds (one set): after the first round, whose keys are the
-        // exact nearest neighbours, the rows take the pruning's order
-        if (tc && tc->prune && r == 1 && (e = prune_reorder(*tc, S.rowd2, (const float *)X, n, d, s))) return e;
         k_round_begin<<<rg, TPB, 0, ISO_S(s)>>>(S.counters, S.cd2, S.cpair, n);
         if (tc) {
             if ((e = tc_sweep_round(*tc, S, (const float *)X, n, d, status, s))) return e;

@@ -105,11 +105,11 @@ constexpr int PRUNE_NEAR = 2;
 bool prune_wanted(int64_t n, int32_t d);
 void prune_set_mode(int mode);
 int prune_mode();
-// After the first (full) round, whose keys are every point's exact nearest
-// neighbour: rows re-ordered for the pruned rounds (points whose nearest
-// neighbour is more than 4x the median distance away at the end, the others
-// in bisection order), the sweep's row data re-placed, the tile geometry.
-cudaError_t prune_reorder(TcScratch &T, const double *rowd2, const float *X, int64_t n, int32_t d, cudaStream_t s);
+// Before the first round: rows re-ordered for the pruned rounds (points whose
+// distance to the nearest of 256 sample points is more than 4x the median
+// of that distance at the end, the others in bisection order), the sweep's
+// row data re-placed, the tile geometry.  rowd2 (n doubles) is scratch here.
+cudaError_t prune_reorder(TcScratch &T, double *rowd2, const float *X, int64_t n, int32_t d, cudaStream_t s);
 // Re-place the sweep's rows (hi/lo split, norms, tile maxima) in T.perm's order.
 cudaError_t tc_place_rows(TcScratch &T, const float *X, int64_t n, int32_t d, cudaStream_t s);
 // Per round, after the near sweep: component bounds and the far items.

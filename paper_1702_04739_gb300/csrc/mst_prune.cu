@@ -17,11 +17,10 @@
 // lightest edge is among them: the round joins the same components by the
 // same edges as the full sweep.
 //
-// The order, set up after the first round (a full sweep, which gives every
-// point's exact nearest neighbour): points whose nearest neighbour is more
-// than 4x the median nearest-neighbour distance away (isolated points: a
-// tile holding some would span the space) go last; the others in recursive
-// bisection of their tile range.  A node (a range of whole tiles) is split
+// The order, set up before the first round: points whose distance to the
+// nearest of 256 evenly spaced sample points is more than 4x the median of
+// that distance (isolated points: a tile holding some would span the space)
+// go last; the others in recursive bisection of their tile range.  A node (a range of whole tiles) is split
 // at its middle tile after sorting its points by their projection on the
 // line through two far-apart points of the node (the farthest point from the
 // node's first point, then the farthest from that one), so the two halves
@@ -110,6 +109,62 @@ __global__ void k_pr_keys(const float *__restrict__ X, int64_t n, int32_t d, con
     uint32_t u = __float_as_uint(proj);
     u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);             // order-preserving bits
     keys[p] = ((uint64_t)id << 32) | (uint64_t)u;
+}
+
+// Isolation proxy before any round: each point's FP32 d2 to the nearest of
+// PR_SAMPLES evenly spaced sample points (itself excluded).  Points of a
+// cluster find a sample nearby; isolated points do not.  A thread per point
+// keeps 32 dimensions of its row in registers against 32 samples staged in
+// shared memory (broadcast reads).
+constexpr int PR_SAMPLES = 256;
+__global__ void __launch_bounds__(256) k_pr_sample_nn(const float *__restrict__ X, int64_t n, int32_t d,
+                                                      int64_t stride, int nsamp, double *__restrict__ out) {
+    extern __shared__ float ss[];                             // [32][d]
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float best = INFINITY;
+    for (int s0 = 0; s0 < nsamp; s0 += 32) {                  // nsamp: a multiple of 32
+        __syncthreads();
+        for (int e = threadIdx.x; e < 32 * d; e += blockDim.x) {
+            const int q = e / d, t = e - q * d;
+            ss[q * d + t] = X[(int64_t)(s0 + q) * stride * d + t];
+        }
+        __syncthreads();
+        if (i < n) {
+            float acc[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) acc[q] = 0.0f;
+            int t0 = 0;
+            for (; t0 + 32 <= d; t0 += 32) {                  // whole chunks of 32 dimensions
+                float xv[32];
+#pragma unroll
+                for (int t = 0; t < 32; t += 4) {
+                    const float4 v = *reinterpret_cast<const float4 *>(X + i * d + t0 + t);
+                    xv[t] = v.x; xv[t + 1] = v.y; xv[t + 2] = v.z; xv[t + 3] = v.w;
+                }
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const float *sq = ss + q * d + t0;
+#pragma unroll
+                    for (int t = 0; t < 32; ++t) {
+                        const float df = xv[t] - sq[t];
+                        acc[q] = fmaf(df, df, acc[q]);
+                    }
+                }
+            }
+            for (int t = t0; t < d; ++t) {                    // the tail
+                const float xt = X[i * d + t];
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const float df = xt - ss[q * d + t];
+                    acc[q] = fmaf(df, df, acc[q]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+                if ((int64_t)(s0 + q) * stride != i) best = fminf(best, acc[q]);
+        }
+    }
+    if (i < n) out[i] = (double)best;
 }
 
 __global__ void k_pr_nn_keys(const double *__restrict__ rowd2, int64_t n, uint64_t *__restrict__ keys,
@@ -387,7 +442,10 @@ int prune_mode() { return g_prune_mode.load(); }
 bool prune_wanted(int64_t n, int32_t d) {
     const int mode = g_prune_mode.load();
     const int64_t nt = ceil_div(n, PR_BM);
-    if (mode == 0 || nt > 16384 || n < 2) return false;
+    // supported: rows of at most 256 dimensions, a multiple of 4 (the
+    // order's sample search stages 32 rows in shared memory and reads rows by
+    // 16 bytes), at least 64 points
+    if (mode == 0 || nt > 16384 || n < 64 || d > 256 || d % 4) return false;
     if (mode == 1) return true;
     // tile bounds separate little in many dimensions; below ~64k points the
     // order and bounds cost more than the pruned tile pairs save
@@ -415,9 +473,14 @@ static cudaError_t prune_bisect(TcScratch &T, const float *X, int64_t m, int32_t
     return cudaGetLastError();
 }
 
-cudaError_t prune_reorder(TcScratch &T, const double *rowd2, const float *X, int64_t n, int32_t d, cudaStream_t s) {
+cudaError_t prune_reorder(TcScratch &T, double *rowd2, const float *X, int64_t n, int32_t d, cudaStream_t s) {
     cudaError_t e;
     const unsigned g = (unsigned)ceil_div(n, 256);
+    // the isolation proxy (into rowd2, free before the first round)
+    const int nsamp = (int)((n < PR_SAMPLES ? n : PR_SAMPLES) & ~(int64_t)31);
+    if (nsamp < 32) return cudaErrorInvalidValue;           // (prune_wanted: n >= 64)
+    if (d % 4) return cudaErrorInvalidValue;                  // (prune_wanted: rows of 4k floats)
+    k_pr_sample_nn<<<g, 256, sizeof(float) * 32 * d, ISO_S(s)>>>(X, n, d, n / nsamp, nsamp, rowd2);
     // the median nearest-neighbour d2, then isolated points last
     k_pr_nn_keys<<<g, 256, 0, ISO_S(s)>>>(rowd2, n, T.keys, T.perm);
     if ((e = sort_pairs_u64(T.keys, T.perm, T.kbuf, T.vbuf, n, s))) return e;
