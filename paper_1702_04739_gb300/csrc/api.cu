@@ -819,6 +819,7 @@ static isoclust_status cluster_sets_impl(const void *X, const int64_t *offsets, 
         int2 *witems;
         double *ed2, *phi, *om, *omp;
         SearchState *SS;
+        uint32_t *set_hist;
         int64_t *pos;
         float *Xp;
         unsigned long long *nnp, *tiles;
@@ -842,6 +843,7 @@ static isoclust_status cluster_sets_impl(const void *X, const int64_t *offsets, 
         B.phi = A.take<double>(N + 1);
         B.om = A.take<double>(N + 1);
         B.SS = A.take<SearchState>(P);
+        B.set_hist = A.take<uint32_t>((size_t)P * CAND_SET_BUCKETS + 1);
         B.pos = A.take<int64_t>(N);
         B.Xp = A.take<float>((size_t)n_pad64 * d);
         B.nnp = A.take<unsigned long long>(n_pad64);
@@ -933,7 +935,7 @@ static isoclust_status cluster_sets_impl(const void *X, const int64_t *offsets, 
         E.rec(4, q);
         if ((e = phi_from_edges(TS, B.ed2, sigma, B.phi, q))) return e;
         // Algorithm 2 + Algorithm 1 per set, then Algorithm 4's labels
-        if ((e = tree_search_and_label_sets(TS, nsets, d_offs, B.set_of, B.ks, B.SS, B.phi, B.om, nullptr, labels,
+        if ((e = tree_search_and_label_sets(TS, nsets, d_offs, B.set_of, B.ks, B.SS, B.set_hist, B.phi, B.om, nullptr, labels,
                                             residual, i_k, beta, q)))
             return e;
         E.rec(5, q);
@@ -1026,7 +1028,7 @@ static isoclust_status cluster_sets_impl(const void *X, const int64_t *offsets, 
     g_prof_ms[5] = E.ms(5, 6);
     g_prof_cnt[0] = cnt[MC_ROUNDS];
     g_prof_cnt[1] = cnt[MC_OVF_TOTAL] + cnt[MC_OVERFLOW];
-    g_prof_cnt[2] = DP_SEARCH_PASSES + 1;
+    g_prof_cnt[2] = DP_TREE_PASSES + 1;
     g_prof_cnt[3] = 0;
     ISO_CUDA(cudaMemcpy(g_prof_tiles, B.tiles, sizeof(g_prof_tiles), cudaMemcpyDeviceToHost));
     g_prof_sym = 1;

@@ -678,7 +678,8 @@ __global__ void __launch_bounds__(256) k_dp_pass_sets(DpArgs A, const SearchStat
                                                       const int32_t *__restrict__ vset, uint8_t *__restrict__ dec,
                                                       double *__restrict__ wh, double *__restrict__ ph,
                                                       int32_t *__restrict__ done, double *__restrict__ rat,
-                                                      int final_pass) {
+                                                      int final_pass, const uint32_t *__restrict__ left) {
+    if (!final_pass && *(const volatile uint32_t *)left == 0u) return;     // every set's search is done
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -887,12 +888,125 @@ __global__ void __launch_bounds__(1024) k_cand_select(SearchState *S, uint32_t *
     S->cand_passes += 1;
 }
 
-// independent sets: one thread per set
-__global__ void k_search_update_sets(SearchState *SS, const int32_t *__restrict__ ks, int32_t nsets, int last,
-                                     uint32_t *st) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < nsets) search_update(SS + b, ks[b], last, st);
+// ---- the same for independent sets: each set in candidate mode counts its
+// vertices' critical ratios in CAND_SET_BUCKETS buckets of its own bracket
+// (hist [nsets][CAND_SET_BUCKETS]); one warp per set then picks its next
+// thresholds exactly as k_cand_select does for one tree.
+__global__ void __launch_bounds__(256) k_cand_hist_sets(DpArgs A, SearchState *SS, const int32_t *__restrict__ vset,
+                                                        int64_t nv, const double *__restrict__ wh,
+                                                        const double *__restrict__ ph, uint32_t *__restrict__ hist,
+                                                        const uint32_t *__restrict__ left) {
+    if (*(const volatile uint32_t *)left == 0u) return;
+    const int64_t gs = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gs) {
+        const int32_t b = vset[v];
+        SearchState *S = SS + b;
+        if (!cand_active(S)) continue;
+        const unsigned long long lo = S->lo_bits, hi = S->hi_bits;
+        const int L = S->lane_lo;
+        const double inv_w = (double)CAND_SET_BUCKETS / (double)(hi - lo);
+        uint32_t *hb = hist + (size_t)b * CAND_SET_BUCKETS;
+        auto add = [&](double c) {
+            const unsigned long long bits = dbits(c);
+            if (!(c > 0.0) || bits <= lo || bits >= hi) return;
+            int j = (int)((double)(bits - lo) * inv_w);
+            j = j < 0 ? 0 : (j >= CAND_SET_BUCKETS ? CAND_SET_BUCKETS - 1 : j);
+            atomicAdd(hb + j, 1u);
+            const unsigned q = atomicAdd(&S->ncand, 1u);
+            if (q < (unsigned)CAND_EXACT) S->cand[q] = bits;
+        };
+        const size_t vl = (size_t)v * DP_LANES + L;
+        const double w = wh[vl], pv = ph[vl];
+        const int32_t u = A.parent[v];
+        const double fe = u >= 0 ? A.phi[v] : 0.0;
+        add(__ddiv_rn(__dadd_rn(fe, pv), w));
+        if (u >= 0) add(__ddiv_rn(__dsub_rn(pv, fe), w));
+    }
 }
+
+__global__ void __launch_bounds__(256) k_cand_select_sets(SearchState *SS, int32_t nsets, uint32_t *__restrict__ hist,
+                                                          const uint32_t *__restrict__ left) {
+    if (*(const volatile uint32_t *)left == 0u) return;
+    __shared__ unsigned int pre_s[8][CAND_SET_BUCKETS];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (b >= nsets) return;
+    SearchState *S = SS + b;
+    uint32_t *hb = hist + (size_t)b * CAND_SET_BUCKETS;
+    unsigned int *pre = pre_s[wib];
+    const bool active = cand_active(S);
+    // inclusive prefix sums of the set's buckets: CAND_SET_BUCKETS / 32 per lane
+    constexpr int PER = CAND_SET_BUCKETS / 32;
+    unsigned int loc[PER], run = 0;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) { run += hb[lane * PER + q]; loc[q] = run; }
+    unsigned int x = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        pre[lane * PER + q] = (x - run) + loc[q];
+        hb[lane * PER + q] = 0u;                      // ready for the next pass
+    }
+    __syncwarp();
+    if (lane != 0) return;
+    if (!active) {
+        if (!S->done) S->mode = 1;                    // k_search_update_sets's bit-search thresholds stand
+        return;
+    }
+    const unsigned long long lo = S->lo_bits, hi = S->hi_bits;
+    const unsigned int m = pre[CAND_SET_BUCKETS - 1];
+    const unsigned int nc = S->ncand;
+    S->ncand = 0u;
+    double t[DP_LANES];
+    t[0] = bitsd(lo);
+    int used = 1;
+    if (hi - lo <= (unsigned long long)DP_LANES) {
+        for (int q = 1; q < DP_LANES; ++q) t[q] = bitsd(lo + (unsigned long long)q < hi ? lo + q : hi);
+        used = DP_LANES;
+    } else if (m == 0u) {
+        S->mode = 1;
+        return;
+    } else if (nc <= (unsigned)CAND_EXACT) {
+        for (unsigned q = 0; q < nc && used + 3 <= DP_LANES; ++q) {
+            const unsigned long long c0 = S->cand[q];
+            const unsigned long long c[3] = {c0 - 1ull, c0, c0 + 1ull};
+            for (int r = 0; r < 3; ++r)
+                if (c[r] > lo && c[r] < hi) t[used++] = bitsd(c[r]);
+        }
+    } else {
+        const double wdt = (double)(hi - lo) / (double)CAND_SET_BUCKETS;
+        int j = 0;
+        for (int q = 1; q < DP_LANES; ++q) {
+            const unsigned long long r = ((unsigned long long)m * (unsigned long long)q) / DP_LANES;
+            while (j < CAND_SET_BUCKETS - 1 && pre[j] < r) ++j;
+            unsigned long long c = lo + (unsigned long long)((double)(j + 1) * wdt);
+            if (c <= lo) c = lo + 1ull;
+            if (c >= hi) c = hi - 1ull;
+            t[used++] = bitsd(c);
+        }
+    }
+    for (int q = used; q < DP_LANES; ++q) t[q] = t[used - 1];
+    for (int q = 0; q < DP_LANES; ++q) S->thr[q] = t[q];
+    S->cand_passes += 1;
+}
+
+// independent sets: one thread per set
+// (left: the sets whose search is not done; the passes after the last one
+// finishes return at once)
+__global__ void k_search_update_sets(SearchState *SS, const int32_t *__restrict__ ks, int32_t nsets, int last,
+                                     uint32_t *st, uint32_t *left) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nsets) return;
+    const int was = SS[b].done;
+    search_update(SS + b, ks[b], last, st);
+    if (!was && SS[b].done) atomicSub(left, 1u);
+}
+
+__global__ void k_sets_left_init(uint32_t *left, int32_t nsets) { *left = (uint32_t)nsets; }
 
 // ------------------------------------------------------------ labels
 __global__ void k_head_init(const uint8_t *__restrict__ dec, const int32_t *__restrict__ parent, int64_t n,
@@ -1147,9 +1261,9 @@ cudaError_t tree_search_and_label(TreeScratch &S, const double *phi_par, const d
 }
 
 cudaError_t tree_search_and_label_sets(TreeScratch &S, int32_t nsets, const int64_t *offs, const int32_t *vset,
-                                       const int32_t *ks, SearchState *SS, const double *phi_par, const double *omega,
-                                       const double *p, int32_t *labels, uint8_t *residual, double *i_k, double *beta,
-                                       cudaStream_t s) {
+                                       const int32_t *ks, SearchState *SS, uint32_t *set_hist, const double *phi_par,
+                                       const double *omega, const double *p, int32_t *labels, uint8_t *residual,
+                                       double *i_k, double *beta, cudaStream_t s) {
     const TreeDev &T = S.T;
     const int64_t n = T.n, nv = n - 1;      // vertex nv is the virtual root
     cudaError_t e;
@@ -1165,13 +1279,23 @@ cudaError_t tree_search_and_label_sets(TreeScratch &S, int32_t nsets, const int6
         dp_occ = 4;
     const unsigned grid = (unsigned)(num_sms() * dp_occ);
     const unsigned gs = (unsigned)ceil_div(nsets, 128);
-    for (int pass = 0; pass < DP_SEARCH_PASSES; ++pass) {
+    // each set: thresholds from its vertices' critical ratios while that
+    // narrows its bracket, else the 33-ary bit search (as for one tree)
+    if ((e = cudaMemsetAsync(set_hist, 0, sizeof(uint32_t) * (size_t)nsets * CAND_SET_BUCKETS, s))) return e;
+    uint32_t *left = set_hist + (size_t)nsets * CAND_SET_BUCKETS;
+    k_sets_left_init<<<1, 1, 0, ISO_S(s)>>>(left, nsets);
+    const unsigned gw = (unsigned)ceil_div((int64_t)nsets * 32, 256);
+    for (int pass = 0; pass < DP_TREE_PASSES; ++pass) {
         if ((e = cudaMemsetAsync(S.done, 0, sizeof(int32_t) * n, s))) return e;
-        k_dp_pass_sets<<<grid, 256, 0, ISO_S(s)>>>(A, S.search, SS, vset, S.dec, S.wh, S.ph, S.done, S.rat, 0);
-        k_search_update_sets<<<gs, 128, 0, ISO_S(s)>>>(SS, ks, nsets, pass == DP_SEARCH_PASSES - 1, S.status);
+        k_dp_pass_sets<<<grid, 256, 0, ISO_S(s)>>>(A, S.search, SS, vset, S.dec, S.wh, S.ph, S.done, S.rat, 0, left);
+        k_search_update_sets<<<gs, 128, 0, ISO_S(s)>>>(SS, ks, nsets, pass == DP_TREE_PASSES - 1, S.status, left);
+        if (pass + 1 < DP_TREE_PASSES) {
+            k_cand_hist_sets<<<grid, 256, 0, ISO_S(s)>>>(A, SS, vset, nv, S.wh, S.ph, set_hist, left);
+            k_cand_select_sets<<<gw, 256, 0, ISO_S(s)>>>(SS, nsets, set_hist, left);
+        }
     }
     if ((e = cudaMemsetAsync(S.done, 0, sizeof(int32_t) * n, s))) return e;
-    k_dp_pass_sets<<<grid, 256, 0, ISO_S(s)>>>(A, S.search, SS, vset, S.dec, S.wh, S.ph, S.done, S.rat, 1);
+    k_dp_pass_sets<<<grid, 256, 0, ISO_S(s)>>>(A, S.search, SS, vset, S.dec, S.wh, S.ph, S.done, S.rat, 1, left);
     k_head_init<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.dec, T.parent, n, S.head);
     int32_t *ha = S.head, *hb = S.head2;
     const int Ln = log2_ceil(n) + 1;

@@ -14,6 +14,7 @@ constexpr int DP_CAND_PASSES = 8;
 constexpr int DP_TREE_PASSES = 1 + DP_CAND_PASSES + 13;
 constexpr int CAND_BUCKETS = 4096;    // histogram of critical ratios over the bracket's bit patterns
 constexpr int CAND_EXACT = 10;        // at most this many left: they are tried exactly (+-1 ulp)
+constexpr int CAND_SET_BUCKETS = 64;  // independent sets: buckets per set (a multiple of 32)
 enum : uint8_t { DEC_DISCARD = 0, DEC_CUT = 1, DEC_JOIN = 2 };
 
 // Device-resident search state of reading S (bisection to the last bit).
@@ -109,11 +110,11 @@ cudaError_t fix_set_roots(TreeScratch &S, int32_t nsets, const int64_t *offs, cu
 // Independent sets on a tree oriented with vset (see orient_tree): each
 // set's own roots, statistics, search (state SS[b], k = ks[b]) and labels.
 // labels / residual cover the real vertices; i_k and beta (nullable) one
-// entry per set.
+// entry per set.  set_hist: nsets x CAND_SET_BUCKETS + 1 counters (scratch).
 cudaError_t tree_search_and_label_sets(TreeScratch &S, int32_t nsets, const int64_t *offs, const int32_t *vset,
-                                       const int32_t *ks, SearchState *SS, const double *phi_par, const double *omega,
-                                       const double *p, int32_t *labels, uint8_t *residual, double *i_k, double *beta,
-                                       cudaStream_t s);
+                                       const int32_t *ks, SearchState *SS, uint32_t *set_hist, const double *phi_par,
+                                       const double *omega, const double *p, int32_t *labels, uint8_t *residual,
+                                       double *i_k, double *beta, cudaStream_t s);
 
 // phi of each oriented parent edge from the MST edge d2 (eq. phi).
 cudaError_t phi_from_edges(const TreeScratch &S, const double *edge_d2, double sigma, double *phi_par,
