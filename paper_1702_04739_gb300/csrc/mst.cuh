@@ -91,6 +91,7 @@ struct TcScratch {
     int4 *items_a = nullptr, *items_b = nullptr;   // [ntiles] near items, [ntiles][PRUNE_SLOTS - 1] far items
     unsigned long long *far = nullptr;             // [2][ntiles] order construction: farthest points per node
     unsigned long long *swept = nullptr;           // [1] tile pairs swept by the pruned rounds so far
+    int32_t *nlists = nullptr;                     // [ntiles] candidate lists the row tile's items write this round
     CUtensorMap map_h, map_l;
     // n_pad_rows / nmeans / lists: 0 = one set
     void carve(Arena &A, int64_t n, int32_t d, int splits, int64_t n_pad_rows = 0, int nmeans = 1, int lists = 0);

@@ -345,7 +345,7 @@ constexpr int PR_RUNCAP = 256;             // runs kept per row tile (more: join
 __global__ void __launch_bounds__(256) k_pr_far_items(const float *__restrict__ tlb2, const float *__restrict__ tmu,
                                                       const int32_t *__restrict__ tcomp, int64_t T,
                                                       int4 *__restrict__ items_b, unsigned long long *swept,
-                                                      const int32_t *counters) {
+                                                      int32_t *__restrict__ nlists, const int32_t *counters) {
     if (!pr_active(counters)) return;
     extern __shared__ uint32_t keep[];                       // ceil(T / 32) words
     __shared__ int32_t rs[PR_RUNCAP], re[PR_RUNCAP];
@@ -431,8 +431,10 @@ __global__ void __launch_bounds__(256) k_pr_far_items(const float *__restrict__ 
             out[q] = make_int4((int)R, 0, 0, q + 1);
         }
     }
-    // tile pairs this row tile sweeps this round, near window included
+    // tile pairs this row tile sweeps this round, near window included;
+    // its rows' candidates are in the lists of slot 0 and of the nr items
     atomicAdd(swept, (unsigned long long)cnt);
+    nlists[R] = 2 * (1 + nr);
 }
 }  // namespace
 
@@ -521,7 +523,8 @@ cudaError_t prune_far_items(TcScratch &T, const int32_t *comp, const double *row
                                                                         (float)(eps_rep * 1.0001), T.cub, counters);
     k_pr_tile_mu<<<(unsigned)nt, 128, 0, ISO_S(s)>>>(T.permp, comp, T.cub, T.tmu, T.tcomp, counters);
     k_pr_far_items<<<(unsigned)nt, 256, sizeof(uint32_t) * ceil_div(nt, 32), ISO_S(s)>>>(T.tlb2, T.tmu, T.tcomp, nt,
-                                                                                       T.items_b, T.swept, counters);
+                                                                                       T.items_b, T.swept, T.nlists,
+                                                                                       counters);
     return cudaGetLastError();
 }
 

@@ -681,7 +681,8 @@ __device__ __forceinline__ void recheck_row(int64_t r, int lane, const float *__
                                             int32_t *__restrict__ rowj, int32_t *__restrict__ ovf,
                                             const int32_t *__restrict__ set_of, const int32_t *__restrict__ setcnt,
                                             int32_t *counters, float *__restrict__ wv_s, float *__restrict__ bv_s,
-                                            int32_t *__restrict__ bj_s, int shard_rank, int shard_world) {
+                                            int32_t *__restrict__ bj_s, int shard_rank, int shard_world,
+                                            const int32_t *__restrict__ row_lists) {
     if (lane == 0) nsurv[r] = 0;           // every row, padding included: k_exact_tc reads them all
     const int64_t i = perm[r];
     if (i < 0) return;                     // padding row
@@ -695,6 +696,9 @@ __device__ __forceinline__ void recheck_row(int64_t r, int lane, const float *__
     }
     // ---- merge: each lane holds EPL of the lists x 8 entries (lists x 8 <=
     //      32 EPL); the best 8 are selected by 8 rounds of a warp arg-min
+    // pruned rounds: only the lists its row tile's items wrote (the others
+    // hold no candidate)
+    if (row_lists) lists = row_lists[r / TC_BM];
     const int ne = lists * TC_TOPK;
     float ev[EPL];
     int32_t ej[EPL];
@@ -952,7 +956,8 @@ __global__ void __launch_bounds__(256, 4) k_recheck_tc(const float *__restrict__
                                                        int32_t *__restrict__ surv, int32_t *__restrict__ rowj,
                                                        int32_t *__restrict__ ovf, const int32_t *__restrict__ set_of,
                                                        const int32_t *__restrict__ setcnt, int32_t *counters,
-                                                       int shard_rank, int shard_world) {
+                                                       int shard_rank, int shard_world,
+                                                       const int32_t *__restrict__ row_lists) {
     if (!mst_active(counters)) return;
     __shared__ float wv_s[8][32], bv_s[8][TC_TOPK];
     __shared__ int32_t bj_s[8][TC_TOPK];
@@ -962,7 +967,7 @@ __global__ void __launch_bounds__(256, 4) k_recheck_tc(const float *__restrict__
     for (int64_t r = w0; r < n; r += nw)
         recheck_row<EPL, CW>(r, lane, xs, n, d, lists, tv, tj, tu, rsq, perm, compp, nmax_bits, eps_rep, mul32, add32, nsurv,
                              surv, rowj, ovf, set_of, setcnt, counters, wv_s[wib], bv_s[wib], bj_s[wib], shard_rank,
-                             shard_world);
+                             shard_world, row_lists);
 }
 
 // Self-contained rescan of a queued row: FP32 direct differences give the
@@ -1126,6 +1131,7 @@ void TcScratch::carve(Arena &A, int64_t n, int32_t d, int splits_, int64_t n_pad
         items_b = A.take<int4>((size_t)nt * (PRUNE_SLOTS - 1));
         far = A.take<unsigned long long>((size_t)4 * nt);
         swept = A.take<unsigned long long>(1);
+        nlists = A.take<int32_t>(nt);
     }
 }
 
@@ -1453,7 +1459,7 @@ cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t 
     k_recheck_tc<EPLV, CWV><<<(unsigned)(rblocks < rcap ? rblocks : rcap), 256, 0, ISO_S(s)>>>(                        \
         T.xs, T.n_pad, d, T.lists, T.tv, T.tj, T.tu, T.rsq, T.permp, T.compp, T.nmax_bits, (float)(eps_rep * 1.0001),  \
         mul32, add32, T.nsurv, T.surv, S.rowj, S.ovf_rows, T.set_of, T.setcnt, S.counters, T.shard_rank,           \
-        T.shard_world)
+        T.shard_world, pruned ? T.nlists : nullptr)
     if (T.lists <= 4)
         {
         if (T.cw == 32) ISO_RECHECK_LAUNCH(1, 32);
