@@ -660,6 +660,7 @@ __global__ void __launch_bounds__(256) k_dp_pass(DpArgs A, SearchState *S, uint8
                                                  int32_t *__restrict__ done, double *__restrict__ rat,
                                                  int final_pass) {
     if (!final_pass && S->done) return;
+    if (final_pass && S->final_lane >= 0) return;      // k_final_from_lane serves
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -884,8 +885,43 @@ __global__ void __launch_bounds__(1024) k_cand_select(SearchState *S, uint32_t *
         }
     }
     for (int q = used; q < DP_LANES; ++q) t[q] = t[used - 1];
+    // a spare lane re-evaluates hi: when the search ends after this pass,
+    // beta's state is then among the pass's lanes (no final pass needed)
+    if (used < DP_LANES) t[DP_LANES - 1] = bitsd(hi);
     for (int q = 0; q < DP_LANES; ++q) S->thr[q] = t[q];
     S->cand_passes += 1;
+}
+
+// After the search (one tree): the lane of the last pass that evaluated beta
+// itself, if any.  Its decisions and omega-hat / p-hat are those of the
+// final call of Algorithm 1 at beta, so k_final_from_lane copies them to
+// lane 0 (and forms the cut ratios) instead of another pass.
+__global__ void k_final_lane(SearchState *S) {
+    if (threadIdx.x != 0) return;
+    S->final_lane = -1;
+    if (S->error || !S->done) return;
+    const unsigned long long b = dbits(S->beta);
+    for (int t = 0; t < DP_LANES; ++t)
+        if (dbits(S->thr[t]) == b) { S->final_lane = t; return; }
+}
+
+__global__ void k_final_from_lane(const SearchState *__restrict__ S, const int32_t *__restrict__ parent,
+                                  const double *__restrict__ phi, int64_t n, uint8_t *__restrict__ dec,
+                                  const double *__restrict__ wh, const double *__restrict__ ph,
+                                  double *__restrict__ rat) {
+    const int L = S->final_lane;
+    if (L < 0) return;
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const size_t vl = (size_t)v * DP_LANES + L;
+    const uint8_t d = dec[vl];
+    dec[(size_t)v * DP_LANES] = d;
+    if (d == DEC_CUT) {
+        // the same operations as the pass at beta: fp = phi(e) + p-hat, fp / omega-hat
+        const int32_t u = parent[v];
+        const double fe = u >= 0 ? phi[v] : 0.0;
+        rat[v] = __ddiv_rn(__dadd_rn(fe, ph[vl]), wh[vl]);
+    }
 }
 
 // ---- the same for independent sets: each set in candidate mode counts its
@@ -1242,7 +1278,10 @@ cudaError_t tree_search_and_label(TreeScratch &S, const double *phi_par, const d
             k_cand_select<<<1, 1024, 0, ISO_S(s)>>>(S.search, S.hist);
         }
     }
-    // Final call of Algorithm 1 at beta: Cut, eta and the set ratios.
+    // Final call of Algorithm 1 at beta: Cut, eta and the set ratios (from the
+    // last pass's lane at beta when it has one, else one more pass)
+    k_final_lane<<<1, 32, 0, ISO_S(s)>>>(S.search);
+    k_final_from_lane<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.search, T.parent, phi_par, n, S.dec, S.wh, S.ph, S.rat);
     if ((e = cudaMemsetAsync(S.done, 0, sizeof(int32_t) * n, s))) return e;
     k_dp_pass<<<grid, 256, 0, ISO_S(s)>>>(A, S.search, S.dec, S.wh, S.ph, S.done, S.rat, 1);
     // Algorithm 4: eta by pointer jumping, exclusive scan over Cut.

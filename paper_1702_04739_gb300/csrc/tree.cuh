@@ -35,6 +35,7 @@ struct SearchState {
     int cand_passes;          // passes that took their thresholds from critical ratios
     unsigned int ncand;       // critical ratios inside the bracket (this pass)
     unsigned long long cand[CAND_EXACT];
+    int final_lane;           // lane of the last pass whose threshold is beta (-1: none; one tree)
 };
 
 // Rooted tree in device scratch.
