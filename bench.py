@@ -687,6 +687,38 @@ def run_reference(args):
     return 0
 
 
+def profile_mst(torch, dev, X, args):
+    """Profiling aid: the MST stage alone (the library's cluster_mst), W untimed
+    and K timed calls, CUDA events on the current stream, L2 flushed before
+    each.  Not a benchmark line: it prints its own keys."""
+    from paper_1702_04739_gb300 import isoclust
+    if args.workload not in (WORKLOAD, SPARSE, MOONS):
+        raise SystemExit("--mst-only takes a one-set workload")
+    Xd = torch.from_numpy(np.ascontiguousarray(X)).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    isoclust.set_mst_prune(args.mst_prune)
+    times = []
+    try:
+        for it in range(args.warmup + args.steps):
+            flush.fill_(it & 0xff)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            isoclust.cluster_mst(Xd)
+            b.record()
+            torch.cuda.synchronize()
+            if it >= args.warmup:
+                times.append(a.elapsed_time(b))
+        prof = isoclust.last_profile()
+    finally:
+        isoclust.set_mst_prune(-1)
+    print(json.dumps({"profile": "mst", "workload": args.workload, "n": int(X.shape[0]), "d": int(X.shape[1]),
+                      "mst_prune": args.mst_prune, "ms_per_call": float(np.median(times)),
+                      "tiles_swept": prof.get("mst_tiles_swept"), "tiles_full": prof.get("mst_tiles_full")}),
+          flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -705,6 +737,11 @@ def main():
     ap.add_argument("--sweep-variant", type=int, default=-1,
                     help="force the MST sweep's tile variant 0..3 (profiling: a profiler distorts the autotuner's "
                          "trial timings); -1 = the library's own choice")
+    ap.add_argument("--mst-only", action="store_true",
+                    help="profiling: time only the minimum spanning tree of the workload's points (no omega "
+                         "buffers on the device) and print one line of its own")
+    ap.add_argument("--mst-prune", type=int, default=-1, choices=[-1, 0, 1],
+                    help="with --mst-only: pruned Boruvka rounds -1 auto, 0 never, 1 whenever supported")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -726,6 +763,8 @@ def main():
         pg = dist
 
     data, k, sigma = load_workload(args.workload, seed=rank, n=args.n, nsets=args.nsets)
+    if args.mst_only:
+        return profile_mst(torch, dev, data, args)
     e2e = not args.no_e2e
     if args.workload == BATCHED:
         X, offs, ks = data

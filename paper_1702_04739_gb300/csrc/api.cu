@@ -437,7 +437,8 @@ static isoclust_status cluster_impl(const void *X, int64_t n, int32_t d, int32_t
     // pruned Boruvka rounds (one set, not sharded); their candidate lists
     // (2 per slot) are all written by the first, full round too, which then
     // sweeps PRUNE_SLOTS column splits
-    TC.prune = use_tc && !sh && prune_wanted(n, d);
+    // (the order's kernels read rows by 16 bytes)
+    TC.prune = use_tc && !sh && prune_wanted(n, d) && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
     const int tlists = TC.prune ? 2 * PRUNE_SLOTS : 0;
     const int tsplits_used = TC.prune ? PRUNE_SLOTS : tsplits;
 

@@ -303,7 +303,16 @@ __global__ void k_cmin_d2(const int32_t *__restrict__ comp, const double *__rest
     if (!active(counters)) return;
     const int64_t gs = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gs) {
-        if (rowj[i] >= 0) atomicMin(cd2 + comp[i], dbits(rowd2[i]));
+        // the lanes of one component fold first (late rounds: few components,
+        // so one atomic per component and warp instead of one per row)
+        const bool has = rowj[i] >= 0;
+        const int32_t c = has ? comp[i] : -1;
+        const unsigned long long v = has ? dbits(rowd2[i]) : ~0ull;
+        const unsigned peers = __match_any_sync(__activemask(), c);
+        const unsigned hi = __reduce_min_sync(peers, (unsigned)(v >> 32));
+        const unsigned lo = __reduce_min_sync(peers, (unsigned)(v >> 32) == hi ? (unsigned)v : 0xffffffffu);
+        if (c >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1)
+            atomicMin(cd2 + c, ((unsigned long long)hi << 32) | lo);
     }
 }
 
@@ -365,12 +374,38 @@ __global__ void k_hook_resolve(const int32_t *__restrict__ comp, int64_t n, cons
     }
 }
 
-__global__ void k_jump(const int32_t *__restrict__ comp, const int32_t *__restrict__ nin, int32_t *__restrict__ nout,
-                       int64_t n, const int32_t *counters) {
+// Every root's pointer to the root of its hook tree, in place, in one
+// launch: a find with path halving from each root.  An entry only ever holds
+// an ancestor of its vertex, and a walk only replaces the entry of a vertex
+// it visits by that vertex's grandparent, and only if the entry still holds
+// the parent it read (compare-and-swap: an entry that already holds its root
+// keeps it), so any interleaving of the walks keeps that true, and the walks
+// halve the paths they share (with more roots than resident threads, a later
+// walk finds the paths of the earlier ones compressed).  A walk ends within
+// the tree's depth; one longer than the number of points is a cycle (the
+// hooks never build one), reported as an internal error.
+__global__ void k_jump_all(const int32_t *__restrict__ comp, int32_t *nxt, int64_t n, const int32_t *counters,
+                           uint32_t *st) {
     if (!active(counters)) return;
+    volatile int32_t *vn = nxt;                       // other walks change the entries under us
     const int64_t gs = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gs) {
-        if (comp[v] == v) nout[v] = nin[nin[v]];
+        if (comp[v] != v) continue;
+        int32_t x = (int32_t)v;
+        for (int64_t it = 0;; ++it) {
+            const int32_t p = vn[x];
+            const int32_t q = (p >= 0 && p < n) ? vn[p] : -1;
+            if (q < 0 || q >= n || it > n) {
+                atomicOr(st, DEV_INTERNAL);
+                break;
+            }
+            if (q == p) {                             // p is a root
+                vn[v] = p;
+                break;
+            }
+            atomicCAS(reinterpret_cast<int *>(nxt) + x, p, q);
+            x = q;
+        }
     }
 }
 
@@ -453,7 +488,6 @@ void MstScratch::carve(Arena &A, int64_t n_, int splits_) {
     int64_t m = n > 1 ? n - 1 : 1;
     comp = A.take<int32_t>(n);
     nxt = A.take<int32_t>(n);
-    nxt2 = A.take<int32_t>(n);
     tgt = A.take<int32_t>(n);
     b1v = A.take<float>((size_t)splits * n);
     b2v = A.take<float>((size_t)splits * n);
@@ -511,18 +545,15 @@ cudaError_t mst_build(MstScratch &S, const void *X, int64_t n, int32_t d, int dt
                       uint32_t *status, cudaStream_t s, TcScratch *tc, int32_t target, int64_t max_n,
                       const Shard *sh) {
     k_mst_init<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.comp, n, target, S.counters);
-    // Boruvka at least halves every unfinished set's components per round;
-    // component chains never leave a set, so pointer jumping needs
-    // log2 of the largest set
+    // Boruvka at least halves every unfinished set's components per round
     const int64_t span = max_n > 0 ? max_n : n;
     const int R = log2_ceil(span) + 1;
-    const int L = log2_ceil(span) + 1;
     const unsigned rg = round_grid(n);
     cudaError_t e;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if ((e = cudaStreamIsCapturing(s, &cs))) return e;
     const bool capturing = cs != cudaStreamCaptureStatusNone;
-    if (tc && (e = tc_prepare(*tc, (const float *)X, n, d, s))) return e;
+    if (tc && (e = tc_prepare(*tc, (const float *)X, n, d, s, !tc->prune))) return e;
     if (tc && tc->prune) {
         // pruned rounds (one set): the rows take the pruning's order; no row
         // has a previous round's pair yet
@@ -547,12 +578,8 @@ cudaError_t mst_build(MstScratch &S, const void *X, int64_t n, int32_t d, int dt
         k_hook_tgt<<<rg, TPB, 0, ISO_S(s)>>>(S.comp, n, S.cd2, S.cpair, S.tgt, S.cu, S.cv, S.cdd, S.counters, status);
         k_hook_resolve<<<rg, TPB, 0, ISO_S(s)>>>(S.comp, n, S.tgt, S.cu, S.cv, S.cdd, S.nxt, S.eu, S.ev, S.ed2,
                                                      S.counters, status);
-        int32_t *na = S.nxt, *nb = S.nxt2;
-        for (int it = 0; it < L; ++it) {
-            k_jump<<<rg, TPB, 0, ISO_S(s)>>>(S.comp, na, nb, n, S.counters);
-            int32_t *t = na; na = nb; nb = t;
-        }
-        k_relabel<<<rg, TPB, 0, ISO_S(s)>>>(S.comp, na, n, S.counters);
+        k_jump_all<<<rg, TPB, 0, ISO_S(s)>>>(S.comp, S.nxt, n, S.counters, status);
+        k_relabel<<<rg, TPB, 0, ISO_S(s)>>>(S.comp, S.nxt, n, S.counters);
         if (tc && (e = tc_count_sets(*tc, S.comp, n, S.counters, s))) return e;
         k_round_end<<<1, 1, 0, ISO_S(s)>>>(S.counters);
         // one point set whose tree is complete: the rounds left would only

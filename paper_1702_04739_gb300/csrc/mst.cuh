@@ -15,7 +15,7 @@ enum : int {
 struct MstScratch {
     int64_t n = 0;
     int splits = 1;                // column splits of the sweep grid
-    int32_t *comp, *nxt, *nxt2, *tgt;
+    int32_t *comp, *nxt, *tgt;
     float *b1v, *b2v;              // [splits][n] approximate best / second best
     int32_t *b1j;                  // [splits][n]
     double *rowd2;                 // [n] exact best key per row
@@ -117,7 +117,9 @@ cudaError_t tc_place_rows(TcScratch &T, const float *X, int64_t n, int32_t d, cu
 cudaError_t prune_far_items(TcScratch &T, const int32_t *comp, const double *rowd2, const int32_t *rowj, int64_t n,
                             const int32_t *counters, cudaStream_t s);
 bool tc_supported();
-cudaError_t tc_prepare(TcScratch &T, const float *X, int64_t n, int32_t d, cudaStream_t s);
+// place = false: the rows are placed later (tc_place_rows, by the pruned
+// rounds' order); only the mean, maps and buffers are prepared.
+cudaError_t tc_prepare(TcScratch &T, const float *X, int64_t n, int32_t d, cudaStream_t s, bool place = true);
 cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t n, int32_t d, uint32_t *status,
                            cudaStream_t s);
 // omega screen on the tensor cores: Xp (n x d, omega's row order) and its

@@ -467,14 +467,35 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
 
 // Centre, split into BF16 hi + lo (zero rows at padding) and the squared
 // norms of the represented points.
-__global__ void k_tc_mean_partial(const float *__restrict__ X, int64_t n, int32_t d, int64_t rows_per,
-                                  double *__restrict__ part) {
-    const int t = threadIdx.x + blockIdx.y * blockDim.x;
-    if (t >= d) return;
+// Partial column sums of rows [r0, r1): warp w sums every 8th row from
+// r0 + w in FP32 (four chains, 32 columns per warp), the block's warps are
+// added in FP64.  Any centre serves (it only shrinks the represented
+// magnitudes); this one is deterministic.
+__global__ void __launch_bounds__(256) k_tc_mean_partial(const float *__restrict__ X, int64_t n, int32_t d,
+                                                         int64_t rows_per, double *__restrict__ part) {
+    __shared__ float acc[8][33];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int t = blockIdx.y * 32 + lane;
     const int64_t r0 = (int64_t)blockIdx.x * rows_per, r1 = min(n, r0 + rows_per);
-    double s = 0.0;
-    for (int64_t r = r0; r < r1; ++r) s += (double)X[r * d + t];
-    part[(int64_t)blockIdx.x * d + t] = s;
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+    if (t < d) {
+        int64_t r = r0 + wp;
+#pragma unroll 2
+        for (; r + 24 < r1; r += 32) {
+            s0 += X[r * d + t];
+            s1 += X[(r + 8) * d + t];
+            s2 += X[(r + 16) * d + t];
+            s3 += X[(r + 24) * d + t];
+        }
+        for (; r < r1; r += 8) s0 += X[r * d + t];
+    }
+    acc[wp][lane] = (s0 + s1) + (s2 + s3);
+    __syncthreads();
+    if (wp == 0 && t < d) {
+        double sum = 0.0;
+        for (int w = 0; w < 8; ++w) sum += (double)acc[w][lane];
+        part[(int64_t)blockIdx.x * d + t] = sum;
+    }
 }
 
 __global__ void k_tc_mean_final(const double *__restrict__ part, int nparts, int64_t n, int32_t d,
@@ -495,10 +516,16 @@ __global__ void __launch_bounds__(256) k_tc_set_mean(const float *__restrict__ X
     const int64_t r0 = offs[b], r1 = offs[b + 1];
     for (int t0 = 0; t0 < d; t0 += 32) {
         const int t = t0 + lane;
-        double s = 0.0;
-        if (t < d)
-            for (int64_t r = r0 + wp; r < r1; r += 8) s += (double)X[r * d + t];
-        acc[wp][lane] = s;
+        float s0 = 0.0f, s1 = 0.0f;                         // FP32 chains; the warps add in FP64
+        if (t < d) {
+            int64_t r = r0 + wp;
+            for (; r + 8 < r1; r += 16) {
+                s0 += X[r * d + t];
+                s1 += X[(r + 8) * d + t];
+            }
+            if (r < r1) s0 += X[r * d + t];
+        }
+        acc[wp][lane] = (double)(s0 + s1);
         __syncthreads();
         if (wp == 0 && t < d) {
             double tot = 0.0;
@@ -654,14 +681,14 @@ __global__ void k_tc_fill_lists(float *__restrict__ tv, int32_t *__restrict__ tj
 // Candidate columns are read from xs (rows in the sweep's order) with their
 // components from compp, so a candidate block is 32 contiguous rows of xs;
 // only the survivors of the FP32 filter are mapped back to point indices.
-// The lists' (column split x tile of the pair) best-8 block lower bounds and
-// their best upper bound U are merged.
+// The lists (column split x tile of the pair) hold each split's best-8
+// block lower bounds and their best upper bound U.
 // The epilogue's bounds hold for the BF16-represented points; the exact
 // points differ by the representation error rep, so a block can hold the
 // nearest foreign point only if its lower bound is <= U + 2 rep.  Those
 // blocks' columns are filtered with FP32 direct differences and the
-// survivors keyed in FP64.  If the 8th kept block still qualifies, the row is
-// queued for a rescan.
+// survivors keyed in FP64.  If 8 or more blocks qualify (a list may have
+// dropped more), the row is queued for a rescan.
 __device__ __forceinline__ float approx_d2_f32(const float *__restrict__ a, const float *__restrict__ b, int d) {
     float acc = 0.0f;
     for (int t = 0; t < d; ++t) {
@@ -669,6 +696,63 @@ __device__ __forceinline__ float approx_d2_f32(const float *__restrict__ a, cons
         acc = __fmaf_rn(df, df, acc);
     }
     return acc;
+}
+
+// FP32 squared differences of row r against the columns of the NU first
+// slots (dimension order, one FMA chain per column; a dead slot reads the
+// row itself and is ignored), unrolled so that fewer columns keep more loads
+// in flight.
+template <int NU>
+__device__ __forceinline__ void rc_dist(const float *__restrict__ xs, int64_t r, int32_t d, bool vec,
+                                        const int32_t (&jp)[4], const bool (&live)[4], float (&acc)[4]) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[u] = 0.0f;
+    const float *xi = xs + r * d;
+    if (vec) {
+        constexpr int UNR = NU == 1 ? 4 : (NU == 2 ? 2 : 1);
+        const float4 *xi4 = reinterpret_cast<const float4 *>(xi);
+        const float4 *b4[NU];
+#pragma unroll
+        for (int u = 0; u < NU; ++u) b4[u] = reinterpret_cast<const float4 *>(xs + (live[u] ? (int64_t)jp[u] : r) * d);
+        const int d4 = d / 4;
+        int t = 0;
+#pragma unroll 1
+        for (; t + UNR <= d4; t += UNR) {
+            float4 a[UNR], b[UNR][NU];
+#pragma unroll
+            for (int v = 0; v < UNR; ++v) {
+                a[v] = xi4[t + v];
+#pragma unroll
+                for (int u = 0; u < NU; ++u) b[v][u] = b4[u][t + v];
+            }
+#pragma unroll
+            for (int v = 0; v < UNR; ++v) {
+#pragma unroll
+                for (int u = 0; u < NU; ++u) {
+                    float df = __fsub_rn(a[v].x, b[v][u].x); acc[u] = __fmaf_rn(df, df, acc[u]);
+                    df = __fsub_rn(a[v].y, b[v][u].y); acc[u] = __fmaf_rn(df, df, acc[u]);
+                    df = __fsub_rn(a[v].z, b[v][u].z); acc[u] = __fmaf_rn(df, df, acc[u]);
+                    df = __fsub_rn(a[v].w, b[v][u].w); acc[u] = __fmaf_rn(df, df, acc[u]);
+                }
+            }
+        }
+#pragma unroll 1
+        for (; t < d4; ++t) {
+            const float4 a = xi4[t];
+#pragma unroll
+            for (int u = 0; u < NU; ++u) {
+                const float4 b = b4[u][t];
+                float df = __fsub_rn(a.x, b.x); acc[u] = __fmaf_rn(df, df, acc[u]);
+                df = __fsub_rn(a.y, b.y); acc[u] = __fmaf_rn(df, df, acc[u]);
+                df = __fsub_rn(a.z, b.z); acc[u] = __fmaf_rn(df, df, acc[u]);
+                df = __fsub_rn(a.w, b.w); acc[u] = __fmaf_rn(df, df, acc[u]);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < NU; ++u)
+            if (live[u]) acc[u] = approx_d2_f32(xi, xs + (int64_t)jp[u] * d, d);
+    }
 }
 
 template <int EPL, int CW>
@@ -680,8 +764,8 @@ __device__ __forceinline__ void recheck_row(int64_t r, int lane, const float *__
                                             float add32, int32_t *__restrict__ nsurv, int32_t *__restrict__ surv,
                                             int32_t *__restrict__ rowj, int32_t *__restrict__ ovf,
                                             const int32_t *__restrict__ set_of, const int32_t *__restrict__ setcnt,
-                                            int32_t *counters, float *__restrict__ wv_s, float *__restrict__ bv_s,
-                                            int32_t *__restrict__ bj_s, int shard_rank, int shard_world,
+                                            int32_t *counters, int32_t *__restrict__ bj_s, int shard_rank,
+                                            int shard_world,
                                             const int32_t *__restrict__ row_lists) {
     if (lane == 0) nsurv[r] = 0;           // every row, padding included: k_exact_tc reads them all
     const int64_t i = perm[r];
@@ -694,87 +778,15 @@ __device__ __forceinline__ void recheck_row(int64_t r, int lane, const float *__
         if (lane == 0) rowj[i] = -1;
         return;
     }
-    // ---- merge: each lane holds EPL of the lists x 8 entries (lists x 8 <=
-    //      32 EPL); the best 8 are selected by 8 rounds of a warp arg-min
-    // pruned rounds: only the lists its row tile's items wrote (the others
-    // hold no candidate)
+    // ---- the cut: U, the smallest upper bound over the lists of the
+    //      row's nearest foreign d2; each lane holds EPL of the lists x 8
+    //      block entries (lists x 8 <= 32 EPL)
     if (row_lists) lists = row_lists[r / TC_BM];
     const int ne = lists * TC_TOPK;
-    float ev[EPL];
-    int32_t ej[EPL];
-#pragma unroll
-    for (int q = 0; q < EPL; ++q) {
-        const int e = lane + 32 * q;
-        if (e < ne) {
-            const int sidx = e / TC_TOPK, k = e - sidx * TC_TOPK;
-            const size_t o = ((size_t)sidx * n + r) * TC_TOPK + k;
-            ev[q] = tv[o];
-            ej[q] = tj[o];
-        } else {
-            ev[q] = INFINITY;
-            ej[q] = -1;
-        }
-    }
     float U = lane < lists ? tu[(size_t)lane * n + r] : INFINITY;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) U = fminf(U, __shfl_xor_sync(0xffffffffu, U, o));
-    float bv[TC_TOPK];
-    int32_t bj[TC_TOPK];
-    if constexpr (EPL == 1) {
-        // one entry per lane: its rank in the order (value, lane) - the
-        // order of repeated arg-mins - from all 32 values in shared memory;
-        // the 8 first scatter themselves, every lane reads them back
-        __syncwarp();
-        wv_s[lane] = ev[0];
-        __syncwarp();
-        int rk0 = 0, rk1 = 0;
-#pragma unroll
-        for (int q = 0; q < 32; q += 2) {
-            const float w0 = wv_s[q], w1 = wv_s[q + 1];
-            rk0 += (w0 < ev[0] || (w0 == ev[0] && q < lane)) ? 1 : 0;
-            rk1 += (w1 < ev[0] || (w1 == ev[0] && q + 1 < lane)) ? 1 : 0;
-        }
-        const int rk = rk0 + rk1;
-        if (rk < TC_TOPK) {
-            bv_s[rk] = ev[0];
-            bj_s[rk] = ej[0];
-        }
-        __syncwarp();
-#pragma unroll
-        for (int k = 0; k < TC_TOPK; ++k) {
-            bv[k] = bv_s[k];
-            bj[k] = bv[k] < INFINITY ? bj_s[k] : -1;
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < TC_TOPK; ++k) {
-            float mv = ev[0];
-            int ms = 0;
-#pragma unroll
-            for (int q = 1; q < EPL; ++q)
-                if (ev[q] < mv) { mv = ev[q]; ms = q; }
-            float wv = mv;
-            int wl = lane;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float ov = __shfl_xor_sync(0xffffffffu, wv, o);
-                const int ol = __shfl_xor_sync(0xffffffffu, wl, o);
-                if (ov < wv || (ov == wv && ol < wl)) { wv = ov; wl = ol; }
-            }
-            int32_t wj = -1;
-#pragma unroll
-            for (int q = 0; q < EPL; ++q) wj = (ms == q) ? ej[q] : wj;
-            wj = __shfl_sync(0xffffffffu, wj, wl);
-            if (lane == wl) {
-#pragma unroll
-                for (int q = 0; q < EPL; ++q)
-                    if (ms == q) ev[q] = INFINITY;
-            }
-            bv[k] = wv;
-            bj[k] = (wv < INFINITY) ? wj : -1;
-        }
-    }
-    if (bj[0] < 0 || !(U < INFINITY)) {
+    if (!(U < INFINITY)) {
         if (lane == 0) rowj[i] = -1;
         return;
     }
@@ -786,7 +798,28 @@ __device__ __forceinline__ void recheck_row(int64_t r, int lane, const float *__
     const float hi_true = __fmul_ru(__fmul_ru(a1, a1), 1.00001f);     // exact nearest foreign d2 <= this
     const float a2 = __fadd_ru(__fsqrt_ru(hi_true), w);
     const float tile_cut = __fmul_ru(__fmul_ru(a2, a2), 1.00001f);   // represented d2 of any candidate <= this
-    if (bj[TC_TOPK - 1] >= 0 && bv[TC_TOPK - 1] <= tile_cut) {
+    // ---- the blocks whose lower bound is within the cut, compacted (their
+    //      order does not matter).  TC_TOPK of them or more: a list may have
+    //      dropped more, so the row is queued for a rescan.
+    int cnt = 0;
+    const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+    for (int q = 0; q < EPL; ++q) {
+        const int e = lane + 32 * q;
+        bool qual = false;
+        int32_t blk = -1;
+        if (e < ne) {
+            const int sidx = e / TC_TOPK, k = e - sidx * TC_TOPK;
+            const size_t o = ((size_t)sidx * n + r) * TC_TOPK + k;
+            blk = tj[o];
+            qual = blk >= 0 && tv[o] <= tile_cut;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, qual);
+        const int slot = cnt + __popc(bal & below);
+        if (qual && slot < TC_TOPK) bj_s[slot] = blk;
+        cnt += __popc(bal);
+    }
+    if (cnt >= TC_TOPK) {
         if (lane == 0) {
             const int q = atomicAdd(counters + MC_OVERFLOW, 1);
             ovf[q] = (int32_t)i;
@@ -794,57 +827,44 @@ __device__ __forceinline__ void recheck_row(int64_t r, int lane, const float *__
         }
         return;
     }
-    // FP32 direct differences over the candidate blocks (four per pass, one
-    // column of each per lane: four FMA chains).  Pass 1: the row's FP32
+    if (cnt == 0) {
+        if (lane == 0) rowj[i] = -1;
+        return;
+    }
+    __syncwarp();
+    int32_t bj[TC_TOPK];
+#pragma unroll
+    for (int k = 0; k < TC_TOPK; ++k) bj[k] = k < cnt ? bj_s[k] : -1;
+    __syncwarp();                           // (bj_s is rewritten by the warp's next row)
+    // FP32 direct differences over the qualifying blocks (up to four columns
+    // per lane per pass, only as many as there are).  Pass 1: the row's FP32
     // minimum m32; the exact best has FP32 value <= m32 * mul32 + add32.
     // Pass 2 filters the first pass's distances and records those columns.
     const int32_t ci = compp[r];
-    const float *xi = xs + r * d;
     const bool vec = (d & 3) == 0 && (reinterpret_cast<uintptr_t>(xs) & 15) == 0;
-    // a pass covers four columns per lane: SPB of each of BPP blocks
+    // a pass covers up to four columns per lane: SPB of each of BPP blocks
     constexpr int SPB = CW / 32, BPP = 4 / SPB;
-    // block q of the sorted list qualifies if its lower bound is within the cut
-    auto qual = [&](int q) { return q < TC_TOPK && bj[q] >= 0 && bv[q] <= tile_cut; };
-    auto scan = [&](int k, int32_t (&jp)[4], bool (&live)[4], float (&acc)[4]) {
+    auto slots = [&](int k, int nu, int32_t (&jp)[4], bool (&live)[4]) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int q = k + u / SPB;
-            const int cand = qual(q) ? bj[q] : -1;
+            const int cand = (u < nu && q < TC_TOPK) ? bj[q < TC_TOPK ? q : 0] : -1;
             jp[u] = cand < 0 ? -1 : cand * CW + lane + 32 * (u % SPB);   // padded column (< n_pad <= 2^31)
             int32_t cj = -2;
             if (jp[u] >= 0 && jp[u] < n) cj = compp[jp[u]];
             live[u] = cj >= 0 && cj != ci;                                 // padding: -2
-            acc[u] = 0.0f;
         }
-        if (vec) {
-            // every slot loads (a dead slot reads the row itself and is
-            // ignored), so the four columns' loads issue together
-            const float4 *xi4 = reinterpret_cast<const float4 *>(xi);
-            const float4 *b4[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) b4[u] = reinterpret_cast<const float4 *>(xs + (live[u] ? (int64_t)jp[u] : r) * d);
-#pragma unroll 1
-            for (int t = 0; t < d / 4; ++t) {
-                const float4 a = xi4[t];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const float4 b = b4[u][t];
-                    float df = __fsub_rn(a.x, b.x); acc[u] = __fmaf_rn(df, df, acc[u]);
-                    df = __fsub_rn(a.y, b.y); acc[u] = __fmaf_rn(df, df, acc[u]);
-                    df = __fsub_rn(a.z, b.z); acc[u] = __fmaf_rn(df, df, acc[u]);
-                    df = __fsub_rn(a.w, b.w); acc[u] = __fmaf_rn(df, df, acc[u]);
-                }
-            }
-        } else {
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (live[u]) acc[u] = approx_d2_f32(xi, xs + (int64_t)jp[u] * d, d);
-        }
+    };
+    auto scan = [&](int k, int32_t (&jp)[4], bool (&live)[4], float (&acc)[4]) {
+        const int nu = min(4, (cnt - k) * SPB);                           // (warp-uniform)
+        slots(k, nu, jp, live);
+        if (nu == 1) rc_dist<1>(xs, r, d, vec, jp, live, acc);
+        else if (nu == 2) rc_dist<2>(xs, r, d, vec, jp, live, acc);
+        else rc_dist<4>(xs, r, d, vec, jp, live, acc);
     };
     // pass 1 keeps the distances of its first KEEP passes in registers; pass
     // 2 filters those against the threshold without reading the columns
-    // again (later passes, rare, are scanned again).  Qualifying blocks are
-    // a prefix of the sorted list, so a pass runs only if its first one does.
+    // again (later passes, rare, are scanned again).
     constexpr int NPASS = TC_TOPK / BPP, KEEP = NPASS < 2 ? NPASS : 2;
     float pmin[NPASS];
     float accs[KEEP][4];
@@ -854,7 +874,7 @@ __device__ __forceinline__ void recheck_row(int64_t r, int lane, const float *__
 #pragma unroll
     for (int p = 0; p < NPASS; ++p) {
         pmin[p] = INFINITY;
-        if (!qual(BPP * p)) continue;
+        if (BPP * p >= cnt) continue;
         int32_t jp[4];
         bool live[4];
         float acc[4];
@@ -877,7 +897,7 @@ __device__ __forceinline__ void recheck_row(int64_t r, int lane, const float *__
         return;
     }
     const float thr = __fadd_ru(__fmul_ru(m32, mul32), add32);
-    int cnt = 0;
+    int ns = 0;
 #pragma unroll
     for (int p = 0; p < NPASS; ++p) {
         if (!__any_sync(0xffffffffu, pmin[p] <= thr)) continue;
@@ -898,18 +918,18 @@ __device__ __forceinline__ void recheck_row(int64_t r, int lane, const float *__
         for (int u = 0; u < 4; ++u) {
             const bool sv = live[u] && acc[u] <= thr;
             const unsigned bal = __ballot_sync(0xffffffffu, sv);
-            const int slot = cnt + __popc(bal & ((1u << lane) - 1u));
+            const int slot = ns + __popc(bal & below);
             if (sv && slot < TC_SURV) surv[r * TC_SURV + slot] = jp[u];
-            cnt += __popc(bal);
+            ns += __popc(bal);
         }
     }
     if (lane == 0) {
-        if (cnt > TC_SURV) {                     // many near-ties: exact rescan of the row
+        if (ns > TC_SURV) {                     // many near-ties: exact rescan of the row
             const int q = atomicAdd(counters + MC_OVERFLOW, 1);
             ovf[q] = (int32_t)i;
             rowj[i] = -2;
         } else {
-            nsurv[r] = cnt;
+            nsurv[r] = ns;
         }
     }
 }
@@ -959,14 +979,13 @@ __global__ void __launch_bounds__(256, 4) k_recheck_tc(const float *__restrict__
                                                        int shard_rank, int shard_world,
                                                        const int32_t *__restrict__ row_lists) {
     if (!mst_active(counters)) return;
-    __shared__ float wv_s[8][32], bv_s[8][TC_TOPK];
     __shared__ int32_t bj_s[8][TC_TOPK];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r = w0; r < n; r += nw)
         recheck_row<EPL, CW>(r, lane, xs, n, d, lists, tv, tj, tu, rsq, perm, compp, nmax_bits, eps_rep, mul32, add32, nsurv,
-                             surv, rowj, ovf, set_of, setcnt, counters, wv_s[wib], bv_s[wib], bj_s[wib], shard_rank,
+                             surv, rowj, ovf, set_of, setcnt, counters, bj_s[wib], shard_rank,
                              shard_world, row_lists);
 }
 
@@ -1314,22 +1333,22 @@ bool tc_supported() {
     return major == 10 && minor == 3 && encode_fn() != nullptr;
 }
 
-cudaError_t tc_prepare(TcScratch &T, const float *X, int64_t n, int32_t d, cudaStream_t s) {
+cudaError_t tc_prepare(TcScratch &T, const float *X, int64_t n, int32_t d, cudaStream_t s, bool place) {
     cudaError_t e;
     const bool sets = T.set_of != nullptr;
     if (sets) {
         k_tc_set_mean<<<(unsigned)T.nsets, 256, 0, ISO_S(s)>>>(X, T.offs, d, T.mean);
     } else {
         const int64_t rows_per = ceil_div(n, 64);
-        dim3 gm(64, (unsigned)ceil_div(d, 128));
-        k_tc_mean_partial<<<gm, 128, 0, ISO_S(s)>>>(X, n, d, rows_per, T.part);
+        dim3 gm(64, (unsigned)ceil_div(d, 32));
+        k_tc_mean_partial<<<gm, 256, 0, ISO_S(s)>>>(X, n, d, rows_per, T.part);
         k_tc_mean_final<<<(unsigned)ceil_div(d, 128), 128, 0, ISO_S(s)>>>(T.part, 64, n, d, T.mean);
     }
     T.prune_ready = false;           // (pruned rounds start after the first, in their own row order)
     if (T.keep_order) {
         // rows as given (the omega screen works in omega's row order)
         k_tc_identity<<<(unsigned)ceil_div(T.n_pad, 256), 256, 0, ISO_S(s)>>>(T.permp, n, T.n_pad);
-    } else {
+    } else if (place) {
         // norm order: tiles of points with similar |x - c| give tight tile bounds
         k_tc_prenorm_keys<<<(unsigned)ceil_div(n, 256), 256, 0, ISO_S(s)>>>(X, T.mean, T.set_of, n, d, T.keys, T.perm);
         if ((e = sort_pairs_u64(T.keys, T.perm, T.kbuf, T.vbuf, n, s))) return e;
@@ -1339,13 +1358,16 @@ cudaError_t tc_prepare(TcScratch &T, const float *X, int64_t n, int32_t d, cudaS
     }
     T.cw = (sets || T.d_pad > 64) ? 32 : 64;      // heuristic variant (see tc_autotune)
     T.resident = true;
-    const int64_t tot = T.n_pad * T.d_pad;
-    k_tc_split<<<(unsigned)ceil_div(tot, 256), 256, 0, ISO_S(s)>>>(X, T.mean, T.set_of, T.permp, d, T.n_pad, T.d_pad,
-                                                                  T.xh, T.xl, T.xs);
-    if ((e = cudaMemsetAsync(T.nmax_bits, 0, sizeof(unsigned int), s))) return e;
-    k_tc_norms<<<(unsigned)ceil_div(T.n_pad, 256), 256, 0, ISO_S(s)>>>(T.xh, T.xl, T.permp, T.n_pad, T.d_pad, T.nrm,
-                                                                      T.cnrm, T.rsq, T.nmax_bits);
-    k_tc_tile_max<<<(unsigned)ceil_div(T.n_pad / TC_BM, 128), 128, 0, ISO_S(s)>>>(T.nrm, T.n_pad, T.tmax, T.tsq);
+    if (place || T.keep_order) {
+        const int64_t tot = T.n_pad * T.d_pad;
+        k_tc_split<<<(unsigned)ceil_div(tot, 256), 256, 0, ISO_S(s)>>>(X, T.mean, T.set_of, T.permp, d, T.n_pad,
+                                                                      T.d_pad, T.xh, T.xl, T.xs);
+        if ((e = cudaMemsetAsync(T.nmax_bits, 0, sizeof(unsigned int), s))) return e;
+        k_tc_norms<<<(unsigned)ceil_div(T.n_pad, 256), 256, 0, ISO_S(s)>>>(T.xh, T.xl, T.permp, T.n_pad, T.d_pad,
+                                                                          T.nrm, T.cnrm, T.rsq, T.nmax_bits);
+        k_tc_tile_max<<<(unsigned)ceil_div(T.n_pad / TC_BM, 128), 128, 0, ISO_S(s)>>>(T.nrm, T.n_pad, T.tmax,
+                                                                                      T.tsq);
+    }
     if (T.swept && (e = cudaMemsetAsync(T.swept, 0, sizeof(unsigned long long), s))) return e;
     if (sets) {
         // lists that no item writes (sets with fewer splits) stay empty

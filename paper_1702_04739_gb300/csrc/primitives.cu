@@ -1,4 +1,4 @@
-// primitives.cu -- exclusive scan and stable merge sort used by the tree stage.
+// primitives.cu -- exclusive scan and stable merge sort.
 #include "common.cuh"
 
 namespace iso {
@@ -124,6 +124,57 @@ __global__ void merge_pass(const uint64_t *__restrict__ kin, const int32_t *__re
     kout[out] = key;
     vout[out] = vin[i];
 }
+
+// The first passes in shared memory: each block sorts its chunk of
+// SORT_CHUNK elements with the same stable rank merge, run widths 1 to
+// SORT_CHUNK / 2, then the global passes continue from SORT_CHUNK.
+constexpr int SORT_CHUNK = 2048, SORT_THREADS = 1024;
+__global__ void __launch_bounds__(SORT_THREADS) chunk_sort(const uint64_t *__restrict__ kin,
+                                                           const int32_t *__restrict__ vin,
+                                                           uint64_t *__restrict__ kout, int32_t *__restrict__ vout,
+                                                           int64_t n) {
+    __shared__ uint64_t sk[2][SORT_CHUNK];
+    __shared__ int32_t sv[2][SORT_CHUNK];
+    const int64_t base = (int64_t)blockIdx.x * SORT_CHUNK;
+    const int cnt = (int)(n - base < SORT_CHUNK ? n - base : SORT_CHUNK);
+    for (int i = threadIdx.x; i < cnt; i += SORT_THREADS) {
+        sk[0][i] = kin[base + i];
+        sv[0][i] = vin[base + i];
+    }
+    __syncthreads();
+    int b = 0;
+    for (int w = 1; w < cnt; w <<= 1, b ^= 1) {
+        const uint64_t *ka = sk[b];
+        for (int i = threadIdx.x; i < cnt; i += SORT_THREADS) {
+            const int run = i / w, start = (run & ~1) * w, pos = i - run * w;
+            const uint64_t key = ka[i];
+            int out;
+            if ((run & 1) == 0) {
+                int lo = start + w < cnt ? start + w : cnt, hi = start + 2 * w < cnt ? start + 2 * w : cnt;
+                const int b0 = lo;
+                while (lo < hi) {                    // first B element with key >= key
+                    const int mid = (lo + hi) >> 1;
+                    if (ka[mid] < key) lo = mid + 1; else hi = mid;
+                }
+                out = start + pos + (lo - b0);
+            } else {
+                int lo = start, hi = start + w;
+                while (lo < hi) {                    // first A element with key > key
+                    const int mid = (lo + hi) >> 1;
+                    if (ka[mid] <= key) lo = mid + 1; else hi = mid;
+                }
+                out = start + pos + (lo - start);
+            }
+            sk[b ^ 1][out] = key;
+            sv[b ^ 1][out] = sv[b][i];
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < cnt; i += SORT_THREADS) {
+        kout[base + i] = sk[b][i];
+        vout[base + i] = sv[b][i];
+    }
+}
 }  // namespace
 
 cudaError_t sort_pairs_u64(uint64_t *keys, int32_t *vals, uint64_t *kbuf, int32_t *vbuf, int64_t n,
@@ -131,7 +182,12 @@ cudaError_t sort_pairs_u64(uint64_t *keys, int32_t *vals, uint64_t *kbuf, int32_
     if (n <= 1) return cudaSuccess;
     uint64_t *ka = keys, *kb = kbuf;
     int32_t *va = vals, *vb = vbuf;
-    for (int64_t w = 1; w < n; w <<= 1) {
+    chunk_sort<<<(unsigned)ceil_div(n, SORT_CHUNK), SORT_THREADS, 0, ISO_S(s)>>>(ka, va, kb, vb, n);
+    {
+        uint64_t *tk = ka; ka = kb; kb = tk;
+        int32_t *tv = va; va = vb; vb = tv;
+    }
+    for (int64_t w = SORT_CHUNK; w < n; w <<= 1) {
         merge_pass<<<(unsigned)ceil_div(n, 256), 256, 0, ISO_S(s)>>>(ka, va, kb, vb, n, w);
         uint64_t *tk = ka; ka = kb; kb = tk;
         int32_t *tv = va; va = vb; vb = tv;

@@ -70,3 +70,23 @@ def test_pruned_after_a_full_call_the_same(iso):
     fu, fv, fd = _mst(iso, X)
     iso.set_mst_prune(-1)
     assert (au == fu).all() and (av == fv).all() and (ad == fd).all()
+
+
+@pytest.mark.parametrize("prune", [0, 1])
+def test_hook_chain_is_the_path(iso, oracle_lib, prune):
+    """Points on a line with strictly shrinking gaps: in the first round every
+    point hooks to its right neighbour, so the hooks form one chain through
+    all the points (the deepest tree the root finding can meet); the tree is
+    the path.  Coordinates and squared gaps are integers below 2^24, exact in
+    FP32."""
+    N = 4000
+    x = np.concatenate([[0], np.cumsum(N - np.arange(N - 1))]).astype(np.float64)
+    X = np.zeros((N, 4), np.float32)
+    X[:, 0] = x
+    iso.set_mst_prune(prune)
+    u, v, d2 = _mst(iso, X)
+    iso.set_mst_prune(-1)
+    lo, hi = np.minimum(u, v), np.maximum(u, v)
+    assert sorted(zip(lo.tolist(), hi.tolist())) == [(k, k + 1) for k in range(N - 1)]
+    ru, rv, rd = oracle_lib.mst_prim(X)[:3]
+    assert (u == ru).all() and (v == rv).all() and (d2 == rd).all()
