@@ -62,6 +62,7 @@ struct TcScratch {
     int32_t *tj = nullptr;
     int32_t *nsurv = nullptr, *surv = nullptr;     // per row: columns to key in FP64 (padded column indices)
     uint32_t *err = nullptr;
+    uint32_t *qctr = nullptr;                      // the sweep's work-item counter (zeroed before each launch)
     // independent sets (null for one set): sweep work items {row tile,
     // first and end column tile, split}, set of each point, set offsets
     // and the first padded row of each set (device arrays)

@@ -52,6 +52,7 @@ constexpr int TC_TOPK = 8;                                // best candidate bloc
 // the sweep's limit) or 32 (independent sets or wider rows: the recheck's
 // column reads are the limit).
 constexpr int TC_SURV = 8;                                // FP64-keyed columns per row (more: rescan)
+constexpr int TC_QD = 4;                                  // work-item queue slots (producer -> MMA, epilogue)
 constexpr long long TC_WAIT_CYCLES = 4000000000LL;         // default bound of one wait (about 2 s)
 
 // Column metadata first: the epilogue reads it with 16-byte vector loads.
@@ -63,6 +64,8 @@ struct __align__(16) TcShared {
     uint64_t a_full, a_empty;
     uint64_t drain;                                       // completion of the issued MMAs at exit
     uint64_t stall;                                       // test hook: a barrier nothing arrives at
+    uint64_t q_full[TC_QD], q_empty[TC_QD];               // work-item queue
+    int32_t q_item[TC_QD];
     uint32_t tmem_base;
     uint32_t pad;
 };
@@ -140,7 +143,8 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
            const int32_t *__restrict__ comp, int64_t nrows, int ntiles, int kchunks, int splits,
            const int4 *__restrict__ witems, int64_t nwitems, const int32_t *__restrict__ setcnt,
            const int32_t *counters, float *__restrict__ out_v, int32_t *__restrict__ out_j, float *__restrict__ out_u,
-           uint32_t *err, ScreenArgs scr, long long wait_limit, int stall_test, int rt_stride, int rt_off) {
+           uint32_t *err, ScreenArgs scr, long long wait_limit, int stall_test, int rt_stride, int rt_off,
+           uint32_t *__restrict__ qctr) {
     if (!SCREEN && !mst_active(counters)) return;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -165,6 +169,10 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
         mbar_init(&sh->a_empty, 1);
         mbar_init(&sh->drain, 1);
         mbar_init(&sh->stall, 1);
+        for (int q = 0; q < TC_QD; ++q) {
+            mbar_init(&sh->q_full[q], 1);
+            mbar_init(&sh->q_empty[q], 1 + TC_EPI_WARPS);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -181,7 +189,11 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
     // work item w: row tile rt against column tiles [c0, c1), candidate list
     // pair sp; either from the item list (sp in the low 4 bits, the set
     // above: items of a set whose forest is complete are skipped) or row tile
-    // x column split
+    // x column split.  Items are handed out in order by the launch's counter
+    // (qctr, zero at launch): the producer takes the next one when it is
+    // ready for it and publishes it to the MMA issuer and the epilogue warps
+    // through a TC_QD-slot queue (-1: none left), so a CTA with long items
+    // takes fewer of them.
     // (a sharded call: only the row tiles rt_off, rt_off + rt_stride, ... of this rank)
     const int64_t own_tiles = rt_off < ntiles ? ((int64_t)ntiles - rt_off + rt_stride - 1) / rt_stride : 0;
     const int64_t items = witems ? nwitems : own_tiles * splits;
@@ -204,8 +216,16 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
         if (lane == 0) {
             uint32_t stage = 0, phase = 0, a_phase = 0;
             uint32_t fills = 0, a_fills = 0;         // ring stages / A blocks whose copies were issued
+            uint32_t qs = 0, qph = 0;
             bool ok = true;
-            for (int64_t w = blockIdx.x; w < items && ok; w += gridDim.x) {
+            while (ok) {
+                if (!(ok = mbar_wait(&sh->q_empty[qs], qph ^ 1u, err, wait_limit))) break;
+                const uint32_t wq = atomicAdd(qctr, 1u);
+                const int64_t w = (int64_t)wq < items ? (int64_t)wq : -1;
+                sh->q_item[qs] = (int32_t)w;
+                mbar_arrive(&sh->q_full[qs]);
+                if (++qs == TC_QD) { qs = 0; qph ^= 1u; }
+                if (w < 0) break;
                 int rt, c0, c1, sp;
                 item(w, rt, c0, c1, sp);
                 if (ARES && c0 < c1) {          // (an empty item only writes its rows' empty lists)
@@ -252,8 +272,14 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
             uint32_t stage = 0, phase = 0, acc = 0, acc_phase = 0, a_phase = 0;
+            uint32_t qs = 0, qph = 0;
             bool ok = true;
-            for (int64_t w = blockIdx.x; w < items && ok; w += gridDim.x) {
+            while (ok) {
+                if (!(ok = mbar_wait(&sh->q_full[qs], qph, err, wait_limit))) break;
+                const int64_t w = *(volatile int32_t *)&sh->q_item[qs];
+                mbar_arrive(&sh->q_empty[qs]);
+                if (++qs == TC_QD) { qs = 0; qph ^= 1u; }
+                if (w < 0) break;
                 int rt, c0, c1, sp;
                 item(w, rt, c0, c1, sp);
                 (void)rt;
@@ -309,8 +335,17 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
         const int trow = quad * 32 + lane;             // row within the tile = TMEM lane
         const int cm = et;                             // column of the pair whose metadata this thread stages
         uint32_t acc = 0, acc_phase = 0;
+        uint32_t qs = 0, qph = 0;
         bool ok = true;
-        for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
+        for (;;) {
+            if (ok) ok = mbar_wait(&sh->q_full[qs], qph, err, wait_limit);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;                            // (a wait ran out: the call reports it)
+            const int64_t w = *(volatile int32_t *)&sh->q_item[qs];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh->q_empty[qs]);
+            if (++qs == TC_QD) { qs = 0; qph ^= 1u; }
+            if (w < 0) break;
             int rt, c0, c1, sp;
             item(w, rt, c0, c1, sp);
             const int64_t row = (int64_t)rt * TC_BM + trow;      // < nrows: whole tiles
@@ -1138,6 +1173,7 @@ void TcScratch::carve(Arena &A, int64_t n, int32_t d, int splits_, int64_t n_pad
     tj = A.take<int32_t>((size_t)lists * n_pad * TC_TOPK);
     tu = A.take<float>((size_t)lists * n_pad);
     err = A.take<uint32_t>(4);
+    qctr = A.take<uint32_t>(4);
     setcnt = nmeans > 1 || n_pad_rows > 0 ? A.take<int32_t>((size_t)(nmeans > 0 ? nmeans : 1)) : nullptr;
     if (prune) {
         tcen = A.take<float>((size_t)nt * d);
@@ -1303,7 +1339,9 @@ cudaError_t tc_omega_screen(TcScratch &T, const float *Xp, int64_t n, int32_t d,
 #define ISO_SCREEN_LAUNCH(AKV)                                                                                    \
     k_sweep_tc<AKV, true, 64><<<grid, TC_THREADS, tc_smem(AKV), ISO_S(s)>>>(                                          \
         T.map_h, T.map_l, T.nrm, T.cnrm, T.rsq, T.tmax, T.tsq, acoef, bcoef, nullptr, T.n_pad, ntiles, kchunks, 1,   \
-        ditems, nit, nullptr, nullptr, nullptr, nullptr, nullptr, T.err, scr, tc_wait_limit(T), T.stall_test, 1, 0)
+        ditems, nit, nullptr, nullptr, nullptr, nullptr, nullptr, T.err, scr, tc_wait_limit(T), T.stall_test, 1, 0,  \
+        T.qctr)
+    if ((e = cudaMemsetAsync(T.qctr, 0, sizeof(uint32_t), s))) return e;
     if (kchunks == 1)
         ISO_SCREEN_LAUNCH(1);
     else if (kchunks == 2)
@@ -1441,7 +1479,9 @@ cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t 
     k_sweep_tc<AKV, false, CWV><<<grid, TC_THREADS, tc_smem(AKV), ISO_S(s)>>>(                                         \
         T.map_h, T.map_l, T.nrm, T.cnrm, T.rsq, T.tmax, T.tsq, acoef, bcoef, T.compp, T.n_pad, ntiles, kchunks,      \
         T.splits, wit, nwit, T.setcnt, S.counters, T.tv, T.tj, T.tu, T.err, ScreenArgs{},                        \
-        tc_wait_limit(T), T.stall_test, wit ? 1 : T.shard_world, wit ? 0 : T.shard_rank)
+        tc_wait_limit(T), T.stall_test, wit ? 1 : T.shard_world, wit ? 0 : T.shard_rank, T.qctr)
+        const cudaError_t me = cudaMemsetAsync(T.qctr, 0, sizeof(uint32_t), s);
+        if (me != cudaSuccess) return me;
         if (kchunks == 1 && T.resident) {
             if (T.cw == 32) ISO_SWEEP_LAUNCH(1, 32);
             else ISO_SWEEP_LAUNCH(1, 64);
@@ -1453,17 +1493,19 @@ cudaError_t tc_sweep_round(TcScratch &T, MstScratch &S, const float *X, int64_t 
             else ISO_SWEEP_LAUNCH(0, 64);
         }
 #undef ISO_SWEEP_LAUNCH
+        return cudaGetLastError();
     };
     if (pruned) {
         // near tiles first (candidate list slot 0); their candidates bound
         // each component's lightest edge, which decides the far items
         // (slots 1 .. PRUNE_SLOTS - 1)
-        sweep(T.items_a, ntiles);
-        cudaError_t pe = prune_far_items(T, S.comp, S.rowd2, S.rowj, n, S.counters, s);
+        cudaError_t pe = sweep(T.items_a, ntiles);
+        if (pe == cudaSuccess) pe = prune_far_items(T, S.comp, S.rowd2, S.rowj, n, S.counters, s);
+        if (pe == cudaSuccess) pe = sweep(T.items_b, (int64_t)ntiles * (PRUNE_SLOTS - 1));
         if (pe != cudaSuccess) return pe;
-        sweep(T.items_b, (int64_t)ntiles * (PRUNE_SLOTS - 1));
     } else {
-        sweep(T.items, T.nitems);
+        const cudaError_t pe = sweep(T.items, T.nitems);
+        if (pe != cudaSuccess) return pe;
     }
     // representation error of a centred point by BF16 hi + lo: 2^-18 relative
     // per element, plus the FP32 rounding of x - c (2^-24); 25 % headroom
