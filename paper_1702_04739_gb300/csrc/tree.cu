@@ -69,6 +69,7 @@ void TreeScratch::carve(Arena &A, int64_t n) {
     cflag = A.take<int32_t>(n + 1);
     cidx = A.take<int32_t>(n + 1);
     hist = A.take<uint32_t>(CAND_BUCKETS);
+    spart = A.take<double>(6 * STATS_BLOCKS);
     search = A.take<SearchState>(1);
     status = A.take<uint32_t>(1);
     hostinfo = A.take<int32_t>(16);
@@ -373,17 +374,19 @@ __device__ void init_search(SearchState *S, double phs, double phm, double wsum,
 
 // ------------------------------------------------------------ stats + search
 // Section 2.2 step 4 / Section 3.5: phi*, phi_* over tree edges, omega*,
-// omega_*, p*, p_* over the vertices; fixed reduction order (deterministic).
-__global__ void __launch_bounds__(1024) k_stats(const int32_t *__restrict__ parent, const double *__restrict__ phi,
-                                                const double *__restrict__ omega, const double *__restrict__ p,
-                                                int64_t n, SearchState *S, uint32_t *st) {
-    __shared__ double sh[6][1024];
+// omega_*, p*, p_* over the vertices; fixed reduction order (deterministic):
+// STATS_BLOCKS blocks reduce contiguous ranges (coalesced loads, a fixed
+// tree per block), then one block reduces their partials in block order.
+__global__ void __launch_bounds__(256) k_stats_part(const int32_t *__restrict__ parent, const double *__restrict__ phi,
+                                                    const double *__restrict__ omega, const double *__restrict__ p,
+                                                    int64_t n, double *__restrict__ spart, uint32_t *st) {
+    __shared__ double sh[6][256];
     const int tid = threadIdx.x;
-    int64_t chunk = ceil_div(n, 1024);
-    int64_t a = tid * chunk, b = min((int64_t)n, a + chunk);
+    const int64_t chunk = ceil_div(n, STATS_BLOCKS);
+    const int64_t a = (int64_t)blockIdx.x * chunk, b = min((int64_t)n, a + chunk);
     double fs = 0.0, fm = INFINITY, ws = 0.0, wm = INFINITY, ps = 0.0, pm = INFINITY;
     uint32_t bad = 0;
-    for (int64_t v = a; v < b; ++v) {
+    for (int64_t v = a + tid; v < b; v += 256) {
         double w = omega[v];
         if (!(w > 0.0) || isinf(w)) bad |= (isnan(w) || isinf(w)) ? DEV_NONFINITE : DEV_NEGATIVE;
         ws = ws + w;
@@ -402,7 +405,28 @@ __global__ void __launch_bounds__(1024) k_stats(const int32_t *__restrict__ pare
     if (bad) flag_status(st, bad);
     sh[0][tid] = fs; sh[1][tid] = fm; sh[2][tid] = ws; sh[3][tid] = wm; sh[4][tid] = ps; sh[5][tid] = pm;
     __syncthreads();
-    for (int s = 512; s > 0; s >>= 1) {
+    for (int s = 128; s > 0; s >>= 1) {
+        if (tid < s) {
+            sh[0][tid] = sh[0][tid] + sh[0][tid + s];
+            sh[1][tid] = fmin(sh[1][tid], sh[1][tid + s]);
+            sh[2][tid] = sh[2][tid] + sh[2][tid + s];
+            sh[3][tid] = fmin(sh[3][tid], sh[3][tid + s]);
+            sh[4][tid] = sh[4][tid] + sh[4][tid + s];
+            sh[5][tid] = fmin(sh[5][tid], sh[5][tid + s]);
+        }
+        __syncthreads();
+    }
+    if (tid < 6) spart[(int64_t)blockIdx.x * 6 + tid] = sh[tid][0];
+}
+
+__global__ void __launch_bounds__(STATS_BLOCKS) k_stats_final(const double *__restrict__ spart, int64_t n,
+                                                              SearchState *S) {
+    __shared__ double sh[6][STATS_BLOCKS];
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) sh[k][tid] = spart[(int64_t)tid * 6 + k];
+    __syncthreads();
+    for (int s = STATS_BLOCKS / 2; s > 0; s >>= 1) {
         if (tid < s) {
             sh[0][tid] = sh[0][tid] + sh[0][tid + s];
             sh[1][tid] = fmin(sh[1][tid], sh[1][tid + s]);
@@ -1264,7 +1288,8 @@ cudaError_t tree_search_and_label(TreeScratch &S, const double *phi_par, const d
     const TreeDev &T = S.T;
     const int64_t n = T.n;
     cudaError_t e;
-    k_stats<<<1, 1024, 0, ISO_S(s)>>>(T.parent, phi_par, omega, p, n, S.search, S.status);
+    k_stats_part<<<STATS_BLOCKS, 256, 0, ISO_S(s)>>>(T.parent, phi_par, omega, p, n, S.spart, S.status);
+    k_stats_final<<<1, STATS_BLOCKS, 0, ISO_S(s)>>>(S.spart, n, S.search);
     DpArgs A{n, T.parent, T.ch_off, T.ch_list, T.leaves, phi_par, omega, p};
     const unsigned grid = (unsigned)(num_sms() * 8);
     if ((e = cudaMemsetAsync(S.hist, 0, sizeof(uint32_t) * CAND_BUCKETS, s))) return e;

@@ -18,6 +18,8 @@ constexpr int CAND_SET_BUCKETS = 64;  // independent sets: buckets per set (a mu
 enum : uint8_t { DEC_DISCARD = 0, DEC_CUT = 1, DEC_JOIN = 2 };
 
 // Device-resident search state of reading S (bisection to the last bit).
+constexpr int STATS_BLOCKS = 128;   // blocks of the statistics' first level (fixed: deterministic sums)
+
 struct SearchState {
     unsigned long long lo_bits, hi_bits;
     int have_lo, have_hi, done, error;
@@ -71,6 +73,7 @@ struct TreeScratch {
     double *wh, *ph, *rat;
     int32_t *done, *head, *head2, *cflag, *cidx;
     uint32_t *hist;      // [CAND_BUCKETS] critical ratios per bucket of the bracket
+    double *spart;       // [STATS_BLOCKS][6] partial sums and minima of the statistics
     SearchState *search;
     uint32_t *status;
     int32_t *hostinfo;   // small device block read back by the host

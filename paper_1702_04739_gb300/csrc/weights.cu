@@ -964,17 +964,33 @@ __global__ void k_weights_reduce(const unsigned long long *__restrict__ nnbits, 
         return J < I ? J * T - J * (J - 1) / 2 + (I - J)      // item (J, I): r is a column
                      : I * T - I * (I - 1) / 2 + (J - I);     // item (I, J): r is a row
     };
+    // 64 tile pairs' flags per step (two loads in flight), then the kept
+    // pairs' partials RB at a time (their loads in flight together), added
+    // in ascending J as they come
+    constexpr int RB = 16;
     float h = 0.f, l = 0.f;
-    for (int64_t J0 = 0; J0 < T; J0 += 32) {
-        const int64_t Jl = J0 + lane;
-        const bool kept = Jl < T && flags[item(Jl)];
-        unsigned m = __ballot_sync(0xffffffffu, kept);
-        while (m) {
-            const int64_t J = J0 + (__ffs(m) - 1);
-            m &= m - 1u;
-            const int64_t w = item(J);
-            const float2 v = J < I ? cpart[w * WT + c] : rpart[w * WT + c];
-            dw_add(h, l, v.x, v.y);
+    for (int64_t J0 = 0; J0 < T; J0 += 64) {
+        const int64_t Ja = J0 + lane, Jb = J0 + 32 + lane;
+        const bool ka = Ja < T && flags[item(Ja)];
+        const bool kb = Jb < T && flags[item(Jb)];
+        unsigned ma = __ballot_sync(0xffffffffu, ka), mb = __ballot_sync(0xffffffffu, kb);
+        while (ma | mb) {                                   // (warp-uniform)
+            float2 v[RB];
+            int nv = 0;
+#pragma unroll
+            for (int q = 0; q < RB; ++q) {
+                if (ma | mb) {
+                    int64_t J;
+                    if (ma) { J = J0 + (__ffs(ma) - 1); ma &= ma - 1u; }
+                    else { J = J0 + 32 + (__ffs(mb) - 1); mb &= mb - 1u; }
+                    const int64_t w = item(J);
+                    v[q] = J < I ? cpart[w * WT + c] : rpart[w * WT + c];
+                    nv = q + 1;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < RB; ++q)
+                if (q < nv) dw_add(h, l, v[q].x, v[q].y);
         }
     }
     if (r >= n) return;
