@@ -385,6 +385,17 @@ struct GramArgs {
     int one_centre;              // 1: every row was centred on the same point (D = 0)
 };
 
+// 16-byte asynchronous global -> shared copies (the Gram tile of an item,
+// landing while the item's cross terms are computed)
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+constexpr int GR_GTILE_BYTES = WT * WT * (int)sizeof(float2);      // one item's Gram tile (32 KB)
+
 // Symmetric omega sweep: each unordered tile pair is screened in FP32 and,
 // if any of its terms can matter in either direction, evaluated once in
 // double-word arithmetic; the pair's d2 serves both omega_i and omega_j.
@@ -412,6 +423,7 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
     __shared__ float2 sC;                      // GRAM: |D|^2
     __shared__ float sMg[GRAM ? 2 * WT : 1];   // GRAM: |y|^2 + 2 |<y, D>| (+ |D|^2 for I): the parts' size
     __shared__ int sFb;                        // GRAM: cancelling pairs of the item
+    extern __shared__ __align__(16) float2 sG[];   // GRAM: the item's Gram tile, [WT][WT] double-words
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     if (tid < 64) tab[tid] = tabv.t[tid];
@@ -522,6 +534,20 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
             }
         }
         ++dw_items;
+        if constexpr (GRAM) {
+            // the item's Gram tile into shared memory (it lands during the
+            // cross terms; every reader of the previous tile is past the
+            // item's first barrier)
+            const int32_t gslot = ga.item_slot[w];
+            if (gslot >= 0) {
+                const float4 *src = reinterpret_cast<const float4 *>(
+                    ga.gbuf + ((size_t)(gslot >> 1) * (2 * WT) + (size_t)(gslot & 1) * WT) * WT);
+                float4 *dst = reinterpret_cast<float4 *>(sG);
+#pragma unroll
+                for (int q = 0; q < GR_GTILE_BYTES / 16 / TPB; ++q) cp_async16(dst + tid + q * TPB, src + tid + q * TPB);
+            }
+            cp_async_commit();
+        }
         // ---- double-word pass
         float S[4][4], E[4][4];
 #pragma unroll
@@ -618,11 +644,12 @@ k_weights_sym(const float *__restrict__ X, int64_t n, int32_t d, const float2 *_
                     sC = make_float2(h, l);
                 }
             }
+            cp_async_wait_all();
             __syncthreads();
             const int32_t slot = ga.item_slot[w];
             // (every kept item has a Gram block; should one lack it, its pairs
             // take the direct sums below)
-            const float2 *Gp = ga.gbuf + ((size_t)(slot >= 0 ? slot >> 1 : 0) * (2 * WT) + (size_t)(slot & 1) * WT) * WT;
+            const float2 *Gp = sG;
             const float2 C = sC;
             unsigned fb = 0u;                  // pairs whose Gram form cancels (bit 4i + j)
 #pragma unroll
@@ -1142,7 +1169,14 @@ cudaError_t weights_launch_sym(const float *X, int64_t n, int32_t d, double sigm
         if ((err = omega_gram_launch(*og, X, n, d, P.cen, P.tskip, status, wait_cycles, s, kev ? kev + 2 : nullptr)))
             return err;
         const GramArgs ga{og->gbuf, og->item_slot, og->yh, og->yl, og->rexp, og->rnorm, P.cen, og->one_centre};
-        k_weights_sym<false, true><<<grid, TPB, 0, ISO_S(s)>>>(X, n, d, P.shdw, is_h, is_l, tab, zskip, shrink, T,
+        static bool gattr = false;
+        if (!gattr) {
+            if ((err = cudaFuncSetAttribute(k_weights_sym<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            GR_GTILE_BYTES)))
+                return err;
+            gattr = true;
+        }
+        k_weights_sym<false, true><<<grid, TPB, GR_GTILE_BYTES, ISO_S(s)>>>(X, n, d, P.shdw, is_h, is_l, tab, zskip, shrink, T,
                                                                items, nullptr, nullptr, P.tskip, 1, P.flags, P.rpart,
                                                                P.cpart, tile_counts, sh ? sh->rank : 0,
                                                                sh ? sh->world : 1, ga);
