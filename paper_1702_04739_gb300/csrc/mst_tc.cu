@@ -410,6 +410,9 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
 #pragma unroll 1
                 for (int hf = 0; hf < 2; ++hf) {
                     float m0 = INFINITY, m1 = INFINITY;   // min over each block of n_j - 2 g (foreign columns)
+                    // (four independent chains per 32 columns, folded after: min is exact)
+                    float ma[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
+                    float mb[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
                     bool near = false;                   // SCREEN: a pair of this half within the cutoff
                     if (ok && mine) {
                         const int cofs = h * TC_BN + hf * 64;
@@ -432,7 +435,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
                                 if constexpr (SCREEN)
                                     near |= v <= fmaxf(Bi, __fadd_ru(__int_as_float(cmv[u]), Ci));
                                 else
-                                    min_foreign(m0, v, cmv[u], crow);
+                                    min_foreign(ma[u], v, cmv[u], crow);
                             }
                         }
 #pragma unroll
@@ -447,8 +450,12 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
                                 if constexpr (SCREEN)
                                     near |= v <= fmaxf(Bi, __fadd_ru(__int_as_float(cmv[u]), Ci));
                                 else
-                                    min_foreign(NB == 2 ? m1 : m0, v, cmv[u], crow);
+                                    min_foreign(NB == 2 ? mb[u] : ma[u], v, cmv[u], crow);
                             }
+                        }
+                        if constexpr (!SCREEN) {
+                            m0 = fminf(fminf(ma[0], ma[1]), fminf(ma[2], ma[3]));
+                            m1 = fminf(fminf(mb[0], mb[1]), fminf(mb[2], mb[3]));
                         }
                     }
                     if constexpr (SCREEN) {
@@ -484,9 +491,14 @@ k_sweep_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUte
                 if (++acc == TC_NACC) { acc = 0; acc_phase ^= 1u; }
             }
             if (!SCREEN) {
-                const size_t o = ((size_t)(2 * sp + h) * nrows + row) * TC_TOPK;
-#pragma unroll
-                for (int q = 0; q < TC_TOPK; ++q) { out_v[o + q] = bv[q]; out_j[o + q] = bj[q]; }
+                const size_t o = ((size_t)(2 * sp + h) * nrows + row) * TC_TOPK;   // (32-byte aligned)
+                static_assert(TC_TOPK == 8, "two 16-byte stores per list");
+                float4 *ov = reinterpret_cast<float4 *>(out_v + o);
+                int4 *oj = reinterpret_cast<int4 *>(out_j + o);
+                ov[0] = make_float4(bv[0], bv[1], bv[2], bv[3]);
+                ov[1] = make_float4(bv[4], bv[5], bv[6], bv[7]);
+                oj[0] = make_int4(bj[0], bj[1], bj[2], bj[3]);
+                oj[1] = make_int4(bj[4], bj[5], bj[6], bj[7]);
                 out_u[(size_t)(2 * sp + h) * nrows + row] = ubest;
             }
         }
