@@ -37,6 +37,7 @@ void TreeScratch::carve(Arena &A, int64_t n) {
     T.adj_key = A.take<uint64_t>(big);
     T.leaves = A.take<int32_t>(n);
     T.depth = A.take<int32_t>(n);
+    T.slot = A.take<int32_t>(n);
     kbuf = A.take<uint64_t>(big);
     vals = A.take<int32_t>(big);
     vbuf = A.take<int32_t>(big);
@@ -70,6 +71,7 @@ void TreeScratch::carve(Arena &A, int64_t n) {
     cidx = A.take<int32_t>(n + 1);
     hist = A.take<uint32_t>(CAND_BUCKETS);
     spart = A.take<double>(6 * STATS_BLOCKS);
+    phis = A.take<double>(n);
     search = A.take<SearchState>(1);
     status = A.take<uint32_t>(1);
     hostinfo = A.take<int32_t>(16);
@@ -236,6 +238,23 @@ __global__ void k_children(const uint64_t *__restrict__ keys, const int32_t *__r
                            const int32_t *__restrict__ fpos, int64_t M, int32_t *__restrict__ ch_list) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < M && flag[i]) ch_list[fpos[i]] = (int32_t)(keys[i] & 0xffffffffu);
+}
+
+// slot[v]: v's position in its parent's child list (the orientation root:
+// n - 1), a permutation of [0, n).  Algorithm 1's per-threshold states are
+// stored by slot, so a vertex's children are the contiguous slots of its
+// child range.
+__global__ void k_slots(const int32_t *__restrict__ ch_list, int64_t n, int32_t root, int32_t *__restrict__ slot) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n - 1) slot[ch_list[q]] = (int32_t)q;
+    else if (q == n - 1) slot[root] = (int32_t)q;
+}
+
+// phi of each child-list entry's parent edge, in child-list order
+__global__ void k_phi_slots(const int32_t *__restrict__ ch_list, const double *__restrict__ phi, int64_t m,
+                            double *__restrict__ phis) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < m) phis[q] = phi[ch_list[q]];
 }
 
 __global__ void k_ch_off(const int32_t *__restrict__ adj_off, const int32_t *__restrict__ fpos,
@@ -506,24 +525,31 @@ struct DpArgs {
     int64_t n;
     const int32_t *parent, *ch_off, *ch_list, *leaves;
     const double *phi, *omega, *p;
+    const int32_t *slot;           // v -> its child-list slot: the index of its states (one tree; null: by vertex)
+    const double *phis;            // phi of each slot's parent edge
 };
 
 // One warp walks from leaf v towards the root, deciding each vertex for the
 // 32 thresholds of its lanes; returns this lane's cuts.
 // Folds the children [c0, c1) of a vertex into (w, pv) for this lane's
 // threshold, in descending index: a joined child adds its omega-hat and
-// p-hat, any other its parent edge's phi.  With up to DP_FEW children their
-// indices are loaded in one round and their states in the next (a walk's
-// steps are latency-bound); more children are folded one by one.
+// p-hat, any other its parent edge's phi.  SLOT (one tree): the children's
+// states sit in their slots c0 .. c1 - 1, no child-index round trip;
+// otherwise (independent sets) they are indexed by vertex, through the child
+// list.  Up to DP_FEW children are loaded in one round (a walk's steps are
+// latency-bound), more are folded one by one.
 constexpr int DP_FEW = 4;
+template <bool SLOT>
 __device__ __forceinline__ void dp_fold_children(const DpArgs &A, int32_t c0, int32_t c1, int lane,
                                                  const uint8_t *__restrict__ dec, const double *__restrict__ wh,
                                                  const double *__restrict__ ph, double &w, double &pv) {
     const int32_t nc = c1 - c0;
     if (nc <= DP_FEW) {
         int32_t ch[DP_FEW];
+        if constexpr (!SLOT) {
 #pragma unroll
-        for (int q = 0; q < DP_FEW; ++q) ch[q] = q < nc ? A.ch_list[c0 + q] : 0;
+            for (int q = 0; q < DP_FEW; ++q) ch[q] = q < nc ? A.ch_list[c0 + q] : 0;
+        }
         uint8_t dcv[DP_FEW];
         double cw[DP_FEW], cp[DP_FEW], cf[DP_FEW];
 #pragma unroll
@@ -531,11 +557,11 @@ __device__ __forceinline__ void dp_fold_children(const DpArgs &A, int32_t c0, in
             dcv[q] = DEC_DISCARD;
             cw[q] = cp[q] = cf[q] = 0.0;
             if (q < nc) {
-                const size_t cl = (size_t)ch[q] * DP_LANES + lane;
+                const size_t cl = (size_t)(SLOT ? c0 + q : ch[q]) * DP_LANES + lane;
                 dcv[q] = ld_cg_u8(dec + cl);
                 cw[q] = ld_cg_f64(wh + cl);
                 cp[q] = ld_cg_f64(ph + cl);
-                cf[q] = A.phi[ch[q]];
+                cf[q] = SLOT ? A.phis[c0 + q] : A.phi[ch[q]];
             }
         }
 #pragma unroll
@@ -551,18 +577,24 @@ __device__ __forceinline__ void dp_fold_children(const DpArgs &A, int32_t c0, in
         }
     } else {
         for (int32_t q = c1 - 1; q >= c0; --q) {       // siblings in descending index
-            const int32_t c = A.ch_list[q];
+            const int32_t c = SLOT ? q : A.ch_list[q];
             const size_t cl = (size_t)c * DP_LANES + lane;
             const uint8_t dc = ld_cg_u8(dec + cl);
             if (dc == DEC_JOIN) {
                 w = __dadd_rn(w, ld_cg_f64(wh + cl));
                 pv = __dadd_rn(pv, ld_cg_f64(ph + cl));
             } else {
-                pv = __dadd_rn(pv, A.phi[c]);
+                pv = __dadd_rn(pv, SLOT ? A.phis[q] : A.phi[c]);
             }
         }
     }
 }
+
+// The hand-off between the warps of sibling walks is message passing: a
+// warp's states are written, then (release fence) its arrival is counted;
+// the last arrival (acquire fence) reads them all.  Acquire-release fences at
+// GPU scope order exactly that.
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 // One warp walks from leaf v towards the root, deciding each vertex for the
 // 32 thresholds of its lanes; returns this lane's cuts.
@@ -577,11 +609,12 @@ __device__ __forceinline__ int dp_walk_tree(const DpArgs &A, int32_t v, double N
     while (true) {
         const int32_t c0 = A.ch_off[v], c1 = A.ch_off[v + 1];
         const int32_t u = A.parent[v];
+        const int32_t sv = A.slot[v];
         double w = A.omega[v];
         double pv = A.p ? A.p[v] : 0.0;
         const double phv = A.phi[v];
         const int32_t uc0 = u >= 0 ? A.ch_off[u] : 0, uc1 = u >= 0 ? A.ch_off[u + 1] : 0;
-        dp_fold_children(A, c0, c1, lane, dec, wh, ph, w, pv);
+        dp_fold_children<true>(A, c0, c1, lane, dec, wh, ph, w, pv);
         const double fe = u >= 0 ? phv : 0.0;
         const double nw = __dmul_rn(N, w);
         const double fp = __dadd_rn(fe, pv);
@@ -595,20 +628,20 @@ __device__ __forceinline__ int dp_walk_tree(const DpArgs &A, int32_t v, double N
         } else {
             d = DEC_DISCARD;
         }
-        const size_t vl = (size_t)v * DP_LANES + lane;
+        const size_t vl = (size_t)sv * DP_LANES + lane;
         dec[vl] = d;
         wh[vl] = w;
         ph[vl] = pv;
         if (u < 0) break;
         const int32_t nu = uc1 - uc0;
         if (nu == 1) { v = u; continue; }          // only child: no one to wait for
-        __threadfence();
+        fence_acq_rel_gpu();
         __syncwarp();
         int old = 0;
         if (lane == 0) old = atomicAdd(done + u, 1);
         old = __shfl_sync(0xffffffffu, old, 0);
         if (old != nu - 1) break;                  // a sibling is still running
-        __threadfence();
+        fence_acq_rel_gpu();
         v = u;
     }
     return cuts;
@@ -640,7 +673,7 @@ __device__ __forceinline__ int dp_walk_sets(const DpArgs &A, int32_t v, double N
             ufe = A.phi[u];
         }
         double w = w0, pv = p0;
-        dp_fold_children(A, c0, c1, lane, dec, wh, ph, w, pv);
+        dp_fold_children<false>(A, c0, c1, lane, dec, wh, ph, w, pv);
         const double nw = __dmul_rn(N, w);
         const double fp = __dadd_rn(fe, pv);
         uint8_t d;
@@ -660,13 +693,13 @@ __device__ __forceinline__ int dp_walk_sets(const DpArgs &A, int32_t v, double N
         if (u < 0) break;
         const int32_t nu = uc1 - uc0;
         if (nu != 1) {                             // an only child has no one to wait for
-            __threadfence();
+            fence_acq_rel_gpu();
             __syncwarp();
             int old = 0;
             if (lane == 0) old = atomicAdd(done + u, 1);
             old = __shfl_sync(0xffffffffu, old, 0);
             if (old != nu - 1) break;              // a sibling is still running
-            __threadfence();
+            fence_acq_rel_gpu();
         }
         v = u;
         c0 = uc0;
@@ -820,7 +853,7 @@ __global__ void __launch_bounds__(256) k_cand_hist(DpArgs A, SearchState *S, con
     };
     const int64_t gs = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < A.n; v += gs) {
-        const size_t vl = (size_t)v * DP_LANES + L;
+        const size_t vl = (size_t)A.slot[v] * DP_LANES + L;
         const double w = wh[vl], pv = ph[vl];
         const int32_t u = A.parent[v];
         const double fe = u >= 0 ? A.phi[v] : 0.0;
@@ -930,16 +963,16 @@ __global__ void k_final_lane(SearchState *S) {
 }
 
 __global__ void k_final_from_lane(const SearchState *__restrict__ S, const int32_t *__restrict__ parent,
-                                  const double *__restrict__ phi, int64_t n, uint8_t *__restrict__ dec,
-                                  const double *__restrict__ wh, const double *__restrict__ ph,
-                                  double *__restrict__ rat) {
+                                  const double *__restrict__ phi, const int32_t *__restrict__ slot, int64_t n,
+                                  uint8_t *__restrict__ dec, const double *__restrict__ wh,
+                                  const double *__restrict__ ph, double *__restrict__ rat) {
     const int L = S->final_lane;
     if (L < 0) return;
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
-    const size_t vl = (size_t)v * DP_LANES + L;
+    const size_t s0 = (size_t)slot[v] * DP_LANES, vl = s0 + L;
     const uint8_t d = dec[vl];
-    dec[(size_t)v * DP_LANES] = d;
+    dec[s0] = d;
     if (d == DEC_CUT) {
         // the same operations as the pass at beta: fp = phi(e) + p-hat, fp / omega-hat
         const int32_t u = parent[v];
@@ -1069,10 +1102,10 @@ __global__ void k_search_update_sets(SearchState *SS, const int32_t *__restrict_
 __global__ void k_sets_left_init(uint32_t *left, int32_t nsets) { *left = (uint32_t)nsets; }
 
 // ------------------------------------------------------------ labels
-__global__ void k_head_init(const uint8_t *__restrict__ dec, const int32_t *__restrict__ parent, int64_t n,
-                            int32_t *__restrict__ head) {
+__global__ void k_head_init(const uint8_t *__restrict__ dec, const int32_t *__restrict__ slot,
+                            const int32_t *__restrict__ parent, int64_t n, int32_t *__restrict__ head) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v < n) head[v] = dec[(size_t)v * DP_LANES] == DEC_JOIN ? parent[v] : (int32_t)v;
+    if (v < n) head[v] = dec[(size_t)(slot ? slot[v] : (int32_t)v) * DP_LANES] == DEC_JOIN ? parent[v] : (int32_t)v;
 }
 
 __global__ void k_head_jump(const int32_t *__restrict__ hin, int32_t *__restrict__ hout, int64_t n) {
@@ -1080,24 +1113,25 @@ __global__ void k_head_jump(const int32_t *__restrict__ hin, int32_t *__restrict
     if (v < n) hout[v] = hin[hin[v]];
 }
 
-__global__ void k_cut_flags(const uint8_t *__restrict__ dec, const int32_t *__restrict__ bfs_pos, int64_t n,
-                            int32_t *__restrict__ cflag) {
+__global__ void k_cut_flags(const uint8_t *__restrict__ dec, const int32_t *__restrict__ slot,
+                            const int32_t *__restrict__ bfs_pos, int64_t n, int32_t *__restrict__ cflag) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v < n) cflag[n - 1 - bfs_pos[v]] = dec[(size_t)v * DP_LANES] == DEC_CUT ? 1 : 0;
+    if (v < n) cflag[n - 1 - bfs_pos[v]] = dec[(size_t)(slot ? slot[v] : (int32_t)v) * DP_LANES] == DEC_CUT ? 1 : 0;
 }
 
-__global__ void k_labels(const uint8_t *__restrict__ dec, const int32_t *__restrict__ bfs_pos,
+__global__ void k_labels(const uint8_t *__restrict__ dec, const int32_t *__restrict__ slot,
+                         const int32_t *__restrict__ bfs_pos,
                          const int32_t *__restrict__ head, const int32_t *__restrict__ cidx,
                          const double *__restrict__ rat, int64_t n, int32_t k, int32_t *__restrict__ labels,
                          uint8_t *__restrict__ residual, SearchState *S) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
     int32_t h = head[v];
-    int32_t c = dec[(size_t)h * DP_LANES] == DEC_CUT ? cidx[n - 1 - bfs_pos[h]] : -1;
+    int32_t c = dec[(size_t)slot[h] * DP_LANES] == DEC_CUT ? cidx[n - 1 - bfs_pos[h]] : -1;
     int32_t lab = (c >= 0 && c < k) ? c : -1;
     labels[v] = lab;
     residual[v] = lab < 0 ? 1 : 0;
-    if (dec[(size_t)v * DP_LANES] == DEC_CUT) {
+    if (dec[(size_t)slot[v] * DP_LANES] == DEC_CUT) {
         int32_t cv = cidx[n - 1 - bfs_pos[v]];
         if (cv < k) {
             atomicMax(&S->ik_bits, dbits(rat[v]));
@@ -1203,6 +1237,7 @@ cudaError_t orient_tree(TreeScratch &S, const int32_t *eu, const int32_t *ev, in
         k_fill_i32<<<1, 32, 0, ISO_S(s)>>>(T.adj_off, 2, 0);
         k_fill_i32<<<1, 32, 0, ISO_S(s)>>>(T.leaves, 1, 0);
         k_fill_i32<<<1, 32, 0, ISO_S(s)>>>(T.depth, 1, 0);
+        k_fill_i32<<<1, 32, 0, ISO_S(s)>>>(T.slot, 1, 0);
         k_fill_i32<<<1, 32, 0, ISO_S(s)>>>(S.pre, 1, 0);
         T.pre = S.pre;
         SearchState *SS = S.search;
@@ -1244,6 +1279,7 @@ cudaError_t orient_tree(TreeScratch &S, const int32_t *eu, const int32_t *ev, in
     if ((e = exclusive_scan_i32(S.flag, S.fpos, M, S.tmp32, s))) return e;
     k_scan_total<<<1, 1, 0, ISO_S(s)>>>(S.flag, S.fpos, M);
     k_children<<<blocks_for(M), TPB, 0, ISO_S(s)>>>(T.adj_key, S.flag, S.fpos, M, T.ch_list);
+    k_slots<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(T.ch_list, n, root, T.slot);
     k_ch_off<<<blocks_for(n + 1), TPB, 0, ISO_S(s)>>>(T.adj_off, S.fpos, n, T.ch_off);
     k_child_sizes<<<blocks_for(m), TPB, 0, ISO_S(s)>>>(T.ch_list, S.size, m, S.ssz);
     if ((e = exclusive_scan_i64(S.ssz, S.sx, m, S.tmp64, s))) return e;
@@ -1290,7 +1326,8 @@ cudaError_t tree_search_and_label(TreeScratch &S, const double *phi_par, const d
     cudaError_t e;
     k_stats_part<<<STATS_BLOCKS, 256, 0, ISO_S(s)>>>(T.parent, phi_par, omega, p, n, S.spart, S.status);
     k_stats_final<<<1, STATS_BLOCKS, 0, ISO_S(s)>>>(S.spart, n, S.search);
-    DpArgs A{n, T.parent, T.ch_off, T.ch_list, T.leaves, phi_par, omega, p};
+    k_phi_slots<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(T.ch_list, phi_par, n - 1, S.phis);
+    DpArgs A{n, T.parent, T.ch_off, T.ch_list, T.leaves, phi_par, omega, p, T.slot, S.phis};
     const unsigned grid = (unsigned)(num_sms() * 8);
     if ((e = cudaMemsetAsync(S.hist, 0, sizeof(uint32_t) * CAND_BUCKETS, s))) return e;
     for (int pass = 0; pass < DP_TREE_PASSES; ++pass) {
@@ -1306,20 +1343,21 @@ cudaError_t tree_search_and_label(TreeScratch &S, const double *phi_par, const d
     // Final call of Algorithm 1 at beta: Cut, eta and the set ratios (from the
     // last pass's lane at beta when it has one, else one more pass)
     k_final_lane<<<1, 32, 0, ISO_S(s)>>>(S.search);
-    k_final_from_lane<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.search, T.parent, phi_par, n, S.dec, S.wh, S.ph, S.rat);
+    k_final_from_lane<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.search, T.parent, phi_par, T.slot, n, S.dec, S.wh, S.ph,
+                                                           S.rat);
     if ((e = cudaMemsetAsync(S.done, 0, sizeof(int32_t) * n, s))) return e;
     k_dp_pass<<<grid, 256, 0, ISO_S(s)>>>(A, S.search, S.dec, S.wh, S.ph, S.done, S.rat, 1);
     // Algorithm 4: eta by pointer jumping, exclusive scan over Cut.
-    k_head_init<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.dec, T.parent, n, S.head);
+    k_head_init<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.dec, T.slot, T.parent, n, S.head);
     int32_t *ha = S.head, *hb = S.head2;
     const int Ln = log2_ceil(n) + 1;
     for (int it = 0; it < Ln; ++it) {
         k_head_jump<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(ha, hb, n);
         int32_t *t = ha; ha = hb; hb = t;
     }
-    k_cut_flags<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.dec, T.bfs_pos, n, S.cflag);
+    k_cut_flags<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.dec, T.slot, T.bfs_pos, n, S.cflag);
     if ((e = exclusive_scan_i32(S.cflag, S.cidx, n, S.tmp32, s))) return e;
-    k_labels<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.dec, T.bfs_pos, ha, S.cidx, S.rat, n, k, labels, residual, S.search);
+    k_labels<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.dec, T.slot, T.bfs_pos, ha, S.cidx, S.rat, n, k, labels, residual, S.search);
     k_finish<<<1, 32, 0, ISO_S(s)>>>(S.search, k, i_k, S.status);
     return cudaGetLastError();
 }
@@ -1334,7 +1372,9 @@ cudaError_t tree_search_and_label_sets(TreeScratch &S, int32_t nsets, const int6
     // the virtual root is never decided: mark it discarded (its own head)
     if ((e = cudaMemsetAsync(S.dec + (size_t)nv * DP_LANES, DEC_DISCARD, DP_LANES, s))) return e;
     k_stats_sets<<<(unsigned)nsets, 256, 0, ISO_S(s)>>>(T.parent, phi_par, omega, p, offs, SS, S.status);
-    DpArgs A{n, T.parent, T.ch_off, T.ch_list, T.leaves, phi_par, omega, p};
+    // (states by vertex: the sets' many short walks and per-vertex sweeps
+    // read them in vertex order)
+    DpArgs A{n, T.parent, T.ch_off, T.ch_list, T.leaves, phi_par, omega, p, nullptr, nullptr};
     // one full wave: every warp takes an equal run of leaves, so a partial
     // second wave would leave SMs idle for half its length
     static int dp_occ = 0;
@@ -1360,14 +1400,14 @@ cudaError_t tree_search_and_label_sets(TreeScratch &S, int32_t nsets, const int6
     }
     if ((e = cudaMemsetAsync(S.done, 0, sizeof(int32_t) * n, s))) return e;
     k_dp_pass_sets<<<grid, 256, 0, ISO_S(s)>>>(A, S.search, SS, vset, S.dec, S.wh, S.ph, S.done, S.rat, 1, left);
-    k_head_init<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.dec, T.parent, n, S.head);
+    k_head_init<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.dec, nullptr, T.parent, n, S.head);
     int32_t *ha = S.head, *hb = S.head2;
     const int Ln = log2_ceil(n) + 1;
     for (int it = 0; it < Ln; ++it) {
         k_head_jump<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(ha, hb, n);
         int32_t *t = ha; ha = hb; hb = t;
     }
-    k_cut_flags<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.dec, T.bfs_pos, n, S.cflag);
+    k_cut_flags<<<blocks_for(n), TPB, 0, ISO_S(s)>>>(S.dec, nullptr, T.bfs_pos, n, S.cflag);
     if ((e = exclusive_scan_i32(S.cflag, S.cidx, n, S.tmp32, s))) return e;
     k_labels_sets<<<blocks_for(nv), TPB, 0, ISO_S(s)>>>(S.dec, T.bfs_pos, ha, S.cidx, S.rat, nv, vset, offs, ks, labels,
                                                         residual, SS);

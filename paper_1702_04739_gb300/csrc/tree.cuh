@@ -54,6 +54,7 @@ struct TreeDev {
     int32_t *leaves;     // [n]
     int32_t *depth;      // [n]
     int32_t *pre;        // [n] preorder rank with children in ascending index (set by orient_tree)
+    int32_t *slot;       // [n] position in the parent's child list (the root: n - 1), set by orient_tree
 };
 
 struct TreeScratchSizes;
@@ -74,6 +75,7 @@ struct TreeScratch {
     int32_t *done, *head, *head2, *cflag, *cidx;
     uint32_t *hist;      // [CAND_BUCKETS] critical ratios per bucket of the bracket
     double *spart;       // [STATS_BLOCKS][6] partial sums and minima of the statistics
+    double *phis;        // [n] phi of each child-list slot's parent edge
     SearchState *search;
     uint32_t *status;
     int32_t *hostinfo;   // small device block read back by the host
