@@ -484,7 +484,9 @@ isoclust_status isoclust_set_omega_gram(int32_t mode);
  * never two tiles wholly inside one component.  The tree is the same edge
  * for edge.  mode -1 (the default): pruned for n >= 65,536 and d <= 256;
  * 1: whenever the tensor-core sweep runs a one-set call of 64 points or
- * more and at most 256 dimensions, a multiple of 4; 0: never.
+ * more and at most 256 dimensions, a multiple of 4; 0: never.  Either way
+ * X must start on a 16-byte boundary (the order's kernels read rows by 16
+ * bytes); otherwise the call runs unpruned.  Not for sharded calls.
  * Process-wide; other values -> INVALID_ARG. */
 isoclust_status isoclust_set_mst_prune(int32_t mode);
 
