@@ -62,6 +62,15 @@ L2_NOTE = "flushed by a 256 MiB write before every step (inside the timed region
 # kernel as it stands, from a one-pass ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum); workloads without a capture report null
 OMEGA_TRAFFIC: dict[str, int] = {}
+# DRAM bytes per unit of the two omega kernels with the Gram on the tensor cores, from their
+# full-section capture at 40,000 x 64 (profiles/k_weights_sym_gram_k_oz_gram_blobs_n40k_d64.md):
+# the sweep 1.504621 + 0.045260 GB over 42,831 kept 64 x 64 tile pairs (their 32 KB Gram tiles,
+# mostly), the Gram kernel 0.236092 + 1.348661 GB over 22,524 blocks of 128 x 64 (its G written).
+# Both grow with those units at this row length; other row lengths read other plane and row
+# bytes, so the line's traffic is null there.
+OMEGA_GRAM_TRAFFIC_D = 64
+OMEGA_SWEEP_BYTES_PER_TILE_PAIR = (1.504621e9 + 0.045260e9) / 42831
+OMEGA_GRAM_BYTES_PER_BLOCK = (0.236092e9 + 1.348661e9) / 22524
 FP32_LANES_PER_SM = 128
 FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64, nominal (context for the FP64-equivalent rate)
 
@@ -253,15 +262,21 @@ def omega_gram_roofline(prof, peaks, src, alu_peak, sms, sweep_ms, items, d, alg
     cross = 0.0 if d >= 1024 else items * (128.0 * 14.0 * d + 12.0 * d)
     sw_ops = items * 4096.0 * 155.0 + cross + direct * (18.75 * d + 60.0)
     sw = sw_ops / (sweep_ms / 1000.0) / 1e12 if sweep_ms > 0 else 0.0
+    scaled = d == OMEGA_GRAM_TRAFFIC_D
     gram_k = {"kernel": "k_oz_gram (omega Gram, tcgen05 BF16 digit planes)", "bound": "tensor", "kernel_ms": g_ms,
-              "achieved": tc, "peak": bf16, "unit": "TFLOP/s", "frac": tc / bf16, "blocks": blocks}
+              "achieved": tc, "peak": bf16, "unit": "TFLOP/s", "frac": tc / bf16, "blocks": blocks,
+              "traffic": blocks * OMEGA_GRAM_BYTES_PER_BLOCK if scaled else None}
     sweep_k = {"kernel": "k_weights_sym<GRAM> (omega terms from the Gram, double-word FP32)", "bound": "alu",
                "kernel_ms": sweep_ms, "achieved": sw, "peak": alu_peak, "unit": "TFLOP/s", "frac": sw / alu_peak,
-               "direct_pairs": direct, "direct_share": direct / max(1.0, items * 4096.0)}
+               "direct_pairs": direct, "direct_share": direct / max(1.0, items * 4096.0),
+               "traffic": items * OMEGA_SWEEP_BYTES_PER_TILE_PAIR if scaled else None}
     top, other = (gram_k, sweep_k) if g_ms >= sweep_ms else (sweep_k, gram_k)
     both_ms = g_ms + sweep_ms
     alg = alg_flop / (both_ms / 1000.0) / 1e12
-    out = dict(top, traffic=None,
+    out = dict(top,
+               traffic_note=("DRAM bytes per launch: the 40,000 x 64 full-section capture's bytes per kept tile pair "
+                             "(sweep) or per block (Gram), times this launch's count" if scaled else
+                             "no capture at this row length"),
                note=f"omega's Gram on the tensor cores: the Gram kernel {g_ms:.2f} ms ({blocks} blocks of 128 x 64, 34 "
                     f"digit-plane MMAs per 16 dimensions, executed flop over the measured BF16 peak, {src}) and the "
                     f"sweep reading it {sweep_ms:.2f} ms (FP32-pipe instructions of the algorithm as built - 155 per "

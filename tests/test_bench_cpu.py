@@ -51,3 +51,20 @@ def test_reference_arm_moons_is_measured_whole():
     line = _run(["--workload", "moons_n20k_d128", "--n", "600", "--steps", "2", "--warmup", "1"])
     _check(line, "moons_n20k_d128")
     assert line["config"]["n"] == 600 and "not scaled" in line["cpu_baseline"]["sample"]
+
+
+def test_omega_gram_roofline_reports_scaled_traffic():
+    """The Gram-path roofline (host arithmetic only): the slower kernel is the
+    line's, its DRAM traffic is the capture's bytes per unit times the run's
+    units at the captured row length, and null at another one."""
+    sys.path.insert(0, ROOT)
+    import bench
+    prof = [{"omega_gram_ms": 7.5, "omega_gram_blocks": 146222, "omega_gram_direct_pairs": 30836874}]
+    peaks = {"bf16_tflops": 1940.5}
+    r = bench.omega_gram_roofline(prof, peaks, "measured", 40.27, 152, 24.5, 285302, 64, 7.65e11)
+    assert r["kernel"].startswith("k_weights_sym") and r["bound"] == "alu"
+    assert r["traffic"] == pytest.approx(285302 * (1.504621e9 + 0.045260e9) / 42831)
+    assert r["other_kernel"]["traffic"] == pytest.approx(146222 * (0.236092e9 + 1.348661e9) / 22524)
+    assert 0.0 < r["frac"] < 1.0 and r["other_kernel"]["bound"] == "tensor"
+    r2 = bench.omega_gram_roofline(prof, peaks, "measured", 40.27, 152, 24.5, 285302, 128, 7.65e11)
+    assert r2["traffic"] is None and r2["other_kernel"]["traffic"] is None
