@@ -22,7 +22,7 @@
 
 namespace iso {
 
-// Scratch of the tree stage for n <= ISOCLUST_NOALLOC_MAX_N (12 MiB measured,
+// Scratch of the tree stage for n <= ISOCLUST_NOALLOC_MAX_N (12.2 MiB measured,
 // 13 MiB reserved).  Host code must not pass this name to a kernel: on the
 // host it is only a stand-in for the symbol.  Its device address is looked
 // up with cudaGetSymbolAddress below.
